@@ -1,0 +1,175 @@
+"""FP64 CPU oracle for OMP / CLOMP (test infrastructure, not the product).
+
+Only the tests, ``__graft_entry__.smoke()`` and the benchmark's CPU-baseline
+leg may import this package.  It compiles ``cs_oracle.c`` with gcc on first
+use (or via :func:`build`) and wraps it with ctypes.  It imports nothing from
+the GPU package and the GPU package imports nothing from here.
+
+Every function returns float64 results; per-iteration arrays come back as
+(B, k) numpy arrays (row b = signal b, in selection order).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "cs_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "libcs_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+# -ffp-contract=off keeps the arithmetic identical on x86-64 and aarch64 hosts
+CFLAGS = ["-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off"]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (idempotent)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + f".tmp{os.getpid()}"
+        subprocess.check_call(["gcc", *CFLAGS, _SRC, "-o", tmp, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            P = ctypes.POINTER
+            d, i32 = ctypes.c_double, ctypes.c_int32
+            pd, pi = P(d), P(i32)
+            L.cs_oracle_lstsq.argtypes = [ctypes.c_int, ctypes.c_int, pd, ctypes.c_int, pd, pd, pd]
+            L.cs_oracle_lstsq.restype = ctypes.c_int
+            L.cs_oracle_clfit_loss_grad.argtypes = [pd, ctypes.c_int, ctypes.c_int, pi, ctypes.c_int,
+                                                    pd, pd, pd, pd, pd]
+            L.cs_oracle_clfit_loss_grad.restype = None
+            L.cs_oracle_clfit_adam.argtypes = [pd, ctypes.c_int, ctypes.c_int, pi, ctypes.c_int, pd,
+                                               pd, pd, pd, pi, ctypes.c_int, d, d, d, d]
+            L.cs_oracle_clfit_adam.restype = None
+            L.cs_oracle_omp.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, d, ctypes.c_int, pi, pd, pi, pd, pi,
+                                        pd, pd, pd, ctypes.c_int]
+            L.cs_oracle_omp.restype = ctypes.c_int
+            L.cs_oracle_clomp.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int,
+                                          ctypes.c_int, ctypes.c_int, d, ctypes.c_int, ctypes.c_int, d, d,
+                                          d, d, ctypes.c_int, pi, pd, pi, pd, pi, pd, pd, pd, ctypes.c_int]
+            L.cs_oracle_clomp.restype = ctypes.c_int
+            L.cs_oracle_max_threads.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a, ct):
+    return a.ctypes.data_as(ctypes.POINTER(ct))
+
+
+def _f64F(a):
+    return np.asfortranarray(np.asarray(a, dtype=np.float64))
+
+
+def max_threads() -> int:
+    return int(lib().cs_oracle_max_threads())
+
+
+def lstsq(As, y):
+    """min ||y - As z|| by Householder QR.  Returns (z, status) with status 3
+    when the last column is dependent."""
+    As = _f64F(As)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    m, t = As.shape
+    z = np.zeros(t)
+    work = np.zeros(m * t + m)
+    st = lib().cs_oracle_lstsq(m, t, _p(As, ctypes.c_double), m, _p(y, ctypes.c_double),
+                               _p(z, ctypes.c_double), _p(work, ctypes.c_double))
+    return z, st
+
+
+def clfit_loss_grad(A, support, s_S, y):
+    """L = 1/2||y - A_S s_S||^2 and its gradient -(A_S^T r); returns (L, grad, r)."""
+    A = _f64F(A)
+    S = np.ascontiguousarray(support, dtype=np.int32)
+    s = np.ascontiguousarray(s_S, dtype=np.float64)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    m = A.shape[0]
+    loss = np.zeros(1)
+    g = np.zeros(len(S))
+    r = np.zeros(m)
+    lib().cs_oracle_clfit_loss_grad(_p(A, ctypes.c_double), m, m, _p(S, ctypes.c_int32), len(S),
+                                    _p(s, ctypes.c_double), _p(y, ctypes.c_double),
+                                    _p(loss, ctypes.c_double), _p(g, ctypes.c_double),
+                                    _p(r, ctypes.c_double))
+    return float(loss[0]), g, r
+
+
+def clfit_adam(A, support, y, s_S, mom, vel, tau, steps, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8):
+    """Run `steps` Adam steps of the CL fit in place-free form; returns
+    (s_S, mom, vel, tau)."""
+    A = _f64F(A)
+    S = np.ascontiguousarray(support, dtype=np.int32)
+    y = np.ascontiguousarray(y, dtype=np.float64)
+    s = np.array(s_S, dtype=np.float64)
+    mo = np.array(mom, dtype=np.float64)
+    ve = np.array(vel, dtype=np.float64)
+    ta = np.array([tau], dtype=np.int32)
+    m = A.shape[0]
+    lib().cs_oracle_clfit_adam(_p(A, ctypes.c_double), m, m, _p(S, ctypes.c_int32), len(S),
+                               _p(y, ctypes.c_double), _p(s, ctypes.c_double),
+                               _p(mo, ctypes.c_double), _p(ve, ctypes.c_double),
+                               _p(ta, ctypes.c_int32), int(steps), lr, beta1, beta2, eps)
+    return s, mo, ve, int(ta[0])
+
+
+def _outputs(B, k):
+    return dict(support=np.zeros((B, k), np.int32), coef=np.zeros((B, k)),
+                n_iter=np.zeros(B, np.int32), res_norm=np.zeros(B), status=np.zeros(B, np.int32),
+                top1=np.zeros((B, k)), top2=np.zeros((B, k)), res_hist=np.zeros((B, k)))
+
+
+def omp(A, Y, k, tol=0.0, max_iter=None, nthreads=0):
+    """Plain OMP for every column of Y.  Returns a dict of outputs."""
+    A = _f64F(A)
+    Y = _f64F(Y if np.ndim(Y) == 2 else np.reshape(Y, (-1, 1)))
+    m, n = A.shape
+    B = Y.shape[1]
+    max_iter = k if max_iter is None else max_iter
+    o = _outputs(B, k)
+    rc = lib().cs_oracle_omp(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B, k,
+                             float(tol), int(max_iter), _p(o["support"], ctypes.c_int32),
+                             _p(o["coef"], ctypes.c_double), _p(o["n_iter"], ctypes.c_int32),
+                             _p(o["res_norm"], ctypes.c_double), _p(o["status"], ctypes.c_int32),
+                             _p(o["top1"], ctypes.c_double), _p(o["top2"], ctypes.c_double),
+                             _p(o["res_hist"], ctypes.c_double), int(nthreads))
+    if rc != 0:
+        raise ValueError("cs_oracle_omp: invalid arguments")
+    return o
+
+
+def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
+          reset_adam=False, nthreads=0):
+    """CLOMP (structure 1, Adam) for every column of Y.  Returns a dict."""
+    A = _f64F(A)
+    Y = _f64F(Y if np.ndim(Y) == 2 else np.reshape(Y, (-1, 1)))
+    m, n = A.shape
+    B = Y.shape[1]
+    max_iter = k if max_iter is None else max_iter
+    o = _outputs(B, k)
+    rc = lib().cs_oracle_clomp(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B, k,
+                               float(tol), int(max_iter), int(steps), float(lr), float(beta1),
+                               float(beta2), float(eps), int(bool(reset_adam)),
+                               _p(o["support"], ctypes.c_int32), _p(o["coef"], ctypes.c_double),
+                               _p(o["n_iter"], ctypes.c_int32), _p(o["res_norm"], ctypes.c_double),
+                               _p(o["status"], ctypes.c_int32), _p(o["top1"], ctypes.c_double),
+                               _p(o["top2"], ctypes.c_double), _p(o["res_hist"], ctypes.c_double),
+                               int(nthreads))
+    if rc != 0:
+        raise ValueError("cs_oracle_clomp: invalid arguments")
+    return o

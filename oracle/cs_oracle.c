@@ -1,0 +1,335 @@
+/*
+ * cs_oracle.c -- plain, slow, FP64 CPU oracle for OMP and CLOMP.
+ *
+ * TEST INFRASTRUCTURE, NOT PART OF THE PRODUCT.  Only the tests, the smoke
+ * check and the benchmark's CPU-baseline leg may load this library.  It shares
+ * no code, header, table or helper with the CUDA implementation.
+ *
+ * What it computes (arXiv 2501.11592):
+ *   - Problem: y = A s + xi (Eq. 1), columns of Y = A S + xi share A (Eq. 3);
+ *     solve min ||s||_0 s.t. ||A s - y||_2 < eps (Eq. 2).
+ *   - OMP (Methods, Table "s forward block", row OMP; Methods "Coefficients
+ *     learning on OMP"): per iteration correlate A^T r, take the position of
+ *     the largest |A^T r| among atoms not yet selected, fit the coefficients on
+ *     the selected columns by least squares (the pinv of A(:,Mask)), update
+ *     the residual.  The least-squares fit here is a Householder QR of A_S
+ *     recomputed from scratch at every iteration (a different algorithm from
+ *     the GPU's incremental Cholesky).
+ *   - CLOMP, structure 1 (Methods "Coefficients learning on OMP"): the same
+ *     selection, but s (n learnable parameters) is masked by the OR-accumulated
+ *     Mask, y' = A (s .* Mask) is formed, and s is learned by back-propagating
+ *     the residual loss; the optimizer is Adam.
+ *
+ * Readings of points the paper leaves open (each one is also listed in the
+ * design notes):
+ *   - one atom per iteration (argmax), lowest index on exact ties;
+ *   - already-selected atoms are excluded from the argmax;
+ *   - residual r = y - A s (the sign of Eq. 2's r does not change |A^T r|);
+ *   - residual loss L = 1/2 ||y - A (s .* Mask)||_2^2, gradient
+ *     -(A^T r) .* Mask;
+ *   - Adam with one state (m, v) and one step counter tau for the whole solve,
+ *     PyTorch/Paddle update rule s -= lr * (m/(1-b1^tau)) / (sqrt(v/(1-b2^tau)) + eps);
+ *     optional reset of (m, v, tau) at every iteration;
+ *   - s starts at zero; stop when |S| = k, ||r||_2 <= tol, or after max_iter
+ *     iterations (R of the paper);
+ *   - an atom whose QR pivot satisfies R_tt^2 <= 1e-12 ||a||^2 is dependent:
+ *     it is not added and the signal stops (status 3);
+ *   - a non-finite measurement stops the signal before any iteration (status 4).
+ *
+ * Per-signal status codes: 0 reached k, 1 reached tol, 2 hit max_iter,
+ * 3 dependent atom, 4 non-finite input.
+ *
+ * Layouts: A is m x n column-major with leading dimension lda; Y is m x B with
+ * leading dimension ldy; per-iteration outputs (support, coef, top1, top2,
+ * res_hist) are k x B column-major, i.e. signal b owns [b*k, b*k + k).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ST_K 0
+#define ST_TOL 1
+#define ST_MAXIT 2
+#define ST_DEP 3
+#define ST_NONFINITE 4
+
+static double dot(const double* a, const double* b, int m) {
+    double s = 0.0;
+    for (int i = 0; i < m; ++i) s += a[i] * b[i];
+    return s;
+}
+
+static double nrm2(const double* a, int m) { return sqrt(dot(a, a, m)); }
+
+/*
+ * Least squares min_z ||y - As z||_2 for As (m x t, column-major, leading
+ * dimension lda) by Householder QR: As = Q R, z = R^{-1} (Q^T y)[0:t].
+ * Returns 0, or 3 when the last column is dependent on the others
+ * (R_tt^2 <= 1e-12 ||a_t||^2).  work must hold m*t + m doubles.
+ */
+int cs_oracle_lstsq(int m, int t, const double* As, int lda, const double* y,
+                    double* z, double* work) {
+    double* Rm = work;            /* m x t copy, overwritten by R and the reflectors */
+    double* qty = work + (size_t)m * t;
+    for (int j = 0; j < t; ++j) memcpy(Rm + (size_t)j * m, As + (size_t)j * lda, sizeof(double) * m);
+    memcpy(qty, y, sizeof(double) * m);
+    double last_norm = nrm2(As + (size_t)(t - 1) * lda, m);
+    for (int j = 0; j < t; ++j) {
+        double* col = Rm + (size_t)j * m;
+        if (j >= m) return ST_DEP;
+        double norm = 0.0;
+        for (int i = j; i < m; ++i) norm += col[i] * col[i];
+        norm = sqrt(norm);
+        if (norm == 0.0) {
+            if (j == t - 1) return ST_DEP;
+            continue;
+        }
+        double alpha = (col[j] >= 0.0) ? -norm : norm;   /* R_jj */
+        /* reflector v = x - alpha e_j stored in place below the diagonal */
+        double v0 = col[j] - alpha;
+        double vtv = v0 * v0;
+        for (int i = j + 1; i < m; ++i) vtv += col[i] * col[i];
+        col[j] = v0;
+        /* apply H = I - 2 v v^T / (v^T v) to the remaining columns and to y */
+        for (int q = j + 1; q < t; ++q) {
+            double* c = Rm + (size_t)q * m;
+            double s = 0.0;
+            for (int i = j; i < m; ++i) s += col[i] * c[i];
+            s = 2.0 * s / vtv;
+            for (int i = j; i < m; ++i) c[i] -= s * col[i];
+        }
+        {
+            double s = 0.0;
+            for (int i = j; i < m; ++i) s += col[i] * qty[i];
+            s = 2.0 * s / vtv;
+            for (int i = j; i < m; ++i) qty[i] -= s * col[i];
+        }
+        col[j] = alpha;   /* keep R_jj on the diagonal (reflector no longer needed) */
+    }
+    {
+        double rtt = Rm[(size_t)(t - 1) * m + (t - 1)];
+        if (rtt * rtt <= 1e-12 * last_norm * last_norm) return ST_DEP;
+    }
+    /* back substitution R z = (Q^T y)[0:t] */
+    for (int i = t - 1; i >= 0; --i) {
+        double s = qty[i];
+        for (int q = i + 1; q < t; ++q) s -= Rm[(size_t)q * m + i] * z[q];
+        z[i] = s / Rm[(size_t)i * m + i];
+    }
+    return 0;
+}
+
+/* r = y - sum_q a_{S_q} x_q  (Eq. 2's residual with the sign flipped) */
+static void residual(const double* A, int m, int lda, const int32_t* S, int t,
+                     const double* x, const double* y, double* r) {
+    for (int i = 0; i < m; ++i) r[i] = y[i];
+    for (int q = 0; q < t; ++q) {
+        const double* a = A + (size_t)S[q] * lda;
+        for (int i = 0; i < m; ++i) r[i] -= a[i] * x[q];
+    }
+}
+
+/*
+ * Residual injection + selection: c = A^T r over all n atoms, then the
+ * position of the largest |c_j| among j not in S (lowest index on ties).
+ * Writes |c| of the best and of the runner-up (or -1 if there is none).
+ */
+static int select_atom(const double* A, int m, int n, int lda, const double* r,
+                       const unsigned char* inS, double* top1, double* top2) {
+    int best = -1;
+    double b1 = -1.0, b2 = -1.0;
+    for (int j = 0; j < n; ++j) {
+        if (inS[j]) continue;
+        double a = fabs(dot(A + (size_t)j * lda, r, m));
+        if (a > b1) { b2 = b1; b1 = a; best = j; }
+        else if (a > b2) { b2 = a; }
+    }
+    *top1 = b1;
+    *top2 = b2;
+    return best;
+}
+
+static int all_finite(const double* y, int m) {
+    for (int i = 0; i < m; ++i) if (!isfinite(y[i])) return 0;
+    return 1;
+}
+
+static void omp_one(const double* A, int m, int n, int lda, const double* y, int k,
+                    double tol, int max_iter, int32_t* support, double* coef,
+                    int32_t* n_iter, double* res_norm, int32_t* status,
+                    double* top1, double* top2, double* res_hist) {
+    for (int q = 0; q < k; ++q) { support[q] = -1; coef[q] = 0.0; top1[q] = -1.0; top2[q] = -1.0; res_hist[q] = NAN; }
+    if (!all_finite(y, m)) { *n_iter = 0; *res_norm = NAN; *status = ST_NONFINITE; return; }
+    double* r = (double*)malloc(sizeof(double) * m);
+    double* As = (double*)malloc(sizeof(double) * (size_t)m * k);
+    double* z = (double*)malloc(sizeof(double) * k);
+    double* work = (double*)malloc(sizeof(double) * ((size_t)m * k + m));
+    unsigned char* inS = (unsigned char*)calloc(n, 1);
+    memcpy(r, y, sizeof(double) * m);
+    double rho = nrm2(r, m);
+    int iters = k < max_iter ? k : max_iter;
+    int t = 0, st = -1;
+    if (rho <= tol) st = ST_TOL;
+    while (st < 0 && t < iters) {
+        int j = select_atom(A, m, n, lda, r, inS, &top1[t], &top2[t]);
+        if (j < 0) { st = ST_MAXIT; break; }
+        memcpy(As + (size_t)t * m, A + (size_t)j * lda, sizeof(double) * m);
+        if (cs_oracle_lstsq(m, t + 1, As, m, y, z, work) != 0) { st = ST_DEP; top1[t] = top2[t] = -1.0; break; }
+        support[t] = j;
+        inS[j] = 1;
+        ++t;
+        for (int q = 0; q < t; ++q) coef[q] = z[q];
+        residual(A, m, lda, support, t, coef, y, r);
+        rho = nrm2(r, m);
+        res_hist[t - 1] = rho;
+        if (rho <= tol) st = ST_TOL;
+    }
+    if (st < 0) st = (t == k) ? ST_K : ST_MAXIT;
+    *n_iter = t;
+    *res_norm = rho;
+    *status = st;
+    free(r); free(As); free(z); free(work); free(inS);
+}
+
+/*
+ * Loss and gradient of the CL s-forward branch restricted to the support:
+ *   r = y - A (s .* Mask),  L = 1/2 ||r||^2,  grad_q = -(a_{S_q})^T r.
+ * (Unmasked coordinates have zero gradient because of the mask.)
+ */
+void cs_oracle_clfit_loss_grad(const double* A, int m, int lda, const int32_t* S, int t,
+                               const double* s_S, const double* y, double* loss,
+                               double* grad_S, double* r_out) {
+    double* r = r_out ? r_out : (double*)malloc(sizeof(double) * m);
+    residual(A, m, lda, S, t, s_S, y, r);
+    if (loss) *loss = 0.5 * dot(r, r, m);
+    if (grad_S)
+        for (int q = 0; q < t; ++q) grad_S[q] = -dot(A + (size_t)S[q] * lda, r, m);
+    if (!r_out) free(r);
+}
+
+/*
+ * `steps` Adam steps on L(s_S) = 1/2 ||y - A_S s_S||^2 (the CL coefficient
+ * fit).  mom, vel and *tau carry the optimizer state between calls.
+ * Coordinates outside the mask are not touched: their gradient is zero, so
+ * their moments stay at zero and their Adam step is exactly zero.
+ */
+void cs_oracle_clfit_adam(const double* A, int m, int lda, const int32_t* S, int t,
+                          const double* y, double* s_S, double* mom, double* vel,
+                          int32_t* tau, int steps, double lr, double beta1,
+                          double beta2, double eps) {
+    double* r = (double*)malloc(sizeof(double) * m);
+    double* g = (double*)malloc(sizeof(double) * (t > 0 ? t : 1));
+    for (int it = 0; it < steps; ++it) {
+        cs_oracle_clfit_loss_grad(A, m, lda, S, t, s_S, y, NULL, g, r);
+        *tau += 1;
+        double bc1 = 1.0 - pow(beta1, (double)*tau);
+        double bc2 = 1.0 - pow(beta2, (double)*tau);
+        for (int q = 0; q < t; ++q) {
+            mom[q] = beta1 * mom[q] + (1.0 - beta1) * g[q];
+            vel[q] = beta2 * vel[q] + (1.0 - beta2) * g[q] * g[q];
+            double mhat = mom[q] / bc1;
+            double vhat = vel[q] / bc2;
+            s_S[q] -= lr * mhat / (sqrt(vhat) + eps);
+        }
+    }
+    free(r); free(g);
+}
+
+static void clomp_one(const double* A, int m, int n, int lda, const double* y, int k,
+                      double tol, int max_iter, int steps, double lr, double beta1,
+                      double beta2, double eps, int reset_adam, int32_t* support,
+                      double* coef, int32_t* n_iter, double* res_norm, int32_t* status,
+                      double* top1, double* top2, double* res_hist) {
+    for (int q = 0; q < k; ++q) { support[q] = -1; coef[q] = 0.0; top1[q] = -1.0; top2[q] = -1.0; res_hist[q] = NAN; }
+    if (!all_finite(y, m)) { *n_iter = 0; *res_norm = NAN; *status = ST_NONFINITE; return; }
+    double* r = (double*)malloc(sizeof(double) * m);
+    double* mom = (double*)calloc(k, sizeof(double));
+    double* vel = (double*)calloc(k, sizeof(double));
+    unsigned char* inS = (unsigned char*)calloc(n, 1);
+    int32_t tau = 0;
+    memcpy(r, y, sizeof(double) * m);              /* s = 0  =>  r = y */
+    double rho = nrm2(r, m);
+    int iters = k < max_iter ? k : max_iter;
+    int t = 0, st = -1;
+    if (rho <= tol) st = ST_TOL;
+    while (st < 0 && t < iters) {
+        int j = select_atom(A, m, n, lda, r, inS, &top1[t], &top2[t]);
+        if (j < 0) { st = ST_MAXIT; break; }
+        support[t] = j;                           /* Mask |= e_j (bitwise or) */
+        inS[j] = 1;
+        coef[t] = 0.0;
+        ++t;
+        if (reset_adam) {
+            memset(mom, 0, sizeof(double) * k);
+            memset(vel, 0, sizeof(double) * k);
+            tau = 0;
+        }
+        cs_oracle_clfit_adam(A, m, lda, support, t, y, coef, mom, vel, &tau, steps,
+                             lr, beta1, beta2, eps);
+        residual(A, m, lda, support, t, coef, y, r);
+        rho = nrm2(r, m);
+        res_hist[t - 1] = rho;
+        if (rho <= tol) st = ST_TOL;
+    }
+    if (st < 0) st = (t == k) ? ST_K : ST_MAXIT;
+    *n_iter = t;
+    *res_norm = rho;
+    *status = st;
+    free(r); free(mom); free(vel); free(inS);
+}
+
+static int bad_args(const double* A, int m, int n, int lda, const double* Y, int ldy,
+                    int B, int k) {
+    if (m <= 0 || n <= 0 || B < 0 || k <= 0 || k > n || k > m) return 1;
+    if (lda < m || ldy < m) return 1;
+    if (!A || (B > 0 && !Y)) return 1;
+    return 0;
+}
+
+int cs_oracle_omp(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
+                  int k, double tol, int max_iter, int32_t* support, double* coef,
+                  int32_t* n_iter, double* res_norm, int32_t* status, double* top1,
+                  double* top2, double* res_hist, int nthreads) {
+    if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int b = 0; b < B; ++b) {
+        size_t o = (size_t)b * k;
+        omp_one(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, support + o, coef + o,
+                n_iter + b, res_norm + b, status + b, top1 + o, top2 + o, res_hist + o);
+    }
+    return 0;
+}
+
+int cs_oracle_clomp(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
+                    int k, double tol, int max_iter, int steps, double lr, double beta1,
+                    double beta2, double eps, int reset_adam, int32_t* support,
+                    double* coef, int32_t* n_iter, double* res_norm, int32_t* status,
+                    double* top1, double* top2, double* res_hist, int nthreads) {
+    if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0 || steps < 0) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int b = 0; b < B; ++b) {
+        size_t o = (size_t)b * k;
+        clomp_one(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, steps, lr, beta1,
+                  beta2, eps, reset_adam, support + o, coef + o, n_iter + b, res_norm + b,
+                  status + b, top1 + o, top2 + o, res_hist + o);
+    }
+    return 0;
+}
+
+int cs_oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}

@@ -1,0 +1,324 @@
+"""Pins of the FP64 oracle against facts other than its own code.
+
+Each test would fail on a plausible mistake in the oracle (a dropped term, a
+wrong sign or index, a transposed operand, a wrong tie-break or stop rule):
+  * brute-force support search on tiny noiseless instances, with the Exact
+    Recovery Condition deciding where OMP must succeed;
+  * orthogonality of the least-squares residual to the selected atoms;
+  * monotone residual norm;
+  * orthonormal A: closed form of every OMP step;
+  * Householder-QR least squares vs numpy.linalg.lstsq (library);
+  * exact recovery on the single-signal workload;
+  * hand-derived worked examples stored under tests/golden/;
+  * CL gradient vs central finite differences of the quadratic loss;
+  * the CL Adam loop vs torch.optim.Adam in float64 (library);
+  * orthonormal A decouples the CL fit coordinate by coordinate;
+  * the CL fit approaches the least-squares coefficients for long, small-step runs.
+"""
+import itertools
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _rand_A(rng, m, n):
+    return workloads.gaussian_matrix(rng, m, n)
+
+
+# ---------------------------------------------------------------- OMP pins
+
+def test_lstsq_matches_numpy():
+    rng = np.random.default_rng(1)
+    for (m, t) in [(8, 1), (16, 5), (64, 20), (256, 32), (33, 33)]:
+        As = rng.standard_normal((m, t))
+        y = rng.standard_normal(m)
+        z, st = oracle.lstsq(As, y)
+        assert st == 0
+        z_ref = np.linalg.lstsq(As, y, rcond=None)[0]
+        assert np.allclose(z, z_ref, rtol=1e-12, atol=1e-12 * np.abs(z_ref).max())
+
+
+def test_lstsq_flags_dependent_column():
+    rng = np.random.default_rng(2)
+    As = rng.standard_normal((10, 3))
+    As = np.column_stack([As, As[:, 0] * 2.0 - As[:, 2]])
+    _, st = oracle.lstsq(As, rng.standard_normal(10))
+    assert st == 3
+
+
+def _erc_holds(A, S):
+    """Tropp's Exact Recovery Condition max_{j not in S} ||pinv(A_S) a_j||_1 < 1."""
+    P = np.linalg.pinv(A[:, S])
+    others = [j for j in range(A.shape[1]) if j not in S]
+    return max(np.abs(P @ A[:, j]).sum() for j in others) < 1.0
+
+
+def test_bruteforce_tiny_noiseless():
+    """n <= 20, k <= 3: the minimum-residual support over all C(n,k) supports
+    is the true one, and OMP recovers it wherever the ERC holds."""
+    rng = np.random.default_rng(3)
+    n_erc = 0
+    for trial in range(60):
+        m, n, k = int(rng.integers(6, 13)), int(rng.integers(10, 21)), int(rng.integers(1, 4))
+        A = _rand_A(rng, m, n)
+        S_true = sorted(rng.choice(n, size=k, replace=False).tolist())
+        x = np.zeros(n)
+        x[S_true] = rng.standard_normal(k) + np.sign(rng.standard_normal(k))
+        y = A @ x
+        best, best_res = None, np.inf
+        for S in itertools.combinations(range(n), k):
+            z = np.linalg.lstsq(A[:, S], y, rcond=None)[0]
+            res = np.linalg.norm(y - A[:, S] @ z)
+            if res < best_res - 1e-12:
+                best, best_res = list(S), res
+        assert best == S_true
+        o = oracle.omp(A, y, k, tol=0.0)
+        if _erc_holds(A, S_true):
+            n_erc += 1
+            assert sorted(o["support"][0].tolist()) == S_true
+            xr = np.zeros(n)
+            xr[o["support"][0]] = o["coef"][0]
+            assert np.allclose(xr, x, atol=1e-10)
+    assert n_erc >= 10
+
+
+def test_residual_orthogonal_and_monotone():
+    rng = np.random.default_rng(4)
+    A = _rand_A(rng, 48, 160)
+    X = workloads.sparse_coefficients(rng, 160, 6, 10, values="gauss")
+    Y = workloads.add_noise(rng, A @ X, 30.0)
+    for kk in range(1, 11):
+        o = oracle.omp(A, Y, kk)
+        for b in range(Y.shape[1]):
+            S = o["support"][b]
+            r = Y[:, b] - A[:, S] @ o["coef"][b]
+            bound = 1e-10 * np.linalg.norm(A[:, S], 2) * np.linalg.norm(Y[:, b])
+            assert np.abs(A[:, S].T @ r).max() <= bound
+            assert abs(np.linalg.norm(r) - o["res_norm"][b]) <= 1e-12 * np.linalg.norm(Y[:, b])
+    h = o["res_hist"]
+    assert np.all(np.diff(h, axis=1) <= 1e-12)
+
+
+def test_orthonormal_closed_form():
+    """A orthonormal (m = n): supports come in descending |A^T y| order, the
+    coefficients are (A^T y)_S and ||r||^2 = ||y||^2 - sum of selected c^2."""
+    rng = np.random.default_rng(5)
+    n = 24
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Y = rng.standard_normal((n, 3))
+    k = 7
+    o = oracle.omp(Q, Y, k)
+    for b in range(3):
+        c = Q.T @ Y[:, b]
+        order = np.argsort(-np.abs(c), kind="stable")[:k]
+        assert o["support"][b].tolist() == order.tolist()
+        assert np.allclose(o["coef"][b], c[order], atol=1e-12)
+        rr = np.sum(Y[:, b] ** 2) - np.sum(c[order] ** 2)
+        assert abs(o["res_norm"][b] ** 2 - rr) < 1e-10
+        for t in range(k):   # the logged top-1 is |c| of the pick itself
+            assert abs(o["top1"][b, t] - abs(c[order[t]])) < 1e-12
+
+
+def test_single_signal_exact_recovery():
+    p = workloads.config_single_fp64()
+    o = oracle.omp(p.A, p.Y, p.k, tol=p.tol)
+    xr = np.zeros(p.n)
+    xr[o["support"][0]] = o["coef"][0]
+    assert sorted(o["support"][0].tolist()) == sorted(np.nonzero(p.X_true[:, 0])[0].tolist())
+    assert np.abs(xr - p.X_true[:, 0]).max() < 1e-10
+    assert o["status"][0] == 1 and o["n_iter"][0] == 8
+
+
+def test_tie_lowest_index_and_dependent_atom():
+    rng = np.random.default_rng(6)
+    A = _rand_A(rng, 12, 30)
+    A[:, 17] = A[:, 5]                     # duplicated atom
+    y = 3.0 * A[:, 5] + 0.5 * A[:, 9]
+    o = oracle.omp(A, y, 2)
+    assert o["support"][0, 0] == 5         # exact tie 5/17 -> lowest index
+    assert o["top2"][0, 0] == o["top1"][0, 0]
+    # more atoms than measurements can carry: the 13th column is dependent
+    Y = rng.standard_normal((12, 1))
+    o = oracle.omp(A, Y, 12, tol=0.0)
+    assert o["status"][0] in (0, 3)
+    B2 = _rand_A(rng, 4, 8)
+    B2[:, 1] = B2[:, 0]
+    B2[:, 2] = B2[:, 0]
+    y2 = B2[:, 0] * 2.0
+    o = oracle.omp(B2, y2, 3, tol=0.0)
+    # after picking atom 0 the residual is 0; the next pick is dependent
+    assert o["status"][0] == 3 and o["n_iter"][0] == 1 and o["support"][0, 0] == 0
+
+
+def test_nonfinite_and_stop_rules():
+    rng = np.random.default_rng(7)
+    A = _rand_A(rng, 16, 40)
+    Y = rng.standard_normal((16, 4))
+    Y[3, 1] = np.nan
+    Y[:, 2] = 0.0
+    o = oracle.omp(A, Y, 5, tol=1e-9, max_iter=3)
+    assert o["status"].tolist() == [2, 4, 1, 2]
+    assert o["n_iter"].tolist() == [3, 0, 0, 3]
+    assert np.all(o["support"][1] == -1)
+    o = oracle.omp(A, Y[:, [0]], 5, tol=0.0, max_iter=5)
+    assert o["status"][0] == 0 and o["n_iter"][0] == 5
+
+
+def test_batch_invariance_and_leading_dims():
+    rng = np.random.default_rng(8)
+    A = _rand_A(rng, 20, 50)
+    Y = rng.standard_normal((20, 5))
+    o_all = oracle.omp(A, Y, 6)
+    for b in range(5):
+        o1 = oracle.omp(A, Y[:, b], 6)
+        assert np.array_equal(o1["support"][0], o_all["support"][b])
+        assert np.array_equal(o1["coef"][0], o_all["coef"][b])
+
+
+def test_golden_worked_examples():
+    """Hand-derived OMP runs (see the derivations inside each fixture)."""
+    for fn in sorted(os.listdir(GOLDEN)):
+        if not fn.startswith("omp_") or not fn.endswith(".json"):
+            continue
+        g = json.load(open(os.path.join(GOLDEN, fn)))
+        A = np.array(eval_expr(g["A"]), dtype=np.float64)
+        y = np.array(eval_expr(g["y"]), dtype=np.float64)
+        o = oracle.omp(A, y, g["k"], tol=g["tol"])
+        assert o["support"][0].tolist() == g["support"], fn
+        assert np.allclose(o["coef"][0], eval_expr(g["coef"]), atol=1e-14), fn
+        assert o["status"][0] == g["status"], fn
+
+
+def eval_expr(v):
+    """Fixture numbers may be written as closed forms such as "sqrt(3)"."""
+    if isinstance(v, list):
+        return [eval_expr(u) for u in v]
+    if isinstance(v, str):
+        return float(eval(v, {"__builtins__": {}}, {"sqrt": math.sqrt}))
+    return float(v)
+
+
+# ---------------------------------------------------------------- CLOMP pins
+
+def test_clfit_gradient_matches_central_differences():
+    """L is quadratic in s_S, so a central difference has no truncation error."""
+    rng = np.random.default_rng(9)
+    A = _rand_A(rng, 40, 90)
+    S = rng.choice(90, size=7, replace=False).astype(np.int32)
+    y = rng.standard_normal(40)
+    s = rng.standard_normal(7)
+    L0, g, r = oracle.clfit_loss_grad(A, S, s, y)
+    assert abs(L0 - 0.5 * np.sum((y - A[:, S] @ s) ** 2)) < 1e-12
+    h = 1e-3
+    for q in range(7):
+        e = np.zeros(7)
+        e[q] = h
+        Lp = oracle.clfit_loss_grad(A, S, s + e, y)[0]
+        Lm = oracle.clfit_loss_grad(A, S, s - e, y)[0]
+        fd = (Lp - Lm) / (2 * h)
+        assert abs(fd - g[q]) <= 1e-9 * max(1.0, abs(g[q]))
+
+
+def test_clfit_adam_matches_torch_adam():
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(10)
+    A = _rand_A(rng, 32, 64)
+    S = np.array([3, 17, 40, 41, 60], dtype=np.int32)
+    y = rng.standard_normal(32)
+    s0 = np.zeros(5)
+    s_o, mo, ve, tau = oracle.clfit_adam(A, S, y, s0, np.zeros(5), np.zeros(5), 0, 300,
+                                         lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8)
+    assert tau == 300
+    At = torch.tensor(A[:, S], dtype=torch.float64)
+    yt = torch.tensor(y, dtype=torch.float64)
+    p = torch.zeros(5, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([p], lr=1e-2, betas=(0.9, 0.999), eps=1e-8, foreach=False)
+    for _ in range(300):
+        opt.zero_grad()
+        loss = 0.5 * torch.sum((yt - At @ p) ** 2)
+        loss.backward()
+        opt.step()
+    assert np.allclose(s_o, p.detach().numpy(), rtol=0, atol=1e-13)
+    st = opt.state[p]
+    assert np.allclose(mo, st["exp_avg"].numpy(), atol=1e-13)
+    assert np.allclose(ve, st["exp_avg_sq"].numpy(), atol=1e-13)
+
+
+def test_clomp_first_iteration_is_adam_on_growing_mask():
+    """CLOMP iteration structure: with steps T the state after t iterations is
+    the state of one Adam run (torch) on the masked loss whose mask grows by
+    the oracle's picks, T steps per pick (one optimizer state for the solve)."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(11)
+    A = _rand_A(rng, 24, 60)
+    X = workloads.sparse_coefficients(rng, 60, 1, 4, values="pm")
+    y = (A @ X)[:, 0]
+    T, k = 20, 4
+    o = oracle.clomp(A, y, k, steps=T, lr=5e-2)
+    S = o["support"][0]
+    p = torch.zeros(60, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([p], lr=5e-2, foreach=False)
+    At = torch.tensor(A, dtype=torch.float64)
+    yt = torch.tensor(y, dtype=torch.float64)
+    mask = torch.zeros(60, dtype=torch.float64)
+    r = yt.clone()
+    for t in range(k):
+        c = (At.T @ r).abs().numpy()
+        c[mask.numpy() > 0] = -1
+        assert int(np.argmax(c)) == S[t]
+        mask[S[t]] = 1.0
+        for _ in range(T):
+            opt.zero_grad()
+            loss = 0.5 * torch.sum((yt - At @ (p * mask)) ** 2)
+            loss.backward()
+            opt.step()
+        with torch.no_grad():
+            r = yt - At @ (p * mask)
+    assert np.allclose(p.detach().numpy()[S], o["coef"][0], atol=1e-12)
+    assert abs(float(torch.linalg.norm(r)) - o["res_norm"][0]) < 1e-12
+
+
+def test_clomp_orthonormal_decouples():
+    """With orthonormal A the CL gradient of coordinate q is s_q - c_q
+    (c = A^T y): every coordinate runs its own scalar Adam on 1/2(s - c)^2."""
+    rng = np.random.default_rng(12)
+    n = 16
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    y = rng.standard_normal(n)
+    c = Q.T @ y
+    S = np.argsort(-np.abs(c))[:3].astype(np.int32)
+    s, mo, ve, tau = oracle.clfit_adam(Q, S, y, np.zeros(3), np.zeros(3), np.zeros(3), 0, 40,
+                                       lr=0.05)
+    for q in range(3):
+        s1, _, _, _ = oracle.clfit_adam(Q, S[[q]], y, [0.0], [0.0], [0.0], 0, 40, lr=0.05)
+        assert abs(s1[0] - s[q]) < 1e-13
+    _, g, _ = oracle.clfit_loss_grad(Q, S, s, y)
+    assert np.allclose(g, s - c[S], atol=1e-13)
+
+
+def test_clomp_long_small_steps_approach_least_squares():
+    p = workloads.config_single_fp64()
+    om = oracle.omp(p.A, p.Y, p.k, tol=0.0)
+    cl = oracle.clomp(p.A, p.Y, p.k, tol=0.0, steps=20000, lr=1e-4, reset_adam=False)
+    assert cl["support"][0].tolist() == om["support"][0].tolist()
+    assert np.abs(cl["coef"][0] - om["coef"][0]).max() < 1e-3
+
+
+def test_clomp_excludes_selected_and_stops():
+    rng = np.random.default_rng(13)
+    A = _rand_A(rng, 30, 80)
+    Y = rng.standard_normal((30, 3))
+    Y[0, 2] = np.inf
+    o = oracle.clomp(A, Y, 10, steps=5)
+    for b in range(2):
+        assert len(set(o["support"][b].tolist())) == 10
+        assert o["status"][b] == 0
+    assert o["status"][2] == 4
