@@ -1,0 +1,197 @@
+/*
+ * cs_omp.h -- C ABI of the GB300 (sm_103a) sparse-reconstruction hot path:
+ * batched Orthogonal Matching Pursuit (OMP) and its coefficients-learning
+ * variant CLOMP, from arXiv 2501.11592 ("Training-free Ultra Small Model for
+ * Universal Sparse Reconstruction in Compressed Sensing").
+ *
+ * Problem (Eq. 1 and Eq. 3): y = A s + xi for every column y of Y, with one
+ * shared measurement matrix A (m x n, m < n) and k-sparse s.  Each solver
+ * iteration (Methods, "Coefficients learning on OMP"):
+ *   1. correlation c = A^T r (the residual-injection branch, a fixed-weight
+ *      fully connected layer applied to r^T);
+ *   2. selection of the atom with the largest |c_j| not yet selected (lowest
+ *      index on exact ties), OR-ed into the support mask;
+ *   3. coefficient fit on the support: least squares, i.e. pinv(A(:,Mask))
+ *      (OMP, Table "s forward block"), or Adam steps on the residual loss
+ *      1/2 ||y - A_S s_S||^2 with s learnable (CLOMP, structure 1);
+ *   4. residual r = y - A_S s_S and the stopping test of Eq. 2.
+ *
+ * Conventions shared by every entry point:
+ *   - All matrices are column-major float32.  A has leading dimension lda >= m;
+ *     Y has leading dimension ldy >= m.  Per-signal outputs with k entries
+ *     (support, coef) are k x batch column-major: signal b owns
+ *     [b*k, b*k + k), in selection order; unused slots hold -1 / 0.
+ *   - Unless an entry point says otherwise, every array pointer is a DEVICE
+ *     pointer owned by the caller.  The library never frees it and keeps no
+ *     reference to it after the call returns.
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream).  Calls
+ *     are asynchronous and stream-ordered; results are valid once the stream
+ *     has been synchronised.
+ *   - Argument errors are reported synchronously (CS_EINVAL / CS_ENOTSUP)
+ *     before anything is launched.  A CUDA error at launch returns CS_ECUDA.
+ *     Per-signal failures never abort the batch: they are written to
+ *     sig_status (see CS_SIG_*).  cs_last_error() gives a message for the
+ *     last non-OK return on the calling thread.
+ *   - A plan owns the device workspace.  It is not thread-safe; use one plan
+ *     per stream (or serialise calls on one stream).
+ */
+#ifndef CS_OMP_H
+#define CS_OMP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    CS_OK = 0,
+    CS_EINVAL = -1,    /* invalid argument (nothing was launched) */
+    CS_ENOMEM = -2,    /* device allocation failed */
+    CS_ECUDA = -3,     /* a CUDA call or launch failed */
+    CS_ETIMEOUT = -4,  /* a bounded device-side wait gave up */
+    CS_ENOTSUP = -5    /* valid but unsupported configuration (e.g. k above the plan limit) */
+} cs_status;
+
+/* Per-signal status written to sig_status (Eq. 2 stopping rule; R = max_iter). */
+enum {
+    CS_SIG_REACHED_K = 0,     /* |S| = k */
+    CS_SIG_REACHED_TOL = 1,   /* ||r||_2 <= tol */
+    CS_SIG_MAX_ITER = 2,      /* max_iter iterations without reaching k or tol */
+    CS_SIG_DEPENDENT = 3,     /* the selected atom is linearly dependent on the support
+                                 (pivot^2 <= 2^-20 ||a||^2); it is not added */
+    CS_SIG_NONFINITE = 4      /* y holds a NaN or Inf; no iteration is run */
+};
+
+/* Arithmetic of the correlation c = A^T r (step 1).  The selection always
+ * re-scores the low-precision candidates in float32 (see topc). */
+typedef enum {
+    CS_CORR_FP32 = 0,   /* float32 SIMT correlation, exact float32 argmax */
+    CS_CORR_BF16 = 1    /* bf16 tensor-core correlation (tcgen05, fp32 accumulate),
+                           top-c candidates per atom tile, fp32 re-score */
+} cs_corr_prec;
+
+/* How the CLOMP coefficient fit evaluates its gradient -A_S^T (y - A_S s_S). */
+typedef enum {
+    CS_CL_GATHER = 0,   /* residual and adjoint by gathering the columns of A_S (literal form) */
+    CS_CL_GRAM = 1      /* same gradient as G s_S - A_S^T y with G = A_S^T A_S kept per signal */
+} cs_cl_form;
+
+typedef struct {
+    int32_t k;          /* target sparsity, 1 <= k <= min(m, n, plan k_max) */
+    double tol;         /* stop once ||r||_2 <= tol (epsilon of Eq. 2); 0 disables it */
+    int32_t max_iter;   /* R: at most this many iterations; <= 0 means k */
+    int32_t prec;       /* cs_corr_prec */
+    int32_t topc;       /* candidates kept per signal and atom tile in bf16 mode
+                           (1..8, default 8 when 0); ignored in fp32 mode */
+} cs_omp_params;
+
+typedef struct {
+    cs_omp_params base;
+    int32_t steps;                  /* Adam steps per iteration (T >= 0) */
+    float lr, beta1, beta2, eps;    /* Adam hyper-parameters (PyTorch update rule) */
+    int32_t reset_adam_each_iter;   /* 0: one Adam state and step counter for the whole
+                                       solve; 1: reset them at every iteration */
+    int32_t form;                   /* cs_cl_form */
+} cs_clomp_params;
+
+typedef struct cs_plan cs_plan;
+
+/* Create a plan on the current CUDA device with workspace for problems up to
+ * m_max x n_max, batch_max signals and k_max <= 64 iterations.  Allocates
+ * device memory once; solves on this plan allocate nothing.
+ * Returns CS_EINVAL for non-positive sizes, CS_ENOTSUP for k_max > 64,
+ * CS_ENOMEM / CS_ECUDA on allocation failure (then *plan is NULL). */
+cs_status cs_plan_create(cs_plan** plan, int32_t m_max, int32_t n_max, int32_t batch_max,
+                         int32_t k_max);
+
+/* Release a plan's device memory (synchronises the device first).  NULL is a no-op. */
+cs_status cs_plan_destroy(cs_plan* plan);
+
+/* Batched plain OMP (Table "s forward block", OMP row: least squares on the
+ * selected columns), one shared A, `batch` columns of Y.
+ * Least squares by an incremental Cholesky factorisation of A_S^T A_S in
+ * float64 (Gram entries from float32 dot products), triangular solves in
+ * float64; correlation and residual in float32 (or bf16 correlation, see prec).
+ * Outputs (device, caller-owned): support, coef (k x batch), n_iter, res_norm
+ * (||r||_2 at exit), sig_status (batch each).  batch == 0 is a no-op. */
+cs_status omp_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                            const float* Y, int32_t ldy, int32_t batch, int32_t* support,
+                            float* coef, int32_t* n_iter, float* res_norm, int32_t* sig_status,
+                            const cs_omp_params* params, void* stream);
+
+/* Single-signal OMP: omp_solve_batched with batch = 1 and y of length m. */
+cs_status omp_solve(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                    const float* y, int32_t* support, float* coef, int32_t* n_iter,
+                    float* res_norm, int32_t* sig_status, const cs_omp_params* params,
+                    void* stream);
+
+/* Batched CLOMP (Methods, "Coefficients learning on OMP", structure 1): the
+ * OMP selection, then `steps` Adam steps on L = 1/2 ||y - A(s .* Mask)||^2
+ * per iteration, s starting at zero and persisting across iterations.  coef
+ * holds s on the support.  Same layouts and outputs as omp_solve_batched. */
+cs_status clomp_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                              const float* Y, int32_t ldy, int32_t batch, int32_t* support,
+                              float* coef, int32_t* n_iter, float* res_norm,
+                              int32_t* sig_status, const cs_clomp_params* params, void* stream);
+
+/* Single-signal CLOMP: clomp_solve_batched with batch = 1. */
+cs_status clomp_solve(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                      const float* y, int32_t* support, float* coef, int32_t* n_iter,
+                      float* res_norm, int32_t* sig_status, const cs_clomp_params* params,
+                      void* stream);
+
+/* Host-buffer forms of the batched solvers: every array pointer is a HOST
+ * pointer (pinned memory gives the fastest copies).  The call copies A and Y
+ * into plan-owned device buffers, solves on `stream`, copies the five
+ * outputs back and synchronises `stream` before returning.  The plan must
+ * have been created with room for the inputs (as for the device forms). */
+cs_status omp_solve_batched_host(cs_plan* plan, const float* A, int32_t m, int32_t n,
+                                 int32_t lda, const float* Y, int32_t ldy, int32_t batch,
+                                 int32_t* support, float* coef, int32_t* n_iter,
+                                 float* res_norm, int32_t* sig_status,
+                                 const cs_omp_params* params, void* stream);
+cs_status clomp_solve_batched_host(cs_plan* plan, const float* A, int32_t m, int32_t n,
+                                   int32_t lda, const float* Y, int32_t ldy, int32_t batch,
+                                   int32_t* support, float* coef, int32_t* n_iter,
+                                   float* res_norm, int32_t* sig_status,
+                                   const cs_clomp_params* params, void* stream);
+
+/* CL fit, forward half (Methods, s forward branch: y' = A (s .* Mask)):
+ *   R[:,b] = Y[:,b] - sum_q A[:, S[b*lds+q]] * Sv[b*lds+q]   (q < t)
+ *   loss[b] = 1/2 ||R[:,b]||^2
+ * S (int32) and Sv (float) are t x batch with leading dimension lds >= t;
+ * R has leading dimension ldr >= m.  loss may be NULL.  Support indices must
+ * lie in [0, n). */
+cs_status clfit_forward(const float* A, int32_t m, int32_t n, int32_t lda, const int32_t* S,
+                        const float* Sv, int32_t t, int32_t lds, const float* Y, int32_t ldy,
+                        int32_t batch, float* R, int32_t ldr, float* loss, void* stream);
+
+/* CL fit, adjoint half (back-propagation of the residual loss through the
+ * fixed layer A):  grad[b*lds+q] = -A[:, S[b*lds+q]]^T R[:,b]  for q < t. */
+cs_status clfit_adjoint(const float* A, int32_t m, int32_t n, int32_t lda, const int32_t* S,
+                        int32_t t, int32_t lds, const float* R, int32_t ldr, int32_t batch,
+                        float* grad, void* stream);
+
+/* Adjoint fused with one Adam step (the optimizer that learns s): computes
+ * g = -A_S^T R as clfit_adjoint does, then for q < t
+ *   mom = b1 mom + (1-b1) g,  vel = b2 vel + (1-b2) g^2,
+ *   Sv -= lr/(1-b1^tau) * mom / (sqrt(vel)/sqrt(1-b2^tau) + eps)
+ * in place.  tau >= 1 is the step counter after this step.  mom and vel are
+ * t x batch with leading dimension lds.  grad may be NULL. */
+cs_status clfit_adam_step(const float* A, int32_t m, int32_t n, int32_t lda, const int32_t* S,
+                          float* Sv, int32_t t, int32_t lds, const float* R, int32_t ldr,
+                          int32_t batch, float* mom, float* vel, int32_t tau, float lr,
+                          float beta1, float beta2, float eps, float* grad, void* stream);
+
+/* Message describing the last non-OK return on the calling thread ("" if none). */
+const char* cs_last_error(void);
+
+/* Library version string. */
+const char* cs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CS_OMP_H */

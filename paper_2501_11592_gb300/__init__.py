@@ -1,0 +1,328 @@
+"""GB300 (sm_103a) batched OMP / CLOMP -- Python binding of the C ABI.
+
+The binding only marshals arguments: torch tensors provide device memory and
+the current CUDA stream; every step of the solve runs in the library's CUDA
+kernels (``_lib/libcs_omp.so``, built by ``paper_2501_11592_gb300.build``).
+There is no CPU path: if the library is missing, :func:`load` raises.
+
+Function names follow the C ABI in ``include/cs_omp.h``.  Matrices are
+column-major: pass ``A`` as an (m, n) tensor whose columns are contiguous
+(e.g. ``torch.from_numpy(np.asfortranarray(A))`` or ``At.t()`` for a
+contiguous (n, m) tensor ``At``); other layouts are copied into that layout.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from dataclasses import dataclass
+
+__all__ = [
+    "load", "Plan", "omp_solve", "omp_solve_batched", "clomp_solve", "clomp_solve_batched",
+    "omp_solve_batched_host", "clomp_solve_batched_host", "clfit_forward", "clfit_adjoint",
+    "clfit_adam_step", "CSError", "SIG_REACHED_K", "SIG_REACHED_TOL", "SIG_MAX_ITER",
+    "SIG_DEPENDENT", "SIG_NONFINITE", "library_path",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+_LIB_PATH = os.path.join(_PKG, "_lib", "libcs_omp.so")
+
+CS_OK, CS_EINVAL, CS_ENOMEM, CS_ECUDA, CS_ETIMEOUT, CS_ENOTSUP = 0, -1, -2, -3, -4, -5
+SIG_REACHED_K, SIG_REACHED_TOL, SIG_MAX_ITER, SIG_DEPENDENT, SIG_NONFINITE = 0, 1, 2, 3, 4
+PREC = {"fp32": 0, "bf16": 1}
+FORM = {"gather": 0, "gram": 1}
+_STATUS_NAMES = {CS_EINVAL: "CS_EINVAL", CS_ENOMEM: "CS_ENOMEM", CS_ECUDA: "CS_ECUDA",
+                 CS_ETIMEOUT: "CS_ETIMEOUT", CS_ENOTSUP: "CS_ENOTSUP"}
+
+
+class CSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_STATUS_NAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+class OmpParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("prec", ctypes.c_int32), ("topc", ctypes.c_int32)]
+
+
+class ClompParams(ctypes.Structure):
+    _fields_ = [("base", OmpParams), ("steps", ctypes.c_int32), ("lr", ctypes.c_float),
+                ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
+                ("reset_adam_each_iter", ctypes.c_int32), ("form", ctypes.c_int32)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def library_path() -> str:
+    return _LIB_PATH
+
+
+def load():
+    """Load the CUDA library (raises FileNotFoundError if it was not built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(_LIB_PATH):
+            raise FileNotFoundError(
+                f"{_LIB_PATH} is missing; build it with `python -m paper_2501_11592_gb300.build`")
+        L = ctypes.CDLL(_LIB_PATH)
+        vp, i32, f32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_float
+        solve_args = [vp, vp, i32, i32, i32, vp, i32, i32, vp, vp, vp, vp, vp]
+        L.cs_plan_create.argtypes = [ctypes.POINTER(vp), i32, i32, i32, i32]
+        L.cs_plan_destroy.argtypes = [vp]
+        L.omp_solve_batched.argtypes = solve_args + [ctypes.POINTER(OmpParams), vp]
+        L.omp_solve_batched_host.argtypes = solve_args + [ctypes.POINTER(OmpParams), vp]
+        L.clomp_solve_batched.argtypes = solve_args + [ctypes.POINTER(ClompParams), vp]
+        L.clomp_solve_batched_host.argtypes = solve_args + [ctypes.POINTER(ClompParams), vp]
+        single = [vp, vp, i32, i32, i32, vp, vp, vp, vp, vp, vp]
+        L.omp_solve.argtypes = single + [ctypes.POINTER(OmpParams), vp]
+        L.clomp_solve.argtypes = single + [ctypes.POINTER(ClompParams), vp]
+        L.clfit_forward.argtypes = [vp, i32, i32, i32, vp, vp, i32, i32, vp, i32, i32, vp, i32, vp, vp]
+        L.clfit_adjoint.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, vp, vp]
+        L.clfit_adam_step.argtypes = [vp, i32, i32, i32, vp, vp, i32, i32, vp, i32, i32, vp, vp,
+                                      i32, f32, f32, f32, f32, vp, vp]
+        for fn in ("cs_plan_create", "cs_plan_destroy", "omp_solve_batched", "omp_solve_batched_host",
+                   "clomp_solve_batched", "clomp_solve_batched_host", "omp_solve", "clomp_solve",
+                   "clfit_forward", "clfit_adjoint", "clfit_adam_step"):
+            getattr(L, fn).restype = ctypes.c_int
+        L.cs_last_error.restype = ctypes.c_char_p
+        L.cs_version.restype = ctypes.c_char_p
+        _lib = L
+        return L
+
+
+def _check(rc):
+    if rc != CS_OK:
+        raise CSError(rc, load().cs_last_error().decode())
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream_ptr(stream=None):
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _colmajor(x, dtype):
+    """(rows, cols) tensor with contiguous columns (stride (1, ld)), on its device."""
+    torch = _torch()
+    if x.dim() == 1:
+        x = x.reshape(-1, 1)
+    if x.dtype != dtype:
+        x = x.to(dtype)
+    if x.stride(0) != 1 or (x.shape[1] > 1 and x.stride(1) < x.shape[0]):
+        x = x.t().contiguous().t()
+    return x
+
+
+def _ld(x):
+    return max(int(x.stride(1)), int(x.shape[0])) if x.shape[1] > 1 else int(x.shape[0])
+
+
+class Plan:
+    """Device workspace for problems up to (m_max, n_max, batch_max, k_max)."""
+
+    def __init__(self, m_max, n_max, batch_max, k_max):
+        L = load()
+        h = ctypes.c_void_p()
+        _check(L.cs_plan_create(ctypes.byref(h), int(m_max), int(n_max), int(batch_max), int(k_max)))
+        self.h = h
+        self.dims = (int(m_max), int(n_max), int(batch_max), int(k_max))
+
+    def fits(self, m, n, B, k):
+        return m <= self.dims[0] and n <= self.dims[1] and B <= self.dims[2] and k <= self.dims[3]
+
+    def close(self):
+        if self.h is not None and self.h.value:
+            load().cs_plan_destroy(self.h)
+        self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+_plans: dict = {}
+
+
+def _plan_for(m, n, B, k, plan):
+    if plan is not None:
+        return plan
+    torch = _torch()
+    dev = torch.cuda.current_device()
+    p = _plans.get(dev)
+    if p is None or not p.fits(m, n, B, k):
+        if p is not None:
+            m, n, B, k = max(m, p.dims[0]), max(n, p.dims[1]), max(B, p.dims[2]), max(k, p.dims[3])
+            p.close()
+        p = Plan(m, n, B, k)
+        _plans[dev] = p
+    return p
+
+
+@dataclass
+class Result:
+    support: "object"    # (B, k) int32, selection order, -1 = unused
+    coef: "object"       # (B, k) float32
+    n_iter: "object"     # (B,) int32
+    res_norm: "object"   # (B,) float32
+    status: "object"     # (B,) int32 (SIG_*)
+
+
+def _outputs(B, k, device):
+    torch = _torch()
+    return Result(torch.empty((B, k), dtype=torch.int32, device=device),
+                  torch.empty((B, k), dtype=torch.float32, device=device),
+                  torch.empty(B, dtype=torch.int32, device=device),
+                  torch.empty(B, dtype=torch.float32, device=device),
+                  torch.empty(B, dtype=torch.int32, device=device))
+
+
+def _omp_params(k, tol, max_iter, prec, topc):
+    return OmpParams(int(k), float(tol), int(max_iter or 0), PREC[prec], int(topc))
+
+
+def _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps, reset_adam, form):
+    return ClompParams(_omp_params(k, tol, max_iter, prec, topc), int(steps), float(lr), float(beta1),
+                       float(beta2), float(eps), int(bool(reset_adam)), FORM[form])
+
+
+def _batched(fn, A, Y, k, params, plan, stream, out):
+    torch = _torch()
+    A = _colmajor(A, torch.float32)
+    Y = _colmajor(Y, torch.float32)
+    m, n = A.shape
+    B = Y.shape[1]
+    if Y.shape[0] != m:
+        raise ValueError(f"Y has {Y.shape[0]} rows, A has {m}")
+    p = _plan_for(m, n, B, k, plan)
+    o = out if out is not None else _outputs(B, k, A.device)
+    _check(fn(p.h, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), ctypes.c_void_p(Y.data_ptr()), m if B <= 1 else _ld(Y),
+              B, ctypes.c_void_p(o.support.data_ptr()), ctypes.c_void_p(o.coef.data_ptr()),
+              ctypes.c_void_p(o.n_iter.data_ptr()), ctypes.c_void_p(o.res_norm.data_ptr()),
+              ctypes.c_void_p(o.status.data_ptr()), ctypes.byref(params), _stream_ptr(stream)))
+    return o
+
+
+def omp_solve_batched(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, plan=None,
+                      stream=None, out=None) -> Result:
+    """Batched plain OMP on the current stream (see include/cs_omp.h)."""
+    return _batched(load().omp_solve_batched, A, Y, k, _omp_params(k, tol, max_iter, prec, topc),
+                    plan, stream, out)
+
+
+def clomp_solve_batched(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, steps=50, lr=1e-2,
+                        beta1=0.9, beta2=0.999, eps=1e-8, reset_adam=False, form="gram",
+                        plan=None, stream=None, out=None) -> Result:
+    """Batched CLOMP (structure 1, Adam) on the current stream."""
+    return _batched(load().clomp_solve_batched, A, Y, k,
+                    _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
+                                  reset_adam, form), plan, stream, out)
+
+
+def omp_solve(A, y, k, **kw) -> Result:
+    return omp_solve_batched(A, y.reshape(-1, 1), k, **kw)
+
+
+def clomp_solve(A, y, k, **kw) -> Result:
+    return clomp_solve_batched(A, y.reshape(-1, 1), k, **kw)
+
+
+def _host_batched(fn, A, Y, k, params, plan, stream, out=None):
+    """A, Y: float32 numpy arrays in Fortran order (pinned or pageable)."""
+    import numpy as np
+    A = np.asfortranarray(A, dtype=np.float32)
+    Y = np.asfortranarray(Y.reshape(Y.shape[0], -1), dtype=np.float32)
+    m, n = A.shape
+    B = Y.shape[1]
+    p = _plan_for(m, n, B, k, plan)
+    if out is None:
+        out = dict(support=np.empty((B, k), np.int32), coef=np.empty((B, k), np.float32),
+                   n_iter=np.empty(B, np.int32), res_norm=np.empty(B, np.float32),
+                   status=np.empty(B, np.int32))
+    ptr = lambda a: ctypes.c_void_p(a.ctypes.data)
+    _check(fn(p.h, ptr(A), m, n, m, ptr(Y), m, B, ptr(out["support"]), ptr(out["coef"]),
+              ptr(out["n_iter"]), ptr(out["res_norm"]), ptr(out["status"]), ctypes.byref(params),
+              _stream_ptr(stream)))
+    return out
+
+
+def omp_solve_batched_host(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, plan=None,
+                           stream=None, out=None):
+    return _host_batched(load().omp_solve_batched_host, A, Y, k,
+                         _omp_params(k, tol, max_iter, prec, topc), plan, stream, out)
+
+
+def clomp_solve_batched_host(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, steps=50,
+                             lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, reset_adam=False,
+                             form="gram", plan=None, stream=None, out=None):
+    return _host_batched(load().clomp_solve_batched_host, A, Y, k,
+                         _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
+                                       reset_adam, form), plan, stream, out)
+
+
+def clfit_forward(A, S, Sv, Y, stream=None):
+    """r = y - A_S s_S and 1/2||r||^2 per signal.  S, Sv: (B, t); Y: (m, B).
+    Returns (R (m, B) column-major, loss (B,))."""
+    torch = _torch()
+    A = _colmajor(A, torch.float32)
+    Y = _colmajor(Y, torch.float32)
+    m, n = A.shape
+    S = S.to(torch.int32).contiguous()
+    Sv = Sv.to(torch.float32).contiguous()
+    B, t = S.shape
+    R = torch.empty((B, m), dtype=torch.float32, device=A.device).t()
+    loss = torch.empty(B, dtype=torch.float32, device=A.device)
+    _check(load().clfit_forward(ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), ctypes.c_void_p(S.data_ptr()),
+                                ctypes.c_void_p(Sv.data_ptr()), t, t, ctypes.c_void_p(Y.data_ptr()),
+                                m if B <= 1 else _ld(Y), B, ctypes.c_void_p(R.data_ptr()), m,
+                                ctypes.c_void_p(loss.data_ptr()), _stream_ptr(stream)))
+    return R, loss
+
+
+def clfit_adjoint(A, S, R, stream=None):
+    """grad = -A_S^T r per signal; S: (B, t); R: (m, B).  Returns (B, t)."""
+    torch = _torch()
+    A = _colmajor(A, torch.float32)
+    R = _colmajor(R, torch.float32)
+    m, n = A.shape
+    S = S.to(torch.int32).contiguous()
+    B, t = S.shape
+    grad = torch.empty((B, t), dtype=torch.float32, device=A.device)
+    _check(load().clfit_adjoint(ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), ctypes.c_void_p(S.data_ptr()),
+                                t, t, ctypes.c_void_p(R.data_ptr()), m if B <= 1 else _ld(R), B,
+                                ctypes.c_void_p(grad.data_ptr()), _stream_ptr(stream)))
+    return grad
+
+
+def clfit_adam_step(A, S, Sv, R, mom, vel, tau, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
+                    stream=None):
+    """Adjoint fused with one Adam step; updates Sv, mom, vel in place and
+    returns the gradient (B, t)."""
+    torch = _torch()
+    A = _colmajor(A, torch.float32)
+    R = _colmajor(R, torch.float32)
+    m, n = A.shape
+    S = S.to(torch.int32).contiguous()
+    for x in (Sv, mom, vel):
+        if x.dtype != torch.float32 or not x.is_contiguous():
+            raise ValueError("Sv, mom, vel must be contiguous float32 (B, t) tensors")
+    B, t = S.shape
+    grad = torch.empty((B, t), dtype=torch.float32, device=A.device)
+    _check(load().clfit_adam_step(ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), ctypes.c_void_p(S.data_ptr()),
+                                  ctypes.c_void_p(Sv.data_ptr()), t, t, ctypes.c_void_p(R.data_ptr()),
+                                  m if B <= 1 else _ld(R), B, ctypes.c_void_p(mom.data_ptr()),
+                                  ctypes.c_void_p(vel.data_ptr()), int(tau), float(lr), float(beta1),
+                                  float(beta2), float(eps), ctypes.c_void_p(grad.data_ptr()),
+                                  _stream_ptr(stream)))
+    return grad

@@ -1,0 +1,500 @@
+// Host runtime of the library: plan/workspace management, argument
+// validation, the per-iteration launch sequence and the C ABI declared in
+// include/cs_omp.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "cs_internal.cuh"
+
+using namespace cs;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+cs_status fail(cs_status st, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return st;
+}
+
+cs_status cuda_fail(cudaError_t e, const char* where) {
+    return fail(CS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    bool changed = false;
+    cudaError_t err = cudaSuccess;
+    explicit DeviceGuard(int dev) {
+        err = cudaGetDevice(&prev);
+        if (err == cudaSuccess && prev != dev) {
+            err = cudaSetDevice(dev);
+            changed = (err == cudaSuccess);
+        }
+    }
+    ~DeviceGuard() {
+        if (changed) cudaSetDevice(prev);
+    }
+};
+
+}  // namespace
+
+struct cs_plan {
+    int device = 0;
+    int m_max = 0, n_max = 0, B_max = 0, k_max = 0;
+    int mp_max = 0, mh_max = 0, nw_max = 0, nch_max = 0;
+    char* ws = nullptr;
+    size_t ws_bytes = 0;
+    float* A32 = nullptr;
+    __nv_bfloat16* A16 = nullptr;
+    float* Y32 = nullptr;
+    float* R32 = nullptr;
+    __nv_bfloat16* R16 = nullptr;
+    uint32_t* mask = nullptr;
+    float* cand_val = nullptr;
+    int* cand_idx = nullptr;
+    float* gcol = nullptr;
+    float* dnorm = nullptr;
+    float* bt = nullptr;
+    double* L = nullptr;
+    double* z = nullptr;
+    double* x64 = nullptr;
+    float* G = nullptr;
+    float* bvec = nullptr;
+    float* am = nullptr;
+    float* av = nullptr;
+    int* tau = nullptr;
+    float* colnorm_max = nullptr;
+    unsigned* counters = nullptr;
+    float* tab = nullptr;      // Adam bias-correction table, grown on demand
+    int tab_cap = 0;
+    char* io = nullptr;        // device staging for the host-buffer entry points
+    size_t io_bytes = 0;
+};
+
+namespace {
+
+struct Carver {
+    size_t off = 0;
+    template <class T>
+    size_t take(size_t count) {
+        off = (off + 255) & ~size_t(255);
+        size_t o = off;
+        off += count * sizeof(T);
+        return o;
+    }
+};
+
+cs_status ensure_tab(cs_plan* P, int len) {
+    if (len <= P->tab_cap) return CS_OK;
+    if (P->tab) {
+        cudaError_t e = cudaFree(P->tab);
+        P->tab = nullptr;
+        P->tab_cap = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
+    }
+    int cap = std::max(len, 2048);
+    cudaError_t e = cudaMalloc(&P->tab, sizeof(float) * 2 * (size_t)cap);
+    if (e != cudaSuccess) return fail(CS_ENOMEM, "cudaMalloc(adam table): %s", cudaGetErrorString(e));
+    P->tab_cap = cap;
+    return CS_OK;
+}
+
+cs_status validate(const cs_plan* P, const float* A, int m, int n, int lda, const float* Y,
+                   int ldy, int B, const int32_t* support, const float* coef, const int32_t* n_iter,
+                   const float* res_norm, const int32_t* sig_status, const cs_omp_params* op) {
+    if (!P) return fail(CS_EINVAL, "plan is NULL");
+    if (!op) return fail(CS_EINVAL, "params is NULL");
+    if (m < 1 || n < 1) return fail(CS_EINVAL, "m=%d, n=%d must be >= 1", m, n);
+    if (B < 0) return fail(CS_EINVAL, "batch=%d must be >= 0", B);
+    if (lda < m) return fail(CS_EINVAL, "lda=%d < m=%d", lda, m);
+    if (ldy < m) return fail(CS_EINVAL, "ldy=%d < m=%d", ldy, m);
+    if (op->k < 1 || op->k > m || op->k > n)
+        return fail(CS_EINVAL, "k=%d must satisfy 1 <= k <= min(m=%d, n=%d)", op->k, m, n);
+    if (!(op->tol >= 0.0)) return fail(CS_EINVAL, "tol must be >= 0");
+    if (op->prec != CS_CORR_FP32 && op->prec != CS_CORR_BF16)
+        return fail(CS_EINVAL, "prec=%d is not a cs_corr_prec", op->prec);
+    if (op->topc < 0 || op->topc > kTopcMax) return fail(CS_EINVAL, "topc=%d not in [0, 8]", op->topc);
+    if (m > P->m_max || n > P->n_max || B > P->B_max)
+        return fail(CS_EINVAL, "problem m=%d n=%d batch=%d exceeds the plan (%d, %d, %d)", m, n, B,
+                    P->m_max, P->n_max, P->B_max);
+    if (op->k > P->k_max) return fail(CS_ENOTSUP, "k=%d exceeds the plan k_max=%d", op->k, P->k_max);
+    if (B > 0 && (!A || !Y || !support || !coef || !n_iter || !res_norm || !sig_status))
+        return fail(CS_EINVAL, "a required array pointer is NULL");
+    if (op->prec == CS_CORR_BF16 && !corr_tc_supported(m, n))
+        return fail(CS_ENOTSUP, "bf16 tensor-core correlation unavailable for m=%d n=%d", m, n);
+    return CS_OK;
+}
+
+IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int32_t* support,
+                   float* coef, int32_t* n_iter, float* res_norm, int32_t* sig_status) {
+    IterArgs a{};
+    a.m = m;
+    a.n = n;
+    a.B = B;
+    a.k = op->k;
+    a.kmax = P->k_max;
+    a.iters = (op->max_iter > 0) ? std::min(op->k, op->max_iter) : op->k;
+    a.mp = round_up(m, 4);
+    a.mh = round_up(m, 8);
+    a.nw = ceil_div(n, 32);
+    a.prec = op->prec;
+    if (op->prec == CS_CORR_FP32) {
+        a.nch = ceil_div(n, kCorrFp32TileN);
+        a.topc = 1;
+    } else {
+        a.nch = ceil_div(n, kCorrTcTileN);
+        a.topc = op->topc > 0 ? op->topc : kTopcMax;
+    }
+    a.tol = op->tol;
+    a.A32 = P->A32;
+    a.A16 = P->A16;
+    a.Y32 = P->Y32;
+    a.R32 = P->R32;
+    a.R16 = (op->prec == CS_CORR_BF16) ? P->R16 : nullptr;
+    a.mask = P->mask;
+    a.cand_val = P->cand_val;
+    a.cand_idx = P->cand_idx;
+    a.gcol = P->gcol;
+    a.dnorm = P->dnorm;
+    a.bt = P->bt;
+    a.L = P->L;
+    a.z = P->z;
+    a.x64 = P->x64;
+    a.G = P->G;
+    a.bvec = P->bvec;
+    a.am = P->am;
+    a.av = P->av;
+    a.tau = P->tau;
+    a.colnorm_max = P->colnorm_max;
+    a.counters = P->counters;
+    a.support = support;
+    a.coef = coef;
+    a.n_iter = n_iter;
+    a.res_norm = res_norm;
+    a.status = sig_status;
+    return a;
+}
+
+#define CS_TRY_LAUNCH(expr, what)                         \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
+// The solve: set-up, then per iteration correlation -> select -> fit -> residual.
+cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* Y, int ldy, int B,
+                int32_t* support, float* coef, int32_t* n_iter, float* res_norm,
+                int32_t* sig_status, const cs_omp_params* op, const cs_clomp_params* cp,
+                cudaStream_t s) {
+    cs_status st = validate(P, A, m, n, lda, Y, ldy, B, support, coef, n_iter, res_norm,
+                            sig_status, op);
+    if (st != CS_OK) return st;
+    if (cp) {
+        if (cp->steps < 0) return fail(CS_EINVAL, "steps=%d must be >= 0", cp->steps);
+        if (cp->form != CS_CL_GATHER && cp->form != CS_CL_GRAM)
+            return fail(CS_EINVAL, "form=%d is not a cs_cl_form", cp->form);
+        if (!(cp->beta1 >= 0.f && cp->beta1 < 1.f && cp->beta2 >= 0.f && cp->beta2 < 1.f))
+            return fail(CS_EINVAL, "Adam betas must lie in [0, 1)");
+        if (!(cp->eps >= 0.f) || !std::isfinite(cp->lr)) return fail(CS_EINVAL, "bad lr/eps");
+    }
+    if (B == 0) return CS_OK;
+    DeviceGuard dg(P->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+
+    IterArgs a = make_args(P, m, n, B, op, support, coef, n_iter, res_norm, sig_status);
+    const bool bf16 = (op->prec == CS_CORR_BF16);
+    a.need_gcol = cp ? 0 : 1;
+    a.need_gram = (cp && cp->form == CS_CL_GRAM) ? 1 : 0;
+
+    ClArgs c{};
+    if (cp) {
+        const int len = (cp->reset_adam_each_iter ? 1 : a.iters) * std::max(cp->steps, 1);
+        st = ensure_tab(P, len);
+        if (st != CS_OK) return st;
+        c.steps = cp->steps;
+        c.beta1 = cp->beta1;
+        c.beta2 = cp->beta2;
+        c.eps = cp->eps;
+        c.reset = cp->reset_adam_each_iter ? 1 : 0;
+        c.tab = P->tab;
+        c.tab_len = len;
+        CS_TRY_LAUNCH(launch_adam_table(P->tab, len, cp->lr, cp->beta1, cp->beta2, s), "adam table");
+    }
+
+    CS_TRY_LAUNCH(launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
+                                P->colnorm_max, s), "prep A");
+    CS_TRY_LAUNCH(launch_setup(a, Y, ldy, cp ? 1 : 0, s), "setup");
+    for (int it = 0; it < a.iters; ++it) {
+        if (bf16) CS_TRY_LAUNCH(launch_corr_tc(a, s), "correlation (tcgen05)");
+        else CS_TRY_LAUNCH(launch_corr_fp32(a, s), "correlation (fp32)");
+        CS_TRY_LAUNCH(launch_select(a, s), "select");
+        if (!cp) CS_TRY_LAUNCH(launch_chol(a, s), "cholesky");
+        else if (cp->form == CS_CL_GRAM) CS_TRY_LAUNCH(launch_clfit_gram(a, c, it, s), "cl fit (gram)");
+        else CS_TRY_LAUNCH(launch_clfit_gather(a, c, it, s), "cl fit (gather)");
+        CS_TRY_LAUNCH(launch_resid(a, s), "residual");
+    }
+    return CS_OK;
+}
+
+cs_status ensure_io(cs_plan* P, size_t bytes) {
+    if (bytes <= P->io_bytes) return CS_OK;
+    if (P->io) {
+        cudaFree(P->io);
+        P->io = nullptr;
+        P->io_bytes = 0;
+    }
+    cudaError_t e = cudaMalloc(&P->io, bytes);
+    if (e != cudaSuccess) return fail(CS_ENOMEM, "cudaMalloc(io): %s", cudaGetErrorString(e));
+    P->io_bytes = bytes;
+    return CS_OK;
+}
+
+cs_status solve_host(cs_plan* P, const float* A, int m, int n, int lda, const float* Y, int ldy,
+                     int B, int32_t* support, float* coef, int32_t* n_iter, float* res_norm,
+                     int32_t* sig_status, const cs_omp_params* op, const cs_clomp_params* cp,
+                     cudaStream_t s) {
+    cs_status st = validate(P, A, m, n, lda, Y, ldy, B, support, coef, n_iter, res_norm,
+                            sig_status, op);
+    if (st != CS_OK) return st;
+    if (B == 0) return CS_OK;
+    DeviceGuard dg(P->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    const int k = op->k;
+    Carver cv;
+    const size_t oA = cv.take<float>((size_t)m * n);
+    const size_t oY = cv.take<float>((size_t)m * B);
+    const size_t oS = cv.take<int32_t>((size_t)k * B);
+    const size_t oC = cv.take<float>((size_t)k * B);
+    const size_t oN = cv.take<int32_t>(B);
+    const size_t oR = cv.take<float>(B);
+    const size_t oT = cv.take<int32_t>(B);
+    st = ensure_io(P, cv.off);
+    if (st != CS_OK) return st;
+    float* dA = reinterpret_cast<float*>(P->io + oA);
+    float* dY = reinterpret_cast<float*>(P->io + oY);
+    int32_t* dS = reinterpret_cast<int32_t*>(P->io + oS);
+    float* dC = reinterpret_cast<float*>(P->io + oC);
+    int32_t* dN = reinterpret_cast<int32_t*>(P->io + oN);
+    float* dR = reinterpret_cast<float*>(P->io + oR);
+    int32_t* dT = reinterpret_cast<int32_t*>(P->io + oT);
+    CS_TRY_LAUNCH(cudaMemcpy2DAsync(dA, sizeof(float) * m, A, sizeof(float) * lda, sizeof(float) * m, n,
+                                    cudaMemcpyHostToDevice, s), "copy A");
+    CS_TRY_LAUNCH(cudaMemcpy2DAsync(dY, sizeof(float) * m, Y, sizeof(float) * ldy, sizeof(float) * m, B,
+                                    cudaMemcpyHostToDevice, s), "copy Y");
+    st = solve(P, dA, m, n, m, dY, m, B, dS, dC, dN, dR, dT, op, cp, s);
+    if (st != CS_OK) return st;
+    CS_TRY_LAUNCH(cudaMemcpyAsync(support, dS, sizeof(int32_t) * k * B, cudaMemcpyDeviceToHost, s), "copy support");
+    CS_TRY_LAUNCH(cudaMemcpyAsync(coef, dC, sizeof(float) * k * B, cudaMemcpyDeviceToHost, s), "copy coef");
+    CS_TRY_LAUNCH(cudaMemcpyAsync(n_iter, dN, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s), "copy n_iter");
+    CS_TRY_LAUNCH(cudaMemcpyAsync(res_norm, dR, sizeof(float) * B, cudaMemcpyDeviceToHost, s), "copy res_norm");
+    CS_TRY_LAUNCH(cudaMemcpyAsync(sig_status, dT, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s), "copy status");
+    CS_TRY_LAUNCH(cudaStreamSynchronize(s), "stream synchronize");
+    return CS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cs_status cs_plan_create(cs_plan** plan, int32_t m_max, int32_t n_max, int32_t batch_max,
+                         int32_t k_max) {
+    if (!plan) return fail(CS_EINVAL, "plan out-pointer is NULL");
+    *plan = nullptr;
+    if (m_max < 1 || n_max < 1 || batch_max < 1 || k_max < 1)
+        return fail(CS_EINVAL, "plan sizes must be >= 1 (m_max=%d n_max=%d batch_max=%d k_max=%d)",
+                    m_max, n_max, batch_max, k_max);
+    if (k_max > kKmaxLimit) return fail(CS_ENOTSUP, "k_max=%d exceeds %d", k_max, kKmaxLimit);
+    if (m_max > kMaxRowChunks * 128) return fail(CS_ENOTSUP, "m_max=%d exceeds %d", m_max, kMaxRowChunks * 128);
+    cs_plan* P = new cs_plan();
+    cudaError_t e = cudaGetDevice(&P->device);
+    if (e != cudaSuccess) {
+        delete P;
+        return cuda_fail(e, "cudaGetDevice");
+    }
+    P->m_max = m_max;
+    P->n_max = n_max;
+    P->B_max = batch_max;
+    P->k_max = k_max <= 32 ? 32 : 64;   // on-chip kernels are built for 32 or 64
+    P->mp_max = round_up(m_max, 4);
+    P->mh_max = round_up(m_max, 8);
+    P->nw_max = ceil_div(n_max, 32);
+    P->nch_max = ceil_div(n_max, kCorrFp32TileN);
+    const size_t Bm = (size_t)batch_max, K = (size_t)P->k_max;
+    Carver cv;
+    const size_t oA32 = cv.take<float>((size_t)n_max * P->mp_max);
+    const size_t oA16 = cv.take<__nv_bfloat16>((size_t)n_max * P->mh_max);
+    const size_t oY32 = cv.take<float>(Bm * P->mp_max);
+    const size_t oR32 = cv.take<float>(Bm * P->mp_max);
+    const size_t oR16 = cv.take<__nv_bfloat16>(Bm * P->mh_max);
+    const size_t oMask = cv.take<uint32_t>(Bm * P->nw_max);
+    const size_t oCv = cv.take<float>(Bm * P->nch_max * kTopcMax);
+    const size_t oCi = cv.take<int>(Bm * P->nch_max * kTopcMax);
+    const size_t oGc = cv.take<float>(K * Bm);
+    const size_t oDn = cv.take<float>(Bm);
+    const size_t oBt = cv.take<float>(Bm);
+    const size_t oL = cv.take<double>(K * K * Bm);
+    const size_t oZ = cv.take<double>(K * Bm);
+    const size_t oX = cv.take<double>(K * Bm);
+    const size_t oG = cv.take<float>(Bm * K * K);
+    const size_t oBv = cv.take<float>(Bm * K);
+    const size_t oAm = cv.take<float>(Bm * K);
+    const size_t oAv = cv.take<float>(Bm * K);
+    const size_t oTau = cv.take<int>(Bm);
+    const size_t oCn = cv.take<float>(1);
+    const size_t oCnt = cv.take<unsigned>(16);
+    e = cudaMalloc(&P->ws, cv.off);
+    if (e != cudaSuccess) {
+        delete P;
+        return fail(CS_ENOMEM, "cudaMalloc(%zu bytes): %s", cv.off, cudaGetErrorString(e));
+    }
+    P->ws_bytes = cv.off;
+    char* w = P->ws;
+    P->A32 = reinterpret_cast<float*>(w + oA32);
+    P->A16 = reinterpret_cast<__nv_bfloat16*>(w + oA16);
+    P->Y32 = reinterpret_cast<float*>(w + oY32);
+    P->R32 = reinterpret_cast<float*>(w + oR32);
+    P->R16 = reinterpret_cast<__nv_bfloat16*>(w + oR16);
+    P->mask = reinterpret_cast<uint32_t*>(w + oMask);
+    P->cand_val = reinterpret_cast<float*>(w + oCv);
+    P->cand_idx = reinterpret_cast<int*>(w + oCi);
+    P->gcol = reinterpret_cast<float*>(w + oGc);
+    P->dnorm = reinterpret_cast<float*>(w + oDn);
+    P->bt = reinterpret_cast<float*>(w + oBt);
+    P->L = reinterpret_cast<double*>(w + oL);
+    P->z = reinterpret_cast<double*>(w + oZ);
+    P->x64 = reinterpret_cast<double*>(w + oX);
+    P->G = reinterpret_cast<float*>(w + oG);
+    P->bvec = reinterpret_cast<float*>(w + oBv);
+    P->am = reinterpret_cast<float*>(w + oAm);
+    P->av = reinterpret_cast<float*>(w + oAv);
+    P->tau = reinterpret_cast<int*>(w + oTau);
+    P->colnorm_max = reinterpret_cast<float*>(w + oCn);
+    P->counters = reinterpret_cast<unsigned*>(w + oCnt);
+    // zero everything once so that padding rows of the bf16 operands are 0
+    e = cudaMemset(P->ws, 0, cv.off);
+    if (e != cudaSuccess) {
+        cudaFree(P->ws);
+        delete P;
+        return cuda_fail(e, "cudaMemset");
+    }
+    *plan = P;
+    return CS_OK;
+}
+
+cs_status cs_plan_destroy(cs_plan* plan) {
+    if (!plan) return CS_OK;
+    DeviceGuard dg(plan->device);
+    cudaDeviceSynchronize();
+    if (plan->ws) cudaFree(plan->ws);
+    if (plan->tab) cudaFree(plan->tab);
+    if (plan->io) cudaFree(plan->io);
+    delete plan;
+    return CS_OK;
+}
+
+cs_status omp_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                            const float* Y, int32_t ldy, int32_t batch, int32_t* support,
+                            float* coef, int32_t* n_iter, float* res_norm, int32_t* sig_status,
+                            const cs_omp_params* params, void* stream) {
+    return solve(plan, A, m, n, lda, Y, ldy, batch, support, coef, n_iter, res_norm, sig_status,
+                 params, nullptr, (cudaStream_t)stream);
+}
+
+cs_status omp_solve(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                    const float* y, int32_t* support, float* coef, int32_t* n_iter,
+                    float* res_norm, int32_t* sig_status, const cs_omp_params* params,
+                    void* stream) {
+    return solve(plan, A, m, n, lda, y, m, 1, support, coef, n_iter, res_norm, sig_status, params,
+                 nullptr, (cudaStream_t)stream);
+}
+
+cs_status clomp_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                              const float* Y, int32_t ldy, int32_t batch, int32_t* support,
+                              float* coef, int32_t* n_iter, float* res_norm,
+                              int32_t* sig_status, const cs_clomp_params* params, void* stream) {
+    if (!params) return fail(CS_EINVAL, "params is NULL");
+    return solve(plan, A, m, n, lda, Y, ldy, batch, support, coef, n_iter, res_norm, sig_status,
+                 &params->base, params, (cudaStream_t)stream);
+}
+
+cs_status clomp_solve(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                      const float* y, int32_t* support, float* coef, int32_t* n_iter,
+                      float* res_norm, int32_t* sig_status, const cs_clomp_params* params,
+                      void* stream) {
+    if (!params) return fail(CS_EINVAL, "params is NULL");
+    return solve(plan, A, m, n, lda, y, m, 1, support, coef, n_iter, res_norm, sig_status,
+                 &params->base, params, (cudaStream_t)stream);
+}
+
+cs_status omp_solve_batched_host(cs_plan* plan, const float* A, int32_t m, int32_t n,
+                                 int32_t lda, const float* Y, int32_t ldy, int32_t batch,
+                                 int32_t* support, float* coef, int32_t* n_iter,
+                                 float* res_norm, int32_t* sig_status,
+                                 const cs_omp_params* params, void* stream) {
+    return solve_host(plan, A, m, n, lda, Y, ldy, batch, support, coef, n_iter, res_norm,
+                      sig_status, params, nullptr, (cudaStream_t)stream);
+}
+
+cs_status clomp_solve_batched_host(cs_plan* plan, const float* A, int32_t m, int32_t n,
+                                   int32_t lda, const float* Y, int32_t ldy, int32_t batch,
+                                   int32_t* support, float* coef, int32_t* n_iter,
+                                   float* res_norm, int32_t* sig_status,
+                                   const cs_clomp_params* params, void* stream) {
+    if (!params) return fail(CS_EINVAL, "params is NULL");
+    return solve_host(plan, A, m, n, lda, Y, ldy, batch, support, coef, n_iter, res_norm,
+                      sig_status, &params->base, params, (cudaStream_t)stream);
+}
+
+cs_status clfit_forward(const float* A, int32_t m, int32_t n, int32_t lda, const int32_t* S,
+                        const float* Sv, int32_t t, int32_t lds, const float* Y, int32_t ldy,
+                        int32_t batch, float* R, int32_t ldr, float* loss, void* stream) {
+    if (m < 1 || n < 1 || t < 0 || batch < 0) return fail(CS_EINVAL, "bad sizes");
+    if (lda < m || ldy < m || ldr < m || lds < t) return fail(CS_EINVAL, "bad leading dimension");
+    if (batch == 0) return CS_OK;
+    if (!A || !Y || !R || (t > 0 && (!S || !Sv))) return fail(CS_EINVAL, "NULL array");
+    cudaError_t e = launch_clfit_forward(A, m, lda, S, Sv, t, lds, Y, ldy, batch, R, ldr, loss,
+                                         (cudaStream_t)stream);
+    return e == cudaSuccess ? CS_OK : cuda_fail(e, "clfit_forward");
+}
+
+cs_status clfit_adjoint(const float* A, int32_t m, int32_t n, int32_t lda, const int32_t* S,
+                        int32_t t, int32_t lds, const float* R, int32_t ldr, int32_t batch,
+                        float* grad, void* stream) {
+    if (m < 1 || n < 1 || t < 0 || batch < 0) return fail(CS_EINVAL, "bad sizes");
+    if (lda < m || ldr < m || lds < t) return fail(CS_EINVAL, "bad leading dimension");
+    if (batch == 0 || t == 0) return CS_OK;
+    if (!A || !R || !S || !grad) return fail(CS_EINVAL, "NULL array");
+    cudaError_t e = launch_clfit_adjoint(A, m, lda, S, nullptr, t, lds, R, ldr, batch, grad, nullptr,
+                                         nullptr, 1, 0.f, 0.f, 0.f, 0.f, 0, (cudaStream_t)stream);
+    return e == cudaSuccess ? CS_OK : cuda_fail(e, "clfit_adjoint");
+}
+
+cs_status clfit_adam_step(const float* A, int32_t m, int32_t n, int32_t lda, const int32_t* S,
+                          float* Sv, int32_t t, int32_t lds, const float* R, int32_t ldr,
+                          int32_t batch, float* mom, float* vel, int32_t tau, float lr,
+                          float beta1, float beta2, float eps, float* grad, void* stream) {
+    if (m < 1 || n < 1 || t < 0 || batch < 0 || tau < 1) return fail(CS_EINVAL, "bad sizes/tau");
+    if (lda < m || ldr < m || lds < t) return fail(CS_EINVAL, "bad leading dimension");
+    if (!(beta1 >= 0.f && beta1 < 1.f && beta2 >= 0.f && beta2 < 1.f)) return fail(CS_EINVAL, "bad betas");
+    if (batch == 0 || t == 0) return CS_OK;
+    if (!A || !R || !S || !Sv || !mom || !vel) return fail(CS_EINVAL, "NULL array");
+    cudaError_t e = launch_clfit_adjoint(A, m, lda, S, Sv, t, lds, R, ldr, batch, grad, mom, vel,
+                                         tau, lr, beta1, beta2, eps, 1, (cudaStream_t)stream);
+    return e == cudaSuccess ? CS_OK : cuda_fail(e, "clfit_adam_step");
+}
+
+const char* cs_last_error(void) { return g_last_error.c_str(); }
+
+const char* cs_version(void) { return "cs-omp-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,144 @@
+// Internal declarations shared by the CUDA translation units of the library.
+// Nothing here is part of the public C ABI (include/cs_omp.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+
+#include "cs_omp.h"
+
+namespace cs {
+
+constexpr int kKmaxLimit = 64;     // largest support size the per-signal kernels hold on chip
+constexpr int kMaxRowChunks = 8;   // m <= 8 * 128 = 1024 for the warp-per-signal kernels
+constexpr int kCorrFp32TileN = 128;   // atoms per CTA of the fp32 correlation
+constexpr int kCorrTcTileN = 256;     // atoms per CTA of the tensor-core correlation
+constexpr int kTopcMax = 8;
+
+__host__ __device__ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int ceil_div(int x, int a) { return (x + a - 1) / a; }
+
+// State of one batched solve, passed by value to every per-iteration kernel.
+// Layouts (B = batch, K = kmax of the plan):
+//   A32   [n][mp]  float, column j of A at A32 + j*mp, zero-padded rows
+//   A16   [n][mh]  bf16 copy of A32 (tensor-core operand)
+//   Y32   [B][mp]  float, measurements, zero-padded
+//   R32   [B][mp]  float residual;  R16 [B][mh] bf16 residual (tensor-core operand)
+//   mask  [B][nw]  selected-atom bitset
+//   cand  [B][nch][topc]  candidate |c| and atom index per atom tile
+//   gcol  [K][B]   Gram column A_S^T a_j of the new atom (float)
+//   L     [K][K][B] Cholesky factor (double), z, x64 [K][B] (double)
+//   G     [B][K][K] Gram matrix of the support (float, CLOMP Gram form), bvec [B][K]
+//   am, av [B][K]  Adam moments; tau [B] Adam step counter
+//   support, coef [B][k] (caller outputs, k = params.k)
+struct IterArgs {
+    int m, n, B, k, kmax, iters, mp, mh, nw, nch, topc, prec;
+    double tol;
+    const float* A32;
+    const __nv_bfloat16* A16;
+    float* Y32;
+    float* R32;
+    __nv_bfloat16* R16;
+    uint32_t* mask;
+    float* cand_val;
+    int* cand_idx;
+    float* gcol;
+    float* dnorm;
+    float* bt;
+    double* L;
+    double* z;
+    double* x64;
+    float* G;
+    float* bvec;
+    float* am;
+    float* av;
+    int* tau;
+    const float* colnorm_max;   // max_j ||a_j||_2 (for the bf16 certificate)
+    unsigned* counters;         // [0] bf16 certificate fallbacks, [1] device error flags
+    int* support;
+    float* coef;
+    int* n_iter;
+    float* res_norm;
+    int* status;
+    int need_gcol;   // OMP: write gcol/dnorm/bt for the Cholesky update
+    int need_gram;   // CLOMP Gram form: maintain G and bvec
+};
+
+struct ClArgs {
+    int steps;
+    float beta1, beta2, eps;
+    int reset;
+    const float* tab;    // [2][tab_len]: lr/(1-b1^tau), 1/sqrt(1-b2^tau) for tau = 1..tab_len
+    int tab_len;
+};
+
+// ---- launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh, float* A32,
+                          __nv_bfloat16* A16, float* colnorm_max, cudaStream_t s);
+cudaError_t launch_setup(const IterArgs& a, const float* Y, int ldy, int clomp, cudaStream_t s);
+cudaError_t launch_adam_table(float* tab, int len, float lr, float beta1, float beta2,
+                              cudaStream_t s);
+cudaError_t launch_corr_fp32(const IterArgs& a, cudaStream_t s);
+cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s);
+bool corr_tc_supported(int m, int n);
+cudaError_t launch_select(const IterArgs& a, cudaStream_t s);
+cudaError_t launch_chol(const IterArgs& a, cudaStream_t s);
+cudaError_t launch_resid(const IterArgs& a, cudaStream_t s);
+cudaError_t launch_clfit_gram(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
+cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
+
+cudaError_t launch_clfit_forward(const float* A, int m, int lda, const int32_t* S, const float* Sv,
+                                 int t, int lds, const float* Y, int ldy, int batch, float* R,
+                                 int ldr, float* loss, cudaStream_t s);
+cudaError_t launch_clfit_adjoint(const float* A, int m, int lda, const int32_t* S, float* Sv,
+                                 int t, int lds, const float* R, int ldr, int batch, float* grad,
+                                 float* mom, float* vel, int tau, float lr, float beta1,
+                                 float beta2, float eps, int adam, cudaStream_t s);
+
+// ---- device helpers -------------------------------------------------------
+#ifdef __CUDACC__
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ float dot4(float4 a, float4 b) {
+    return fmaf(a.w, b.w, fmaf(a.z, b.z, fmaf(a.y, b.y, a.x * b.x)));
+}
+
+// Candidate order: larger |c| first, lower atom index on equal |c|; j < 0 is empty.
+__device__ __forceinline__ bool cand_better(float v, int j, float bv, int bj) {
+    if (j < 0) return false;
+    if (bj < 0) return true;
+    return v > bv || (v == bv && j < bj);
+}
+
+__device__ __forceinline__ void warp_argmax(float& v, int& j) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        float ov = __shfl_xor_sync(0xffffffffu, v, o);
+        int oj = __shfl_xor_sync(0xffffffffu, j, o);
+        if (cand_better(ov, oj, v, j)) { v = ov; j = oj; }
+    }
+}
+
+// Transposing reduction: every lane holds v[0..31]; afterwards v[0] of lane l
+// holds the sum over the warp of v[l].  31 shuffles.
+__device__ __forceinline__ void warp_reduce_scatter32(float (&v)[32]) {
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            float send = upper ? v[i] : v[i + off];
+            float keep = upper ? v[i + off] : v[i];
+            v[i] = keep + __shfl_xor_sync(0xffffffffu, send, off);
+        }
+    }
+}
+#endif
+
+}  // namespace cs
