@@ -1,0 +1,417 @@
+#!/usr/bin/env python
+"""Benchmark of the batched OMP / CLOMP hot path on GB300.
+
+Workload (one step): n=1024, m=256, one shared Gaussian A with unit columns,
+4096 signals, each 32-sparse with values +-(1+|N(0,1)|), 40 dB noise; CLOMP
+with 50 Adam steps per iteration at lr 1e-2, k = 32 iterations.  Inputs are
+synthetic (seeded), resident in HBM when the timed region starts; L2 is
+flushed (256 MiB write, untimed) before every timed step.
+
+Headline: CLOMP signals/s (bf16 tensor-core correlation, Gram-form CL fit),
+with plain float32 OMP and the other forms timed on the same GPU, the
+per-phase kernel times and the roofline of the dominant kernel, a live parity
+check of a sample against the FP64 oracle, the oracle's own throughput on the
+host cores (cpu_baseline) and an end-to-end run through the host-buffer C ABI.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+For N > 1 (torchrun), each rank solves its own 4096-signal batch (signals are
+independent problems, Eq. 3): weak scaling, no collective on the data path;
+the timing barrier and max over ranks use torch.distributed.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "signals/s at rel-err≤1e-5 vs FP64 oracle; CLOMP vs plain OMP, same GB300"
+UNIT = "signals/s"
+CL = dict(steps=50, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8)
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--prec", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--form", choices=["gram", "gather"], default="gram")
+    ap.add_argument("--batch", type=int, default=4096)
+    ap.add_argument("--cpu-sample", type=int, default=1024)
+    ap.add_argument("--no-extras", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(args, p):
+    return {"workload": f"batched OMP/CLOMP, n={p.n}, m={p.m}, {p.B} signals per GPU, k={p.k}, "
+                        f"Gaussian A (unit columns), 32-sparse +-(1+|N(0,1)|), 40 dB SNR",
+            "n": p.n, "m": p.m, "signals_per_gpu": p.B, "k": p.k, "algo": "clomp",
+            "correlation": args.prec, "cl_form": args.form, "adam_steps_per_iter": CL["steps"],
+            "lr": CL["lr"], "l2": "flushed before every timed step (256 MiB write, untimed)",
+            "parallelism": "signals sharded across GPUs, A replicated (no collective)"}
+
+
+# ------------------------------------------------------------ reference arm
+def run_reference(args):
+    """The reference arm is the FP64 CPU oracle, run as it stands on the host
+    cores: each step solves a bounded sample of the same workload."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    import workloads
+    p = workloads.config_batched(B=args.batch)
+    sample = min(256, p.B)
+    A32 = np.asfortranarray(p.A, dtype=np.float32).astype(np.float64, order="F")
+    Y32 = np.asfortranarray(p.Y[:, :sample], dtype=np.float32).astype(np.float64, order="F")
+    f = lambda x: float(np.float32(x))
+    kw = dict(steps=CL["steps"], lr=f(CL["lr"]), beta1=f(CL["beta1"]), beta2=f(CL["beta2"]), eps=f(CL["eps"]))
+    for _ in range(args.warmup):
+        oracle.clomp(A32, Y32[:, :32], p.k, **kw)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.clomp(A32, Y32, p.k, **kw)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = sample / (ms / 1e3)
+    cores = oracle.max_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, p),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{sample} of the {p.B} signals per step (CLOMP, FP64 oracle, OpenMP)"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------ clocks
+class ClockSampler:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                                       "-lms", "100", "-i", str(self.idx)], stdout=self.f,
+                                      stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.25)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[5:9]))
+                except ValueError:
+                    pass
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for _, _, r in rows for i, v in enumerate(r) if v.lower() == "active"})
+        loaded = [c for c, _, _ in rows if c > 300] or [c for c, _, _ in rows]
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(m for _, m, _ in rows),
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ------------------------------------------------------------ our arm
+def kernel_sha(rel):
+    h = hashlib.sha256(open(os.path.join(ROOT, rel), "rb").read()).hexdigest()
+    return h[:16]
+
+
+def recorded_traffic(kernel, sha):
+    """dram bytes per launch from a committed ncu summary, if it was taken on
+    this exact kernel source; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.split()
+        if len(f) >= 3 and not line.startswith("#") and f[0] == kernel and f[1] == sha:
+            return float(f[2])
+    return None
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+    ws, rank, local = dist_env()
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    import paper_2501_11592_gb300 as cs
+    import workloads
+    cs.load()
+
+    p = workloads.config_batched(B=args.batch)
+    A32 = np.asfortranarray(p.A, dtype=np.float32)
+    Y32 = np.asfortranarray(p.Y, dtype=np.float32)
+    A = torch.from_numpy(A32).cuda()
+    Y = torch.from_numpy(Y32).cuda()
+    plan = cs.Plan(p.m, p.n, p.B, p.k)
+    out = cs._outputs(p.B, p.k, A.device)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def make_step(algo, prec, form="gram"):
+        if algo == "omp":
+            return lambda: cs.omp_solve_batched(A, Y, p.k, prec=prec, plan=plan, out=out)
+        return lambda: cs.clomp_solve_batched(A, Y, p.k, prec=prec, form=form, plan=plan, out=out, **CL)
+
+    def barrier():
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(fn, steps, warmup):
+        for _ in range(warmup):
+            fn()
+        barrier()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        plan.profile(reset=True)
+        t0 = time.perf_counter()
+        for a, b in ev:
+            flush.zero_()
+            a.record(stream)
+            fn()
+            b.record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+        ms = sum(a.elapsed_time(b) for a, b in ev)
+        launches = sum(n for n, _ in plan.profile(reset=True).values())
+        if dist is not None:
+            t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / steps, wall, launches
+
+    # --- headline: CLOMP, bf16 correlation, Gram-form fit
+    head = make_step("clomp", args.prec, args.form)
+    gpu_index = int(os.environ.get("CUDA_VISIBLE_DEVICES", str(local)).split(",")[local]) \
+        if os.environ.get("CUDA_VISIBLE_DEVICES", "").replace(",", "").isdigit() else local
+    clk = ClockSampler(gpu_index)
+    clk.start()
+    ms, wall, launches = timed(head, args.steps, args.warmup)
+    clocks = clk.stop()
+    plan.counters(reset=True)
+    value = ws * p.B / (ms / 1e3)
+
+    # --- per-phase kernel times (separate pass with events around every launch)
+    plan.set_profiling(True)
+    for _ in range(args.warmup):
+        head()
+    plan.profile(reset=True)
+    nprof = max(3, min(args.steps, 20))
+    for _ in range(nprof):
+        flush.zero_()
+        head()
+    phases = plan.profile(reset=True)
+    plan.set_profiling(False)
+    fallbacks, errflags = plan.counters(reset=True)
+
+    # --- live parity check of a sample against the FP64 oracle
+    head()
+    torch.cuda.synchronize()
+    parity = None
+    if rank == 0:
+        import oracle
+        idx = np.random.default_rng(7).choice(p.B, size=128, replace=False)
+        idx.sort()
+        f = lambda x: float(np.float32(x))
+        o = oracle.clomp(A32.astype(np.float64), Y32[:, idx].astype(np.float64), p.k, steps=CL["steps"],
+                         lr=f(CL["lr"]), beta1=f(CL["beta1"]), beta2=f(CL["beta2"]), eps=f(CL["eps"]))
+        sup = out.support.cpu().numpy()[idx]
+        coef = out.coef.cpu().numpy()[idx].astype(np.float64)
+        match = np.all(sup == o["support"], axis=1)
+        err = np.linalg.norm(coef - o["coef"], axis=1) / np.linalg.norm(o["coef"], axis=1)
+        parity = {"signals": int(len(idx)), "supports_identical": int(match.sum()),
+                  "max_coef_rel_err": float(err[match].max()) if match.any() else None,
+                  "tolerance": 1e-5}
+
+    # --- the other forms on the same GPU
+    compare = {}
+    if not args.no_extras:
+        ksteps = max(3, min(args.steps, 10))
+        for name, algo, prec, form in [("omp_fp32", "omp", "fp32", "gram"), ("omp_bf16", "omp", "bf16", "gram"),
+                                       ("clomp_fp32_gram", "clomp", "fp32", "gram"),
+                                       ("clomp_bf16_gather", "clomp", "bf16", "gather")]:
+            m_, _, _ = timed(make_step(algo, prec, form), ksteps, 3)
+            compare[name] = {"ms_per_step": m_, "signals_per_s": ws * p.B / (m_ / 1e3)}
+        compare["clomp_headline"] = {"ms_per_step": ms, "signals_per_s": value}
+        compare["clomp_over_omp_fp32"] = value / compare["omp_fp32"]["signals_per_s"]
+
+    # --- end to end through the host-buffer C ABI (copies inside the timed region)
+    Ah = torch.from_numpy(A32.T.copy()).pin_memory().numpy().T          # Fortran-order pinned views
+    Yh = torch.from_numpy(Y32.T.copy()).pin_memory().numpy().T
+    hout = dict(support=torch.empty((p.B, p.k), dtype=torch.int32).pin_memory().numpy(),
+                coef=torch.empty((p.B, p.k), dtype=torch.float32).pin_memory().numpy(),
+                n_iter=torch.empty(p.B, dtype=torch.int32).pin_memory().numpy(),
+                res_norm=torch.empty(p.B, dtype=torch.float32).pin_memory().numpy(),
+                status=torch.empty(p.B, dtype=torch.int32).pin_memory().numpy())
+    hstep = lambda: cs.clomp_solve_batched_host(Ah, Yh, p.k, prec=args.prec, form=args.form, plan=plan,
+                                                out=hout, **CL)
+    for _ in range(3):
+        hstep()
+    barrier()
+    esteps = max(3, min(args.steps, 20))
+    te = 0.0
+    for _ in range(esteps):
+        flush.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hstep()            # returns after the outputs are back on the host
+        te += time.perf_counter() - t0
+    if dist is not None:
+        t = torch.tensor([te], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        te = float(t.item())
+    e2e_value = ws * p.B * esteps / te
+    h2d = (p.m * p.n + p.m * p.B) * 4
+    d2h = p.B * p.k * 8 + p.B * 12
+
+    # --- CPU baseline: the FP64 oracle on the host cores, bounded sample
+    cpu = None
+    if rank == 0 and ws == 1:
+        import oracle
+        S = min(args.cpu_sample, p.B)
+        f = lambda x: float(np.float32(x))
+        A64 = A32.astype(np.float64, order="F")
+        Y64 = np.asfortranarray(Y32[:, :S], dtype=np.float64)
+        t0 = time.perf_counter()
+        oracle.clomp(A64, Y64, p.k, steps=CL["steps"], lr=f(CL["lr"]), beta1=f(CL["beta1"]),
+                     beta2=f(CL["beta2"]), eps=f(CL["eps"]))
+        tc = time.perf_counter() - t0
+        cpu = {"value": S / tc, "unit": UNIT, "cores": oracle.max_threads(), "kind": "oracle",
+               "sample": f"first {S} of the {p.B} signals (CLOMP, FP64 oracle, OpenMP over signals), {tc:.1f} s"}
+
+    # --- roofline of the dominant kernel
+    peaks, src = measured_peaks()
+    per = {ph: {"launches": n, "ms_total": t, "ms_avg": (t / n if n else None)} for ph, (n, t) in phases.items()}
+    dom = max((ph for ph in phases if ph != "setup"), key=lambda ph: phases[ph][1])
+    iters = p.k
+    B = p.B
+    roof_corr = None
+    n_corr, t_corr = phases["correlation"]
+    if n_corr:
+        flops = 2.0 * p.m * p.n * B                    # per launch: every signal is live for all k iterations
+        avg_s = t_corr / n_corr / 1e3
+        ach = flops / avg_s / 1e12
+        if args.prec == "bf16":
+            pk = peaks["bf16_tflops_sustained"]
+            roof_corr = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                         "peak_source": f"bf16_tflops_sustained ({src})"}
+        else:
+            pk = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+            roof_corr = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
+                         "peak_source": "152 SMs x 128 FP32 FMA/clk x 2 x sm_max_mhz"}
+        sha = kernel_sha("paper_2501_11592_gb300/csrc/" + ("k_corr_tc.cu" if args.prec == "bf16" else "k_corr_fp32.cu"))
+        tr = recorded_traffic("corr_" + args.prec, sha)
+        roof_corr["traffic"] = tr
+    # algorithmic work of the other phases (per solve, summed over the k iterations)
+    sum_t = iters * (iters + 1) / 2.0
+    sum_t2 = iters * (iters + 1) * (2 * iters + 1) / 6.0
+    fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    work = {
+        # Gram form: g = G s - b per Adam step (2 t^2 flops) + Adam update (~10 t flops)
+        "fit": ("alu", B * CL["steps"] * (2 * sum_t2 + 10 * sum_t), fp32_peak, "TFLOP/s"),
+        # residual: read t columns of A (4m bytes each), y, write r (fp32 + bf16)
+        "residual": ("hbm", B * (4.0 * p.m * sum_t + iters * p.m * (4 + 4 + 2)), peaks["hbm_gbs"], "GB/s"),
+        # select: read topc*nch candidate pairs and re-score 8 columns + the new column and y
+        "select": ("hbm", B * iters * (8.0 * 8 * 4 + 10 * 4.0 * p.m), peaks["hbm_gbs"], "GB/s"),
+    }
+    roofs = {"correlation": roof_corr}
+    for ph, (bound, amount, pk, unit) in work.items():
+        n_, t_ = phases[ph]
+        if not n_ or t_ <= 0:
+            continue
+        nsolves = n_ / iters
+        ach = amount * nsolves / (t_ / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
+        roofs[ph] = {"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk,
+                     "traffic": None}
+    roofline = dict(roofs[dom]) if roofs.get(dom) else roof_corr
+    roofline["kernel_phase"] = dom
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": args.prec, "data": "synthetic",
+            "config": workload_config(args, p),
+            "roofline": roofline,
+            "roofline_correlation": roof_corr,
+            "roofline_phases": roofs,
+            "phases": per,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "api": "clomp_solve_batched_host (pinned host buffers, outputs copied back)"},
+            "clocks": clocks,
+            "gpu_launches": int(launches),
+            "parity": parity,
+            "bf16_certificate_fallbacks": fallbacks,
+            "device_error_flags": errflags,
+            "compare": compare,
+            "wall_s_timed_region": wall}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

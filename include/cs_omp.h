@@ -98,8 +98,10 @@ typedef struct {
 typedef struct cs_plan cs_plan;
 
 /* Create a plan on the current CUDA device with workspace for problems up to
- * m_max x n_max, batch_max signals and k_max <= 64 iterations.  Allocates
- * device memory once; solves on this plan allocate nothing.
+ * m_max x n_max (m_max <= 1024), batch_max signals and k_max <= 64
+ * iterations.  Allocates the workspace once.  Later calls allocate only
+ * when a CLOMP call needs a longer Adam bias-correction table than any
+ * earlier call, and on the first use of the host-buffer entry points.
  * Returns CS_EINVAL for non-positive sizes, CS_ENOTSUP for k_max > 64,
  * CS_ENOMEM / CS_ECUDA on allocation failure (then *plan is NULL). */
 cs_status cs_plan_create(cs_plan** plan, int32_t m_max, int32_t n_max, int32_t batch_max,
@@ -183,6 +185,42 @@ cs_status clfit_adam_step(const float* A, int32_t m, int32_t n, int32_t lda, con
                           float* Sv, int32_t t, int32_t lds, const float* R, int32_t ldr,
                           int32_t batch, float* mom, float* vel, int32_t tau, float lr,
                           float beta1, float beta2, float eps, float* grad, void* stream);
+
+/* The residual-injection layer alone (Methods, "Coefficients learning on
+ * OMP": A^T r as a fully connected layer with fixed weights A):
+ *   C = A^T R,  C is n x batch column-major with ldc >= n, R is m x batch
+ * with ldr >= m.  prec selects float32 SIMT or bf16 tensor cores (fp32
+ * accumulation).  Uses the plan's workspace; asynchronous on `stream`. */
+cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                       const float* R, int32_t ldr, int32_t batch, int32_t prec, float* C,
+                       int32_t ldc, void* stream);
+
+/* Synchronise `stream` and copy the plan's device counters to out[0..3]:
+ * out[0] = signals whose bf16 candidate certificate failed and were
+ * re-scored over all atoms in float32; out[1] = device error flags (non-zero
+ * when a bounded wait inside a kernel gave up).  reset != 0 zeroes them.
+ * Returns CS_ETIMEOUT when out[1] != 0. */
+cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* stream);
+
+/* Measurement support.  Phases of a solve: */
+enum {
+    CS_PHASE_SETUP = 0,    /* copy/convert A and Y, initial state, Adam table */
+    CS_PHASE_CORR = 1,     /* correlation A^T r with the fused candidate epilogue */
+    CS_PHASE_SELECT = 2,   /* candidate merge, float32 re-score, support update, Gram column */
+    CS_PHASE_FIT = 3,      /* Cholesky update (OMP) or Adam coefficient fit (CLOMP) */
+    CS_PHASE_RESID = 4,    /* residual, norm and stopping test */
+    CS_PHASES = 5
+};
+
+/* enable != 0: bracket every later kernel launch of solves on this plan with
+ * CUDA events on the solve's stream (adds a little GPU time per launch). */
+cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable);
+
+/* Kernel launches per phase since the last reset (always counted), and --
+ * when profiling was enabled -- the summed event time per phase in
+ * milliseconds.  ms and launches hold CS_PHASES entries each (either may be
+ * NULL).  Waits for the recorded events.  reset != 0 clears both. */
+cs_status cs_plan_profile(cs_plan* plan, double* ms, int64_t* launches, int32_t reset);
 
 /* Message describing the last non-OK return on the calling thread ("" if none). */
 const char* cs_last_error(void);

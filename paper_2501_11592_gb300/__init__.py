@@ -21,7 +21,7 @@ __all__ = [
     "load", "Plan", "omp_solve", "omp_solve_batched", "clomp_solve", "clomp_solve_batched",
     "omp_solve_batched_host", "clomp_solve_batched_host", "clfit_forward", "clfit_adjoint",
     "clfit_adam_step", "CSError", "SIG_REACHED_K", "SIG_REACHED_TOL", "SIG_MAX_ITER",
-    "SIG_DEPENDENT", "SIG_NONFINITE", "library_path",
+    "SIG_DEPENDENT", "SIG_NONFINITE", "library_path", "correlate", "PHASES",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -31,6 +31,7 @@ CS_OK, CS_EINVAL, CS_ENOMEM, CS_ECUDA, CS_ETIMEOUT, CS_ENOTSUP = 0, -1, -2, -3, 
 SIG_REACHED_K, SIG_REACHED_TOL, SIG_MAX_ITER, SIG_DEPENDENT, SIG_NONFINITE = 0, 1, 2, 3, 4
 PREC = {"fp32": 0, "bf16": 1}
 FORM = {"gather": 0, "gram": 1}
+PHASES = ("setup", "correlation", "select", "fit", "residual")
 _STATUS_NAMES = {CS_EINVAL: "CS_EINVAL", CS_ENOMEM: "CS_ENOMEM", CS_ECUDA: "CS_ECUDA",
                  CS_ETIMEOUT: "CS_ETIMEOUT", CS_ENOTSUP: "CS_ENOTSUP"}
 
@@ -85,7 +86,12 @@ def load():
         L.clfit_adjoint.argtypes = [vp, i32, i32, i32, vp, i32, i32, vp, i32, i32, vp, vp]
         L.clfit_adam_step.argtypes = [vp, i32, i32, i32, vp, vp, i32, i32, vp, i32, i32, vp, vp,
                                       i32, f32, f32, f32, f32, vp, vp]
-        for fn in ("cs_plan_create", "cs_plan_destroy", "omp_solve_batched", "omp_solve_batched_host",
+        L.cs_correlate.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, i32, vp, i32, vp]
+        L.cs_plan_counters.argtypes = [vp, vp, i32, vp]
+        L.cs_plan_set_profiling.argtypes = [vp, i32]
+        L.cs_plan_profile.argtypes = [vp, vp, vp, i32]
+        for fn in ("cs_correlate", "cs_plan_counters", "cs_plan_set_profiling", "cs_plan_profile",
+                   "cs_plan_create", "cs_plan_destroy", "omp_solve_batched", "omp_solve_batched_host",
                    "clomp_solve_batched", "clomp_solve_batched_host", "omp_solve", "clomp_solve",
                    "clfit_forward", "clfit_adjoint", "clfit_adam_step"):
             getattr(L, fn).restype = ctypes.c_int
@@ -139,6 +145,28 @@ class Plan:
 
     def fits(self, m, n, B, k):
         return m <= self.dims[0] and n <= self.dims[1] and B <= self.dims[2] and k <= self.dims[3]
+
+    def counters(self, reset=False, stream=None):
+        """(certificate fallbacks, device error flags); synchronises the stream."""
+        import numpy as np
+        out = np.zeros(4, np.uint32)
+        rc = load().cs_plan_counters(self.h, ctypes.c_void_p(out.ctypes.data), int(bool(reset)),
+                                     _stream_ptr(stream))
+        if rc not in (CS_OK, CS_ETIMEOUT):
+            _check(rc)
+        return int(out[0]), int(out[1])
+
+    def set_profiling(self, enable=True):
+        _check(load().cs_plan_set_profiling(self.h, int(bool(enable))))
+
+    def profile(self, reset=True):
+        """{phase: (launches, milliseconds)} since the last reset."""
+        import numpy as np
+        ms = np.zeros(len(PHASES), np.float64)
+        n = np.zeros(len(PHASES), np.int64)
+        _check(load().cs_plan_profile(self.h, ctypes.c_void_p(ms.ctypes.data),
+                                      ctypes.c_void_p(n.ctypes.data), int(bool(reset))))
+        return {ph: (int(n[i]), float(ms[i])) for i, ph in enumerate(PHASES)}
 
     def close(self):
         if self.h is not None and self.h.value:
@@ -269,6 +297,21 @@ def clomp_solve_batched_host(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=
     return _host_batched(load().clomp_solve_batched_host, A, Y, k,
                          _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
                                        reset_adam, form), plan, stream, out)
+
+
+def correlate(A, R, prec="fp32", plan=None, stream=None):
+    """C = A^T R (n x B, column-major) -- the residual-injection layer alone."""
+    torch = _torch()
+    A = _colmajor(A, torch.float32)
+    R = _colmajor(R, torch.float32)
+    m, n = A.shape
+    B = R.shape[1]
+    p = _plan_for(m, n, B, 1, plan)
+    C = torch.empty((B, n), dtype=torch.float32, device=A.device).t()
+    _check(load().cs_correlate(p.h, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), ctypes.c_void_p(R.data_ptr()),
+                               m if B <= 1 else _ld(R), B, PREC[prec], ctypes.c_void_p(C.data_ptr()), n,
+                               _stream_ptr(stream)))
+    return C
 
 
 def clfit_forward(A, S, Sv, Y, stream=None):

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "cs_internal.cuh"
 
@@ -79,6 +80,13 @@ struct cs_plan {
     int tab_cap = 0;
     char* io = nullptr;        // device staging for the host-buffer entry points
     size_t io_bytes = 0;
+    // measurement: launch counts per phase (always) and, when profiling is
+    // enabled, CUDA event pairs around every launch
+    int64_t launches[CS_PHASES] = {};
+    int profiling = 0;
+    struct Mark { int phase; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    std::vector<cudaEvent_t> pool;
 };
 
 namespace {
@@ -145,7 +153,7 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
     a.kmax = P->k_max;
     a.iters = (op->max_iter > 0) ? std::min(op->k, op->max_iter) : op->k;
     a.mp = round_up(m, 4);
-    a.mh = round_up(m, 8);
+    a.mh = round_up(m, 64);   // bf16 rows: whole 128-byte swizzle rows for TMA
     a.nw = ceil_div(n, 32);
     a.prec = op->prec;
     if (op->prec == CS_CORR_FP32) {
@@ -191,6 +199,32 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
         if (e_ != cudaSuccess) return cuda_fail(e_, what); \
     } while (0)
 
+cudaEvent_t pool_event(cs_plan* P) {
+    if (!P->pool.empty()) {
+        cudaEvent_t e = P->pool.back();
+        P->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Run one launch of `phase`, counting it and (when profiling) timing it.
+template <class F>
+cudaError_t timed(cs_plan* P, int phase, cudaStream_t s, F&& launch) {
+    P->launches[phase] += 1;
+    if (!P->profiling) return launch();
+    cudaEvent_t a = pool_event(P), b = pool_event(P);
+    if (a && b) cudaEventRecord(a, s);
+    cudaError_t e = launch();
+    if (a && b) {
+        cudaEventRecord(b, s);
+        P->marks.push_back({phase, a, b});
+    }
+    return e;
+}
+
 // The solve: set-up, then per iteration correlation -> select -> fit -> residual.
 cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* Y, int ldy, int B,
                 int32_t* support, float* coef, int32_t* n_iter, float* res_norm,
@@ -228,20 +262,25 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         c.reset = cp->reset_adam_each_iter ? 1 : 0;
         c.tab = P->tab;
         c.tab_len = len;
-        CS_TRY_LAUNCH(launch_adam_table(P->tab, len, cp->lr, cp->beta1, cp->beta2, s), "adam table");
+        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] { return launch_adam_table(P->tab, len, cp->lr, cp->beta1, cp->beta2, s); }),
+                      "adam table");
     }
 
-    CS_TRY_LAUNCH(launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
-                                P->colnorm_max, s), "prep A");
-    CS_TRY_LAUNCH(launch_setup(a, Y, ldy, cp ? 1 : 0, s), "setup");
+    CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] {
+                      return launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
+                                           P->colnorm_max, s);
+                  }), "prep A");
+    CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] { return launch_setup(a, Y, ldy, cp ? 1 : 0, s); }), "setup");
     for (int it = 0; it < a.iters; ++it) {
-        if (bf16) CS_TRY_LAUNCH(launch_corr_tc(a, s), "correlation (tcgen05)");
-        else CS_TRY_LAUNCH(launch_corr_fp32(a, s), "correlation (fp32)");
-        CS_TRY_LAUNCH(launch_select(a, s), "select");
-        if (!cp) CS_TRY_LAUNCH(launch_chol(a, s), "cholesky");
-        else if (cp->form == CS_CL_GRAM) CS_TRY_LAUNCH(launch_clfit_gram(a, c, it, s), "cl fit (gram)");
-        else CS_TRY_LAUNCH(launch_clfit_gather(a, c, it, s), "cl fit (gather)");
-        CS_TRY_LAUNCH(launch_resid(a, s), "residual");
+        if (bf16) CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, s, [&] { return launch_corr_tc(a, s); }), "correlation (tcgen05)");
+        else CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, s, [&] { return launch_corr_fp32(a, s); }), "correlation (fp32)");
+        CS_TRY_LAUNCH(timed(P, CS_PHASE_SELECT, s, [&] { return launch_select(a, s); }), "select");
+        if (!cp) CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, s, [&] { return launch_chol(a, s); }), "cholesky");
+        else if (cp->form == CS_CL_GRAM)
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, s, [&] { return launch_clfit_gram(a, c, it, s); }), "cl fit (gram)");
+        else
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, s, [&] { return launch_clfit_gather(a, c, it, s); }), "cl fit (gather)");
+        CS_TRY_LAUNCH(timed(P, CS_PHASE_RESID, s, [&] { return launch_resid(a, s); }), "residual");
     }
     return CS_OK;
 }
@@ -326,7 +365,7 @@ cs_status cs_plan_create(cs_plan** plan, int32_t m_max, int32_t n_max, int32_t b
     P->B_max = batch_max;
     P->k_max = k_max <= 32 ? 32 : 64;   // on-chip kernels are built for 32 or 64
     P->mp_max = round_up(m_max, 4);
-    P->mh_max = round_up(m_max, 8);
+    P->mh_max = round_up(m_max, 64);
     P->nw_max = ceil_div(n_max, 32);
     P->nch_max = ceil_div(n_max, kCorrFp32TileN);
     const size_t Bm = (size_t)batch_max, K = (size_t)P->k_max;
@@ -395,6 +434,11 @@ cs_status cs_plan_destroy(cs_plan* plan) {
     if (!plan) return CS_OK;
     DeviceGuard dg(plan->device);
     cudaDeviceSynchronize();
+    for (auto& mk : plan->marks) {
+        cudaEventDestroy(mk.a);
+        cudaEventDestroy(mk.b);
+    }
+    for (auto e : plan->pool) cudaEventDestroy(e);
     if (plan->ws) cudaFree(plan->ws);
     if (plan->tab) cudaFree(plan->tab);
     if (plan->io) cudaFree(plan->io);
@@ -491,6 +535,84 @@ cs_status clfit_adam_step(const float* A, int32_t m, int32_t n, int32_t lda, con
     cudaError_t e = launch_clfit_adjoint(A, m, lda, S, Sv, t, lds, R, ldr, batch, grad, mom, vel,
                                          tau, lr, beta1, beta2, eps, 1, (cudaStream_t)stream);
     return e == cudaSuccess ? CS_OK : cuda_fail(e, "clfit_adam_step");
+}
+
+cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                       const float* R, int32_t ldr, int32_t batch, int32_t prec, float* C,
+                       int32_t ldc, void* stream) {
+    if (!plan) return fail(CS_EINVAL, "plan is NULL");
+    if (m < 1 || n < 1 || batch < 0) return fail(CS_EINVAL, "bad sizes m=%d n=%d batch=%d", m, n, batch);
+    if (lda < m || ldr < m || ldc < n) return fail(CS_EINVAL, "bad leading dimension");
+    if (m > plan->m_max || n > plan->n_max || batch > plan->B_max)
+        return fail(CS_EINVAL, "problem exceeds the plan");
+    if (prec != CS_CORR_FP32 && prec != CS_CORR_BF16) return fail(CS_EINVAL, "prec=%d", prec);
+    if (prec == CS_CORR_BF16 && !corr_tc_supported(m, n))
+        return fail(CS_ENOTSUP, "bf16 tensor-core correlation unavailable for m=%d n=%d", m, n);
+    if (batch == 0) return CS_OK;
+    if (!A || !R || !C) return fail(CS_EINVAL, "NULL array");
+    DeviceGuard dg(plan->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int mp = round_up(m, 4), mh = round_up(m, 64);
+    const bool bf16 = (prec == CS_CORR_BF16);
+    CS_TRY_LAUNCH(launch_prep_A(A, lda, m, n, mp, mh, plan->A32, bf16 ? plan->A16 : nullptr, nullptr, s),
+                  "prep A");
+    CS_TRY_LAUNCH(launch_prep_R(R, ldr, m, batch, mp, mh, bf16 ? nullptr : plan->R32,
+                                bf16 ? plan->R16 : nullptr, s), "prep R");
+    if (bf16)
+        CS_TRY_LAUNCH(launch_corr_tc_dense(plan->R16, plan->A16, mh, batch, n, C, ldc, plan->counters + 1, s),
+                      "correlation (tcgen05)");
+    else
+        CS_TRY_LAUNCH(launch_corr_fp32_dense(plan->R32, plan->A32, mp, batch, n, C, ldc, s),
+                      "correlation (fp32)");
+    return CS_OK;
+}
+
+cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* stream) {
+    if (!plan || !out) return fail(CS_EINVAL, "NULL argument");
+    DeviceGuard dg(plan->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    cudaStream_t s = (cudaStream_t)stream;
+    CS_TRY_LAUNCH(cudaMemcpyAsync(out, plan->counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s),
+                  "copy counters");
+    if (reset) CS_TRY_LAUNCH(cudaMemsetAsync(plan->counters, 0, 4 * sizeof(uint32_t), s), "reset counters");
+    CS_TRY_LAUNCH(cudaStreamSynchronize(s), "stream synchronize");
+    if (out[1] != 0) return fail(CS_ETIMEOUT, "a bounded device-side wait gave up (flags 0x%x)", out[1]);
+    return CS_OK;
+}
+
+cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable) {
+    if (!plan) return fail(CS_EINVAL, "plan is NULL");
+    plan->profiling = enable ? 1 : 0;
+    return CS_OK;
+}
+
+cs_status cs_plan_profile(cs_plan* plan, double* ms, int64_t* launches, int32_t reset) {
+    if (!plan) return fail(CS_EINVAL, "plan is NULL");
+    DeviceGuard dg(plan->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    double acc[CS_PHASES] = {};
+    for (auto& mk : plan->marks) {
+        float t = 0.f;
+        cudaError_t e = cudaEventSynchronize(mk.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventSynchronize");
+        e = cudaEventElapsedTime(&t, mk.a, mk.b);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaEventElapsedTime");
+        acc[mk.phase] += t;
+    }
+    for (int i = 0; i < CS_PHASES; ++i) {
+        if (ms) ms[i] = acc[i];
+        if (launches) launches[i] = plan->launches[i];
+    }
+    if (reset) {
+        for (auto& mk : plan->marks) {
+            plan->pool.push_back(mk.a);
+            plan->pool.push_back(mk.b);
+        }
+        plan->marks.clear();
+        for (int i = 0; i < CS_PHASES; ++i) plan->launches[i] = 0;
+    }
+    return CS_OK;
 }
 
 const char* cs_last_error(void) { return g_last_error.c_str(); }

@@ -22,7 +22,7 @@ __host__ __device__ inline int ceil_div(int x, int a) { return (x + a - 1) / a; 
 // State of one batched solve, passed by value to every per-iteration kernel.
 // Layouts (B = batch, K = kmax of the plan):
 //   A32   [n][mp]  float, column j of A at A32 + j*mp, zero-padded rows
-//   A16   [n][mh]  bf16 copy of A32 (tensor-core operand)
+//   A16   [n][mh]  bf16 copy of A32 (tensor-core operand), mh = m rounded up to 64
 //   Y32   [B][mp]  float, measurements, zero-padded
 //   R32   [B][mp]  float residual;  R16 [B][mh] bf16 residual (tensor-core operand)
 //   mask  [B][nw]  selected-atom bitset
@@ -80,7 +80,13 @@ cudaError_t launch_setup(const IterArgs& a, const float* Y, int ldy, int clomp, 
 cudaError_t launch_adam_table(float* tab, int len, float lr, float beta1, float beta2,
                               cudaStream_t s);
 cudaError_t launch_corr_fp32(const IterArgs& a, cudaStream_t s);
+cudaError_t launch_corr_fp32_dense(const float* R32, const float* A32, int mp, int B, int n, float* C,
+                                   int ldc, cudaStream_t s);
 cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s);
+cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n,
+                                 float* C, int ldc, unsigned* errflag, cudaStream_t s);
+cudaError_t launch_prep_R(const float* R, int ldr, int m, int B, int mp, int mh, float* R32,
+                          __nv_bfloat16* R16, cudaStream_t s);
 bool corr_tc_supported(int m, int n);
 cudaError_t launch_select(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_chol(const IterArgs& a, cudaStream_t s);

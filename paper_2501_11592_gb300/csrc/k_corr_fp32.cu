@@ -15,10 +15,13 @@ namespace {
 
 constexpr int BM = 128, BN = kCorrFp32TileN, BK = 16, PAD = 4;
 
+// DENSE: write C^T (B x n, row stride ldd) instead of the argmax epilogue.
+template <bool DENSE>
 __global__ void __launch_bounds__(256, 2)
 k_corr_fp32(const float* __restrict__ R32, const float* __restrict__ A32, int mp, int B, int n,
             const uint32_t* __restrict__ mask, int nw, const int* __restrict__ status,
-            float* __restrict__ cand_val, int* __restrict__ cand_idx, int nch) {
+            float* __restrict__ cand_val, int* __restrict__ cand_idx, int nch,
+            float* __restrict__ dense, int ldd) {
     __shared__ __align__(16) float As[2][BK][BM + PAD];
     __shared__ __align__(16) float Bs[2][BK][BN + PAD];
     __shared__ int any_live;
@@ -31,7 +34,7 @@ k_corr_fp32(const float* __restrict__ R32, const float* __restrict__ A32, int mp
     __syncthreads();
     if (tid < BM) {
         const int b = b0 + tid;
-        if (b < B && status[b] < 0) any_live = 1;
+        if (b < B && (DENSE || status[b] < 0)) any_live = 1;
     }
     __syncthreads();
     if (!any_live) return;
@@ -98,6 +101,18 @@ k_corr_fp32(const float* __restrict__ R32, const float* __restrict__ A32, int mp
         __syncthreads();
     }
 
+    if constexpr (DENSE) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+            const int sig = b0 + (i < 4 ? ty * 4 + i : 64 + ty * 4 + (i - 4));
+            if (sig >= B) continue;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int atom = j0 + (j < 4 ? tx * 4 + j : 64 + tx * 4 + (j - 4));
+                if (atom < n) dense[(size_t)sig * ldd + atom] = acc[i][j];
+            }
+        }
+    } else {
     // Epilogue: masked |c| argmax per signal over this atom tile.
 #pragma unroll
     for (int i = 0; i < 8; ++i) {
@@ -130,14 +145,23 @@ k_corr_fp32(const float* __restrict__ R32, const float* __restrict__ A32, int mp
             cand_idx[(size_t)sig * nch + blockIdx.y] = bj;
         }
     }
+    }
 }
 
 }  // namespace
 
 cudaError_t launch_corr_fp32(const IterArgs& a, cudaStream_t s) {
     dim3 grid(ceil_div(a.B, BM), ceil_div(a.n, BN));
-    k_corr_fp32<<<grid, 256, 0, s>>>(a.R32, a.A32, a.mp, a.B, a.n, a.mask, a.nw, a.status,
-                                     a.cand_val, a.cand_idx, a.nch);
+    k_corr_fp32<false><<<grid, 256, 0, s>>>(a.R32, a.A32, a.mp, a.B, a.n, a.mask, a.nw, a.status,
+                                            a.cand_val, a.cand_idx, a.nch, nullptr, 0);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_corr_fp32_dense(const float* R32, const float* A32, int mp, int B, int n, float* C,
+                                   int ldc, cudaStream_t s) {
+    dim3 grid(ceil_div(B, BM), ceil_div(n, BN));
+    k_corr_fp32<true><<<grid, 256, 0, s>>>(R32, A32, mp, B, n, nullptr, 0, nullptr, nullptr, nullptr, 1,
+                                           C, ldc);
     return cudaGetLastError();
 }
 

@@ -1,10 +1,375 @@
-// K1: bf16 tensor-core correlation (tcgen05 + TMA) -- not built yet.
+// K1: bf16 tensor-core correlation C^T = R^T A on sm_103a (tcgen05 + TMA),
+// fp32 accumulation in tensor memory, fused masked top-c epilogue.
+//
+// The residual-injection branch (Methods, "Coefficients learning on OMP")
+// applies the fixed layer A to r^T for all signals at once -- a GEMM with
+// M = signals, N = atoms, K = m.  Both operands are K-major (one residual /
+// one column of A is contiguous), which is the native operand layout of
+// tcgen05.mma:
+//   * one CTA owns 128 signals x 256 atoms; the residual tile (128 x m) and
+//     the atom tile (256 x m) are staged by TMA in 64-element K chunks with
+//     the 128-byte swizzle, one mbarrier per chunk, so the MMAs of chunk 0
+//     start while later chunks are still in flight;
+//   * one thread issues 4 x tcgen05.mma (M=128, N=256, K=16) per chunk into a
+//     256-column fp32 accumulator in tensor memory;
+//   * the 4 warps then read their 32 TMEM lanes (= 32 signals) with
+//     tcgen05.ld, mask already-selected atoms, take |c| and keep a sorted
+//     top-c list per signal -- C itself never reaches global memory.
+// Every wait is bounded; on time-out the kernel raises a device error flag,
+// skips the epilogue, frees its tensor memory and returns.
+#include <cuda.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <mutex>
+
 #include "cs_internal.cuh"
 
 namespace cs {
+namespace {
 
-bool corr_tc_supported(int, int) { return false; }
+constexpr int TM = 128;              // signals per CTA (UMMA M, TMEM lanes)
+constexpr int TN = kCorrTcTileN;     // atoms per CTA (UMMA N, TMEM columns)
+constexpr int KCH = 64;              // bf16 elements per 128-byte swizzled row
+constexpr int R_CHUNK_BYTES = TM * KCH * 2;   // 16 KiB
+constexpr int A_CHUNK_BYTES = TN * KCH * 2;   // 32 KiB
+constexpr int MAX_KC = 4;            // m <= 256 staged at once
+constexpr unsigned long long WAIT_CYCLES = 4000000000ull;   // ~2 s
 
-cudaError_t launch_corr_tc(const IterArgs&, cudaStream_t) { return cudaErrorNotSupported; }
+static_assert(TN % 16 == 0 && TN >= 16 && TN <= 256, "UMMA N for M=128");
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Bounded wait on an mbarrier phase; false on time-out.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    const unsigned long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > WAIT_CYCLES) return false;
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), sm_100 descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFFu);   // start address
+    d |= (uint64_t)1u << 16;                    // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024u >> 4) << 32;          // stride byte offset
+    d |= (uint64_t)1u << 46;                    // descriptor version
+    d |= (uint64_t)2u << 61;                    // SWIZZLE_128B
+    return d;
+}
+
+// Instruction descriptor, kind::f16: bf16 A and B, fp32 D, both K-major.
+constexpr uint32_t make_idesc(int M, int N) {
+    return (1u << 4)                         // D format: f32
+           | (1u << 7)                       // A format: bf16
+           | (1u << 10)                      // B format: bf16
+           | ((uint32_t)(N >> 3) << 17)      // N / 8
+           | ((uint32_t)(M >> 4) << 24);     // M / 16
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
+        "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]),
+          "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]),
+          "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+struct TcArgs {
+    int B, n, kc, nch, topc, nw;
+    const uint32_t* mask;
+    const int* status;
+    float* cand_val;
+    int* cand_idx;
+    float* dense;       // optional dense output C^T (B x n, row stride ldd); nullptr = top-c only
+    int ldd;
+    unsigned* errflag;
+};
+
+__global__ void __launch_bounds__(128, 1)
+k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapA, TcArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[MAX_KC];
+    __shared__ __align__(8) uint64_t done_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int any_live;
+    __shared__ int failed;
+
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const int b0 = blockIdx.x * TM;
+    const int j0 = blockIdx.y * TN;
+
+    // Skip tiles whose signals have all stopped (uniform exit, before any
+    // barrier or tensor memory is set up).
+    if (tid == 0) { any_live = 0; failed = 0; }
+    __syncthreads();
+    {
+        const int b = b0 + tid;
+        if (p.dense != nullptr || (b < p.B && p.status[b] < 0)) any_live = 1;
+    }
+    __syncthreads();
+    if (!any_live) return;
+
+    // 1024-byte aligned operand tiles (128-byte swizzle atoms)
+    const uint32_t raw = smem_u32(smem_raw);
+    const uint32_t pad = ((raw + 1023u) & ~1023u) - raw;
+    uint8_t* sR = smem_raw + pad;                       // kc x 16 KiB
+    uint8_t* sA = sR + (size_t)p.kc * R_CHUNK_BYTES;    // kc x 32 KiB
+
+    if (tid == 0) {
+        for (int c = 0; c < p.kc; ++c) mbar_init(&full_bar[c], 1);
+        mbar_init(&done_bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(TN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+
+    if (tid == 0) {
+        // producer: all K chunks of both operands, one barrier per chunk
+        for (int c = 0; c < p.kc; ++c) {
+            mbar_arrive_expect_tx(&full_bar[c], R_CHUNK_BYTES + A_CHUNK_BYTES);
+            tma_load_2d(sR + (size_t)c * R_CHUNK_BYTES, &mapR, &full_bar[c], c * KCH, b0);
+            tma_load_2d(sA + (size_t)c * A_CHUNK_BYTES, &mapA, &full_bar[c], c * KCH, j0);
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        constexpr uint32_t idesc = make_idesc(TM, TN);
+        bool ok = true;
+        for (int c = 0; c < p.kc && ok; ++c) {
+            if (!mbar_wait(&full_bar[c], 0)) { ok = false; break; }
+            tc_fence_after();
+            const uint64_t da = smem_desc_sw128(smem_u32(sR + (size_t)c * R_CHUNK_BYTES));
+            const uint64_t db = smem_desc_sw128(smem_u32(sA + (size_t)c * A_CHUNK_BYTES));
+#pragma unroll
+            for (int k = 0; k < KCH / 16; ++k) {
+                // advance 16 elements (32 bytes) along K inside the swizzled row
+                umma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (c | k) != 0);
+            }
+        }
+        if (!ok) {
+            failed = 1;
+            atomicOr(p.errflag, 1u);
+        }
+        umma_commit(&done_bar);   // arrives once every issued MMA has completed
+    }
+
+    // Epilogue: all 4 warps; warp w reads TMEM lanes 32w..32w+31 (= signals).
+    const bool ok = mbar_wait(&done_bar, 0);
+    tc_fence_after();
+    if (!ok) {
+        if (lane == 0) atomicOr(p.errflag, 2u);
+    }
+    __syncwarp();
+    const int sig = b0 + warp * 32 + lane;
+    if (ok && !failed) {
+        float tv[kTopcMax];
+        int ti[kTopcMax];
+#pragma unroll
+        for (int e = 0; e < kTopcMax; ++e) { tv[e] = -1.f; ti[e] = -1; }
+        const bool live = sig < p.B;
+        for (int c0 = 0; c0 < TN; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld_wait();
+            if (!live) continue;
+            if (p.dense) {
+                for (int q = 0; q < 32; ++q) {
+                    const int atom = j0 + c0 + q;
+                    if (atom < p.n) p.dense[(size_t)sig * p.ldd + atom] = __uint_as_float(v[q]);
+                }
+                continue;
+            }
+            const int wbase = j0 + c0;   // 32-aligned: one mask word covers the chunk
+            const uint32_t mw = (wbase < p.n) ? p.mask[(size_t)sig * p.nw + (wbase >> 5)] : 0xffffffffu;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int atom = wbase + q;
+                if (atom < p.n && !((mw >> q) & 1u)) {
+                    const float a = fabsf(__uint_as_float(v[q]));
+                    if (cand_better(a, atom, tv[kTopcMax - 1], ti[kTopcMax - 1])) {
+                        tv[kTopcMax - 1] = a;
+                        ti[kTopcMax - 1] = atom;
+#pragma unroll
+                        for (int e = kTopcMax - 1; e > 0; --e) {
+                            if (cand_better(tv[e], ti[e], tv[e - 1], ti[e - 1])) {
+                                const float fv = tv[e]; tv[e] = tv[e - 1]; tv[e - 1] = fv;
+                                const int fi = ti[e]; ti[e] = ti[e - 1]; ti[e - 1] = fi;
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (live && !p.dense) {
+            const size_t o = ((size_t)sig * p.nch + blockIdx.y) * p.topc;
+#pragma unroll
+            for (int e = 0; e < kTopcMax; ++e)
+                if (e < p.topc) { p.cand_val[o + e] = tv[e]; p.cand_idx[o + e] = ti[e]; }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 1) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+    }
+}
+
+// ---- host side: tensor maps through the driver entry point (no libcuda link)
+using EncodeFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                              const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                              CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeFn get_encode() {
+    static EncodeFn fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeFn>(f);
+    });
+    return fn;
+}
+
+// 2-D bf16 map over rows of `row_elems` (a multiple of 64) with byte stride
+// `row_bytes`; box = 64 x box_rows, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap* map, const void* base, int row_elems, int rows, size_t row_bytes, int box_rows) {
+    EncodeFn enc = get_encode();
+    if (!enc) return false;
+    cuuint64_t gdim[2] = {(cuuint64_t)row_elems, (cuuint64_t)rows};
+    cuuint64_t gstride[1] = {(cuuint64_t)row_bytes};
+    cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+                     CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+size_t smem_bytes(int kc) { return (size_t)kc * (R_CHUNK_BYTES + A_CHUNK_BYTES) + 1024; }
+
+cudaError_t launch_tc(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n, TcArgs p,
+                      cudaStream_t s) {
+    CUtensorMap mR, mA;
+    if (!make_map(&mR, R16, mh, B, (size_t)mh * 2, TM) || !make_map(&mA, A16, mh, n, (size_t)mh * 2, TN))
+        return cudaErrorInvalidValue;
+    const size_t smem = std::max(smem_bytes(p.kc), (size_t)100 * 1024);   // <= 2 CTAs per SM (TMEM)
+    static int configured = 0;
+    if (!configured) {
+        cudaError_t e = cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes(MAX_KC));
+        if (e != cudaSuccess) return e;
+        configured = 1;
+    }
+    dim3 grid(ceil_div(B, TM), ceil_div(n, TN));
+    k_corr_tc<<<grid, 128, smem, s>>>(mR, mA, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool corr_tc_supported(int m, int n) { return m >= 1 && m <= MAX_KC * KCH && n >= 1 && get_encode() != nullptr; }
+
+cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s) {
+    TcArgs p{};
+    p.B = a.B;
+    p.n = a.n;
+    p.kc = a.mh / KCH;
+    p.nch = a.nch;
+    p.topc = a.topc;
+    p.nw = a.nw;
+    p.mask = a.mask;
+    p.status = a.status;
+    p.cand_val = a.cand_val;
+    p.cand_idx = a.cand_idx;
+    p.dense = nullptr;
+    p.errflag = a.counters + 1;
+    return launch_tc(a.R16, a.A16, a.mh, a.B, a.n, p, s);
+}
+
+cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n,
+                                 float* C, int ldc, unsigned* errflag, cudaStream_t s) {
+    TcArgs p{};
+    p.B = B;
+    p.n = n;
+    p.kc = mh / KCH;
+    p.nch = 1;
+    p.topc = 1;
+    p.nw = 1;
+    p.dense = C;
+    p.ldd = ldc;
+    p.errflag = errflag;
+    return launch_tc(R16, A16, mh, B, n, p, s);
+}
 
 }  // namespace cs

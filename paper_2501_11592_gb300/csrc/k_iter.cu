@@ -45,6 +45,20 @@ __global__ void k_prep_A(const float* __restrict__ A, int lda, int m, int n, int
     }
 }
 
+// Copy caller residuals (m x B, leading dimension ldr) into the padded
+// float32 and/or bf16 row layouts used by the correlation kernels.
+__global__ void k_prep_R(const float* __restrict__ R, int ldr, int m, int B, int mp, int mh,
+                         float* __restrict__ R32, __nv_bfloat16* __restrict__ R16) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= B) return;
+    const float* r = R + (size_t)b * ldr;
+    if (R32)
+        for (int i = lane; i < mp; i += 32) R32[(size_t)b * mp + i] = (i < m) ? r[i] : 0.f;
+    if (R16)
+        for (int i = lane; i < mh; i += 32) R16[(size_t)b * mh + i] = __float2bfloat16_rn(i < m ? r[i] : 0.f);
+}
+
 // Per-signal initial state: r = y, s = 0, empty support, status "running".
 __global__ void k_setup(IterArgs a, const float* __restrict__ Y, int ldy, int clomp) {
     const int lane = threadIdx.x & 31;
@@ -559,6 +573,12 @@ cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh,
         if (e != cudaSuccess) return e;
     }
     k_prep_A<<<ceil_div(n, 8), 256, 0, s>>>(A, lda, m, n, mp, mh, A32, A16, colnorm_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_R(const float* R, int ldr, int m, int B, int mp, int mh, float* R32,
+                          __nv_bfloat16* R16, cudaStream_t s) {
+    k_prep_R<<<ceil_div(B, 8), 256, 0, s>>>(R, ldr, m, B, mp, mh, R32, R16);
     return cudaGetLastError();
 }
 
