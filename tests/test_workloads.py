@@ -27,6 +27,6 @@ def test_batched_config_noise_and_values():
 
 def test_columnwise_2d_config():
     p = workloads.config_columnwise_2d(0.1, n_images=2)
-    assert (p.m, p.n, p.B, p.k) == (25, 256, 512, 8)
+    assert (p.m, p.n, p.B, p.k) == (26, 256, 512, 8)
     D = workloads.dct_synthesis(16)
     assert np.allclose(D.T @ D, np.eye(16))

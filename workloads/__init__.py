@@ -153,9 +153,10 @@ def config_batched(B=4096) -> Problem:
 def config_columnwise_2d(sr=0.3, n_images=64) -> Problem:
     """64 synthetic 256x256 images whose 2D-DCT coefficients are
     |N(0,1)| * (1+i+j)^-1.5 with random signs, processed as 256-long columns;
-    A = Phi * D256 with Phi i.i.d. N(0,1/m); m = floor(256*Sr); k = floor(m/3)."""
+    A = Phi * D256 with Phi i.i.d. N(0,1/m); m = 26/77/128 for Sr = 0.1/0.3/0.5
+    (256*Sr rounded to nearest); k = floor(m/3)."""
     N = 256
-    m = int(math.floor(N * sr))
+    m = int(math.floor(N * sr + 0.5))
     rng = rng_for(CFG_COLUMNWISE_2D, salt=int(round(sr * 10)))
     D = dct_synthesis(N)
     i = np.arange(N)[:, None]
