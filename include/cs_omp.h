@@ -202,6 +202,24 @@ cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int3
  * Returns CS_ETIMEOUT when out[1] != 0. */
 cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* stream);
 
+/* Batched plain OMP without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot allocate device memory when
+ * they solve -- real-time loops that forbid allocator calls after start-up,
+ * or host applications and plug-ins whose own allocator already owns the
+ * device memory and hands none to libraries.  Same arguments, kernels and
+ * results as omp_solve_batched, minus the plan: the scratch is one fixed
+ * 32 MiB device array that every GPU loading this library reserves until
+ * the process exits (about 12 KiB per signal at m = 256, k <= 32, plus
+ * 6 bytes per element of A; larger problems get CS_EINVAL and belong on
+ * omp_solve_batched).  The first call on each device looks the array's
+ * address up (make it before any stream capture); calls whose GPU work
+ * overlaps -- on different streams or threads -- race on the shared array. */
+cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_t n, int32_t lda,
+                                    const float* Y, int32_t ldy, int32_t batch, int32_t* support,
+                                    float* coef, int32_t* n_iter, float* res_norm,
+                                    int32_t* sig_status, const cs_omp_params* params,
+                                    void* stream);
+
 /* Measurement support.  Phases of a solve: */
 enum {
     CS_PHASE_SETUP = 0,    /* copy/convert A and Y, initial state, Adam table */

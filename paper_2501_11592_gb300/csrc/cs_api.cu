@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -620,3 +621,123 @@ const char* cs_last_error(void) { return g_last_error.c_str(); }
 const char* cs_version(void) { return "cs-omp-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Allocation-free batched OMP.
+//
+// Some callers cannot allocate device memory at the time they want to solve:
+// real-time loops that forbid allocator calls after start-up (an allocation
+// can block for an unbounded time), and host applications or plug-ins whose
+// own device allocator owns all the memory and hands none to libraries.
+// omp_solve_batched_noalloc serves them: it runs the
+// same kernels as omp_solve_batched, but its scratch (the padded copies of A
+// and Y, the residuals, candidate lists, support bitsets and the float64
+// Cholesky factors) lives in one fixed file-scope device array instead of a
+// plan.  Every GPU that loads this library reserves that array until the
+// process exits.
+//
+// The host cannot use the array's name as a device address, so the first
+// call on each device (with that device current) looks the address up with
+// cudaGetSymbolAddress and caches it; later calls reuse it.  That first call
+// therefore belongs before any stream capture.  All calls share the one
+// array and find the previous call's contents in it: everything a solve reads
+// is written by that solve first, and the device counters are cleared at the
+// start of every call.  Two calls whose work overlaps on the GPU (different
+// streams, or different host threads) race on the array.
+
+static constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+namespace {
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_base[kNoAllocMaxDevices] = {};
+
+}  // namespace
+
+extern "C" cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_t n, int32_t lda,
+                                               const float* Y, int32_t ldy, int32_t batch,
+                                               int32_t* support, float* coef, int32_t* n_iter,
+                                               float* res_norm, int32_t* sig_status,
+                                               const cs_omp_params* params, void* stream) {
+    if (!params) return fail(CS_EINVAL, "params is NULL");
+    if (m < 1 || n < 1 || batch < 0 || params->k < 1 || params->k > kKmaxLimit)
+        return fail(CS_EINVAL, "bad sizes m=%d n=%d batch=%d k=%d", m, n, batch, params->k);
+    if (m > kMaxRowChunks * 128) return fail(CS_ENOTSUP, "m=%d exceeds %d", m, kMaxRowChunks * 128);
+
+    // Scratch layout for exactly this problem (same buffers as a plan).
+    cs_plan P;
+    P.m_max = m;
+    P.n_max = n;
+    P.B_max = std::max(batch, 1);
+    P.k_max = params->k <= 32 ? 32 : 64;
+    P.mp_max = round_up(m, 4);
+    P.mh_max = round_up(m, 64);
+    P.nw_max = ceil_div(n, 32);
+    P.nch_max = ceil_div(n, kCorrFp32TileN);
+    const size_t Bm = (size_t)P.B_max, K = (size_t)P.k_max;
+    Carver cv;
+    const size_t oA32 = cv.take<float>((size_t)n * P.mp_max);
+    const size_t oA16 = cv.take<__nv_bfloat16>((size_t)n * P.mh_max);
+    const size_t oY32 = cv.take<float>(Bm * P.mp_max);
+    const size_t oR32 = cv.take<float>(Bm * P.mp_max);
+    const size_t oR16 = cv.take<__nv_bfloat16>(Bm * P.mh_max);
+    const size_t oMask = cv.take<uint32_t>(Bm * P.nw_max);
+    const size_t oCv = cv.take<float>(Bm * P.nch_max * kTopcMax);
+    const size_t oCi = cv.take<int>(Bm * P.nch_max * kTopcMax);
+    const size_t oGc = cv.take<float>(K * Bm);
+    const size_t oDn = cv.take<float>(Bm);
+    const size_t oBt = cv.take<float>(Bm);
+    const size_t oL = cv.take<double>(K * K * Bm);
+    const size_t oZ = cv.take<double>(K * Bm);
+    const size_t oX = cv.take<double>(K * Bm);
+    const size_t oTau = cv.take<int>(Bm);
+    const size_t oCn = cv.take<float>(1);
+    const size_t oCnt = cv.take<unsigned>(16);
+    if (cv.off > kNoAllocScratchBytes)
+        return fail(CS_EINVAL,
+                    "problem needs %zu bytes of scratch; omp_solve_batched_noalloc holds %zu "
+                    "(use omp_solve_batched with a plan)",
+                    cv.off, kNoAllocScratchBytes);
+    if (batch == 0) return CS_OK;
+
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CS_ENOTSUP, "device %d out of range", dev);
+    char* base = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_noalloc_mu);
+        if (!g_noalloc_base[dev]) {
+            void* ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+            g_noalloc_base[dev] = ptr;
+        }
+        base = static_cast<char*>(g_noalloc_base[dev]);
+    }
+    P.device = dev;
+    P.A32 = reinterpret_cast<float*>(base + oA32);
+    P.A16 = reinterpret_cast<__nv_bfloat16*>(base + oA16);
+    P.Y32 = reinterpret_cast<float*>(base + oY32);
+    P.R32 = reinterpret_cast<float*>(base + oR32);
+    P.R16 = reinterpret_cast<__nv_bfloat16*>(base + oR16);
+    P.mask = reinterpret_cast<uint32_t*>(base + oMask);
+    P.cand_val = reinterpret_cast<float*>(base + oCv);
+    P.cand_idx = reinterpret_cast<int*>(base + oCi);
+    P.gcol = reinterpret_cast<float*>(base + oGc);
+    P.dnorm = reinterpret_cast<float*>(base + oDn);
+    P.bt = reinterpret_cast<float*>(base + oBt);
+    P.L = reinterpret_cast<double*>(base + oL);
+    P.z = reinterpret_cast<double*>(base + oZ);
+    P.x64 = reinterpret_cast<double*>(base + oX);
+    P.tau = reinterpret_cast<int*>(base + oTau);
+    P.colnorm_max = reinterpret_cast<float*>(base + oCn);
+    P.counters = reinterpret_cast<unsigned*>(base + oCnt);
+    // The previous call's counters must not leak into this one.
+    e = cudaMemsetAsync(P.counters, 0, 16 * sizeof(unsigned), (cudaStream_t)stream);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
+    return solve(&P, A, m, n, lda, Y, ldy, batch, support, coef, n_iter, res_norm, sig_status, params,
+                 nullptr, (cudaStream_t)stream);
+}
