@@ -292,8 +292,17 @@ def main():
         for name, algo, prec, form in [("omp_fp32", "omp", "fp32", "gram"), ("omp_bf16", "omp", "bf16", "gram"),
                                        ("clomp_fp32_gram", "clomp", "fp32", "gram"),
                                        ("clomp_bf16_gather", "clomp", "bf16", "gather")]:
-            m_, _, _ = timed(make_step(algo, prec, form), ksteps, 3)
-            compare[name] = {"ms_per_step": m_, "signals_per_s": ws * p.B / (m_ / 1e3)}
+            fn = make_step(algo, prec, form)
+            m_, _, _ = timed(fn, ksteps, 3)
+            plan.set_profiling(True)
+            plan.profile(reset=True)
+            for _ in range(3):
+                flush.zero_()
+                fn()
+            ph = plan.profile(reset=True)
+            plan.set_profiling(False)
+            compare[name] = {"ms_per_step": m_, "signals_per_s": ws * p.B / (m_ / 1e3),
+                             "phase_ms_per_step": {k: round(v[1] / 3, 4) for k, v in ph.items()}}
         compare["clomp_headline"] = {"ms_per_step": ms, "signals_per_s": value}
         compare["clomp_over_omp_fp32"] = value / compare["omp_fp32"]["signals_per_s"]
 

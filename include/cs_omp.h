@@ -64,11 +64,13 @@ enum {
 };
 
 /* Arithmetic of the correlation c = A^T r (step 1).  The selection always
- * re-scores the low-precision candidates in float32 (see topc). */
+ * re-scores the low-precision candidates in float32. */
 typedef enum {
     CS_CORR_FP32 = 0,   /* float32 SIMT correlation, exact float32 argmax */
-    CS_CORR_BF16 = 1    /* bf16 tensor-core correlation (tcgen05, fp32 accumulate),
-                           top-c candidates per atom tile, fp32 re-score */
+    CS_CORR_BF16 = 1    /* bf16 tensor-core correlation (tcgen05, fp32 accumulate), two
+                           best atoms per 16-atom group, fp32 re-score of the 8 best and of
+                           every atom the rounding bound cannot rule out (n <= 4096,
+                           m <= 256) */
 } cs_corr_prec;
 
 /* How the CLOMP coefficient fit evaluates its gradient -A_S^T (y - A_S s_S). */
@@ -82,8 +84,7 @@ typedef struct {
     double tol;         /* stop once ||r||_2 <= tol (epsilon of Eq. 2); 0 disables it */
     int32_t max_iter;   /* R: at most this many iterations; <= 0 means k */
     int32_t prec;       /* cs_corr_prec */
-    int32_t topc;       /* candidates kept per signal and atom tile in bf16 mode
-                           (1..8, default 8 when 0); ignored in fp32 mode */
+    int32_t topc;       /* reserved, must be 0..8 */
 } cs_omp_params;
 
 typedef struct {
@@ -196,8 +197,8 @@ cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int3
                        int32_t ldc, void* stream);
 
 /* Synchronise `stream` and copy the plan's device counters to out[0..3]:
- * out[0] = signals whose bf16 candidate certificate failed and were
- * re-scored over all atoms in float32; out[1] = device error flags (non-zero
+ * out[0] = picks where the bf16 candidates did not certify the winner and
+ * further atoms (the "suspects") were re-scored in float32; out[1] = device error flags (non-zero
  * when a bounded wait inside a kernel gave up).  reset != 0 zeroes them.
  * Returns CS_ETIMEOUT when out[1] != 0. */
 cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* stream);

@@ -64,6 +64,7 @@ struct cs_plan {
     uint32_t* mask = nullptr;
     float* cand_val = nullptr;
     int* cand_idx = nullptr;
+    float* cand_bound = nullptr;
     float* gcol = nullptr;
     float* dnorm = nullptr;
     float* bt = nullptr;
@@ -76,6 +77,7 @@ struct cs_plan {
     float* av = nullptr;
     int* tau = nullptr;
     float* colnorm_max = nullptr;
+    float* GA = nullptr;       // n_max x n_max when n_max <= kGramAMax
     unsigned* counters = nullptr;
     float* tab = nullptr;      // Adam bias-correction table, grown on demand
     int tab_cap = 0;
@@ -102,6 +104,75 @@ struct Carver {
         return o;
     }
 };
+
+// Device workspace layout of a solve, shared by plans and the allocation-free
+// entry point.  clomp: CLOMP state (G, bvec, Adam moments); gram_a: the
+// n x n Gram matrix of A.
+struct WsLayout {
+    size_t A32, A16, Y32, R32, R16, mask, cval, cidx, cbound, gcol, dnorm, bt, L, z, x64, G, bvec, am,
+        av, tau, colnorm, counters, GA, total;
+};
+
+WsLayout ws_layout(int m, int n, int B, int K, bool clomp, bool gram_a) {
+    const size_t Bm = (size_t)B, Kk = (size_t)K;
+    const size_t mp = round_up(m, 4), mh = round_up(m, 64), nw = ceil_div(n, 32);
+    const size_t slots = cand_slots(n), tiles = ceil_div(n, kCorrTcTileN);
+    Carver cv;
+    WsLayout L{};
+    L.A32 = cv.take<float>((size_t)n * mp);
+    L.A16 = cv.take<__nv_bfloat16>((size_t)n * mh);
+    L.Y32 = cv.take<float>(Bm * mp);
+    L.R32 = cv.take<float>(Bm * mp);
+    L.R16 = cv.take<__nv_bfloat16>(Bm * mh);
+    L.mask = cv.take<uint32_t>(Bm * nw);
+    L.cval = cv.take<float>(Bm * slots);
+    L.cidx = cv.take<int>(Bm * slots);
+    L.cbound = cv.take<float>(Bm * tiles * (kCorrTcTileN / kTcGroup));
+    L.gcol = cv.take<float>(Kk * Bm);
+    L.dnorm = cv.take<float>(Bm);
+    L.bt = cv.take<float>(Bm);
+    L.L = cv.take<double>(Kk * Kk * Bm);
+    L.z = cv.take<double>(Kk * Bm);
+    L.x64 = cv.take<double>(Kk * Bm);
+    if (clomp) {
+        L.G = cv.take<float>(Bm * Kk * Kk);
+        L.bvec = cv.take<float>(Bm * Kk);
+        L.am = cv.take<float>(Bm * Kk);
+        L.av = cv.take<float>(Bm * Kk);
+    }
+    L.tau = cv.take<int>(Bm);
+    L.colnorm = cv.take<float>(1);
+    L.counters = cv.take<unsigned>(16);
+    if (gram_a) L.GA = cv.take<float>((size_t)n * n);
+    L.total = cv.off;
+    return L;
+}
+
+void bind_workspace(cs_plan* P, char* w, const WsLayout& L) {
+    P->A32 = reinterpret_cast<float*>(w + L.A32);
+    P->A16 = reinterpret_cast<__nv_bfloat16*>(w + L.A16);
+    P->Y32 = reinterpret_cast<float*>(w + L.Y32);
+    P->R32 = reinterpret_cast<float*>(w + L.R32);
+    P->R16 = reinterpret_cast<__nv_bfloat16*>(w + L.R16);
+    P->mask = reinterpret_cast<uint32_t*>(w + L.mask);
+    P->cand_val = reinterpret_cast<float*>(w + L.cval);
+    P->cand_idx = reinterpret_cast<int*>(w + L.cidx);
+    P->cand_bound = reinterpret_cast<float*>(w + L.cbound);
+    P->gcol = reinterpret_cast<float*>(w + L.gcol);
+    P->dnorm = reinterpret_cast<float*>(w + L.dnorm);
+    P->bt = reinterpret_cast<float*>(w + L.bt);
+    P->L = reinterpret_cast<double*>(w + L.L);
+    P->z = reinterpret_cast<double*>(w + L.z);
+    P->x64 = reinterpret_cast<double*>(w + L.x64);
+    P->G = L.G ? reinterpret_cast<float*>(w + L.G) : nullptr;
+    P->bvec = L.bvec ? reinterpret_cast<float*>(w + L.bvec) : nullptr;
+    P->am = L.am ? reinterpret_cast<float*>(w + L.am) : nullptr;
+    P->av = L.av ? reinterpret_cast<float*>(w + L.av) : nullptr;
+    P->tau = reinterpret_cast<int*>(w + L.tau);
+    P->colnorm_max = reinterpret_cast<float*>(w + L.colnorm);
+    P->counters = reinterpret_cast<unsigned*>(w + L.counters);
+    P->GA = L.GA ? reinterpret_cast<float*>(w + L.GA) : nullptr;
+}
 
 cs_status ensure_tab(cs_plan* P, int len) {
     if (len <= P->tab_cap) return CS_OK;
@@ -162,7 +233,7 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
         a.topc = 1;
     } else {
         a.nch = ceil_div(n, kCorrTcTileN);
-        a.topc = op->topc > 0 ? op->topc : kTopcMax;
+        a.topc = kTcCandPerTile;
     }
     a.tol = op->tol;
     a.A32 = P->A32;
@@ -173,6 +244,7 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
     a.mask = P->mask;
     a.cand_val = P->cand_val;
     a.cand_idx = P->cand_idx;
+    a.cand_bound = P->cand_bound;
     a.gcol = P->gcol;
     a.dnorm = P->dnorm;
     a.bt = P->bt;
@@ -185,6 +257,7 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
     a.av = P->av;
     a.tau = P->tau;
     a.colnorm_max = P->colnorm_max;
+    a.GA = (P->GA && n <= kGramAMax) ? P->GA : nullptr;
     a.counters = P->counters;
     a.support = support;
     a.coef = coef;
@@ -271,8 +344,11 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                       return launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
                                            P->colnorm_max, s);
                   }), "prep A");
+    if (a.GA && (a.need_gcol || a.need_gram))
+        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, s); }), "gram of A");
     CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] { return launch_setup(a, Y, ldy, cp ? 1 : 0, s); }), "setup");
     for (int it = 0; it < a.iters; ++it) {
+        c.tau0 = c.reset ? 0 : it * c.steps;
         if (bf16) CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, s, [&] { return launch_corr_tc(a, s); }), "correlation (tcgen05)");
         else CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, s, [&] { return launch_corr_fp32(a, s); }), "correlation (fp32)");
         CS_TRY_LAUNCH(timed(P, CS_PHASE_SELECT, s, [&] { return launch_select(a, s); }), "select");
@@ -369,59 +445,17 @@ cs_status cs_plan_create(cs_plan** plan, int32_t m_max, int32_t n_max, int32_t b
     P->mh_max = round_up(m_max, 64);
     P->nw_max = ceil_div(n_max, 32);
     P->nch_max = ceil_div(n_max, kCorrFp32TileN);
-    const size_t Bm = (size_t)batch_max, K = (size_t)P->k_max;
-    Carver cv;
-    const size_t oA32 = cv.take<float>((size_t)n_max * P->mp_max);
-    const size_t oA16 = cv.take<__nv_bfloat16>((size_t)n_max * P->mh_max);
-    const size_t oY32 = cv.take<float>(Bm * P->mp_max);
-    const size_t oR32 = cv.take<float>(Bm * P->mp_max);
-    const size_t oR16 = cv.take<__nv_bfloat16>(Bm * P->mh_max);
-    const size_t oMask = cv.take<uint32_t>(Bm * P->nw_max);
-    const size_t oCv = cv.take<float>(Bm * P->nch_max * kTopcMax);
-    const size_t oCi = cv.take<int>(Bm * P->nch_max * kTopcMax);
-    const size_t oGc = cv.take<float>(K * Bm);
-    const size_t oDn = cv.take<float>(Bm);
-    const size_t oBt = cv.take<float>(Bm);
-    const size_t oL = cv.take<double>(K * K * Bm);
-    const size_t oZ = cv.take<double>(K * Bm);
-    const size_t oX = cv.take<double>(K * Bm);
-    const size_t oG = cv.take<float>(Bm * K * K);
-    const size_t oBv = cv.take<float>(Bm * K);
-    const size_t oAm = cv.take<float>(Bm * K);
-    const size_t oAv = cv.take<float>(Bm * K);
-    const size_t oTau = cv.take<int>(Bm);
-    const size_t oCn = cv.take<float>(1);
-    const size_t oCnt = cv.take<unsigned>(16);
-    e = cudaMalloc(&P->ws, cv.off);
+    const bool gram_a = n_max <= kGramAMax;
+    const WsLayout L = ws_layout(m_max, n_max, batch_max, P->k_max, true, gram_a);
+    e = cudaMalloc(&P->ws, L.total);
     if (e != cudaSuccess) {
         delete P;
-        return fail(CS_ENOMEM, "cudaMalloc(%zu bytes): %s", cv.off, cudaGetErrorString(e));
+        return fail(CS_ENOMEM, "cudaMalloc(%zu bytes): %s", L.total, cudaGetErrorString(e));
     }
-    P->ws_bytes = cv.off;
-    char* w = P->ws;
-    P->A32 = reinterpret_cast<float*>(w + oA32);
-    P->A16 = reinterpret_cast<__nv_bfloat16*>(w + oA16);
-    P->Y32 = reinterpret_cast<float*>(w + oY32);
-    P->R32 = reinterpret_cast<float*>(w + oR32);
-    P->R16 = reinterpret_cast<__nv_bfloat16*>(w + oR16);
-    P->mask = reinterpret_cast<uint32_t*>(w + oMask);
-    P->cand_val = reinterpret_cast<float*>(w + oCv);
-    P->cand_idx = reinterpret_cast<int*>(w + oCi);
-    P->gcol = reinterpret_cast<float*>(w + oGc);
-    P->dnorm = reinterpret_cast<float*>(w + oDn);
-    P->bt = reinterpret_cast<float*>(w + oBt);
-    P->L = reinterpret_cast<double*>(w + oL);
-    P->z = reinterpret_cast<double*>(w + oZ);
-    P->x64 = reinterpret_cast<double*>(w + oX);
-    P->G = reinterpret_cast<float*>(w + oG);
-    P->bvec = reinterpret_cast<float*>(w + oBv);
-    P->am = reinterpret_cast<float*>(w + oAm);
-    P->av = reinterpret_cast<float*>(w + oAv);
-    P->tau = reinterpret_cast<int*>(w + oTau);
-    P->colnorm_max = reinterpret_cast<float*>(w + oCn);
-    P->counters = reinterpret_cast<unsigned*>(w + oCnt);
+    P->ws_bytes = L.total;
+    bind_workspace(P, P->ws, L);
     // zero everything once so that padding rows of the bf16 operands are 0
-    e = cudaMemset(P->ws, 0, cv.off);
+    e = cudaMemset(P->ws, 0, L.total);
     if (e != cudaSuccess) {
         cudaFree(P->ws);
         delete P;
@@ -676,30 +710,12 @@ extern "C" cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_
     P.mh_max = round_up(m, 64);
     P.nw_max = ceil_div(n, 32);
     P.nch_max = ceil_div(n, kCorrFp32TileN);
-    const size_t Bm = (size_t)P.B_max, K = (size_t)P.k_max;
-    Carver cv;
-    const size_t oA32 = cv.take<float>((size_t)n * P.mp_max);
-    const size_t oA16 = cv.take<__nv_bfloat16>((size_t)n * P.mh_max);
-    const size_t oY32 = cv.take<float>(Bm * P.mp_max);
-    const size_t oR32 = cv.take<float>(Bm * P.mp_max);
-    const size_t oR16 = cv.take<__nv_bfloat16>(Bm * P.mh_max);
-    const size_t oMask = cv.take<uint32_t>(Bm * P.nw_max);
-    const size_t oCv = cv.take<float>(Bm * P.nch_max * kTopcMax);
-    const size_t oCi = cv.take<int>(Bm * P.nch_max * kTopcMax);
-    const size_t oGc = cv.take<float>(K * Bm);
-    const size_t oDn = cv.take<float>(Bm);
-    const size_t oBt = cv.take<float>(Bm);
-    const size_t oL = cv.take<double>(K * K * Bm);
-    const size_t oZ = cv.take<double>(K * Bm);
-    const size_t oX = cv.take<double>(K * Bm);
-    const size_t oTau = cv.take<int>(Bm);
-    const size_t oCn = cv.take<float>(1);
-    const size_t oCnt = cv.take<unsigned>(16);
-    if (cv.off > kNoAllocScratchBytes)
+    const WsLayout L = ws_layout(m, n, P.B_max, P.k_max, false, false);
+    if (L.total > kNoAllocScratchBytes)
         return fail(CS_EINVAL,
                     "problem needs %zu bytes of scratch; omp_solve_batched_noalloc holds %zu "
                     "(use omp_solve_batched with a plan)",
-                    cv.off, kNoAllocScratchBytes);
+                    L.total, kNoAllocScratchBytes);
     if (batch == 0) return CS_OK;
 
     int dev = 0;
@@ -718,23 +734,7 @@ extern "C" cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_
         base = static_cast<char*>(g_noalloc_base[dev]);
     }
     P.device = dev;
-    P.A32 = reinterpret_cast<float*>(base + oA32);
-    P.A16 = reinterpret_cast<__nv_bfloat16*>(base + oA16);
-    P.Y32 = reinterpret_cast<float*>(base + oY32);
-    P.R32 = reinterpret_cast<float*>(base + oR32);
-    P.R16 = reinterpret_cast<__nv_bfloat16*>(base + oR16);
-    P.mask = reinterpret_cast<uint32_t*>(base + oMask);
-    P.cand_val = reinterpret_cast<float*>(base + oCv);
-    P.cand_idx = reinterpret_cast<int*>(base + oCi);
-    P.gcol = reinterpret_cast<float*>(base + oGc);
-    P.dnorm = reinterpret_cast<float*>(base + oDn);
-    P.bt = reinterpret_cast<float*>(base + oBt);
-    P.L = reinterpret_cast<double*>(base + oL);
-    P.z = reinterpret_cast<double*>(base + oZ);
-    P.x64 = reinterpret_cast<double*>(base + oX);
-    P.tau = reinterpret_cast<int*>(base + oTau);
-    P.colnorm_max = reinterpret_cast<float*>(base + oCn);
-    P.counters = reinterpret_cast<unsigned*>(base + oCnt);
+    bind_workspace(&P, base, L);
     // The previous call's counters must not leak into this one.
     e = cudaMemsetAsync(P.counters, 0, 16 * sizeof(unsigned), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");

@@ -14,7 +14,18 @@ constexpr int kKmaxLimit = 64;     // largest support size the per-signal kernel
 constexpr int kMaxRowChunks = 8;   // m <= 8 * 128 = 1024 for the warp-per-signal kernels
 constexpr int kCorrFp32TileN = 128;   // atoms per CTA of the fp32 correlation
 constexpr int kCorrTcTileN = 256;     // atoms per CTA of the tensor-core correlation
-constexpr int kTopcMax = 8;
+constexpr int kTopcMax = 8;          // candidates re-scored in float32 per signal (bf16 mode)
+constexpr int kTcGroup = 16;         // bf16 mode keeps the two largest |c| of every 16-atom group
+constexpr int kTcCandPerTile = 2 * kCorrTcTileN / kTcGroup;   // 32 candidates per 256-atom tile
+constexpr int kGramAMax = 4096;      // n up to which A^T A is precomputed per solve
+constexpr int kCorrTcMaxN = 4096;    // candidate merge holds <= 512 per signal
+
+// Candidate slots per signal, enough for either correlation kernel.
+__host__ __device__ inline int cand_slots(int n) {
+    const int a = (n + kCorrFp32TileN - 1) / kCorrFp32TileN;
+    const int b = ((n + kCorrTcTileN - 1) / kCorrTcTileN) * kTcCandPerTile;
+    return a > b ? a : b;
+}
 
 __host__ __device__ inline int round_up(int x, int a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline int ceil_div(int x, int a) { return (x + a - 1) / a; }
@@ -26,7 +37,11 @@ __host__ __device__ inline int ceil_div(int x, int a) { return (x + a - 1) / a; 
 //   Y32   [B][mp]  float, measurements, zero-padded
 //   R32   [B][mp]  float residual;  R16 [B][mh] bf16 residual (tensor-core operand)
 //   mask  [B][nw]  selected-atom bitset
-//   cand  [B][nch][topc]  candidate |c| and atom index per atom tile
+//   cand  [B][nch][topc]  candidate |c| and atom index per atom tile (fp32: best of
+//                   each 128-atom tile; bf16: two best of each 16-atom group, unsorted)
+//   cbound [B][n/16]     bf16: third largest |c| of each 16-atom group (bounds the
+//                   group's atoms that are not candidates)
+//   GA    [n][n]   Gram matrix of A (n <= kGramAMax), row j = a_j^T A
 //   gcol  [K][B]   Gram column A_S^T a_j of the new atom (float)
 //   L     [K][K][B] Cholesky factor (double), z, x64 [K][B] (double)
 //   G     [B][K][K] Gram matrix of the support (float, CLOMP Gram form), bvec [B][K]
@@ -43,6 +58,7 @@ struct IterArgs {
     uint32_t* mask;
     float* cand_val;
     int* cand_idx;
+    float* cand_bound;
     float* gcol;
     float* dnorm;
     float* bt;
@@ -54,6 +70,7 @@ struct IterArgs {
     float* am;
     float* av;
     int* tau;
+    const float* GA;            // n x n Gram matrix A^T A (nullptr: gather the columns instead)
     const float* colnorm_max;   // max_j ||a_j||_2 (for the bf16 certificate)
     unsigned* counters;         // [0] bf16 certificate fallbacks, [1] device error flags
     int* support;
@@ -67,6 +84,7 @@ struct IterArgs {
 
 struct ClArgs {
     int steps;
+    int tau0;            // Adam step counter before this fit (the same for every live signal)
     float beta1, beta2, eps;
     int reset;
     const float* tab;    // [2][tab_len]: lr/(1-b1^tau), 1/sqrt(1-b2^tau) for tau = 1..tab_len
@@ -85,6 +103,7 @@ cudaError_t launch_corr_fp32_dense(const float* R32, const float* A32, int mp, i
 cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n,
                                  float* C, int ldc, unsigned* errflag, cudaStream_t s);
+cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s);
 cudaError_t launch_prep_R(const float* R, int ldr, int m, int B, int mp, int mh, float* R32,
                           __nv_bfloat16* R16, cudaStream_t s);
 bool corr_tc_supported(int m, int n);

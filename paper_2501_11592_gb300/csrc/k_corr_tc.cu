@@ -12,9 +12,11 @@
 //     start while later chunks are still in flight;
 //   * one thread issues 4 x tcgen05.mma (M=128, N=256, K=16) per chunk into a
 //     256-column fp32 accumulator in tensor memory;
-//   * the 4 warps then read their 32 TMEM lanes (= 32 signals) with
-//     tcgen05.ld, mask already-selected atoms, take |c| and keep a sorted
-//     top-c list per signal -- C itself never reaches global memory.
+//   * 8 warps (two per TMEM lane quadrant, one per column half) read their
+//     32 lanes (= 32 signals) with tcgen05.ld, mask already-selected atoms,
+//     take |c|, and keep for every 16-atom group its two best atoms and the
+//     third value (a bound on the rest of the group) -- C itself never
+//     reaches global memory.
 // Every wait is bounded; on time-out the kernel raises a device error flag,
 // skips the epilogue, frees its tensor memory and returns.
 #include <cuda.h>
@@ -139,12 +141,16 @@ struct TcArgs {
     const int* status;
     float* cand_val;
     int* cand_idx;
+    float* cand_bound;
     float* dense;       // optional dense output C^T (B x n, row stride ldd); nullptr = top-c only
     int ldd;
     unsigned* errflag;
 };
 
-__global__ void __launch_bounds__(128, 1)
+constexpr int NTHREADS = 256;          // 8 warps: two per TMEM lane quadrant
+constexpr int HALF = TN / 2;           // columns per epilogue warp
+
+__global__ void __launch_bounds__(NTHREADS, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapA, TcArgs p) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[MAX_KC];
@@ -155,6 +161,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
+    const int quad = warp & 3;           // TMEM lanes 32*quad .. 32*quad+31
+    const int half = warp >> 2;          // columns half*HALF .. +HALF-1
     const int b0 = blockIdx.x * TM;
     const int j0 = blockIdx.y * TN;
 
@@ -162,7 +170,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
     // barrier or tensor memory is set up).
     if (tid == 0) { any_live = 0; failed = 0; }
     __syncthreads();
-    {
+    if (tid < TM) {
         const int b = b0 + tid;
         if (p.dense != nullptr || (b < p.B && p.status[b] < 0)) any_live = 1;
     }
@@ -220,58 +228,73 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
         umma_commit(&done_bar);   // arrives once every issued MMA has completed
     }
 
-    // Epilogue: all 4 warps; warp w reads TMEM lanes 32w..32w+31 (= signals).
-    const bool ok = mbar_wait(&done_bar, 0);
+    const bool waited = mbar_wait(&done_bar, 0);
     tc_fence_after();
-    if (!ok) {
-        if (lane == 0) atomicOr(p.errflag, 2u);
-    }
-    __syncwarp();
-    const int sig = b0 + warp * 32 + lane;
-    if (ok && !failed) {
-        float tv[kTopcMax];
-        int ti[kTopcMax];
-#pragma unroll
-        for (int e = 0; e < kTopcMax; ++e) { tv[e] = -1.f; ti[e] = -1; }
-        const bool live = sig < p.B;
-        for (int c0 = 0; c0 < TN; c0 += 32) {
+    if (!waited && lane == 0) atomicOr(p.errflag, 2u);
+    // block-uniform verdict (also the barrier after which the operand tiles,
+    // no longer read by any MMA, are reused as epilogue scratch)
+    const bool ok = __syncthreads_and(waited && !failed) != 0;
+    const int sig = b0 + quad * 32 + lane;
+    const bool live = sig < p.B;
+    const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * HALF);
+    const int a0 = j0 + half * HALF;     // first atom of this warp's half
+
+    if (ok && p.dense) {
+        for (int c0 = 0; c0 < HALF; c0 += 32) {
             uint32_t v[32];
-            tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)c0, v);
+            tmem_ld32(tbase + (uint32_t)c0, v);
             tmem_ld_wait();
             if (!live) continue;
-            if (p.dense) {
-                for (int q = 0; q < 32; ++q) {
-                    const int atom = j0 + c0 + q;
-                    if (atom < p.n) p.dense[(size_t)sig * p.ldd + atom] = __uint_as_float(v[q]);
-                }
-                continue;
-            }
-            const int wbase = j0 + c0;   // 32-aligned: one mask word covers the chunk
-            const uint32_t mw = (wbase < p.n) ? p.mask[(size_t)sig * p.nw + (wbase >> 5)] : 0xffffffffu;
-#pragma unroll
             for (int q = 0; q < 32; ++q) {
-                const int atom = wbase + q;
-                if (atom < p.n && !((mw >> q) & 1u)) {
-                    const float a = fabsf(__uint_as_float(v[q]));
-                    if (cand_better(a, atom, tv[kTopcMax - 1], ti[kTopcMax - 1])) {
-                        tv[kTopcMax - 1] = a;
-                        ti[kTopcMax - 1] = atom;
-#pragma unroll
-                        for (int e = kTopcMax - 1; e > 0; --e) {
-                            if (cand_better(tv[e], ti[e], tv[e - 1], ti[e - 1])) {
-                                const float fv = tv[e]; tv[e] = tv[e - 1]; tv[e - 1] = fv;
-                                const int fi = ti[e]; ti[e] = ti[e - 1]; ti[e - 1] = fi;
-                            }
-                        }
-                    }
-                }
+                const int atom = a0 + c0 + q;
+                if (atom < p.n) p.dense[(size_t)sig * p.ldd + atom] = __uint_as_float(v[q]);
             }
         }
-        if (live && !p.dense) {
-            const size_t o = ((size_t)sig * p.nch + blockIdx.y) * p.topc;
+    } else if (ok) {
+        // Per 16-atom group: the two largest masked |c| (lower atom first on
+        // ties) become candidates, the third largest bounds every other atom
+        // of the group.  Branch-free, ~11 instructions per value.
+        auto mask_word = [&](int c) -> uint32_t {   // atoms past n count as selected
+            const int wb = a0 + 32 * c;
+            if (!live || wb >= p.n) return 0xffffffffu;
+            uint32_t w = p.mask[(size_t)sig * p.nw + (wb >> 5)];
+            if (p.n - wb < 32) w |= ~0u << (p.n - wb);
+            return w;
+        };
+        constexpr int PER_HALF = 2 * HALF / kTcGroup;          // 16 candidates per half
+        const size_t o = ((size_t)sig * p.nch + blockIdx.y) * kTcCandPerTile + half * PER_HALF;
+        const size_t ob = ((size_t)sig * p.nch + blockIdx.y) * (kCorrTcTileN / kTcGroup) +
+                          half * (HALF / kTcGroup);
+#pragma unroll 1
+        for (int c = 0; c < HALF / 32; ++c) {
+            const uint32_t mw = mask_word(c);
+            uint32_t v[32];
+            tmem_ld32(tbase + (uint32_t)(32 * c), v);
+            tmem_ld_wait();
 #pragma unroll
-            for (int e = 0; e < kTopcMax; ++e)
-                if (e < p.topc) { p.cand_val[o + e] = tv[e]; p.cand_idx[o + e] = ti[e]; }
+            for (int g = 0; g < 32 / kTcGroup; ++g) {
+                float m1 = -1.f, m2 = -1.f, m3 = -1.f;
+                int i1 = 0, i2 = 0;
+#pragma unroll
+                for (int q = 0; q < kTcGroup; ++q) {
+                    const int qq = kTcGroup * g + q;
+                    const float x = ((mw >> qq) & 1u) ? -1.f : fabsf(__uint_as_float(v[qq]));
+                    const bool gt1 = x > m1, gt2 = x > m2;
+                    m3 = gt2 ? m2 : fmaxf(m3, x);
+                    m2 = gt1 ? m1 : (gt2 ? x : m2);
+                    i2 = gt1 ? i1 : (gt2 ? qq : i2);
+                    m1 = gt1 ? x : m1;
+                    i1 = gt1 ? qq : i1;
+                }
+                if (live) {
+                    const int e = 4 * c + 2 * g;
+                    p.cand_val[o + e] = m1;
+                    p.cand_idx[o + e] = (m1 >= 0.f) ? a0 + 32 * c + i1 : -1;
+                    p.cand_val[o + e + 1] = m2;
+                    p.cand_idx[o + e + 1] = (m2 >= 0.f) ? a0 + 32 * c + i2 : -1;
+                    p.cand_bound[ob + 2 * c + g] = m3;
+                }
+            }
         }
     }
     tc_fence_before();
@@ -332,13 +355,15 @@ cudaError_t launch_tc(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh
         configured = 1;
     }
     dim3 grid(ceil_div(B, TM), ceil_div(n, TN));
-    k_corr_tc<<<grid, 128, smem, s>>>(mR, mA, p);
+    k_corr_tc<<<grid, NTHREADS, smem, s>>>(mR, mA, p);
     return cudaGetLastError();
 }
 
 }  // namespace
 
-bool corr_tc_supported(int m, int n) { return m >= 1 && m <= MAX_KC * KCH && n >= 1 && get_encode() != nullptr; }
+bool corr_tc_supported(int m, int n) {
+    return m >= 1 && m <= MAX_KC * KCH && n >= 1 && n <= kCorrTcMaxN && get_encode() != nullptr;
+}
 
 cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s) {
     TcArgs p{};
@@ -352,6 +377,7 @@ cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s) {
     p.status = a.status;
     p.cand_val = a.cand_val;
     p.cand_idx = a.cand_idx;
+    p.cand_bound = a.cand_bound;
     p.dense = nullptr;
     p.errflag = a.counters + 1;
     return launch_tc(a.R16, a.A16, a.mh, a.B, a.n, p, s);

@@ -1,0 +1,226 @@
+// Set-up kernels of a solve: padded float32 / bf16 copies of A and the
+// residuals, the Gram matrix of A, the initial per-signal state (r = y,
+// s = 0, empty support, status "running") and the Adam bias-correction table.
+#include <mutex>
+#include <unordered_map>
+
+#include "k_common.cuh"
+
+namespace cs {
+namespace {
+
+// ---------------------------------------------------------------- set-up --
+
+// Copy A (caller layout, lda) into the padded float32 layout and, when A16 is
+// given, its bf16 copy; record max_j ||a_j||_2.  One warp per column.
+__global__ void k_prep_A(const float* __restrict__ A, int lda, int m, int n, int mp, int mh,
+                         float* __restrict__ A32, __nv_bfloat16* __restrict__ A16,
+                         float* colnorm_max) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const float* a = A + (size_t)j * lda;
+    float ss = 0.f;
+    for (int i = lane; i < mp; i += 32) {
+        const float v = (i < m) ? a[i] : 0.f;
+        A32[(size_t)j * mp + i] = v;
+        ss = fmaf(v, v, ss);
+    }
+    if (A16) {
+        for (int i = lane; i < mh; i += 32)
+            A16[(size_t)j * mh + i] = __float2bfloat16_rn(i < m ? a[i] : 0.f);
+    }
+    ss = warp_sum(ss);
+    if (lane == 0 && colnorm_max) {
+        // non-negative floats order like their bit patterns
+        atomicMax(reinterpret_cast<unsigned int*>(colnorm_max), __float_as_uint(sqrtf(ss)));
+    }
+}
+
+// Gram matrix of the dictionary, GA = A^T A (n x n, row j = a_j^T A), from
+// the padded float32 copy.  Each thread owns a 4 x 4 block of outputs; the
+// K = m sum is accumulated in 16-term partial sums that are then added, so
+// the rounding error grows with 16 + m/16 rather than with m.
+__global__ void __launch_bounds__(256) k_gram_A(const float* __restrict__ A32, int mp, int n,
+                                                float* __restrict__ GA) {
+    constexpr int T = 64, BK = 16;
+    __shared__ __align__(16) float Ai[BK][T + 4];
+    __shared__ __align__(16) float Aj[BK][T + 4];
+    const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+    const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
+    float acc[4][4] = {};
+    for (int k0 = 0; k0 < mp; k0 += BK) {
+        // 64 columns x 16 rows per operand = 256 float4 loads each
+        {
+            const int row = tid >> 2, kq = (tid & 3) * 4;
+            const int kk = k0 + kq;
+            float4 vi = make_float4(0.f, 0.f, 0.f, 0.f), vj = vi;
+            if (i0 + row < n && kk < mp) vi = *reinterpret_cast<const float4*>(A32 + (size_t)(i0 + row) * mp + kk);
+            if (j0 + row < n && kk < mp) vj = *reinterpret_cast<const float4*>(A32 + (size_t)(j0 + row) * mp + kk);
+            Ai[kq + 0][row] = vi.x; Ai[kq + 1][row] = vi.y; Ai[kq + 2][row] = vi.z; Ai[kq + 3][row] = vi.w;
+            Aj[kq + 0][row] = vj.x; Aj[kq + 1][row] = vj.y; Aj[kq + 2][row] = vj.z; Aj[kq + 3][row] = vj.w;
+        }
+        __syncthreads();
+        float part[4][4] = {};
+#pragma unroll
+        for (int k = 0; k < BK; ++k) {
+            const float4 a = *reinterpret_cast<const float4*>(&Ai[k][ty * 4]);
+            const float4 c = *reinterpret_cast<const float4*>(&Aj[k][tx * 4]);
+            const float av[4] = {a.x, a.y, a.z, a.w}, cv[4] = {c.x, c.y, c.z, c.w};
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) part[u][w] = fmaf(av[u], cv[w], part[u][w]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int w = 0; w < 4; ++w) acc[u][w] += part[u][w];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int i = i0 + ty * 4 + u;
+        if (i >= n) continue;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) {
+            const int j = j0 + tx * 4 + w;
+            if (j < n) GA[(size_t)i * n + j] = acc[u][w];
+        }
+    }
+}
+
+// Copy caller residuals (m x B, leading dimension ldr) into the padded
+// float32 and/or bf16 row layouts used by the correlation kernels.
+__global__ void k_prep_R(const float* __restrict__ R, int ldr, int m, int B, int mp, int mh,
+                         float* __restrict__ R32, __nv_bfloat16* __restrict__ R16) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= B) return;
+    const float* r = R + (size_t)b * ldr;
+    if (R32)
+        for (int i = lane; i < mp; i += 32) R32[(size_t)b * mp + i] = (i < m) ? r[i] : 0.f;
+    if (R16)
+        for (int i = lane; i < mh; i += 32) R16[(size_t)b * mh + i] = __float2bfloat16_rn(i < m ? r[i] : 0.f);
+}
+
+// Per-signal initial state: r = y, s = 0, empty support, status "running".
+__global__ void k_setup(IterArgs a, const float* __restrict__ Y, int ldy, int clomp) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= a.B) return;
+    const float* y = Y + (size_t)b * ldy;
+    float ss = 0.f;
+    int finite = 1;
+    for (int i = lane; i < a.mp; i += 32) {
+        const float v = (i < a.m) ? y[i] : 0.f;
+        finite &= isfinite(v) ? 1 : 0;
+        a.Y32[(size_t)b * a.mp + i] = v;
+        a.R32[(size_t)b * a.mp + i] = v;
+        ss = fmaf(v, v, ss);
+    }
+    if (a.R16)
+        for (int i = lane; i < a.mh; i += 32)
+            a.R16[(size_t)b * a.mh + i] = __float2bfloat16_rn(i < a.m ? y[i] : 0.f);
+    for (int w = lane; w < a.nw; w += 32) a.mask[(size_t)b * a.nw + w] = 0u;
+    for (int q = lane; q < a.k; q += 32) {
+        a.support[(size_t)b * a.k + q] = -1;
+        a.coef[(size_t)b * a.k + q] = 0.f;
+    }
+    if (clomp) {
+        for (int q = lane; q < a.kmax; q += 32) {
+            a.am[(size_t)b * a.kmax + q] = 0.f;
+            a.av[(size_t)b * a.kmax + q] = 0.f;
+        }
+    }
+    ss = warp_sum(ss);
+    finite = __all_sync(FULL, finite);
+    if (lane == 0) {
+        const float rho = sqrtf(ss);
+        a.n_iter[b] = 0;
+        a.tau[b] = 0;
+        if (!finite) {
+            a.status[b] = CS_SIG_NONFINITE;
+            a.res_norm[b] = __int_as_float(0x7fffffff);
+        } else {
+            a.res_norm[b] = rho;
+            a.status[b] = ((double)rho <= a.tol) ? CS_SIG_REACHED_TOL : -1;
+        }
+    }
+}
+
+// Adam bias-correction factors for tau = 1..len, evaluated in float64 from
+// the float32 hyper-parameters and rounded once:
+//   tab[tau-1]       = lr / (1 - beta1^tau)
+//   tab[len + tau-1] = 1 / sqrt(1 - beta2^tau)
+__global__ void k_adam_table(float* tab, int len, float lr, float beta1, float beta2) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= len) return;
+    const double tau = (double)(i + 1);
+    tab[i] = (float)((double)lr / (1.0 - pow((double)beta1, tau)));
+    tab[len + i] = (float)(1.0 / sqrt(1.0 - pow((double)beta2, tau)));
+}
+
+
+}  // namespace
+
+cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh, float* A32,
+                          __nv_bfloat16* A16, float* colnorm_max, cudaStream_t s) {
+    if (colnorm_max) {
+        cudaError_t e = cudaMemsetAsync(colnorm_max, 0, sizeof(float), s);
+        if (e != cudaSuccess) return e;
+    }
+    k_prep_A<<<ceil_div(n, 8), 256, 0, s>>>(A, lda, m, n, mp, mh, A32, A16, colnorm_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s) {
+    dim3 grid(ceil_div(n, 64), ceil_div(n, 64));
+    k_gram_A<<<grid, 256, 0, s>>>(A32, mp, n, GA);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_R(const float* R, int ldr, int m, int B, int mp, int mh, float* R32,
+                          __nv_bfloat16* R16, cudaStream_t s) {
+    k_prep_R<<<ceil_div(B, 8), 256, 0, s>>>(R, ldr, m, B, mp, mh, R32, R16);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_setup(const IterArgs& a, const float* Y, int ldy, int clomp, cudaStream_t s) {
+    k_setup<<<ceil_div(a.B, 8), 256, 0, s>>>(a, Y, ldy, clomp);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adam_table(float* tab, int len, float lr, float beta1, float beta2,
+                              cudaStream_t s) {
+    if (len <= 0) return cudaSuccess;
+    k_adam_table<<<ceil_div(len, 256), 256, 0, s>>>(tab, len, lr, beta1, beta2);
+    return cudaGetLastError();
+}
+
+
+int resident_grid(const void* kernel, int block, int needed) {
+    static std::mutex mu;
+    static std::unordered_map<long long, int> cache;   // (device, kernel) -> CTAs per SM
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return needed;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return needed;
+    const long long key = ((long long)dev << 48) ^ (long long)(uintptr_t)kernel;
+    int per_sm = 0;
+    {
+        std::lock_guard<std::mutex> lk(mu);
+        auto it = cache.find(key);
+        if (it != cache.end()) {
+            per_sm = it->second;
+        } else {
+            if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, block, 0) != cudaSuccess)
+                per_sm = 1;
+            per_sm = per_sm > 0 ? per_sm : 1;
+            cache[key] = per_sm;
+        }
+    }
+    const long long g = (long long)per_sm * sms;
+    return (int)(g < needed ? g : needed);
+}
+
+}  // namespace cs
