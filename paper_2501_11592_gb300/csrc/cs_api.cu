@@ -6,6 +6,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -90,6 +91,17 @@ struct cs_plan {
     struct Mark { int phase; cudaEvent_t a, b; };
     std::vector<Mark> marks;
     std::vector<cudaEvent_t> pool;
+    // CUDA graphs of whole solves, keyed by every argument the launches bake
+    // in: the first call of a configuration runs eagerly, the second is
+    // captured on a private stream, later ones replay the graph.
+    struct GraphEntry {
+        cudaGraphExec_t exec = nullptr;
+        int seen = 0;
+        int64_t launches[CS_PHASES] = {};
+    };
+    int use_graphs = 1;
+    cudaStream_t cap_stream = nullptr;
+    std::map<std::string, GraphEntry> graphs;
 };
 
 namespace {
@@ -336,29 +348,99 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         c.reset = cp->reset_adam_each_iter ? 1 : 0;
         c.tab = P->tab;
         c.tab_len = len;
-        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] { return launch_adam_table(P->tab, len, cp->lr, cp->beta1, cp->beta2, s); }),
-                      "adam table");
     }
 
-    CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] {
-                      return launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
-                                           P->colnorm_max, s);
-                  }), "prep A");
-    if (a.GA && (a.need_gcol || a.need_gram))
-        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, s); }), "gram of A");
-    CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] { return launch_setup(a, Y, ldy, cp ? 1 : 0, s); }), "setup");
-    for (int it = 0; it < a.iters; ++it) {
-        c.tau0 = c.reset ? 0 : it * c.steps;
-        if (bf16) CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, s, [&] { return launch_corr_tc(a, s); }), "correlation (tcgen05)");
-        else CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, s, [&] { return launch_corr_fp32(a, s); }), "correlation (fp32)");
-        CS_TRY_LAUNCH(timed(P, CS_PHASE_SELECT, s, [&] { return launch_select(a, s); }), "select");
-        if (!cp) CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, s, [&] { return launch_chol(a, s); }), "cholesky");
-        else if (cp->form == CS_CL_GRAM)
-            CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, s, [&] { return launch_clfit_gram(a, c, it, s); }), "cl fit (gram)");
-        else
-            CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, s, [&] { return launch_clfit_gather(a, c, it, s); }), "cl fit (gather)");
-        CS_TRY_LAUNCH(timed(P, CS_PHASE_RESID, s, [&] { return launch_resid(a, s); }), "residual");
+    // Every launch of the solve, on stream `st`.
+    auto enqueue = [&](cudaStream_t st) -> cs_status {
+        if (cp)
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
+                              return launch_adam_table(P->tab, c.tab_len, cp->lr, cp->beta1, cp->beta2, st);
+                          }), "adam table");
+        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
+                          return launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
+                                               P->colnorm_max, st);
+                      }), "prep A");
+        if (a.GA && (a.need_gcol || a.need_gram))
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, st); }),
+                          "gram of A");
+        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_setup(a, Y, ldy, cp ? 1 : 0, st); }), "setup");
+        for (int it = 0; it < a.iters; ++it) {
+            c.tau0 = c.reset ? 0 : it * c.steps;
+            if (bf16)
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, st, [&] { return launch_corr_tc(a, st); }), "correlation (tcgen05)");
+            else
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, st, [&] { return launch_corr_fp32(a, st); }), "correlation (fp32)");
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_SELECT, st, [&] { return launch_select(a, st); }), "select");
+            if (!cp)
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] { return launch_chol(a, st); }), "cholesky");
+            else if (cp->form == CS_CL_GRAM)
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] { return launch_clfit_gram(a, c, it, st); }), "cl fit (gram)");
+            else
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] { return launch_clfit_gather(a, c, it, st); }),
+                              "cl fit (gather)");
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_RESID, st, [&] { return launch_resid(a, st); }), "residual");
+        }
+        return CS_OK;
+    };
+    if (!P->use_graphs || P->profiling) return enqueue(s);
+
+    // graph cache key: everything the launches bake in
+    std::string key;
+    auto put = [&](const void* v, size_t nb) { key.append(static_cast<const char*>(v), nb); };
+    const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab};
+    put(ptrs, sizeof(ptrs));
+    const int ints[] = {m, n, lda, ldy, B, c.tab_len};
+    put(ints, sizeof(ints));
+    // field by field (struct padding is not part of the key)
+    const double dk[] = {(double)op->k, op->tol, (double)op->max_iter, (double)op->prec,
+                         cp ? (double)cp->steps : -1.0, cp ? (double)cp->lr : 0.0,
+                         cp ? (double)cp->beta1 : 0.0, cp ? (double)cp->beta2 : 0.0,
+                         cp ? (double)cp->eps : 0.0, cp ? (double)cp->reset_adam_each_iter : 0.0,
+                         cp ? (double)cp->form : -1.0};
+    put(dk, sizeof(dk));
+    if (P->graphs.size() > 16 && !P->graphs.count(key)) {
+        for (auto& kv : P->graphs)
+            if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+        P->graphs.clear();
     }
+    cs_plan::GraphEntry& ge = P->graphs[key];
+    if (!ge.exec && ge.seen++ == 0) return enqueue(s);     // first call: eager
+    if (!ge.exec) {
+        // second identical call: capture on the private stream
+        if (!P->cap_stream) {
+            cudaError_t e = cudaStreamCreateWithFlags(&P->cap_stream, cudaStreamNonBlocking);
+            if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+        }
+        int64_t before[CS_PHASES];
+        for (int i = 0; i < CS_PHASES; ++i) before[i] = P->launches[i];
+        cudaError_t e = cudaStreamBeginCapture(P->cap_stream, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaStreamBeginCapture");
+        const cs_status st_cap = enqueue(P->cap_stream);
+        cudaGraph_t g = nullptr;
+        e = cudaStreamEndCapture(P->cap_stream, &g);
+        for (int i = 0; i < CS_PHASES; ++i) {
+            ge.launches[i] = P->launches[i] - before[i];
+            P->launches[i] = before[i];
+        }
+        if (st_cap != CS_OK || e != cudaSuccess || !g) {
+            if (g) cudaGraphDestroy(g);
+            P->graphs.erase(key);
+            P->use_graphs = 0;              // capture unavailable here: stay eager
+            cudaGetLastError();
+            return enqueue(s);
+        }
+        e = cudaGraphInstantiate(&ge.exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            ge.exec = nullptr;
+            P->graphs.erase(key);
+            P->use_graphs = 0;
+            cudaGetLastError();
+            return enqueue(s);
+        }
+    }
+    for (int i = 0; i < CS_PHASES; ++i) P->launches[i] += ge.launches[i];
+    CS_TRY_LAUNCH(cudaGraphLaunch(ge.exec, s), "cudaGraphLaunch");
     return CS_OK;
 }
 
@@ -474,6 +556,9 @@ cs_status cs_plan_destroy(cs_plan* plan) {
         cudaEventDestroy(mk.b);
     }
     for (auto e : plan->pool) cudaEventDestroy(e);
+    for (auto& kv : plan->graphs)
+        if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
+    if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
     if (plan->ws) cudaFree(plan->ws);
     if (plan->tab) cudaFree(plan->tab);
     if (plan->io) cudaFree(plan->io);
@@ -734,6 +819,7 @@ extern "C" cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_
         base = static_cast<char*>(g_noalloc_base[dev]);
     }
     P.device = dev;
+    P.use_graphs = 0;
     bind_workspace(&P, base, L);
     // The previous call's counters must not leak into this one.
     e = cudaMemsetAsync(P.counters, 0, 16 * sizeof(unsigned), (cudaStream_t)stream);

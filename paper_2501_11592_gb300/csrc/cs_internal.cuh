@@ -140,13 +140,16 @@ __device__ __forceinline__ bool cand_better(float v, int j, float bv, int bj) {
     return v > bv || (v == bv && j < bj);
 }
 
+// Warp-wide (max |c|, lowest atom on ties) with two redux.sync instructions.
+// Valid entries have j >= 0 and v >= 0 (non-negative floats order like their
+// bit patterns); the result is (-1, -1) when no lane holds a valid entry.
 __device__ __forceinline__ void warp_argmax(float& v, int& j) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        float ov = __shfl_xor_sync(0xffffffffu, v, o);
-        int oj = __shfl_xor_sync(0xffffffffu, j, o);
-        if (cand_better(ov, oj, v, j)) { v = ov; j = oj; }
-    }
+    const unsigned key = (j >= 0) ? __float_as_uint(v) : 0u;
+    const unsigned mx = __reduce_max_sync(0xffffffffu, key);
+    const int cand = (j >= 0 && key == mx) ? j : 0x7fffffff;
+    const int jmin = __reduce_min_sync(0xffffffffu, cand);
+    j = (jmin == 0x7fffffff) ? -1 : jmin;
+    v = (j >= 0) ? __uint_as_float(mx) : -1.f;
 }
 
 // Transposing reduction: every lane holds v[0..31]; afterwards v[0] of lane l

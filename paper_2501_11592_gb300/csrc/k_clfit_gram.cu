@@ -61,6 +61,10 @@ __global__ void __launch_bounds__(128) k_clfit_gram(IterArgs a, ClArgs c, int it
         }
         const float omb1 = 1.f - c.beta1, omb2 = 1.f - c.beta2;
         float* my_s = &sh_s[w][sub][0];
+        unsigned long long nb[NQ];                // (-b_q, 0): initial partial sums
+#pragma unroll
+        for (int h = 0; h < NQ; ++h) nb[h] = pack2(-bb[h], 0.f);
+#pragma unroll 2
         for (int step = 0; step < c.steps; ++step) {
 #pragma unroll
             for (int h = 0; h < NQ; ++h)
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(128) k_clfit_gram(IterArgs a, ClArgs c, int it
             unsigned long long g2[NQ][2];
 #pragma unroll
             for (int h = 0; h < NQ; ++h) {
-                g2[h][0] = pack2(-bb[h], 0.f);
+                g2[h][0] = nb[h];
                 g2[h][1] = 0ull;
             }
 #pragma unroll
@@ -86,21 +90,19 @@ __global__ void __launch_bounds__(128) k_clfit_gram(IterArgs a, ClArgs c, int it
             __syncwarp();
             const float c1 = staged ? sh_c1[step] : c.tab[c.tau0 + step];
             const float c2 = staged ? sh_c2[step] : c.tab[c.tab_len + c.tau0 + step];
+            // Coordinates beyond the support have zero rows, zero b and zero
+            // state, so the update leaves them at exactly zero: no masking.
 #pragma unroll
             for (int h = 0; h < NQ; ++h) {
                 float g0, g1, g2v, g3;
                 unpack2(g2[h][0], g0, g1);
                 unpack2(g2[h][1], g2v, g3);
                 const float gq = (g0 + g1) + (g2v + g3);
-                const float mn = fmaf(c.beta1, mo[h], omb1 * gq);
-                const float vn = fmaf(c.beta2, ve[h], omb2 * gq * gq);
-                // sqrt(v) as v * rsqrt(v) (0 stays 0), one approximate reciprocal
-                const float rt = vn * rsqrtf(fmaxf(vn, 1e-37f));
-                const float sn = s[h] - c1 * mn * __frcp_rn(fmaf(rt, c2, c.eps));
-                const bool upd = ql + LPS * h < sz;
-                mo[h] = upd ? mn : mo[h];
-                ve[h] = upd ? vn : ve[h];
-                s[h] = upd ? sn : s[h];
+                mo[h] = fmaf(c.beta1, mo[h], omb1 * gq);
+                ve[h] = fmaf(c.beta2, ve[h], omb2 * gq * gq);
+                // sqrt(v) as v * rsqrt(v) (0 stays 0), approximate reciprocal
+                const float rt = ve[h] * rsqrtf(fmaxf(ve[h], 1e-37f));
+                s[h] -= c1 * mo[h] * rcp_approx(fmaf(rt, c2, c.eps));
             }
         }
         if (live) {

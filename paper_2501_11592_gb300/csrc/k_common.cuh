@@ -25,6 +25,13 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
 }
 
 
+// Approximate reciprocal (rcp.approx.ftz, relative error ~2^-23).
+__device__ __forceinline__ float rcp_approx(float x) {
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // ------------------------------------------------------------- selection --
 
 template <int MCH>

@@ -12,7 +12,7 @@
 //     start while later chunks are still in flight;
 //   * one thread issues 4 x tcgen05.mma (M=128, N=256, K=16) per chunk into a
 //     256-column fp32 accumulator in tensor memory;
-//   * 8 warps (two per TMEM lane quadrant, one per column half) read their
+//   * 16 warps (four per TMEM lane quadrant, 64 columns each) read their
 //     32 lanes (= 32 signals) with tcgen05.ld, mask already-selected atoms,
 //     take |c|, and keep for every 16-atom group its two best atoms and the
 //     third value (a bound on the rest of the group) -- C itself never
@@ -147,8 +147,9 @@ struct TcArgs {
     unsigned* errflag;
 };
 
-constexpr int NTHREADS = 256;          // 8 warps: two per TMEM lane quadrant
-constexpr int HALF = TN / 2;           // columns per epilogue warp
+constexpr int NTHREADS = 512;          // 16 warps: four per TMEM lane quadrant
+constexpr int NPART = NTHREADS / 128;  // column parts per quadrant
+constexpr int HALF = TN / NPART;       // columns per epilogue warp (64)
 
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapA, TcArgs p) {
@@ -162,7 +163,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3;           // TMEM lanes 32*quad .. 32*quad+31
-    const int half = warp >> 2;          // columns half*HALF .. +HALF-1
+    const int half = warp >> 2;          // column part: half*HALF .. +HALF-1
     const int b0 = blockIdx.x * TM;
     const int j0 = blockIdx.y * TN;
 
@@ -254,20 +255,26 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
         // Per 16-atom group: the two largest masked |c| (lower atom first on
         // ties) become candidates, the third largest bounds every other atom
         // of the group.  Branch-free, ~11 instructions per value.
-        auto mask_word = [&](int c) -> uint32_t {   // atoms past n count as selected
+        // mask words of this part, fetched before any TMEM read; atoms past n
+        // count as selected
+        uint32_t mws[HALF / 32];
+#pragma unroll
+        for (int c = 0; c < HALF / 32; ++c) {
             const int wb = a0 + 32 * c;
-            if (!live || wb >= p.n) return 0xffffffffu;
-            uint32_t w = p.mask[(size_t)sig * p.nw + (wb >> 5)];
-            if (p.n - wb < 32) w |= ~0u << (p.n - wb);
-            return w;
-        };
-        constexpr int PER_HALF = 2 * HALF / kTcGroup;          // 16 candidates per half
+            uint32_t w = 0xffffffffu;
+            if (live && wb < p.n) {
+                w = p.mask[(size_t)sig * p.nw + (wb >> 5)];
+                if (p.n - wb < 32) w |= ~0u << (p.n - wb);
+            }
+            mws[c] = w;
+        }
+        constexpr int PER_HALF = 2 * HALF / kTcGroup;          // 8 candidates per part
         const size_t o = ((size_t)sig * p.nch + blockIdx.y) * kTcCandPerTile + half * PER_HALF;
         const size_t ob = ((size_t)sig * p.nch + blockIdx.y) * (kCorrTcTileN / kTcGroup) +
                           half * (HALF / kTcGroup);
-#pragma unroll 1
+#pragma unroll
         for (int c = 0; c < HALF / 32; ++c) {
-            const uint32_t mw = mask_word(c);
+            const uint32_t mw = mws[c];
             uint32_t v[32];
             tmem_ld32(tbase + (uint32_t)(32 * c), v);
             tmem_ld_wait();

@@ -63,45 +63,36 @@ __device__ __forceinline__ void resid_one(const IterArgs& a, const int b) {
     load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, r);
     const int* sup = a.support + (size_t)b * a.k;
     const float* x = a.coef + (size_t)b * a.k;
-    // columns in selection order (the oracle's order); four columns' loads are
-    // issued before their FMAs to keep more requests in flight
-    int q = 0;
-    for (; q + 4 <= t; q += 4) {
-        float4 v[4][MCH];
-        float xq[4];
+    // Columns in selection order (the oracle's order).  Lane q loads support
+    // index and coefficient q once; the indices are then broadcast by
+    // shuffles, so up to 8 columns' loads are in flight before their FMAs.
+    for (int q0 = 0; q0 < t; q0 += 32) {
+        const int qn = min(32, t - q0);
+        const int my_j = (lane < qn) ? sup[q0 + lane] : 0;
+        const float my_x = (lane < qn) ? x[q0 + lane] : 0.f;
+        for (int u0 = 0; u0 < qn; u0 += 8) {
+            float4 v[8][MCH];
+            float xq[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const float4* col = reinterpret_cast<const float4*>(a.A32 + (size_t)sup[q + u] * a.mp);
-            xq[u] = x[q + u];
+            for (int u = 0; u < 8; ++u) {
+                const int j = __shfl_sync(0xffffffffu, my_j, u0 + u);
+                xq[u] = __shfl_sync(0xffffffffu, my_x, u0 + u);
+                const float4* col = reinterpret_cast<const float4*>(a.A32 + (size_t)j * a.mp);
 #pragma unroll
-            for (int c = 0; c < MCH; ++c) {
-                const int i4 = c * 32 + lane;
-                v[u][c] = (i4 * 4 < a.mp) ? col[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int c = 0; c < MCH; ++c) {
+                    const int i4 = c * 32 + lane;
+                    v[u][c] = (u0 + u < qn && i4 * 4 < a.mp) ? col[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
-        }
 #pragma unroll
-        for (int u = 0; u < 4; ++u)
+            for (int u = 0; u < 8; ++u)
 #pragma unroll
-            for (int c = 0; c < MCH; ++c) {
-                r[c].x = fmaf(-v[u][c].x, xq[u], r[c].x);
-                r[c].y = fmaf(-v[u][c].y, xq[u], r[c].y);
-                r[c].z = fmaf(-v[u][c].z, xq[u], r[c].z);
-                r[c].w = fmaf(-v[u][c].w, xq[u], r[c].w);
-            }
-    }
-    for (; q < t; ++q) {
-        const float xq = x[q];
-        const float4* col = reinterpret_cast<const float4*>(a.A32 + (size_t)sup[q] * a.mp);
-#pragma unroll
-        for (int c = 0; c < MCH; ++c) {
-            const int i4 = c * 32 + lane;
-            if (i4 * 4 < a.mp) {
-                const float4 v = col[i4];
-                r[c].x = fmaf(-v.x, xq, r[c].x);
-                r[c].y = fmaf(-v.y, xq, r[c].y);
-                r[c].z = fmaf(-v.z, xq, r[c].z);
-                r[c].w = fmaf(-v.w, xq, r[c].w);
-            }
+                for (int c = 0; c < MCH; ++c) {
+                    r[c].x = fmaf(-v[u][c].x, xq[u], r[c].x);
+                    r[c].y = fmaf(-v[u][c].y, xq[u], r[c].y);
+                    r[c].z = fmaf(-v[u][c].z, xq[u], r[c].z);
+                    r[c].w = fmaf(-v[u][c].w, xq[u], r[c].w);
+                }
         }
     }
     float ss = 0.f;

@@ -174,3 +174,34 @@ def test_clomp_reset_adam_option(cs_gpu, torch):
     g = run_gpu(cs_gpu, torch, A32, Y32, 6, "clomp", reset_adam=True, steps=30, lr=2e-2)
     o = run_oracle(A64, Y64, 6, "clomp", reset_adam=True, steps=30, lr=2e-2)
     compare(g, o)
+
+
+@pytest.mark.parametrize("algo", ["omp", "clomp"])
+def test_graph_replay_matches_eager(cs_gpu, torch, algo):
+    """Repeated solves on one plan run eagerly, then as a captured CUDA graph;
+    replays read the buffers' current contents and match eager runs bit for bit."""
+    rng = np.random.default_rng(61)
+    A = workloads.gaussian_matrix(rng, 64, 200)
+    X1 = workloads.sparse_coefficients(rng, 200, 300, 10, values="pm")
+    X2 = workloads.sparse_coefficients(rng, 200, 300, 10, values="pm")
+    A32, Y1, _, _ = f32_problem(A, A @ X1)
+    _, Y2, _, _ = f32_problem(A, A @ X2)
+    At = _dev(torch, A32)
+    Y = _dev(torch, Y1)
+    plan = cs_gpu.Plan(64, 200, 300, 10)
+    out = cs_gpu._outputs(300, 10, At.device)
+    solve = (lambda: cs_gpu.omp_solve_batched(At, Y, 10, prec="bf16", plan=plan, out=out)) if algo == "omp" \
+        else (lambda: cs_gpu.clomp_solve_batched(At, Y, 10, prec="bf16", plan=plan, out=out, **CL))
+    got = []
+    for Yh in (Y1, Y2, Y1, Y2):          # eager, capture + replay, replay, replay
+        Y.copy_(torch.from_numpy(Yh))
+        solve()
+        torch.cuda.synchronize()
+        got.append({q: v.clone() for q, v in vars(out).items()})
+    for q in ("support", "coef", "n_iter", "res_norm", "status"):
+        assert torch.equal(got[0][q], got[2][q]), q
+        assert torch.equal(got[1][q], got[3][q]), q
+    # the captured run equals an eager run on a fresh plan
+    fresh = run_gpu(cs_gpu, torch, A32, Y2, 10, algo, prec="bf16", **({} if algo == "omp" else CL))
+    assert np.array_equal(fresh["support"], got[1]["support"].cpu().numpy())
+    assert np.array_equal(fresh["coef"], got[1]["coef"].cpu().numpy())
