@@ -291,8 +291,10 @@ def main():
         ksteps = max(3, min(args.steps, 10))
         for name, algo, prec, form in [("omp_fp32", "omp", "fp32", "gram"), ("omp_bf16", "omp", "bf16", "gram"),
                                        ("clomp_fp32_gram", "clomp", "fp32", "gram"),
-                                       ("clomp_bf16_gather", "clomp", "bf16", "gather")]:
+                                       ("clomp_bf16_gather", "clomp", "bf16", "gather"),
+                                       ("clomp_bf16_gram_unfused", "clomp", "bf16", "gram")]:
             fn = make_step(algo, prec, form)
+            plan.set_option(cs.OPT_FUSE_UPDATE, 0 if name.endswith("unfused") else 1)
             m_, _, _ = timed(fn, ksteps, 3)
             plan.set_profiling(True)
             plan.profile(reset=True)
@@ -303,6 +305,7 @@ def main():
             plan.set_profiling(False)
             compare[name] = {"ms_per_step": m_, "signals_per_s": ws * p.B / (m_ / 1e3),
                              "phase_ms_per_step": {k: round(v[1] / 3, 4) for k, v in ph.items()}}
+        plan.set_option(cs.OPT_FUSE_UPDATE, 1)
         compare["clomp_headline"] = {"ms_per_step": ms, "signals_per_s": value}
         compare["clomp_over_omp_fp32"] = value / compare["omp_fp32"]["signals_per_s"]
 
@@ -377,9 +380,12 @@ def main():
     sum_t = iters * (iters + 1) / 2.0
     sum_t2 = iters * (iters + 1) * (2 * iters + 1) / 6.0
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    fit_flops = B * CL["steps"] * (2 * sum_t2 + 10 * sum_t)
     work = {
         # Gram form: g = G s - b per Adam step (2 t^2 flops) + Adam update (~10 t flops)
-        "fit": ("alu", B * CL["steps"] * (2 * sum_t2 + 10 * sum_t), fp32_peak, "TFLOP/s"),
+        "fit": ("alu", fit_flops, fp32_peak, "TFLOP/s"),
+        # fused selection + fit + residual: its arithmetic is the fit's
+        "update": ("alu", fit_flops, fp32_peak, "TFLOP/s"),
         # residual: read t columns of A (4m bytes each), y, write r (fp32 + bf16)
         "residual": ("hbm", B * (4.0 * p.m * sum_t + iters * p.m * (4 + 4 + 2)), peaks["hbm_gbs"], "GB/s"),
         # select: read topc*nch candidate pairs and re-score 8 columns + the new column and y

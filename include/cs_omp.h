@@ -228,12 +228,23 @@ enum {
     CS_PHASE_SELECT = 2,   /* candidate merge, float32 re-score, support update, Gram column */
     CS_PHASE_FIT = 3,      /* Cholesky update (OMP) or Adam coefficient fit (CLOMP) */
     CS_PHASE_RESID = 4,    /* residual, norm and stopping test */
-    CS_PHASES = 5
+    CS_PHASE_UPDATE = 5,   /* CLOMP Gram form: selection + fit + residual in one kernel */
+    CS_PHASES = 6
 };
 
 /* enable != 0: bracket every later kernel launch of solves on this plan with
  * CUDA events on the solve's stream (adds a little GPU time per launch). */
 cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable);
+
+/* Plan options (all on by default):
+ *   CS_OPT_GRAPHS: replay repeated identical solves as a captured CUDA graph
+ *     (the first call of a configuration runs eagerly, the second is
+ *     captured on a private stream, later ones replay it on `stream`);
+ *   CS_OPT_FUSE_UPDATE: CLOMP in Gram form runs selection, Adam fit and
+ *     residual of an iteration as one kernel (m <= 256).
+ * Results are identical either way. */
+enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1 };
+cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value);
 
 /* Kernel launches per phase since the last reset (always counted), and --
  * when profiling was enabled -- the summed event time per phase in

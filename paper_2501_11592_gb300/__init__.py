@@ -31,7 +31,8 @@ CS_OK, CS_EINVAL, CS_ENOMEM, CS_ECUDA, CS_ETIMEOUT, CS_ENOTSUP = 0, -1, -2, -3, 
 SIG_REACHED_K, SIG_REACHED_TOL, SIG_MAX_ITER, SIG_DEPENDENT, SIG_NONFINITE = 0, 1, 2, 3, 4
 PREC = {"fp32": 0, "bf16": 1}
 FORM = {"gather": 0, "gram": 1}
-PHASES = ("setup", "correlation", "select", "fit", "residual")
+PHASES = ("setup", "correlation", "select", "fit", "residual", "update")
+OPT_GRAPHS, OPT_FUSE_UPDATE = 0, 1
 _STATUS_NAMES = {CS_EINVAL: "CS_EINVAL", CS_ENOMEM: "CS_ENOMEM", CS_ECUDA: "CS_ECUDA",
                  CS_ETIMEOUT: "CS_ETIMEOUT", CS_ENOTSUP: "CS_ENOTSUP"}
 
@@ -90,7 +91,8 @@ def load():
         L.cs_plan_counters.argtypes = [vp, vp, i32, vp]
         L.cs_plan_set_profiling.argtypes = [vp, i32]
         L.cs_plan_profile.argtypes = [vp, vp, vp, i32]
-        for fn in ("cs_correlate", "cs_plan_counters", "cs_plan_set_profiling", "cs_plan_profile",
+        L.cs_plan_set_option.argtypes = [vp, i32, i32]
+        for fn in ("cs_plan_set_option", "cs_correlate", "cs_plan_counters", "cs_plan_set_profiling", "cs_plan_profile",
                    "cs_plan_create", "cs_plan_destroy", "omp_solve_batched", "omp_solve_batched_host",
                    "clomp_solve_batched", "clomp_solve_batched_host", "omp_solve", "clomp_solve",
                    "clfit_forward", "clfit_adjoint", "clfit_adam_step"):
@@ -155,6 +157,9 @@ class Plan:
         if rc not in (CS_OK, CS_ETIMEOUT):
             _check(rc)
         return int(out[0]), int(out[1])
+
+    def set_option(self, option, value):
+        _check(load().cs_plan_set_option(self.h, int(option), int(value)))
 
     def set_profiling(self, enable=True):
         _check(load().cs_plan_set_profiling(self.h, int(bool(enable))))

@@ -100,6 +100,7 @@ struct cs_plan {
         int64_t launches[CS_PHASES] = {};
     };
     int use_graphs = 1;
+    int fuse_update = 1;       // CLOMP Gram form: one fused kernel per iteration
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -350,6 +351,9 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         c.tab_len = len;
     }
 
+    // CLOMP in Gram form runs selection, fit and residual as one kernel
+    const bool fused = cp && cp->form == CS_CL_GRAM && P->fuse_update && update_clomp_fused_supported(a);
+
     // Every launch of the solve, on stream `st`.
     auto enqueue = [&](cudaStream_t st) -> cs_status {
         if (cp)
@@ -370,6 +374,11 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, st, [&] { return launch_corr_tc(a, st); }), "correlation (tcgen05)");
             else
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, st, [&] { return launch_corr_fp32(a, st); }), "correlation (fp32)");
+            if (fused) {
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_UPDATE, st, [&] { return launch_update_clomp(a, c, it, st); }),
+                              "fused update");
+                continue;
+            }
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SELECT, st, [&] { return launch_select(a, st); }), "select");
             if (!cp)
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] { return launch_chol(a, st); }), "cholesky");
@@ -389,7 +398,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
     auto put = [&](const void* v, size_t nb) { key.append(static_cast<const char*>(v), nb); };
     const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab};
     put(ptrs, sizeof(ptrs));
-    const int ints[] = {m, n, lda, ldy, B, c.tab_len};
+    const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0};
     put(ints, sizeof(ints));
     // field by field (struct padding is not part of the key)
     const double dk[] = {(double)op->k, op->tol, (double)op->max_iter, (double)op->prec,
@@ -705,6 +714,15 @@ cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable) {
     if (!plan) return fail(CS_EINVAL, "plan is NULL");
     plan->profiling = enable ? 1 : 0;
     return CS_OK;
+}
+
+cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value) {
+    if (!plan) return fail(CS_EINVAL, "plan is NULL");
+    switch (option) {
+        case CS_OPT_GRAPHS: plan->use_graphs = value ? 1 : 0; return CS_OK;
+        case CS_OPT_FUSE_UPDATE: plan->fuse_update = value ? 1 : 0; return CS_OK;
+        default: return fail(CS_EINVAL, "unknown option %d", option);
+    }
 }
 
 cs_status cs_plan_profile(cs_plan* plan, double* ms, int64_t* launches, int32_t reset) {

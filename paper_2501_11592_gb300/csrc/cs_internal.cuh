@@ -112,6 +112,8 @@ cudaError_t launch_chol(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_resid(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_clfit_gram(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
+bool update_clomp_fused_supported(const IterArgs& a);
+cudaError_t launch_update_clomp(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 
 cudaError_t launch_clfit_forward(const float* A, int m, int lda, const int32_t* S, const float* Sv,
                                  int t, int lds, const float* Y, int ldy, int batch, float* R,

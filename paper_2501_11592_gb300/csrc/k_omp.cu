@@ -3,7 +3,7 @@
 // Eq. 2 shared by OMP and CLOMP.  The Cholesky runs one thread per signal so
 // that every float64 lane does useful work on a part whose float64 rate is
 // low; the residual runs one warp per signal (coalesced column gathers).
-#include "k_common.cuh"
+#include "k_resid.cuh"
 
 namespace cs {
 namespace {
@@ -50,83 +50,6 @@ __global__ void __launch_bounds__(32) k_chol(IterArgs a) {
     }
     a.n_iter[b] = t + 1;
 #undef LAT
-}
-
-
-// ------------------------------------------------ residual + stop test -----
-template <int MCH>
-__device__ __forceinline__ void resid_one(const IterArgs& a, const int b) {
-    const int lane = threadIdx.x & 31;
-    if (a.status[b] >= 0) return;
-    const int t = a.n_iter[b];
-    float4 r[MCH];
-    load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, r);
-    const int* sup = a.support + (size_t)b * a.k;
-    const float* x = a.coef + (size_t)b * a.k;
-    // Columns in selection order (the oracle's order).  Lane q loads support
-    // index and coefficient q once; the indices are then broadcast by
-    // shuffles, so up to 8 columns' loads are in flight before their FMAs.
-    for (int q0 = 0; q0 < t; q0 += 32) {
-        const int qn = min(32, t - q0);
-        const int my_j = (lane < qn) ? sup[q0 + lane] : 0;
-        const float my_x = (lane < qn) ? x[q0 + lane] : 0.f;
-        for (int u0 = 0; u0 < qn; u0 += 8) {
-            float4 v[8][MCH];
-            float xq[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int j = __shfl_sync(0xffffffffu, my_j, u0 + u);
-                xq[u] = __shfl_sync(0xffffffffu, my_x, u0 + u);
-                const float4* col = reinterpret_cast<const float4*>(a.A32 + (size_t)j * a.mp);
-#pragma unroll
-                for (int c = 0; c < MCH; ++c) {
-                    const int i4 = c * 32 + lane;
-                    v[u][c] = (u0 + u < qn && i4 * 4 < a.mp) ? col[i4] : make_float4(0.f, 0.f, 0.f, 0.f);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u)
-#pragma unroll
-                for (int c = 0; c < MCH; ++c) {
-                    r[c].x = fmaf(-v[u][c].x, xq[u], r[c].x);
-                    r[c].y = fmaf(-v[u][c].y, xq[u], r[c].y);
-                    r[c].z = fmaf(-v[u][c].z, xq[u], r[c].z);
-                    r[c].w = fmaf(-v[u][c].w, xq[u], r[c].w);
-                }
-        }
-    }
-    float ss = 0.f;
-    float4* R = reinterpret_cast<float4*>(a.R32 + (size_t)b * a.mp);
-#pragma unroll
-    for (int c = 0; c < MCH; ++c) {
-        const int i4 = c * 32 + lane;
-        if (i4 * 4 < a.mp) {
-            R[i4] = r[c];
-            ss += dot4(r[c], r[c]);
-        }
-    }
-    if (a.R16) {
-        // bf16 copy for the tensor-core correlation (row stride mh >= mp rounded to 8)
-        __nv_bfloat16* R16 = a.R16 + (size_t)b * a.mh;
-#pragma unroll
-        for (int c = 0; c < MCH; ++c) {
-            const int i = (c * 32 + lane) * 4;
-            if (i < a.mp) {
-                __nv_bfloat162 lo = __floats2bfloat162_rn(r[c].x, r[c].y);
-                __nv_bfloat162 hi = __floats2bfloat162_rn(r[c].z, r[c].w);
-                *reinterpret_cast<__nv_bfloat162*>(R16 + i) = lo;
-                *reinterpret_cast<__nv_bfloat162*>(R16 + i + 2) = hi;
-            }
-        }
-    }
-    ss = warp_sum(ss);
-    if (lane == 0) {
-        const float rho = sqrtf(ss);
-        a.res_norm[b] = rho;
-        if ((double)rho <= a.tol) a.status[b] = CS_SIG_REACHED_TOL;
-        else if (t >= a.k) a.status[b] = CS_SIG_REACHED_K;
-        else if (t >= a.iters) a.status[b] = CS_SIG_MAX_ITER;
-    }
 }
 
 

@@ -205,3 +205,22 @@ def test_graph_replay_matches_eager(cs_gpu, torch, algo):
     fresh = run_gpu(cs_gpu, torch, A32, Y2, 10, algo, prec="bf16", **({} if algo == "omp" else CL))
     assert np.array_equal(fresh["support"], got[1]["support"].cpu().numpy())
     assert np.array_equal(fresh["coef"], got[1]["coef"].cpu().numpy())
+
+
+def test_fused_update_matches_separate_kernels(cs_gpu, torch):
+    """The fused CLOMP update (selection + fit + residual in one kernel) runs
+    the same per-signal arithmetic as the three separate kernels."""
+    p = workloads.random_problem(77, 301, 333, 20, seed=71, snr_db=30.0, values="pm")
+    A32, Y32, _, _ = f32_problem(p.A, p.Y)
+    A = _dev(torch, A32)
+    Y = _dev(torch, Y32)
+    res = []
+    for fuse in (1, 0):
+        plan = cs_gpu.Plan(77, 301, 333, 20)
+        plan.set_option(cs_gpu.OPT_FUSE_UPDATE, fuse)
+        r = cs_gpu.clomp_solve_batched(A, Y, 20, prec="bf16", plan=plan, **CL)
+        plan.profile(reset=False)
+        torch.cuda.synchronize()
+        res.append(to_numpy(r))
+    for q in ("support", "coef", "n_iter", "res_norm", "status"):
+        assert np.array_equal(res[0][q], res[1][q]), q
