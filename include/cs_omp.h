@@ -160,6 +160,35 @@ cs_status clomp_solve_batched_host(cs_plan* plan, const float* A, int32_t m, int
                                    float* res_norm, int32_t* sig_status,
                                    const cs_clomp_params* params, void* stream);
 
+/* One instance of an uneven batch (thousands of signals of different n, m
+ * and k, e.g. image columns, blocks and 1-D sequences of several sizes):
+ * its own dictionary, measurement vector, sparsity and outputs.  Every
+ * pointer is a DEVICE pointer owned by the caller; A is m x n column-major
+ * with leading dimension lda; support and coef hold k entries. */
+typedef struct {
+    const float* A;
+    int32_t m, n, lda;
+    const float* y;
+    int32_t k;
+    int32_t* support;
+    float* coef;
+    int32_t* n_iter;
+    float* res_norm;
+    int32_t* sig_status;
+} cs_instance;
+
+/* Uneven batches: instances is a HOST array of `count` descriptors.  The
+ * call groups the instances that share (A, m, n, lda, k), gathers each
+ * group's measurements into a batch, runs the batched solver on it and
+ * scatters the outputs back, all on `stream`.  params->k is ignored (each
+ * instance has its own).  Every instance must fit the plan (m <= m_max,
+ * n <= n_max, k <= k_max); groups larger than batch_max run in chunks.
+ * Device staging for the gather/scatter is allocated on first use. */
+cs_status omp_solve_varlen(cs_plan* plan, const cs_instance* instances, int32_t count,
+                           const cs_omp_params* params, void* stream);
+cs_status clomp_solve_varlen(cs_plan* plan, const cs_instance* instances, int32_t count,
+                             const cs_clomp_params* params, void* stream);
+
 /* CL fit, forward half (Methods, s forward branch: y' = A (s .* Mask)):
  *   R[:,b] = Y[:,b] - sum_q A[:, S[b*lds+q]] * Sv[b*lds+q]   (q < t)
  *   loss[b] = 1/2 ||R[:,b]||^2

@@ -21,7 +21,8 @@ __all__ = [
     "load", "Plan", "omp_solve", "omp_solve_batched", "clomp_solve", "clomp_solve_batched",
     "omp_solve_batched_host", "clomp_solve_batched_host", "clfit_forward", "clfit_adjoint",
     "clfit_adam_step", "CSError", "SIG_REACHED_K", "SIG_REACHED_TOL", "SIG_MAX_ITER",
-    "SIG_DEPENDENT", "SIG_NONFINITE", "library_path", "correlate", "PHASES",
+    "SIG_DEPENDENT", "SIG_NONFINITE", "library_path", "correlate", "PHASES", "omp_solve_varlen",
+    "clomp_solve_varlen",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -46,6 +47,13 @@ class CSError(RuntimeError):
 class OmpParams(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("prec", ctypes.c_int32), ("topc", ctypes.c_int32)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("A", ctypes.c_void_p), ("m", ctypes.c_int32), ("n", ctypes.c_int32),
+                ("lda", ctypes.c_int32), ("y", ctypes.c_void_p), ("k", ctypes.c_int32),
+                ("support", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("n_iter", ctypes.c_void_p),
+                ("res_norm", ctypes.c_void_p), ("sig_status", ctypes.c_void_p)]
 
 
 class ClompParams(ctypes.Structure):
@@ -92,7 +100,9 @@ def load():
         L.cs_plan_set_profiling.argtypes = [vp, i32]
         L.cs_plan_profile.argtypes = [vp, vp, vp, i32]
         L.cs_plan_set_option.argtypes = [vp, i32, i32]
-        for fn in ("cs_plan_set_option", "cs_correlate", "cs_plan_counters", "cs_plan_set_profiling", "cs_plan_profile",
+        L.omp_solve_varlen.argtypes = [vp, ctypes.POINTER(Instance), i32, ctypes.POINTER(OmpParams), vp]
+        L.clomp_solve_varlen.argtypes = [vp, ctypes.POINTER(Instance), i32, ctypes.POINTER(ClompParams), vp]
+        for fn in ("omp_solve_varlen", "clomp_solve_varlen", "cs_plan_set_option", "cs_correlate", "cs_plan_counters", "cs_plan_set_profiling", "cs_plan_profile",
                    "cs_plan_create", "cs_plan_destroy", "omp_solve_batched", "omp_solve_batched_host",
                    "clomp_solve_batched", "clomp_solve_batched_host", "omp_solve", "clomp_solve",
                    "clfit_forward", "clfit_adjoint", "clfit_adam_step"):
@@ -302,6 +312,43 @@ def clomp_solve_batched_host(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=
     return _host_batched(load().clomp_solve_batched_host, A, Y, k,
                          _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
                                        reset_adam, form), plan, stream, out)
+
+
+def _varlen(fn, instances, params, plan, stream):
+    """instances: list of (A (m, n) column-major tensor, y (m,) tensor, k).
+    Returns a list of Result (one signal each)."""
+    torch = _torch()
+    if plan is None:
+        m_max = max(int(A.shape[0]) for A, _, _ in instances)
+        n_max = max(int(A.shape[1]) for A, _, _ in instances)
+        k_max = max(int(k) for _, _, k in instances)
+        plan = _plan_for(m_max, n_max, 1024, k_max, None)
+    keep, outs = [], []
+    arr = (Instance * len(instances))()
+    for i, (A, y, k) in enumerate(instances):
+        A = _colmajor(A, torch.float32)
+        y = y.to(torch.float32).contiguous()
+        o = _outputs(1, int(k), A.device)
+        keep += [A, y]
+        outs.append(o)
+        arr[i] = Instance(A.data_ptr(), A.shape[0], A.shape[1], _ld(A), y.data_ptr(), int(k),
+                          o.support.data_ptr(), o.coef.data_ptr(), o.n_iter.data_ptr(),
+                          o.res_norm.data_ptr(), o.status.data_ptr())
+    _check(fn(plan.h, arr, len(instances), ctypes.byref(params), _stream_ptr(stream)))
+    return outs
+
+
+def omp_solve_varlen(instances, tol=0.0, max_iter=None, prec="fp32", plan=None, stream=None):
+    """Uneven batch of (A, y, k) instances, plain OMP."""
+    return _varlen(load().omp_solve_varlen, instances, _omp_params(1, tol, max_iter, prec, 0), plan, stream)
+
+
+def clomp_solve_varlen(instances, tol=0.0, max_iter=None, prec="fp32", steps=50, lr=1e-2, beta1=0.9,
+                       beta2=0.999, eps=1e-8, reset_adam=False, form="gram", plan=None, stream=None):
+    """Uneven batch of (A, y, k) instances, CLOMP."""
+    return _varlen(load().clomp_solve_varlen, instances,
+                   _clomp_params(1, tol, max_iter, prec, 0, steps, lr, beta1, beta2, eps, reset_adam, form),
+                   plan, stream)
 
 
 def correlate(A, R, prec="fp32", plan=None, stream=None):

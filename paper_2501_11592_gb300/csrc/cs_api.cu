@@ -84,6 +84,8 @@ struct cs_plan {
     int tab_cap = 0;
     char* io = nullptr;        // device staging for the host-buffer entry points
     size_t io_bytes = 0;
+    char* vl = nullptr;        // device staging for uneven batches
+    size_t vl_bytes = 0;
     // measurement: launch counts per phase (always) and, when profiling is
     // enabled, CUDA event pairs around every launch
     int64_t launches[CS_PHASES] = {};
@@ -509,6 +511,109 @@ cs_status solve_host(cs_plan* P, const float* A, int m, int n, int lda, const fl
     return CS_OK;
 }
 
+// Uneven batches: group instances by (A, m, n, lda, k), gather each group's
+// measurements into a batch, solve it with the batched path, scatter back.
+cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_omp_params* op,
+                       const cs_clomp_params* cp, cudaStream_t s) {
+    if (!P) return fail(CS_EINVAL, "plan is NULL");
+    if (!op) return fail(CS_EINVAL, "params is NULL");
+    if (count < 0) return fail(CS_EINVAL, "count=%d", count);
+    if (count == 0) return CS_OK;
+    if (!inst) return fail(CS_EINVAL, "instances is NULL");
+    for (int i = 0; i < count; ++i) {
+        const cs_instance& x = inst[i];
+        if (!x.A || !x.y || !x.support || !x.coef || !x.n_iter || !x.res_norm || !x.sig_status)
+            return fail(CS_EINVAL, "instance %d has a NULL pointer", i);
+        if (x.m < 1 || x.n < 1 || x.lda < x.m || x.k < 1 || x.k > x.m || x.k > x.n)
+            return fail(CS_EINVAL, "instance %d: bad sizes m=%d n=%d lda=%d k=%d", i, x.m, x.n, x.lda, x.k);
+        if (x.m > P->m_max || x.n > P->n_max || x.k > P->k_max)
+            return fail(CS_EINVAL, "instance %d (m=%d n=%d k=%d) exceeds the plan", i, x.m, x.n, x.k);
+    }
+    // groups in order of first appearance
+    std::vector<std::vector<int>> groups;
+    {
+        std::map<std::string, int> at;
+        for (int i = 0; i < count; ++i) {
+            const cs_instance& x = inst[i];
+            std::string key;
+            key.append(reinterpret_cast<const char*>(&x.A), sizeof(x.A));
+            const int dims[] = {x.m, x.n, x.lda, x.k};
+            key.append(reinterpret_cast<const char*>(dims), sizeof(dims));
+            auto it = at.find(key);
+            if (it == at.end()) {
+                at[key] = (int)groups.size();
+                groups.push_back({i});
+            } else {
+                groups[it->second].push_back(i);
+            }
+        }
+    }
+    // staging: batch measurements, batch outputs and the pointer tables
+    const size_t Bm = (size_t)P->B_max, K = (size_t)P->k_max;
+    Carver cv;
+    const size_t oY = cv.take<float>((size_t)P->m_max * Bm);
+    const size_t oS = cv.take<int32_t>(K * Bm);
+    const size_t oC = cv.take<float>(K * Bm);
+    const size_t oN = cv.take<int32_t>(Bm);
+    const size_t oR = cv.take<float>(Bm);
+    const size_t oT = cv.take<int32_t>(Bm);
+    const size_t oYp = cv.take<const float*>(Bm);
+    const size_t oOut = cv.take<VarlenOut>(Bm);
+    if (cv.off > P->vl_bytes) {
+        if (P->vl) {
+            cudaFree(P->vl);
+            P->vl = nullptr;
+            P->vl_bytes = 0;
+        }
+        cudaError_t e = cudaMalloc(&P->vl, cv.off);
+        if (e != cudaSuccess) return fail(CS_ENOMEM, "cudaMalloc(varlen staging): %s", cudaGetErrorString(e));
+        P->vl_bytes = cv.off;
+    }
+    DeviceGuard dg(P->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    float* Yb = reinterpret_cast<float*>(P->vl + oY);
+    int32_t* Sb = reinterpret_cast<int32_t*>(P->vl + oS);
+    float* Cb = reinterpret_cast<float*>(P->vl + oC);
+    int32_t* Nb = reinterpret_cast<int32_t*>(P->vl + oN);
+    float* Rb = reinterpret_cast<float*>(P->vl + oR);
+    int32_t* Tb = reinterpret_cast<int32_t*>(P->vl + oT);
+    const float** Yp = reinterpret_cast<const float**>(P->vl + oYp);
+    VarlenOut* Ot = reinterpret_cast<VarlenOut*>(P->vl + oOut);
+    std::vector<const float*> yp;
+    std::vector<VarlenOut> ot;
+    for (const auto& g : groups) {
+        const cs_instance& x0 = inst[g[0]];
+        cs_omp_params o = *op;
+        o.k = x0.k;
+        cs_clomp_params c;
+        if (cp) {
+            c = *cp;
+            c.base = o;
+        }
+        for (size_t b0 = 0; b0 < g.size(); b0 += Bm) {
+            const int Bg = (int)std::min(Bm, g.size() - b0);
+            yp.assign(Bg, nullptr);
+            ot.assign(Bg, VarlenOut{});
+            for (int j = 0; j < Bg; ++j) {
+                const cs_instance& x = inst[g[b0 + j]];
+                yp[j] = x.y;
+                ot[j] = VarlenOut{x.support, x.coef, x.n_iter, x.res_norm, x.sig_status};
+            }
+            // the host vectors are pageable: the copies are staged before the call returns
+            CS_TRY_LAUNCH(cudaMemcpyAsync(Yp, yp.data(), sizeof(const float*) * Bg, cudaMemcpyHostToDevice, s),
+                          "copy varlen table");
+            CS_TRY_LAUNCH(cudaMemcpyAsync(Ot, ot.data(), sizeof(VarlenOut) * Bg, cudaMemcpyHostToDevice, s),
+                          "copy varlen table");
+            CS_TRY_LAUNCH(launch_varlen_gather(Yp, x0.m, Bg, Yb, s), "varlen gather");
+            cs_status st = solve(P, x0.A, x0.m, x0.n, x0.lda, Yb, x0.m, Bg, Sb, Cb, Nb, Rb, Tb, &o,
+                                 cp ? &c : nullptr, s);
+            if (st != CS_OK) return st;
+            CS_TRY_LAUNCH(launch_varlen_scatter(Ot, x0.k, Bg, Sb, Cb, Nb, Rb, Tb, s), "varlen scatter");
+        }
+    }
+    return CS_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -571,6 +676,7 @@ cs_status cs_plan_destroy(cs_plan* plan) {
     if (plan->ws) cudaFree(plan->ws);
     if (plan->tab) cudaFree(plan->tab);
     if (plan->io) cudaFree(plan->io);
+    if (plan->vl) cudaFree(plan->vl);
     delete plan;
     return CS_OK;
 }
@@ -626,6 +732,17 @@ cs_status clomp_solve_batched_host(cs_plan* plan, const float* A, int32_t m, int
     if (!params) return fail(CS_EINVAL, "params is NULL");
     return solve_host(plan, A, m, n, lda, Y, ldy, batch, support, coef, n_iter, res_norm,
                       sig_status, &params->base, params, (cudaStream_t)stream);
+}
+
+cs_status omp_solve_varlen(cs_plan* plan, const cs_instance* instances, int32_t count,
+                           const cs_omp_params* params, void* stream) {
+    return solve_varlen(plan, instances, count, params, nullptr, (cudaStream_t)stream);
+}
+
+cs_status clomp_solve_varlen(cs_plan* plan, const cs_instance* instances, int32_t count,
+                             const cs_clomp_params* params, void* stream) {
+    if (!params) return fail(CS_EINVAL, "params is NULL");
+    return solve_varlen(plan, instances, count, &params->base, params, (cudaStream_t)stream);
 }
 
 cs_status clfit_forward(const float* A, int32_t m, int32_t n, int32_t lda, const int32_t* S,

@@ -91,7 +91,19 @@ struct ClArgs {
     int tab_len;
 };
 
+// Output pointers of one uneven-batch instance.
+struct VarlenOut {
+    int* support;
+    float* coef;
+    int* n_iter;
+    float* res_norm;
+    int* status;
+};
+
 // ---- launchers (defined in the .cu files) --------------------------------
+cudaError_t launch_varlen_gather(const float* const* ys, int m, int B, float* Y, cudaStream_t s);
+cudaError_t launch_varlen_scatter(const VarlenOut* outs, int k, int B, const int* support, const float* coef,
+                                  const int* n_iter, const float* res_norm, const int* status, cudaStream_t s);
 cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh, float* A32,
                           __nv_bfloat16* A16, float* colnorm_max, cudaStream_t s);
 cudaError_t launch_setup(const IterArgs& a, const float* Y, int ldy, int clomp, cudaStream_t s);

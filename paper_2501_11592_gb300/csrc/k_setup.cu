@@ -104,6 +104,36 @@ __global__ void k_prep_R(const float* __restrict__ R, int ldr, int m, int B, int
         for (int i = lane; i < mh; i += 32) R16[(size_t)b * mh + i] = __float2bfloat16_rn(i < m ? r[i] : 0.f);
 }
 
+// Uneven batches: gather instance measurements into a batch (column b of Y
+// from the pointer ys[b]) and scatter the batch outputs back to the
+// instances' own arrays.  One warp per instance.
+__global__ void k_varlen_gather(const float* const* __restrict__ ys, int m, int B, float* __restrict__ Y) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= B) return;
+    const float* y = ys[b];
+    for (int i = lane; i < m; i += 32) Y[(size_t)b * m + i] = y[i];
+}
+
+__global__ void k_varlen_scatter(const VarlenOut* __restrict__ outs, int k, int B,
+                                 const int* __restrict__ support, const float* __restrict__ coef,
+                                 const int* __restrict__ n_iter, const float* __restrict__ res_norm,
+                                 const int* __restrict__ status) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= B) return;
+    const VarlenOut o = outs[b];
+    for (int q = lane; q < k; q += 32) {
+        o.support[q] = support[(size_t)b * k + q];
+        o.coef[q] = coef[(size_t)b * k + q];
+    }
+    if (lane == 0) {
+        *o.n_iter = n_iter[b];
+        *o.res_norm = res_norm[b];
+        *o.status = status[b];
+    }
+}
+
 // Per-signal initial state: r = y, s = 0, empty support, status "running".
 __global__ void k_setup(IterArgs a, const float* __restrict__ Y, int ldy, int clomp) {
     const int lane = threadIdx.x & 31;
@@ -177,6 +207,17 @@ cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh,
 cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s) {
     dim3 grid(ceil_div(n, 64), ceil_div(n, 64));
     k_gram_A<<<grid, 256, 0, s>>>(A32, mp, n, GA);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_varlen_gather(const float* const* ys, int m, int B, float* Y, cudaStream_t s) {
+    k_varlen_gather<<<ceil_div(B, 8), 256, 0, s>>>(ys, m, B, Y);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_varlen_scatter(const VarlenOut* outs, int k, int B, const int* support, const float* coef,
+                                  const int* n_iter, const float* res_norm, const int* status, cudaStream_t s) {
+    k_varlen_scatter<<<ceil_div(B, 8), 256, 0, s>>>(outs, k, B, support, coef, n_iter, res_norm, status);
     return cudaGetLastError();
 }
 
