@@ -17,6 +17,7 @@ __global__ void __launch_bounds__(256) k_clfit_gather(IterArgs a, ClArgs c, int 
     __shared__ __align__(16) float sh_s[KMAX];
     __shared__ float red[8][KMAX];
     __shared__ int sh_j[KMAX];
+    pdl_wait();
     const int b = blockIdx.x;
     if (a.status[b] >= 0) return;
     const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
@@ -120,13 +121,13 @@ cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cu
     const int nth = a.m <= 256 ? round_up(a.m, 32) : 256;
     const int rpt = ceil_div(a.m, nth);
     if (a.kmax <= 32) {
-        if (rpt == 1) k_clfit_gather<32, 1><<<a.B, nth, 0, s>>>(a, c, iter);
-        else if (rpt == 2) k_clfit_gather<32, 2><<<a.B, nth, 0, s>>>(a, c, iter);
-        else k_clfit_gather<32, 4><<<a.B, nth, 0, s>>>(a, c, iter);
+        if (rpt == 1) launch_pdl(k_clfit_gather<32, 1>, dim3(a.B), dim3(nth), 0, s, a, c, iter);
+        else if (rpt == 2) launch_pdl(k_clfit_gather<32, 2>, dim3(a.B), dim3(nth), 0, s, a, c, iter);
+        else launch_pdl(k_clfit_gather<32, 4>, dim3(a.B), dim3(nth), 0, s, a, c, iter);
     } else {
-        if (rpt == 1) k_clfit_gather<64, 1><<<a.B, nth, 0, s>>>(a, c, iter);
-        else if (rpt == 2) k_clfit_gather<64, 2><<<a.B, nth, 0, s>>>(a, c, iter);
-        else k_clfit_gather<64, 4><<<a.B, nth, 0, s>>>(a, c, iter);
+        if (rpt == 1) launch_pdl(k_clfit_gather<64, 1>, dim3(a.B), dim3(nth), 0, s, a, c, iter);
+        else if (rpt == 2) launch_pdl(k_clfit_gather<64, 2>, dim3(a.B), dim3(nth), 0, s, a, c, iter);
+        else launch_pdl(k_clfit_gather<64, 4>, dim3(a.B), dim3(nth), 0, s, a, c, iter);
     }
     return cudaGetLastError();
 }

@@ -26,6 +26,7 @@ k_corr_fp32(const float* __restrict__ R32, const float* __restrict__ A32, int mp
     __shared__ __align__(16) float Bs[2][BK][BN + PAD];
     __shared__ int any_live;
 
+    pdl_wait();
     const int tid = threadIdx.x;
     const int b0 = blockIdx.x * BM;
     const int j0 = blockIdx.y * BN;
@@ -152,9 +153,8 @@ k_corr_fp32(const float* __restrict__ R32, const float* __restrict__ A32, int mp
 
 cudaError_t launch_corr_fp32(const IterArgs& a, cudaStream_t s) {
     dim3 grid(ceil_div(a.B, BM), ceil_div(a.n, BN));
-    k_corr_fp32<false><<<grid, 256, 0, s>>>(a.R32, a.A32, a.mp, a.B, a.n, a.mask, a.nw, a.status,
-                                            a.cand_val, a.cand_idx, a.nch, nullptr, 0);
-    return cudaGetLastError();
+    return launch_pdl(k_corr_fp32<false>, grid, dim3(256), 0, s, a.R32, a.A32, a.mp, a.B, a.n, a.mask, a.nw,
+                      a.status, a.cand_val, a.cand_idx, a.nch, (float*)nullptr, 0);
 }
 
 cudaError_t launch_corr_fp32_dense(const float* R32, const float* A32, int mp, int B, int n, float* C,

@@ -157,8 +157,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
     __shared__ __align__(8) uint64_t full_bar[MAX_KC];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_slot;
-    __shared__ int any_live;
     __shared__ int failed;
+    __shared__ uint32_t sMask[TM][TN / 32];     // selected-atom bits of the tile (past n: set)
 
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -167,16 +167,7 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
     const int b0 = blockIdx.x * TM;
     const int j0 = blockIdx.y * TN;
 
-    // Skip tiles whose signals have all stopped (uniform exit, before any
-    // barrier or tensor memory is set up).
-    if (tid == 0) { any_live = 0; failed = 0; }
-    __syncthreads();
-    if (tid < TM) {
-        const int b = b0 + tid;
-        if (p.dense != nullptr || (b < p.B && p.status[b] < 0)) any_live = 1;
-    }
-    __syncthreads();
-    if (!any_live) return;
+    if (tid == 0) failed = 0;
 
     // 1024-byte aligned operand tiles (128-byte swizzle atoms)
     const uint32_t raw = smem_u32(smem_raw);
@@ -184,6 +175,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
     uint8_t* sR = smem_raw + pad;                       // kc x 16 KiB
     uint8_t* sA = sR + (size_t)p.kc * R_CHUNK_BYTES;    // kc x 32 KiB
 
+    // Prologue that reads nothing earlier kernels wrote: it overlaps the
+    // tail of the previous kernel (programmatic dependent launch).
     if (tid == 0) {
         for (int c = 0; c < p.kc; ++c) mbar_init(&full_bar[c], 1);
         mbar_init(&done_bar, 1);
@@ -199,6 +192,36 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    pdl_wait();
+
+    // Skip tiles whose signals have all stopped.
+    int live_here = 0;
+    if (tid < TM) {
+        const int b = b0 + tid;
+        live_here = (p.dense != nullptr || (b < p.B && p.status[b] < 0)) ? 1 : 0;
+    }
+    if (!__syncthreads_or(live_here)) {
+        if (warp == 1) {
+            tc_fence_after();
+            asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN) : "memory");
+        }
+        return;
+    }
+
+    // Bitset words of the tile's 128 signals x 256 atoms, loaded coalesced
+    // while TMA and the MMAs run (read by the epilogue after the barrier).
+    if (!p.dense) {
+        for (int e = tid; e < TM * (TN / 32); e += NTHREADS) {
+            const int sl = e / (TN / 32), w = e % (TN / 32);
+            const int sg = b0 + sl, wb = j0 + 32 * w;
+            uint32_t bits = 0xffffffffu;
+            if (sg < p.B && wb < p.n) {
+                bits = p.mask[(size_t)sg * p.nw + (wb >> 5)];
+                if (p.n - wb < 32) bits |= ~0u << (p.n - wb);
+            }
+            sMask[sl][w] = bits;
+        }
+    }
 
     if (tid == 0) {
         // producer: all K chunks of both operands, one barrier per chunk
@@ -254,27 +277,19 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
     } else if (ok) {
         // Per 16-atom group: the two largest masked |c| (lower atom first on
         // ties) become candidates, the third largest bounds every other atom
-        // of the group.  Branch-free, ~11 instructions per value.
-        // mask words of this part, fetched before any TMEM read; atoms past n
-        // count as selected
-        uint32_t mws[HALF / 32];
-#pragma unroll
-        for (int c = 0; c < HALF / 32; ++c) {
-            const int wb = a0 + 32 * c;
-            uint32_t w = 0xffffffffu;
-            if (live && wb < p.n) {
-                w = p.mask[(size_t)sig * p.nw + (wb >> 5)];
-                if (p.n - wb < 32) w |= ~0u << (p.n - wb);
-            }
-            mws[c] = w;
-        }
+        // of the group.  Branch-free, ~11 instructions per value.  Results go
+        // to shared memory first (the operand tiles are free now) and leave
+        // the CTA in contiguous 128-byte rows per signal.
+        constexpr int SV = kTcCandPerTile + 1;                  // padded row strides
+        constexpr int SB = kCorrTcTileN / kTcGroup + 1;
+        float* sVal = reinterpret_cast<float*>(sR);             // [TM][SV]
+        int* sIdx = reinterpret_cast<int*>(sVal + TM * SV);     // [TM][SV]
+        float* sBnd = reinterpret_cast<float*>(sIdx + TM * SV); // [TM][SB]
+        const int sl = quad * 32 + lane;
         constexpr int PER_HALF = 2 * HALF / kTcGroup;          // 8 candidates per part
-        const size_t o = ((size_t)sig * p.nch + blockIdx.y) * kTcCandPerTile + half * PER_HALF;
-        const size_t ob = ((size_t)sig * p.nch + blockIdx.y) * (kCorrTcTileN / kTcGroup) +
-                          half * (HALF / kTcGroup);
 #pragma unroll
         for (int c = 0; c < HALF / 32; ++c) {
-            const uint32_t mw = mws[c];
+            const uint32_t mw = sMask[sl][half * (HALF / 32) + c];
             uint32_t v[32];
             tmem_ld32(tbase + (uint32_t)(32 * c), v);
             tmem_ld_wait();
@@ -293,17 +308,32 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
                     m1 = gt1 ? x : m1;
                     i1 = gt1 ? qq : i1;
                 }
-                if (live) {
-                    const int e = 4 * c + 2 * g;
-                    p.cand_val[o + e] = m1;
-                    p.cand_idx[o + e] = (m1 >= 0.f) ? a0 + 32 * c + i1 : -1;
-                    p.cand_val[o + e + 1] = m2;
-                    p.cand_idx[o + e + 1] = (m2 >= 0.f) ? a0 + 32 * c + i2 : -1;
-                    p.cand_bound[ob + 2 * c + g] = m3;
-                }
+                const int e = half * PER_HALF + 4 * c + 2 * g;
+                sVal[sl * SV + e] = m1;
+                sIdx[sl * SV + e] = (m1 >= 0.f) ? a0 + 32 * c + i1 : -1;
+                sVal[sl * SV + e + 1] = m2;
+                sIdx[sl * SV + e + 1] = (m2 >= 0.f) ? a0 + 32 * c + i2 : -1;
+                sBnd[sl * SB + half * (HALF / kTcGroup) + 2 * c + g] = m3;
             }
         }
+        __syncthreads();
+        for (int e = tid; e < TM * kTcCandPerTile; e += NTHREADS) {
+            const int r = e / kTcCandPerTile, q = e % kTcCandPerTile;
+            const int sg = b0 + r;
+            if (sg < p.B) {
+                const size_t o = ((size_t)sg * p.nch + blockIdx.y) * kTcCandPerTile + q;
+                p.cand_val[o] = sVal[r * SV + q];
+                p.cand_idx[o] = sIdx[r * SV + q];
+            }
+        }
+        constexpr int G = kCorrTcTileN / kTcGroup;
+        for (int e = tid; e < TM * G; e += NTHREADS) {
+            const int r = e / G, q = e % G;
+            const int sg = b0 + r;
+            if (sg < p.B) p.cand_bound[((size_t)sg * p.nch + blockIdx.y) * G + q] = sBnd[r * SB + q];
+        }
     }
+    pdl_trigger();   // after the epilogue: the successor only overlaps our teardown
     tc_fence_before();
     __syncthreads();
     if (warp == 1) {
@@ -362,8 +392,7 @@ cudaError_t launch_tc(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh
         configured = 1;
     }
     dim3 grid(ceil_div(B, TM), ceil_div(n, TN));
-    k_corr_tc<<<grid, NTHREADS, smem, s>>>(mR, mA, p);
-    return cudaGetLastError();
+    return launch_pdl(k_corr_tc, grid, dim3(NTHREADS), smem, s, mR, mA, p);
 }
 
 }  // namespace

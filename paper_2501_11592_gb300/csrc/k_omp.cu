@@ -12,6 +12,7 @@ namespace {
 // Row t of L with L L^T = A_S^T A_S:  L[0:t,0:t] l = g,  L_tt = sqrt(d - l.l);
 // then z_t = (a_j^T y - l.z)/L_tt and x = L^{-T} z.  float64 throughout.
 __global__ void __launch_bounds__(32) k_chol(IterArgs a) {
+    pdl_wait();      // no early trigger: the successor launches when this grid completes
     const int b = blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= a.B) return;
     if (a.status[b] >= 0) return;
@@ -55,24 +56,25 @@ __global__ void __launch_bounds__(32) k_chol(IterArgs a) {
 
 template <int MCH>
 __global__ void __launch_bounds__(256) k_resid(IterArgs a) {
+    pdl_wait();
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < a.B; b += nwarps)
         resid_one<MCH>(a, b);
+    pdl_trigger();
 }
 
 }  // namespace
 
 cudaError_t launch_chol(const IterArgs& a, cudaStream_t s) {
     // one warp per CTA spreads the float64 work over as many SMs as possible
-    k_chol<<<ceil_div(a.B, 32), 32, 0, s>>>(a);
-    return cudaGetLastError();
+    return launch_pdl(k_chol, dim3(ceil_div(a.B, 32)), dim3(32), 0, s, a);
 }
 
 
 template <int MCH>
 void launch_resid_m(const IterArgs& a, cudaStream_t s) {
     const int grid = resident_grid((const void*)k_resid<MCH>, 256, ceil_div(a.B, 8));
-    k_resid<MCH><<<grid, 256, 0, s>>>(a);
+    launch_pdl(k_resid<MCH>, dim3(grid), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_resid(const IterArgs& a, cudaStream_t s) {

@@ -11,9 +11,11 @@ namespace {
 // resident capacity of the GPU, so no partial last wave).
 template <int MCH>
 __global__ void __launch_bounds__(256) k_select(IterArgs a) {
+    pdl_wait();
     const int nwarps = gridDim.x * (blockDim.x >> 5);
     for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < a.B; b += nwarps)
         select_one<MCH>(a, b);
+    pdl_trigger();   // after the work: the successor only overlaps our tail
 }
 
 }  // namespace
@@ -21,7 +23,7 @@ __global__ void __launch_bounds__(256) k_select(IterArgs a) {
 template <int MCH>
 void launch_select_m(const IterArgs& a, cudaStream_t s) {
     const int grid = resident_grid((const void*)k_select<MCH>, 256, ceil_div(a.B, 8));
-    k_select<MCH><<<grid, 256, 0, s>>>(a);
+    launch_pdl(k_select<MCH>, dim3(grid), dim3(256), 0, s, a);
 }
 
 cudaError_t launch_select(const IterArgs& a, cudaStream_t s) {

@@ -19,8 +19,9 @@ __global__ void __launch_bounds__(128) k_update_clomp(IterArgs a, ClArgs c, int 
     constexpr int P = 32 / LPS;
     __shared__ __align__(16) float sh_s[4][P * KT];
     __shared__ float sh_c1[kAdamStaged], sh_c2[kAdamStaged];
-    const bool staged = stage_adam(c, sh_c1, sh_c2);
+    const bool staged = stage_adam(c, sh_c1, sh_c2);   // solve constants: safe before the wait
     __syncthreads();
+    pdl_wait();
     const int w = threadIdx.x >> 5;
     const int units = ceil_div(a.B, P);
     for (int u = blockIdx.x * 4 + w; u < units; u += gridDim.x * 4) {
@@ -36,13 +37,14 @@ __global__ void __launch_bounds__(128) k_update_clomp(IterArgs a, ClArgs c, int 
             if (b < a.B) resid_one<MCH>(a, b);
         }
     }
+    pdl_trigger();   // after the work: the successor only overlaps our tail
 }
 
 template <int MCH, int KT, int LPS>
 void launch_one(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s) {
     const int grid = resident_grid((const void*)k_update_clomp<MCH, KT, LPS>, 128,
                                    ceil_div(a.B, 4 * (32 / LPS)));
-    k_update_clomp<MCH, KT, LPS><<<grid, 128, 0, s>>>(a, c, iter);
+    launch_pdl(k_update_clomp<MCH, KT, LPS>, dim3(grid), dim3(128), 0, s, a, c, iter);
 }
 
 template <int MCH>
