@@ -258,7 +258,8 @@ enum {
     CS_PHASE_FIT = 3,      /* Cholesky update (OMP) or Adam coefficient fit (CLOMP) */
     CS_PHASE_RESID = 4,    /* residual, norm and stopping test */
     CS_PHASE_UPDATE = 5,   /* CLOMP Gram form: selection + fit + residual in one kernel */
-    CS_PHASES = 6
+    CS_PHASE_PERSIST = 6,  /* CLOMP Gram form, bf16: every iteration in one persistent kernel */
+    CS_PHASES = 7
 };
 
 /* enable != 0: bracket every later kernel launch of solves on this plan with
@@ -270,9 +271,15 @@ cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable);
  *     (the first call of a configuration runs eagerly, the second is
  *     captured on a private stream, later ones replay it on `stream`);
  *   CS_OPT_FUSE_UPDATE: CLOMP in Gram form runs selection, Adam fit and
- *     residual of an iteration as one kernel (m <= 256).
- * Results are identical either way. */
-enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1 };
+ *     residual of an iteration as one kernel (m <= 256);
+ *   CS_OPT_PERSIST: CLOMP in Gram form with the bf16 correlation runs the
+ *     whole solve as one persistent kernel, one CTA per SM owning a block of
+ *     signals (m <= 256, n <= 2048, k <= 32; otherwise the per-iteration
+ *     kernels run).
+ * Results are identical either way: every form selects the float32 argmax of
+ * |A^T r| (certified from the bf16 correlation) and runs the same float32
+ * fit and residual arithmetic. */
+enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1, CS_OPT_PERSIST = 2 };
 cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value);
 
 /* Kernel launches per phase since the last reset (always counted), and --

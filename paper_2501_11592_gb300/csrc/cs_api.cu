@@ -80,7 +80,7 @@ struct cs_plan {
     float* colnorm_max = nullptr;
     float* GA = nullptr;       // n_max x n_max when n_max <= kGramAMax
     unsigned* counters = nullptr;
-    float* tab = nullptr;      // Adam bias-correction table, grown on demand
+    float2* tab = nullptr;     // Adam bias-correction table, grown on demand
     int tab_cap = 0;
     char* io = nullptr;        // device staging for the host-buffer entry points
     size_t io_bytes = 0;
@@ -103,6 +103,7 @@ struct cs_plan {
     };
     int use_graphs = 1;
     int fuse_update = 1;       // CLOMP Gram form: one fused kernel per iteration
+    int persist = 1;           // CLOMP Gram form, bf16: one persistent kernel per solve
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -198,7 +199,7 @@ cs_status ensure_tab(cs_plan* P, int len) {
         if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
     }
     int cap = std::max(len, 2048);
-    cudaError_t e = cudaMalloc(&P->tab, sizeof(float) * 2 * (size_t)cap);
+    cudaError_t e = cudaMalloc(&P->tab, sizeof(float2) * (size_t)cap);
     if (e != cudaSuccess) return fail(CS_ENOMEM, "cudaMalloc(adam table): %s", cudaGetErrorString(e));
     P->tab_cap = cap;
     return CS_OK;
@@ -353,8 +354,10 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         c.tab_len = len;
     }
 
-    // CLOMP in Gram form runs selection, fit and residual as one kernel
+    // CLOMP in Gram form runs selection, fit and residual as one kernel, or
+    // (bf16 correlation) the whole solve as one persistent kernel
     const bool fused = cp && cp->form == CS_CL_GRAM && P->fuse_update && update_clomp_fused_supported(a);
+    const bool persist = cp && cp->form == CS_CL_GRAM && bf16 && P->persist && clomp_persist_supported(a, c);
 
     // Every launch of the solve, on stream `st`.
     auto enqueue = [&](cudaStream_t st) -> cs_status {
@@ -370,6 +373,11 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, st); }),
                           "gram of A");
         CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_setup(a, Y, ldy, cp ? 1 : 0, st); }), "setup");
+        if (persist) {
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_PERSIST, st, [&] { return launch_clomp_persist(a, c, st); }),
+                          "persistent solve");
+            return CS_OK;
+        }
         for (int it = 0; it < a.iters; ++it) {
             c.tau0 = c.reset ? 0 : it * c.steps;
             if (bf16)
@@ -400,7 +408,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
     auto put = [&](const void* v, size_t nb) { key.append(static_cast<const char*>(v), nb); };
     const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab};
     put(ptrs, sizeof(ptrs));
-    const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0};
+    const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0, persist ? 1 : 0};
     put(ints, sizeof(ints));
     // field by field (struct padding is not part of the key)
     const double dk[] = {(double)op->k, op->tol, (double)op->max_iter, (double)op->prec,
@@ -838,6 +846,7 @@ cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value) {
     switch (option) {
         case CS_OPT_GRAPHS: plan->use_graphs = value ? 1 : 0; return CS_OK;
         case CS_OPT_FUSE_UPDATE: plan->fuse_update = value ? 1 : 0; return CS_OK;
+        case CS_OPT_PERSIST: plan->persist = value ? 1 : 0; return CS_OK;
         default: return fail(CS_EINVAL, "unknown option %d", option);
     }
 }

@@ -2,6 +2,7 @@
 // Nothing here is part of the public C ABI (include/cs_omp.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
 #include <stdint.h>
@@ -87,7 +88,7 @@ struct ClArgs {
     int tau0;            // Adam step counter before this fit (the same for every live signal)
     float beta1, beta2, eps;
     int reset;
-    const float* tab;    // [2][tab_len]: lr/(1-b1^tau), 1/sqrt(1-b2^tau) for tau = 1..tab_len
+    const float2* tab;   // [tab_len] pairs (lr/(1-b1^tau), 1/sqrt(1-b2^tau)) for tau = 1..tab_len
     int tab_len;
 };
 
@@ -107,7 +108,7 @@ cudaError_t launch_varlen_scatter(const VarlenOut* outs, int k, int B, const int
 cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh, float* A32,
                           __nv_bfloat16* A16, float* colnorm_max, cudaStream_t s);
 cudaError_t launch_setup(const IterArgs& a, const float* Y, int ldy, int clomp, cudaStream_t s);
-cudaError_t launch_adam_table(float* tab, int len, float lr, float beta1, float beta2,
+cudaError_t launch_adam_table(float2* tab, int len, float lr, float beta1, float beta2,
                               cudaStream_t s);
 cudaError_t launch_corr_fp32(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_corr_fp32_dense(const float* R32, const float* A32, int mp, int B, int n, float* C,
@@ -119,6 +120,12 @@ cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream
 cudaError_t launch_prep_R(const float* R, int ldr, int m, int B, int mp, int mh, float* R32,
                           __nv_bfloat16* R16, cudaStream_t s);
 bool corr_tc_supported(int m, int n);
+// 2-D bf16 TMA map over `rows` rows of `row_elems` elements (a multiple of 64,
+// byte stride row_bytes): box 64 x box_rows, 128-byte swizzle, zero fill.
+bool make_tma_map_bf16(CUtensorMap* map, const void* base, int row_elems, int rows, size_t row_bytes,
+                       int box_rows);
+bool clomp_persist_supported(const IterArgs& a, const ClArgs& c);
+cudaError_t launch_clomp_persist(const IterArgs& a, const ClArgs& c, cudaStream_t s);
 cudaError_t launch_select(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_chol(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_resid(const IterArgs& a, cudaStream_t s);

@@ -80,7 +80,8 @@ __global__ void __launch_bounds__(256) k_clfit_gather(IterArgs a, ClArgs c, int 
         __syncthreads();
         ++tau;
         if (w == 0) {
-            const float c1 = c.tab[tau - 1], c2 = c.tab[c.tab_len + tau - 1];
+            const float2 cc = c.tab[tau - 1];
+            const float c1 = cc.x, c2 = cc.y;
 #pragma unroll
             for (int h = 0; h < NQ; ++h) {
                 const int q = lane + 32 * h;

@@ -11,15 +11,16 @@ template <int KT, int LPS>
 __global__ void __launch_bounds__(128) k_clfit_gram(IterArgs a, ClArgs c, int iter) {
     constexpr int P = 32 / LPS;
     __shared__ __align__(16) float sh_s[4][P * KT];
-    __shared__ float sh_c1[kAdamStaged], sh_c2[kAdamStaged];
-    const bool staged = stage_adam(c, sh_c1, sh_c2);   // solve constants: safe before the wait
+    __shared__ float2 sh_tab[kAdamStaged];
+    const float2* tab = stage_adam(c, sh_tab);   // solve constants: safe before the wait
     __syncthreads();
     pdl_wait();
     const int w = threadIdx.x >> 5;
     // warps stride over units of P signals (resident-sized grid)
     const int units = ceil_div(a.B, P);
     for (int u = blockIdx.x * 4 + w; u < units; u += gridDim.x * 4)
-        fit_unit<KT, LPS>(a, c, u, sh_s[w], sh_c1, sh_c2, staged);
+        if constexpr (KT <= 32) fit_grid<KT>(a, c, u, c.tau0, sh_s[w], tab);
+        else fit_unit<KT, LPS>(a, c, u, c.tau0, sh_s[w], tab);
     pdl_trigger();
 }
 
@@ -27,15 +28,15 @@ __global__ void __launch_bounds__(128) k_clfit_gram(IterArgs a, ClArgs c, int it
 
 cudaError_t launch_clfit_gram(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s) {
     // every live signal holds exactly `iter` atoms before this fit, so the
-    // support after it has iter + 1 <= KT atoms; small supports share a warp
+    // support after it has iter + 1 <= KT atoms; one signal per warp
     const int kt = round_up(iter + 1, 8);
 #define CS_GRAM_LAUNCH(KT_, LPS_)                                                              \
     launch_pdl(k_clfit_gram<KT_, LPS_>,                                                         \
                dim3(resident_grid((const void*)k_clfit_gram<KT_, LPS_>, 128, ceil_div(a.B, 4 * (32 / LPS_)))), \
                dim3(128), 0, s, a, c, iter)
     switch (kt) {
-        case 8: CS_GRAM_LAUNCH(8, 8); break;
-        case 16: CS_GRAM_LAUNCH(16, 16); break;
+        case 8: CS_GRAM_LAUNCH(8, 32); break;
+        case 16: CS_GRAM_LAUNCH(16, 32); break;
         case 24: CS_GRAM_LAUNCH(24, 32); break;
         case 32: CS_GRAM_LAUNCH(32, 32); break;
         case 40: CS_GRAM_LAUNCH(40, 32); break;

@@ -1,0 +1,567 @@
+// Persistent batched CLOMP (Methods, "Coefficients learning on OMP"; Gram-form
+// fit) with the bf16 tensor-core correlation: the whole solve in one launch.
+//
+// One CTA per SM owns a block of up to 27 signals and runs every iteration of
+// them on chip, so no iteration boundary costs a launch, a ramp-up or a tail:
+//   * the bf16 atom tiles A16[128 atoms][64] stream by TMA through an 8-deep
+//     ring, one stage per signal warp 1..8 (the copy rate of this machine
+//     grows with the number of issuing warps, not with the ring depth); A is
+//     the same in every iteration, so each pass's first tiles are prefetched
+//     while the previous pass ends;
+//   * one thread of warp 0 issues tcgen05.mma with M = 128 atoms, N = 32
+//     signal columns, K = 16: the correlation c = A^T r of the block's
+//     signals lands in tensor memory, 32 fp32 columns per atom tile;
+//   * warps 1..27 (one per signal) read the accumulators in two passes:
+//     pass 1 finds each signal's largest masked bf16 |c| (a packed
+//     value/index key, transposed max-reduction per 32 atoms), pass 2 lists
+//     every atom within 2 delta of it (delta bounds |c_bf16 - c_fp32| as in
+//     the per-iteration path).  Re-scoring that short list in float32 yields
+//     the float32 argmax over all atoms.  The signal's warp then appends the
+//     atom (Gram row from A^T A), runs the T Adam steps of the Gram-form fit,
+//     forms the residual and stop test, and writes the residual as bf16
+//     straight into the swizzled shared-memory B operand of the next MMAs.
+// Every CTA runs a fixed schedule: k correlation passes per block of signals
+// (rounds without a live signal skip the epilogue).
+// Every wait is bounded: on time-out the CTA raises a device error flag,
+// stops all roles, lets copies and MMAs in flight finish and frees its
+// tensor memory.
+#include "k_fit.cuh"
+#include "k_resid.cuh"
+#include "k_select.cuh"
+#include "k_tc.cuh"
+
+#include <algorithm>
+
+namespace cs {
+namespace {
+
+constexpr int PS_NS = 27;                    // signals per block = signal warps
+constexpr int PS_WARPS = PS_NS + 1;          // + one control warp (TMA producer, MMA issuer)
+constexpr int PS_THREADS = 32 * PS_WARPS;
+constexpr int PS_SIGTHREADS = 32 * PS_NS;
+constexpr int PS_N = 32;                     // UMMA N: the block's signals, padded
+constexpr int PS_TM = 128;                   // atoms per UMMA M tile (TMEM lanes)
+constexpr int PS_KCH = 64;                   // bf16 per 128-byte swizzled row
+constexpr int PS_TILE = PS_TM * PS_KCH * 2;  // 16 KiB atom tile
+constexpr int PS_ST = 8;                     // atom-tile ring depth
+constexpr int PS_BSTRIDE = PS_N * 128;       // bytes per 64-element K block of the B operand
+constexpr int PS_MAXKB = 4;                  // m <= 256
+constexpr int PS_CAP = 32;                   // candidates held per signal
+constexpr int PS_KT = 32;                    // largest support
+constexpr int PS_IDXB = 11;                  // atom-index bits of the packed key
+constexpr int PS_MAXN = 1 << PS_IDXB;        // n <= 2048 (also: 16 tiles x 32 TMEM columns)
+constexpr int PS_MAXCH = PS_MAXN / PS_TM;
+constexpr int PS_TAB = 2048;                 // Adam factor pairs staged
+
+// shared-memory carve-up (from a 1024-byte aligned base)
+constexpr int PS_OFF_B = PS_ST * PS_TILE;
+constexpr int PS_OFF_MASK = PS_OFF_B + PS_MAXKB * PS_BSTRIDE;
+constexpr int PS_OFF_PART = PS_OFF_MASK + PS_MAXN * 4;
+constexpr int PS_OFF_THETA = PS_OFF_PART + PS_MAXCH * 4 * 32 * 4;
+constexpr int PS_OFF_CCOUNT = PS_OFF_THETA + 32 * 4;
+constexpr int PS_OFF_CLIST = PS_OFF_CCOUNT + 32 * 4;
+constexpr int PS_OFF_SVEC = PS_OFF_CLIST + 32 * PS_CAP * 4;
+constexpr int PS_OFF_TAB = PS_OFF_SVEC + PS_NS * PS_KT * 4;
+constexpr int PS_SMEM = PS_OFF_TAB + PS_TAB * 8 + 1024;
+
+struct PsArgs {
+    IterArgs a;
+    ClArgs c;        // tau0 is derived per iteration
+    int ns;          // signals per block
+    int nblk;        // number of blocks
+    int nslots;      // blocks per CTA (the last slot may be empty for some CTAs)
+    int kb;          // K blocks of 64 (mh / 64)
+    int nchunk;      // atom tiles, ceil(n / 128)
+    int tmem_cols;   // power of two >= 32 * nchunk
+    int staged;      // Adam table staged in shared memory
+};
+
+__device__ __forceinline__ void named_sync() {
+    asm volatile("barrier.sync 1, %0;" ::"n"(PS_SIGTHREADS) : "memory");
+}
+
+// Barrier over the signal warps that also ORs a predicate across them.
+__device__ __forceinline__ bool named_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.ne.u32 p, %1, 0;\n\t"
+        "barrier.red.or.pred q, 1, %2, p;\n\t"
+        "selp.u32 %0, 1, 0, q;\n\t}\n"
+        : "=r"(r)
+        : "r"((uint32_t)v), "n"(PS_SIGTHREADS)
+        : "memory");
+    return r != 0;
+}
+
+// Bounded wait that also gives up when *flag becomes non-zero:
+// 1 = phase complete, 0 = flag raised, -1 = timed out.
+__device__ __forceinline__ int wait_or_flag(uint64_t* bar, uint32_t parity, const volatile int* flag) {
+    const unsigned long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*flag) return 0;
+        if (clock64() - t0 > WAIT_CYCLES) return -1;
+    }
+    return 1;
+}
+
+// Transposed max-reduction: lane l ends with the maximum over the warp of
+// k[l] (in k[0]).  31 shuffles.
+__device__ __forceinline__ void warp_max_scatter32(uint32_t (&k)[32]) {
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const uint32_t send = upper ? k[i] : k[i + off];
+            const uint32_t keep = upper ? k[i + off] : k[i];
+            k[i] = max(keep, __shfl_xor_sync(0xffffffffu, send, off));
+        }
+    }
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+        "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
+          "=r"(r[15])
+        : "r"(taddr));
+}
+
+// Residual row of signal s (row-sliced like load_row) as bf16 into the
+// K-major, 128-byte-swizzled B operand: element k of row s sits in K block
+// k/64, 8-row group s/8, row s%8, 16-byte chunk ((k%64)/8) ^ (s%8).
+template <int MCH>
+__device__ __forceinline__ void put_b_row(uint8_t* sB, int s, int mp, const float4 (&r)[MCH], bool zero) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < MCH; ++c) {
+        const int k = (c * 32 + lane) * 4;
+        if (k < mp) {
+            const int kb = k >> 6, ch = (k & 63) >> 3, hf = (k >> 2) & 1;
+            uint8_t* dst = sB + kb * PS_BSTRIDE + (s >> 3) * 1024 + (s & 7) * 128 + ((ch ^ (s & 7)) << 4) + hf * 8;
+            __nv_bfloat162 lo = __floats2bfloat162_rn(zero ? 0.f : r[c].x, zero ? 0.f : r[c].y);
+            __nv_bfloat162 hi = __floats2bfloat162_rn(zero ? 0.f : r[c].z, zero ? 0.f : r[c].w);
+            uint2 v;
+            v.x = *reinterpret_cast<uint32_t*>(&lo);
+            v.y = *reinterpret_cast<uint32_t*>(&hi);
+            *reinterpret_cast<uint2*>(dst) = v;
+        }
+    }
+}
+
+__device__ __forceinline__ void fit_dispatch(const IterArgs& a, const ClArgs& c, int b, int t, int tau0,
+                                             float* sv, const float2* tab) {
+    switch (round_up(t + 1, 8)) {
+        case 8: fit_grid<8>(a, c, b, tau0, sv, tab); break;
+        case 16: fit_grid<16>(a, c, b, tau0, sv, tab); break;
+        case 24: fit_grid<24>(a, c, b, tau0, sv, tab); break;
+        default: fit_grid<32>(a, c, b, tau0, sv, tab); break;
+    }
+}
+
+template <int MCH>
+__global__ void __launch_bounds__(PS_THREADS, 1)
+k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
+    extern __shared__ uint8_t smem_raw[];
+    __shared__ __align__(8) uint64_t full_bar[PS_ST], empty_bar[PS_ST], rready_bar, acc_bar, fin_bar;
+    __shared__ uint32_t tmem_slot;
+    __shared__ uint32_t live_bits[2];
+    __shared__ volatile int abort_flag;
+
+    const IterArgs& a = p.a;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const uint32_t raw = smem_u32(smem_raw);
+    uint8_t* base = smem_raw + (((raw + 1023u) & ~1023u) - raw);
+    uint8_t* ring = base;
+    uint8_t* sB = base + PS_OFF_B;
+    uint32_t* mask_t = reinterpret_cast<uint32_t*>(base + PS_OFF_MASK);   // bit s: signal s holds the atom
+    uint32_t* part = reinterpret_cast<uint32_t*>(base + PS_OFF_PART);     // [tile*4 + quadrant][32]
+    float* theta = reinterpret_cast<float*>(base + PS_OFF_THETA);
+    int* ccount = reinterpret_cast<int*>(base + PS_OFF_CCOUNT);
+    int* clist = reinterpret_cast<int*>(base + PS_OFF_CLIST);
+    float* svec = reinterpret_cast<float*>(base + PS_OFF_SVEC);
+    float2* tabs = reinterpret_cast<float2*>(base + PS_OFF_TAB);
+    unsigned* errflag = a.counters + 1;
+
+    if (tid == 0) {
+        for (int i = 0; i < PS_ST; ++i) {
+            mbar_init(&full_bar[i], 1);
+            mbar_init(&empty_bar[i], 1);
+        }
+        mbar_init(&rready_bar, PS_NS);
+        mbar_init(&acc_bar, 1);
+        mbar_init(&fin_bar, 1);
+        abort_flag = 0;
+        live_bits[0] = live_bits[1] = 0u;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(p.tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    for (int i = tid; i < PS_MAXKB * PS_BSTRIDE / 16; i += PS_THREADS)
+        reinterpret_cast<uint4*>(sB)[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (tid < 32) {
+        theta[tid] = __int_as_float(0x7f800000);
+        ccount[tid] = 0;
+    }
+    if (p.staged)
+        for (int i = tid; i < p.c.tab_len; i += PS_THREADS) tabs[i] = p.c.tab[i];
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int passes = p.nslots * a.iters;
+    const int per_pass = p.nchunk * p.kb;                     // atom tiles per pass
+    const uint32_t total = (uint32_t)passes * (uint32_t)per_pass;
+
+    if (warp == 0) {
+        // ------------------------------------------------ MMA issuer ------
+        if (lane == 0) {
+            constexpr uint32_t idesc = make_idesc(PS_TM, PS_N);
+            uint32_t gc = 0;   // tiles consumed
+            bool ok = true;
+            for (int pass = 0; pass < passes && ok; ++pass) {
+                const int w = wait_or_flag(&rready_bar, (uint32_t)pass & 1u, &abort_flag);
+                if (w <= 0) {
+                    if (w < 0) atomicOr(errflag, 8u);
+                    ok = false;
+                    break;
+                }
+                tc_fence_after();
+                for (int c = 0; c < p.nchunk && ok; ++c) {
+                    for (int kk = 0; kk < p.kb; ++kk) {
+                        const int st = gc % PS_ST;
+                        const int w2 = wait_or_flag(&full_bar[st], (gc / PS_ST) & 1u, &abort_flag);
+                        if (w2 <= 0) {
+                            if (w2 < 0) atomicOr(errflag, 8u);
+                            ok = false;
+                            break;
+                        }
+                        tc_fence_after();
+                        const uint64_t da = smem_desc_sw128(smem_u32(ring + st * PS_TILE));
+                        const uint64_t db = smem_desc_sw128(smem_u32(sB + kk * PS_BSTRIDE));
+#pragma unroll
+                        for (int k16 = 0; k16 < PS_KCH / 16; ++k16)
+                            umma_bf16(tmem + (uint32_t)(c * PS_N), da + (uint64_t)(2 * k16),
+                                      db + (uint64_t)(2 * k16), idesc, (kk | k16) != 0);
+                        umma_commit(&empty_bar[st]);   // frees the ring slot once these MMAs are done
+                        ++gc;
+                    }
+                }
+                if (ok) umma_commit(&acc_bar);     // the block's accumulators are complete
+            }
+            if (!ok) abort_flag = 1;
+            // every MMA issued so far completes before teardown
+            umma_commit(&fin_bar);
+            if (!mbar_wait(&fin_bar, 0)) atomicOr(errflag, 8u);
+        }
+    } else {
+        // ------------------------------------------------ signal warps ----
+        const int s = warp - 1;
+        const int q = warp & 3;                       // TMEM lane quadrant this warp may read
+        const int qfirst = (q >= 1) ? q : 4;          // first signal warp of the quadrant
+        const int qidx = (warp - qfirst) >> 2;
+        const int qcnt = (PS_WARPS - qfirst + 3) >> 2;   // signal warps of the quadrant
+        const float cert = (0x1p-7f + 0x1p-16f + (float)a.m * (0x1p-22f + 0x1p-23f)) * (*a.colnorm_max) * 1.01f;
+        uint32_t accp = 0, rnd = 0;
+        bool aborted = false;
+        // producer of ring stage `st` (signal warps 1..PS_ST): tiles st, st+ST, ...
+        const bool producer = (s < PS_ST) && lane == 0;
+        const int st = s;
+        uint32_t pg = (uint32_t)st;   // next tile this producer issues
+        for (int slot = 0; slot < p.nslots && !aborted; ++slot) {
+            const int blk = blockIdx.x + slot * gridDim.x;
+            const bool have = blk < p.nblk;
+            const int b = blk * p.ns + s;
+            const bool mine = have && s < p.ns && b < a.B;
+            bool live = false;
+            int t = 0;
+            float rho = 0.f;
+            named_sync();   // every warp is done with the previous block's selected-atom bits
+            for (int i = tid - 32; i < p.nchunk * PS_TM; i += PS_SIGTHREADS) mask_t[i] = 0u;
+            {
+                float4 y[MCH];
+#pragma unroll
+                for (int c2 = 0; c2 < MCH; ++c2) y[c2] = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (mine) {
+                    load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, y);
+                    live = a.status[b] < 0;
+                    rho = a.res_norm[b];
+                }
+                put_b_row<MCH>(sB, s, a.mp, y, !live);
+            }
+            // k rounds per block whatever the signals do (a fixed schedule);
+            // rounds without a live signal skip the epilogue
+            for (int it = 0; it < a.iters; ++it, ++rnd) {
+                if (lane == 0 && live) atomicOr(&live_bits[rnd & 1u], 1u << s);
+                const bool any = named_sync_or(live);
+                if (warp == 1 && lane == 0) live_bits[(rnd + 1) & 1u] = 0u;
+                fence_proxy_async_smem();   // the B rows written above, for the tensor core
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&rready_bar);
+                if (producer) {
+                    // this pass's tiles of my stage, then the next pass's first
+                    // ones: tile g reuses the slot of tile g - ST, which this
+                    // or the previous pass consumes (g < (pass+1) per_pass + ST)
+                    const uint32_t lim = min(total, (rnd + 1u) * (uint32_t)per_pass + (uint32_t)PS_ST);
+                    for (; pg < lim; pg += PS_ST) {
+                        if (pg >= (uint32_t)PS_ST) {
+                            const int we = wait_or_flag(&empty_bar[st], ((pg / PS_ST) & 1u) ^ 1u, &abort_flag);
+                            if (we <= 0) {
+                                if (we < 0) {
+                                    abort_flag = 1;
+                                    atomicOr(errflag, 4u);
+                                }
+                                break;
+                            }
+                        }
+                        const int tile = (int)(pg % (uint32_t)per_pass);
+                        mbar_arrive_expect_tx(&full_bar[st], PS_TILE);
+                        tma_load_2d(ring + st * PS_TILE, &mapA, &full_bar[st], (tile % p.kb) * PS_KCH,
+                                    (tile / p.kb) * PS_TM);
+                    }
+                }
+                __syncwarp();
+
+                const int w = wait_or_flag(&acc_bar, accp & 1u, &abort_flag);
+                ++accp;
+                tc_fence_after();
+                if (w < 0 && lane == 0) {
+                    abort_flag = 1;
+                    atomicOr(errflag, 16u);
+                }
+                if (named_sync_or(w <= 0)) {
+                    aborted = true;
+                    break;
+                }
+                if (!any) continue;
+                const uint32_t lb = live_bits[rnd & 1u];
+
+                // pass 1: per 32 atoms x 32 signals, the largest masked key per signal
+                for (int c = qidx; c < p.nchunk; c += qcnt) {
+                    uint32_t k[32];
+                    tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * PS_N), k);
+                    tmem_ld_wait();
+                    const int atom = c * PS_TM + 32 * q + lane;
+                    const uint32_t mw = ((atom < a.n) ? mask_t[atom] : 0xffffffffu) | ~lb;
+                    const uint32_t ilo = (uint32_t)((PS_MAXN - 1) - atom);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        k[i] = ((mw >> i) & 1u) ? 0u : (((k[i] & 0x7fffffffu) & ~(uint32_t)(PS_MAXN - 1)) | ilo);
+                    warp_max_scatter32(k);
+                    part[(c * 4 + q) * 32 + lane] = k[0];
+                }
+                named_sync();
+                // threshold of my signal: largest bf16 |c| minus 2 delta
+                {
+                    uint32_t km = 0u;
+                    if (live)
+                        for (int e = lane; e < p.nchunk * 4; e += 32) km = max(km, part[e * 32 + s]);
+                    km = __reduce_max_sync(0xffffffffu, km);
+                    // (no usable key: every unselected atom becomes a candidate)
+                    float th = __int_as_float(0x7f800000);
+                    if (live)
+                        th = (km == 0u) ? __int_as_float(0xff800000)
+                                        : __uint_as_float(km & ~(uint32_t)(PS_MAXN - 1)) - 2.f * cert * rho;
+                    if (lane == 0) theta[s] = th;
+                }
+                named_sync();
+                // pass 2: list the atoms at or above the threshold
+                for (int c = qidx; c < p.nchunk; c += qcnt) {
+                    const int atom = c * PS_TM + 32 * q + lane;
+                    const uint32_t mw = ((atom < a.n) ? mask_t[atom] : 0xffffffffu) | ~lb;
+                    uint32_t hit = 0u;
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        uint32_t v[16];
+                        tmem_ld16(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * PS_N + 16 * h), v);
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int i = 0; i < 16; ++i)
+                            hit |= (fabsf(__uint_as_float(v[i])) >= theta[16 * h + i] ? 1u : 0u) << (16 * h + i);
+                    }
+                    hit &= ~mw;
+                    while (hit) {
+                        const int i = __ffs(hit) - 1;
+                        hit &= hit - 1u;
+                        const int pos = atomicAdd(&ccount[i], 1);
+                        if (pos < PS_CAP) clist[i * PS_CAP + pos] = atom;
+                    }
+                }
+                tc_fence_before();
+                named_sync();
+
+                if (live) {
+                    // ---- selection: float32 re-score of the listed atoms
+                    float4 r[MCH];
+                    load_row<MCH>(a.R32 + (size_t)b * a.mp, a.mp, r);
+                    const int cnt = ccount[s];
+                    float bv = -1.f;
+                    int bj = -1;
+                    if (cnt <= PS_CAP) {
+                        const int my = (lane < cnt) ? clist[s * PS_CAP + lane] : -1;
+                        for (int u0 = 0; u0 < cnt; u0 += 4) {
+                            float pr[4];
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const int j = __shfl_sync(0xffffffffu, my, (u0 + u) & 31);
+                                pr[u] = 0.f;
+                                if (u0 + u < cnt) {
+                                    const float4* col = reinterpret_cast<const float4*>(a.A32 + (size_t)j * a.mp);
+#pragma unroll
+                                    for (int cc = 0; cc < MCH; ++cc) {
+                                        const int i4 = cc * 32 + lane;
+                                        if (i4 * 4 < a.mp) pr[u] += dot4(col[i4], r[cc]);
+                                    }
+                                }
+                            }
+#pragma unroll
+                            for (int u = 0; u < 4; ++u) {
+                                const float v = fabsf(warp_sum(pr[u]));
+                                const int j = __shfl_sync(0xffffffffu, my, (u0 + u) & 31);
+                                if (u0 + u < cnt && cand_better(v, j, bv, bj)) {
+                                    bv = v;
+                                    bj = j;
+                                }
+                            }
+                        }
+                    } else {
+                        // list overflow: float32 scan of every unselected atom
+                        for (int j0 = 0; j0 < a.n; j0 += 32) {
+                            const int j = j0 + lane;
+                            const bool ok = j < a.n && !((mask_t[j] >> s) & 1u);
+                            float v = fabsf(warp_dots32<MCH>(a.A32, a.mp, ok ? j : -1, r));
+                            int jj = ok ? j : -1;
+                            warp_argmax(v, jj);
+                            if (cand_better(v, jj, bv, bj)) {
+                                bv = v;
+                                bj = jj;
+                            }
+                        }
+                        if (lane == 0) atomicAdd(&a.counters[0], 1u);
+                    }
+                    if (lane == 0) ccount[s] = 0;
+                    if (bj < 0) {
+                        // nothing left to select
+                        live = false;
+                        if (lane == 0) a.status[b] = CS_SIG_MAX_ITER;
+                    } else {
+                        if (lane == 0) atomicOr(&mask_t[bj], 1u << s);
+                        float4 y[MCH];
+                        load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, y);
+                        append_atom<MCH>(a, b, t, bj, y);
+                        __syncwarp();
+                        // ---- Gram-form Adam fit on the t+1 support atoms
+                        const int tau0 = p.c.reset ? 0 : t * p.c.steps;
+                        fit_dispatch(a, p.c, b, t, tau0, svec + s * PS_KT, (p.staged ? tabs : p.c.tab) + tau0);
+                        __syncwarp();
+                        ++t;
+                        // ---- residual, stop test, next B operand row
+                        r[0] = y[0];
+#pragma unroll
+                        for (int c2 = 1; c2 < MCH; ++c2) r[c2] = y[c2];
+                        resid_vector<MCH>(a, b, t, r);
+                        float ss = 0.f;
+                        float4* R = reinterpret_cast<float4*>(a.R32 + (size_t)b * a.mp);
+#pragma unroll
+                        for (int c2 = 0; c2 < MCH; ++c2) {
+                            const int i4 = c2 * 32 + lane;
+                            if (i4 * 4 < a.mp) {
+                                R[i4] = r[c2];
+                                ss += dot4(r[c2], r[c2]);
+                            }
+                        }
+                        rho = sqrtf(warp_sum(ss));
+                        if (lane == 0) stop_test(a, b, t, rho);
+                        live = !((double)rho <= a.tol || t >= a.k || t >= a.iters);
+                        if (live) put_b_row<MCH>(sB, s, a.mp, r, false);
+                    }
+                }
+            }
+        }
+        // the last copy of my stage (the only one that can still be in
+        // flight after an abort) lands before the CTA exits
+        if (producer && pg >= (uint32_t)PS_ST) {
+            const uint32_t last = pg - PS_ST;
+            if (!mbar_wait(&full_bar[st], (last / PS_ST) & 1u)) atomicOr(errflag, 4u);
+        }
+    }
+
+    // ---------------------------------------------------------- teardown --
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(p.tmem_cols)
+                     : "memory");
+    }
+}
+
+int sm_count() {
+    static int n = 0;
+    if (!n) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 1;
+    }
+    return n;
+}
+
+}  // namespace
+
+bool clomp_persist_supported(const IterArgs& a, const ClArgs& c) {
+    return a.R16 != nullptr && a.need_gram && a.GA != nullptr && a.mh <= PS_MAXKB * PS_KCH &&
+           a.n <= PS_MAXN && a.k <= PS_KT && c.steps >= 0;
+}
+
+namespace {
+
+template <int MCH>
+cudaError_t configure_once() {
+    static const cudaError_t st =
+        cudaFuncSetAttribute(k_clomp_persist<MCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, PS_SMEM);
+    return st;
+}
+
+template <int MCH>
+cudaError_t launch_mch(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
+    cudaError_t e = configure_once<MCH>();
+    if (e != cudaSuccess) return e;
+    PsArgs p{};
+    p.a = a;
+    p.c = c;
+    p.kb = a.mh / PS_KCH;
+    p.nchunk = ceil_div(a.n, PS_TM);
+    p.tmem_cols = 32;
+    while (p.tmem_cols < p.nchunk * PS_N) p.tmem_cols *= 2;
+    p.staged = c.tab_len <= PS_TAB ? 1 : 0;
+    // one CTA per SM, blocks of <= PS_NS signals
+    const int nsm = sm_count();
+    const int grid0 = std::min(nsm, a.B);
+    p.ns = std::min(PS_NS, ceil_div(a.B, grid0));
+    p.nblk = ceil_div(a.B, p.ns);
+    const int grid = std::min(grid0, p.nblk);
+    p.nslots = ceil_div(p.nblk, grid);
+    CUtensorMap mA;
+    if (!make_tma_map_bf16(&mA, a.A16, a.mh, a.n, (size_t)a.mh * 2, PS_TM)) return cudaErrorInvalidValue;
+    k_clomp_persist<MCH><<<grid, PS_THREADS, PS_SMEM, s>>>(mA, p);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_clomp_persist(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
+    if (!clomp_persist_supported(a, c)) return cudaErrorNotSupported;
+    return ceil_div(a.mp, 128) == 1 ? launch_mch<1>(a, c, s) : launch_mch<2>(a, c, s);
+}
+
+}  // namespace cs

@@ -9,13 +9,11 @@ namespace cs {
 namespace {
 
 // ------------------------------------------------ residual + stop test -----
+// r <- r - A_S s_S for the t support atoms of signal b (one warp; r enters
+// holding y, row-sliced like load_row).
 template <int MCH>
-__device__ __forceinline__ void resid_one(const IterArgs& a, const int b) {
+__device__ __forceinline__ void resid_vector(const IterArgs& a, const int b, const int t, float4 (&r)[MCH]) {
     const int lane = threadIdx.x & 31;
-    if (a.status[b] >= 0) return;
-    const int t = a.n_iter[b];
-    float4 r[MCH];
-    load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, r);
     const int* sup = a.support + (size_t)b * a.k;
     const float* x = a.coef + (size_t)b * a.k;
     // Columns in selection order (the oracle's order).  Lane q loads support
@@ -50,6 +48,24 @@ __device__ __forceinline__ void resid_one(const IterArgs& a, const int b) {
                 }
         }
     }
+}
+
+// Stopping test of Eq. 2 after t atoms (lane 0 of the signal's warp).
+__device__ __forceinline__ void stop_test(const IterArgs& a, const int b, const int t, const float rho) {
+    a.res_norm[b] = rho;
+    if ((double)rho <= a.tol) a.status[b] = CS_SIG_REACHED_TOL;
+    else if (t >= a.k) a.status[b] = CS_SIG_REACHED_K;
+    else if (t >= a.iters) a.status[b] = CS_SIG_MAX_ITER;
+}
+
+template <int MCH>
+__device__ __forceinline__ void resid_one(const IterArgs& a, const int b) {
+    const int lane = threadIdx.x & 31;
+    if (a.status[b] >= 0) return;
+    const int t = a.n_iter[b];
+    float4 r[MCH];
+    load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, r);
+    resid_vector<MCH>(a, b, t, r);
     float ss = 0.f;
     float4* R = reinterpret_cast<float4*>(a.R32 + (size_t)b * a.mp);
 #pragma unroll
@@ -75,13 +91,7 @@ __device__ __forceinline__ void resid_one(const IterArgs& a, const int b) {
         }
     }
     ss = warp_sum(ss);
-    if (lane == 0) {
-        const float rho = sqrtf(ss);
-        a.res_norm[b] = rho;
-        if ((double)rho <= a.tol) a.status[b] = CS_SIG_REACHED_TOL;
-        else if (t >= a.k) a.status[b] = CS_SIG_REACHED_K;
-        else if (t >= a.iters) a.status[b] = CS_SIG_MAX_ITER;
-    }
+    if (lane == 0) stop_test(a, b, t, sqrtf(ss));
 }
 
 }  // namespace

@@ -7,6 +7,53 @@
 namespace cs {
 namespace {
 
+// Append atom bj as the (t+1)-th support atom of signal b (one warp): the
+// support entry and, when the fit needs them, the new Gram row / column and
+// A_S^T y entry (OMP: gcol, dnorm, bt for the Cholesky update; CLOMP Gram
+// form: G and bvec).  y: the signal, row-sliced like load_row.
+template <int MCH>
+__device__ __forceinline__ void append_atom(const IterArgs& a, const int b, const int t, const int bj,
+                                            const float4 (&y)[MCH]) {
+    const int lane = threadIdx.x & 31;
+    if (lane == 0) a.support[(size_t)b * a.k + t] = bj;
+    if (a.need_gcol || a.need_gram) {
+        float4 aj[MCH];
+        load_row<MCH>(a.A32 + (size_t)bj * a.mp, a.mp, aj);
+        float dd = 0.f, by = 0.f;
+#pragma unroll
+        for (int c = 0; c < MCH; ++c) {
+            dd += dot4(aj[c], aj[c]);
+            by += dot4(aj[c], y[c]);
+        }
+        dd = warp_sum(dd);
+        by = warp_sum(by);
+        const int* sup = a.support + (size_t)b * a.k;
+        const float* garow = a.GA ? a.GA + (size_t)bj * a.n : nullptr;
+        if (garow) dd = garow[bj];     // same arithmetic as the other Gram entries
+        for (int i0 = 0; i0 < t; i0 += 32) {
+            const int i = i0 + lane;
+            const int ji = (i < t) ? sup[i] : -1;
+            const float g = garow ? (ji >= 0 ? garow[ji] : 0.f) : warp_dots32<MCH>(a.A32, a.mp, ji, aj);
+            if (i < t) {
+                if (a.need_gcol) a.gcol[(size_t)i * a.B + b] = g;
+                if (a.need_gram) {
+                    float* G = a.G + (size_t)b * a.kmax * a.kmax;
+                    G[(size_t)t * a.kmax + i] = g;
+                    G[(size_t)i * a.kmax + t] = g;
+                }
+            }
+        }
+        if (lane == 0) {
+            a.dnorm[b] = dd;
+            a.bt[b] = by;
+            if (a.need_gram) {
+                a.G[((size_t)b * a.kmax + t) * a.kmax + t] = dd;
+                a.bvec[(size_t)b * a.kmax + t] = by;
+            }
+        }
+    }
+}
+
 template <int MCH>
 __device__ __forceinline__ void select_one(const IterArgs& a, const int b) {
     const int lane = threadIdx.x & 31;
@@ -154,48 +201,10 @@ __device__ __forceinline__ void select_one(const IterArgs& a, const int b) {
         if (lane == 0) a.status[b] = CS_SIG_MAX_ITER;
         return;
     }
-    if (lane == 0) {
-        a.support[(size_t)b * a.k + t] = bj;
-        a.mask[(size_t)b * a.nw + (bj >> 5)] |= (1u << (bj & 31));
-    }
-
-    if (a.need_gcol || a.need_gram) {
-        float4 aj[MCH], y[MCH];
-        load_row<MCH>(a.A32 + (size_t)bj * a.mp, a.mp, aj);
-        load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, y);
-        float dd = 0.f, by = 0.f;
-#pragma unroll
-        for (int c = 0; c < MCH; ++c) {
-            dd += dot4(aj[c], aj[c]);
-            by += dot4(aj[c], y[c]);
-        }
-        dd = warp_sum(dd);
-        by = warp_sum(by);
-        const int* sup = a.support + (size_t)b * a.k;
-        const float* garow = a.GA ? a.GA + (size_t)bj * a.n : nullptr;
-        if (garow) dd = garow[bj];     // same arithmetic as the other Gram entries
-        for (int i0 = 0; i0 < t; i0 += 32) {
-            const int i = i0 + lane;
-            const int ji = (i < t) ? sup[i] : -1;
-            const float g = garow ? (ji >= 0 ? garow[ji] : 0.f) : warp_dots32<MCH>(a.A32, a.mp, ji, aj);
-            if (i < t) {
-                if (a.need_gcol) a.gcol[(size_t)i * a.B + b] = g;
-                if (a.need_gram) {
-                    float* G = a.G + (size_t)b * a.kmax * a.kmax;
-                    G[(size_t)t * a.kmax + i] = g;
-                    G[(size_t)i * a.kmax + t] = g;
-                }
-            }
-        }
-        if (lane == 0) {
-            a.dnorm[b] = dd;
-            a.bt[b] = by;
-            if (a.need_gram) {
-                a.G[((size_t)b * a.kmax + t) * a.kmax + t] = dd;
-                a.bvec[(size_t)b * a.kmax + t] = by;
-            }
-        }
-    }
+    if (lane == 0) a.mask[(size_t)b * a.nw + (bj >> 5)] |= (1u << (bj & 31));
+    float4 y[MCH];
+    load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, y);
+    append_atom<MCH>(a, b, t, bj, y);
 }
 
 }  // namespace

@@ -183,12 +183,12 @@ __global__ void k_setup(IterArgs a, const float* __restrict__ Y, int ldy, int cl
 // the float32 hyper-parameters and rounded once:
 //   tab[tau-1]       = lr / (1 - beta1^tau)
 //   tab[len + tau-1] = 1 / sqrt(1 - beta2^tau)
-__global__ void k_adam_table(float* tab, int len, float lr, float beta1, float beta2) {
+__global__ void k_adam_table(float2* tab, int len, float lr, float beta1, float beta2) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= len) return;
     const double tau = (double)(i + 1);
-    tab[i] = (float)((double)lr / (1.0 - pow((double)beta1, tau)));
-    tab[len + i] = (float)(1.0 / sqrt(1.0 - pow((double)beta2, tau)));
+    tab[i] = make_float2((float)((double)lr / (1.0 - pow((double)beta1, tau))),
+                         (float)(1.0 / sqrt(1.0 - pow((double)beta2, tau))));
 }
 
 
@@ -232,7 +232,7 @@ cudaError_t launch_setup(const IterArgs& a, const float* Y, int ldy, int clomp, 
     return cudaGetLastError();
 }
 
-cudaError_t launch_adam_table(float* tab, int len, float lr, float beta1, float beta2,
+cudaError_t launch_adam_table(float2* tab, int len, float lr, float beta1, float beta2,
                               cudaStream_t s) {
     if (len <= 0) return cudaSuccess;
     k_adam_table<<<ceil_div(len, 256), 256, 0, s>>>(tab, len, lr, beta1, beta2);

@@ -18,8 +18,8 @@ template <int MCH, int KT, int LPS>
 __global__ void __launch_bounds__(128) k_update_clomp(IterArgs a, ClArgs c, int iter) {
     constexpr int P = 32 / LPS;
     __shared__ __align__(16) float sh_s[4][P * KT];
-    __shared__ float sh_c1[kAdamStaged], sh_c2[kAdamStaged];
-    const bool staged = stage_adam(c, sh_c1, sh_c2);   // solve constants: safe before the wait
+    __shared__ float2 sh_tab[kAdamStaged];
+    const float2* tab = stage_adam(c, sh_tab);   // solve constants: safe before the wait
     __syncthreads();
     pdl_wait();
     const int w = threadIdx.x >> 5;
@@ -30,7 +30,8 @@ __global__ void __launch_bounds__(128) k_update_clomp(IterArgs a, ClArgs c, int 
             if (b < a.B) select_one<MCH>(a, b);
         }
         __syncwarp();      // Gram rows and support written by other lanes
-        fit_unit<KT, LPS>(a, c, u, sh_s[w], sh_c1, sh_c2, staged);
+        if constexpr (KT <= 32) fit_grid<KT>(a, c, u, c.tau0, sh_s[w], tab);
+        else fit_unit<KT, LPS>(a, c, u, c.tau0, sh_s[w], tab);
         __syncwarp();      // coefficients and n_iter written by other lanes
         for (int sb = 0; sb < P; ++sb) {
             const int b = u * P + sb;
