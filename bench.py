@@ -292,9 +292,12 @@ def main():
         for name, algo, prec, form in [("omp_fp32", "omp", "fp32", "gram"), ("omp_bf16", "omp", "bf16", "gram"),
                                        ("clomp_fp32_gram", "clomp", "fp32", "gram"),
                                        ("clomp_bf16_gather", "clomp", "bf16", "gather"),
+                                       ("clomp_bf16_gram_per_iteration", "clomp", "bf16", "gram"),
                                        ("clomp_bf16_gram_unfused", "clomp", "bf16", "gram")]:
             fn = make_step(algo, prec, form)
             plan.set_option(cs.OPT_FUSE_UPDATE, 0 if name.endswith("unfused") else 1)
+            # the per-iteration kernels instead of the persistent solve
+            plan.set_option(cs.OPT_PERSIST, 0 if name.startswith("clomp_bf16_gram_") else 1)
             m_, _, _ = timed(fn, ksteps, 3)
             plan.set_profiling(True)
             plan.profile(reset=True)
@@ -306,6 +309,7 @@ def main():
             compare[name] = {"ms_per_step": m_, "signals_per_s": ws * p.B / (m_ / 1e3),
                              "phase_ms_per_step": {k: round(v[1] / 3, 4) for k, v in ph.items()}}
         plan.set_option(cs.OPT_FUSE_UPDATE, 1)
+        plan.set_option(cs.OPT_PERSIST, 1)
         compare["clomp_headline"] = {"ms_per_step": ms, "signals_per_s": value}
         compare["clomp_over_omp_fp32"] = value / compare["omp_fp32"]["signals_per_s"]
 
@@ -361,6 +365,13 @@ def main():
     B = p.B
     roof_corr = None
     n_corr, t_corr = phases["correlation"]
+    corr_src = "headline"
+    if not n_corr and "clomp_bf16_gram_per_iteration" in compare:
+        # the persistent solve has no separate correlation launch: take the
+        # tensor-core correlation kernel of the per-iteration form
+        n_corr = iters
+        t_corr = compare["clomp_bf16_gram_per_iteration"]["phase_ms_per_step"]["correlation"]
+        corr_src = "per-iteration bf16 CLOMP (k_corr_tc)"
     if n_corr:
         flops = 2.0 * p.m * p.n * B                    # per launch: every signal is live for all k iterations
         avg_s = t_corr / n_corr / 1e3
@@ -368,7 +379,7 @@ def main():
         if args.prec == "bf16":
             pk = peaks["bf16_tflops_sustained"]
             roof_corr = {"bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
-                         "peak_source": f"bf16_tflops_sustained ({src})"}
+                         "peak_source": f"bf16_tflops_sustained ({src})", "kernel": corr_src}
         else:
             pk = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
             roof_corr = {"bound": "alu", "achieved": ach, "peak": pk, "unit": "TFLOP/s", "frac": ach / pk,
@@ -381,9 +392,13 @@ def main():
     sum_t2 = iters * (iters + 1) * (2 * iters + 1) / 6.0
     fp32_peak = 152 * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     fit_flops = B * CL["steps"] * (2 * sum_t2 + 10 * sum_t)
+    resid_flops = B * 2.0 * p.m * sum_t
     work = {
         # Gram form: g = G s - b per Adam step (2 t^2 flops) + Adam update (~10 t flops)
         "fit": ("alu", fit_flops, fp32_peak, "TFLOP/s"),
+        # persistent solve: its CUDA-core arithmetic (fit + residual); the
+        # correlation's tensor work is reported separately below
+        "persist": ("alu", fit_flops + resid_flops, fp32_peak, "TFLOP/s"),
         # fused selection + fit + residual: its arithmetic is the fit's
         "update": ("alu", fit_flops, fp32_peak, "TFLOP/s"),
         # residual: read t columns of A (4m bytes each), y, write r (fp32 + bf16)
@@ -396,12 +411,18 @@ def main():
         n_, t_ = phases[ph]
         if not n_ or t_ <= 0:
             continue
-        nsolves = n_ / iters
+        nsolves = n_ if ph == "persist" else n_ / iters   # one persistent launch per solve
         ach = amount * nsolves / (t_ / 1e3) / (1e12 if unit == "TFLOP/s" else 1e9)
         roofs[ph] = {"bound": bound, "achieved": ach, "peak": pk, "unit": unit, "frac": ach / pk,
                      "traffic": None}
     roofline = dict(roofs[dom]) if roofs.get(dom) else roof_corr
     roofline["kernel_phase"] = dom
+    if dom == "persist":
+        n_, t_ = phases["persist"]
+        tflops = 2.0 * p.m * p.n * B * iters * (n_ / 1) / (t_ / 1e3) / 1e12
+        pk = peaks["bf16_tflops_sustained"]
+        roofline["tensor_work"] = {"achieved": tflops, "peak": pk, "unit": "TFLOP/s", "frac": tflops / pk,
+                                   "note": "bf16 correlation flops of the solve over the whole persistent kernel"}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",

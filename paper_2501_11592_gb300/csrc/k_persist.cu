@@ -4,13 +4,15 @@
 // One CTA per SM owns a block of up to 27 signals and runs every iteration of
 // them on chip, so no iteration boundary costs a launch, a ramp-up or a tail:
 //   * the bf16 atom tiles A16[128 atoms][64] stream by TMA through an 8-deep
-//     ring, one stage per signal warp 1..8 (the copy rate of this machine
-//     grows with the number of issuing warps, not with the ring depth); A is
-//     the same in every iteration, so each pass's first tiles are prefetched
-//     while the previous pass ends;
+//     ring, two stages for each of signal warps 1..4 (the copy rate of this
+//     machine grows with the number of issuing warps, not with the ring
+//     depth); A is the same in every iteration, so each pass's first tiles
+//     are prefetched while the previous pass ends;
 //   * one thread of warp 0 issues tcgen05.mma with M = 128 atoms, N = 32
 //     signal columns, K = 16: the correlation c = A^T r of the block's
-//     signals lands in tensor memory, 32 fp32 columns per atom tile;
+//     signals lands in tensor memory, 32 fp32 columns per atom tile, each
+//     tile committed to its own mbarrier so that the epilogue starts on the
+//     first tiles while the later ones are still streaming;
 //   * warps 1..27 (one per signal) read the accumulators in two passes:
 //     pass 1 finds each signal's largest masked bf16 |c| (a packed
 //     value/index key, transposed max-reduction per 32 atoms), pass 2 lists
@@ -44,6 +46,7 @@ constexpr int PS_TM = 128;                   // atoms per UMMA M tile (TMEM lane
 constexpr int PS_KCH = 64;                   // bf16 per 128-byte swizzled row
 constexpr int PS_TILE = PS_TM * PS_KCH * 2;  // 16 KiB atom tile
 constexpr int PS_ST = 8;                     // atom-tile ring depth
+constexpr int PS_PROD = 4;                   // producer warps (PS_ST / PS_PROD stages each)
 constexpr int PS_BSTRIDE = PS_N * 128;       // bytes per 64-element K block of the B operand
 constexpr int PS_MAXKB = 4;                  // m <= 256
 constexpr int PS_CAP = 32;                   // candidates held per signal
@@ -167,7 +170,7 @@ template <int MCH>
 __global__ void __launch_bounds__(PS_THREADS, 1)
 k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t full_bar[PS_ST], empty_bar[PS_ST], rready_bar, acc_bar, fin_bar;
+    __shared__ __align__(8) uint64_t full_bar[PS_ST], empty_bar[PS_ST], chunk_bar[PS_MAXCH], rready_bar, fin_bar;
     __shared__ uint32_t tmem_slot;
     __shared__ uint32_t live_bits[2];
     __shared__ volatile int abort_flag;
@@ -193,7 +196,7 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
             mbar_init(&empty_bar[i], 1);
         }
         mbar_init(&rready_bar, PS_NS);
-        mbar_init(&acc_bar, 1);
+        for (int i = 0; i < PS_MAXCH; ++i) mbar_init(&chunk_bar[i], 1);
         mbar_init(&fin_bar, 1);
         abort_flag = 0;
         live_bits[0] = live_bits[1] = 0u;
@@ -254,8 +257,8 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                         umma_commit(&empty_bar[st]);   // frees the ring slot once these MMAs are done
                         ++gc;
                     }
+                    if (ok) umma_commit(&chunk_bar[c]);   // this atom tile's accumulators are complete
                 }
-                if (ok) umma_commit(&acc_bar);     // the block's accumulators are complete
             }
             if (!ok) abort_flag = 1;
             // every MMA issued so far completes before teardown
@@ -270,12 +273,11 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
         const int qidx = (warp - qfirst) >> 2;
         const int qcnt = (PS_WARPS - qfirst + 3) >> 2;   // signal warps of the quadrant
         const float cert = (0x1p-7f + 0x1p-16f + (float)a.m * (0x1p-22f + 0x1p-23f)) * (*a.colnorm_max) * 1.01f;
-        uint32_t accp = 0, rnd = 0;
+        uint32_t rnd = 0;
         bool aborted = false;
-        // producer of ring stage `st` (signal warps 1..PS_ST): tiles st, st+ST, ...
-        const bool producer = (s < PS_ST) && lane == 0;
-        const int st = s;
-        uint32_t pg = (uint32_t)st;   // next tile this producer issues
+        // producer s (signal warps 1..PS_PROD): tiles s, s + PS_PROD, ...
+        const bool producer = (s < PS_PROD) && lane == 0;
+        uint32_t pg = (uint32_t)s;   // next tile this producer issues
         for (int slot = 0; slot < p.nslots && !aborted; ++slot) {
             const int blk = blockIdx.x + slot * gridDim.x;
             const bool have = blk < p.nblk;
@@ -311,7 +313,8 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                     // ones: tile g reuses the slot of tile g - ST, which this
                     // or the previous pass consumes (g < (pass+1) per_pass + ST)
                     const uint32_t lim = min(total, (rnd + 1u) * (uint32_t)per_pass + (uint32_t)PS_ST);
-                    for (; pg < lim; pg += PS_ST) {
+                    for (; pg < lim; pg += PS_PROD) {
+                        const int st = pg % PS_ST;
                         if (pg >= (uint32_t)PS_ST) {
                             const int we = wait_or_flag(&empty_bar[st], ((pg / PS_ST) & 1u) ^ 1u, &abort_flag);
                             if (we <= 0) {
@@ -329,23 +332,38 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                     }
                 }
                 __syncwarp();
-
-                const int w = wait_or_flag(&acc_bar, accp & 1u, &abort_flag);
-                ++accp;
-                tc_fence_after();
-                if (w < 0 && lane == 0) {
-                    abort_flag = 1;
-                    atomicOr(errflag, 16u);
+                if (!any) {
+                    // nothing to read this pass; still wait for it (its last
+                    // tile's commit covers every MMA of the pass), so that no
+                    // warp arrives for the next pass before the MMA issuer has
+                    // seen this one
+                    const int w = wait_or_flag(&chunk_bar[p.nchunk - 1], rnd & 1u, &abort_flag);
+                    if (w < 0 && lane == 0) {
+                        abort_flag = 1;
+                        atomicOr(errflag, 16u);
+                    }
+                    if (named_sync_or(w <= 0)) {
+                        aborted = true;
+                        break;
+                    }
+                    continue;
                 }
-                if (named_sync_or(w <= 0)) {
-                    aborted = true;
-                    break;
-                }
-                if (!any) continue;
                 const uint32_t lb = live_bits[rnd & 1u];
 
-                // pass 1: per 32 atoms x 32 signals, the largest masked key per signal
-                for (int c = qidx; c < p.nchunk; c += qcnt) {
+                // pass 1: per 32 atoms x 32 signals, the largest masked key per
+                // signal, each atom tile as soon as its MMAs have completed
+                bool failed = false;
+                for (int c = qidx; c < p.nchunk && !failed; c += qcnt) {
+                    const int w = wait_or_flag(&chunk_bar[c], rnd & 1u, &abort_flag);
+                    if (w <= 0) {
+                        if (w < 0 && lane == 0) {
+                            abort_flag = 1;
+                            atomicOr(errflag, 16u);
+                        }
+                        failed = true;
+                        break;
+                    }
+                    tc_fence_after();
                     uint32_t k[32];
                     tmem_ld32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(c * PS_N), k);
                     tmem_ld_wait();
@@ -358,7 +376,10 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                     warp_max_scatter32(k);
                     part[(c * 4 + q) * 32 + lane] = k[0];
                 }
-                named_sync();
+                if (named_sync_or(failed)) {
+                    aborted = true;
+                    break;
+                }
                 // threshold of my signal: largest bf16 |c| minus 2 delta
                 {
                     uint32_t km = 0u;
@@ -486,12 +507,11 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                 }
             }
         }
-        // the last copy of my stage (the only one that can still be in
-        // flight after an abort) lands before the CTA exits
-        if (producer && pg >= (uint32_t)PS_ST) {
-            const uint32_t last = pg - PS_ST;
-            if (!mbar_wait(&full_bar[st], (last / PS_ST) & 1u)) atomicOr(errflag, 4u);
-        }
+        // the last copies of my stages (the only ones that can still be in
+        // flight after an abort) land before the CTA exits
+        if (producer)
+            for (uint32_t g2 = (pg >= (uint32_t)PS_ST) ? pg - PS_ST : (uint32_t)s; g2 < pg; g2 += PS_PROD)
+                if (!mbar_wait(&full_bar[g2 % PS_ST], (g2 / PS_ST) & 1u)) atomicOr(errflag, 4u);
     }
 
     // ---------------------------------------------------------- teardown --
