@@ -418,6 +418,7 @@ def main():
     roofline = dict(roofs[dom]) if roofs.get(dom) else roof_corr
     roofline["kernel_phase"] = dom
     if dom == "persist":
+        roofline["traffic"] = recorded_traffic("persist_bf16", kernel_sha("paper_2501_11592_gb300/csrc/k_persist.cu"))
         n_, t_ = phases["persist"]
         tflops = 2.0 * p.m * p.n * B * iters * (n_ / 1) / (t_ / 1e3) / 1e12
         pk = peaks["bf16_tflops_sustained"]
