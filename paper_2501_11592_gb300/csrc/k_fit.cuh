@@ -165,10 +165,11 @@ __device__ __forceinline__ bool grid_owner(int j) {
 // the four lanes of a row block finish the row sums with shuffles.  Each
 // coordinate q = RB*i + grid_row(j) is owned (Adam state, update) by one
 // lane.  Coordinates beyond the support have zero rows, zero b and zero
-// state, so the update leaves them at exactly zero.
+// state, so the update leaves them at exactly zero.  coef_copy (optional)
+// receives the coefficients as well.
 template <int KT>
 __device__ __forceinline__ void fit_grid(const IterArgs& a, const ClArgs& c, const int b, const int tau0,
-                                         float* sh_s_w, const float2* tab) {
+                                         float* sh_s_w, const float2* tab, float* coef_copy = nullptr) {
     static_assert(KT % 8 == 0 && KT >= 8 && KT <= 32, "fit_grid: KT in {8, 16, 24, 32}");
     constexpr int RB = KT / 8, CB = KT / 4, CP = CB / 2;
     const int lane = threadIdx.x & 31, i = lane >> 2, j = lane & 3;
@@ -237,6 +238,7 @@ __device__ __forceinline__ void fit_grid(const IterArgs& a, const ClArgs& c, con
     }
     if (on) {
         a.coef[(size_t)b * a.k + q] = s;
+        if (coef_copy) coef_copy[q] = s;
         a.am[(size_t)b * K + q] = mo;
         a.av[(size_t)b * K + q] = ve;
     }

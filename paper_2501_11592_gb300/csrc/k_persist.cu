@@ -64,7 +64,9 @@ constexpr int PS_OFF_THETA = PS_OFF_PART + PS_MAXCH * 4 * 32 * 4;
 constexpr int PS_OFF_CCOUNT = PS_OFF_THETA + 32 * 4;
 constexpr int PS_OFF_CLIST = PS_OFF_CCOUNT + 32 * 4;
 constexpr int PS_OFF_SVEC = PS_OFF_CLIST + 32 * PS_CAP * 4;
-constexpr int PS_OFF_TAB = PS_OFF_SVEC + PS_NS * PS_KT * 4;
+constexpr int PS_OFF_SUP = PS_OFF_SVEC + PS_NS * PS_KT * 4;     // support of each signal
+constexpr int PS_OFF_CF = PS_OFF_SUP + PS_NS * PS_KT * 4;       // its coefficients
+constexpr int PS_OFF_TAB = PS_OFF_CF + PS_NS * PS_KT * 4;
 constexpr int PS_SMEM = PS_OFF_TAB + PS_TAB * 8 + 1024;
 
 struct PsArgs {
@@ -157,12 +159,41 @@ __device__ __forceinline__ void put_b_row(uint8_t* sB, int s, int mp, const floa
 }
 
 __device__ __forceinline__ void fit_dispatch(const IterArgs& a, const ClArgs& c, int b, int t, int tau0,
-                                             float* sv, const float2* tab) {
+                                             float* sv, const float2* tab, float* coef_copy) {
     switch (round_up(t + 1, 8)) {
-        case 8: fit_grid<8>(a, c, b, tau0, sv, tab); break;
-        case 16: fit_grid<16>(a, c, b, tau0, sv, tab); break;
-        case 24: fit_grid<24>(a, c, b, tau0, sv, tab); break;
-        default: fit_grid<32>(a, c, b, tau0, sv, tab); break;
+        case 8: fit_grid<8>(a, c, b, tau0, sv, tab, coef_copy); break;
+        case 16: fit_grid<16>(a, c, b, tau0, sv, tab, coef_copy); break;
+        case 24: fit_grid<24>(a, c, b, tau0, sv, tab, coef_copy); break;
+        default: fit_grid<32>(a, c, b, tau0, sv, tab, coef_copy); break;
+    }
+}
+
+// Support append of atom bj as the (t+1)-th atom of signal b (one warp; the
+// same arithmetic as the per-iteration append_atom): support entry, Gram row
+// and column from A^T A, A_S^T y entry.  The support sits in shared memory,
+// so the Gram-row gathers leave together with the new column's loads.
+template <int MCH>
+__device__ __forceinline__ void append_ps(const IterArgs& a, const int b, const int t, const int bj,
+                                          const float4 (&y)[MCH], const int* sup) {
+    const int lane = threadIdx.x & 31;
+    const float* garow = a.GA + (size_t)bj * a.n;
+    const float g = (lane < t) ? garow[sup[lane]] : 0.f;
+    const float gdd = garow[bj];
+    float4 aj[MCH];
+    load_row<MCH>(a.A32 + (size_t)bj * a.mp, a.mp, aj);
+    float by = 0.f;
+#pragma unroll
+    for (int c = 0; c < MCH; ++c) by += dot4(aj[c], y[c]);
+    by = warp_sum(by);
+    float* G = a.G + (size_t)b * a.kmax * a.kmax;
+    if (lane < t) {
+        G[(size_t)t * a.kmax + lane] = g;
+        G[(size_t)lane * a.kmax + t] = g;
+    }
+    if (lane == 0) {
+        a.support[(size_t)b * a.k + t] = bj;
+        G[(size_t)t * a.kmax + t] = gdd;
+        a.bvec[(size_t)b * a.kmax + t] = by;
     }
 }
 
@@ -188,6 +219,8 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
     int* clist = reinterpret_cast<int*>(base + PS_OFF_CLIST);
     float* svec = reinterpret_cast<float*>(base + PS_OFF_SVEC);
     float2* tabs = reinterpret_cast<float2*>(base + PS_OFF_TAB);
+    int* sup_s = reinterpret_cast<int*>(base + PS_OFF_SUP);
+    float* cf_s = reinterpret_cast<float*>(base + PS_OFF_CF);
     unsigned* errflag = a.counters + 1;
 
     if (tid == 0) {
@@ -286,6 +319,7 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
             bool live = false;
             int t = 0;
             float rho = 0.f;
+            float4 r[MCH];   // the residual, kept in registers from one iteration to the next
             named_sync();   // every warp is done with the previous block's selected-atom bits
             for (int i = tid - 32; i < p.nchunk * PS_TM; i += PS_SIGTHREADS) mask_t[i] = 0u;
             {
@@ -298,6 +332,8 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                     rho = a.res_norm[b];
                 }
                 put_b_row<MCH>(sB, s, a.mp, y, !live);
+#pragma unroll
+                for (int c2 = 0; c2 < MCH; ++c2) r[c2] = y[c2];
             }
             // k rounds per block whatever the signals do (a fixed schedule);
             // rounds without a live signal skip the epilogue
@@ -421,8 +457,6 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
 
                 if (live) {
                     // ---- selection: float32 re-score of the listed atoms
-                    float4 r[MCH];
-                    load_row<MCH>(a.R32 + (size_t)b * a.mp, a.mp, r);
                     const int cnt = ccount[s];
                     float bv = -1.f;
                     int bj = -1;
@@ -474,30 +508,30 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                         live = false;
                         if (lane == 0) a.status[b] = CS_SIG_MAX_ITER;
                     } else {
-                        if (lane == 0) atomicOr(&mask_t[bj], 1u << s);
+                        if (lane == 0) {
+                            atomicOr(&mask_t[bj], 1u << s);
+                            sup_s[s * PS_KT + t] = bj;
+                        }
                         float4 y[MCH];
                         load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, y);
-                        append_atom<MCH>(a, b, t, bj, y);
+                        append_ps<MCH>(a, b, t, bj, y, sup_s + s * PS_KT);
                         __syncwarp();
                         // ---- Gram-form Adam fit on the t+1 support atoms
                         const int tau0 = p.c.reset ? 0 : t * p.c.steps;
-                        fit_dispatch(a, p.c, b, t, tau0, svec + s * PS_KT, (p.staged ? tabs : p.c.tab) + tau0);
+                        fit_dispatch(a, p.c, b, t, tau0, svec + s * PS_KT, (p.staged ? tabs : p.c.tab) + tau0,
+                                     cf_s + s * PS_KT);
                         __syncwarp();
                         ++t;
                         // ---- residual, stop test, next B operand row
                         r[0] = y[0];
 #pragma unroll
                         for (int c2 = 1; c2 < MCH; ++c2) r[c2] = y[c2];
-                        resid_vector<MCH>(a, b, t, r);
+                        resid_vector_from<MCH>(a, t, r, sup_s + s * PS_KT, cf_s + s * PS_KT);
                         float ss = 0.f;
-                        float4* R = reinterpret_cast<float4*>(a.R32 + (size_t)b * a.mp);
 #pragma unroll
                         for (int c2 = 0; c2 < MCH; ++c2) {
                             const int i4 = c2 * 32 + lane;
-                            if (i4 * 4 < a.mp) {
-                                R[i4] = r[c2];
-                                ss += dot4(r[c2], r[c2]);
-                            }
+                            if (i4 * 4 < a.mp) ss += dot4(r[c2], r[c2]);
                         }
                         rho = sqrtf(warp_sum(ss));
                         if (lane == 0) stop_test(a, b, t, rho);

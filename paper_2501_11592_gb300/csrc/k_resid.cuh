@@ -9,13 +9,12 @@ namespace cs {
 namespace {
 
 // ------------------------------------------------ residual + stop test -----
-// r <- r - A_S s_S for the t support atoms of signal b (one warp; r enters
-// holding y, row-sliced like load_row).
+// r <- r - A_S s_S for the t support atoms `sup` with coefficients `x` (one
+// warp; r enters holding y, row-sliced like load_row).
 template <int MCH>
-__device__ __forceinline__ void resid_vector(const IterArgs& a, const int b, const int t, float4 (&r)[MCH]) {
+__device__ __forceinline__ void resid_vector_from(const IterArgs& a, const int t, float4 (&r)[MCH],
+                                                  const int* sup, const float* x) {
     const int lane = threadIdx.x & 31;
-    const int* sup = a.support + (size_t)b * a.k;
-    const float* x = a.coef + (size_t)b * a.k;
     // Columns in selection order (the oracle's order).  Lane q loads support
     // index and coefficient q once; the indices are then broadcast by
     // shuffles, so up to 4 columns' loads are in flight before their FMAs.
@@ -48,6 +47,12 @@ __device__ __forceinline__ void resid_vector(const IterArgs& a, const int b, con
                 }
         }
     }
+}
+
+// r <- r - A_S s_S for signal b, support and coefficients from its outputs.
+template <int MCH>
+__device__ __forceinline__ void resid_vector(const IterArgs& a, const int b, const int t, float4 (&r)[MCH]) {
+    resid_vector_from<MCH>(a, t, r, a.support + (size_t)b * a.k, a.coef + (size_t)b * a.k);
 }
 
 // Stopping test of Eq. 2 after t atoms (lane 0 of the signal's warp).
