@@ -77,7 +77,8 @@ struct PsArgs {
     int nslots;      // blocks per CTA (the last slot may be empty for some CTAs)
     int kb;          // K blocks of 64 (mh / 64)
     int nchunk;      // atom tiles, ceil(n / 128)
-    int tmem_cols;   // power of two >= 32 * nchunk
+    int nres;        // leading atom tiles kept in tensor memory as the MMA A operand
+    int tmem_cols;   // tensor-memory columns allocated (512)
     int staged;      // Adam table staged in shared memory
 };
 
@@ -134,6 +135,30 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
           "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]),
           "=r"(r[15])
         : "r"(taddr));
+}
+
+// tcgen05.mma with the A operand (M = 128 rows in the 128 lanes, K packed two
+// bf16 per 32-bit column) in tensor memory.
+__device__ __forceinline__ void umma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                             uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st32(uint32_t taddr, const uint32_t (&r)[32]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], "
+        "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16, "
+        "%17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31, %32};"
+        ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+          "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15]),
+          "r"(r[16]), "r"(r[17]), "r"(r[18]), "r"(r[19]), "r"(r[20]), "r"(r[21]), "r"(r[22]), "r"(r[23]),
+          "r"(r[24]), "r"(r[25]), "r"(r[26]), "r"(r[27]), "r"(r[28]), "r"(r[29]), "r"(r[30]), "r"(r[31])
+        : "memory");
 }
 
 // Residual row of signal s (row-sliced like load_row) as bf16 into the
@@ -250,11 +275,44 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
     if (p.staged)
         for (int i = tid; i < p.c.tab_len; i += PS_THREADS) tabs[i] = p.c.tab[i];
     tc_fence_before();
-    __syncthreads();
+    __syncthreads();   // the allocation is visible
     tc_fence_after();
     const uint32_t tmem = tmem_slot;
+    // Leading atom tiles, resident for the whole solve: tile (c, kk) of row
+    // 128c + lane-of-quadrant sits in columns 32 (nchunk + c kb + kk) ...,
+    // its 64 bf16 packed in pairs.  Work units (tile, lane quadrant) go to
+    // the warps of that quadrant.
+    {
+        const int q = warp & 3;
+        const int wq = warp >> 2, nwq = (PS_WARPS - q + 3) >> 2;   // warps of quadrant q
+        const int row = 32 * q + lane;
+        for (int u = wq; u < p.nres * p.kb; u += nwq) {
+            const int c = u / p.kb, kk = u % p.kb;
+            const int atom = c * PS_TM + row;
+            uint32_t v[32];
+            if (atom < a.n) {
+                const uint4* src = reinterpret_cast<const uint4*>(a.A16 + (size_t)atom * a.mh + kk * PS_KCH);
+#pragma unroll
+                for (int i = 0; i < 8; ++i) {
+                    const uint4 w4 = src[i];
+                    v[4 * i] = w4.x;
+                    v[4 * i + 1] = w4.y;
+                    v[4 * i + 2] = w4.z;
+                    v[4 * i + 3] = w4.w;
+                }
+            } else {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) v[i] = 0u;
+            }
+            tmem_st32(tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(32 * (p.nchunk + u)), v);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
     const int passes = p.nslots * a.iters;
-    const int per_pass = p.nchunk * p.kb;                     // atom tiles per pass
+    const int per_pass = (p.nchunk - p.nres) * p.kb;          // streamed atom tiles per pass
     const uint32_t total = (uint32_t)passes * (uint32_t)per_pass;
 
     if (warp == 0) {
@@ -271,7 +329,19 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                     break;
                 }
                 tc_fence_after();
-                for (int c = 0; c < p.nchunk && ok; ++c) {
+                for (int c = 0; c < p.nres; ++c) {
+                    // resident tiles: A from tensor memory, no wait
+                    for (int kk = 0; kk < p.kb; ++kk) {
+                        const uint32_t ta = tmem + (uint32_t)(32 * (p.nchunk + c * p.kb + kk));
+                        const uint64_t db = smem_desc_sw128(smem_u32(sB + kk * PS_BSTRIDE));
+#pragma unroll
+                        for (int k16 = 0; k16 < PS_KCH / 16; ++k16)
+                            umma_bf16_ta(tmem + (uint32_t)(c * PS_N), ta + (uint32_t)(8 * k16),
+                                         db + (uint64_t)(2 * k16), idesc, (kk | k16) != 0);
+                    }
+                    umma_commit(&chunk_bar[c]);
+                }
+                for (int c = p.nres; c < p.nchunk && ok; ++c) {
                     for (int kk = 0; kk < p.kb; ++kk) {
                         const int st = gc % PS_ST;
                         const int w2 = wait_or_flag(&full_bar[st], (gc / PS_ST) & 1u, &abort_flag);
@@ -361,7 +431,7 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                                 break;
                             }
                         }
-                        const int tile = (int)(pg % (uint32_t)per_pass);
+                        const int tile = (int)(pg % (uint32_t)per_pass) + p.nres * p.kb;
                         mbar_arrive_expect_tx(&full_bar[st], PS_TILE);
                         tma_load_2d(ring + st * PS_TILE, &mapA, &full_bar[st], (tile % p.kb) * PS_KCH,
                                     (tile / p.kb) * PS_TM);
@@ -595,8 +665,10 @@ cudaError_t launch_mch(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
     p.c = c;
     p.kb = a.mh / PS_KCH;
     p.nchunk = ceil_div(a.n, PS_TM);
-    p.tmem_cols = 32;
-    while (p.tmem_cols < p.nchunk * PS_N) p.tmem_cols *= 2;
+    // tensor memory: the accumulators (32 columns per atom tile), and as many
+    // whole leading atom tiles as fit in the rest of the 512 columns
+    p.tmem_cols = 512;
+    p.nres = std::min(p.nchunk, (512 - p.nchunk * PS_N) / (32 * p.kb));
     p.staged = c.tab_len <= PS_TAB ? 1 : 0;
     // one CTA per SM, blocks of <= PS_NS signals
     const int nsm = sm_count();
