@@ -137,6 +137,40 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
         : "r"(taddr));
 }
 
+// The four K = 16 MMAs of one 64-element K block (descriptors advance 32
+// bytes per step inside the 128-byte swizzled rows); `first` clears the
+// accumulator.
+__device__ __forceinline__ void umma_kblock(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                           uint32_t first) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.eq.u32 p, %4, 0;\n\t"
+        "setp.eq.u32 q, %4, %4;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %5, %6, %3, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %7, %8, %3, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %9, %10, %3, q;\n\t}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(first), "l"(adesc + 2), "l"(bdesc + 2),
+          "l"(adesc + 4), "l"(bdesc + 4), "l"(adesc + 6), "l"(bdesc + 6)
+        : "memory");
+}
+
+// Same with the A operand in tensor memory (8 columns per K = 16 step).
+__device__ __forceinline__ void umma_kblock_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
+                                              uint32_t first) {
+    asm volatile(
+        "{\n\t.reg .pred p, q;\n\t"
+        "setp.eq.u32 p, %4, 0;\n\t"
+        "setp.eq.u32 q, %4, %4;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%5], %6, %3, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%7], %8, %3, q;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], [%9], %10, %3, q;\n\t}\n"
+        ::"r"(d_tmem), "r"(a_tmem), "l"(bdesc), "r"(idesc), "r"(first), "r"(a_tmem + 8), "l"(bdesc + 2),
+          "r"(a_tmem + 16), "l"(bdesc + 4), "r"(a_tmem + 24), "l"(bdesc + 6)
+        : "memory");
+}
+
 // tcgen05.mma with the A operand (M = 128 rows in the 128 lanes, K packed two
 // bf16 per 32-bit column) in tensor memory.
 __device__ __forceinline__ void umma_bf16_ta(uint32_t d_tmem, uint32_t a_tmem, uint64_t bdesc, uint32_t idesc,
@@ -222,9 +256,10 @@ __device__ __forceinline__ void append_ps(const IterArgs& a, const int b, const 
     }
 }
 
-template <int MCH>
+template <int KB>
 __global__ void __launch_bounds__(PS_THREADS, 1)
 k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
+    constexpr int MCH = (KB + 1) / 2;   // 128-row chunks of the fp32 vectors (m <= 64 KB)
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t full_bar[PS_ST], empty_bar[PS_ST], chunk_bar[PS_MAXCH], rready_bar, fin_bar;
     __shared__ uint32_t tmem_slot;
@@ -286,8 +321,8 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
         const int q = warp & 3;
         const int wq = warp >> 2, nwq = (PS_WARPS - q + 3) >> 2;   // warps of quadrant q
         const int row = 32 * q + lane;
-        for (int u = wq; u < p.nres * p.kb; u += nwq) {
-            const int c = u / p.kb, kk = u % p.kb;
+        for (int u = wq; u < p.nres * KB; u += nwq) {
+            const int c = u / KB, kk = u % KB;
             const int atom = c * PS_TM + row;
             uint32_t v[32];
             if (atom < a.n) {
@@ -312,13 +347,17 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
     __syncthreads();
     tc_fence_after();
     const int passes = p.nslots * a.iters;
-    const int per_pass = (p.nchunk - p.nres) * p.kb;          // streamed atom tiles per pass
+    const int per_pass = (p.nchunk - p.nres) * KB;            // streamed atom tiles per pass
     const uint32_t total = (uint32_t)passes * (uint32_t)per_pass;
 
     if (warp == 0) {
         // ------------------------------------------------ MMA issuer ------
         if (lane == 0) {
             constexpr uint32_t idesc = make_idesc(PS_TM, PS_N);
+            uint64_t db[KB];   // B operand (the block's residuals), one descriptor per K block
+#pragma unroll
+            for (int kk = 0; kk < KB; ++kk) db[kk] = smem_desc_sw128(smem_u32(sB + kk * PS_BSTRIDE));
+            const uint64_t da0 = smem_desc_sw128(smem_u32(ring));   // ring slot st: + st * PS_TILE / 16
             uint32_t gc = 0;   // tiles consumed
             bool ok = true;
             for (int pass = 0; pass < passes && ok; ++pass) {
@@ -331,32 +370,28 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                 tc_fence_after();
                 for (int c = 0; c < p.nres; ++c) {
                     // resident tiles: A from tensor memory, no wait
-                    for (int kk = 0; kk < p.kb; ++kk) {
-                        const uint32_t ta = tmem + (uint32_t)(32 * (p.nchunk + c * p.kb + kk));
-                        const uint64_t db = smem_desc_sw128(smem_u32(sB + kk * PS_BSTRIDE));
+                    const uint32_t ta = tmem + (uint32_t)(32 * (p.nchunk + c * KB));
 #pragma unroll
-                        for (int k16 = 0; k16 < PS_KCH / 16; ++k16)
-                            umma_bf16_ta(tmem + (uint32_t)(c * PS_N), ta + (uint32_t)(8 * k16),
-                                         db + (uint64_t)(2 * k16), idesc, (kk | k16) != 0);
-                    }
+                    for (int kk = 0; kk < KB; ++kk)
+                        umma_kblock_ta(tmem + (uint32_t)(c * PS_N), ta + (uint32_t)(32 * kk), db[kk], idesc,
+                                       kk == 0 ? 1u : 0u);
                     umma_commit(&chunk_bar[c]);
                 }
                 for (int c = p.nres; c < p.nchunk && ok; ++c) {
-                    for (int kk = 0; kk < p.kb; ++kk) {
+#pragma unroll
+                    for (int kk = 0; kk < KB; ++kk) {
                         const int st = gc % PS_ST;
-                        const int w2 = wait_or_flag(&full_bar[st], (gc / PS_ST) & 1u, &abort_flag);
-                        if (w2 <= 0) {
-                            if (w2 < 0) atomicOr(errflag, 8u);
-                            ok = false;
-                            break;
+                        if (!mbar_try_wait(&full_bar[st], (gc / PS_ST) & 1u)) {
+                            const int w2 = wait_or_flag(&full_bar[st], (gc / PS_ST) & 1u, &abort_flag);
+                            if (w2 <= 0) {
+                                if (w2 < 0) atomicOr(errflag, 8u);
+                                ok = false;
+                                break;
+                            }
                         }
                         tc_fence_after();
-                        const uint64_t da = smem_desc_sw128(smem_u32(ring + st * PS_TILE));
-                        const uint64_t db = smem_desc_sw128(smem_u32(sB + kk * PS_BSTRIDE));
-#pragma unroll
-                        for (int k16 = 0; k16 < PS_KCH / 16; ++k16)
-                            umma_bf16(tmem + (uint32_t)(c * PS_N), da + (uint64_t)(2 * k16),
-                                      db + (uint64_t)(2 * k16), idesc, (kk | k16) != 0);
+                        umma_kblock(tmem + (uint32_t)(c * PS_N), da0 + (uint64_t)(st * (PS_TILE >> 4)), db[kk], idesc,
+                                    kk == 0 ? 1u : 0u);
                         umma_commit(&empty_bar[st]);   // frees the ring slot once these MMAs are done
                         ++gc;
                     }
@@ -431,10 +466,10 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                                 break;
                             }
                         }
-                        const int tile = (int)(pg % (uint32_t)per_pass) + p.nres * p.kb;
+                        const int tile = (int)(pg % (uint32_t)per_pass) + p.nres * KB;
                         mbar_arrive_expect_tx(&full_bar[st], PS_TILE);
-                        tma_load_2d(ring + st * PS_TILE, &mapA, &full_bar[st], (tile % p.kb) * PS_KCH,
-                                    (tile / p.kb) * PS_TM);
+                        tma_load_2d(ring + st * PS_TILE, &mapA, &full_bar[st], (tile % KB) * PS_KCH,
+                                    (tile / KB) * PS_TM);
                     }
                 }
                 __syncwarp();
@@ -649,16 +684,16 @@ bool clomp_persist_supported(const IterArgs& a, const ClArgs& c) {
 
 namespace {
 
-template <int MCH>
+template <int KB>
 cudaError_t configure_once() {
     static const cudaError_t st =
-        cudaFuncSetAttribute(k_clomp_persist<MCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, PS_SMEM);
+        cudaFuncSetAttribute(k_clomp_persist<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, PS_SMEM);
     return st;
 }
 
-template <int MCH>
-cudaError_t launch_mch(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
-    cudaError_t e = configure_once<MCH>();
+template <int KB>
+cudaError_t launch_kb(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
+    cudaError_t e = configure_once<KB>();
     if (e != cudaSuccess) return e;
     PsArgs p{};
     p.a = a;
@@ -679,7 +714,7 @@ cudaError_t launch_mch(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
     p.nslots = ceil_div(p.nblk, grid);
     CUtensorMap mA;
     if (!make_tma_map_bf16(&mA, a.A16, a.mh, a.n, (size_t)a.mh * 2, PS_TM)) return cudaErrorInvalidValue;
-    k_clomp_persist<MCH><<<grid, PS_THREADS, PS_SMEM, s>>>(mA, p);
+    k_clomp_persist<KB><<<grid, PS_THREADS, PS_SMEM, s>>>(mA, p);
     return cudaGetLastError();
 }
 
@@ -687,7 +722,12 @@ cudaError_t launch_mch(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
 
 cudaError_t launch_clomp_persist(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
     if (!clomp_persist_supported(a, c)) return cudaErrorNotSupported;
-    return ceil_div(a.mp, 128) == 1 ? launch_mch<1>(a, c, s) : launch_mch<2>(a, c, s);
+    switch (a.mh / PS_KCH) {
+        case 1: return launch_kb<1>(a, c, s);
+        case 2: return launch_kb<2>(a, c, s);
+        case 3: return launch_kb<3>(a, c, s);
+        default: return launch_kb<4>(a, c, s);
+    }
 }
 
 }  // namespace cs
