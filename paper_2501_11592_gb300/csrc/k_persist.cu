@@ -535,10 +535,20 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                     if (lane == 0) theta[s] = th;
                 }
                 named_sync();
-                // pass 2: list the atoms at or above the threshold
+                // pass 2: list the atoms at or above the threshold.  A block of
+                // 32 atoms whose pass-1 key bounds every |c| of a signal below
+                // its threshold (value bits with the truncated low bits set)
+                // cannot hold a candidate of that signal; blocks with no such
+                // signal are skipped.
                 for (int c = qidx; c < p.nchunk; c += qcnt) {
+                    const uint32_t kb_ = part[(c * 4 + q) * 32 + lane];   // this block's key for signal `lane`
+                    const float th_l = theta[lane];
+                    const bool hot = !(th_l > 0.f) ||
+                                     __uint_as_float((kb_ & ~(uint32_t)(PS_MAXN - 1)) | (uint32_t)(PS_MAXN - 1)) >= th_l;
+                    const uint32_t hotmask = __ballot_sync(0xffffffffu, hot);
+                    if (hotmask == 0u) continue;
                     const int atom = c * PS_TM + 32 * q + lane;
-                    const uint32_t mw = ((atom < a.n) ? mask_t[atom] : 0xffffffffu) | ~lb;
+                    const uint32_t mw = ((atom < a.n) ? mask_t[atom] : 0xffffffffu) | ~lb | ~hotmask;
                     uint32_t hit = 0u;
 #pragma unroll
                     for (int h = 0; h < 2; ++h) {

@@ -47,7 +47,16 @@ __global__ void __launch_bounds__(256) k_gram_A(const float* __restrict__ A32, i
     __shared__ __align__(16) float Ai[BK][T + 4];
     __shared__ __align__(16) float Aj[BK][T + 4];
     const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-    const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
+    // upper-triangle tile (bi <= bj) of the 1-D grid; the product a_i . a_j is
+    // evaluated in the same order for (i, j) and (j, i), so the lower triangle
+    // is the transpose, written by the same tile
+    int bj = 0, rem = blockIdx.x;
+    while (rem > bj) {
+        rem -= bj + 1;
+        ++bj;
+    }
+    const int bi = rem;
+    const int i0 = bi * T, j0 = bj * T;
     float acc[4][4] = {};
     for (int k0 = 0; k0 < mp; k0 += BK) {
         // 64 columns x 16 rows per operand = 256 float4 loads each
@@ -85,7 +94,10 @@ __global__ void __launch_bounds__(256) k_gram_A(const float* __restrict__ A32, i
 #pragma unroll
         for (int w = 0; w < 4; ++w) {
             const int j = j0 + tx * 4 + w;
-            if (j < n) GA[(size_t)i * n + j] = acc[u][w];
+            if (j < n) {
+                GA[(size_t)i * n + j] = acc[u][w];
+                if (bi != bj) GA[(size_t)j * n + i] = acc[u][w];
+            }
         }
     }
 }
@@ -205,8 +217,8 @@ cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh,
 }
 
 cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s) {
-    dim3 grid(ceil_div(n, 64), ceil_div(n, 64));
-    k_gram_A<<<grid, 256, 0, s>>>(A32, mp, n, GA);
+    const int t = ceil_div(n, 64);
+    k_gram_A<<<t * (t + 1) / 2, 256, 0, s>>>(A32, mp, n, GA);
     return cudaGetLastError();
 }
 
@@ -235,7 +247,8 @@ cudaError_t launch_setup(const IterArgs& a, const float* Y, int ldy, int clomp, 
 cudaError_t launch_adam_table(float2* tab, int len, float lr, float beta1, float beta2,
                               cudaStream_t s) {
     if (len <= 0) return cudaSuccess;
-    k_adam_table<<<ceil_div(len, 256), 256, 0, s>>>(tab, len, lr, beta1, beta2);
+    // one warp per block: the fp64 pow of every entry spreads over many SMs
+    k_adam_table<<<ceil_div(len, 32), 32, 0, s>>>(tab, len, lr, beta1, beta2);
     return cudaGetLastError();
 }
 
