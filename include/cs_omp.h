@@ -279,7 +279,15 @@ cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable);
  * Results are identical either way: every form selects the float32 argmax of
  * |A^T r| (certified from the bf16 correlation) and runs the same float32
  * fit and residual arithmetic. */
-enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1, CS_OPT_PERSIST = 2 };
+enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1, CS_OPT_PERSIST = 2, CS_OPT_STALL_TEST = 3 };
+/* CS_OPT_STALL_TEST (test hook for the failure path, value 1): the next
+ * persistent CLOMP solve on this plan runs without graphs and withholds the
+ * completion signal of the last atom tile of its first correlation pass, so
+ * that the signal warps' bounded wait (about 2 s) runs out.  The kernel then
+ * stops every role, lets its copies and MMAs finish, frees its tensor memory
+ * and returns; cs_plan_counters reports CS_ETIMEOUT; that solve's outputs are
+ * unspecified; the context and the plan stay usable.  The option clears
+ * itself after that solve. */
 cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value);
 
 /* Kernel launches per phase since the last reset (always counted), and --

@@ -104,6 +104,7 @@ struct cs_plan {
     int use_graphs = 1;
     int fuse_update = 1;       // CLOMP Gram form: one fused kernel per iteration
     int persist = 1;           // CLOMP Gram form, bf16: one persistent kernel per solve
+    int stall_test = 0;        // test hook: the next persistent solve lets a bounded wait run out
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -374,7 +375,9 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                           "gram of A");
         CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_setup(a, Y, ldy, cp ? 1 : 0, st); }), "setup");
         if (persist) {
-            CS_TRY_LAUNCH(timed(P, CS_PHASE_PERSIST, st, [&] { return launch_clomp_persist(a, c, st); }),
+            const int stall = P->stall_test;
+            P->stall_test = 0;
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_PERSIST, st, [&] { return launch_clomp_persist(a, c, stall, st); }),
                           "persistent solve");
             return CS_OK;
         }
@@ -401,7 +404,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         }
         return CS_OK;
     };
-    if (!P->use_graphs || P->profiling) return enqueue(s);
+    if (!P->use_graphs || P->profiling || (persist && P->stall_test)) return enqueue(s);
 
     // graph cache key: everything the launches bake in
     std::string key;
@@ -847,6 +850,7 @@ cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value) {
         case CS_OPT_GRAPHS: plan->use_graphs = value ? 1 : 0; return CS_OK;
         case CS_OPT_FUSE_UPDATE: plan->fuse_update = value ? 1 : 0; return CS_OK;
         case CS_OPT_PERSIST: plan->persist = value ? 1 : 0; return CS_OK;
+        case CS_OPT_STALL_TEST: plan->stall_test = value ? 1 : 0; return CS_OK;
         default: return fail(CS_EINVAL, "unknown option %d", option);
     }
 }

@@ -125,7 +125,8 @@ bool corr_tc_supported(int m, int n);
 bool make_tma_map_bf16(CUtensorMap* map, const void* base, int row_elems, int rows, size_t row_bytes,
                        int box_rows);
 bool clomp_persist_supported(const IterArgs& a, const ClArgs& c);
-cudaError_t launch_clomp_persist(const IterArgs& a, const ClArgs& c, cudaStream_t s);
+// stall: test hook, withhold one completion signal of the first pass (see CS_OPT_STALL_TEST)
+cudaError_t launch_clomp_persist(const IterArgs& a, const ClArgs& c, int stall, cudaStream_t s);
 cudaError_t launch_select(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_chol(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_resid(const IterArgs& a, cudaStream_t s);

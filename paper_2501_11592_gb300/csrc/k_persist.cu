@@ -80,6 +80,7 @@ struct PsArgs {
     int nres;        // leading atom tiles kept in tensor memory as the MMA A operand
     int tmem_cols;   // tensor-memory columns allocated (512)
     int staged;      // Adam table staged in shared memory
+    int stall;       // test hook: withhold the last tile's completion signal in the first pass
 };
 
 __device__ __forceinline__ void named_sync() {
@@ -375,7 +376,7 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                     for (int kk = 0; kk < KB; ++kk)
                         umma_kblock_ta(tmem + (uint32_t)(c * PS_N), ta + (uint32_t)(32 * kk), db[kk], idesc,
                                        kk == 0 ? 1u : 0u);
-                    umma_commit(&chunk_bar[c]);
+                    if (!(p.stall && pass == 0 && c == p.nchunk - 1)) umma_commit(&chunk_bar[c]);
                 }
                 for (int c = p.nres; c < p.nchunk && ok; ++c) {
 #pragma unroll
@@ -395,7 +396,9 @@ k_clomp_persist(const __grid_constant__ CUtensorMap mapA, const PsArgs p) {
                         umma_commit(&empty_bar[st]);   // frees the ring slot once these MMAs are done
                         ++gc;
                     }
-                    if (ok) umma_commit(&chunk_bar[c]);   // this atom tile's accumulators are complete
+                    // this atom tile's accumulators are complete (the test hook
+                    // withholds the signal once, so that the readers time out)
+                    if (ok && !(p.stall && pass == 0 && c == p.nchunk - 1)) umma_commit(&chunk_bar[c]);
                 }
             }
             if (!ok) abort_flag = 1;
@@ -702,7 +705,7 @@ cudaError_t configure_once() {
 }
 
 template <int KB>
-cudaError_t launch_kb(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
+cudaError_t launch_kb(const IterArgs& a, const ClArgs& c, int stall, cudaStream_t s) {
     cudaError_t e = configure_once<KB>();
     if (e != cudaSuccess) return e;
     PsArgs p{};
@@ -715,6 +718,7 @@ cudaError_t launch_kb(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
     p.tmem_cols = 512;
     p.nres = std::min(p.nchunk, (512 - p.nchunk * PS_N) / (32 * p.kb));
     p.staged = c.tab_len <= PS_TAB ? 1 : 0;
+    p.stall = stall;
     // one CTA per SM, blocks of <= PS_NS signals
     const int nsm = sm_count();
     const int grid0 = std::min(nsm, a.B);
@@ -730,13 +734,13 @@ cudaError_t launch_kb(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
 
 }  // namespace
 
-cudaError_t launch_clomp_persist(const IterArgs& a, const ClArgs& c, cudaStream_t s) {
+cudaError_t launch_clomp_persist(const IterArgs& a, const ClArgs& c, int stall, cudaStream_t s) {
     if (!clomp_persist_supported(a, c)) return cudaErrorNotSupported;
     switch (a.mh / PS_KCH) {
-        case 1: return launch_kb<1>(a, c, s);
-        case 2: return launch_kb<2>(a, c, s);
-        case 3: return launch_kb<3>(a, c, s);
-        default: return launch_kb<4>(a, c, s);
+        case 1: return launch_kb<1>(a, c, stall, s);
+        case 2: return launch_kb<2>(a, c, stall, s);
+        case 3: return launch_kb<3>(a, c, stall, s);
+        default: return launch_kb<4>(a, c, stall, s);
     }
 }
 

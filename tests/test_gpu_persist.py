@@ -134,3 +134,24 @@ def test_persist_reset_adam_and_graph_replay(cs_gpu, torch):
         got.append(to_numpy(r))
     for q in ("support", "coef", "n_iter", "res_norm", "status"):
         assert np.array_equal(got[0][q], got[1][q]) and np.array_equal(got[0][q], got[2][q]), q
+
+
+def test_persist_bounded_wait_reports_timeout(cs_gpu, torch):
+    """Failure path of the persistent solve without a GPU fault: the test hook
+    withholds one MMA completion signal, the signal warps' bounded wait runs
+    out, the kernel shuts down cleanly and the plan reports a device error
+    (CS_ETIMEOUT); the next solve on the same plan is correct."""
+    p = workloads.random_problem(64, 300, 40, 8, seed=76, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    A = torch.from_numpy(A32).cuda()
+    Y = torch.from_numpy(Y32).cuda()
+    plan = cs_gpu.Plan(64, 300, 40, 8)
+    plan.set_option(cs_gpu.OPT_STALL_TEST, 1)
+    cs_gpu.clomp_solve_batched(A, Y, 8, prec="bf16", plan=plan, **CL)
+    torch.cuda.synchronize()                   # returns: every wait is bounded
+    _, errs = plan.counters(reset=True)
+    assert errs & 16, f"expected the signal-warp wait flag, got {errs:#x}"
+    r = cs_gpu.clomp_solve_batched(A, Y, 8, prec="bf16", plan=plan, **CL)
+    torch.cuda.synchronize()
+    assert plan.counters(reset=True)[1] == 0
+    compare(to_numpy(r), oracle_clomp(A64, Y64, 8))
