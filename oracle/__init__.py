@@ -61,7 +61,7 @@ def lib():
             L.cs_oracle_omp.restype = ctypes.c_int
             L.cs_oracle_clomp.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, d, ctypes.c_int, ctypes.c_int, d, d,
-                                          d, d, ctypes.c_int, pi, pd, pi, pd, pi, pd, pd, pd, ctypes.c_int]
+                                          d, d, ctypes.c_int, d, pi, pd, pi, pd, pi, pd, pd, pd, ctypes.c_int]
             L.cs_oracle_clomp.restype = ctypes.c_int
             L.cs_oracle_max_threads.restype = ctypes.c_int
             _lib = L
@@ -154,8 +154,14 @@ def omp(A, Y, k, tol=0.0, max_iter=None, nthreads=0):
 
 
 def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
-          reset_adam=False, nthreads=0):
-    """CLOMP (structure 1, Adam) for every column of Y.  Returns a dict."""
+          reset_adam=False, th=0.0, nthreads=0):
+    """CLOMP (structure 1, Adam) for every column of Y.  Returns a dict.
+
+    th: 0 selects one atom per iteration (argmax); 0 < th < 1 selects every
+    unselected atom with |c| >= th * max|c| per iteration (largest first, at
+    most k in total); n_iter then counts atoms.  top1/top2 of such picks hold
+    1 and 1 - margin, margin being the smallest relative gap deciding the
+    iteration's set and order."""
     A = _f64F(A)
     Y = _f64F(Y if np.ndim(Y) == 2 else np.reshape(Y, (-1, 1)))
     m, n = A.shape
@@ -164,7 +170,7 @@ def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0
     o = _outputs(B, k)
     rc = lib().cs_oracle_clomp(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B, k,
                                float(tol), int(max_iter), int(steps), float(lr), float(beta1),
-                               float(beta2), float(eps), int(bool(reset_adam)),
+                               float(beta2), float(eps), int(bool(reset_adam)), float(th),
                                _p(o["support"], ctypes.c_int32), _p(o["coef"], ctypes.c_double),
                                _p(o["n_iter"], ctypes.c_int32), _p(o["res_norm"], ctypes.c_double),
                                _p(o["status"], ctypes.c_int32), _p(o["top1"], ctypes.c_double),

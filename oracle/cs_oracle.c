@@ -22,7 +22,10 @@
  *
  * Readings of points the paper leaves open (each one is also listed in the
  * design notes):
- *   - one atom per iteration (argmax), lowest index on exact ties;
+ *   - one atom per iteration (argmax), lowest index on exact ties; or, as an
+ *     option (the paper's threshold Th of the "s forward block", used with
+ *     stOMP-style selection), every atom not yet selected with
+ *     |c_j| >= Th * max |c|, largest |c| first, at most k atoms in total;
  *   - already-selected atoms are excluded from the argmax;
  *   - residual r = y - A s (the sign of Eq. 2's r does not change |A^T r|);
  *   - residual loss L = 1/2 ||y - A (s .* Mask)||_2^2, gradient
@@ -153,6 +156,63 @@ static int select_atom(const double* A, int m, int n, int lda, const double* r,
     return best;
 }
 
+/*
+ * Threshold selection: every j not in S with |c_j| >= th * M, M = the largest
+ * |c_j| over j not in S; largest |c| first (lowest index on exact ties); at
+ * most `room` of them.  Returns the count (0: no atom left).  *margin is the
+ * smallest relative gap (over M) that decides the chosen set and its order:
+ * chosen atoms above the threshold, the others below it (or below the last
+ * chosen one when `room` cuts the list), and consecutive chosen atoms.
+ */
+static int select_atoms_th(const double* A, int m, int n, int lda, const double* r,
+                           const unsigned char* inS, double th, int room, int32_t* out,
+                           double* margin) {
+    double* c = (double*)malloc(sizeof(double) * n);
+    int* idx = (int*)malloc(sizeof(int) * n);
+    double M = -1.0;
+    int cnt = 0;
+    for (int j = 0; j < n; ++j) {
+        c[j] = inS[j] ? -1.0 : fabs(dot(A + (size_t)j * lda, r, m));
+        if (c[j] > M) M = c[j];
+    }
+    *margin = INFINITY;
+    if (M < 0.0) { free(c); free(idx); return 0; }
+    if (M == 0.0) *margin = 0.0;                  /* r = 0: every remaining atom ties */
+    const double thr = th * M;
+    for (int j = 0; j < n; ++j)
+        if (!inS[j] && c[j] >= thr) idx[cnt++] = j;
+    /* insertion sort by (|c| descending, index ascending) */
+    for (int a = 1; a < cnt; ++a) {
+        int v = idx[a], b = a - 1;
+        while (b >= 0 && (c[idx[b]] < c[v] || (c[idx[b]] == c[v] && idx[b] > v))) {
+            idx[b + 1] = idx[b];
+            --b;
+        }
+        idx[b + 1] = v;
+    }
+    const int take = cnt < room ? cnt : room;
+    for (int a = 0; a < take; ++a) out[a] = idx[a];
+    const double lowest = c[idx[take - 1]];
+    for (int a = 0; a < take; ++a) {
+        if (M == 0.0) break;
+        double g = (c[idx[a]] - thr) / M;
+        if (g < *margin) *margin = g;
+        if (a + 1 < take && (c[idx[a]] - c[idx[a + 1]]) / M < *margin) *margin = (c[idx[a]] - c[idx[a + 1]]) / M;
+    }
+    for (int j = 0; j < n && M > 0.0; ++j) {
+        if (inS[j]) continue;
+        int chosen = 0;
+        for (int a = 0; a < take; ++a) if (idx[a] == j) { chosen = 1; break; }
+        if (chosen) continue;
+        /* not chosen: below the threshold, or cut by `room` below the last chosen */
+        double g = (c[j] < thr) ? (thr - c[j]) / M : (lowest - c[j]) / M;
+        if (g < *margin) *margin = g;
+    }
+    free(c);
+    free(idx);
+    return take;
+}
+
 static int all_finite(const double* y, int m) {
     for (int i = 0; i < m; ++i) if (!isfinite(y[i])) return 0;
     return 1;
@@ -241,7 +301,7 @@ void cs_oracle_clfit_adam(const double* A, int m, int lda, const int32_t* S, int
 
 static void clomp_one(const double* A, int m, int n, int lda, const double* y, int k,
                       double tol, int max_iter, int steps, double lr, double beta1,
-                      double beta2, double eps, int reset_adam, int32_t* support,
+                      double beta2, double eps, int reset_adam, double th, int32_t* support,
                       double* coef, int32_t* n_iter, double* res_norm, int32_t* status,
                       double* top1, double* top2, double* res_hist) {
     for (int q = 0; q < k; ++q) { support[q] = -1; coef[q] = 0.0; top1[q] = -1.0; top2[q] = -1.0; res_hist[q] = NAN; }
@@ -254,15 +314,30 @@ static void clomp_one(const double* A, int m, int n, int lda, const double* y, i
     memcpy(r, y, sizeof(double) * m);              /* s = 0  =>  r = y */
     double rho = nrm2(r, m);
     int iters = k < max_iter ? k : max_iter;
-    int t = 0, st = -1;
+    int t = 0, st = -1, it = 0;
+    const int multi = th > 0.0 && th < 1.0;
     if (rho <= tol) st = ST_TOL;
-    while (st < 0 && t < iters) {
-        int j = select_atom(A, m, n, lda, r, inS, &top1[t], &top2[t]);
-        if (j < 0) { st = ST_MAXIT; break; }
-        support[t] = j;                           /* Mask |= e_j (bitwise or) */
-        inS[j] = 1;
-        coef[t] = 0.0;
-        ++t;
+    while (st < 0 && t < k && it < iters) {
+        if (!multi) {
+            int j = select_atom(A, m, n, lda, r, inS, &top1[t], &top2[t]);
+            if (j < 0) { st = ST_MAXIT; break; }
+            support[t] = j;                       /* Mask |= e_j (bitwise or) */
+            inS[j] = 1;
+            coef[t] = 0.0;
+            ++t;
+        } else {
+            double margin;
+            int cnt = select_atoms_th(A, m, n, lda, r, inS, th, k - t, support + t, &margin);
+            if (cnt == 0) { st = ST_MAXIT; break; }
+            for (int a = 0; a < cnt; ++a) {
+                inS[support[t + a]] = 1;
+                coef[t + a] = 0.0;
+                top1[t + a] = 1.0;                /* parity rule reads (top1 - top2) / top1 */
+                top2[t + a] = 1.0 - margin;
+            }
+            t += cnt;
+        }
+        ++it;
         if (reset_adam) {
             memset(mom, 0, sizeof(double) * k);
             memset(vel, 0, sizeof(double) * k);
@@ -307,12 +382,14 @@ int cs_oracle_omp(const double* A, int m, int n, int lda, const double* Y, int l
     return 0;
 }
 
+/* th: 0 (or >= 1) selects one atom per iteration; 0 < th < 1 selects by the
+ * threshold rule (n_iter then counts atoms, not iterations). */
 int cs_oracle_clomp(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
                     int k, double tol, int max_iter, int steps, double lr, double beta1,
-                    double beta2, double eps, int reset_adam, int32_t* support,
+                    double beta2, double eps, int reset_adam, double th, int32_t* support,
                     double* coef, int32_t* n_iter, double* res_norm, int32_t* status,
                     double* top1, double* top2, double* res_hist, int nthreads) {
-    if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0 || steps < 0) return -1;
+    if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0 || steps < 0 || !(th >= 0.0)) return -1;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -320,7 +397,7 @@ int cs_oracle_clomp(const double* A, int m, int n, int lda, const double* Y, int
     for (int b = 0; b < B; ++b) {
         size_t o = (size_t)b * k;
         clomp_one(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, steps, lr, beta1,
-                  beta2, eps, reset_adam, support + o, coef + o, n_iter + b, res_norm + b,
+                  beta2, eps, reset_adam, th, support + o, coef + o, n_iter + b, res_norm + b,
                   status + b, top1 + o, top2 + o, res_hist + o);
     }
     return 0;

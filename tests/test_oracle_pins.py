@@ -13,7 +13,10 @@ wrong sign or index, a transposed operand, a wrong tie-break or stop rule):
   * CL gradient vs central finite differences of the quadratic loss;
   * the CL Adam loop vs torch.optim.Adam in float64 (library);
   * orthonormal A decouples the CL fit coordinate by coordinate;
-  * the CL fit approaches the least-squares coefficients for long, small-step runs.
+  * the CL fit approaches the least-squares coefficients for long, small-step runs;
+  * threshold (Th) selection: closed-form sets, order and margin on an
+    orthonormal dictionary over several iterations, the k cap, and Th -> 1
+    reducing to the argmax rule.
 """
 import itertools
 import json
@@ -322,3 +325,68 @@ def test_clomp_excludes_selected_and_stops():
         assert len(set(o["support"][b].tolist())) == 10
         assert o["status"][b] == 0
     assert o["status"][2] == 4
+
+
+# ------------------------------------------------ threshold selection pins
+
+def _threshold_sets(x, th, k):
+    """Closed form of the threshold rule on an orthonormal dictionary:
+    c_j = x_j for every unselected atom at every iteration, so each iteration
+    takes the unselected atoms with |x_j| >= th * max, largest first."""
+    chosen, sets = [], []
+    ax = np.abs(x)
+    while len(chosen) < k:
+        rest = [j for j in range(len(x)) if j not in chosen]
+        M = max(ax[j] for j in rest)
+        it = sorted([j for j in rest if ax[j] >= th * M], key=lambda j: (-ax[j], j))
+        it = it[: k - len(chosen)]
+        sets.append(it)
+        chosen += it
+    return sets
+
+
+def test_clomp_threshold_orthonormal_closed_form():
+    """Orthonormal A: the threshold rule's sets, their order and the recorded
+    margin follow from x alone (Th multi-select reading)."""
+    rng = np.random.default_rng(14)
+    n = 16
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    x = rng.standard_normal(n) * np.exp(rng.standard_normal(n))
+    y = Q @ x
+    th, k = 0.6, 9
+    sets = _threshold_sets(x, th, k)
+    o = oracle.clomp(Q, y, k, th=th, steps=30)
+    assert o["support"][0].tolist() == [j for st in sets for j in st]
+    assert int(o["n_iter"][0]) == k and int(o["status"][0]) == 0
+    # margin of the first iteration, from x
+    ax = np.abs(x)
+    M = ax.max()
+    first = sets[0]
+    gaps = [(ax[j] - th * M) / M for j in first]
+    gaps += [(ax[a] - ax[b]) / M for a, b in zip(first, first[1:])]
+    gaps += [(th * M - ax[j]) / M for j in range(n) if j not in first and ax[j] < th * M]
+    gaps += [(ax[first[-1]] - ax[j]) / M for j in range(n) if j not in first and ax[j] >= th * M]
+    assert np.allclose(o["top1"][0, : len(first)] - o["top2"][0, : len(first)], min(gaps), atol=1e-12)
+
+
+def test_clomp_threshold_room_caps_the_set():
+    """More atoms pass than k allows: the largest ones are taken."""
+    rng = np.random.default_rng(15)
+    n = 12
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    x = rng.standard_normal(n)
+    o = oracle.clomp(Q, Q @ x, 3, th=1e-9, steps=10)
+    assert o["support"][0].tolist() == np.argsort(-np.abs(x), kind="stable")[:3].tolist()
+    assert int(o["n_iter"][0]) == 3 and int(o["status"][0]) == 0
+
+
+def test_clomp_threshold_near_one_is_the_argmax_rule():
+    """Th just below 1 keeps one atom per iteration on inputs without
+    near-ties: the same support and coefficients as the argmax rule."""
+    rng = np.random.default_rng(16)
+    A = _rand_A(rng, 40, 120)
+    Y = rng.standard_normal((40, 4))
+    one = oracle.clomp(A, Y, 8, steps=20)
+    thr = oracle.clomp(A, Y, 8, steps=20, th=1.0 - 1e-9)
+    assert np.array_equal(one["support"], thr["support"])
+    assert np.array_equal(one["coef"], thr["coef"])
