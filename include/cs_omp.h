@@ -94,6 +94,16 @@ typedef struct {
     int32_t reset_adam_each_iter;   /* 0: one Adam state and step counter for the whole
                                        solve; 1: reset them at every iteration */
     int32_t form;                   /* cs_cl_form */
+    float select_threshold;         /* Th.  0 (or >= 1): one atom per iteration, the largest
+                                       |c_j| among unselected atoms.  0 < Th < 1: every
+                                       unselected atom with |c_j| >= Th * max|c| joins the
+                                       support in the iteration, largest first, until k
+                                       (the paper's normalized cut-off threshold of the
+                                       s forward block; Methods).  n_iter then counts
+                                       atoms.  0 < Th < 1 needs the float32 correlation
+                                       (CS_CORR_FP32), the Gram form, m <= 1024 and
+                                       k <= 32, else CS_ENOTSUP; the plan then holds a
+                                       batch_max x n_max float32 correlation buffer. */
 } cs_clomp_params;
 
 typedef struct cs_plan cs_plan;

@@ -59,7 +59,8 @@ class Instance(ctypes.Structure):
 class ClompParams(ctypes.Structure):
     _fields_ = [("base", OmpParams), ("steps", ctypes.c_int32), ("lr", ctypes.c_float),
                 ("beta1", ctypes.c_float), ("beta2", ctypes.c_float), ("eps", ctypes.c_float),
-                ("reset_adam_each_iter", ctypes.c_int32), ("form", ctypes.c_int32)]
+                ("reset_adam_each_iter", ctypes.c_int32), ("form", ctypes.c_int32),
+                ("select_threshold", ctypes.c_float)]
 
 
 _lib = None
@@ -235,9 +236,9 @@ def _omp_params(k, tol, max_iter, prec, topc):
     return OmpParams(int(k), float(tol), int(max_iter or 0), PREC[prec], int(topc))
 
 
-def _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps, reset_adam, form):
+def _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps, reset_adam, form, th=0.0):
     return ClompParams(_omp_params(k, tol, max_iter, prec, topc), int(steps), float(lr), float(beta1),
-                       float(beta2), float(eps), int(bool(reset_adam)), FORM[form])
+                       float(beta2), float(eps), int(bool(reset_adam)), FORM[form], float(th))
 
 
 def _batched(fn, A, Y, k, params, plan, stream, out):
@@ -266,11 +267,12 @@ def omp_solve_batched(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, plan
 
 def clomp_solve_batched(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, steps=50, lr=1e-2,
                         beta1=0.9, beta2=0.999, eps=1e-8, reset_adam=False, form="gram",
-                        plan=None, stream=None, out=None) -> Result:
-    """Batched CLOMP (structure 1, Adam) on the current stream."""
+                        plan=None, stream=None, out=None, th=0.0) -> Result:
+    """Batched CLOMP (structure 1, Adam) on the current stream; th: the
+    selection threshold Th (0: one atom per iteration)."""
     return _batched(load().clomp_solve_batched, A, Y, k,
                     _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
-                                  reset_adam, form), plan, stream, out)
+                                  reset_adam, form, th), plan, stream, out)
 
 
 def omp_solve(A, y, k, **kw) -> Result:
@@ -308,10 +310,10 @@ def omp_solve_batched_host(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8,
 
 def clomp_solve_batched_host(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, steps=50,
                              lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8, reset_adam=False,
-                             form="gram", plan=None, stream=None, out=None):
+                             form="gram", plan=None, stream=None, out=None, th=0.0):
     return _host_batched(load().clomp_solve_batched_host, A, Y, k,
                          _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
-                                       reset_adam, form), plan, stream, out)
+                                       reset_adam, form, th), plan, stream, out)
 
 
 def _varlen(fn, instances, params, plan, stream):

@@ -82,6 +82,7 @@ struct cs_plan {
     unsigned* counters = nullptr;
     float2* tab = nullptr;     // Adam bias-correction table, grown on demand
     int tab_cap = 0;
+    float* cbuf = nullptr;     // B_max x n_max float32 correlations (threshold rule), on first use
     char* io = nullptr;        // device staging for the host-buffer entry points
     size_t io_bytes = 0;
     char* vl = nullptr;        // device staging for uneven batches
@@ -203,6 +204,17 @@ cs_status ensure_tab(cs_plan* P, int len) {
     cudaError_t e = cudaMalloc(&P->tab, sizeof(float2) * (size_t)cap);
     if (e != cudaSuccess) return fail(CS_ENOMEM, "cudaMalloc(adam table): %s", cudaGetErrorString(e));
     P->tab_cap = cap;
+    return CS_OK;
+}
+
+// The dense correlation buffer of the threshold rule, sized for the plan once.
+cs_status ensure_cbuf(cs_plan* P) {
+    if (P->cbuf) return CS_OK;
+    cudaError_t e = cudaMalloc(&P->cbuf, sizeof(float) * (size_t)P->B_max * (size_t)P->n_max);
+    if (e != cudaSuccess) {
+        P->cbuf = nullptr;
+        return fail(CS_ENOMEM, "cudaMalloc(correlation buffer): %s", cudaGetErrorString(e));
+    }
     return CS_OK;
 }
 
@@ -331,6 +343,8 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (!(cp->beta1 >= 0.f && cp->beta1 < 1.f && cp->beta2 >= 0.f && cp->beta2 < 1.f))
             return fail(CS_EINVAL, "Adam betas must lie in [0, 1)");
         if (!(cp->eps >= 0.f) || !std::isfinite(cp->lr)) return fail(CS_EINVAL, "bad lr/eps");
+        if (!(cp->select_threshold >= 0.f) || !std::isfinite(cp->select_threshold))
+            return fail(CS_EINVAL, "select_threshold must be finite and >= 0");
     }
     if (B == 0) return CS_OK;
     DeviceGuard dg(P->device);
@@ -353,12 +367,23 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         c.reset = cp->reset_adam_each_iter ? 1 : 0;
         c.tab = P->tab;
         c.tab_len = len;
+        c.th = (cp->select_threshold > 0.f && cp->select_threshold < 1.f) ? cp->select_threshold : 0.f;
     }
 
     // CLOMP in Gram form runs selection, fit and residual as one kernel, or
     // (bf16 correlation) the whole solve as one persistent kernel
     const bool fused = cp && cp->form == CS_CL_GRAM && P->fuse_update && update_clomp_fused_supported(a);
     const bool persist = cp && cp->form == CS_CL_GRAM && bf16 && P->persist && clomp_persist_supported(a, c);
+    // threshold rule: float32 correlation of every atom, then one fused
+    // selection + fit + residual kernel per iteration
+    const bool th_rule = cp && c.th > 0.f;
+    if (th_rule) {
+        if (cp->form != CS_CL_GRAM || bf16 || !clomp_th_supported(a))
+            return fail(CS_ENOTSUP, "select_threshold in (0, 1) runs with the float32 correlation "
+                                    "(CS_CORR_FP32), the Gram-form fit, m <= 1024 and k <= 32");
+        st = ensure_cbuf(P);
+        if (st != CS_OK) return st;
+    }
 
     // Every launch of the solve, on stream `st`.
     auto enqueue = [&](cudaStream_t st) -> cs_status {
@@ -374,6 +399,16 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, st); }),
                           "gram of A");
         CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_setup(a, Y, ldy, cp ? 1 : 0, st); }), "setup");
+        if (th_rule) {
+            for (int it = 0; it < a.iters; ++it) {
+                c.tau0 = c.reset ? 0 : it * c.steps;
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, st, [&] { return launch_corr_fp32_dense_live(a, P->cbuf, n, st); }),
+                              "correlation (fp32, dense)");
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_UPDATE, st, [&] { return launch_clomp_th(a, c, P->cbuf, n, it, st); }),
+                              "threshold-rule update");
+            }
+            return CS_OK;
+        }
         if (persist) {
             const int stall = P->stall_test;
             P->stall_test = 0;
@@ -409,7 +444,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
     // graph cache key: everything the launches bake in
     std::string key;
     auto put = [&](const void* v, size_t nb) { key.append(static_cast<const char*>(v), nb); };
-    const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab};
+    const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab, P->cbuf};
     put(ptrs, sizeof(ptrs));
     const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0, persist ? 1 : 0};
     put(ints, sizeof(ints));
@@ -418,7 +453,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                          cp ? (double)cp->steps : -1.0, cp ? (double)cp->lr : 0.0,
                          cp ? (double)cp->beta1 : 0.0, cp ? (double)cp->beta2 : 0.0,
                          cp ? (double)cp->eps : 0.0, cp ? (double)cp->reset_adam_each_iter : 0.0,
-                         cp ? (double)cp->form : -1.0};
+                         cp ? (double)cp->form : -1.0, cp ? (double)c.th : 0.0};
     put(dk, sizeof(dk));
     if (P->graphs.size() > 16 && !P->graphs.count(key)) {
         for (auto& kv : P->graphs)
@@ -686,6 +721,7 @@ cs_status cs_plan_destroy(cs_plan* plan) {
     if (plan->cap_stream) cudaStreamDestroy(plan->cap_stream);
     if (plan->ws) cudaFree(plan->ws);
     if (plan->tab) cudaFree(plan->tab);
+    if (plan->cbuf) cudaFree(plan->cbuf);
     if (plan->io) cudaFree(plan->io);
     if (plan->vl) cudaFree(plan->vl);
     delete plan;

@@ -85,6 +85,7 @@ struct IterArgs {
 
 struct ClArgs {
     int steps;
+    float th;            // selection threshold Th (0 < th < 1: threshold rule; else one atom)
     int tau0;            // Adam step counter before this fit (the same for every live signal)
     float beta1, beta2, eps;
     int reset;
@@ -113,6 +114,8 @@ cudaError_t launch_adam_table(float2* tab, int len, float lr, float beta1, float
 cudaError_t launch_corr_fp32(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_corr_fp32_dense(const float* R32, const float* A32, int mp, int B, int n, float* C,
                                    int ldc, cudaStream_t s);
+// C^T = R^T A (B x n, row stride ldc) in float32 for the live signals' tiles
+cudaError_t launch_corr_fp32_dense_live(const IterArgs& a, float* C, int ldc, cudaStream_t s);
 cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n,
                                  float* C, int ldc, unsigned* errflag, cudaStream_t s);
@@ -134,6 +137,10 @@ cudaError_t launch_clfit_gram(const IterArgs& a, const ClArgs& c, int iter, cuda
 cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 bool update_clomp_fused_supported(const IterArgs& a);
 cudaError_t launch_update_clomp(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
+// Threshold rule (0 < c.th < 1): one iteration's selection, Gram-form fit,
+// residual and stop test from the float32 correlation C (B x n, stride ldc).
+bool clomp_th_supported(const IterArgs& a);
+cudaError_t launch_clomp_th(const IterArgs& a, const ClArgs& c, const float* C, int ldc, int iter, cudaStream_t s);
 
 cudaError_t launch_clfit_forward(const float* A, int m, int lda, const int32_t* S, const float* Sv,
                                  int t, int lds, const float* Y, int ldy, int batch, float* R,

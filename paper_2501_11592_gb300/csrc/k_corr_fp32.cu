@@ -16,6 +16,7 @@ namespace {
 constexpr int BM = 128, BN = kCorrFp32TileN, BK = 16, PAD = 4;
 
 // DENSE: write C^T (B x n, row stride ldd) instead of the argmax epilogue.
+// status (optional): tiles of signals that have all stopped are skipped.
 template <bool DENSE>
 __global__ void __launch_bounds__(256, 2)
 k_corr_fp32(const float* __restrict__ R32, const float* __restrict__ A32, int mp, int B, int n,
@@ -35,7 +36,7 @@ k_corr_fp32(const float* __restrict__ R32, const float* __restrict__ A32, int mp
     __syncthreads();
     if (tid < BM) {
         const int b = b0 + tid;
-        if (b < B && (DENSE || status[b] < 0)) any_live = 1;
+        if (b < B && (status == nullptr || status[b] < 0)) any_live = 1;
     }
     __syncthreads();
     if (!any_live) return;
@@ -155,6 +156,13 @@ cudaError_t launch_corr_fp32(const IterArgs& a, cudaStream_t s) {
     dim3 grid(ceil_div(a.B, BM), ceil_div(a.n, BN));
     return launch_pdl(k_corr_fp32<false>, grid, dim3(256), 0, s, a.R32, a.A32, a.mp, a.B, a.n, a.mask, a.nw,
                       a.status, a.cand_val, a.cand_idx, a.nch, (float*)nullptr, 0);
+}
+
+cudaError_t launch_corr_fp32_dense_live(const IterArgs& a, float* C, int ldc, cudaStream_t s) {
+    dim3 grid(ceil_div(a.B, BM), ceil_div(a.n, BN));
+    k_corr_fp32<true><<<grid, 256, 0, s>>>(a.R32, a.A32, a.mp, a.B, a.n, nullptr, 0, a.status, nullptr, nullptr, 1,
+                                           C, ldc);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_corr_fp32_dense(const float* R32, const float* A32, int mp, int B, int n, float* C,

@@ -166,15 +166,17 @@ __device__ __forceinline__ bool grid_owner(int j) {
 // coordinate q = RB*i + grid_row(j) is owned (Adam state, update) by one
 // lane.  Coordinates beyond the support have zero rows, zero b and zero
 // state, so the update leaves them at exactly zero.  coef_copy (optional)
-// receives the coefficients as well.
+// receives the coefficients as well; support_size (optional) overrides the
+// one-new-atom size n_iter + 1.
 template <int KT>
 __device__ __forceinline__ void fit_grid(const IterArgs& a, const ClArgs& c, const int b, const int tau0,
-                                         float* sh_s_w, const float2* tab, float* coef_copy = nullptr) {
+                                         float* sh_s_w, const float2* tab, float* coef_copy = nullptr,
+                                         const int support_size = 0) {
     static_assert(KT % 8 == 0 && KT >= 8 && KT <= 32, "fit_grid: KT in {8, 16, 24, 32}");
     constexpr int RB = KT / 8, CB = KT / 4, CP = CB / 2;
     const int lane = threadIdx.x & 31, i = lane >> 2, j = lane & 3;
     if (b >= a.B || a.status[b] >= 0) return;
-    const int sz = a.n_iter[b] + 1;
+    const int sz = support_size > 0 ? support_size : a.n_iter[b] + 1;
     const int K = a.kmax;
     const float* Gb = a.G + (size_t)b * K * K;
     unsigned long long gp[RB][CP];
