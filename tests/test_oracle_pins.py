@@ -390,3 +390,81 @@ def test_clomp_threshold_near_one_is_the_argmax_rule():
     thr = oracle.clomp(A, Y, 8, steps=20, th=1.0 - 1e-9)
     assert np.array_equal(one["support"], thr["support"])
     assert np.array_equal(one["coef"], thr["coef"])
+
+
+# ---------------------------------------------------------------------------
+# Column-wise 2D output path: x = D s, PSNR, SSIM (oracle/image.py)
+
+def test_image_synthesize_orthonormal_round_trip():
+    """Orthonormal DCT basis: the full code s = D^T x synthesises x back, in
+    any support order, and entries past n_iter or < 0 are ignored."""
+    from oracle import image as oi
+    N = 64
+    D = workloads.dct_synthesis(N)
+    rng = np.random.default_rng(90)
+    x = rng.standard_normal((N, 3))
+    s = D.T @ x
+    perm = [np.arange(N), rng.permutation(N), rng.permutation(N)]
+    support = np.stack([p for p in perm])
+    coef = np.stack([s[perm[b], b] for b in range(3)])
+    X = oi.synthesize(D, support, coef, [N, N, N])
+    np.testing.assert_allclose(X, x, atol=1e-12)
+    sup2 = support.copy()
+    sup2[1, 5] = -1
+    X2 = oi.synthesize(D, sup2, coef, [N, 10, 0])
+    np.testing.assert_allclose(X2[:, 1], D[:, support[1, :10]] @ coef[1, :10] - D[:, support[1, 5]] * coef[1, 5],
+                               atol=1e-12)
+    assert np.all(X2[:, 2] == 0.0)
+
+
+def test_psnr_closed_form():
+    from oracle import image as oi
+    rng = np.random.default_rng(91)
+    ref = rng.uniform(-2.0, 3.0, size=(40, 33))
+    L = ref.max() - ref.min()
+    # a constant offset d gives MSE = d^2
+    assert abs(oi.psnr(ref + 0.03, ref) - 10.0 * np.log10(L * L / 0.03 ** 2)) < 1e-9
+    assert abs(oi.psnr(ref - 0.5, ref, L=255.0) - 10.0 * np.log10(255.0 ** 2 / 0.25)) < 1e-9
+    assert oi.psnr(ref, ref) == np.inf
+
+
+def test_ssim_identity_symmetry_and_constant_images():
+    from oracle import image as oi
+    rng = np.random.default_rng(92)
+    x = rng.standard_normal((30, 26))
+    y = x + 0.3 * rng.standard_normal((30, 26))
+    assert abs(oi.ssim(x, x) - 1.0) < 1e-14
+    assert abs(oi.ssim(x, y, L=4.0) - oi.ssim(y, x, L=4.0)) < 1e-14
+    assert oi.ssim(x, y) < 1.0
+    # two constant images a, b: every window has zero variance, so the index
+    # is the luminance term alone, (2ab + C1) / (a^2 + b^2 + C1)
+    a, b, L = 0.7, 1.9, 2.0
+    C1 = (0.01 * L) ** 2
+    got = oi.ssim(np.full((16, 20), a), np.full((16, 20), b), L=L)
+    # (the variances cancel to rounding: ~121 terms x 2^-52 x b^2 / C2 ~ 3e-11)
+    assert abs(got - (2 * a * b + C1) / (a * a + b * b + C1)) < 1e-10
+
+
+def test_ssim_against_window_by_window_loop():
+    """The vectorised index equals a loop over every window placement with
+    the weighted mean, centred variances and covariance written out."""
+    from oracle import image as oi
+    rng = np.random.default_rng(93)
+    x = rng.uniform(0, 1, size=(14, 13))
+    y = np.clip(x + 0.1 * rng.standard_normal(x.shape), 0, 1)
+    w = oi.gaussian_window()
+    L = 1.0
+    C1, C2 = (0.01 * L) ** 2, (0.03 * L) ** 2
+    vals = []
+    for i in range(14 - 11 + 1):
+        for j in range(13 - 11 + 1):
+            px, py = x[i:i + 11, j:j + 11], y[i:i + 11, j:j + 11]
+            mx, my = (w * px).sum(), (w * py).sum()
+            vx = (w * (px - mx) ** 2).sum()
+            vy = (w * (py - my) ** 2).sum()
+            cxy = (w * (px - mx) * (py - my)).sum()
+            vals.append(((2 * mx * my + C1) * (2 * cxy + C2)) / ((mx * mx + my * my + C1) * (vx + vy + C2)))
+    assert abs(oi.ssim(x, y, L=L) - np.mean(vals)) < 1e-13
+    # the window is the 11 x 11 Gaussian of standard deviation 1.5, unit sum
+    assert w.shape == (11, 11) and abs(w.sum() - 1.0) < 1e-15
+    assert abs(w[5, 5] / w[5, 6] - np.exp(1.0 / (2 * 1.5 ** 2))) < 1e-12
