@@ -235,6 +235,36 @@ cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int3
                        const float* R, int32_t ldr, int32_t batch, int32_t prec, float* C,
                        int32_t ldc, void* stream);
 
+/* Image columns from sparse codes (Eq. 3: the solver sees A = M D with the
+ * sparsifying basis D and returns s; the signal itself is x = D s):
+ *   X[:, b] = sum_{q < n_iter[b]} coef[b*k + q] * D[:, support[b*k + q]]
+ * summed in q order in float32.  D is N x n column-major (ldd >= N);
+ * support, coef (batch x k, row b = signal b) and n_iter are the outputs of
+ * a solve; entries outside [0, n) are skipped and n_iter is clamped to
+ * [0, k].  X is N x batch column-major (ldx >= N), written in full.  All
+ * pointers are device memory owned by the caller; asynchronous on `stream`;
+ * argument errors return CS_EINVAL with no launch. */
+cs_status cs_synthesize(const float* D, int32_t N, int32_t n, int32_t ldd, const int32_t* support,
+                        const float* coef, const int32_t* n_iter, int32_t k, int32_t batch, float* X,
+                        int32_t ldx, void* stream);
+
+/* Quality of `count` reconstructed images against references (the figures
+ * the paper reports for its image experiments, Results).  Each image is H x W
+ * column-major with leading dimension H, images consecutive (image i at
+ * offset i*H*W) -- e.g. the columns of a column-wise 2D solve after
+ * cs_synthesize.  Per image i:
+ *   psnr[i] = 10 log10(L^2 / MSE)  (+inf when MSE = 0),
+ *   ssim[i] = the SSIM index of Wang, Bovik, Sheikh and Simoncelli (2004):
+ *             11 x 11 Gaussian window of standard deviation 1.5 (unit sum),
+ *             C1 = (0.01 L)^2, C2 = (0.03 L)^2, averaged over every window
+ *             placed fully inside the image,
+ * with dynamic range L = peak if peak > 0, else max - min of the reference
+ * image.  Window statistics in float32 (means, then centred moments), sums
+ * over windows and pixels in float64.  H, W >= 11.  psnr and ssim are
+ * device arrays of count floats; asynchronous on `stream`. */
+cs_status cs_image_quality(const float* X, const float* Xref, int32_t H, int32_t W, int32_t count,
+                           float peak, float* psnr, float* ssim, void* stream);
+
 /* Synchronise `stream` and copy the plan's device counters to out[0..3]:
  * out[0] = picks where the bf16 candidates did not certify the winner and
  * further atoms (the "suspects") were re-scored in float32; out[1] = device error flags (non-zero

@@ -22,7 +22,7 @@ __all__ = [
     "omp_solve_batched_host", "clomp_solve_batched_host", "clfit_forward", "clfit_adjoint",
     "clfit_adam_step", "CSError", "SIG_REACHED_K", "SIG_REACHED_TOL", "SIG_MAX_ITER",
     "SIG_DEPENDENT", "SIG_NONFINITE", "library_path", "correlate", "PHASES", "omp_solve_varlen",
-    "clomp_solve_varlen",
+    "clomp_solve_varlen", "synthesize", "image_quality", "reconstruct_columnwise",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -97,6 +97,8 @@ def load():
         L.clfit_adam_step.argtypes = [vp, i32, i32, i32, vp, vp, i32, i32, vp, i32, i32, vp, vp,
                                       i32, f32, f32, f32, f32, vp, vp]
         L.cs_correlate.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, i32, vp, i32, vp]
+        L.cs_synthesize.argtypes = [vp, i32, i32, i32, vp, vp, vp, i32, i32, vp, i32, vp]
+        L.cs_image_quality.argtypes = [vp, vp, i32, i32, i32, f32, vp, vp, vp]
         L.cs_plan_counters.argtypes = [vp, vp, i32, vp]
         L.cs_plan_set_profiling.argtypes = [vp, i32]
         L.cs_plan_profile.argtypes = [vp, vp, vp, i32]
@@ -366,6 +368,61 @@ def correlate(A, R, prec="fp32", plan=None, stream=None):
                                m if B <= 1 else _ld(R), B, PREC[prec], ctypes.c_void_p(C.data_ptr()), n,
                                _stream_ptr(stream)))
     return C
+
+
+def synthesize(D, support, coef, n_iter, stream=None):
+    """X[:, b] = D[:, support[b, :n_iter[b]]] @ coef[b, :n_iter[b]]: the
+    signals (image columns) from a solve's sparse codes.  D: (N, n);
+    support, coef: (B, k); n_iter: (B,).  Returns X (N, B), column-major."""
+    torch = _torch()
+    D = _colmajor(D, torch.float32)
+    N, n = D.shape
+    support = support.to(torch.int32).contiguous()
+    coef = coef.to(torch.float32).contiguous()
+    n_iter = n_iter.to(torch.int32).contiguous()
+    B, k = support.shape
+    X = torch.empty((B, N), dtype=torch.float32, device=D.device).t()
+    _check(load().cs_synthesize(ctypes.c_void_p(D.data_ptr()), N, n, _ld(D), ctypes.c_void_p(support.data_ptr()),
+                                ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(n_iter.data_ptr()), k, B,
+                                ctypes.c_void_p(X.data_ptr()), N, _stream_ptr(stream)))
+    return X
+
+
+def image_quality(X, Xref, W, peak=0.0, stream=None):
+    """Per-image PSNR and SSIM of the consecutive H x W images held as the
+    columns of X (H rows, count * W columns) against Xref (same layout).
+    peak <= 0: each reference's max - min.  Returns (psnr, ssim) tensors."""
+    torch = _torch()
+    X = _colmajor(X, torch.float32)
+    R = _colmajor(Xref, torch.float32)
+    H = X.shape[0]
+    if X.shape != R.shape or X.shape[1] % W:
+        raise ValueError(f"X {tuple(X.shape)} and Xref {tuple(R.shape)} must match and hold whole H x {W} images")
+    if (X.shape[1] > 1 and X.stride(1) != H) or (R.shape[1] > 1 and R.stride(1) != H):
+        X = X.t().contiguous().t()
+        R = R.t().contiguous().t()
+    count = X.shape[1] // W
+    psnr = torch.empty(count, dtype=torch.float32, device=X.device)
+    ssim = torch.empty(count, dtype=torch.float32, device=X.device)
+    _check(load().cs_image_quality(ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(R.data_ptr()), H, W, count,
+                                   float(peak), ctypes.c_void_p(psnr.data_ptr()), ctypes.c_void_p(ssim.data_ptr()),
+                                   _stream_ptr(stream)))
+    return psnr, ssim
+
+
+def reconstruct_columnwise(A, D, Y, k, W, ref=None, algo="clomp", prec="bf16", peak=0.0, plan=None,
+                           stream=None, **kw):
+    """Column-wise 2D reconstruction (Eq. 3 applied to the columns of
+    images): solve every measured column y = A s with A = M D, synthesise the
+    image columns x = D s, and, given the reference images, their PSNR and
+    SSIM.  Y: (m, count * W); returns dict(X, result, psnr, ssim)."""
+    fn = clomp_solve_batched if algo == "clomp" else omp_solve_batched
+    res = fn(A, Y, k, prec=prec, plan=plan, stream=stream, **kw)
+    X = synthesize(D, res.support, res.coef, res.n_iter, stream=stream)
+    out = dict(X=X, result=res, psnr=None, ssim=None)
+    if ref is not None:
+        out["psnr"], out["ssim"] = image_quality(X, ref, W, peak=peak, stream=stream)
+    return out
 
 
 def clfit_forward(A, S, Sv, Y, stream=None):

@@ -861,6 +861,31 @@ cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int3
     return CS_OK;
 }
 
+cs_status cs_synthesize(const float* D, int32_t N, int32_t n, int32_t ldd, const int32_t* support,
+                        const float* coef, const int32_t* n_iter, int32_t k, int32_t batch, float* X,
+                        int32_t ldx, void* stream) {
+    if (N < 1 || n < 1 || k < 1 || batch < 0) return fail(CS_EINVAL, "bad sizes N=%d n=%d k=%d batch=%d", N, n, k, batch);
+    if (ldd < N || ldx < N) return fail(CS_EINVAL, "bad leading dimension (ldd=%d ldx=%d, N=%d)", ldd, ldx, N);
+    if (batch == 0) return CS_OK;
+    if (!D || !support || !coef || !n_iter || !X) return fail(CS_EINVAL, "NULL array");
+    CS_TRY_LAUNCH(launch_synthesize(D, N, n, ldd, support, coef, n_iter, k, batch, X, ldx, (cudaStream_t)stream),
+                  "synthesize");
+    return CS_OK;
+}
+
+cs_status cs_image_quality(const float* X, const float* Xref, int32_t H, int32_t W, int32_t count, float peak,
+                           float* psnr, float* ssim, void* stream) {
+    if (H < 11 || W < 11 || count < 0)
+        return fail(CS_EINVAL, "images must be at least 11 x 11 (H=%d W=%d count=%d)", H, W, count);
+    if ((int64_t)H * W > INT32_MAX) return fail(CS_EINVAL, "image too large");
+    if (!std::isfinite(peak)) return fail(CS_EINVAL, "peak must be finite");
+    if (count == 0) return CS_OK;
+    if (!X || !Xref || !psnr || !ssim) return fail(CS_EINVAL, "NULL array");
+    CS_TRY_LAUNCH(launch_image_quality(X, Xref, H, W, count, peak, psnr, ssim, (cudaStream_t)stream),
+                  "image quality");
+    return CS_OK;
+}
+
 cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* stream) {
     if (!plan || !out) return fail(CS_EINVAL, "NULL argument");
     DeviceGuard dg(plan->device);

@@ -139,6 +139,12 @@ bool update_clomp_fused_supported(const IterArgs& a);
 cudaError_t launch_update_clomp(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 // Threshold rule (0 < c.th < 1): one iteration's selection, Gram-form fit,
 // residual and stop test from the float32 correlation C (B x n, stride ldc).
+// Column-wise 2D output: X[:, b] = D[:, support] coef (one warp per signal), and
+// per-image PSNR / SSIM of H x W column-major images against references.
+cudaError_t launch_synthesize(const float* D, int N, int n, int ldd, const int* support, const float* coef,
+                              const int* n_iter, int k, int B, float* X, int ldx, cudaStream_t s);
+cudaError_t launch_image_quality(const float* X, const float* R, int H, int W, int count, float peak,
+                                 float* psnr, float* ssim, cudaStream_t s);
 bool clomp_th_supported(const IterArgs& a);
 cudaError_t launch_clomp_th(const IterArgs& a, const ClArgs& c, const float* C, int ldc, int iter, cudaStream_t s);
 

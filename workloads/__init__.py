@@ -173,7 +173,7 @@ def config_columnwise_2d(sr=0.3, n_images=64) -> Problem:
     Y = np.asfortranarray(Phi @ X_img)
     return Problem(name=f"colwise2d_sr{sr}_m{m}_B{Y.shape[1]}", A=A, Y=Y,
                    k=m // 3, tol=0.0, max_iter=m // 3,
-                   meta=dict(sr=sr, images=n_images))
+                   meta=dict(sr=sr, images=n_images, X_img=X_img, D=D))
 
 
 def config_uneven(n_instances=2000, n_classes=32):
