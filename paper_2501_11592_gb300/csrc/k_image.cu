@@ -41,11 +41,10 @@ __global__ void __launch_bounds__(256) k_synthesize(const float* __restrict__ D,
 }
 
 constexpr int SSIM_R = 11;          // window size
-constexpr int QT = 256;             // threads per image
+constexpr int QT = 512;             // threads per image (the window loops are latency-bound)
 
-struct Window {
-    float g[SSIM_R];                // 1-D Gaussian factors, g[u] g[v] = window weight (unit sum)
-};
+// 1-D Gaussian factors of the window: weight (u, v) = g[u] g[v], unit sum
+__constant__ float c_gauss[SSIM_R];
 
 __device__ __forceinline__ double block_sum(double v, double* sh) {
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(FULL, v, o);
@@ -77,7 +76,7 @@ __device__ __forceinline__ float block_minmax(float v, float* sh, bool is_max) {
 // moments (no cancellation of E[x^2] - mean^2); per-window indices and the
 // squared errors are summed in float64.
 __global__ void __launch_bounds__(QT) k_image_quality(const float* __restrict__ X, const float* __restrict__ R,
-                                                      int H, int W, float peak, Window win,
+                                                      int H, int W, float peak,
                                                       float* __restrict__ psnr, float* __restrict__ ssim) {
     __shared__ double shd[QT / 32];
     __shared__ float shf[QT / 32];
@@ -111,11 +110,11 @@ __global__ void __launch_bounds__(QT) k_image_quality(const float* __restrict__ 
             float sx = 0.f, sy = 0.f;
 #pragma unroll
             for (int u = 0; u < SSIM_R; ++u) {
-                sx = fmaf(win.g[u], xc[u], sx);
-                sy = fmaf(win.g[u], yc[u], sy);
+                sx = fmaf(c_gauss[u], xc[u], sx);
+                sy = fmaf(c_gauss[u], yc[u], sy);
             }
-            mx = fmaf(win.g[v], sx, mx);
-            my = fmaf(win.g[v], sy, my);
+            mx = fmaf(c_gauss[v], sx, mx);
+            my = fmaf(c_gauss[v], sy, my);
         }
         float vx = 0.f, vy = 0.f, cxy = 0.f;
         for (int v = 0; v < SSIM_R; ++v) {
@@ -125,13 +124,13 @@ __global__ void __launch_bounds__(QT) k_image_quality(const float* __restrict__ 
 #pragma unroll
             for (int u = 0; u < SSIM_R; ++u) {
                 const float dx = xc[u] - mx, dy = yc[u] - my;
-                sxx = fmaf(win.g[u] * dx, dx, sxx);
-                syy = fmaf(win.g[u] * dy, dy, syy);
-                sxy = fmaf(win.g[u] * dx, dy, sxy);
+                sxx = fmaf(c_gauss[u] * dx, dx, sxx);
+                syy = fmaf(c_gauss[u] * dy, dy, syy);
+                sxy = fmaf(c_gauss[u] * dx, dy, sxy);
             }
-            vx = fmaf(win.g[v], sxx, vx);
-            vy = fmaf(win.g[v], syy, vy);
-            cxy = fmaf(win.g[v], sxy, cxy);
+            vx = fmaf(c_gauss[v], sxx, vx);
+            vy = fmaf(c_gauss[v], syy, vy);
+            cxy = fmaf(c_gauss[v], sxy, cxy);
         }
         const double num = (2.0 * mx * my + C1) * (2.0 * cxy + C2);
         const double den = ((double)mx * mx + (double)my * my + C1) * ((double)vx + vy + C2);
@@ -158,15 +157,17 @@ cudaError_t launch_synthesize(const float* D, int N, int n, int ldd, const int* 
 cudaError_t launch_image_quality(const float* X, const float* R, int H, int W, int count, float peak,
                                  float* psnr, float* ssim, cudaStream_t s) {
     if (count <= 0) return cudaSuccess;
-    Window win;
+    float win[SSIM_R];
     double g[SSIM_R], sum = 0.0;
     for (int u = 0; u < SSIM_R; ++u) {
         const double d = u - (SSIM_R - 1) / 2.0;
         g[u] = exp(-d * d / (2.0 * 1.5 * 1.5));
         sum += g[u];
     }
-    for (int u = 0; u < SSIM_R; ++u) win.g[u] = (float)(g[u] / sum);
-    k_image_quality<<<count, QT, 0, s>>>(X, R, H, W, peak, win, psnr, ssim);
+    for (int u = 0; u < SSIM_R; ++u) win[u] = (float)(g[u] / sum);
+    cudaError_t e = cudaMemcpyToSymbolAsync(c_gauss, win, sizeof(win), 0, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return e;
+    k_image_quality<<<count, QT, 0, s>>>(X, R, H, W, peak, psnr, ssim);
     return cudaGetLastError();
 }
 
