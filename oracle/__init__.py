@@ -61,8 +61,11 @@ def lib():
             L.cs_oracle_omp.restype = ctypes.c_int
             L.cs_oracle_clomp.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, d, ctypes.c_int, ctypes.c_int, d, d,
-                                          d, d, ctypes.c_int, d, pi, pd, pi, pd, pi, pd, pd, pd, ctypes.c_int]
+                                          d, d, ctypes.c_int, d, d, pd, ctypes.c_int, ctypes.c_int,
+                                          pi, pd, pi, pd, pi, pd, pd, pd, ctypes.c_int]
             L.cs_oracle_clomp.restype = ctypes.c_int
+            L.cs_oracle_tv_loss_grad.argtypes = [pd, ctypes.c_int, ctypes.c_int, pi, ctypes.c_int, pd, d, pd]
+            L.cs_oracle_tv_loss_grad.restype = d
             L.cs_oracle_max_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -153,24 +156,46 @@ def omp(A, Y, k, tol=0.0, max_iter=None, nthreads=0):
     return o
 
 
+def tv_loss_grad(D, n, support, s_S, w):
+    """w * TV(x) of Eq. 5 for x = D[:, support] @ s_S (D None: x = s placed
+    at `support` in a length-n vector) and its gradient w.r.t. s_S."""
+    S = np.ascontiguousarray(support, dtype=np.int32)
+    s_S = np.ascontiguousarray(s_S, dtype=np.float64)
+    g = np.zeros(len(S))
+    if D is None:
+        val = lib().cs_oracle_tv_loss_grad(None, int(n), int(n), _p(S, ctypes.c_int32), len(S),
+                                           _p(s_S, ctypes.c_double), float(w), _p(g, ctypes.c_double))
+    else:
+        Df = _f64F(D)
+        val = lib().cs_oracle_tv_loss_grad(_p(Df, ctypes.c_double), Df.shape[0], Df.shape[0],
+                                           _p(S, ctypes.c_int32), len(S), _p(s_S, ctypes.c_double),
+                                           float(w), _p(g, ctypes.c_double))
+    return val, g
+
+
 def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
-          reset_adam=False, th=0.0, nthreads=0):
+          reset_adam=False, th=0.0, tv_weight=0.0, D=None, nthreads=0):
     """CLOMP (structure 1, Adam) for every column of Y.  Returns a dict.
 
     th: 0 selects one atom per iteration (argmax); 0 < th < 1 selects every
     unselected atom with |c| >= th * max|c| per iteration (largest first, at
     most k in total); n_iter then counts atoms.  top1/top2 of such picks hold
     1 and 1 - margin, margin being the smallest relative gap deciding the
-    iteration's set and order."""
+    iteration's set and order.  tv_weight > 0 adds tv_weight * TV(D s) (Eq. 5)
+    to the fit's loss; D (N x n) None means x = s."""
     A = _f64F(A)
     Y = _f64F(Y if np.ndim(Y) == 2 else np.reshape(Y, (-1, 1)))
     m, n = A.shape
     B = Y.shape[1]
     max_iter = k if max_iter is None else max_iter
     o = _outputs(B, k)
+    Df = None if D is None else _f64F(D)
+    Dp = None if Df is None else _p(Df, ctypes.c_double)
+    N = n if Df is None else Df.shape[0]
     rc = lib().cs_oracle_clomp(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B, k,
                                float(tol), int(max_iter), int(steps), float(lr), float(beta1),
                                float(beta2), float(eps), int(bool(reset_adam)), float(th),
+                               float(tv_weight), Dp, int(N), int(N),
                                _p(o["support"], ctypes.c_int32), _p(o["coef"], ctypes.c_double),
                                _p(o["n_iter"], ctypes.c_int32), _p(o["res_norm"], ctypes.c_double),
                                _p(o["status"], ctypes.c_int32), _p(o["top1"], ctypes.c_double),

@@ -272,19 +272,67 @@ void cs_oracle_clfit_loss_grad(const double* A, int m, int lda, const int32_t* S
 }
 
 /*
- * `steps` Adam steps on L(s_S) = 1/2 ||y - A_S s_S||^2 (the CL coefficient
- * fit).  mom, vel and *tau carry the optimizer state between calls.
- * Coordinates outside the mask are not touched: their gradient is zero, so
- * their moments stay at zero and their Adam step is exactly zero.
+ * Total-variation prior of a 1-D signal (Eq. 5) on x = D s, restricted to the
+ * support: x = sum_q s_q D[:, S_q] (length N; D = NULL means x = s, N = the
+ * number of atoms), TV(x) = (1/N) sum_{j < N-1} (x_j - x_{j+1})^2.  Returns
+ * w * TV and adds w * dTV/ds_S to grad_S:
+ *   dTV/dx_j = (2/N) (d_j - d_{j-1}),  d_j = x_j - x_{j+1}  (d_{-1} = d_{N-1} = 0),
+ *   dTV/ds_q = sum_j D[j, S_q] dTV/dx_j.
  */
-void cs_oracle_clfit_adam(const double* A, int m, int lda, const int32_t* S, int t,
-                          const double* y, double* s_S, double* mom, double* vel,
-                          int32_t* tau, int steps, double lr, double beta1,
-                          double beta2, double eps) {
+double cs_oracle_tv_loss_grad(const double* D, int N, int ldd, const int32_t* S, int t,
+                              const double* s_S, double w, double* grad_S) {
+    if (w == 0.0 || N < 2) return 0.0;
+    double* x = (double*)calloc(N, sizeof(double));
+    double* gx = (double*)calloc(N, sizeof(double));
+    for (int q = 0; q < t; ++q) {
+        if (D) {
+            const double* dq = D + (size_t)S[q] * ldd;
+            for (int j = 0; j < N; ++j) x[j] += s_S[q] * dq[j];
+        } else {
+            x[S[q]] += s_S[q];
+        }
+    }
+    double tv = 0.0;
+    for (int j = 0; j + 1 < N; ++j) {
+        const double d = x[j] - x[j + 1];
+        tv += d * d;
+        gx[j] += 2.0 * d / N;
+        gx[j + 1] -= 2.0 * d / N;
+    }
+    tv /= N;
+    if (grad_S)
+        for (int q = 0; q < t; ++q) {
+            double g = 0.0;
+            if (D) {
+                const double* dq = D + (size_t)S[q] * ldd;
+                for (int j = 0; j < N; ++j) g += dq[j] * gx[j];
+            } else {
+                g = gx[S[q]];
+            }
+            grad_S[q] += w * g;
+        }
+    free(x);
+    free(gx);
+    return w * tv;
+}
+
+/*
+ * `steps` Adam steps on L(s_S) = 1/2 ||y - A_S s_S||^2 (the CL coefficient
+ * fit), plus tv_w * TV(D_S s_S) when tv_w != 0 (the prior loss of Eq. 5).
+ * mom, vel and *tau carry the optimizer state between calls.  Coordinates
+ * outside the mask are not touched: their gradient is zero, so their
+ * moments stay at zero and their Adam step is exactly zero.
+ */
+void cs_oracle_clfit_adam_tv(const double* A, int m, int lda, const int32_t* S, int t,
+                             const double* y, double* s_S, double* mom, double* vel,
+                             int32_t* tau, int steps, double lr, double beta1,
+                             double beta2, double eps, double tv_w, const double* D, int N,
+                             int ldd) {
     double* r = (double*)malloc(sizeof(double) * m);
     double* g = (double*)malloc(sizeof(double) * (t > 0 ? t : 1));
     for (int it = 0; it < steps; ++it) {
         cs_oracle_clfit_loss_grad(A, m, lda, S, t, s_S, y, NULL, g, r);
+        cs_oracle_tv_loss_grad(D, N, ldd, S, t, s_S, tv_w, g);
         *tau += 1;
         double bc1 = 1.0 - pow(beta1, (double)*tau);
         double bc2 = 1.0 - pow(beta2, (double)*tau);
@@ -299,9 +347,18 @@ void cs_oracle_clfit_adam(const double* A, int m, int lda, const int32_t* S, int
     free(r); free(g);
 }
 
+void cs_oracle_clfit_adam(const double* A, int m, int lda, const int32_t* S, int t,
+                          const double* y, double* s_S, double* mom, double* vel,
+                          int32_t* tau, int steps, double lr, double beta1,
+                          double beta2, double eps) {
+    cs_oracle_clfit_adam_tv(A, m, lda, S, t, y, s_S, mom, vel, tau, steps, lr, beta1, beta2, eps,
+                            0.0, NULL, 0, 0);
+}
+
 static void clomp_one(const double* A, int m, int n, int lda, const double* y, int k,
                       double tol, int max_iter, int steps, double lr, double beta1,
-                      double beta2, double eps, int reset_adam, double th, int32_t* support,
+                      double beta2, double eps, int reset_adam, double th, double tv_w,
+                      const double* D, int N, int ldd, int32_t* support,
                       double* coef, int32_t* n_iter, double* res_norm, int32_t* status,
                       double* top1, double* top2, double* res_hist) {
     for (int q = 0; q < k; ++q) { support[q] = -1; coef[q] = 0.0; top1[q] = -1.0; top2[q] = -1.0; res_hist[q] = NAN; }
@@ -343,8 +400,8 @@ static void clomp_one(const double* A, int m, int n, int lda, const double* y, i
             memset(vel, 0, sizeof(double) * k);
             tau = 0;
         }
-        cs_oracle_clfit_adam(A, m, lda, support, t, y, coef, mom, vel, &tau, steps,
-                             lr, beta1, beta2, eps);
+        cs_oracle_clfit_adam_tv(A, m, lda, support, t, y, coef, mom, vel, &tau, steps,
+                                lr, beta1, beta2, eps, tv_w, D, N, ldd);
         residual(A, m, lda, support, t, coef, y, r);
         rho = nrm2(r, m);
         res_hist[t - 1] = rho;
@@ -383,13 +440,18 @@ int cs_oracle_omp(const double* A, int m, int n, int lda, const double* Y, int l
 }
 
 /* th: 0 (or >= 1) selects one atom per iteration; 0 < th < 1 selects by the
- * threshold rule (n_iter then counts atoms, not iterations). */
+ * threshold rule (n_iter then counts atoms, not iterations).  tv_w > 0 adds
+ * the total-variation prior of Eq. 5 on x = D s to the fit's loss (D: N x n
+ * column-major with leading dimension ldd; NULL: x = s, N = n). */
 int cs_oracle_clomp(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
                     int k, double tol, int max_iter, int steps, double lr, double beta1,
-                    double beta2, double eps, int reset_adam, double th, int32_t* support,
+                    double beta2, double eps, int reset_adam, double th, double tv_w,
+                    const double* D, int N, int ldd, int32_t* support,
                     double* coef, int32_t* n_iter, double* res_norm, int32_t* status,
                     double* top1, double* top2, double* res_hist, int nthreads) {
     if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0 || steps < 0 || !(th >= 0.0)) return -1;
+    if (!(tv_w >= 0.0) || (tv_w > 0.0 && D && (N < 2 || ldd < N))) return -1;
+    if (!D) N = n;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
 #pragma omp parallel for schedule(dynamic, 4)
@@ -397,7 +459,7 @@ int cs_oracle_clomp(const double* A, int m, int n, int lda, const double* Y, int
     for (int b = 0; b < B; ++b) {
         size_t o = (size_t)b * k;
         clomp_one(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, steps, lr, beta1,
-                  beta2, eps, reset_adam, th, support + o, coef + o, n_iter + b, res_norm + b,
+                  beta2, eps, reset_adam, th, tv_w, D, N, ldd, support + o, coef + o, n_iter + b, res_norm + b,
                   status + b, top1 + o, top2 + o, res_hist + o);
     }
     return 0;

@@ -468,3 +468,86 @@ def test_ssim_against_window_by_window_loop():
     # the window is the 11 x 11 Gaussian of standard deviation 1.5, unit sum
     assert w.shape == (11, 11) and abs(w.sum() - 1.0) < 1e-15
     assert abs(w[5, 5] / w[5, 6] - np.exp(1.0 / (2 * 1.5 ** 2))) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Total-variation prior of Eq. 5 in the CL fit (oracle.tv_loss_grad, clomp(tv_weight))
+
+def test_tv_value_and_gradient_closed_forms():
+    """x = s (no basis): a ramp of slope c has TV = (n-1) c^2 / n; the
+    gradient of w TV is (2w/n) L s with L the path-graph Laplacian
+    (1, 2, ..., 2, 1 on the diagonal, -1 beside it)."""
+    n, c, w = 7, 0.75, 1.3
+    val, g = oracle.tv_loss_grad(None, n, list(range(n)), c * np.arange(n), w)
+    assert abs(val - w * (n - 1) * c * c / n) < 1e-14
+    Lap = 2.0 * np.eye(n) - np.eye(n, k=1) - np.eye(n, k=-1)
+    Lap[0, 0] = Lap[-1, -1] = 1.0
+    rng = np.random.default_rng(110)
+    s = rng.standard_normal(n)
+    _, g = oracle.tv_loss_grad(None, n, list(range(n)), s, w)
+    np.testing.assert_allclose(g, (2.0 * w / n) * (Lap @ s), atol=1e-14)
+    # a subset support sees the Laplacian's rows and columns of its atoms
+    S = [5, 1, 3]
+    _, gS = oracle.tv_loss_grad(None, n, S, s[S], w)
+    np.testing.assert_allclose(gS, (2.0 * w / n) * (Lap[np.ix_(S, S)] @ s[S]), atol=1e-14)
+
+
+def test_tv_gradient_matches_central_differences():
+    """The whole CL loss 1/2||y - A_S s||^2 + w TV(D_S s) is quadratic in s,
+    so central differences are exact up to rounding."""
+    rng = np.random.default_rng(111)
+    m, n, N, w = 9, 10, 14, 0.8
+    A = rng.standard_normal((m, n))
+    D = rng.standard_normal((N, n))
+    y = rng.standard_normal(m)
+    S = np.array([7, 2, 9, 4], dtype=np.int32)
+    s = rng.standard_normal(4)
+
+    def loss(v):
+        r = y - A[:, S] @ v
+        x = D[:, S] @ v
+        return 0.5 * r @ r + w * np.sum(np.diff(x) ** 2) / N
+
+    _, g_data, _ = oracle.clfit_loss_grad(A, S, s, y)
+    _, g_tv = oracle.tv_loss_grad(D, n, S, s, w)
+    h = 1e-4
+    fd = np.array([(loss(s + h * e) - loss(s - h * e)) / (2 * h) for e in np.eye(4)])
+    np.testing.assert_allclose(g_data + g_tv, fd, rtol=1e-8, atol=1e-9)
+
+
+def test_clomp_with_tv_prior_is_adam_on_the_prior_loss():
+    """CLOMP with the prior: one torch Adam run (float64, autograd) on
+    1/2||y - A(p * mask)||^2 + w TV(D (p * mask)), T steps per pick, the
+    mask growing by the picks of the residual's correlation."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(112)
+    m, n, N, k, T, w = 20, 40, 40, 4, 25, 0.6
+    A = _rand_A(rng, m, n)
+    D = workloads.dct_synthesis(N)
+    y = rng.standard_normal(m)
+    o = oracle.clomp(A, y, k, steps=T, lr=3e-2, tv_weight=w, D=D)
+    S = o["support"][0]
+    p = torch.zeros(n, dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([p], lr=3e-2, foreach=False)
+    At = torch.tensor(A, dtype=torch.float64)
+    Dt = torch.tensor(D, dtype=torch.float64)
+    yt = torch.tensor(y, dtype=torch.float64)
+    mask = torch.zeros(n, dtype=torch.float64)
+    for t in range(k):
+        r = (yt - At @ (p * mask)).detach()
+        c = (At.T @ r).abs().numpy()
+        c[mask.numpy() > 0] = -1
+        assert int(np.argmax(c)) == S[t]
+        mask[S[t]] = 1.0
+        for _ in range(T):
+            opt.zero_grad()
+            v = p * mask
+            x = Dt @ v
+            loss = 0.5 * torch.sum((yt - At @ v) ** 2) + w * torch.sum((x[1:] - x[:-1]) ** 2) / N
+            loss.backward()
+            opt.step()
+    np.testing.assert_allclose(o["coef"][0], p.detach().numpy()[S], rtol=0, atol=1e-12)
+    # w = 0 is the plain CLOMP
+    o0 = oracle.clomp(A, y, k, steps=T, lr=3e-2, tv_weight=0.0, D=D)
+    o1 = oracle.clomp(A, y, k, steps=T, lr=3e-2)
+    assert np.array_equal(o0["coef"], o1["coef"]) and np.array_equal(o0["support"], o1["support"])
