@@ -104,6 +104,19 @@ typedef struct {
                                        (CS_CORR_FP32), the Gram form, m <= 1024 and
                                        k <= 32, else CS_ENOTSUP; the plan then holds a
                                        batch_max x n_max float32 correlation buffer. */
+    float tv_weight;                /* w >= 0: adds w * TV(x) to the fit's loss, the total-
+                                       variation prior of a 1-D signal (Eq. 5) on x = D s:
+                                       TV(x) = (1/N) sum_{j<N-1} (x_j - x_{j+1})^2.  0: no
+                                       prior.  Needs the Gram form and n <= 4096 (the prior
+                                       enters as (2w/N) (Delta D)^T (Delta D) added to A^T A);
+                                       the plan then holds n_max x (n_max + N) float32
+                                       scratch.  The selection and the residual are those of
+                                       the data term. */
+    const float* tv_D;              /* N x n sparsifying basis (device, column-major,
+                                       leading dimension tv_ldd >= N), x = D s; NULL: x = s
+                                       (N = n). */
+    int32_t tv_N;                   /* N, the signal length (rows of tv_D, >= 2) */
+    int32_t tv_ldd;
 } cs_clomp_params;
 
 typedef struct cs_plan cs_plan;

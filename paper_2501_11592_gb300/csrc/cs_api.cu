@@ -83,6 +83,9 @@ struct cs_plan {
     float2* tab = nullptr;     // Adam bias-correction table, grown on demand
     int tab_cap = 0;
     float* cbuf = nullptr;     // B_max x n_max float32 correlations (threshold rule), on first use
+    float* tvE = nullptr;      // TV prior: differenced basis [n][Ep] (grown on demand)
+    size_t tvE_cap = 0;
+    float* tvT = nullptr;      // TV prior: (Delta D)^T (Delta D), n_max x n_max, on first use
     char* io = nullptr;        // device staging for the host-buffer entry points
     size_t io_bytes = 0;
     char* vl = nullptr;        // device staging for uneven batches
@@ -204,6 +207,33 @@ cs_status ensure_tab(cs_plan* P, int len) {
     cudaError_t e = cudaMalloc(&P->tab, sizeof(float2) * (size_t)cap);
     if (e != cudaSuccess) return fail(CS_ENOMEM, "cudaMalloc(adam table): %s", cudaGetErrorString(e));
     P->tab_cap = cap;
+    return CS_OK;
+}
+
+// Scratch of the total-variation prior: the differenced basis (n x Ep floats,
+// grown when a longer signal needs it) and its n_max x n_max Gram matrix.
+cs_status ensure_tv(cs_plan* P, size_t e_floats) {
+    if (!P->tvT) {
+        cudaError_t e = cudaMalloc(&P->tvT, sizeof(float) * (size_t)P->n_max * (size_t)P->n_max);
+        if (e != cudaSuccess) {
+            P->tvT = nullptr;
+            return fail(CS_ENOMEM, "cudaMalloc(TV Gram matrix): %s", cudaGetErrorString(e));
+        }
+    }
+    if (e_floats > P->tvE_cap) {
+        if (P->tvE) {
+            cudaError_t e = cudaFree(P->tvE);
+            P->tvE = nullptr;
+            P->tvE_cap = 0;
+            if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
+        }
+        cudaError_t e = cudaMalloc(&P->tvE, sizeof(float) * e_floats);
+        if (e != cudaSuccess) {
+            P->tvE = nullptr;
+            return fail(CS_ENOMEM, "cudaMalloc(TV differences): %s", cudaGetErrorString(e));
+        }
+        P->tvE_cap = e_floats;
+    }
     return CS_OK;
 }
 
@@ -345,6 +375,11 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (!(cp->eps >= 0.f) || !std::isfinite(cp->lr)) return fail(CS_EINVAL, "bad lr/eps");
         if (!(cp->select_threshold >= 0.f) || !std::isfinite(cp->select_threshold))
             return fail(CS_EINVAL, "select_threshold must be finite and >= 0");
+        if (!(cp->tv_weight >= 0.f) || !std::isfinite(cp->tv_weight))
+            return fail(CS_EINVAL, "tv_weight must be finite and >= 0");
+        if (cp->tv_weight > 0.f && cp->tv_D && (cp->tv_N < 2 || cp->tv_ldd < cp->tv_N))
+            return fail(CS_EINVAL, "tv_D needs tv_N >= 2 and tv_ldd >= tv_N (tv_N=%d tv_ldd=%d)", cp->tv_N,
+                        cp->tv_ldd);
     }
     if (B == 0) return CS_OK;
     DeviceGuard dg(P->device);
@@ -368,6 +403,20 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         c.tab = P->tab;
         c.tab_len = len;
         c.th = (cp->select_threshold > 0.f && cp->select_threshold < 1.f) ? cp->select_threshold : 0.f;
+    }
+
+    // total-variation prior: added once to A^T A, from which the fit's Gram
+    // matrices are gathered
+    const bool tv = cp && cp->tv_weight > 0.f;
+    int tvN = 0, tvEp = 0;
+    if (tv) {
+        if (cp->form != CS_CL_GRAM || !a.GA)
+            return fail(CS_ENOTSUP, "the TV prior needs the Gram form and n <= %d", kGramAMax);
+        tvN = cp->tv_D ? cp->tv_N : n;
+        if (tvN < 2) return fail(CS_EINVAL, "the TV prior needs a signal of length >= 2");
+        tvEp = round_up(tvN - 1, 4);
+        st = ensure_tv(P, (size_t)n * tvEp);
+        if (st != CS_OK) return st;
     }
 
     // CLOMP in Gram form runs selection, fit and residual as one kernel, or
@@ -398,6 +447,11 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (a.GA && (a.need_gcol || a.need_gram))
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, st); }),
                           "gram of A");
+        if (tv)
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
+                              return launch_tv_prior(cp->tv_D, tvN, cp->tv_ldd, n, 2.f * cp->tv_weight / (float)tvN,
+                                                     P->tvE, tvEp, P->tvT, P->GA, st);
+                          }), "TV prior");
         CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_setup(a, Y, ldy, cp ? 1 : 0, st); }), "setup");
         if (th_rule) {
             for (int it = 0; it < a.iters; ++it) {
@@ -444,7 +498,8 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
     // graph cache key: everything the launches bake in
     std::string key;
     auto put = [&](const void* v, size_t nb) { key.append(static_cast<const char*>(v), nb); };
-    const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab, P->cbuf};
+    const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab, P->cbuf,
+                          tv ? (const void*)cp->tv_D : nullptr, P->tvE, P->tvT};
     put(ptrs, sizeof(ptrs));
     const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0, persist ? 1 : 0};
     put(ints, sizeof(ints));
@@ -453,7 +508,8 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                          cp ? (double)cp->steps : -1.0, cp ? (double)cp->lr : 0.0,
                          cp ? (double)cp->beta1 : 0.0, cp ? (double)cp->beta2 : 0.0,
                          cp ? (double)cp->eps : 0.0, cp ? (double)cp->reset_adam_each_iter : 0.0,
-                         cp ? (double)cp->form : -1.0, cp ? (double)c.th : 0.0};
+                         cp ? (double)cp->form : -1.0, cp ? (double)c.th : 0.0,
+                         tv ? (double)cp->tv_weight : 0.0, (double)tvN, tv ? (double)cp->tv_ldd : 0.0};
     put(dk, sizeof(dk));
     if (P->graphs.size() > 16 && !P->graphs.count(key)) {
         for (auto& kv : P->graphs)
@@ -722,6 +778,8 @@ cs_status cs_plan_destroy(cs_plan* plan) {
     if (plan->ws) cudaFree(plan->ws);
     if (plan->tab) cudaFree(plan->tab);
     if (plan->cbuf) cudaFree(plan->cbuf);
+    if (plan->tvE) cudaFree(plan->tvE);
+    if (plan->tvT) cudaFree(plan->tvT);
     if (plan->io) cudaFree(plan->io);
     if (plan->vl) cudaFree(plan->vl);
     delete plan;

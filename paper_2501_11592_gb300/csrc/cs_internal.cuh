@@ -120,6 +120,10 @@ cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n,
                                  float* C, int ldc, unsigned* errflag, cudaStream_t s);
 cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s);
+// Total-variation prior (Eq. 5): GA += lambda (Delta D)^T (Delta D), D N x n
+// (ld ldd; nullptr: the identity, N = n); E [n][Ep] and T [n][n] are scratch.
+cudaError_t launch_tv_prior(const float* D, int N, int ldd, int n, float lambda, float* E, int Ep, float* T,
+                            float* GA, cudaStream_t s);
 cudaError_t launch_prep_R(const float* R, int ldr, int m, int B, int mp, int mh, float* R32,
                           __nv_bfloat16* R16, cudaStream_t s);
 bool corr_tc_supported(int m, int n);
