@@ -327,25 +327,29 @@ def main():
         Dc = torch.from_numpy(np.asfortranarray(pc.meta["D"], dtype=np.float32)).cuda()
         Rc = torch.from_numpy(np.asfortranarray(pc.meta["X_img"], dtype=np.float32)).cuda()
         planc = cs.Plan(pc.A.shape[0], pc.A.shape[1], pc.Y.shape[1], pc.k)
-        fnc = lambda: cs.reconstruct_columnwise(Ac, Dc, Yc, pc.k, 256, ref=Rc, algo="clomp", prec="bf16",
-                                                plan=planc, **CL)
-        for _ in range(3):
-            rc = fnc()
-        barrier()
-        tc_ms = []
-        for _ in range(ksteps):
-            flush.zero_()
-            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a_.record(stream)
-            rc = fnc()
-            b_.record(stream)
+        for tvw in (0.0, 32.0):
+            fnc = lambda: cs.reconstruct_columnwise(Ac, Dc, Yc, pc.k, 256, ref=Rc, algo="clomp", prec="bf16",
+                                                    plan=planc, tv_weight=tvw, **CL)
+            for _ in range(3):
+                rc = fnc()
             barrier()
-            tc_ms.append(a_.elapsed_time(b_))
-        mc = float(np.mean(tc_ms))
-        compare["columnwise_2d_sr0.3"] = {
-            "ms_per_step": mc, "images_per_s": ws * 64 / (mc / 1e3), "columns_per_s": ws * pc.Y.shape[1] / (mc / 1e3),
-            "mean_psnr_db": float(rc["psnr"].mean().item()), "mean_ssim": float(rc["ssim"].mean().item()),
-            "note": "64 images 256x256, m=77, k=25: CLOMP (bf16, persistent) + x = D s + PSNR/SSIM per image"}
+            tc_ms = []
+            for _ in range(ksteps):
+                flush.zero_()
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                rc = fnc()
+                b_.record(stream)
+                barrier()
+                tc_ms.append(a_.elapsed_time(b_))
+            mc = float(np.mean(tc_ms))
+            key = "columnwise_2d_sr0.3" + ("" if tvw == 0.0 else "_tv%g" % tvw)
+            compare[key] = {
+                "ms_per_step": mc, "images_per_s": ws * 64 / (mc / 1e3),
+                "columns_per_s": ws * pc.Y.shape[1] / (mc / 1e3),
+                "mean_psnr_db": float(rc["psnr"].mean().item()), "mean_ssim": float(rc["ssim"].mean().item()),
+                "note": ("64 images 256x256, m=77, k=25: CLOMP (bf16, persistent) + x = D s + PSNR/SSIM per image"
+                         + ("" if tvw == 0.0 else "; total-variation prior (Eq. 5) on x = D s, w = %g" % tvw))}
         del planc
         compare["clomp_headline"] = {"ms_per_step": ms, "signals_per_s": value}
         compare["clomp_over_omp_fp32"] = value / compare["omp_fp32"]["signals_per_s"]
