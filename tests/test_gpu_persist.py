@@ -157,3 +157,16 @@ def test_persist_bounded_wait_reports_timeout(cs_gpu, torch):
     torch.cuda.synchronize()
     assert plan.counters(reset=True)[1] == 0
     compare(to_numpy(r), oracle_clomp(A64, Y64, 8))
+
+
+@pytest.mark.parametrize("m,n", [(256, 2048), (250, 2000)])
+def test_persist_largest_sizes(cs_gpu, torch, m, n):
+    """The persistent solve's limits: n = 2048 atoms (16 atom tiles, the
+    key's 11 index bits), m = 256 (four K blocks), k = 32; and a ragged
+    neighbour (m = 250 padded to 256, a partial last atom tile)."""
+    p = workloads.random_problem(m, n, 300, 32, seed=78 + n, snr_db=40.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    g = solve(cs_gpu, torch, A32, Y32, 32)
+    assert g["launches"]["persist"] == 1
+    idx = np.sort(np.random.default_rng(5).choice(300, size=48, replace=False))
+    print(compare(g, oracle_clomp(A64, Y64[:, idx], 32), idx=idx), "list overflows:", g["fallbacks"])

@@ -152,3 +152,12 @@ def test_threshold_rule_limits(cs_gpu, torch):
     assert e.value.code == cs_gpu.CS_ENOTSUP
     with pytest.raises(cs_gpu.CSError):
         cs_gpu.clomp_solve_batched(A, Y, 4, prec="fp32", th=-0.5)
+
+
+@pytest.mark.parametrize("m", [400, 700])
+def test_threshold_larger_m(cs_gpu, torch, m):
+    """Row chunks beyond two (m > 256: the kernel's 4- and 8-chunk forms)."""
+    p = workloads.random_problem(m, 900, 40, 20, seed=84 + m, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    g = solve(cs_gpu, torch, A32, Y32, 20, 0.7)
+    compare(g, oracle_th(A64, Y64, 20, 0.7))
