@@ -327,7 +327,7 @@ def main():
         Dc = torch.from_numpy(np.asfortranarray(pc.meta["D"], dtype=np.float32)).cuda()
         Rc = torch.from_numpy(np.asfortranarray(pc.meta["X_img"], dtype=np.float32)).cuda()
         planc = cs.Plan(pc.A.shape[0], pc.A.shape[1], pc.Y.shape[1], pc.k)
-        for tvw in (0.0, 32.0):
+        for tvw in (0.0, 32.0):  # (the prior's weight; 0: none)
             fnc = lambda: cs.reconstruct_columnwise(Ac, Dc, Yc, pc.k, 256, ref=Rc, algo="clomp", prec="bf16",
                                                     plan=planc, tv_weight=tvw, **CL)
             for _ in range(3):
@@ -351,6 +351,67 @@ def main():
                 "note": ("64 images 256x256, m=77, k=25: CLOMP (bf16, persistent) + x = D s + PSNR/SSIM per image"
                          + ("" if tvw == 0.0 else "; total-variation prior (Eq. 5) on x = D s, w = %g" % tvw))}
         del planc
+        # the column-wise workload at the other sampling rates (Sr = 0.5: k = 42
+        # runs on the per-iteration kernels)
+        for sr in (0.1, 0.5):
+            pq = workloads.config_columnwise_2d(sr, n_images=64)
+            Aq = torch.from_numpy(np.asfortranarray(pq.A, dtype=np.float32)).cuda()
+            Yq = torch.from_numpy(np.asfortranarray(pq.Y, dtype=np.float32)).cuda()
+            Rq = torch.from_numpy(np.asfortranarray(pq.meta["X_img"], dtype=np.float32)).cuda()
+            planq = cs.Plan(pq.A.shape[0], pq.A.shape[1], pq.Y.shape[1], pq.k)
+            fnq = lambda: cs.reconstruct_columnwise(Aq, Dc, Yq, pq.k, 256, ref=Rq, algo="clomp", prec="bf16",
+                                                    plan=planq, **CL)
+            for _ in range(3):
+                rq = fnq()
+            barrier()
+            tq = []
+            for _ in range(ksteps):
+                flush.zero_()
+                a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a_.record(stream)
+                rq = fnq()
+                b_.record(stream)
+                barrier()
+                tq.append(a_.elapsed_time(b_))
+            mq = float(np.mean(tq))
+            compare["columnwise_2d_sr%g" % sr] = {
+                "ms_per_step": mq, "images_per_s": ws * 64 / (mq / 1e3),
+                "columns_per_s": ws * pq.Y.shape[1] / (mq / 1e3), "m": pq.A.shape[0], "k": pq.k,
+                "mean_psnr_db": float(rq["psnr"].mean().item()), "mean_ssim": float(rq["ssim"].mean().item())}
+            del planq
+        # single signal (n = 256, m = 64, k = 8, noiseless, tol 1e-10): latency of
+        # one plain-OMP solve (graph replay), and the oracle on one host core
+        p1 = workloads.config_single_fp64()
+        A1 = torch.from_numpy(np.asfortranarray(p1.A, dtype=np.float32)).cuda()
+        y1 = torch.from_numpy(np.asfortranarray(p1.Y, dtype=np.float32)).cuda()
+        plan1 = cs.Plan(64, 256, 1, 8)
+        f1 = lambda: cs.omp_solve_batched(A1, y1, p1.k, tol=p1.tol, plan=plan1)
+        for _ in range(5):
+            f1()
+        barrier()
+        t1 = []
+        for _ in range(50):
+            a_, b_ = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a_.record(stream)
+            f1()
+            b_.record(stream)
+            barrier()
+            t1.append(a_.elapsed_time(b_))
+        single = {"gpu_ms_median": float(np.median(t1)), "algo": "omp fp32 (fp64 Cholesky)"}
+        if rank == 0:
+            import oracle
+            A1h = np.asfortranarray(p1.A, dtype=np.float32).astype(np.float64, order="F")
+            y1h = np.asfortranarray(p1.Y, dtype=np.float32).astype(np.float64, order="F")
+            n0 = oracle.max_threads()
+            tt = []
+            for _ in range(20):
+                t0_ = time.perf_counter()
+                oracle.omp(A1h, y1h, p1.k, tol=p1.tol, nthreads=1)
+                tt.append(time.perf_counter() - t0_)
+            oracle.omp(A1h, y1h, p1.k, tol=p1.tol, nthreads=n0)   # back to all host cores
+            single["oracle_ms_median_1_core"] = 1e3 * float(np.median(tt))
+        compare["single_signal_n256_m64_k8"] = single
+        del plan1
         compare["clomp_headline"] = {"ms_per_step": ms, "signals_per_s": value}
         compare["clomp_over_omp_fp32"] = value / compare["omp_fp32"]["signals_per_s"]
 
