@@ -328,11 +328,15 @@ cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable);
  *   CS_OPT_PERSIST: CLOMP in Gram form with the bf16 correlation runs the
  *     whole solve as one persistent kernel, one CTA per SM owning a block of
  *     signals (m <= 256, n <= 2048, k <= 32; otherwise the per-iteration
- *     kernels run).
+ *     kernels run);
+ *   CS_OPT_FUSED_OMP: plain OMP with the float32 correlation runs a batch
+ *     of at most one signal per SM as one kernel, one CTA per signal (the
+ *     whole solve in one launch; n <= 4096, m <= 1024).
  * Results are identical either way: every form selects the float32 argmax of
  * |A^T r| (certified from the bf16 correlation) and runs the same float32
  * fit and residual arithmetic. */
-enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1, CS_OPT_PERSIST = 2, CS_OPT_STALL_TEST = 3 };
+enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1, CS_OPT_PERSIST = 2, CS_OPT_STALL_TEST = 3,
+       CS_OPT_FUSED_OMP = 4 };
 /* CS_OPT_STALL_TEST (test hook for the failure path, value 1): the next
  * persistent CLOMP solve on this plan runs without graphs and withholds the
  * completion signal of the last atom tile of its first correlation pass, so

@@ -33,7 +33,7 @@ SIG_REACHED_K, SIG_REACHED_TOL, SIG_MAX_ITER, SIG_DEPENDENT, SIG_NONFINITE = 0, 
 PREC = {"fp32": 0, "bf16": 1}
 FORM = {"gather": 0, "gram": 1}
 PHASES = ("setup", "correlation", "select", "fit", "residual", "update", "persist")
-OPT_GRAPHS, OPT_FUSE_UPDATE, OPT_PERSIST, OPT_STALL_TEST = 0, 1, 2, 3
+OPT_GRAPHS, OPT_FUSE_UPDATE, OPT_PERSIST, OPT_STALL_TEST, OPT_FUSED_OMP = 0, 1, 2, 3, 4
 _STATUS_NAMES = {CS_EINVAL: "CS_EINVAL", CS_ENOMEM: "CS_ENOMEM", CS_ECUDA: "CS_ECUDA",
                  CS_ETIMEOUT: "CS_ETIMEOUT", CS_ENOTSUP: "CS_ENOTSUP"}
 

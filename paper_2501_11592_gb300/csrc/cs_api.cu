@@ -109,6 +109,7 @@ struct cs_plan {
     int fuse_update = 1;       // CLOMP Gram form: one fused kernel per iteration
     int persist = 1;           // CLOMP Gram form, bf16: one persistent kernel per solve
     int stall_test = 0;        // test hook: the next persistent solve lets a bounded wait run out
+    int fused_omp = 1;         // plain OMP (fp32), at most one signal per SM: one kernel per solve
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -235,6 +236,21 @@ cs_status ensure_tv(cs_plan* P, size_t e_floats) {
         P->tvE_cap = e_floats;
     }
     return CS_OK;
+}
+
+// Multiprocessors of the current device (cached per device).
+int device_sm_count() {
+    static std::mutex mu;
+    static std::map<int, int> cache;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(dev);
+    if (it != cache.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 1;
+    cache[dev] = n;
+    return n;
 }
 
 // The dense correlation buffer of the threshold rule, sized for the plan once.
@@ -419,6 +435,9 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (st != CS_OK) return st;
     }
 
+    // plain OMP on small batches: the whole solve in one kernel, one CTA per signal
+    const bool omp_fused = !cp && P->fused_omp && a.B <= device_sm_count() && omp_fused_supported(a);
+
     // CLOMP in Gram form runs selection, fit and residual as one kernel, or
     // (bf16 correlation) the whole solve as one persistent kernel
     const bool fused = cp && cp->form == CS_CL_GRAM && P->fuse_update && update_clomp_fused_supported(a);
@@ -470,6 +489,10 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                           "persistent solve");
             return CS_OK;
         }
+        if (omp_fused) {
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_PERSIST, st, [&] { return launch_omp_fused(a, st); }), "fused OMP");
+            return CS_OK;
+        }
         for (int it = 0; it < a.iters; ++it) {
             c.tau0 = c.reset ? 0 : it * c.steps;
             if (bf16)
@@ -501,7 +524,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
     const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab, P->cbuf,
                           tv ? (const void*)cp->tv_D : nullptr, P->tvE, P->tvT};
     put(ptrs, sizeof(ptrs));
-    const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0, persist ? 1 : 0};
+    const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0, persist ? 1 : 0, omp_fused ? 1 : 0};
     put(ints, sizeof(ints));
     // field by field (struct padding is not part of the key)
     const double dk[] = {(double)op->k, op->tol, (double)op->max_iter, (double)op->prec,
@@ -970,6 +993,7 @@ cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value) {
         case CS_OPT_FUSE_UPDATE: plan->fuse_update = value ? 1 : 0; return CS_OK;
         case CS_OPT_PERSIST: plan->persist = value ? 1 : 0; return CS_OK;
         case CS_OPT_STALL_TEST: plan->stall_test = value ? 1 : 0; return CS_OK;
+        case CS_OPT_FUSED_OMP: plan->fused_omp = value ? 1 : 0; return CS_OK;
         default: return fail(CS_EINVAL, "unknown option %d", option);
     }
 }

@@ -136,6 +136,9 @@ bool clomp_persist_supported(const IterArgs& a, const ClArgs& c);
 cudaError_t launch_clomp_persist(const IterArgs& a, const ClArgs& c, int stall, cudaStream_t s);
 cudaError_t launch_select(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_chol(const IterArgs& a, cudaStream_t s);
+// Whole plain-OMP solves (float32 correlation), one CTA per signal, one launch.
+bool omp_fused_supported(const IterArgs& a);
+cudaError_t launch_omp_fused(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_resid(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_clfit_gram(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
