@@ -1,42 +1,87 @@
 // Whole plain-OMP solves of small batches, one CTA per signal, one launch
-// (the single-signal case is latency-bound: the per-iteration kernels would
-// spend it in launches).  Each iteration of Eq. 2's greedy loop:
+// (a single signal is latency-bound: the per-iteration kernels would spend
+// it in launches and in round trips through L2).  Each iteration of Eq. 2's
+// greedy loop:
 //   * correlation c = A^T r of every unselected atom, float32, k ascending
 //     with one fused multiply-add per term -- the order of the batched
 //     float32 correlation kernel, so the values are the same -- and the
-//     masked argmax (lowest atom on ties): threads over atoms, A's columns
-//     staged through shared memory a few K values at a time;
+//     masked argmax (lowest atom on ties): threads over atoms, A held in
+//     shared memory for the whole solve when it fits (else staged a few K
+//     values at a time);
 //   * warp 0 appends the atom (bitset, support, Gram column from A^T A,
-//     a_j^T y), thread 0 runs the float64 Cholesky update and the
-//     triangular solves on the factor held in shared memory (a dependent
-//     chain of L2 round trips otherwise), warp 0 forms the residual and
-//     the stop test.
-// The append, Cholesky and residual are the batched path's own functions,
-// so a solve gives the same bits either way.
+//     a_j^T y), thread 0 runs the float64 Cholesky update and the triangular
+//     solves, warp 0 forms the residual and applies the stop test.
+// The signal's residual, y, support, coefficients, Gram column, bitset and
+// Cholesky factor stay in shared memory for the whole solve; the outputs are
+// written as they change.  Every step uses the batched path's arithmetic in
+// the same order (the same device functions where they exist), so a solve
+// gives the same bits either way.
 #include "k_chol.cuh"
 #include "k_resid.cuh"
-#include "k_select.cuh"
 
 namespace cs {
 namespace {
 
 constexpr int OF_THREADS = 256;
 constexpr int OF_KC = 8;              // K values of A staged per step
+constexpr int OF_MAX_SMEM = 200 * 1024;
+constexpr size_t OF_STATIC = sizeof(float) * OF_KC * (OF_THREADS + 1) + 1024;
+
+// Dynamic shared memory: L (K x K), z, x (float64) | r, y (mp floats) |
+// Gram column, coefficients (K floats) | support (K ints) | bitset (nw words)
+// | (when it fits) A itself, K-major with a padded row of n + 1 atoms.
+__host__ __device__ inline size_t of_state(int K, int mp, int nw) {
+    const size_t v = sizeof(double) * ((size_t)K * K + 2 * (size_t)K) + sizeof(float) * (2 * (size_t)mp + 2 * (size_t)K) +
+                     sizeof(int) * (size_t)K + sizeof(uint32_t) * (size_t)nw;
+    return (v + 15) & ~(size_t)15;
+}
+__host__ __device__ inline size_t of_resident_a(int mp, int n) { return sizeof(float) * (size_t)mp * (n + 1); }
+__host__ __device__ inline bool of_a_fits(int K, int mp, int nw, int n) {
+    return of_state(K, mp, nw) + of_resident_a(mp, n) + OF_STATIC <= (size_t)OF_MAX_SMEM;
+}
 
 template <int MCH>
 __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
     __shared__ float sh_v[OF_THREADS / 32];
     __shared__ int sh_j[OF_THREADS / 32];
     __shared__ float sh_a[OF_KC][OF_THREADS + 1];   // A[q0 + q][j0 + atom], padded rows
-    extern __shared__ double sh_chol[];   // L (kmax x kmax), z, x of the signal
+    __shared__ int sh_status, sh_t;
+    extern __shared__ __align__(16) unsigned char sh_dyn[];
+    const int K = a.kmax;
+    double* Ls = reinterpret_cast<double*>(sh_dyn);
+    double* zs = Ls + (size_t)K * K;
+    double* xs = zs + K;
+    float* rs = reinterpret_cast<float*>(xs + K);
+    float* ys = rs + a.mp;
+    float* gs = ys + a.mp;
+    float* cs_ = gs + K;
+    int* ss = reinterpret_cast<int*>(cs_ + K);
+    uint32_t* ms = reinterpret_cast<uint32_t*>(ss + K);
+    // A resident for the whole solve when it fits: sa[q * (n + 1) + j]
+    const bool resident = of_a_fits(K, a.mp, a.nw, a.n);
+    float* sa = reinterpret_cast<float*>(sh_dyn + of_state(K, a.mp, a.nw));
+    const int np1 = a.n + 1;
+
     const int b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float* r = a.R32 + (size_t)b * a.mp;
-    uint32_t* mrow = a.mask + (size_t)b * a.nw;
+    for (int i = tid; i < a.mp; i += OF_THREADS) {
+        rs[i] = a.R32[(size_t)b * a.mp + i];
+        ys[i] = a.Y32[(size_t)b * a.mp + i];
+    }
+    for (int w = tid; w < a.nw; w += OF_THREADS) ms[w] = a.mask[(size_t)b * a.nw + w];
+    if (resident)
+        for (int e = tid; e < a.n * a.mp; e += OF_THREADS) {
+            const int j = e / a.mp, q = e % a.mp;    // consecutive threads: one column's consecutive K values
+            sa[(size_t)q * np1 + j] = a.A32[(size_t)j * a.mp + q];
+        }
+    if (tid == 0) {
+        sh_status = a.status[b];
+        sh_t = a.n_iter[b];
+    }
     for (int it = 0; it < a.iters; ++it) {
         __syncthreads();                 // last iteration's residual, bitset and status
-        if (a.status[b] >= 0) break;     // the same value for every thread
-        const int t = a.n_iter[b];
+        if (sh_status >= 0) break;       // the same value for every thread
+        const int t = sh_t;
         float bv = -1.f;
         int bj = -1;
         for (int j0 = 0; j0 < a.n; j0 += OF_THREADS) {
@@ -46,7 +91,10 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
             // ascending k with one fused multiply-add per term
             const int j = j0 + tid;
             float acc = 0.f;
-            for (int q0 = 0; q0 < a.mp; q0 += OF_KC) {
+            if (resident) {
+                if (j < a.n)
+                    for (int q = 0; q < a.mp; ++q) acc = fmaf(rs[q], sa[(size_t)q * np1 + j], acc);
+            } else for (int q0 = 0; q0 < a.mp; q0 += OF_KC) {
                 __syncthreads();         // the previous chunk is consumed
                 for (int e = tid; e < OF_KC * OF_THREADS; e += OF_THREADS) {
                     const int ja = j0 + e / OF_KC, q = q0 + e % OF_KC;
@@ -54,9 +102,9 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
                 }
                 __syncthreads();
                 const int qn = min(OF_KC, a.mp - q0);
-                for (int q = 0; q < qn; ++q) acc = fmaf(r[q0 + q], sh_a[q][tid], acc);
+                for (int q = 0; q < qn; ++q) acc = fmaf(rs[q0 + q], sh_a[q][tid], acc);
             }
-            if (j < a.n && !((mrow[j >> 5] >> (j & 31)) & 1u)) {
+            if (j < a.n && !((ms[j >> 5] >> (j & 31)) & 1u)) {
                 const float v = fabsf(acc);
                 if (cand_better(v, j, bv, bj)) {
                     bv = v;
@@ -70,53 +118,109 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
             sh_j[warp] = bj;
         }
         __syncthreads();
-        if (warp == 0) {
-            float v = lane < OF_THREADS / 32 ? sh_v[lane] : -1.f;
-            int j = lane < OF_THREADS / 32 ? sh_j[lane] : -1;
-            warp_argmax(v, j);
-            if (j < 0) {                 // nothing left to select
-                if (lane == 0) a.status[b] = CS_SIG_MAX_ITER;
-            } else {
-                if (lane == 0) mrow[j >> 5] |= 1u << (j & 31);
-                float4 y[MCH];
-                load_row<MCH>(a.Y32 + (size_t)b * a.mp, a.mp, y);
-                append_atom<MCH>(a, b, t, j, y);
-                __syncwarp();            // Gram column, dnorm, a_j^T y for thread 0
-                if (lane == 0) {
-                    double* Ls = sh_chol;
-                    double* zs = Ls + (size_t)a.kmax * a.kmax;
-                    chol_update_at(a, b, Ls, 1, zs, zs + a.kmax, 1);
-                }
-                __syncwarp();            // coefficients, n_iter, status for the warp
-                resid_one<MCH>(a, b);
+        if (warp != 0) continue;
+        float v = lane < OF_THREADS / 32 ? sh_v[lane] : -1.f;
+        int j = lane < OF_THREADS / 32 ? sh_j[lane] : -1;
+        warp_argmax(v, j);
+        if (j < 0) {                     // nothing left to select
+            if (lane == 0) {
+                a.status[b] = CS_SIG_MAX_ITER;
+                sh_status = CS_SIG_MAX_ITER;
             }
+            continue;
+        }
+        // ---- append atom j as support entry t (the batched append's arithmetic)
+        if (lane == 0) {
+            ms[j >> 5] |= 1u << (j & 31);
+            ss[t] = j;
+            a.support[(size_t)b * a.k + t] = j;
+        }
+        float4 aj[MCH], yv[MCH];
+        load_row<MCH>(a.A32 + (size_t)j * a.mp, a.mp, aj);
+        load_row<MCH>(ys, a.mp, yv);
+        float dd = 0.f, by = 0.f;
+#pragma unroll
+        for (int c = 0; c < MCH; ++c) {
+            dd += dot4(aj[c], aj[c]);
+            by += dot4(aj[c], yv[c]);
+        }
+        dd = warp_sum(dd);
+        by = warp_sum(by);
+        const float* garow = a.GA + (size_t)j * a.n;
+        dd = garow[j];
+        __syncwarp();                    // the support entry
+        for (int i0 = 0; i0 < t; i0 += 32) {
+            const int i = i0 + lane;
+            if (i < t) gs[i] = garow[ss[i]];
+        }
+        __syncwarp();                    // the Gram column, for thread 0
+        // ---- float64 Cholesky update and solves (thread 0)
+        if (lane == 0) {
+            if (!chol_core(t, K, gs, 1, (double)dd, (double)by, Ls, 1, zs, xs, 1, cs_)) {
+                a.status[b] = CS_SIG_DEPENDENT;
+                a.support[(size_t)b * a.k + t] = -1;
+                sh_status = CS_SIG_DEPENDENT;
+            } else {
+                sh_t = t + 1;
+                a.n_iter[b] = t + 1;
+            }
+        }
+        __syncwarp();
+        if (sh_status >= 0) continue;    // dependent atom
+        const int t1 = t + 1;
+        for (int i = lane; i < t1; i += 32) a.coef[(size_t)b * a.k + i] = cs_[i];
+        // ---- residual r = y - A_S x_S, its norm, the stop test (the batched
+        // residual's arithmetic)
+        float4 rv[MCH];
+#pragma unroll
+        for (int c = 0; c < MCH; ++c) rv[c] = yv[c];
+        resid_vector_from<MCH>(a, t1, rv, ss, cs_);
+        float sq = 0.f;
+        float4* R = reinterpret_cast<float4*>(rs);
+#pragma unroll
+        for (int c = 0; c < MCH; ++c) {
+            const int i4 = c * 32 + lane;
+            if (i4 * 4 < a.mp) {
+                R[i4] = rv[c];
+                sq += dot4(rv[c], rv[c]);
+            }
+        }
+        sq = warp_sum(sq);
+        if (lane == 0) {
+            stop_test(a, b, t1, sqrtf(sq));
+            sh_status = a.status[b];
         }
     }
 }
 
 template <int MCH>
-void launch_m(const IterArgs& a, cudaStream_t s) {
-    const size_t smem = sizeof(double) * ((size_t)a.kmax * a.kmax + 2 * (size_t)a.kmax);
+cudaError_t launch_m(const IterArgs& a, cudaStream_t s) {
+    static const cudaError_t attr =
+        cudaFuncSetAttribute(k_omp_fused<MCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, OF_MAX_SMEM);
+    if (attr != cudaSuccess) return attr;
+    const size_t smem = of_state(a.kmax, a.mp, a.nw) +
+                        (of_a_fits(a.kmax, a.mp, a.nw, a.n) ? of_resident_a(a.mp, a.n) : 0);
     k_omp_fused<MCH><<<a.B, OF_THREADS, smem, s>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace
 
 bool omp_fused_supported(const IterArgs& a) {
-    return a.need_gcol && a.GA != nullptr && a.prec == CS_CORR_FP32 && row_chunks(a.mp) <= kMaxRowChunks;
+    return a.need_gcol && a.GA != nullptr && a.prec == CS_CORR_FP32 && row_chunks(a.mp) <= kMaxRowChunks &&
+           of_state(a.kmax, a.mp, a.nw) + OF_STATIC <= (size_t)OF_MAX_SMEM;
 }
 
 cudaError_t launch_omp_fused(const IterArgs& a, cudaStream_t s) {
     if (!omp_fused_supported(a)) return cudaErrorNotSupported;
     if (a.B <= 0) return cudaSuccess;
     switch (row_chunks(a.mp)) {
-        case 1: launch_m<1>(a, s); break;
-        case 2: launch_m<2>(a, s); break;
+        case 1: return launch_m<1>(a, s);
+        case 2: return launch_m<2>(a, s);
         case 3:
-        case 4: launch_m<4>(a, s); break;
-        default: launch_m<8>(a, s); break;
+        case 4: return launch_m<4>(a, s);
+        default: return launch_m<8>(a, s);
     }
-    return cudaGetLastError();
 }
 
 }  // namespace cs
