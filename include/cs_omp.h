@@ -251,7 +251,9 @@ cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int3
 /* Image columns from sparse codes (Eq. 3: the solver sees A = M D with the
  * sparsifying basis D and returns s; the signal itself is x = D s):
  *   X[:, b] = sum_{q < n_iter[b]} coef[b*k + q] * D[:, support[b*k + q]]
- * summed in q order in float32.  D is N x n column-major (ldd >= N);
+ * summed in q order in float32.  D is N x n column-major (ldd >= N); D =
+ * NULL gives the dense code itself, x = s (N must equal n; ldd ignored):
+ * the optional dense output X (n x batch) of a solve;
  * support, coef (batch x k, row b = signal b) and n_iter are the outputs of
  * a solve; entries outside [0, n) are skipped and n_iter is clamped to
  * [0, k].  X is N x batch column-major (ldx >= N), written in full.  All

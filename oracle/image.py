@@ -27,10 +27,11 @@ SSIM_K1 = 0.01
 SSIM_K2 = 0.03
 
 
-def synthesize(D, support, coef, n_iter):
+def synthesize(D, support, coef, n_iter, n=None):
     """X[:, b] = sum over the first n_iter[b] support entries q of
-    coef[b, q] * D[:, support[b, q]] (entries < 0 are skipped)."""
-    D = np.asarray(D, dtype=np.float64)
+    coef[b, q] * D[:, support[b, q]] (entries < 0 are skipped).  D None: the
+    dense code itself (D = the n x n identity)."""
+    D = np.eye(n) if D is None else np.asarray(D, dtype=np.float64)
     support = np.asarray(support)
     coef = np.asarray(coef, dtype=np.float64)
     B = support.shape[0]

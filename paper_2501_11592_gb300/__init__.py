@@ -379,19 +379,29 @@ def correlate(A, R, prec="fp32", plan=None, stream=None):
     return C
 
 
-def synthesize(D, support, coef, n_iter, stream=None):
+def synthesize(D, support, coef, n_iter, stream=None, n=None):
     """X[:, b] = D[:, support[b, :n_iter[b]]] @ coef[b, :n_iter[b]]: the
     signals (image columns) from a solve's sparse codes.  D: (N, n);
-    support, coef: (B, k); n_iter: (B,).  Returns X (N, B), column-major."""
+    support, coef: (B, k); n_iter: (B,).  D None: the dense codes themselves
+    (X is n x B; give n).  Returns X (N, B), column-major."""
     torch = _torch()
-    D = _colmajor(D, torch.float32)
-    N, n = D.shape
+    if D is None:
+        if n is None:
+            raise ValueError("synthesize without a basis needs n")
+        N = int(n)
+        Dp, ldd = None, N
+        dev = support.device
+    else:
+        D = _colmajor(D, torch.float32)
+        N, n = D.shape
+        Dp, ldd = ctypes.c_void_p(D.data_ptr()), _ld(D)
+        dev = D.device
     support = support.to(torch.int32).contiguous()
     coef = coef.to(torch.float32).contiguous()
     n_iter = n_iter.to(torch.int32).contiguous()
     B, k = support.shape
-    X = torch.empty((B, N), dtype=torch.float32, device=D.device).t()
-    _check(load().cs_synthesize(ctypes.c_void_p(D.data_ptr()), N, n, _ld(D), ctypes.c_void_p(support.data_ptr()),
+    X = torch.empty((B, N), dtype=torch.float32, device=dev).t()
+    _check(load().cs_synthesize(Dp, N, int(n), ldd, ctypes.c_void_p(support.data_ptr()),
                                 ctypes.c_void_p(coef.data_ptr()), ctypes.c_void_p(n_iter.data_ptr()), k, B,
                                 ctypes.c_void_p(X.data_ptr()), N, _stream_ptr(stream)))
     return X

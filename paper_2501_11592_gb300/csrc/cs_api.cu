@@ -946,9 +946,10 @@ cs_status cs_synthesize(const float* D, int32_t N, int32_t n, int32_t ldd, const
                         const float* coef, const int32_t* n_iter, int32_t k, int32_t batch, float* X,
                         int32_t ldx, void* stream) {
     if (N < 1 || n < 1 || k < 1 || batch < 0) return fail(CS_EINVAL, "bad sizes N=%d n=%d k=%d batch=%d", N, n, k, batch);
-    if (ldd < N || ldx < N) return fail(CS_EINVAL, "bad leading dimension (ldd=%d ldx=%d, N=%d)", ldd, ldx, N);
+    if (!D && N != n) return fail(CS_EINVAL, "without a basis the signal length is n (N=%d n=%d)", N, n);
+    if ((D && ldd < N) || ldx < N) return fail(CS_EINVAL, "bad leading dimension (ldd=%d ldx=%d, N=%d)", ldd, ldx, N);
     if (batch == 0) return CS_OK;
-    if (!D || !support || !coef || !n_iter || !X) return fail(CS_EINVAL, "NULL array");
+    if (!support || !coef || !n_iter || !X) return fail(CS_EINVAL, "NULL array");
     CS_TRY_LAUNCH(launch_synthesize(D, N, n, ldd, support, coef, n_iter, k, batch, X, ldx, (cudaStream_t)stream),
                   "synthesize");
     return CS_OK;

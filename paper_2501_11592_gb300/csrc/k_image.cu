@@ -21,6 +21,17 @@ __global__ void __launch_bounds__(256) k_synthesize(const float* __restrict__ D,
     const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (b >= B) return;
     const int t = min(max(n_iter[b], 0), k);
+    if (D == nullptr) {
+        // no basis: the dense code itself (N = n), coefficients scattered
+        // into a zeroed column (support entries are distinct)
+        for (int i = lane; i < N; i += 32) X[(size_t)b * ldx + i] = 0.f;
+        __syncwarp();
+        for (int q = lane; q < t; q += 32) {
+            const int j = support[(size_t)b * k + q];
+            if (j >= 0 && j < n) X[(size_t)b * ldx + j] = coef[(size_t)b * k + q];
+        }
+        return;
+    }
     for (int i0 = 0; i0 < N; i0 += 32) {
         const int i = i0 + lane;
         float acc = 0.f;

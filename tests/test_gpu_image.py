@@ -118,3 +118,22 @@ def test_reconstruct_columnwise_end_to_end(cs_gpu, torch):
     pg, sg = float(out["psnr"].cpu()[0]), float(out["ssim"].cpu()[0])
     print(s, "psnr gpu/oracle", pg, po, "ssim gpu/oracle", sg, so)
     assert abs(pg - po) < 0.05 and abs(sg - so) < 1e-3
+
+
+def test_dense_code_output(cs_gpu, torch):
+    """Without a basis cs_synthesize writes the dense n x B code of a solve
+    (the coefficients scattered to their atoms), equal to synthesising with
+    the identity basis."""
+    p = workloads.random_problem(64, 300, 40, 10, seed=103, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    A = torch.from_numpy(A32).cuda()
+    Y = torch.from_numpy(Y32).cuda()
+    r = cs_gpu.clomp_solve_batched(A, Y, 10, prec="bf16", **CL)
+    X = cs_gpu.synthesize(None, r.support, r.coef, r.n_iter, n=300)
+    Xi = cs_gpu.synthesize(torch.eye(300, device="cuda"), r.support, r.coef, r.n_iter)
+    torch.cuda.synchronize()
+    g = to_numpy(r)
+    Xo = oi.synthesize(None, g["support"], g["coef"].astype(np.float64), g["n_iter"], n=300)
+    assert np.array_equal(X.cpu().numpy(), Xo.astype(np.float32))
+    assert np.array_equal(X.cpu().numpy(), Xi.cpu().numpy())
+    assert np.count_nonzero(X.cpu().numpy()[:, 0]) == g["n_iter"][0]
