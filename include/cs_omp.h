@@ -317,6 +317,21 @@ enum {
     CS_PHASES = 7
 };
 
+/* A as a fixed layer (Methods: A is set once as the fixed parameters of a
+ * fully connected layer).  generation != 0: a solve leaves A's preparation in
+ * the plan (the float32 and bf16 copies, the largest column norm, A^T A), and
+ * a later solve whose generation, A pointer, m, n and lda all match reuses it
+ * instead of preparing A again.  The generation is the authority: the caller
+ * must change it whenever the contents of A change, under the same pointer or
+ * not (a pointer check alone cannot tell a freed and reallocated buffer from
+ * the old one).  The host-buffer entry points key on the caller's host A and
+ * still copy A to the device on every call.  0 (the default): every solve
+ * prepares A.  A solve with the TV prior re-prepares A and leaves A^T A
+ * modified, so nothing of its A^T A is reused; cs_correlate, a failed solve
+ * and a new generation drop what was kept.  Errors: CS_EINVAL for a NULL
+ * plan. */
+cs_status cs_plan_set_A_generation(cs_plan* plan, uint64_t generation);
+
 /* enable != 0: bracket every later kernel launch of solves on this plan with
  * CUDA events on the solve's stream (adds a little GPU time per launch). */
 cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable);

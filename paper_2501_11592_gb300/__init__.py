@@ -98,6 +98,7 @@ def load():
         L.clfit_adam_step.argtypes = [vp, i32, i32, i32, vp, vp, i32, i32, vp, i32, i32, vp, vp,
                                       i32, f32, f32, f32, f32, vp, vp]
         L.cs_correlate.argtypes = [vp, vp, i32, i32, i32, vp, i32, i32, i32, vp, i32, vp]
+        L.cs_plan_set_A_generation.argtypes = [vp, ctypes.c_uint64]
         L.cs_synthesize.argtypes = [vp, i32, i32, i32, vp, vp, vp, i32, i32, vp, i32, vp]
         L.cs_image_quality.argtypes = [vp, vp, i32, i32, i32, f32, vp, vp, vp]
         L.cs_plan_counters.argtypes = [vp, vp, i32, vp]
@@ -174,6 +175,13 @@ class Plan:
 
     def set_option(self, option, value):
         _check(load().cs_plan_set_option(self.h, int(option), int(value)))
+
+    def set_A_generation(self, generation):
+        """Keep A's preparation for later solves with the same A until the
+        generation changes (0: prepare A in every solve).  Change the
+        generation whenever A's contents change: a row-major A is copied to a
+        temporary column-major buffer whose address can repeat."""
+        _check(load().cs_plan_set_A_generation(self.h, int(generation)))
 
     def set_profiling(self, enable=True):
         _check(load().cs_plan_set_profiling(self.h, int(bool(enable))))

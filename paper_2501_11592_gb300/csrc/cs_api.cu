@@ -110,6 +110,16 @@ struct cs_plan {
     int persist = 1;           // CLOMP Gram form, bf16: one persistent kernel per solve
     int stall_test = 0;        // test hook: the next persistent solve lets a bounded wait run out
     int fused_omp = 1;         // plain OMP (fp32), at most one signal per SM: one kernel per solve
+    // A's preparation (fp32 / bf16 copies, largest column norm, A^T A) kept
+    // for later solves with the same A and generation (generation 0: never)
+    uint64_t a_gen = 0;
+    struct Prep {
+        const void* A = nullptr;   // the caller's A (device, or host for the host-buffer calls)
+        int m = 0, n = 0, lda = 0;
+        uint64_t gen = 0;
+        int bf16 = 0, gram = 0;
+    } prep;
+    const void* a_host = nullptr;   // set by the host-buffer solve around its call of solve()
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -374,6 +384,9 @@ cudaError_t timed(cs_plan* P, int phase, cudaStream_t s, F&& launch) {
     return e;
 }
 
+template <class E, class K>
+cs_status run_solve(cs_plan* P, cudaStream_t s, E& enqueue, K&& make_key, bool graphs);
+
 // The solve: set-up, then per iteration correlation -> select -> fit -> residual.
 cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* Y, int ldy, int B,
                 int32_t* support, float* coef, int32_t* n_iter, float* res_norm,
@@ -435,6 +448,13 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (st != CS_OK) return st;
     }
 
+    // A prepared by an earlier solve of this plan (same A, generation != 0)
+    const bool need_gram = a.GA && (a.need_gcol || a.need_gram);
+    const cs_plan::Prep& pr = P->prep;
+    const void* a_key = P->a_host ? P->a_host : (const void*)A;
+    const bool reuse_a = P->a_gen != 0 && pr.gen == P->a_gen && pr.A == a_key && pr.m == m && pr.n == n &&
+                         pr.lda == lda && (pr.bf16 || !bf16) && (pr.gram || !need_gram) && !tv;
+
     // plain OMP on small batches: the whole solve in one kernel, one CTA per signal
     const bool omp_fused = !cp && P->fused_omp && a.B <= device_sm_count() && omp_fused_supported(a);
 
@@ -459,13 +479,15 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
                               return launch_adam_table(P->tab, c.tab_len, cp->lr, cp->beta1, cp->beta2, st);
                           }), "adam table");
-        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
-                          return launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
-                                               P->colnorm_max, st);
-                      }), "prep A");
-        if (a.GA && (a.need_gcol || a.need_gram))
-            CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, st); }),
-                          "gram of A");
+        if (!reuse_a) {
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
+                              return launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
+                                                   P->colnorm_max, st);
+                          }), "prep A");
+            if (need_gram)
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, st); }),
+                              "gram of A");
+        }
         if (tv)
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
                               return launch_tv_prior(cp->tv_D, tvN, cp->tv_ldd, n, 2.f * cp->tv_weight / (float)tvN,
@@ -516,24 +538,50 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         }
         return CS_OK;
     };
-    if (!P->use_graphs || P->profiling || (persist && P->stall_test)) return enqueue(s);
+    // Eagerly or as a replayed CUDA graph; on any failure nothing counts as prepared.
+    if (!reuse_a) {
+        // what this solve leaves prepared (the TV prior changes A^T A in place)
+        cs_plan::Prep np;
+        np.A = a_key;
+        np.m = m;
+        np.n = n;
+        np.lda = lda;
+        np.gen = P->a_gen;
+        np.bf16 = bf16 ? 1 : 0;
+        np.gram = (need_gram && !tv) ? 1 : 0;
+        P->prep = np;
+    }
+    const cs_status rs = run_solve(P, s, enqueue, [&](std::string& key) {
+        auto put = [&](const void* v, size_t nb) { key.append(static_cast<const char*>(v), nb); };
+        const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab, P->cbuf,
+                              tv ? (const void*)cp->tv_D : nullptr, P->tvE, P->tvT};
+        put(ptrs, sizeof(ptrs));
+        const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0, persist ? 1 : 0, omp_fused ? 1 : 0,
+                            reuse_a ? 1 : 0};
+        put(ints, sizeof(ints));
+        // field by field (struct padding is not part of the key)
+        const double dk[] = {(double)op->k, op->tol, (double)op->max_iter, (double)op->prec,
+                             cp ? (double)cp->steps : -1.0, cp ? (double)cp->lr : 0.0,
+                             cp ? (double)cp->beta1 : 0.0, cp ? (double)cp->beta2 : 0.0,
+                             cp ? (double)cp->eps : 0.0, cp ? (double)cp->reset_adam_each_iter : 0.0,
+                             cp ? (double)cp->form : -1.0, cp ? (double)c.th : 0.0,
+                             tv ? (double)cp->tv_weight : 0.0, (double)tvN, tv ? (double)cp->tv_ldd : 0.0};
+        put(dk, sizeof(dk));
+    }, P->use_graphs && !P->profiling && !(persist && P->stall_test));
+    if (rs != CS_OK) P->prep = cs_plan::Prep{};
+    return rs;
+}
+
+// Runs a solve's launches eagerly (graphs off, or the first call with a key),
+// or captures them into a CUDA graph on the second identical call and replays
+// that graph from then on.
+template <class E, class K>
+cs_status run_solve(cs_plan* P, cudaStream_t s, E& enqueue, K&& make_key, bool graphs) {
+    if (!graphs) return enqueue(s);
 
     // graph cache key: everything the launches bake in
     std::string key;
-    auto put = [&](const void* v, size_t nb) { key.append(static_cast<const char*>(v), nb); };
-    const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab, P->cbuf,
-                          tv ? (const void*)cp->tv_D : nullptr, P->tvE, P->tvT};
-    put(ptrs, sizeof(ptrs));
-    const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0, persist ? 1 : 0, omp_fused ? 1 : 0};
-    put(ints, sizeof(ints));
-    // field by field (struct padding is not part of the key)
-    const double dk[] = {(double)op->k, op->tol, (double)op->max_iter, (double)op->prec,
-                         cp ? (double)cp->steps : -1.0, cp ? (double)cp->lr : 0.0,
-                         cp ? (double)cp->beta1 : 0.0, cp ? (double)cp->beta2 : 0.0,
-                         cp ? (double)cp->eps : 0.0, cp ? (double)cp->reset_adam_each_iter : 0.0,
-                         cp ? (double)cp->form : -1.0, cp ? (double)c.th : 0.0,
-                         tv ? (double)cp->tv_weight : 0.0, (double)tvN, tv ? (double)cp->tv_ldd : 0.0};
-    put(dk, sizeof(dk));
+    make_key(key);
     if (P->graphs.size() > 16 && !P->graphs.count(key)) {
         for (auto& kv : P->graphs)
             if (kv.second.exec) cudaGraphExecDestroy(kv.second.exec);
@@ -625,7 +673,9 @@ cs_status solve_host(cs_plan* P, const float* A, int m, int n, int lda, const fl
                                     cudaMemcpyHostToDevice, s), "copy A");
     CS_TRY_LAUNCH(cudaMemcpy2DAsync(dY, sizeof(float) * m, Y, sizeof(float) * ldy, sizeof(float) * m, B,
                                     cudaMemcpyHostToDevice, s), "copy Y");
+    P->a_host = A;
     st = solve(P, dA, m, n, m, dY, m, B, dS, dC, dN, dR, dT, op, cp, s);
+    P->a_host = nullptr;
     if (st != CS_OK) return st;
     CS_TRY_LAUNCH(cudaMemcpyAsync(support, dS, sizeof(int32_t) * k * B, cudaMemcpyDeviceToHost, s), "copy support");
     CS_TRY_LAUNCH(cudaMemcpyAsync(coef, dC, sizeof(float) * k * B, cudaMemcpyDeviceToHost, s), "copy coef");
@@ -929,6 +979,7 @@ cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int3
     cudaStream_t s = (cudaStream_t)stream;
     const int mp = round_up(m, 4), mh = round_up(m, 64);
     const bool bf16 = (prec == CS_CORR_BF16);
+    plan->prep = cs_plan::Prep{};   // A32 / A16 are overwritten
     CS_TRY_LAUNCH(launch_prep_A(A, lda, m, n, mp, mh, plan->A32, bf16 ? plan->A16 : nullptr, nullptr, s),
                   "prep A");
     CS_TRY_LAUNCH(launch_prep_R(R, ldr, m, batch, mp, mh, bf16 ? nullptr : plan->R32,
@@ -978,6 +1029,13 @@ cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* st
     if (reset) CS_TRY_LAUNCH(cudaMemsetAsync(plan->counters, 0, 4 * sizeof(uint32_t), s), "reset counters");
     CS_TRY_LAUNCH(cudaStreamSynchronize(s), "stream synchronize");
     if (out[1] != 0) return fail(CS_ETIMEOUT, "a bounded device-side wait gave up (flags 0x%x)", out[1]);
+    return CS_OK;
+}
+
+cs_status cs_plan_set_A_generation(cs_plan* plan, uint64_t generation) {
+    if (!plan) return fail(CS_EINVAL, "plan is NULL");
+    plan->a_gen = generation;
+    if (generation == 0) plan->prep = cs_plan::Prep{};
     return CS_OK;
 }
 
