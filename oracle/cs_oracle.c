@@ -38,6 +38,12 @@
  *   - an atom whose QR pivot satisfies R_tt^2 <= 1e-12 ||a||^2 is dependent:
  *     it is not added and the signal stops (status 3);
  *   - a non-finite measurement stops the signal before any iteration (status 4).
+ *   - prior losses (Eq. 4-6) join the fit's loss with weight w: the 1-D total
+ *     variation of each column x = D s (Eq. 5), or, for a batch of images of
+ *     W consecutive columns, the image form (Eq. 6) whose horizontal part
+ *     couples neighbouring columns; the columns of an image then take their
+ *     Adam steps together, each step's gradients from the coefficients
+ *     before it.
  *
  * Per-signal status codes: 0 reached k, 1 reached tol, 2 hit max_iter,
  * 3 dependent atom, 4 non-finite input.
@@ -461,6 +467,209 @@ int cs_oracle_clomp(const double* A, int m, int n, int lda, const double* Y, int
         clomp_one(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, steps, lr, beta1,
                   beta2, eps, reset_adam, th, tv_w, D, N, ldd, support + o, coef + o, n_iter + b, res_norm + b,
                   status + b, top1 + o, top2 + o, res_hist + o);
+    }
+    return 0;
+}
+
+/*
+ * Horizontal part of the total variation of an image (Eq. 6).  The image has
+ * W columns, column j being the signal x_j = D s_j (length N; D = NULL means
+ * x_j = s_j placed in a length-n vector, N = n), so I_{i,j} = (x_j)_i and
+ *   TV_h = (1/W) sum_i sum_{j < W-1} (I_{i,j} - I_{i,j+1})^2
+ *        = (1/W) sum_{j < W-1} ||x_j - x_{j+1}||^2.
+ * (The vertical part, (1/H) sum over columns of sum_i (I_{i,j} - I_{i+1,j})^2
+ * with H = N, is the per-column 1-D form of Eq. 5: cs_oracle_tv_loss_grad.)
+ * Column j's support is S[j*k .. j*k + t[j]) with coefficients s[j*k ..].
+ * Returns w * TV_h; when grad is not NULL adds w * dTV_h/ds to it (same
+ * layout as s, support entries only):
+ *   dTV_h/dx_j = (2/W) ((x_j - x_{j+1}) [j < W-1] + (x_j - x_{j-1}) [j > 0]),
+ *   dTV_h/ds_{j,q} = D[:, S_{j,q}]^T dTV_h/dx_j.
+ */
+double cs_oracle_tv2d_h_loss_grad(const double* D, int N, int ldd, int W, int k,
+                                  const int32_t* S, const int32_t* t, const double* s,
+                                  double w, double* grad) {
+    if (w == 0.0 || W < 2) return 0.0;
+    double* x = (double*)calloc((size_t)N * W, sizeof(double));
+    double* gx = (double*)calloc((size_t)N * W, sizeof(double));
+    for (int j = 0; j < W; ++j) {
+        double* xj = x + (size_t)j * N;
+        for (int q = 0; q < t[j]; ++q) {
+            const int a = S[(size_t)j * k + q];
+            const double v = s[(size_t)j * k + q];
+            if (D) {
+                const double* da = D + (size_t)a * ldd;
+                for (int i = 0; i < N; ++i) xj[i] += v * da[i];
+            } else {
+                xj[a] += v;
+            }
+        }
+    }
+    double tv = 0.0;
+    for (int j = 0; j + 1 < W; ++j) {
+        const double* xa = x + (size_t)j * N;
+        const double* xb = x + (size_t)(j + 1) * N;
+        double* ga = gx + (size_t)j * N;
+        double* gb = gx + (size_t)(j + 1) * N;
+        for (int i = 0; i < N; ++i) {
+            const double d = xa[i] - xb[i];
+            tv += d * d;
+            ga[i] += 2.0 * d / W;
+            gb[i] -= 2.0 * d / W;
+        }
+    }
+    tv /= W;
+    if (grad)
+        for (int j = 0; j < W; ++j) {
+            const double* gj = gx + (size_t)j * N;
+            for (int q = 0; q < t[j]; ++q) {
+                const int a = S[(size_t)j * k + q];
+                double g = 0.0;
+                if (D) {
+                    const double* da = D + (size_t)a * ldd;
+                    for (int i = 0; i < N; ++i) g += da[i] * gj[i];
+                } else {
+                    g = gj[a];
+                }
+                grad[(size_t)j * k + q] += w * g;
+            }
+        }
+    free(x);
+    free(gx);
+    return w * tv;
+}
+
+/*
+ * CLOMP on images with the total-variation prior of Eq. 6: the batch is a
+ * sequence of images of W consecutive columns (B a multiple of W), and the
+ * fit's loss of an image is
+ *   sum_j 1/2 ||y_j - A (s_j .* Mask_j)||^2 + tv_w * TV(I),   I = [D s_1 ... D s_W],
+ * which couples neighbouring columns.  Per iteration every live column
+ * selects its atom from its own residual (as in cs_oracle_clomp), then all
+ * live columns of the image take the `steps` Adam steps together: every
+ * step's gradients come from the coefficients before that step.  A stopped
+ * column keeps its coefficients and still enters its neighbours' terms.
+ * Outputs, status codes and the remaining readings are those of
+ * cs_oracle_clomp (one atom per iteration).
+ */
+static void clomp_tv2d_image(const double* A, int m, int n, int lda, const double* Y, int ldy,
+                             int W, int k, double tol, int max_iter, int steps, double lr,
+                             double beta1, double beta2, double eps, int reset_adam, double tv_w,
+                             const double* D, int N, int ldd, int32_t* support, double* coef,
+                             int32_t* n_iter, double* res_norm, int32_t* status, double* top1,
+                             double* top2, double* res_hist) {
+    double* r = (double*)malloc(sizeof(double) * (size_t)m * W);
+    double* mom = (double*)calloc((size_t)k * W, sizeof(double));
+    double* vel = (double*)calloc((size_t)k * W, sizeof(double));
+    double* g = (double*)calloc((size_t)k * W, sizeof(double));
+    double* rg = (double*)malloc(sizeof(double) * m);
+    unsigned char* inS = (unsigned char*)calloc((size_t)n * W, 1);
+    int32_t* tau = (int32_t*)calloc(W, sizeof(int32_t));
+    int32_t* st = (int32_t*)malloc(sizeof(int32_t) * W);
+    unsigned char* fit = (unsigned char*)calloc(W, 1);
+    double* rho = (double*)malloc(sizeof(double) * W);
+    for (int j = 0; j < W; ++j) {
+        const double* y = Y + (size_t)j * ldy;
+        for (int q = 0; q < k; ++q) {
+            size_t o = (size_t)j * k + q;
+            support[o] = -1; coef[o] = 0.0; top1[o] = -1.0; top2[o] = -1.0; res_hist[o] = NAN;
+        }
+        n_iter[j] = 0;
+        st[j] = -1;
+        if (!all_finite(y, m)) { st[j] = ST_NONFINITE; rho[j] = NAN; continue; }
+        memcpy(r + (size_t)j * m, y, sizeof(double) * m);          /* s = 0  =>  r = y */
+        rho[j] = nrm2(y, m);
+        if (rho[j] <= tol) st[j] = ST_TOL;
+    }
+    const int iters = k < max_iter ? k : max_iter;
+    for (int it = 0; it < iters; ++it) {
+        int any = 0;
+        for (int j = 0; j < W; ++j) {
+            fit[j] = 0;
+            if (st[j] >= 0) continue;
+            const size_t o = (size_t)j * k;
+            const int t = n_iter[j];
+            const int a = select_atom(A, m, n, lda, r + (size_t)j * m, inS + (size_t)j * n,
+                                      &top1[o + t], &top2[o + t]);
+            if (a < 0) { st[j] = ST_MAXIT; continue; }
+            support[o + t] = a;                    /* Mask |= e_a */
+            inS[(size_t)j * n + a] = 1;
+            coef[o + t] = 0.0;
+            n_iter[j] = t + 1;
+            fit[j] = 1;
+            any = 1;
+            if (reset_adam) {
+                memset(mom + o, 0, sizeof(double) * k);
+                memset(vel + o, 0, sizeof(double) * k);
+                tau[j] = 0;
+            }
+        }
+        if (!any) break;
+        for (int step = 0; step < steps; ++step) {
+            /* every gradient of this step from the coefficients before it */
+            for (int j = 0; j < W; ++j) {
+                const size_t o = (size_t)j * k;
+                const int t = n_iter[j];
+                for (int q = 0; q < k; ++q) g[o + q] = 0.0;
+                if (!fit[j]) continue;
+                cs_oracle_clfit_loss_grad(A, m, lda, support + o, t, coef + o, Y + (size_t)j * ldy,
+                                          NULL, g + o, rg);
+                cs_oracle_tv_loss_grad(D, N, ldd, support + o, t, coef + o, tv_w, g + o);
+            }
+            cs_oracle_tv2d_h_loss_grad(D, N, ldd, W, k, support, n_iter, coef, tv_w, g);
+            for (int j = 0; j < W; ++j) {
+                if (!fit[j]) continue;
+                const size_t o = (size_t)j * k;
+                tau[j] += 1;
+                const double bc1 = 1.0 - pow(beta1, (double)tau[j]);
+                const double bc2 = 1.0 - pow(beta2, (double)tau[j]);
+                for (int q = 0; q < n_iter[j]; ++q) {
+                    mom[o + q] = beta1 * mom[o + q] + (1.0 - beta1) * g[o + q];
+                    vel[o + q] = beta2 * vel[o + q] + (1.0 - beta2) * g[o + q] * g[o + q];
+                    const double mhat = mom[o + q] / bc1;
+                    const double vhat = vel[o + q] / bc2;
+                    coef[o + q] -= lr * mhat / (sqrt(vhat) + eps);
+                }
+            }
+        }
+        for (int j = 0; j < W; ++j) {
+            if (!fit[j]) continue;
+            const size_t o = (size_t)j * k;
+            const int t = n_iter[j];
+            residual(A, m, lda, support + o, t, coef + o, Y + (size_t)j * ldy, r + (size_t)j * m);
+            rho[j] = nrm2(r + (size_t)j * m, m);
+            res_hist[o + t - 1] = rho[j];
+            if (rho[j] <= tol) st[j] = ST_TOL;
+            else if (t == k) st[j] = ST_K;
+        }
+    }
+    for (int j = 0; j < W; ++j) {
+        if (st[j] < 0) st[j] = (n_iter[j] == k) ? ST_K : ST_MAXIT;
+        status[j] = st[j];
+        res_norm[j] = rho[j];
+    }
+    free(r); free(mom); free(vel); free(g); free(rg); free(inS); free(tau); free(st); free(fit); free(rho);
+}
+
+/* The batch as B / W images of W columns each (see clomp_tv2d_image); the
+ * prior's weight tv_w > 0, D as in cs_oracle_clomp. */
+int cs_oracle_clomp_tv2d(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
+                         int W, int k, double tol, int max_iter, int steps, double lr, double beta1,
+                         double beta2, double eps, int reset_adam, double tv_w, const double* D,
+                         int N, int ldd, int32_t* support, double* coef, int32_t* n_iter,
+                         double* res_norm, int32_t* status, double* top1, double* top2,
+                         double* res_hist, int nthreads) {
+    if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0 || steps < 0) return -1;
+    if (W < 1 || B % W != 0 || !(tv_w >= 0.0) || (D && (N < 2 || ldd < N))) return -1;
+    if (!D) N = n;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int g = 0; g < B / W; ++g) {
+        const size_t b0 = (size_t)g * W, o = b0 * k;
+        clomp_tv2d_image(A, m, n, lda, Y + b0 * ldy, ldy, W, k, tol, max_iter, steps, lr, beta1,
+                         beta2, eps, reset_adam, tv_w, D, N, ldd, support + o, coef + o, n_iter + b0,
+                         res_norm + b0, status + b0, top1 + o, top2 + o, res_hist + o);
     }
     return 0;
 }

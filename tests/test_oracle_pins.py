@@ -551,3 +551,130 @@ def test_clomp_with_tv_prior_is_adam_on_the_prior_loss():
     o0 = oracle.clomp(A, y, k, steps=T, lr=3e-2, tv_weight=0.0, D=D)
     o1 = oracle.clomp(A, y, k, steps=T, lr=3e-2)
     assert np.array_equal(o0["coef"], o1["coef"]) and np.array_equal(o0["support"], o1["support"])
+
+
+# Total variation of an image (Eq. 6) in the CL fit: oracle.tv2d_h_loss_grad
+# (the horizontal part) and clomp(tv_width=W), which fits the W columns of an
+# image together
+
+def test_tv2d_horizontal_closed_forms():
+    """x_j = s_j (no basis), every pixel of column j equal to c j: each of the
+    W - 1 neighbouring pairs differs by c in all n pixels, so TV_h =
+    (W - 1) n c^2 / W; alternating columns +-c differ by 2c.  Columns with
+    disjoint supports see each other's coefficients as zeros."""
+    n, W, c, w = 6, 5, 0.5, 1.7
+    full = list(range(n))
+    val, g = oracle.tv2d_h_loss_grad(None, n, [full] * W, [c * j * np.ones(n) for j in range(W)], w)
+    assert abs(val - w * (W - 1) * n * c * c / W) < 1e-13
+    # interior columns of a ramp have zero gradient; the ends are pulled inwards
+    for j in range(1, W - 1):
+        np.testing.assert_allclose(g[j], 0.0, atol=1e-14)
+    np.testing.assert_allclose(g[0], -2.0 * w * c / W, rtol=1e-14)
+    np.testing.assert_allclose(g[-1], 2.0 * w * c / W, rtol=1e-14)
+    val, _ = oracle.tv2d_h_loss_grad(None, n, [full] * W, [c * (-1) ** j * np.ones(n) for j in range(W)], w)
+    assert abs(val - w * (W - 1) * n * 4 * c * c / W) < 1e-13
+    val, g = oracle.tv2d_h_loss_grad(None, n, [[0, 1], [2, 3]], [np.array([1.0, 2.0]), np.array([3.0, -1.0])], w)
+    assert abs(val - w * (1 + 4 + 9 + 1) / 2) < 1e-14
+    np.testing.assert_allclose(g[0], w * np.array([1.0, 2.0]), rtol=1e-14)
+    np.testing.assert_allclose(g[1], w * np.array([3.0, -1.0]), rtol=1e-14)
+    # one column: no horizontal pairs
+    assert oracle.tv2d_h_loss_grad(None, n, [full], [np.ones(n)], w)[0] == 0.0
+
+
+def test_tv2d_gradient_matches_central_differences():
+    """Image loss sum_j 1/2||y_j - A_Sj s_j||^2 + w TV(I), I = [D s_1 .. D s_W]
+    (Eq. 6: (1/H) sum of vertical squared differences + (1/W) sum of
+    horizontal ones), a quadratic: central differences are exact up to
+    rounding.  D is a general (non-orthonormal) basis."""
+    rng = np.random.default_rng(150)
+    m, n, H, W, w = 7, 9, 11, 4, 0.9
+    A = rng.standard_normal((m, n))
+    D = rng.standard_normal((H, n))
+    Y = rng.standard_normal((m, W))
+    sup = [np.array([3, 1, 8], np.int32), np.array([1, 5], np.int32), np.array([8, 3, 0, 6], np.int32),
+           np.array([2], np.int32)]
+    coefs = [rng.standard_normal(len(q)) for q in sup]
+
+    def loss(cs):
+        I = np.stack([D[:, q] @ v for q, v in zip(sup, cs)], axis=1)     # H x W image
+        data = sum(0.5 * np.sum((Y[:, j] - A[:, q] @ v) ** 2) for j, (q, v) in enumerate(zip(sup, cs)))
+        vert = np.sum((I[:-1, :] - I[1:, :]) ** 2) / H
+        horiz = np.sum((I[:, :-1] - I[:, 1:]) ** 2) / W
+        return data + w * (vert + horiz)
+
+    _, gh = oracle.tv2d_h_loss_grad(D, n, sup, coefs, w)
+    h = 1e-4
+    for j in range(W):
+        _, gd, _ = oracle.clfit_loss_grad(A, sup[j], coefs[j], Y[:, j])
+        _, gv = oracle.tv_loss_grad(D, n, sup[j], coefs[j], w)
+        fd = []
+        for e in np.eye(len(sup[j])):
+            up = [v.copy() for v in coefs]
+            dn = [v.copy() for v in coefs]
+            up[j] += h * e
+            dn[j] -= h * e
+            fd.append((loss(up) - loss(dn)) / (2 * h))
+        np.testing.assert_allclose(gd + gv + gh[j], fd, rtol=1e-8, atol=1e-9)
+
+
+def test_clomp_tv2d_is_adam_on_the_image_loss():
+    """CLOMP with the image prior: one torch Adam run (float64, autograd) over
+    the n x W learnable coefficients of an image, loss sum_j 1/2||y_j -
+    A(p_j * mask_j)||^2 + w TV(D (P * Mask)) (Eq. 6), T steps per iteration,
+    each column's mask growing by the pick of its own residual's
+    correlation."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(151)
+    m, n, W, k, T, w = 16, 32, 5, 4, 20, 0.7
+    A = _rand_A(rng, m, n)
+    D = workloads.dct_synthesis(n)
+    Y = rng.standard_normal((m, W))
+    o = oracle.clomp(A, Y, k, steps=T, lr=3e-2, tv_weight=w, D=D, tv_width=W)
+    assert np.all(o["status"] == 0) and np.all(o["n_iter"] == k)
+    P = torch.zeros((n, W), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([P], lr=3e-2, foreach=False)
+    At = torch.tensor(A, dtype=torch.float64)
+    Dt = torch.tensor(D, dtype=torch.float64)
+    Yt = torch.tensor(Y, dtype=torch.float64)
+    mask = torch.zeros((n, W), dtype=torch.float64)
+    for t in range(k):
+        R = (Yt - At @ (P * mask)).detach()
+        C = (At.T @ R).abs().numpy()
+        C[mask.numpy() > 0] = -1
+        for j in range(W):
+            assert int(np.argmax(C[:, j])) == o["support"][j, t]
+            mask[o["support"][j, t], j] = 1.0
+        for _ in range(T):
+            opt.zero_grad()
+            V = P * mask
+            I = Dt @ V
+            loss = (0.5 * torch.sum((Yt - At @ V) ** 2)
+                    + w * (torch.sum((I[1:, :] - I[:-1, :]) ** 2) / n + torch.sum((I[:, 1:] - I[:, :-1]) ** 2) / W))
+            loss.backward()
+            opt.step()
+    Pn = P.detach().numpy()
+    for j in range(W):
+        np.testing.assert_allclose(o["coef"][j], Pn[o["support"][j], j], rtol=0, atol=1e-12)
+
+
+def test_clomp_tv2d_reductions():
+    """Identical columns stay identical, so the horizontal term vanishes and
+    the image fit is the per-column fit with the 1-D prior; one-column images
+    have no horizontal pairs; w = 0 is plain CLOMP."""
+    rng = np.random.default_rng(152)
+    m, n, k = 24, 48, 5
+    A = _rand_A(rng, m, n)
+    D = workloads.dct_synthesis(n)
+    y = rng.standard_normal(m)
+    Y = np.repeat(y[:, None], 6, axis=1)
+    a = oracle.clomp(A, Y, k, steps=30, tv_weight=0.8, D=D, tv_width=3)
+    b = oracle.clomp(A, Y, k, steps=30, tv_weight=0.8, D=D)
+    assert np.array_equal(a["support"], b["support"])
+    np.testing.assert_allclose(a["coef"], b["coef"], rtol=0, atol=1e-15)
+    Y2 = rng.standard_normal((m, 4))
+    a = oracle.clomp(A, Y2, k, steps=30, tv_weight=0.8, D=D, tv_width=1)
+    b = oracle.clomp(A, Y2, k, steps=30, tv_weight=0.8, D=D)
+    assert np.array_equal(a["support"], b["support"]) and np.array_equal(a["coef"], b["coef"])
+    a = oracle.clomp(A, Y2, k, steps=30, tv_weight=0.0, D=D, tv_width=2)
+    b = oracle.clomp(A, Y2, k, steps=30)
+    assert np.array_equal(a["support"], b["support"]) and np.array_equal(a["coef"], b["coef"])
