@@ -117,6 +117,21 @@ typedef struct {
                                        (N = n). */
     int32_t tv_N;                   /* N, the signal length (rows of tv_D, >= 2) */
     int32_t tv_ldd;
+    int32_t tv_width;               /* W.  0 or 1: the 1-D prior above on every column.
+                                       W >= 2 (with tv_weight > 0): the batch is a sequence
+                                       of images of W consecutive columns (signal b is
+                                       column b mod W of image b / W) and the prior is the
+                                       total variation of an image (Eq. 6):
+                                       TV(I) = (1/N) sum_{i<N-1,j} (I_ij - I_i+1,j)^2
+                                             + (1/W) sum_{i,j<W-1} (I_ij - I_i,j+1)^2,
+                                       I = [D s_1 ... D s_W].  The horizontal part couples
+                                       neighbouring columns, so an image's columns take
+                                       their Adam steps together; it is evaluated as
+                                       (1/W) sum_j ||s_j - s_j+1||^2, which needs tv_D with
+                                       orthonormal columns (D^T D = I, e.g. the DCT) or NULL.
+                                       Runs the per-iteration kernels (not the persistent
+                                       solve); needs one atom per iteration, k <= 32,
+                                       W <= 512 and batch a multiple of W, else CS_ENOTSUP. */
 } cs_clomp_params;
 
 typedef struct cs_plan cs_plan;

@@ -120,6 +120,7 @@ struct cs_plan {
         int bf16 = 0, gram = 0;
     } prep;
     const void* a_host = nullptr;   // set by the host-buffer solve around its call of solve()
+    int tv2d_ready = 0;             // image width whose cluster launch was checked
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -409,6 +410,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (cp->tv_weight > 0.f && cp->tv_D && (cp->tv_N < 2 || cp->tv_ldd < cp->tv_N))
             return fail(CS_EINVAL, "tv_D needs tv_N >= 2 and tv_ldd >= tv_N (tv_N=%d tv_ldd=%d)", cp->tv_N,
                         cp->tv_ldd);
+        if (cp->tv_width < 0) return fail(CS_EINVAL, "tv_width=%d must be >= 0", cp->tv_width);
     }
     if (B == 0) return CS_OK;
     DeviceGuard dg(P->device);
@@ -447,6 +449,21 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         st = ensure_tv(P, (size_t)n * tvEp);
         if (st != CS_OK) return st;
     }
+    // the image form of the prior (Eq. 6): images of tvW consecutive columns
+    const int tvW = tv ? cp->tv_width : 0;
+    const bool tv2d = tvW >= 2;
+    if (tv2d) {
+        if (c.th > 0.f || !clfit_tv2d_supported(a, tvW))
+            return fail(CS_ENOTSUP, "the image prior (tv_width=%d) needs one atom per iteration, k <= 32, "
+                                    "2 <= tv_width <= 512 and a batch of whole images (batch=%d)", tvW, B);
+        if (P->tv2d_ready != tvW) {
+            int ok = 0;
+            const cudaError_t e = clfit_tv2d_prepare(tvW, &ok);
+            if (e != cudaSuccess) return cuda_fail(e, "image prior: cluster check");
+            if (!ok) return fail(CS_ENOTSUP, "image prior: clusters for tv_width=%d do not fit this device", tvW);
+            P->tv2d_ready = tvW;
+        }
+    }
 
     // A prepared by an earlier solve of this plan (same A, generation != 0)
     const bool need_gram = a.GA && (a.need_gcol || a.need_gram);
@@ -460,8 +477,9 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
 
     // CLOMP in Gram form runs selection, fit and residual as one kernel, or
     // (bf16 correlation) the whole solve as one persistent kernel
-    const bool fused = cp && cp->form == CS_CL_GRAM && P->fuse_update && update_clomp_fused_supported(a);
-    const bool persist = cp && cp->form == CS_CL_GRAM && bf16 && P->persist && clomp_persist_supported(a, c);
+    const bool fused = cp && cp->form == CS_CL_GRAM && P->fuse_update && !tv2d && update_clomp_fused_supported(a);
+    const bool persist = cp && cp->form == CS_CL_GRAM && bf16 && P->persist && !tv2d &&
+                         clomp_persist_supported(a, c);
     // threshold rule: float32 correlation of every atom, then one fused
     // selection + fit + residual kernel per iteration
     const bool th_rule = cp && c.th > 0.f;
@@ -529,6 +547,10 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SELECT, st, [&] { return launch_select(a, st); }), "select");
             if (!cp)
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] { return launch_chol(a, st); }), "cholesky");
+            else if (tv2d)
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] {
+                                  return launch_clfit_tv2d(a, c, it, tvW, 2.f * cp->tv_weight / (float)tvW, st);
+                              }), "cl fit (image prior)");
             else if (cp->form == CS_CL_GRAM)
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] { return launch_clfit_gram(a, c, it, st); }), "cl fit (gram)");
             else
@@ -565,7 +587,8 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                              cp ? (double)cp->beta1 : 0.0, cp ? (double)cp->beta2 : 0.0,
                              cp ? (double)cp->eps : 0.0, cp ? (double)cp->reset_adam_each_iter : 0.0,
                              cp ? (double)cp->form : -1.0, cp ? (double)c.th : 0.0,
-                             tv ? (double)cp->tv_weight : 0.0, (double)tvN, tv ? (double)cp->tv_ldd : 0.0};
+                             tv ? (double)cp->tv_weight : 0.0, (double)tvN, tv ? (double)cp->tv_ldd : 0.0,
+                             (double)tvW};
         put(dk, sizeof(dk));
     }, P->use_graphs && !P->profiling && !(persist && P->stall_test));
     if (rs != CS_OK) P->prep = cs_plan::Prep{};

@@ -141,6 +141,11 @@ bool omp_fused_supported(const IterArgs& a);
 cudaError_t launch_omp_fused(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_resid(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_clfit_gram(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
+// CL fit with the image prior of Eq. 6 (k_tv2d.cu): images of W consecutive
+// columns, one thread-block cluster per image; lam_h = 2w/W.
+bool clfit_tv2d_supported(const IterArgs& a, int W);
+cudaError_t clfit_tv2d_prepare(int W, int* ok);
+cudaError_t launch_clfit_tv2d(const IterArgs& a, const ClArgs& c, int iter, int W, float lam_h, cudaStream_t s);
 cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 bool update_clomp_fused_supported(const IterArgs& a);
 cudaError_t launch_update_clomp(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
