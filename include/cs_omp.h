@@ -117,7 +117,7 @@ typedef struct {
                                        (N = n). */
     int32_t tv_N;                   /* N, the signal length (rows of tv_D, >= 2) */
     int32_t tv_ldd;
-    int32_t tv_width;               /* W.  0 or 1: the 1-D prior above on every column.
+    int32_t image_width;            /* W.  0 or 1: the 1-D prior above on every column.
                                        W >= 2 (with tv_weight > 0): the batch is a sequence
                                        of images of W consecutive columns (signal b is
                                        column b mod W of image b / W) and the prior is the

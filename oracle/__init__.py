@@ -66,12 +66,15 @@ def lib():
             L.cs_oracle_clomp.restype = ctypes.c_int
             L.cs_oracle_tv_loss_grad.argtypes = [pd, ctypes.c_int, ctypes.c_int, pi, ctypes.c_int, pd, d, pd]
             L.cs_oracle_tv_loss_grad.restype = d
-            L.cs_oracle_clomp_tv2d.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd,
-                                               ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, d,
-                                               ctypes.c_int, ctypes.c_int, d, d, d, d, ctypes.c_int, d,
-                                               pd, ctypes.c_int, ctypes.c_int, pi, pd, pi, pd, pi, pd,
-                                               pd, pd, ctypes.c_int]
-            L.cs_oracle_clomp_tv2d.restype = ctypes.c_int
+            L.cs_oracle_clomp_image.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd,
+                                                ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, d,
+                                                ctypes.c_int, ctypes.c_int, d, d, d, d, ctypes.c_int, d, d,
+                                                pd, ctypes.c_int, ctypes.c_int, pi, pd, pi, pd, pi, pd,
+                                                pd, pd, ctypes.c_int]
+            L.cs_oracle_clomp_image.restype = ctypes.c_int
+            L.cs_oracle_lv_loss_grad.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, pi, pi, pd, d, pd]
+            L.cs_oracle_lv_loss_grad.restype = d
             L.cs_oracle_tv2d_h_loss_grad.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, pi, pi, pd, d, pd]
             L.cs_oracle_tv2d_h_loss_grad.restype = d
@@ -182,11 +185,7 @@ def tv_loss_grad(D, n, support, s_S, w):
     return val, g
 
 
-def tv2d_h_loss_grad(D, n, supports, coefs, w):
-    """w * TV_h(I), the horizontal part of Eq. 6, for the image whose column j
-    is x_j = D[:, supports[j]] @ coefs[j] (D None: x_j = coefs[j] placed at
-    supports[j] in a length-n vector), and its gradient: a list of arrays,
-    one per column, w.r.t. coefs[j]."""
+def _image_loss_grad(fn, D, n, supports, coefs, w):
     W = len(supports)
     k = max(1, max(len(q) for q in supports))
     S = np.full((W, k), -1, np.int32)
@@ -202,13 +201,28 @@ def tv2d_h_loss_grad(D, n, supports, coefs, w):
     else:
         Df = _f64F(D)
         Dp, N = _p(Df, ctypes.c_double), Df.shape[0]
-    val = lib().cs_oracle_tv2d_h_loss_grad(Dp, N, N, W, k, _p(S, ctypes.c_int32), _p(t, ctypes.c_int32),
-                                          _p(C, ctypes.c_double), float(w), _p(G, ctypes.c_double))
+    val = fn(Dp, N, N, W, k, _p(S, ctypes.c_int32), _p(t, ctypes.c_int32), _p(C, ctypes.c_double),
+             float(w), _p(G, ctypes.c_double))
     return val, [G[j, :t[j]].copy() for j in range(W)]
 
 
+def tv2d_h_loss_grad(D, n, supports, coefs, w):
+    """w * TV_h(I), the horizontal part of Eq. 6, for the image whose column j
+    is x_j = D[:, supports[j]] @ coefs[j] (D None: x_j = coefs[j] placed at
+    supports[j] in a length-n vector), and its gradient: a list of arrays,
+    one per column, w.r.t. coefs[j]."""
+    return _image_loss_grad(lib().cs_oracle_tv2d_h_loss_grad, D, n, supports, coefs, w)
+
+
+def lv_loss_grad(D, n, supports, coefs, w):
+    """w * LV(I) of Eq. 7 (3 x 3 windows at every placement, sample standard
+    deviation) for the image of columns x_j as in tv2d_h_loss_grad, and its
+    gradient w.r.t. coefs[j]."""
+    return _image_loss_grad(lib().cs_oracle_lv_loss_grad, D, n, supports, coefs, w)
+
+
 def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
-          reset_adam=False, th=0.0, tv_weight=0.0, D=None, tv_width=0, nthreads=0):
+          reset_adam=False, th=0.0, tv_weight=0.0, D=None, image_width=0, lv_weight=0.0, nthreads=0):
     """CLOMP (structure 1, Adam) for every column of Y.  Returns a dict.
 
     th: 0 selects one atom per iteration (argmax); 0 < th < 1 selects every
@@ -216,9 +230,10 @@ def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0
     most k in total); n_iter then counts atoms.  top1/top2 of such picks hold
     1 and 1 - margin, margin being the smallest relative gap deciding the
     iteration's set and order.  tv_weight > 0 adds tv_weight * TV(D s) (Eq. 5)
-    to the fit's loss; D (N x n) None means x = s.  tv_width = W >= 1 reads
+    to the fit's loss; D (N x n) None means x = s.  image_width = W >= 1 reads
     the batch as images of W consecutive columns and uses the image form of
-    the prior (Eq. 6), which couples neighbouring columns in the fit."""
+    the prior (Eq. 6), which couples neighbouring columns in the fit;
+    lv_weight > 0 (with image_width) adds lv_weight * LV(I) of Eq. 7."""
     A = _f64F(A)
     Y = _f64F(Y if np.ndim(Y) == 2 else np.reshape(Y, (-1, 1)))
     m, n = A.shape
@@ -228,20 +243,22 @@ def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0
     Df = None if D is None else _f64F(D)
     Dp = None if Df is None else _p(Df, ctypes.c_double)
     N = n if Df is None else Df.shape[0]
-    if tv_width:
+    if lv_weight and not image_width:
+        raise ValueError("the local variation needs image_width")
+    if image_width:
         if th:
             raise ValueError("the image prior runs with one atom per iteration (th = 0)")
-        rc = lib().cs_oracle_clomp_tv2d(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B,
-                                        int(tv_width), k, float(tol), int(max_iter), int(steps), float(lr),
+        rc = lib().cs_oracle_clomp_image(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B,
+                                        int(image_width), k, float(tol), int(max_iter), int(steps), float(lr),
                                         float(beta1), float(beta2), float(eps), int(bool(reset_adam)),
-                                        float(tv_weight), Dp, int(N), int(N),
+                                        float(tv_weight), float(lv_weight), Dp, int(N), int(N),
                                         _p(o["support"], ctypes.c_int32), _p(o["coef"], ctypes.c_double),
                                         _p(o["n_iter"], ctypes.c_int32), _p(o["res_norm"], ctypes.c_double),
                                         _p(o["status"], ctypes.c_int32), _p(o["top1"], ctypes.c_double),
                                         _p(o["top2"], ctypes.c_double), _p(o["res_hist"], ctypes.c_double),
                                         int(nthreads))
         if rc != 0:
-            raise ValueError("cs_oracle_clomp_tv2d: invalid arguments")
+            raise ValueError("cs_oracle_clomp_image: invalid arguments")
         return o
     rc = lib().cs_oracle_clomp(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B, k,
                                float(tol), int(max_iter), int(steps), float(lr), float(beta1),

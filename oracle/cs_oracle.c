@@ -41,7 +41,8 @@
  *   - prior losses (Eq. 4-6) join the fit's loss with weight w: the 1-D total
  *     variation of each column x = D s (Eq. 5), or, for a batch of images of
  *     W consecutive columns, the image form (Eq. 6) whose horizontal part
- *     couples neighbouring columns; the columns of an image then take their
+ *     couples neighbouring columns, as does the local variation of Eq. 7
+ *     (standard deviations over 3 x 3 windows); the columns of an image then take their
  *     Adam steps together, each step's gradients from the coefficients
  *     before it.
  *
@@ -539,10 +540,85 @@ double cs_oracle_tv2d_h_loss_grad(const double* D, int N, int ldd, int W, int k,
 }
 
 /*
- * CLOMP on images with the total-variation prior of Eq. 6: the batch is a
- * sequence of images of W consecutive columns (B a multiple of W), and the
- * fit's loss of an image is
- *   sum_j 1/2 ||y_j - A (s_j .* Mask_j)||^2 + tv_w * TV(I),   I = [D s_1 ... D s_W],
+ * Local variation of an image (Eq. 7): the mean, over the 3 x 3 windows at
+ * every placement inside the image (sliding step 1, no padding; B = (N-2) *
+ * (W-2) windows), of the standard deviation of the window's nine pixels,
+ * taken with the sample normalisation (divide by 9 - 1):
+ *   LV = (1/B) sum_b sigma_b,  sigma_b = sqrt(sum_{p in b} (I_p - mu_b)^2 / 8).
+ * The columns are x_j = D s_j as in cs_oracle_tv2d_h_loss_grad.  Returns
+ * w * LV; when grad is not NULL adds w * dLV/ds (support entries only):
+ *   dLV/dI_p = (1/B) sum_{b containing p} (I_p - mu_b) / (8 sigma_b),
+ * a window with sigma_b = 0 contributing 0 (the subgradient at a constant
+ * window), and dLV/ds_{j,q} = D[:, S_{j,q}]^T dLV/dx_j.
+ */
+double cs_oracle_lv_loss_grad(const double* D, int N, int ldd, int W, int k, const int32_t* S,
+                              const int32_t* t, const double* s, double w, double* grad) {
+    if (w == 0.0 || N < 3 || W < 3) return 0.0;
+    double* x = (double*)calloc((size_t)N * W, sizeof(double));
+    double* gx = (double*)calloc((size_t)N * W, sizeof(double));
+    for (int j = 0; j < W; ++j) {
+        double* xj = x + (size_t)j * N;
+        for (int q = 0; q < t[j]; ++q) {
+            const int a = S[(size_t)j * k + q];
+            const double v = s[(size_t)j * k + q];
+            if (D) {
+                const double* da = D + (size_t)a * ldd;
+                for (int i = 0; i < N; ++i) xj[i] += v * da[i];
+            } else {
+                xj[a] += v;
+            }
+        }
+    }
+    const double nb = (double)(N - 2) * (double)(W - 2);
+    double lv = 0.0;
+    for (int c0 = 0; c0 + 2 < W; ++c0)
+        for (int r0 = 0; r0 + 2 < N; ++r0) {
+            double mu = 0.0;
+            for (int dc = 0; dc < 3; ++dc)
+                for (int dr = 0; dr < 3; ++dr) mu += x[(size_t)(c0 + dc) * N + r0 + dr];
+            mu /= 9.0;
+            double ss = 0.0;
+            for (int dc = 0; dc < 3; ++dc)
+                for (int dr = 0; dr < 3; ++dr) {
+                    const double d = x[(size_t)(c0 + dc) * N + r0 + dr] - mu;
+                    ss += d * d;
+                }
+            const double sigma = sqrt(ss / 8.0);
+            lv += sigma;
+            if (sigma > 0.0)
+                for (int dc = 0; dc < 3; ++dc)
+                    for (int dr = 0; dr < 3; ++dr) {
+                        const size_t p = (size_t)(c0 + dc) * N + r0 + dr;
+                        gx[p] += (x[p] - mu) / (8.0 * sigma) / nb;
+                    }
+        }
+    lv /= nb;
+    if (grad)
+        for (int j = 0; j < W; ++j) {
+            const double* gj = gx + (size_t)j * N;
+            for (int q = 0; q < t[j]; ++q) {
+                const int a = S[(size_t)j * k + q];
+                double g = 0.0;
+                if (D) {
+                    const double* da = D + (size_t)a * ldd;
+                    for (int i = 0; i < N; ++i) g += da[i] * gj[i];
+                } else {
+                    g = gj[a];
+                }
+                grad[(size_t)j * k + q] += w * g;
+            }
+        }
+    free(x);
+    free(gx);
+    return w * lv;
+}
+
+/*
+ * CLOMP on images with the image priors: the total variation of Eq. 6 and
+ * the local variation of Eq. 7.  The batch is a sequence of images of W
+ * consecutive columns (B a multiple of W), and the fit's loss of an image is
+ *   sum_j 1/2 ||y_j - A (s_j .* Mask_j)||^2 + tv_w TV(I) + lv_w LV(I),
+ *   I = [D s_1 ... D s_W],
  * which couples neighbouring columns.  Per iteration every live column
  * selects its atom from its own residual (as in cs_oracle_clomp), then all
  * live columns of the image take the `steps` Adam steps together: every
@@ -551,10 +627,10 @@ double cs_oracle_tv2d_h_loss_grad(const double* D, int N, int ldd, int W, int k,
  * Outputs, status codes and the remaining readings are those of
  * cs_oracle_clomp (one atom per iteration).
  */
-static void clomp_tv2d_image(const double* A, int m, int n, int lda, const double* Y, int ldy,
-                             int W, int k, double tol, int max_iter, int steps, double lr,
-                             double beta1, double beta2, double eps, int reset_adam, double tv_w,
-                             const double* D, int N, int ldd, int32_t* support, double* coef,
+static void clomp_image(const double* A, int m, int n, int lda, const double* Y, int ldy,
+                        int W, int k, double tol, int max_iter, int steps, double lr,
+                        double beta1, double beta2, double eps, int reset_adam, double tv_w,
+                        double lv_w, const double* D, int N, int ldd, int32_t* support, double* coef,
                              int32_t* n_iter, double* res_norm, int32_t* status, double* top1,
                              double* top2, double* res_hist) {
     double* r = (double*)malloc(sizeof(double) * (size_t)m * W);
@@ -616,6 +692,7 @@ static void clomp_tv2d_image(const double* A, int m, int n, int lda, const doubl
                 cs_oracle_tv_loss_grad(D, N, ldd, support + o, t, coef + o, tv_w, g + o);
             }
             cs_oracle_tv2d_h_loss_grad(D, N, ldd, W, k, support, n_iter, coef, tv_w, g);
+            cs_oracle_lv_loss_grad(D, N, ldd, W, k, support, n_iter, coef, lv_w, g);
             for (int j = 0; j < W; ++j) {
                 if (!fit[j]) continue;
                 const size_t o = (size_t)j * k;
@@ -650,16 +727,17 @@ static void clomp_tv2d_image(const double* A, int m, int n, int lda, const doubl
     free(r); free(mom); free(vel); free(g); free(rg); free(inS); free(tau); free(st); free(fit); free(rho);
 }
 
-/* The batch as B / W images of W columns each (see clomp_tv2d_image); the
- * prior's weight tv_w > 0, D as in cs_oracle_clomp. */
-int cs_oracle_clomp_tv2d(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
-                         int W, int k, double tol, int max_iter, int steps, double lr, double beta1,
-                         double beta2, double eps, int reset_adam, double tv_w, const double* D,
+/* The batch as B / W images of W columns each (see clomp_image); the priors'
+ * weights tv_w, lv_w >= 0, D as in cs_oracle_clomp. */
+int cs_oracle_clomp_image(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
+                          int W, int k, double tol, int max_iter, int steps, double lr, double beta1,
+                          double beta2, double eps, int reset_adam, double tv_w, double lv_w,
+                          const double* D,
                          int N, int ldd, int32_t* support, double* coef, int32_t* n_iter,
                          double* res_norm, int32_t* status, double* top1, double* top2,
                          double* res_hist, int nthreads) {
     if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0 || steps < 0) return -1;
-    if (W < 1 || B % W != 0 || !(tv_w >= 0.0) || (D && (N < 2 || ldd < N))) return -1;
+    if (W < 1 || B % W != 0 || !(tv_w >= 0.0) || !(lv_w >= 0.0) || (D && (N < 2 || ldd < N))) return -1;
     if (!D) N = n;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -667,9 +745,9 @@ int cs_oracle_clomp_tv2d(const double* A, int m, int n, int lda, const double* Y
 #endif
     for (int g = 0; g < B / W; ++g) {
         const size_t b0 = (size_t)g * W, o = b0 * k;
-        clomp_tv2d_image(A, m, n, lda, Y + b0 * ldy, ldy, W, k, tol, max_iter, steps, lr, beta1,
-                         beta2, eps, reset_adam, tv_w, D, N, ldd, support + o, coef + o, n_iter + b0,
-                         res_norm + b0, status + b0, top1 + o, top2 + o, res_hist + o);
+        clomp_image(A, m, n, lda, Y + b0 * ldy, ldy, W, k, tol, max_iter, steps, lr, beta1,
+                    beta2, eps, reset_adam, tv_w, lv_w, D, N, ldd, support + o, coef + o, n_iter + b0,
+                    res_norm + b0, status + b0, top1 + o, top2 + o, res_hist + o);
     }
     return 0;
 }

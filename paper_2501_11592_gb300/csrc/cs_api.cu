@@ -410,7 +410,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (cp->tv_weight > 0.f && cp->tv_D && (cp->tv_N < 2 || cp->tv_ldd < cp->tv_N))
             return fail(CS_EINVAL, "tv_D needs tv_N >= 2 and tv_ldd >= tv_N (tv_N=%d tv_ldd=%d)", cp->tv_N,
                         cp->tv_ldd);
-        if (cp->tv_width < 0) return fail(CS_EINVAL, "tv_width=%d must be >= 0", cp->tv_width);
+        if (cp->image_width < 0) return fail(CS_EINVAL, "image_width=%d must be >= 0", cp->image_width);
     }
     if (B == 0) return CS_OK;
     DeviceGuard dg(P->device);
@@ -450,17 +450,17 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (st != CS_OK) return st;
     }
     // the image form of the prior (Eq. 6): images of tvW consecutive columns
-    const int tvW = tv ? cp->tv_width : 0;
+    const int tvW = tv ? cp->image_width : 0;
     const bool tv2d = tvW >= 2;
     if (tv2d) {
         if (c.th > 0.f || !clfit_tv2d_supported(a, tvW))
-            return fail(CS_ENOTSUP, "the image prior (tv_width=%d) needs one atom per iteration, k <= 32, "
-                                    "2 <= tv_width <= 512 and a batch of whole images (batch=%d)", tvW, B);
+            return fail(CS_ENOTSUP, "the image prior (image_width=%d) needs one atom per iteration, k <= 32, "
+                                    "2 <= image_width <= 512 and a batch of whole images (batch=%d)", tvW, B);
         if (P->tv2d_ready != tvW) {
             int ok = 0;
             const cudaError_t e = clfit_tv2d_prepare(tvW, &ok);
             if (e != cudaSuccess) return cuda_fail(e, "image prior: cluster check");
-            if (!ok) return fail(CS_ENOTSUP, "image prior: clusters for tv_width=%d do not fit this device", tvW);
+            if (!ok) return fail(CS_ENOTSUP, "image prior: clusters for image_width=%d do not fit this device", tvW);
             P->tv2d_ready = tvW;
         }
     }

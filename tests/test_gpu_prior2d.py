@@ -1,4 +1,4 @@
-"""GPU parity of the image total-variation prior of Eq. 6 (tv_width = W: the
+"""GPU parity of the image total-variation prior of Eq. 6 (image_width = W: the
 batch is images of W consecutive columns whose Adam steps are coupled by the
 horizontal differences) against the FP64 oracle."""
 import numpy as np
@@ -28,7 +28,7 @@ def gpu_solve(cs, torch, A32, Y32, k, W, prec="bf16", D32=None, graphs=1, **kw):
     plan.set_option(cs.OPT_GRAPHS, graphs)
     cl = dict(CL)
     cl.update(kw)
-    r = cs.clomp_solve_batched(A, Y, k, prec=prec, form="gram", plan=plan, D=D, tv_width=W, **cl)
+    r = cs.clomp_solve_batched(A, Y, k, prec=prec, form="gram", plan=plan, D=D, image_width=W, **cl)
     torch.cuda.synchronize()
     assert plan.counters()[1] == 0
     out = to_numpy(r)
@@ -41,7 +41,7 @@ def oracle_2d(A64, Y64, k, w, W, D64=None, **kw):
     p.update({q: f32(v) for q, v in kw.items() if q in p})
     rest = {q: v for q, v in kw.items() if q in ("tol", "max_iter")}
     return oracle.clomp(A64, Y64, k, steps=kw.get("steps", CL["steps"]), tv_weight=f32(w), D=D64,
-                        tv_width=W, **rest, **p)
+                        image_width=W, **rest, **p)
 
 
 @pytest.mark.parametrize("W,images,prec", [(24, 4, "bf16"), (24, 4, "fp32"), (2, 7, "bf16"),
@@ -124,19 +124,19 @@ def test_image_prior_limits(cs_gpu, torch):
     A = torch.from_numpy(A32).cuda()
     Y = torch.from_numpy(Y32).cuda()
     cs = cs_gpu
-    for bad in (dict(tv_width=7),                            # 30 columns are not whole images
-                dict(tv_width=10, th=0.7, prec="fp32"),      # one atom per iteration only
-                dict(tv_width=1000)):                        # wider than 512
+    for bad in (dict(image_width=7),                            # 30 columns are not whole images
+                dict(image_width=10, th=0.7, prec="fp32"),      # one atom per iteration only
+                dict(image_width=1000)):                        # wider than 512
         kw = dict(prec="bf16", tv_weight=0.5)
         kw.update(bad)
         with pytest.raises(cs.CSError) as e:
             cs.clomp_solve_batched(A, Y, 6, **kw)
         assert e.value.code == cs.CS_ENOTSUP, bad
     with pytest.raises(cs.CSError) as e:
-        cs.clomp_solve_batched(A, Y, 6, prec="bf16", tv_weight=0.5, tv_width=-1)
+        cs.clomp_solve_batched(A, Y, 6, prec="bf16", tv_weight=0.5, image_width=-1)
     assert e.value.code == cs.CS_EINVAL
     # without a prior weight the width changes nothing
-    a = to_numpy(cs.clomp_solve_batched(A, Y, 6, prec="bf16", tv_width=10))
+    a = to_numpy(cs.clomp_solve_batched(A, Y, 6, prec="bf16", image_width=10))
     b = to_numpy(cs.clomp_solve_batched(A, Y, 6, prec="bf16"))
     for q in ("support", "coef", "n_iter", "status"):
         assert np.array_equal(a[q], b[q]), q

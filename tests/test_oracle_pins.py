@@ -554,7 +554,7 @@ def test_clomp_with_tv_prior_is_adam_on_the_prior_loss():
 
 
 # Total variation of an image (Eq. 6) in the CL fit: oracle.tv2d_h_loss_grad
-# (the horizontal part) and clomp(tv_width=W), which fits the W columns of an
+# (the horizontal part) and clomp(image_width=W), which fits the W columns of an
 # image together
 
 def test_tv2d_horizontal_closed_forms():
@@ -629,7 +629,7 @@ def test_clomp_tv2d_is_adam_on_the_image_loss():
     A = _rand_A(rng, m, n)
     D = workloads.dct_synthesis(n)
     Y = rng.standard_normal((m, W))
-    o = oracle.clomp(A, Y, k, steps=T, lr=3e-2, tv_weight=w, D=D, tv_width=W)
+    o = oracle.clomp(A, Y, k, steps=T, lr=3e-2, tv_weight=w, D=D, image_width=W)
     assert np.all(o["status"] == 0) and np.all(o["n_iter"] == k)
     P = torch.zeros((n, W), dtype=torch.float64, requires_grad=True)
     opt = torch.optim.Adam([P], lr=3e-2, foreach=False)
@@ -667,14 +667,116 @@ def test_clomp_tv2d_reductions():
     D = workloads.dct_synthesis(n)
     y = rng.standard_normal(m)
     Y = np.repeat(y[:, None], 6, axis=1)
-    a = oracle.clomp(A, Y, k, steps=30, tv_weight=0.8, D=D, tv_width=3)
+    a = oracle.clomp(A, Y, k, steps=30, tv_weight=0.8, D=D, image_width=3)
     b = oracle.clomp(A, Y, k, steps=30, tv_weight=0.8, D=D)
     assert np.array_equal(a["support"], b["support"])
     np.testing.assert_allclose(a["coef"], b["coef"], rtol=0, atol=1e-15)
     Y2 = rng.standard_normal((m, 4))
-    a = oracle.clomp(A, Y2, k, steps=30, tv_weight=0.8, D=D, tv_width=1)
+    a = oracle.clomp(A, Y2, k, steps=30, tv_weight=0.8, D=D, image_width=1)
     b = oracle.clomp(A, Y2, k, steps=30, tv_weight=0.8, D=D)
     assert np.array_equal(a["support"], b["support"]) and np.array_equal(a["coef"], b["coef"])
-    a = oracle.clomp(A, Y2, k, steps=30, tv_weight=0.0, D=D, tv_width=2)
+    a = oracle.clomp(A, Y2, k, steps=30, tv_weight=0.0, D=D, image_width=2)
     b = oracle.clomp(A, Y2, k, steps=30)
     assert np.array_equal(a["support"], b["support"]) and np.array_equal(a["coef"], b["coef"])
+
+
+# Local variation of Eq. 7 (oracle.lv_loss_grad, clomp(lv_weight, image_width))
+
+def test_lv_closed_forms():
+    """3 x 3 windows at every placement, sample standard deviation: a ramp of
+    step c along either axis puts {0, c, 2c} three times in every window, so
+    each window's deviation is c sqrt(6/8) and so is their mean; a constant
+    image has LV = 0 and zero gradient; a single 3 x 3 image is the sample
+    standard deviation of its nine pixels (numpy, ddof=1)."""
+    n, W, c, w = 7, 6, 0.4, 1.9
+    full = list(range(n))
+    val, g = oracle.lv_loss_grad(None, n, [full] * W, [c * j * np.ones(n) for j in range(W)], w)
+    assert abs(val - w * c * math.sqrt(0.75)) < 1e-14
+    val, _ = oracle.lv_loss_grad(None, n, [full] * W, [c * np.arange(n) for _ in range(W)], w)
+    assert abs(val - w * c * math.sqrt(0.75)) < 1e-14
+    val, g = oracle.lv_loss_grad(None, n, [full] * W, [2.5 * np.ones(n) for _ in range(W)], w)
+    assert val == 0.0 and all(np.all(q == 0.0) for q in g)
+    rng = np.random.default_rng(180)
+    v = rng.standard_normal((3, 3))
+    val, _ = oracle.lv_loss_grad(None, 3, [[0, 1, 2]] * 3, [v[:, j] for j in range(3)], 1.0)
+    assert abs(val - np.std(v, ddof=1)) < 1e-14
+    # fewer than three rows or columns: no window
+    assert oracle.lv_loss_grad(None, n, [full] * 2, [np.ones(n), -np.ones(n)], w)[0] == 0.0
+
+
+def test_lv_gradient_matches_central_differences():
+    """LV is smooth where no window is constant: central differences of
+    w LV(I), I = [D s_1 .. D s_W] with a general basis, to 1e-7."""
+    rng = np.random.default_rng(181)
+    n, H, W, w = 9, 8, 5, 1.3
+    D = rng.standard_normal((H, n))
+    sup = [np.array([3, 1, 8], np.int32), np.array([1, 5], np.int32), np.array([8, 3, 0, 6], np.int32),
+           np.array([2], np.int32), np.array([7, 4], np.int32)]
+    coefs = [rng.standard_normal(len(q)) for q in sup]
+
+    def lv(cs):
+        I = np.stack([D[:, q] @ v for q, v in zip(sup, cs)], axis=1)
+        sig = [np.std(I[r:r + 3, c:c + 3], ddof=1) for r in range(H - 2) for c in range(W - 2)]
+        return w * np.mean(sig)
+
+    val, g = oracle.lv_loss_grad(D, n, sup, coefs, w)
+    assert abs(val - lv(coefs)) < 1e-13
+    h = 1e-5
+    for j in range(W):
+        fd = []
+        for e in np.eye(len(sup[j])):
+            up = [v.copy() for v in coefs]
+            dn = [v.copy() for v in coefs]
+            up[j] += h * e
+            dn[j] -= h * e
+            fd.append((lv(up) - lv(dn)) / (2 * h))
+        np.testing.assert_allclose(g[j], fd, rtol=1e-6, atol=1e-9)
+
+
+def test_clomp_lv_is_adam_on_the_image_loss():
+    """CLOMP with both image priors: one torch Adam run (float64, autograd)
+    over the n x W coefficients, loss data + w_tv TV(I) + w_lv LV(I); a
+    constant window (all pixels zero at the start) contributes no gradient."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(182)
+    m, n, W, k, T, wt, wl = 16, 32, 6, 4, 20, 0.4, 0.9
+    A = _rand_A(rng, m, n)
+    D = workloads.dct_synthesis(n)
+    Y = rng.standard_normal((m, W))
+    o = oracle.clomp(A, Y, k, steps=T, lr=3e-2, tv_weight=wt, lv_weight=wl, D=D, image_width=W)
+    assert np.all(o["status"] == 0) and np.all(o["n_iter"] == k)
+    P = torch.zeros((n, W), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([P], lr=3e-2, foreach=False)
+    At = torch.tensor(A, dtype=torch.float64)
+    Dt = torch.tensor(D, dtype=torch.float64)
+    Yt = torch.tensor(Y, dtype=torch.float64)
+    mask = torch.zeros((n, W), dtype=torch.float64)
+
+    def lv(I):
+        win = I.unfold(0, 3, 1).unfold(1, 3, 1).reshape(-1, 9)       # every 3 x 3 placement
+        var = torch.sum((win - win.mean(dim=1, keepdim=True)) ** 2, dim=1) / 8.0
+        sig = torch.where(var > 0, torch.sqrt(torch.clamp(var, min=1e-300)), torch.zeros_like(var))
+        return sig.mean()
+
+    for t in range(k):
+        R = (Yt - At @ (P * mask)).detach()
+        C = (At.T @ R).abs().numpy()
+        C[mask.numpy() > 0] = -1
+        for j in range(W):
+            assert int(np.argmax(C[:, j])) == o["support"][j, t]
+            mask[o["support"][j, t], j] = 1.0
+        for _ in range(T):
+            opt.zero_grad()
+            V = P * mask
+            I = Dt @ V
+            tv = torch.sum((I[1:, :] - I[:-1, :]) ** 2) / n + torch.sum((I[:, 1:] - I[:, :-1]) ** 2) / W
+            loss = 0.5 * torch.sum((Yt - At @ V) ** 2) + wt * tv + wl * lv(I)
+            loss.backward()
+            opt.step()
+    Pn = P.detach().numpy()
+    for j in range(W):
+        np.testing.assert_allclose(o["coef"][j], Pn[o["support"][j], j], rtol=0, atol=1e-12)
+    # w_lv = 0 is the image TV alone
+    a = oracle.clomp(A, Y, k, steps=T, lr=3e-2, tv_weight=wt, lv_weight=0.0, D=D, image_width=W)
+    b = oracle.clomp(A, Y, k, steps=T, lr=3e-2, tv_weight=wt, D=D, image_width=W)
+    assert np.array_equal(a["coef"], b["coef"])
