@@ -327,10 +327,12 @@ def main():
         Dc = torch.from_numpy(np.asfortranarray(pc.meta["D"], dtype=np.float32)).cuda()
         Rc = torch.from_numpy(np.asfortranarray(pc.meta["X_img"], dtype=np.float32)).cuda()
         planc = cs.Plan(pc.A.shape[0], pc.A.shape[1], pc.Y.shape[1], pc.k)
-        # (the prior's weight, 0: none; image form of the prior, Eq. 6)
-        for tvw, img in ((0.0, False), (32.0, False), (32.0, True)):
+        # (the TV prior's weight, 0: none; its image form, Eq. 6; the LV prior's
+        # weight, Eq. 7)
+        for tvw, img, lvw in ((0.0, False, 0.0), (32.0, False, 0.0), (32.0, True, 0.0), (0.0, True, 40.0)):
             fnc = lambda: cs.reconstruct_columnwise(Ac, Dc, Yc, pc.k, 256, ref=Rc, algo="clomp", prec="bf16",
-                                                    plan=planc, tv_weight=tvw, image_prior=img, **CL)
+                                                    plan=planc, tv_weight=tvw, image_prior=img, lv_weight=lvw,
+                                                    **CL)
             for _ in range(3):
                 rc = fnc()
             barrier()
@@ -344,7 +346,8 @@ def main():
                 barrier()
                 tc_ms.append(a_.elapsed_time(b_))
             mc = float(np.mean(tc_ms))
-            key = "columnwise_2d_sr0.3" + ("" if tvw == 0.0 else "_tv%g" % tvw) + ("_image" if img else "")
+            key = ("columnwise_2d_sr0.3" + ("" if tvw == 0.0 else "_tv%g" % tvw)
+                   + ("_image" if img and tvw else "") + ("" if lvw == 0.0 else "_lv%g" % lvw))
             compare[key] = {
                 "ms_per_step": mc, "images_per_s": ws * 64 / (mc / 1e3),
                 "columns_per_s": ws * pc.Y.shape[1] / (mc / 1e3),
@@ -352,7 +355,9 @@ def main():
                 "note": ("64 images 256x256, m=77, k=25: CLOMP (bf16) + x = D s + PSNR/SSIM per image"
                          + ("" if tvw == 0.0 or img else "; total-variation prior (Eq. 5) on x = D s, w = %g" % tvw)
                          + ("; image total-variation prior (Eq. 6), w = %g: per-iteration kernels, the fit one "
-                            "cluster per image" % tvw if img else ""))}
+                            "cluster per image" % tvw if img and tvw else "")
+                         + ("; local-variation prior (Eq. 7, 3x3 windows), w = %g: per-iteration kernels, the "
+                            "fit one cluster per image synthesising D s every Adam step" % lvw if lvw else ""))}
         del planc
         # the column-wise workload at the other sampling rates (Sr = 0.5: k = 42
         # runs on the per-iteration kernels)

@@ -114,7 +114,7 @@ typedef struct {
                                        the data term. */
     const float* tv_D;              /* N x n sparsifying basis (device, column-major,
                                        leading dimension tv_ldd >= N), x = D s; NULL: x = s
-                                       (N = n). */
+                                       (N = n).  Used by both priors. */
     int32_t tv_N;                   /* N, the signal length (rows of tv_D, >= 2) */
     int32_t tv_ldd;
     int32_t image_width;            /* W.  0 or 1: the 1-D prior above on every column.
@@ -131,7 +131,26 @@ typedef struct {
                                        orthonormal columns (D^T D = I, e.g. the DCT) or NULL.
                                        Runs the per-iteration kernels (not the persistent
                                        solve); needs one atom per iteration, k <= 32,
-                                       W <= 512 and batch a multiple of W, else CS_ENOTSUP. */
+                                       W <= 512 and batch a multiple of W, else CS_ENOTSUP.
+                                       With lv_weight > 0 it is the width of the images the
+                                       local variation is taken over. */
+    float lv_weight;                /* w_lv >= 0: adds w_lv * LV(I) to the fit's loss, the
+                                       local variation of an image (Eq. 7): the mean, over
+                                       the 3 x 3 windows at every placement inside the
+                                       image, of the window's sample standard deviation
+                                       (nine pixels, divided by 8, smoothed as
+                                       sqrt(var + lv_eps^2)), I = [D s_1 ... D s_W]
+                                       (tv_D with any columns, or NULL: x = s; its N <= 256
+                                       pixels per column).  A constant window adds no
+                                       gradient.  Needs image_width >= 2 (CS_EINVAL
+                                       otherwise; widths or heights below 3 have no window)
+                                       and the limits of image_width above. */
+    float lv_eps;                   /* >= 0: the deviation's smoothing.  With 0 (the plain
+                                       deviation) the fit is ill-conditioned where windows
+                                       are nearly constant: the deviation's gradient there
+                                       follows the pixels' rounding.  Choose it small
+                                       against the pixels' scale (the Python binding uses
+                                       1e-4). */
 } cs_clomp_params;
 
 typedef struct cs_plan cs_plan;

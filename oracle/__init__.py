@@ -68,12 +68,12 @@ def lib():
             L.cs_oracle_tv_loss_grad.restype = d
             L.cs_oracle_clomp_image.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd,
                                                 ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, d,
-                                                ctypes.c_int, ctypes.c_int, d, d, d, d, ctypes.c_int, d, d,
+                                                ctypes.c_int, ctypes.c_int, d, d, d, d, ctypes.c_int, d, d, d,
                                                 pd, ctypes.c_int, ctypes.c_int, pi, pd, pi, pd, pi, pd,
                                                 pd, pd, ctypes.c_int]
             L.cs_oracle_clomp_image.restype = ctypes.c_int
             L.cs_oracle_lv_loss_grad.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int,
-                                                 ctypes.c_int, pi, pi, pd, d, pd]
+                                                 ctypes.c_int, pi, pi, pd, d, d, pd]
             L.cs_oracle_lv_loss_grad.restype = d
             L.cs_oracle_tv2d_h_loss_grad.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, pi, pi, pd, d, pd]
@@ -185,7 +185,7 @@ def tv_loss_grad(D, n, support, s_S, w):
     return val, g
 
 
-def _image_loss_grad(fn, D, n, supports, coefs, w):
+def _image_loss_grad(fn, D, n, supports, coefs, w, *extra):
     W = len(supports)
     k = max(1, max(len(q) for q in supports))
     S = np.full((W, k), -1, np.int32)
@@ -202,7 +202,7 @@ def _image_loss_grad(fn, D, n, supports, coefs, w):
         Df = _f64F(D)
         Dp, N = _p(Df, ctypes.c_double), Df.shape[0]
     val = fn(Dp, N, N, W, k, _p(S, ctypes.c_int32), _p(t, ctypes.c_int32), _p(C, ctypes.c_double),
-             float(w), _p(G, ctypes.c_double))
+             float(w), *[float(e) for e in extra], _p(G, ctypes.c_double))
     return val, [G[j, :t[j]].copy() for j in range(W)]
 
 
@@ -214,15 +214,16 @@ def tv2d_h_loss_grad(D, n, supports, coefs, w):
     return _image_loss_grad(lib().cs_oracle_tv2d_h_loss_grad, D, n, supports, coefs, w)
 
 
-def lv_loss_grad(D, n, supports, coefs, w):
+def lv_loss_grad(D, n, supports, coefs, w, eps=0.0):
     """w * LV(I) of Eq. 7 (3 x 3 windows at every placement, sample standard
-    deviation) for the image of columns x_j as in tv2d_h_loss_grad, and its
-    gradient w.r.t. coefs[j]."""
-    return _image_loss_grad(lib().cs_oracle_lv_loss_grad, D, n, supports, coefs, w)
+    deviation smoothed as sqrt(var + eps^2)) for the image of columns x_j as
+    in tv2d_h_loss_grad, and its gradient w.r.t. coefs[j]."""
+    return _image_loss_grad(lib().cs_oracle_lv_loss_grad, D, n, supports, coefs, w, eps)
 
 
 def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0.999, eps=1e-8,
-          reset_adam=False, th=0.0, tv_weight=0.0, D=None, image_width=0, lv_weight=0.0, nthreads=0):
+          reset_adam=False, th=0.0, tv_weight=0.0, D=None, image_width=0, lv_weight=0.0, lv_eps=0.0,
+          nthreads=0):
     """CLOMP (structure 1, Adam) for every column of Y.  Returns a dict.
 
     th: 0 selects one atom per iteration (argmax); 0 < th < 1 selects every
@@ -233,7 +234,8 @@ def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0
     to the fit's loss; D (N x n) None means x = s.  image_width = W >= 1 reads
     the batch as images of W consecutive columns and uses the image form of
     the prior (Eq. 6), which couples neighbouring columns in the fit;
-    lv_weight > 0 (with image_width) adds lv_weight * LV(I) of Eq. 7."""
+    lv_weight > 0 (with image_width) adds lv_weight * LV(I) of Eq. 7, each
+    window's deviation smoothed as sqrt(var + lv_eps^2)."""
     A = _f64F(A)
     Y = _f64F(Y if np.ndim(Y) == 2 else np.reshape(Y, (-1, 1)))
     m, n = A.shape
@@ -251,7 +253,7 @@ def clomp(A, Y, k, tol=0.0, max_iter=None, steps=50, lr=1e-2, beta1=0.9, beta2=0
         rc = lib().cs_oracle_clomp_image(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B,
                                         int(image_width), k, float(tol), int(max_iter), int(steps), float(lr),
                                         float(beta1), float(beta2), float(eps), int(bool(reset_adam)),
-                                        float(tv_weight), float(lv_weight), Dp, int(N), int(N),
+                                        float(tv_weight), float(lv_weight), float(lv_eps), Dp, int(N), int(N),
                                         _p(o["support"], ctypes.c_int32), _p(o["coef"], ctypes.c_double),
                                         _p(o["n_iter"], ctypes.c_int32), _p(o["res_norm"], ctypes.c_double),
                                         _p(o["status"], ctypes.c_int32), _p(o["top1"], ctypes.c_double),

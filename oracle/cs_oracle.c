@@ -543,16 +543,17 @@ double cs_oracle_tv2d_h_loss_grad(const double* D, int N, int ldd, int W, int k,
  * Local variation of an image (Eq. 7): the mean, over the 3 x 3 windows at
  * every placement inside the image (sliding step 1, no padding; B = (N-2) *
  * (W-2) windows), of the standard deviation of the window's nine pixels,
- * taken with the sample normalisation (divide by 9 - 1):
- *   LV = (1/B) sum_b sigma_b,  sigma_b = sqrt(sum_{p in b} (I_p - mu_b)^2 / 8).
+ * taken with the sample normalisation (divide by 9 - 1) and smoothed by eps:
+ *   LV = (1/B) sum_b sigma_b,  sigma_b = sqrt(sum_{p in b} (I_p - mu_b)^2 / 8 + eps^2)
+ * (eps = 0: the plain deviation).
  * The columns are x_j = D s_j as in cs_oracle_tv2d_h_loss_grad.  Returns
  * w * LV; when grad is not NULL adds w * dLV/ds (support entries only):
  *   dLV/dI_p = (1/B) sum_{b containing p} (I_p - mu_b) / (8 sigma_b),
- * a window with sigma_b = 0 contributing 0 (the subgradient at a constant
- * window), and dLV/ds_{j,q} = D[:, S_{j,q}]^T dLV/dx_j.
+ * a window with sigma_b = 0 (constant, eps = 0) contributing 0 (the
+ * subgradient there), and dLV/ds_{j,q} = D[:, S_{j,q}]^T dLV/dx_j.
  */
 double cs_oracle_lv_loss_grad(const double* D, int N, int ldd, int W, int k, const int32_t* S,
-                              const int32_t* t, const double* s, double w, double* grad) {
+                              const int32_t* t, const double* s, double w, double eps, double* grad) {
     if (w == 0.0 || N < 3 || W < 3) return 0.0;
     double* x = (double*)calloc((size_t)N * W, sizeof(double));
     double* gx = (double*)calloc((size_t)N * W, sizeof(double));
@@ -583,7 +584,7 @@ double cs_oracle_lv_loss_grad(const double* D, int N, int ldd, int W, int k, con
                     const double d = x[(size_t)(c0 + dc) * N + r0 + dr] - mu;
                     ss += d * d;
                 }
-            const double sigma = sqrt(ss / 8.0);
+            const double sigma = sqrt(ss / 8.0 + eps * eps);
             lv += sigma;
             if (sigma > 0.0)
                 for (int dc = 0; dc < 3; ++dc)
@@ -630,9 +631,9 @@ double cs_oracle_lv_loss_grad(const double* D, int N, int ldd, int W, int k, con
 static void clomp_image(const double* A, int m, int n, int lda, const double* Y, int ldy,
                         int W, int k, double tol, int max_iter, int steps, double lr,
                         double beta1, double beta2, double eps, int reset_adam, double tv_w,
-                        double lv_w, const double* D, int N, int ldd, int32_t* support, double* coef,
-                             int32_t* n_iter, double* res_norm, int32_t* status, double* top1,
-                             double* top2, double* res_hist) {
+                        double lv_w, double lv_eps, const double* D, int N, int ldd, int32_t* support,
+                        double* coef, int32_t* n_iter, double* res_norm, int32_t* status, double* top1,
+                        double* top2, double* res_hist) {
     double* r = (double*)malloc(sizeof(double) * (size_t)m * W);
     double* mom = (double*)calloc((size_t)k * W, sizeof(double));
     double* vel = (double*)calloc((size_t)k * W, sizeof(double));
@@ -692,7 +693,7 @@ static void clomp_image(const double* A, int m, int n, int lda, const double* Y,
                 cs_oracle_tv_loss_grad(D, N, ldd, support + o, t, coef + o, tv_w, g + o);
             }
             cs_oracle_tv2d_h_loss_grad(D, N, ldd, W, k, support, n_iter, coef, tv_w, g);
-            cs_oracle_lv_loss_grad(D, N, ldd, W, k, support, n_iter, coef, lv_w, g);
+            cs_oracle_lv_loss_grad(D, N, ldd, W, k, support, n_iter, coef, lv_w, lv_eps, g);
             for (int j = 0; j < W; ++j) {
                 if (!fit[j]) continue;
                 const size_t o = (size_t)j * k;
@@ -728,16 +729,19 @@ static void clomp_image(const double* A, int m, int n, int lda, const double* Y,
 }
 
 /* The batch as B / W images of W columns each (see clomp_image); the priors'
- * weights tv_w, lv_w >= 0, D as in cs_oracle_clomp. */
+ * weights tv_w, lv_w >= 0, the deviation's smoothing lv_eps >= 0 (see
+ * cs_oracle_lv_loss_grad), D as in cs_oracle_clomp. */
 int cs_oracle_clomp_image(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
                           int W, int k, double tol, int max_iter, int steps, double lr, double beta1,
                           double beta2, double eps, int reset_adam, double tv_w, double lv_w,
-                          const double* D,
+                          double lv_eps, const double* D,
                          int N, int ldd, int32_t* support, double* coef, int32_t* n_iter,
                          double* res_norm, int32_t* status, double* top1, double* top2,
                          double* res_hist, int nthreads) {
     if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0 || steps < 0) return -1;
-    if (W < 1 || B % W != 0 || !(tv_w >= 0.0) || !(lv_w >= 0.0) || (D && (N < 2 || ldd < N))) return -1;
+    if (W < 1 || B % W != 0 || !(tv_w >= 0.0) || !(lv_w >= 0.0) || !(lv_eps >= 0.0) ||
+        (D && (N < 2 || ldd < N)))
+        return -1;
     if (!D) N = n;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
@@ -746,7 +750,7 @@ int cs_oracle_clomp_image(const double* A, int m, int n, int lda, const double* 
     for (int g = 0; g < B / W; ++g) {
         const size_t b0 = (size_t)g * W, o = b0 * k;
         clomp_image(A, m, n, lda, Y + b0 * ldy, ldy, W, k, tol, max_iter, steps, lr, beta1,
-                    beta2, eps, reset_adam, tv_w, lv_w, D, N, ldd, support + o, coef + o, n_iter + b0,
+                    beta2, eps, reset_adam, tv_w, lv_w, lv_eps, D, N, ldd, support + o, coef + o, n_iter + b0,
                     res_norm + b0, status + b0, top1 + o, top2 + o, res_hist + o);
     }
     return 0;

@@ -62,7 +62,7 @@ class ClompParams(ctypes.Structure):
                 ("reset_adam_each_iter", ctypes.c_int32), ("form", ctypes.c_int32),
                 ("select_threshold", ctypes.c_float), ("tv_weight", ctypes.c_float),
                 ("tv_D", ctypes.c_void_p), ("tv_N", ctypes.c_int32), ("tv_ldd", ctypes.c_int32),
-                ("image_width", ctypes.c_int32)]
+                ("image_width", ctypes.c_int32), ("lv_weight", ctypes.c_float), ("lv_eps", ctypes.c_float)]
 
 
 _lib = None
@@ -249,14 +249,14 @@ def _omp_params(k, tol, max_iter, prec, topc):
 
 
 def _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps, reset_adam, form, th=0.0,
-                  tv_weight=0.0, D=None, image_width=0):
+                  tv_weight=0.0, D=None, image_width=0, lv_weight=0.0, lv_eps=1e-4):
     Dp, N, ldd = None, 0, 0
     if D is not None:
         N, ldd = int(D.shape[0]), _ld(D)
         Dp = ctypes.c_void_p(D.data_ptr())
     return ClompParams(_omp_params(k, tol, max_iter, prec, topc), int(steps), float(lr), float(beta1),
                        float(beta2), float(eps), int(bool(reset_adam)), FORM[form], float(th),
-                       float(tv_weight), Dp, N, ldd, int(image_width))
+                       float(tv_weight), Dp, N, ldd, int(image_width), float(lv_weight), float(lv_eps))
 
 
 def _batched(fn, A, Y, k, params, plan, stream, out):
@@ -286,16 +286,19 @@ def omp_solve_batched(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, plan
 def clomp_solve_batched(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, steps=50, lr=1e-2,
                         beta1=0.9, beta2=0.999, eps=1e-8, reset_adam=False, form="gram",
                         plan=None, stream=None, out=None, th=0.0, tv_weight=0.0, D=None,
-                        image_width=0) -> Result:
+                        image_width=0, lv_weight=0.0, lv_eps=1e-4) -> Result:
     """Batched CLOMP (structure 1, Adam) on the current stream; th: the
     selection threshold Th (0: one atom per iteration); tv_weight, D: the
     total-variation prior of Eq. 5 on x = D s (D None: x = s); image_width W >= 2:
     the batch is images of W consecutive columns and the prior is that of an
-    image (Eq. 6; D with orthonormal columns or None)."""
+    image (Eq. 6; D with orthonormal columns or None); lv_weight: the local
+    variation of Eq. 7 over those images (any D), each window's deviation
+    smoothed as sqrt(var + lv_eps^2)."""
     Dt = None if D is None else _colmajor(D, _torch().float32)
     return _batched(load().clomp_solve_batched, A, Y, k,
                     _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
-                                  reset_adam, form, th, tv_weight, Dt, image_width), plan, stream, out)
+                                  reset_adam, form, th, tv_weight, Dt, image_width, lv_weight, lv_eps), plan,
+                    stream, out)
 
 
 def omp_solve(A, y, k, **kw) -> Result:
@@ -448,11 +451,12 @@ def reconstruct_columnwise(A, D, Y, k, W, ref=None, algo="clomp", prec="bf16", p
     image columns x = D s, and, given the reference images, their PSNR and
     SSIM.  Y: (m, count * W); tv_weight > 0 (CLOMP) adds the total-variation
     prior of Eq. 5 on each column x = D s, or with image_prior=True that of
-    the whole image (Eq. 6).  Returns dict(X, result, psnr, ssim)."""
+    the whole image (Eq. 6); lv_weight > 0 adds the local variation of Eq. 7
+    over each image.  Returns dict(X, result, psnr, ssim)."""
     fn = clomp_solve_batched if algo == "clomp" else omp_solve_batched
-    if algo == "clomp" and kw.get("tv_weight", 0.0) > 0.0:
-        kw.setdefault("D", D)       # the prior acts on the image columns x = D s
-        if image_prior:
+    if algo == "clomp" and (kw.get("tv_weight", 0.0) > 0.0 or kw.get("lv_weight", 0.0) > 0.0):
+        kw.setdefault("D", D)       # the priors act on the image columns x = D s
+        if image_prior or kw.get("lv_weight", 0.0) > 0.0:
             kw.setdefault("image_width", W)
     res = fn(A, Y, k, prec=prec, plan=plan, stream=stream, **kw)
     X = synthesize(D, res.support, res.coef, res.n_iter, stream=stream)

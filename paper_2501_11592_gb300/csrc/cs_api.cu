@@ -120,7 +120,7 @@ struct cs_plan {
         int bf16 = 0, gram = 0;
     } prep;
     const void* a_host = nullptr;   // set by the host-buffer solve around its call of solve()
-    int tv2d_ready = 0;             // image width whose cluster launch was checked
+    int img_ready = 0, img_ready_h = 0;   // image shape whose cluster launch was checked
     cudaStream_t cap_stream = nullptr;
     std::map<std::string, GraphEntry> graphs;
 };
@@ -411,6 +411,12 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             return fail(CS_EINVAL, "tv_D needs tv_N >= 2 and tv_ldd >= tv_N (tv_N=%d tv_ldd=%d)", cp->tv_N,
                         cp->tv_ldd);
         if (cp->image_width < 0) return fail(CS_EINVAL, "image_width=%d must be >= 0", cp->image_width);
+        if (!(cp->lv_weight >= 0.f) || !std::isfinite(cp->lv_weight))
+            return fail(CS_EINVAL, "lv_weight must be finite and >= 0");
+        if (!(cp->lv_eps >= 0.f) || !std::isfinite(cp->lv_eps))
+            return fail(CS_EINVAL, "lv_eps must be finite and >= 0");
+        if (cp->lv_weight > 0.f && cp->tv_D && (cp->tv_N < 1 || cp->tv_ldd < cp->tv_N))
+            return fail(CS_EINVAL, "tv_D needs tv_ldd >= tv_N >= 1 (tv_N=%d tv_ldd=%d)", cp->tv_N, cp->tv_ldd);
     }
     if (B == 0) return CS_OK;
     DeviceGuard dg(P->device);
@@ -449,19 +455,31 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         st = ensure_tv(P, (size_t)n * tvEp);
         if (st != CS_OK) return st;
     }
-    // the image form of the prior (Eq. 6): images of tvW consecutive columns
-    const int tvW = tv ? cp->image_width : 0;
-    const bool tv2d = tvW >= 2;
-    if (tv2d) {
-        if (c.th > 0.f || !clfit_tv2d_supported(a, tvW))
-            return fail(CS_ENOTSUP, "the image prior (image_width=%d) needs one atom per iteration, k <= 32, "
-                                    "2 <= image_width <= 512 and a batch of whole images (batch=%d)", tvW, B);
-        if (P->tv2d_ready != tvW) {
+    // the image priors (Eq. 6 and 7): images of imgW consecutive columns
+    const bool lv = cp && cp->lv_weight > 0.f;
+    const int imgW = (tv || lv) ? cp->image_width : 0;
+    const bool img = imgW >= 2;
+    const int imgH = cp && cp->tv_D ? cp->tv_N : n;     // pixels per column
+    float lv_scale = 0.f;
+    if (lv) {
+        if (!img) return fail(CS_EINVAL, "lv_weight needs image_width >= 2 (image_width=%d)", cp->image_width);
+        if (cp->form != CS_CL_GRAM || !a.GA)
+            return fail(CS_ENOTSUP, "the LV prior needs the Gram form and n <= %d", kGramAMax);
+        if (imgH >= 3 && imgW >= 3) lv_scale = cp->lv_weight / ((float)(imgH - 2) * (float)(imgW - 2));
+    }
+    if (img) {
+        if (c.th > 0.f || !clfit_image_supported(a, imgW, lv_scale != 0.f, imgH))
+            return fail(CS_ENOTSUP, "the image priors (image_width=%d) need one atom per iteration, k <= 32, "
+                                    "2 <= image_width <= 512, a batch of whole images (batch=%d) and, with "
+                                    "lv_weight, at most 256 pixels per column", imgW, B);
+        const int shape = imgW * 2 + (lv_scale != 0.f ? 1 : 0);
+        if (P->img_ready != shape || P->img_ready_h != imgH) {
             int ok = 0;
-            const cudaError_t e = clfit_tv2d_prepare(tvW, &ok);
+            const cudaError_t e = clfit_image_prepare(imgW, lv_scale != 0.f, imgH, &ok);
             if (e != cudaSuccess) return cuda_fail(e, "image prior: cluster check");
-            if (!ok) return fail(CS_ENOTSUP, "image prior: clusters for image_width=%d do not fit this device", tvW);
-            P->tv2d_ready = tvW;
+            if (!ok) return fail(CS_ENOTSUP, "image prior: clusters for image_width=%d do not fit this device", imgW);
+            P->img_ready = shape;
+            P->img_ready_h = imgH;
         }
     }
 
@@ -477,8 +495,8 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
 
     // CLOMP in Gram form runs selection, fit and residual as one kernel, or
     // (bf16 correlation) the whole solve as one persistent kernel
-    const bool fused = cp && cp->form == CS_CL_GRAM && P->fuse_update && !tv2d && update_clomp_fused_supported(a);
-    const bool persist = cp && cp->form == CS_CL_GRAM && bf16 && P->persist && !tv2d &&
+    const bool fused = cp && cp->form == CS_CL_GRAM && P->fuse_update && !img && update_clomp_fused_supported(a);
+    const bool persist = cp && cp->form == CS_CL_GRAM && bf16 && P->persist && !img &&
                          clomp_persist_supported(a, c);
     // threshold rule: float32 correlation of every atom, then one fused
     // selection + fit + residual kernel per iteration
@@ -547,10 +565,12 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SELECT, st, [&] { return launch_select(a, st); }), "select");
             if (!cp)
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] { return launch_chol(a, st); }), "cholesky");
-            else if (tv2d)
+            else if (img)
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] {
-                                  return launch_clfit_tv2d(a, c, it, tvW, 2.f * cp->tv_weight / (float)tvW, st);
-                              }), "cl fit (image prior)");
+                                  return launch_clfit_image(a, c, it, imgW, tv ? 2.f * cp->tv_weight / (float)imgW : 0.f,
+                                                            lv_scale, cp->lv_eps, cp->tv_D, imgH,
+                                                            cp->tv_D ? cp->tv_ldd : imgH, st);
+                              }), "cl fit (image priors)");
             else if (cp->form == CS_CL_GRAM)
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_FIT, st, [&] { return launch_clfit_gram(a, c, it, st); }), "cl fit (gram)");
             else
@@ -576,7 +596,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
     const cs_status rs = run_solve(P, s, enqueue, [&](std::string& key) {
         auto put = [&](const void* v, size_t nb) { key.append(static_cast<const char*>(v), nb); };
         const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->tab, P->cbuf,
-                              tv ? (const void*)cp->tv_D : nullptr, P->tvE, P->tvT};
+                              (tv || lv) ? (const void*)cp->tv_D : nullptr, P->tvE, P->tvT};
         put(ptrs, sizeof(ptrs));
         const int ints[] = {m, n, lda, ldy, B, c.tab_len, fused ? 1 : 0, persist ? 1 : 0, omp_fused ? 1 : 0,
                             reuse_a ? 1 : 0};
@@ -588,7 +608,9 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                              cp ? (double)cp->eps : 0.0, cp ? (double)cp->reset_adam_each_iter : 0.0,
                              cp ? (double)cp->form : -1.0, cp ? (double)c.th : 0.0,
                              tv ? (double)cp->tv_weight : 0.0, (double)tvN, tv ? (double)cp->tv_ldd : 0.0,
-                             (double)tvW};
+                             (double)imgW, lv ? (double)cp->lv_weight : 0.0, lv ? (double)cp->lv_eps : 0.0,
+                             (double)imgH,
+                             cp && cp->tv_D ? (double)cp->tv_ldd : 0.0};
         put(dk, sizeof(dk));
     }, P->use_graphs && !P->profiling && !(persist && P->stall_test));
     if (rs != CS_OK) P->prep = cs_plan::Prep{};

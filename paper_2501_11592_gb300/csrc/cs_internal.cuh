@@ -141,11 +141,14 @@ bool omp_fused_supported(const IterArgs& a);
 cudaError_t launch_omp_fused(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_resid(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_clfit_gram(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
-// CL fit with the image prior of Eq. 6 (k_tv2d.cu): images of W consecutive
-// columns, one thread-block cluster per image; lam_h = 2w/W.
-bool clfit_tv2d_supported(const IterArgs& a, int W);
-cudaError_t clfit_tv2d_prepare(int W, int* ok);
-cudaError_t launch_clfit_tv2d(const IterArgs& a, const ClArgs& c, int iter, int W, float lam_h, cudaStream_t s);
+// CL fit with the image priors of Eq. 6 and 7 (k_image_prior.cu): images of
+// W consecutive columns, one thread-block cluster per image; lam_h = 2 w_tv / W,
+// lv_scale = w_lv / ((H-2)(W-2)) (0: no local variation), lv_eps: the window
+// deviation's smoothing, D: H x n (nullptr: x = s).
+bool clfit_image_supported(const IterArgs& a, int W, bool lv, int H);
+cudaError_t clfit_image_prepare(int W, bool lv, int H, int* ok);
+cudaError_t launch_clfit_image(const IterArgs& a, const ClArgs& c, int iter, int W, float lam_h, float lv_scale,
+                               float lv_eps, const float* D, int H, int ldd, cudaStream_t s);
 cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 bool update_clomp_fused_supported(const IterArgs& a);
 cudaError_t launch_update_clomp(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);

@@ -1,6 +1,6 @@
-"""GPU parity of the image total-variation prior of Eq. 6 (image_width = W: the
-batch is images of W consecutive columns whose Adam steps are coupled by the
-horizontal differences) against the FP64 oracle."""
+"""GPU parity of the image priors against the FP64 oracle: the total
+variation of Eq. 6 and the local variation of Eq. 7 (image_width = W: the
+batch is images of W consecutive columns whose Adam steps are coupled)."""
 import numpy as np
 import pytest
 
@@ -140,3 +140,80 @@ def test_image_prior_limits(cs_gpu, torch):
     b = to_numpy(cs.clomp_solve_batched(A, Y, 6, prec="bf16"))
     for q in ("support", "coef", "n_iter", "status"):
         assert np.array_equal(a[q], b[q]), q
+
+
+# Local variation (Eq. 7) over the same images, alone and with the image TV
+
+LV_EPS = 1e-4          # the binding's default smoothing of the window deviation
+
+
+def oracle_img(A64, Y64, k, W, tv=0.0, lv=0.0, D64=None, **kw):
+    p = {q: f32(v) for q, v in CL.items() if q != "steps"}
+    p.update({q: f32(v) for q, v in kw.items() if q in p})
+    return oracle.clomp(A64, Y64, k, steps=kw.get("steps", CL["steps"]), tv_weight=f32(tv),
+                        lv_weight=f32(lv), lv_eps=f32(LV_EPS), D=D64, image_width=W, **p)
+
+
+@pytest.mark.parametrize("W,images,tv,lv", [(24, 3, 0.0, 0.5), (24, 3, 0.5, 0.5), (40, 2, 0.0, 1.0),
+                                            (100, 1, 0.3, 0.8), (3, 5, 0.0, 2.0)])
+def test_local_variation_without_basis(cs_gpu, torch, W, images, tv, lv):
+    """x = s (n = 200 pixels per column): windows across the CTA edges of 2-
+    and 4-CTA clusters, with and without the image TV; W = 3 has one window
+    column."""
+    k = 8
+    p = workloads.random_problem(64, 200, W * images, k, seed=180 + W, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    g = gpu_solve(cs_gpu, torch, A32, Y32, k, W, tv_weight=tv, lv_weight=lv)
+    assert g["launches"]["persist"] == 0 and g["launches"]["fit"] == k
+    print(compare(g, oracle_img(A64, Y64, k, W, tv=tv, lv=lv)))
+
+
+def test_local_variation_columnwise_dct_strip(cs_gpu, torch):
+    """A 256 x 64 strip of a column-wise image (A = Phi D, D the DCT): both
+    image priors, pixels synthesised through D every step.  With the smoothed
+    deviation the fit is well-conditioned: the test first checks that a 1e-7
+    relative change of Y leaves the oracle's supports and (to 1e-6) its
+    coefficients in place, then compares."""
+    p = workloads.config_columnwise_2d(0.3, n_images=1)
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y[:, :64])
+    D32 = np.asfortranarray(p.meta["D"], dtype=np.float32)
+    D64 = D32.astype(np.float64)
+    o = oracle_img(A64, Y64, p.k, 64, tv=32.0, lv=4.0, D64=D64)
+    rng = np.random.default_rng(188)
+    o2 = oracle_img(A64, Y64 * (1 + 1e-7 * rng.standard_normal(Y64.shape)), p.k, 64, tv=32.0, lv=4.0, D64=D64)
+    assert np.array_equal(o["support"], o2["support"])
+    assert np.max(np.linalg.norm(o["coef"] - o2["coef"], axis=1) / np.linalg.norm(o["coef"], axis=1)) < 1e-6
+    g = gpu_solve(cs_gpu, torch, A32, Y32, p.k, 64, D32=D32, tv_weight=32.0, lv_weight=4.0)
+    print(compare(g, o))
+    g0 = gpu_solve(cs_gpu, torch, A32, Y32, p.k, 64, D32=D32, tv_weight=32.0)
+    assert np.abs(g["coef"] - g0["coef"]).max() > 1e-3
+
+
+def test_local_variation_general_basis_short_columns(cs_gpu, torch):
+    """A general (non-orthonormal) basis of 5 rows: three window rows per
+    column; the LV term needs no orthonormality."""
+    rng = np.random.default_rng(185)
+    k, W, n = 6, 12, 80
+    p = workloads.random_problem(40, n, 2 * W, k, seed=186, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    D32 = np.asfortranarray(rng.standard_normal((5, n)) / np.sqrt(5), dtype=np.float32)
+    g = gpu_solve(cs_gpu, torch, A32, Y32, k, W, D32=D32, lv_weight=1.5)
+    print(compare(g, oracle_img(A64, Y64, k, W, lv=1.5, D64=D32.astype(np.float64))))
+
+
+def test_local_variation_limits(cs_gpu, torch):
+    p = workloads.random_problem(40, 300, 30, 6, seed=187, snr_db=30.0, values="pm")
+    A32, Y32, _, _ = f32_problem(p.A, p.Y)
+    A = torch.from_numpy(A32).cuda()
+    Y = torch.from_numpy(Y32).cuda()
+    cs = cs_gpu
+    with pytest.raises(cs.CSError) as e:          # no image width
+        cs.clomp_solve_batched(A, Y, 6, prec="bf16", lv_weight=0.5)
+    assert e.value.code == cs.CS_EINVAL
+    with pytest.raises(cs.CSError) as e:          # 300 pixels per column (x = s)
+        cs.clomp_solve_batched(A, Y, 6, prec="bf16", lv_weight=0.5, image_width=10)
+    assert e.value.code == cs.CS_ENOTSUP
+    for bad in (dict(lv_weight=float("nan")), dict(lv_weight=0.5, lv_eps=-1.0)):
+        with pytest.raises(cs.CSError) as e:
+            cs.clomp_solve_batched(A, Y, 6, prec="bf16", image_width=10, **bad)
+        assert e.value.code == cs.CS_EINVAL, bad

@@ -780,3 +780,66 @@ def test_clomp_lv_is_adam_on_the_image_loss():
     a = oracle.clomp(A, Y, k, steps=T, lr=3e-2, tv_weight=wt, lv_weight=0.0, D=D, image_width=W)
     b = oracle.clomp(A, Y, k, steps=T, lr=3e-2, tv_weight=wt, D=D, image_width=W)
     assert np.array_equal(a["coef"], b["coef"])
+
+
+def test_lv_smoothed_deviation():
+    """sqrt(var + eps^2): a constant image gives LV = eps with zero gradient, a
+    ramp sqrt(0.75 c^2 + eps^2); the smoothed loss is differentiable at
+    constant windows, so central differences hold on a mostly-zero image
+    (x = s, many constant windows); and a torch Adam run with the smoothed
+    deviation reproduces the image fit."""
+    n, W, c, w, eps = 7, 6, 0.4, 1.9, 0.05
+    full = list(range(n))
+    val, g = oracle.lv_loss_grad(None, n, [full] * W, [2.5 * np.ones(n) for _ in range(W)], w, eps)
+    assert abs(val - w * eps) < 1e-15 and all(np.all(q == 0.0) for q in g)
+    val, _ = oracle.lv_loss_grad(None, n, [full] * W, [c * j * np.ones(n) for j in range(W)], w, eps)
+    assert abs(val - w * math.sqrt(0.75 * c * c + eps * eps)) < 1e-14
+    rng = np.random.default_rng(190)
+    n, W = 20, 7
+    sup = [rng.choice(n, 2, replace=False).astype(np.int32) for _ in range(W)]
+    coefs = [rng.standard_normal(2) for _ in range(W)]
+
+    def lv(cs):
+        I = np.zeros((n, W))
+        for j, (q, v) in enumerate(zip(sup, cs)):
+            I[q, j] += v
+        sig = [math.sqrt(np.var(I[r:r + 3, cc:cc + 3], ddof=1) + eps * eps)
+               for r in range(n - 2) for cc in range(W - 2)]
+        return w * np.mean(sig)
+
+    val, g = oracle.lv_loss_grad(None, n, sup, coefs, w, eps)
+    assert abs(val - lv(coefs)) < 1e-13
+    h = 1e-6
+    for j in range(W):
+        fd = []
+        for e in np.eye(2):
+            up = [v.copy() for v in coefs]
+            dn = [v.copy() for v in coefs]
+            up[j] += h * e
+            dn[j] -= h * e
+            fd.append((lv(up) - lv(dn)) / (2 * h))
+        np.testing.assert_allclose(g[j], fd, rtol=1e-6, atol=1e-10)
+    torch = pytest.importorskip("torch")
+    m, n, W, k, T, wl = 16, 32, 5, 3, 20, 0.9
+    A = _rand_A(rng, m, n)
+    D = workloads.dct_synthesis(n)
+    Y = rng.standard_normal((m, W))
+    o = oracle.clomp(A, Y, k, steps=T, lr=3e-2, lv_weight=wl, lv_eps=eps, D=D, image_width=W)
+    P = torch.zeros((n, W), dtype=torch.float64, requires_grad=True)
+    opt = torch.optim.Adam([P], lr=3e-2, foreach=False)
+    At, Dt, Yt = (torch.tensor(v, dtype=torch.float64) for v in (A, D, Y))
+    mask = torch.zeros((n, W), dtype=torch.float64)
+    for t in range(k):
+        for j in range(W):
+            mask[o["support"][j, t], j] = 1.0
+        for _ in range(T):
+            opt.zero_grad()
+            V = P * mask
+            win = (Dt @ V).unfold(0, 3, 1).unfold(1, 3, 1).reshape(-1, 9)
+            var = torch.sum((win - win.mean(dim=1, keepdim=True)) ** 2, dim=1) / 8.0
+            loss = 0.5 * torch.sum((Yt - At @ V) ** 2) + wl * torch.sqrt(var + eps * eps).mean()
+            loss.backward()
+            opt.step()
+    Pn = P.detach().numpy()
+    for j in range(W):
+        np.testing.assert_allclose(o["coef"][j], Pn[o["support"][j], j], rtol=0, atol=1e-12)
