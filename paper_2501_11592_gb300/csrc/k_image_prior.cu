@@ -87,9 +87,12 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
     const int sz = in_img ? a.n_iter[b] + (live ? 1 : 0) : 0;
     const bool on = lane < sz;
 
-    float grow[KT];
-    {
-        const float* Gr = a.G + ((size_t)b * K + (on ? lane : 0)) * K;
+    // row q of G: in registers, or (LV, whose pixel work needs the registers)
+    // read from L1 every step
+    constexpr int GR = LV ? 1 : KT;
+    float grow[GR];
+    const float* Gr = a.G + ((size_t)b * K + (on ? lane : 0)) * K;
+    if constexpr (!LV) {
 #pragma unroll
         for (int p = 0; p < KT; ++p) grow[p] = (live && on && p < sz) ? Gr[p] : 0.f;
     }
@@ -158,7 +161,24 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
                 float acc[NR];
 #pragma unroll
                 for (int r = 0; r < NR; ++r) acc[r] = 0.f;
-                for (int q = 0; q < sz; ++q) {
+                int q = 0;
+                // four atoms at a time: 4 * NR independent loads in flight
+                for (; q + 4 <= sz; q += 4) {
+                    const float* d0 = g.D + sh_off[w][q];
+                    const float* d1 = g.D + sh_off[w][q + 1];
+                    const float* d2 = g.D + sh_off[w][q + 2];
+                    const float* d3 = g.D + sh_off[w][q + 3];
+                    const float s0 = mine[q], s1 = mine[q + 1], s2 = mine[q + 2], s3 = mine[q + 3];
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const int i = lane + 32 * r;
+                        if (i < g.H) {
+                            const float v0 = d0[i], v1 = d1[i], v2 = d2[i], v3 = d3[i];
+                            acc[r] = fmaf(v3, s3, fmaf(v2, s2, fmaf(v1, s1, fmaf(v0, s0, acc[r]))));
+                        }
+                    }
+                }
+                for (; q < sz; ++q) {
                     const float sq = mine[q];
                     const float* dq = g.D + sh_off[w][q];
 #pragma unroll
@@ -205,13 +225,26 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
         }
         // g = G s - b + c_j lam s - lam (s_left + s_right) at this atom
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
+        if constexpr (!LV) {
 #pragma unroll
-        for (int p4 = 0; p4 < KT; p4 += 4) {
-            const float4 v = *reinterpret_cast<const float4*>(&mine[p4]);
-            acc[0] = fmaf(grow[p4], v.x, acc[0]);
-            acc[1] = fmaf(grow[p4 + 1], v.y, acc[1]);
-            acc[2] = fmaf(grow[p4 + 2], v.z, acc[2]);
-            acc[3] = fmaf(grow[p4 + 3], v.w, acc[3]);
+            for (int p4 = 0; p4 < KT; p4 += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(&mine[p4]);
+                acc[0] = fmaf(grow[p4], v.x, acc[0]);
+                acc[1] = fmaf(grow[p4 + 1], v.y, acc[1]);
+                acc[2] = fmaf(grow[p4 + 2], v.z, acc[2]);
+                acc[3] = fmaf(grow[p4 + 3], v.w, acc[3]);
+            }
+        } else if (live && on) {
+#pragma unroll
+            for (int p4 = 0; p4 < KT; p4 += 4) {
+                const float4 v = *reinterpret_cast<const float4*>(&mine[p4]);
+#pragma unroll
+                for (int e = 0; e < 4; ++e) {
+                    const int p = p4 + e;
+                    const float sv = e == 0 ? v.x : e == 1 ? v.y : e == 2 ? v.z : v.w;
+                    if (p < sz) acc[e] = fmaf(__ldg(&Gr[p]), sv, acc[e]);
+                }
+            }
         }
         float nsum = 0.f;
         if (pos_l >= 0) {
@@ -255,13 +288,43 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
             __syncwarp();
             // back to the support: (D_S^T gx)_q, a warp sum per atom
             if (g.D) {
-                for (int q = 0; q < sz; ++q) {
+                float gxr[NR];
+#pragma unroll
+                for (int r = 0; r < NR; ++r) gxr[r] = lane + 32 * r < g.H ? my_x[lane + 32 * r] : 0.f;
+                int q = 0;
+                // four atoms at a time, then four warp sums
+                for (; q + 4 <= sz; q += 4) {
+                    const float* d0 = g.D + sh_off[w][q];
+                    const float* d1 = g.D + sh_off[w][q + 1];
+                    const float* d2 = g.D + sh_off[w][q + 2];
+                    const float* d3 = g.D + sh_off[w][q + 3];
+                    float p0 = 0.f, p1 = 0.f, p2 = 0.f, p3 = 0.f;
+#pragma unroll
+                    for (int r = 0; r < NR; ++r) {
+                        const int i = lane + 32 * r;
+                        if (i < g.H) {
+                            p0 = fmaf(d0[i], gxr[r], p0);
+                            p1 = fmaf(d1[i], gxr[r], p1);
+                            p2 = fmaf(d2[i], gxr[r], p2);
+                            p3 = fmaf(d3[i], gxr[r], p3);
+                        }
+                    }
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) {
+                        p0 += __shfl_xor_sync(0xffffffffu, p0, o);
+                        p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+                        p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+                        p3 += __shfl_xor_sync(0xffffffffu, p3, o);
+                    }
+                    glv = lane == q ? p0 : lane == q + 1 ? p1 : lane == q + 2 ? p2 : lane == q + 3 ? p3 : glv;
+                }
+                for (; q < sz; ++q) {
                     const float* dq = g.D + sh_off[w][q];
                     float part = 0.f;
 #pragma unroll
                     for (int r = 0; r < NR; ++r) {
                         const int i = lane + 32 * r;
-                        if (i < g.H) part = fmaf(dq[i], my_x[i], part);
+                        if (i < g.H) part = fmaf(dq[i], gxr[r], part);
                     }
 #pragma unroll
                     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
