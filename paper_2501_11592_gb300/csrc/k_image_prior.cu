@@ -71,9 +71,7 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
     __shared__ __align__(16) float sh_s[2][kImgWarps][KT];
     __shared__ int sh_off[kImgWarps][KT];      // LV: column offsets of the support atoms in D
     __shared__ float2 sh_tab[kAdamStaged];
-    // LV: pixels [wpc][NP], window stats [wpc][NP], then the halos of the
-    // edge warps: pixels [2][2][NP], window stats [2][2][NP]
-    extern __shared__ __align__(16) float dyn[];
+    extern __shared__ __align__(16) float dyn[];   // LV: pixels [wpc][NP], then window stats [wpc][NP]
     const float2* tab = stage_adam(c, sh_tab);
 
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -130,8 +128,6 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
     // previous two columns' statistics (windows that contain this column)
     float* xs = dyn;
     float2* st = reinterpret_cast<float2*>(dyn + (size_t)wpc * g.NP);
-    float* hx = dyn + (size_t)wpc * g.NP * 3;
-    float2* hs = reinterpret_cast<float2*>(hx + (size_t)4 * g.NP);
     float* my_x = xs + (size_t)w * g.NP;
     float2* my_st = st + (size_t)w * g.NP;
     if (LV) {
@@ -143,39 +139,13 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
     const float* x2 = nullptr;
     const float2* sm1 = nullptr;
     const float2* sm2 = nullptr;
-    // columns in the neighbouring CTA are copied to this warp's halo once per
-    // step (one batch of vector loads) instead of being read element-wise
-    // through distributed shared memory
-    const float* rx[2] = {nullptr, nullptr};
-    const float2* rs[2] = {nullptr, nullptr};
     if (LV) {
         if (lv_left) {
             x1 = column_slot(cl, xs, g.NP, col + 1, wpc, rank);
             x2 = column_slot(cl, xs, g.NP, col + 2, wpc, rank);
-            const int e = w - (wpc - 2);          // 0, 1: the last two warps
-            if ((col + 1) / wpc != rank) {
-                rx[0] = x1;
-                x1 = hx + (size_t)(2 * e) * g.NP;
-            }
-            if ((col + 2) / wpc != rank) {
-                rx[1] = x2;
-                x2 = hx + (size_t)(2 * e + 1) * g.NP;
-            }
         }
-        if (in_img && col >= 1 && col - 1 + 2 < W) {
-            sm1 = column_slot(cl, st, g.NP, col - 1, wpc, rank);
-            if ((col - 1) / wpc != rank) {       // w = 0
-                rs[0] = sm1;
-                sm1 = hs + (size_t)(2 * w) * g.NP;
-            }
-        }
-        if (in_img && col >= 2) {
-            sm2 = column_slot(cl, st, g.NP, col - 2, wpc, rank);
-            if ((col - 2) / wpc != rank) {       // w = 0, 1
-                rs[1] = sm2;
-                sm2 = hs + (size_t)(2 * w + 1) * g.NP;
-            }
-        }
+        if (in_img && col >= 1 && col - 1 + 2 < W) sm1 = column_slot(cl, st, g.NP, col - 1, wpc, rank);
+        if (in_img && col >= 2) sm2 = column_slot(cl, st, g.NP, col - 2, wpc, rank);
     }
     const bool lv_self = LV && lv_left;   // windows starting at this column contain it too
     const float omb1 = 1.f - c.beta1, omb2 = 1.f - c.beta2;
@@ -230,16 +200,6 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
         }
         cl.sync();
         if (LV) {
-            if (rx[0] || rx[1]) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (rx[h]) {
-                        const float4* src = reinterpret_cast<const float4*>(rx[h]);
-                        float4* dst = reinterpret_cast<float4*>(const_cast<float*>(h ? x2 : x1));
-                        for (int t = lane; t < g.NP / 4; t += 32) dst[t] = src[t];
-                    }
-                __syncwarp();
-            }
             // mean and 1/(8 sigma) of the windows whose left column is this one
             if (lv_left) {
                 for (int r0 = lane; r0 + 2 < g.H; r0 += 32) {
@@ -262,16 +222,6 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
                 }
             }
             cl.sync();
-            if (rs[0] || rs[1]) {
-#pragma unroll
-                for (int h = 0; h < 2; ++h)
-                    if (rs[h]) {
-                        const float4* src = reinterpret_cast<const float4*>(rs[h]);
-                        float4* dst = reinterpret_cast<float4*>(const_cast<float2*>(h ? sm2 : sm1));
-                        for (int t = lane; t < g.NP / 2; t += 32) dst[t] = src[t];
-                    }
-                __syncwarp();
-            }
         }
         // g = G s - b + c_j lam s - lam (s_left + s_right) at this atom
         float acc[4] = {0.f, 0.f, 0.f, 0.f};
@@ -411,9 +361,7 @@ __global__ void __launch_bounds__(1024, 1) k_clfit_image(IterArgs a, ClArgs c, I
     }
 }
 
-size_t lv_smem_bytes(int wpc, int NP) {
-    return (size_t)(wpc + 4) * NP * (sizeof(float) + sizeof(float2));
-}
+size_t lv_smem_bytes(int wpc, int NP) { return (size_t)wpc * NP * (sizeof(float) + sizeof(float2)); }
 
 cudaLaunchConfig_t image_config(int W, bool lv, int NP, int images, cudaStream_t s, cudaLaunchAttribute* at) {
     const int csz = ceil_div(W, kImgWarps);
