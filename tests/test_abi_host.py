@@ -58,3 +58,11 @@ def test_solve_argument_checks_without_gpu(lib):
     assert lib.clfit_adam_step(null, 16, 40, 16, null, null, 2, 2, null, 16, 1, null, null, 0,
                                ctypes.c_float(0.01), ctypes.c_float(0.9), ctypes.c_float(0.999),
                                ctypes.c_float(1e-8), null, null) == -1
+
+
+def test_plan_setters_reject_a_null_plan(lib):
+    lib.cs_plan_set_A_generation.argtypes = [ctypes.c_void_p, ctypes.c_uint64]
+    assert lib.cs_plan_set_A_generation(None, 1) == -1
+    assert b"plan" in lib.cs_last_error()
+    assert lib.cs_plan_set_profiling(None, 1) == -1
+    assert lib.cs_plan_set_option(None, 0, 1) == -1
