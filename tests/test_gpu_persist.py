@@ -151,7 +151,7 @@ def test_persist_bounded_wait_reports_timeout(cs_gpu, torch):
     torch.cuda.synchronize()                   # returns: every wait is bounded
     _, errs = plan.counters(reset=True)
     # whichever bounded wait runs out first reports: the signal warps' (16)
-    # or the MMA issuer's wait for the next pass over the residual tiles (8)
+    # or the MMA issuer's wait for the residuals of the next pass (8)
     assert errs & (8 | 16), f"expected a bounded-wait flag, got {errs:#x}"
     r = cs_gpu.clomp_solve_batched(A, Y, 8, prec="bf16", plan=plan, **CL)
     torch.cuda.synchronize()
