@@ -389,8 +389,10 @@ cudaError_t prepare_kt(int W, int NP, int* clusters) {
         return e;
     cudaLaunchAttribute at[1];
     const cudaLaunchConfig_t cfg = image_config(W, LV, NP, 1, 0, at);
+    // the largest size any image needs: the attribute is the kernel's, shared
+    // by every plan, so it never shrinks below what another plan launches with
     if (LV && (e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        (int)cfg.dynamicSmemBytes)) != cudaSuccess)
+                                        (int)lv_smem_bytes(kImgWarps, kLvMaxN))) != cudaSuccess)
         return e;
     return cudaOccupancyMaxActiveClusters(clusters, kern, &cfg);
 }

@@ -217,3 +217,29 @@ def test_local_variation_limits(cs_gpu, torch):
         with pytest.raises(cs.CSError) as e:
             cs.clomp_solve_batched(A, Y, 6, prec="bf16", image_width=10, **bad)
         assert e.value.code == cs.CS_EINVAL, bad
+
+
+def test_local_variation_plans_of_different_heights(cs_gpu, torch):
+    """Two plans whose images need different shared memory, used in turn
+    (the first plan's second solve reuses its launch check): the kernel's
+    shared-memory limit set for one plan does not break the other."""
+    cs = cs_gpu
+    W, k = 40, 6
+    probs, plans, first = {}, {}, {}
+    for n in (200, 64):
+        p = workloads.random_problem(48, n, 2 * W, k, seed=190 + n, snr_db=30.0, values="pm")
+        probs[n] = f32_problem(p.A, p.Y)
+        plans[n] = cs.Plan(48, n, 2 * W, k)
+    for n in (200, 64, 200):
+        A32, Y32, A64, Y64 = probs[n]
+        A = torch.from_numpy(np.asfortranarray(A32)).cuda()
+        Y = torch.from_numpy(np.asfortranarray(Y32)).cuda()
+        r = to_numpy(cs.clomp_solve_batched(A, Y, k, prec="bf16", plan=plans[n], image_width=W, lv_weight=0.7,
+                                            **CL))
+        torch.cuda.synchronize()
+        if n in first:
+            for q in ("support", "coef", "n_iter", "status"):
+                assert np.array_equal(r[q], first[n][q]), q
+        else:
+            print(compare(r, oracle_img(A64, Y64, k, W, lv=0.7)))
+            first[n] = r
