@@ -843,3 +843,63 @@ def test_lv_smoothed_deviation():
     Pn = P.detach().numpy()
     for j in range(W):
         np.testing.assert_allclose(o["coef"][j], Pn[o["support"][j], j], rtol=0, atol=1e-12)
+
+
+def test_clomp_image_stopped_column_is_frozen_neighbour():
+    """An image whose second column is one atom exactly stops after its first
+    iteration (tol); the other columns go on, and the stopped column keeps its
+    coefficient yet still pulls on its neighbours through the horizontal TV.
+    Torch reference: one float64 Adam per column (its own state and step
+    counter), a column steps only while it is live."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(195)
+    m, n, W, k, T, lr, w, tol = 16, 32, 4, 4, 100, 5e-2, 0.4, 0.8
+    A = rng.standard_normal((m, n))
+    A /= np.linalg.norm(A, axis=0)
+    D = workloads.dct_synthesis(n)
+    Y = rng.standard_normal((m, W))
+    Y[:, 1] = 2.0 * A[:, 5]
+    Y[:, 2] += 3.0 * A[:, 5]          # the third column picks atom 5 too
+    o = oracle.clomp(A, Y, k, tol=tol, steps=T, lr=lr, tv_weight=w, D=D, image_width=W)
+    assert list(o["n_iter"]) == [4, 1, 4, 4] and list(o["status"]) == [0, 1, 0, 0]
+    assert o["support"][2, 0] == 5
+    At, Dt, Yt = (torch.tensor(v, dtype=torch.float64) for v in (A, D, Y))
+    P = [torch.zeros(n, dtype=torch.float64, requires_grad=True) for _ in range(W)]
+    opts = [torch.optim.Adam([p], lr=lr, foreach=False) for p in P]
+    mask = torch.zeros((n, W), dtype=torch.float64)
+    live = [True] * W
+    for t in range(k):
+        for j in range(W):
+            if live[j]:
+                r = (Yt[:, j] - At @ (P[j] * mask[:, j])).detach()
+                c = (At.T @ r).abs().numpy()
+                c[mask[:, j].numpy() > 0] = -1
+                a = int(np.argmax(c))
+                assert a == o["support"][j, t]
+                mask[a, j] = 1.0
+        for _ in range(T):
+            for opt in opts:
+                opt.zero_grad()
+            V = torch.stack(P, dim=1) * mask
+            I = Dt @ V
+            loss = (0.5 * torch.sum((Yt - At @ V) ** 2)
+                    + w * (torch.sum((I[1:, :] - I[:-1, :]) ** 2) / n + torch.sum((I[:, 1:] - I[:, :-1]) ** 2) / W))
+            loss.backward()
+            for j in range(W):
+                if live[j]:
+                    opts[j].step()
+        for j in range(W):
+            if live[j]:
+                res = float(torch.linalg.norm(Yt[:, j] - At @ (P[j].detach() * mask[:, j])))
+                if res <= tol:
+                    live[j] = False
+    for j in range(W):
+        np.testing.assert_allclose(o["coef"][j, :o["n_iter"][j]], P[j].detach().numpy()[o["support"][j, :o["n_iter"][j]]],
+                                   rtol=0, atol=1e-12)
+    # the frozen column still pulls its neighbour's coefficient of their
+    # shared atom: with the column zero (stopped at once, s = 0) it differs
+    Y0 = Y.copy()
+    Y0[:, 1] = 0.0
+    o0 = oracle.clomp(A, Y0, k, tol=tol, steps=T, lr=lr, tv_weight=w, D=D, image_width=W)
+    assert o0["n_iter"][1] == 0 and o0["support"][2, 0] == 5
+    assert abs(o0["coef"][2, 0] - o["coef"][2, 0]) > 1e-3
