@@ -240,7 +240,10 @@ typedef struct {
  * scatters the outputs back, all on `stream`.  params->k is ignored (each
  * instance has its own).  Every instance must fit the plan (m <= m_max,
  * n <= n_max, k <= k_max); groups larger than batch_max run in chunks.
- * Device staging for the gather/scatter is allocated on first use. */
+ * Device staging for the gather/scatter is allocated on first use.  The
+ * image priors (image_width >= 2 with tv_weight or lv_weight > 0) couple
+ * consecutive signals of a batch, which the regrouping would mix:
+ * CS_ENOTSUP. */
 cs_status omp_solve_varlen(cs_plan* plan, const cs_instance* instances, int32_t count,
                            const cs_omp_params* params, void* stream);
 cs_status clomp_solve_varlen(cs_plan* plan, const cs_instance* instances, int32_t count,

@@ -737,6 +737,8 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
                        const cs_clomp_params* cp, cudaStream_t s) {
     if (!P) return fail(CS_EINVAL, "plan is NULL");
     if (!op) return fail(CS_EINVAL, "params is NULL");
+    if (cp && cp->image_width >= 2 && (cp->tv_weight > 0.f || cp->lv_weight > 0.f))
+        return fail(CS_ENOTSUP, "the image priors need a batched call (the uneven-batch regrouping mixes images)");
     if (count < 0) return fail(CS_EINVAL, "count=%d", count);
     if (count == 0) return CS_OK;
     if (!inst) return fail(CS_EINVAL, "instances is NULL");

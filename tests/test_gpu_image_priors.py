@@ -243,3 +243,18 @@ def test_local_variation_plans_of_different_heights(cs_gpu, torch):
         else:
             print(compare(r, oracle_img(A64, Y64, k, W, lv=0.7)))
             first[n] = r
+
+
+def test_image_priors_refused_by_the_uneven_batch_calls(cs_gpu, torch):
+    """The uneven-batch calls regroup instances by size class, which would
+    mix images: the image priors are refused there (CS_ENOTSUP)."""
+    cs = cs_gpu
+    p = workloads.random_problem(32, 96, 4, 4, seed=196, snr_db=30.0, values="pm")
+    A32, Y32, _, _ = f32_problem(p.A, p.Y)
+    A = torch.from_numpy(A32).cuda()
+    inst = [(A, torch.from_numpy(np.ascontiguousarray(Y32[:, b])).cuda(), 4) for b in range(4)]
+    for extra in (dict(tv_weight=0.5, image_width=2), dict(lv_weight=0.5, image_width=4)):
+        params = cs._clomp_params(1, 0.0, None, "bf16", 0, 50, 1e-2, 0.9, 0.999, 1e-8, False, "gram", **extra)
+        with pytest.raises(cs.CSError) as e:
+            cs._varlen(cs.load().clomp_solve_varlen, inst, params, None, None)
+        assert e.value.code == cs.CS_ENOTSUP, extra
