@@ -60,7 +60,10 @@ enum {
     CS_SIG_MAX_ITER = 2,      /* max_iter iterations without reaching k or tol */
     CS_SIG_DEPENDENT = 3,     /* the selected atom is linearly dependent on the support
                                  (pivot^2 <= 2^-20 ||a||^2); it is not added */
-    CS_SIG_NONFINITE = 4      /* y holds a NaN or Inf; no iteration is run */
+    CS_SIG_NONFINITE = 4,     /* y holds a NaN or Inf; no iteration is run */
+    CS_SIG_UNSUPPORTED = 5    /* uneven batches only: the instance's sizes exceed what the
+                                 plan or the kernels solve (see omp_solve_varlen); it is not
+                                 solved: support -1, coef 0, n_iter 0, res_norm ||y||_2 */
 };
 
 /* Arithmetic of the correlation c = A^T r (step 1).  The selection always
@@ -238,9 +241,13 @@ typedef struct {
  * call groups the instances that share (A, m, n, lda, k), gathers each
  * group's measurements into a batch, runs the batched solver on it and
  * scatters the outputs back, all on `stream`.  params->k is ignored (each
- * instance has its own).  Every instance must fit the plan (m <= m_max,
- * n <= n_max, k <= k_max); groups larger than batch_max run in chunks.
- * Device staging for the gather/scatter is allocated on first use.  The
+ * instance has its own).  An instance whose sizes exceed the plan (m > m_max,
+ * n > n_max or k > k_max) or the chosen correlation (bf16: m <= 256,
+ * n <= 4096) is not solved: its sig_status is set to CS_SIG_UNSUPPORTED
+ * (its A is never read) and the call goes on with the others.  Groups larger
+ * than batch_max run in chunks.  Device staging for the gather/scatter is
+ * allocated on first use.  Malformed instances (NULL pointers, k > m or
+ * k > n, lda < m) are argument errors (CS_EINVAL, nothing launched).  The
  * image priors (image_width >= 2 with tv_weight or lv_weight > 0) couple
  * consecutive signals of a batch, which the regrouping would mix:
  * CS_ENOTSUP. */
@@ -334,13 +341,26 @@ cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* st
  * the process exits (about 12 KiB per signal at m = 256, k <= 32, plus
  * 6 bytes per element of A; larger problems get CS_EINVAL and belong on
  * omp_solve_batched).  The first call on each device looks the array's
- * address up (make it before any stream capture); calls whose GPU work
- * overlaps -- on different streams or threads -- race on the shared array. */
+ * address up (make it before any stream capture) and keeps it for the life
+ * of the process, so do not use this entry point on a device after a reset
+ * of that device (cudaDeviceReset).  Calls whose GPU work overlaps -- on
+ * different streams or threads -- race on the shared array.  Each call
+ * clears the device counters (certificate fallbacks, error flags) when it
+ * starts; omp_solve_batched_noalloc_counters reads them. */
 cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_t n, int32_t lda,
                                     const float* Y, int32_t ldy, int32_t batch, int32_t* support,
                                     float* coef, int32_t* n_iter, float* res_norm,
                                     int32_t* sig_status, const cs_omp_params* params,
                                     void* stream);
+
+/* The counters of the last omp_solve_batched_noalloc call on the current
+ * device, as cs_plan_counters gives them for a plan: synchronises `stream`,
+ * copies them to out[0..3] (out[0] = certificate fallbacks of the bf16
+ * correlation, out[1] = device error flags), zeroes them when reset != 0 and
+ * returns CS_ETIMEOUT when out[1] != 0 -- the results of that call are then
+ * unspecified, although the call itself returned CS_OK.  Read them after the
+ * call and before the next one (which clears them).  Allocates nothing. */
+cs_status omp_solve_batched_noalloc_counters(uint32_t* out, int32_t reset, void* stream);
 
 /* Measurement support.  Phases of a solve: */
 enum {

@@ -21,7 +21,7 @@ __all__ = [
     "load", "Plan", "omp_solve", "omp_solve_batched", "clomp_solve", "clomp_solve_batched",
     "omp_solve_batched_host", "clomp_solve_batched_host", "clfit_forward", "clfit_adjoint",
     "clfit_adam_step", "CSError", "SIG_REACHED_K", "SIG_REACHED_TOL", "SIG_MAX_ITER",
-    "SIG_DEPENDENT", "SIG_NONFINITE", "library_path", "correlate", "PHASES", "omp_solve_varlen",
+    "SIG_DEPENDENT", "SIG_NONFINITE", "SIG_UNSUPPORTED", "library_path", "correlate", "PHASES", "omp_solve_varlen",
     "clomp_solve_varlen", "synthesize", "image_quality", "reconstruct_columnwise",
 ]
 
@@ -29,7 +29,7 @@ _PKG = os.path.dirname(os.path.abspath(__file__))
 _LIB_PATH = os.path.join(_PKG, "_lib", "libcs_omp.so")
 
 CS_OK, CS_EINVAL, CS_ENOMEM, CS_ECUDA, CS_ETIMEOUT, CS_ENOTSUP = 0, -1, -2, -3, -4, -5
-SIG_REACHED_K, SIG_REACHED_TOL, SIG_MAX_ITER, SIG_DEPENDENT, SIG_NONFINITE = 0, 1, 2, 3, 4
+SIG_REACHED_K, SIG_REACHED_TOL, SIG_MAX_ITER, SIG_DEPENDENT, SIG_NONFINITE, SIG_UNSUPPORTED = 0, 1, 2, 3, 4, 5
 PREC = {"fp32": 0, "bf16": 1}
 FORM = {"gather": 0, "gram": 1}
 PHASES = ("setup", "correlation", "select", "fit", "residual", "update", "persist")
@@ -347,9 +347,11 @@ def _varlen(fn, instances, params, plan, stream):
     Returns a list of Result (one signal each)."""
     torch = _torch()
     if plan is None:
-        m_max = max(int(A.shape[0]) for A, _, _ in instances)
+        # instances beyond the kernels' limits are refused per instance
+        # (SIG_UNSUPPORTED), so the default plan stops at those limits
+        m_max = min(1024, max(int(A.shape[0]) for A, _, _ in instances))
         n_max = max(int(A.shape[1]) for A, _, _ in instances)
-        k_max = max(int(k) for _, _, k in instances)
+        k_max = min(64, max(int(k) for _, _, k in instances))
         plan = _plan_for(m_max, n_max, 1024, k_max, None)
     keep, outs = [], []
     arr = (Instance * len(instances))()

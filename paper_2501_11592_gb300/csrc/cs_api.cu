@@ -673,6 +673,16 @@ cs_status run_solve(cs_plan* P, cudaStream_t s, E& enqueue, K&& make_key, bool g
     return CS_OK;
 }
 
+// Copy the four device counters at `dev` to out (after the stream's work),
+// optionally zero them, and turn a set error flag into CS_ETIMEOUT.
+cs_status read_counters(unsigned* dev, uint32_t* out, int32_t reset, cudaStream_t s) {
+    CS_TRY_LAUNCH(cudaMemcpyAsync(out, dev, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s), "copy counters");
+    if (reset) CS_TRY_LAUNCH(cudaMemsetAsync(dev, 0, 4 * sizeof(uint32_t), s), "reset counters");
+    CS_TRY_LAUNCH(cudaStreamSynchronize(s), "stream synchronize");
+    if (out[1] != 0) return fail(CS_ETIMEOUT, "a bounded device-side wait gave up (flags 0x%x)", out[1]);
+    return CS_OK;
+}
+
 cs_status ensure_io(cs_plan* P, size_t bytes) {
     if (bytes <= P->io_bytes) return CS_OK;
     if (P->io) {
@@ -748,15 +758,23 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
             return fail(CS_EINVAL, "instance %d has a NULL pointer", i);
         if (x.m < 1 || x.n < 1 || x.lda < x.m || x.k < 1 || x.k > x.m || x.k > x.n)
             return fail(CS_EINVAL, "instance %d: bad sizes m=%d n=%d lda=%d k=%d", i, x.m, x.n, x.lda, x.k);
-        if (x.m > P->m_max || x.n > P->n_max || x.k > P->k_max)
-            return fail(CS_EINVAL, "instance %d (m=%d n=%d k=%d) exceeds the plan", i, x.m, x.n, x.k);
     }
+    // instances beyond the plan or the correlation's limits are not solved
+    auto refused = [&](const cs_instance& x) {
+        return x.m > P->m_max || x.n > P->n_max || x.k > P->k_max ||
+               (op->prec == CS_CORR_BF16 && !corr_tc_supported(x.m, x.n));
+    };
     // groups in order of first appearance
     std::vector<std::vector<int>> groups;
+    std::vector<int> refuse;
     {
         std::map<std::string, int> at;
         for (int i = 0; i < count; ++i) {
             const cs_instance& x = inst[i];
+            if (refused(x)) {
+                refuse.push_back(i);
+                continue;
+            }
             std::string key;
             key.append(reinterpret_cast<const char*>(&x.A), sizeof(x.A));
             const int dims[] = {x.m, x.n, x.lda, x.k};
@@ -781,6 +799,7 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
     const size_t oT = cv.take<int32_t>(Bm);
     const size_t oYp = cv.take<const float*>(Bm);
     const size_t oOut = cv.take<VarlenOut>(Bm);
+    const size_t oRef = cv.take<VarlenRefuse>(Bm);
     if (cv.off > P->vl_bytes) {
         if (P->vl) {
             cudaFree(P->vl);
@@ -801,8 +820,22 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
     int32_t* Tb = reinterpret_cast<int32_t*>(P->vl + oT);
     const float** Yp = reinterpret_cast<const float**>(P->vl + oYp);
     VarlenOut* Ot = reinterpret_cast<VarlenOut*>(P->vl + oOut);
+    VarlenRefuse* Rt = reinterpret_cast<VarlenRefuse*>(P->vl + oRef);
     std::vector<const float*> yp;
     std::vector<VarlenOut> ot;
+    std::vector<VarlenRefuse> rt;
+    for (size_t r0 = 0; r0 < refuse.size(); r0 += Bm) {
+        const int nr = (int)std::min(Bm, refuse.size() - r0);
+        rt.assign(nr, VarlenRefuse{});
+        for (int j = 0; j < nr; ++j) {
+            const cs_instance& x = inst[refuse[r0 + j]];
+            rt[j] = VarlenRefuse{VarlenOut{x.support, x.coef, x.n_iter, x.res_norm, x.sig_status}, x.y, x.m, x.k};
+        }
+        // pageable source: staged before the call returns
+        CS_TRY_LAUNCH(cudaMemcpyAsync(Rt, rt.data(), sizeof(VarlenRefuse) * nr, cudaMemcpyHostToDevice, s),
+                      "copy varlen table");
+        CS_TRY_LAUNCH(launch_varlen_refuse(Rt, nr, s), "varlen refuse");
+    }
     for (const auto& g : groups) {
         const cs_instance& x0 = inst[g[0]];
         cs_omp_params o = *op;
@@ -1070,13 +1103,7 @@ cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* st
     if (!plan || !out) return fail(CS_EINVAL, "NULL argument");
     DeviceGuard dg(plan->device);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
-    cudaStream_t s = (cudaStream_t)stream;
-    CS_TRY_LAUNCH(cudaMemcpyAsync(out, plan->counters, 4 * sizeof(uint32_t), cudaMemcpyDeviceToHost, s),
-                  "copy counters");
-    if (reset) CS_TRY_LAUNCH(cudaMemsetAsync(plan->counters, 0, 4 * sizeof(uint32_t), s), "reset counters");
-    CS_TRY_LAUNCH(cudaStreamSynchronize(s), "stream synchronize");
-    if (out[1] != 0) return fail(CS_ETIMEOUT, "a bounded device-side wait gave up (flags 0x%x)", out[1]);
-    return CS_OK;
+    return read_counters(plan->counters, out, reset, (cudaStream_t)stream);
 }
 
 cs_status cs_plan_set_A_generation(cs_plan* plan, uint64_t generation) {
@@ -1155,11 +1182,15 @@ const char* cs_version(void) { return "cs-omp-gb300 0.1 (sm_103a)"; }
 // The host cannot use the array's name as a device address, so the first
 // call on each device (with that device current) looks the address up with
 // cudaGetSymbolAddress and caches it; later calls reuse it.  That first call
-// therefore belongs before any stream capture.  All calls share the one
-// array and find the previous call's contents in it: everything a solve reads
-// is written by that solve first, and the device counters are cleared at the
-// start of every call.  Two calls whose work overlaps on the GPU (different
-// streams, or different host threads) race on the array.
+// therefore belongs before any stream capture, and the cached address is not
+// valid across a reset of the device (cudaDeviceReset destroys the context
+// the address belongs to).  All calls share the one array and find the
+// previous call's contents in it: everything a solve reads is written by that
+// solve first, and the device counters -- kept in the array's first 256
+// bytes, where omp_solve_batched_noalloc_counters finds them whatever the
+// problem's layout -- are cleared at the start of every call.  Two calls
+// whose work overlaps on the GPU (different streams, or different host
+// threads) race on the array.
 
 static constexpr size_t kNoAllocScratchBytes = (size_t)32 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
@@ -1167,8 +1198,28 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratch
 namespace {
 
 constexpr int kNoAllocMaxDevices = 64;
+constexpr size_t kNoAllocCounterBytes = 256;   // the counters, ahead of the solve's layout
 std::mutex g_noalloc_mu;
 void* g_noalloc_base[kNoAllocMaxDevices] = {};
+
+// The array's device address on the current device (looked up on the first
+// call per device).
+cs_status noalloc_base(char** base, int* device) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CS_ENOTSUP, "device %d out of range", dev);
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_base[dev]) {
+        void* ptr = nullptr;
+        e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
+        g_noalloc_base[dev] = ptr;
+    }
+    *base = static_cast<char*>(g_noalloc_base[dev]);
+    *device = dev;
+    return CS_OK;
+}
 
 }  // namespace
 
@@ -1193,34 +1244,33 @@ extern "C" cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_
     P.nw_max = ceil_div(n, 32);
     P.nch_max = ceil_div(n, kCorrFp32TileN);
     const WsLayout L = ws_layout(m, n, P.B_max, P.k_max, false, false);
-    if (L.total > kNoAllocScratchBytes)
+    if (L.total > kNoAllocScratchBytes - kNoAllocCounterBytes)
         return fail(CS_EINVAL,
                     "problem needs %zu bytes of scratch; omp_solve_batched_noalloc holds %zu "
                     "(use omp_solve_batched with a plan)",
-                    L.total, kNoAllocScratchBytes);
+                    L.total, kNoAllocScratchBytes - kNoAllocCounterBytes);
     if (batch == 0) return CS_OK;
 
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
-    if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(CS_ENOTSUP, "device %d out of range", dev);
     char* base = nullptr;
-    {
-        std::lock_guard<std::mutex> lk(g_noalloc_mu);
-        if (!g_noalloc_base[dev]) {
-            void* ptr = nullptr;
-            e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-            if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(scratch)");
-            g_noalloc_base[dev] = ptr;
-        }
-        base = static_cast<char*>(g_noalloc_base[dev]);
-    }
+    int dev = 0;
+    cs_status st = noalloc_base(&base, &dev);
+    if (st != CS_OK) return st;
     P.device = dev;
     P.use_graphs = 0;
-    bind_workspace(&P, base, L);
+    bind_workspace(&P, base + kNoAllocCounterBytes, L);
+    P.counters = reinterpret_cast<unsigned*>(base);
     // The previous call's counters must not leak into this one.
-    e = cudaMemsetAsync(P.counters, 0, 16 * sizeof(unsigned), (cudaStream_t)stream);
+    cudaError_t e = cudaMemsetAsync(P.counters, 0, 16 * sizeof(unsigned), (cudaStream_t)stream);
     if (e != cudaSuccess) return cuda_fail(e, "cudaMemsetAsync(counters)");
     return solve(&P, A, m, n, lda, Y, ldy, batch, support, coef, n_iter, res_norm, sig_status, params,
                  nullptr, (cudaStream_t)stream);
+}
+
+extern "C" cs_status omp_solve_batched_noalloc_counters(uint32_t* out, int32_t reset, void* stream) {
+    if (!out) return fail(CS_EINVAL, "out is NULL");
+    char* base = nullptr;
+    int dev = 0;
+    cs_status st = noalloc_base(&base, &dev);
+    if (st != CS_OK) return st;
+    return read_counters(reinterpret_cast<unsigned*>(base), out, reset, (cudaStream_t)stream);
 }

@@ -102,7 +102,18 @@ struct VarlenOut {
     int* status;
 };
 
+// An uneven-batch instance that is not solved (CS_SIG_UNSUPPORTED): its
+// outputs, measurement vector, length m and sparsity k.
+struct VarlenRefuse {
+    VarlenOut o;
+    const float* y;
+    int m, k;
+};
+
 // ---- launchers (defined in the .cu files) --------------------------------
+// Outputs of refused instances: support -1, coef 0, n_iter 0, res_norm ||y||,
+// status CS_SIG_UNSUPPORTED (one warp each).
+cudaError_t launch_varlen_refuse(const VarlenRefuse* items, int count, cudaStream_t s);
 cudaError_t launch_varlen_gather(const float* const* ys, int m, int B, float* Y, cudaStream_t s);
 cudaError_t launch_varlen_scatter(const VarlenOut* outs, int k, int B, const int* support, const float* coef,
                                   const int* n_iter, const float* res_norm, const int* status, cudaStream_t s);

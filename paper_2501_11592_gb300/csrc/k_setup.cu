@@ -146,6 +146,25 @@ __global__ void k_varlen_scatter(const VarlenOut* __restrict__ outs, int k, int 
     }
 }
 
+__global__ void k_varlen_refuse(const VarlenRefuse* __restrict__ items, int count) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= count) return;
+    const VarlenRefuse it = items[b];
+    for (int q = lane; q < it.k; q += 32) {
+        it.o.support[q] = -1;
+        it.o.coef[q] = 0.f;
+    }
+    float ss = 0.f;
+    for (int i = lane; i < it.m; i += 32) ss = fmaf(it.y[i], it.y[i], ss);
+    ss = warp_sum(ss);
+    if (lane == 0) {
+        *it.o.n_iter = 0;
+        *it.o.res_norm = sqrtf(ss);
+        *it.o.status = CS_SIG_UNSUPPORTED;
+    }
+}
+
 // Per-signal initial state: r = y, s = 0, empty support, status "running".
 __global__ void k_setup(IterArgs a, const float* __restrict__ Y, int ldy, int clomp) {
     const int lane = threadIdx.x & 31;
@@ -219,6 +238,12 @@ cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh,
 cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s) {
     const int t = ceil_div(n, 64);
     k_gram_A<<<t * (t + 1) / 2, 256, 0, s>>>(A32, mp, n, GA);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_varlen_refuse(const VarlenRefuse* items, int count, cudaStream_t s) {
+    if (count <= 0) return cudaSuccess;
+    k_varlen_refuse<<<ceil_div(count, 8), 256, 0, s>>>(items, count);
     return cudaGetLastError();
 }
 

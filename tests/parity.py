@@ -36,6 +36,15 @@ def compare(gpu, ora, idx=None, coef_rtol=COEF_RTOL, margin=AMBIGUOUS_MARGIN,
     """gpu: dict of numpy arrays over the full batch; ora: oracle dict over the
     signals `idx` (default: all).  Returns a summary dict; raises
     AssertionError on any non-ambiguous difference."""
+    summary, fails = summarize(gpu, ora, idx, coef_rtol, margin, check_status, status_equiv)
+    assert not fails, "\n".join(fails[:20]) + f"\n({len(fails)} failures) {summary}"
+    assert summary["ambiguous"] <= max(1, int(MAX_AMBIGUOUS_FRAC * summary["signals"])), summary
+    return summary
+
+
+def summarize(gpu, ora, idx=None, coef_rtol=COEF_RTOL, margin=AMBIGUOUS_MARGIN,
+              check_status=True, status_equiv=None):
+    """The comparison of compare() without raising: (summary, failures)."""
     B = ora["support"].shape[0]
     idx = np.arange(B) if idx is None else np.asarray(idx)
     ambiguous, worst, fails = [], 0.0, []
@@ -66,10 +75,8 @@ def compare(gpu, ora, idx=None, coef_rtol=COEF_RTOL, margin=AMBIGUOUS_MARGIN,
             if int(gpu["n_iter"][b]) != int(ora["n_iter"][r]):
                 fails.append(f"signal {b}: n_iter gpu={gpu['n_iter'][b]} oracle={ora['n_iter'][r]}")
     summary = dict(signals=len(idx), ambiguous=len(ambiguous), max_coef_rel_err=worst,
-                   ambiguous_list=ambiguous[:10])
-    assert not fails, "\n".join(fails[:20]) + f"\n({len(fails)} failures) {summary}"
-    assert len(ambiguous) <= max(1, int(MAX_AMBIGUOUS_FRAC * len(idx))), summary
-    return summary
+                   failures=len(fails), ambiguous_list=ambiguous[:10])
+    return summary, fails
 
 
 def to_numpy(res):

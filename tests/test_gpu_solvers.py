@@ -69,19 +69,33 @@ def test_ragged_sizes(cs_gpu, torch, algo, form):
     print(algo, form, s)
 
 
-@pytest.mark.parametrize("algo,form", [("omp", None), ("clomp", "gram"), ("clomp", "gather")])
-def test_batched_workload_sampled(cs_gpu, torch, algo, form):
+_BATCHED_ORACLE = {}
+
+
+def batched_oracle(algo):
+    """The FP64 oracle over all 4096 signals of the benchmark workload (once
+    per algorithm and module)."""
+    if algo not in _BATCHED_ORACLE:
+        p = workloads.config_batched()
+        _, _, A64, Y64 = f32_problem(p.A, p.Y)
+        _BATCHED_ORACLE[algo] = run_oracle(A64, Y64, p.k, algo)
+    return _BATCHED_ORACLE[algo]
+
+
+@pytest.mark.parametrize("algo,prec,form", [("omp", "fp32", None), ("omp", "bf16", None),
+                                            ("clomp", "fp32", "gram"), ("clomp", "bf16", "gather")])
+def test_batched_workload_every_signal(cs_gpu, torch, algo, prec, form):
     """n=1024, m=256, 4096 signals, k=32 -- the benchmark's launch
-    configuration -- checked on a sample of 384 signals."""
+    configuration -- every signal against the FP64 oracle (plain fp32 OMP,
+    bf16 OMP, fp32 CLOMP in Gram form, bf16 CLOMP in the literal gather
+    form; the bf16 Gram form is the persistent solve, tested beside it)."""
     p = workloads.config_batched()
-    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
-    kw = {} if algo == "omp" else dict(form=form, **CL)
+    A32, Y32, _, _ = f32_problem(p.A, p.Y)
+    kw = dict(prec=prec) if algo == "omp" else dict(prec=prec, form=form, **CL)
     g = run_gpu(cs_gpu, torch, A32, Y32, p.k, algo, **kw)
-    idx = np.random.default_rng(0).choice(p.B, size=384, replace=False)
-    idx.sort()
-    o = run_oracle(A64, Y64[:, idx], p.k, algo)
-    s = compare(g, o, idx=idx)
-    print(algo, form, s)
+    s = compare(g, batched_oracle(algo))
+    print(algo, prec, form, s)
+    assert s["signals"] == p.B
     assert np.all(g["status"] == 0) and np.all(g["n_iter"] == 32)
 
 

@@ -196,33 +196,23 @@ def config_uneven(n_instances=2000, n_classes=32):
     return classes, assign, ks
 
 
-def uneven_batch(n_instances=192, n_classes=8, n_range=(256, 2048), ratio=(0.1, 0.25),
-                 k_frac=(0.01, 0.1), k_cap=64, m_cap=256, snr_db=30.0, seed=None):
-    """An uneven batch within the batched kernels' limits (m <= 256, k <= 64):
-    size classes with n log-uniform in n_range (rounded to 64), m/n uniform in
-    `ratio` (rounded to 16, capped at m_cap), Gaussian A (unit columns) for
-    even classes and +-1/sqrt(m) Bernoulli for odd ones; instances assigned
-    uniformly to classes with k uniform in k_frac * n (capped at k_cap and m);
-    values N(0,1); per-signal noise at snr_db.  Returns (classes, instances)
-    with classes[c] = A and instances[i] = (class, y, k, x_true)."""
-    rng = np.random.default_rng(SEED_BASE + CFG_UNEVEN if seed is None else seed)
-    classes = []
-    for c in range(n_classes):
-        n = int(round(math.exp(rng.uniform(math.log(n_range[0]), math.log(n_range[1]))) / 64.0)) * 64
-        n = max(n_range[0], min(n_range[1], n))
-        m = max(16, min(m_cap, int(round(n * rng.uniform(*ratio) / 16.0)) * 16))
-        A = bernoulli_matrix(rng, m, n) if c % 2 else gaussian_matrix(rng, m, n)
-        classes.append(A)
-    insts = []
-    for _ in range(n_instances):
-        c = int(rng.integers(0, n_classes))
-        m, n = classes[c].shape
-        lo, hi = max(1, int(k_frac[0] * n)), max(1, int(k_frac[1] * n))
-        k = int(min(k_cap, m, rng.integers(lo, hi + 1)))
+def uneven_class_data(classes, assign, ks, c, snr_db=30.0, dtype=np.float64):
+    """Materialise size class c of config_uneven: its matrix A (m x n; Gaussian
+    with unit columns for even classes, +-1/sqrt(m) Bernoulli for odd ones)
+    and, for every instance assigned to it, (instance index, y, x_true) with
+    x k-sparse N(0,1) at uniform positions and per-signal noise at snr_db.
+    Each class has its own seed, so classes can be drawn one at a time."""
+    cl = classes[c]
+    rng = rng_for(CFG_UNEVEN, salt=c + 1)
+    m, n = cl["m"], cl["n"]
+    A = bernoulli_matrix(rng, m, n) if cl["bernoulli"] else gaussian_matrix(rng, m, n)
+    items = []
+    for i in np.nonzero(np.asarray(assign) == c)[0]:
+        k = int(ks[i])
         x = sparse_coefficients(rng, n, 1, k, values="gauss")
-        y = add_noise(rng, classes[c] @ x, snr_db)[:, 0]
-        insts.append((c, y, k, x[:, 0]))
-    return classes, insts
+        y = add_noise(rng, A @ x, snr_db)[:, 0]
+        items.append((int(i), y, x[:, 0]))
+    return np.asfortranarray(A, dtype=dtype), items
 
 
 def named(name: str) -> Problem:
