@@ -338,7 +338,7 @@ cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* st
  * device memory and hands none to libraries.  Same arguments, kernels and
  * results as omp_solve_batched, minus the plan: the scratch is one fixed
  * 32 MiB device array that every GPU loading this library reserves until
- * the process exits (about 12 KiB per signal at m = 256, k <= 32, plus
+ * the process exits (about 21 KiB per signal at m = 256, k <= 32, plus
  * 6 bytes per element of A; larger problems get CS_EINVAL and belong on
  * omp_solve_batched).  The first call on each device looks the array's
  * address up (make it before any stream capture) and keeps it for the life

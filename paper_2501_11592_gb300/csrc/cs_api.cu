@@ -164,7 +164,7 @@ WsLayout ws_layout(int m, int n, int B, int K, bool clomp, bool gram_a) {
     L.gcol = cv.take<float>(Kk * Bm);
     L.dnorm = cv.take<float>(Bm);
     L.bt = cv.take<float>(Bm);
-    L.L = cv.take<double>(Kk * Kk * Bm);
+    L.L = cv.take<double>(2 * Kk * Kk * Bm);
     L.z = cv.take<double>(Kk * Bm);
     L.x64 = cv.take<double>(Kk * Bm);
     if (clomp) {

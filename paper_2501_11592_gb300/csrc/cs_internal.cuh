@@ -43,8 +43,9 @@ __host__ __device__ inline int ceil_div(int x, int a) { return (x + a - 1) / a; 
 //   cbound [B][n/16]     bf16: third largest |c| of each 16-atom group (bounds the
 //                   group's atoms that are not candidates)
 //   GA    [n][n]   Gram matrix of A (n <= kGramAMax), row j = a_j^T A
-//   gcol  [K][B]   Gram column A_S^T a_j of the new atom (float)
-//   L     [K][K][B] Cholesky factor (double), z, x64 [K][B] (double)
+//   gcol  [B][K]   Gram column A_S^T a_j of the new atom (float)
+//   L     [B][2][K][K] W = L^{-T} of the Cholesky factor L (double), by rows then
+//                   by columns; z, x64 [B][K] (double)
 //   G     [B][K][K] Gram matrix of the support (float, CLOMP Gram form), bvec [B][K]
 //   am, av [B][K]  Adam moments; tau [B] Adam step counter
 //   support, coef [B][k] (caller outputs, k = params.k)

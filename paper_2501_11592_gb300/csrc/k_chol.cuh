@@ -1,7 +1,20 @@
 // OMP least squares (Table "s forward block", OMP row: pinv of A(:,Mask)) as
-// an incremental float64 Cholesky update of one signal, shared by the
-// one-thread-per-signal kernel and the fused small-batch solve
-// (internal header).
+// an incremental float64 Cholesky update of one signal, run by one warp and
+// shared by the batched kernel (state in global memory) and the fused
+// small-batch solve (state in shared memory) (internal header).
+//
+// With L L^T = A_S^T A_S the solve keeps W = L^{-T} (upper triangular)
+// instead of L.  Adding atom a with Gram column g = A_S^T a, d = ||a||^2 and
+// b_t = a^T y:
+//   l    = L^{-1} g = W^T g            (the new row of L, a matrix-vector product)
+//   L_tt = sqrt(d - l.l)
+//   z_t  = (b_t - l.z) / L_tt          (forward substitution of L z = A_S^T y, one row)
+//   w    = [-W l; 1] / L_tt            (the new column of W = L'^{-T})
+//   x   += z_t w                       (x = W z = (A_S^T A_S)^{-1} A_S^T y)
+// Every step is a product over the lanes' entries with no serial triangular
+// solve, so the 32 lanes share the float64 work.  W is stored twice, by rows
+// (Wr[i*K + p] = W_ip) and by columns (Wc[p*K + i] = W_ip), so that both
+// products read consecutive addresses across the lanes.
 #pragma once
 
 #include "k_common.cuh"
@@ -9,55 +22,123 @@
 namespace cs {
 namespace {
 
-// Row t of L with L L^T = A_S^T A_S:  L[0:t,0:t] l = g,  L_tt = sqrt(d - l.l);
-// then z_t = (a_j^T y - l.z)/L_tt and x = L^{-T} z, written (as float) to
-// coef[0..t].  float64 throughout; one thread.  g_i = g[i * gs]; L (K x K),
-// z and x at element strides ls and vs.  Returns false for a dependent atom
-// (pivot below 2^-20 d, or NaN), leaving coef untouched.
-__device__ __forceinline__ bool chol_core(const int t, const int K, const float* g, const size_t gs,
-                                          const double d, const double bt, double* L, const size_t ls,
-                                          double* zv, double* xv, const size_t vs, float* coef) {
-#define LAT(i, p) L[((size_t)(i) * K + (p)) * ls]
-    double ssq = 0.0;
-    for (int i = 0; i < t; ++i) {
-        double s = (double)g[(size_t)i * gs];
-        for (int p = 0; p < i; ++p) s -= LAT(i, p) * LAT(t, p);
-        const double li = s / LAT(i, i);
-        LAT(t, i) = li;
-        ssq += li * li;
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;   // the same value on every lane (each step adds a commutative pair)
+}
+
+// One warp, NP = K/32 entries per lane (entry e of lane q is index q + 32e).
+// g[e]: the Gram column entry of that index (0 past t); d, bt as above; W
+// (both layouts, K x K), z and x (K) of this signal; coef[0..t] receives x
+// as float.  Returns false (the same on every lane) for a dependent atom
+// (pivot below 2^-20 d, or NaN), leaving the state untouched.  The caller
+// synchronises the warp before other lanes read what this wrote.
+template <int NP>
+__device__ __forceinline__ bool chol_warp(const int t, const int K, const float (&g)[NP], const double d,
+                                          const double bt, double* __restrict__ Wr, double* __restrict__ Wc,
+                                          double* __restrict__ z, double* __restrict__ x, float* __restrict__ coef) {
+    static_assert(NP == 1 || NP == 2, "K is 32 or 64");
+    const int lane = threadIdx.x & 31;
+    // l = W^T g: l_p = sum_{i <= p} W_ip g_i, i ascending
+    double l[NP];
+#pragma unroll
+    for (int e = 0; e < NP; ++e) l[e] = 0.0;
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+        const int i1 = min(t, 32 * (h + 1));
+        for (int i = 32 * h; i < i1; ++i) {
+            const double gi = (double)__shfl_sync(0xffffffffu, g[h], i & 31);
+            const double* row = Wr + (size_t)i * K;
+#pragma unroll
+            for (int e = h; e < NP; ++e) {
+                const int p = lane + 32 * e;
+                if (i <= p && p < t) l[e] = fma(row[p], gi, l[e]);
+            }
+        }
     }
+    double ssq = 0.0, lz = 0.0;
+#pragma unroll
+    for (int e = 0; e < NP; ++e) {
+        const int p = lane + 32 * e;
+        if (p < t) {
+            ssq = fma(l[e], l[e], ssq);
+            lz = fma(l[e], z[p], lz);
+        }
+    }
+    ssq = warp_sum_f64(ssq);
+    lz = warp_sum_f64(lz);
     const double piv = d - ssq;
     if (!(piv > 0x1p-20 * d)) return false;
     const double ltt = sqrt(piv);
-    LAT(t, t) = ltt;
-    double zt = bt;
-    for (int i = 0; i < t; ++i) zt -= LAT(t, i) * zv[(size_t)i * vs];
-    zt /= ltt;
-    zv[(size_t)t * vs] = zt;
-    for (int i = t; i >= 0; --i) {
-        double s = zv[(size_t)i * vs];
-        for (int p = i + 1; p <= t; ++p) s -= LAT(p, i) * xv[(size_t)p * vs];
-        const double xi = s / LAT(i, i);
-        xv[(size_t)i * vs] = xi;
-        coef[i] = (float)xi;
+    const double rinv = 1.0 / ltt;
+    const double zt = (bt - lz) / ltt;
+    // u = W l: u_i = sum_{p >= i} W_ip l_p, p ascending
+    double u[NP];
+#pragma unroll
+    for (int e = 0; e < NP; ++e) u[e] = 0.0;
+#pragma unroll
+    for (int h = 0; h < NP; ++h) {
+        const int p1 = min(t, 32 * (h + 1));
+        for (int p = 32 * h; p < p1; ++p) {
+            const double lp = __shfl_sync(0xffffffffu, l[h], p & 31);
+            const double* col = Wc + (size_t)p * K;
+#pragma unroll
+            for (int e = 0; e <= h; ++e) {
+                const int i = lane + 32 * e;
+                if (i <= p) u[e] = fma(col[i], lp, u[e]);
+            }
+        }
+    }
+    // the new column of W, and x += z_t w
+#pragma unroll
+    for (int e = 0; e < NP; ++e) {
+        const int i = lane + 32 * e;
+        if (i < t) {
+            const double w = -u[e] * rinv;
+            Wr[(size_t)i * K + t] = w;
+            Wc[(size_t)t * K + i] = w;
+            const double xi = fma(zt, w, x[i]);
+            x[i] = xi;
+            coef[i] = (float)xi;
+        } else if (i == t) {
+            Wr[(size_t)t * K + t] = rinv;
+            Wc[(size_t)t * K + t] = rinv;
+            z[t] = zt;
+            const double xt = zt * rinv;
+            x[t] = xt;
+            coef[t] = (float)xt;
+        }
     }
     return true;
-#undef LAT
 }
 
-// The batched layout: L[(i*K + p)*B + b], z[i*B + b], x[i*B + b], the Gram
-// column gcol[i*B + b]; status, support and n_iter updated in place.
+// The batched layout: per signal b, W by rows then by columns at
+// L + b * 2K^2, z and x at b*K, the Gram column gcol[b*K + i]; status,
+// support and n_iter updated in place.  One warp.
+template <int NP>
 __device__ __forceinline__ void chol_update(const IterArgs& a, const int b) {
+    const int lane = threadIdx.x & 31;
     if (a.status[b] >= 0) return;
     const int t = a.n_iter[b];
-    const size_t B = (size_t)a.B;
-    if (!chol_core(t, a.kmax, a.gcol + b, B, (double)a.dnorm[b], (double)a.bt[b], a.L + b, B, a.z + b, a.x64 + b, B,
-                   a.coef + (size_t)b * a.k)) {
-        a.status[b] = CS_SIG_DEPENDENT;
-        a.support[(size_t)b * a.k + t] = -1;
-        return;
+    const int K = a.kmax;
+    float g[NP];
+#pragma unroll
+    for (int e = 0; e < NP; ++e) {
+        const int i = lane + 32 * e;
+        g[e] = (i < t) ? a.gcol[(size_t)b * K + i] : 0.f;
     }
-    a.n_iter[b] = t + 1;
+    double* Wr = a.L + (size_t)b * 2 * K * K;
+    const bool ok = chol_warp<NP>(t, K, g, (double)a.dnorm[b], (double)a.bt[b], Wr, Wr + (size_t)K * K,
+                                  a.z + (size_t)b * K, a.x64 + (size_t)b * K, a.coef + (size_t)b * a.k);
+    if (lane == 0) {
+        if (!ok) {
+            a.status[b] = CS_SIG_DEPENDENT;
+            a.support[(size_t)b * a.k + t] = -1;
+        } else {
+            a.n_iter[b] = t + 1;
+        }
+    }
 }
 
 }  // namespace

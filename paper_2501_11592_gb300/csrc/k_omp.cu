@@ -1,19 +1,20 @@
 // OMP least squares (Table "s forward block", OMP row: pinv of A(:,Mask)) as
 // an incremental float64 Cholesky update, and the residual + stopping test of
-// Eq. 2 shared by OMP and CLOMP.  The Cholesky runs one thread per signal so
-// that every float64 lane does useful work on a part whose float64 rate is
-// low; the residual runs one warp per signal (coalesced column gathers).
+// Eq. 2 shared by OMP and CLOMP.  Both run one warp per signal: the Cholesky
+// update as two matrix-vector products over the lanes (k_chol.cuh), the
+// residual with coalesced column gathers.
 #include "k_chol.cuh"
 #include "k_resid.cuh"
 
 namespace cs {
 namespace {
 
-__global__ void __launch_bounds__(32) k_chol(IterArgs a) {
+template <int NP>
+__global__ void __launch_bounds__(256) k_chol(IterArgs a) {
     pdl_wait();      // no early trigger: the successor launches when this grid completes
-    const int b = blockIdx.x * blockDim.x + threadIdx.x;
-    if (b >= a.B) return;
-    chol_update(a, b);
+    const int nwarps = gridDim.x * (blockDim.x >> 5);
+    for (int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); b < a.B; b += nwarps)
+        chol_update<NP>(a, b);
 }
 
 
@@ -29,8 +30,12 @@ __global__ void __launch_bounds__(256) k_resid(IterArgs a) {
 }  // namespace
 
 cudaError_t launch_chol(const IterArgs& a, cudaStream_t s) {
-    // one warp per CTA spreads the float64 work over as many SMs as possible
-    return launch_pdl(k_chol, dim3(ceil_div(a.B, 32)), dim3(32), 0, s, a);
+    if (a.kmax == 32) {
+        const int grid = resident_grid((const void*)k_chol<1>, 256, ceil_div(a.B, 8));
+        return launch_pdl(k_chol<1>, dim3(grid), dim3(256), 0, s, a);
+    }
+    const int grid = resident_grid((const void*)k_chol<2>, 256, ceil_div(a.B, 8));
+    return launch_pdl(k_chol<2>, dim3(grid), dim3(256), 0, s, a);
 }
 
 

@@ -9,8 +9,8 @@
 //     shared memory for the whole solve when it fits (else staged a few K
 //     values at a time);
 //   * warp 0 appends the atom (bitset, support, Gram column from A^T A,
-//     a_j^T y), thread 0 runs the float64 Cholesky update and the triangular
-//     solves, warp 0 forms the residual and applies the stop test.
+//     a_j^T y), runs the float64 Cholesky update (k_chol.cuh), forms the
+//     residual and applies the stop test.
 // The signal's residual, y, support, coefficients, Gram column, bitset and
 // Cholesky factor stay in shared memory for the whole solve; the outputs are
 // written as they change.  Every step uses the batched path's arithmetic in
@@ -27,11 +27,12 @@ constexpr int OF_KC = 8;              // K values of A staged per step
 constexpr int OF_MAX_SMEM = 200 * 1024;
 constexpr size_t OF_STATIC = sizeof(float) * OF_KC * (OF_THREADS + 1) + 1024;
 
-// Dynamic shared memory: L (K x K), z, x (float64) | r, y (mp floats) |
-// Gram column, coefficients (K floats) | support (K ints) | bitset (nw words)
-// | (when it fits) A itself, K-major with a padded row of n + 1 atoms.
+// Dynamic shared memory: W = L^{-T} by rows and by columns (2 K x K), z, x
+// (float64) | r, y (mp floats) | Gram column, coefficients (K floats) |
+// support (K ints) | bitset (nw words) | (when it fits) A itself, K-major
+// with a padded row of n + 1 atoms.
 __host__ __device__ inline size_t of_state(int K, int mp, int nw) {
-    const size_t v = sizeof(double) * ((size_t)K * K + 2 * (size_t)K) + sizeof(float) * (2 * (size_t)mp + 2 * (size_t)K) +
+    const size_t v = sizeof(double) * (2 * (size_t)K * K + 2 * (size_t)K) + sizeof(float) * (2 * (size_t)mp + 2 * (size_t)K) +
                      sizeof(int) * (size_t)K + sizeof(uint32_t) * (size_t)nw;
     return (v + 15) & ~(size_t)15;
 }
@@ -48,8 +49,8 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
     __shared__ int sh_status, sh_t;
     extern __shared__ __align__(16) unsigned char sh_dyn[];
     const int K = a.kmax;
-    double* Ls = reinterpret_cast<double*>(sh_dyn);
-    double* zs = Ls + (size_t)K * K;
+    double* Ws = reinterpret_cast<double*>(sh_dyn);
+    double* zs = Ws + 2 * (size_t)K * K;
     double* xs = zs + K;
     float* rs = reinterpret_cast<float*>(xs + K);
     float* ys = rs + a.mp;
@@ -153,10 +154,18 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
             const int i = i0 + lane;
             if (i < t) gs[i] = garow[ss[i]];
         }
-        __syncwarp();                    // the Gram column, for thread 0
-        // ---- float64 Cholesky update and solves (thread 0)
+        __syncwarp();                    // the Gram column
+        // ---- float64 Cholesky update (the batched kernel's arithmetic)
+        bool ok;
+        if (K == 32) {
+            float gl[1] = {lane < t ? gs[lane] : 0.f};
+            ok = chol_warp<1>(t, K, gl, (double)dd, (double)by, Ws, Ws + (size_t)K * K, zs, xs, cs_);
+        } else {
+            float gl[2] = {lane < t ? gs[lane] : 0.f, lane + 32 < t ? gs[lane + 32] : 0.f};
+            ok = chol_warp<2>(t, K, gl, (double)dd, (double)by, Ws, Ws + (size_t)K * K, zs, xs, cs_);
+        }
         if (lane == 0) {
-            if (!chol_core(t, K, gs, 1, (double)dd, (double)by, Ls, 1, zs, xs, 1, cs_)) {
+            if (!ok) {
                 a.status[b] = CS_SIG_DEPENDENT;
                 a.support[(size_t)b * a.k + t] = -1;
                 sh_status = CS_SIG_DEPENDENT;

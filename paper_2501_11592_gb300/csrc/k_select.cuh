@@ -35,7 +35,7 @@ __device__ __forceinline__ void append_atom(const IterArgs& a, const int b, cons
             const int ji = (i < t) ? sup[i] : -1;
             const float g = garow ? (ji >= 0 ? garow[ji] : 0.f) : warp_dots32<MCH>(a.A32, a.mp, ji, aj);
             if (i < t) {
-                if (a.need_gcol) a.gcol[(size_t)i * a.B + b] = g;
+                if (a.need_gcol) a.gcol[(size_t)b * a.kmax + i] = g;
                 if (a.need_gram) {
                     float* G = a.G + (size_t)b * a.kmax * a.kmax;
                     G[(size_t)t * a.kmax + i] = g;
