@@ -59,6 +59,10 @@ def lib():
                                         ctypes.c_int, ctypes.c_int, d, ctypes.c_int, pi, pd, pi, pd, pi,
                                         pd, pd, pd, ctypes.c_int]
             L.cs_oracle_omp.restype = ctypes.c_int
+            L.cs_oracle_omp_method.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int,
+                                               ctypes.c_int, ctypes.c_int, d, ctypes.c_int, ctypes.c_int, pi,
+                                               pd, pi, pd, pi, pd, pd, pd, ctypes.c_int]
+            L.cs_oracle_omp_method.restype = ctypes.c_int
             L.cs_oracle_clomp.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int,
                                           ctypes.c_int, ctypes.c_int, d, ctypes.c_int, ctypes.c_int, d, d,
                                           d, d, ctypes.c_int, d, d, pd, ctypes.c_int, ctypes.c_int,
@@ -149,16 +153,24 @@ def _outputs(B, k):
                 top1=np.zeros((B, k)), top2=np.zeros((B, k)), res_hist=np.zeros((B, k)))
 
 
-def omp(A, Y, k, tol=0.0, max_iter=None, nthreads=0):
-    """Plain OMP for every column of Y.  Returns a dict of outputs."""
+_OMP_METHODS = {"auto": 0, "householder": 1, "iqr": 2}
+
+
+def omp(A, Y, k, tol=0.0, max_iter=None, nthreads=0, method="auto"):
+    """Plain OMP for every column of Y.  Returns a dict of outputs.
+    method: "householder" refactorises A_S by Householder QR every
+    iteration, "iqr" grows a QR factorisation by modified Gram-Schmidt
+    (twice) one column per iteration, "auto" takes the latter when the
+    refactorisations would cost m k^3 / 3 > 1e9 flops.  A single signal correlates with the atoms split over the
+    threads."""
     A = _f64F(A)
     Y = _f64F(Y if np.ndim(Y) == 2 else np.reshape(Y, (-1, 1)))
     m, n = A.shape
     B = Y.shape[1]
     max_iter = k if max_iter is None else max_iter
     o = _outputs(B, k)
-    rc = lib().cs_oracle_omp(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B, k,
-                             float(tol), int(max_iter), _p(o["support"], ctypes.c_int32),
+    rc = lib().cs_oracle_omp_method(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B, k,
+                             float(tol), int(max_iter), _OMP_METHODS[method], _p(o["support"], ctypes.c_int32),
                              _p(o["coef"], ctypes.c_double), _p(o["n_iter"], ctypes.c_int32),
                              _p(o["res_norm"], ctypes.c_double), _p(o["status"], ctypes.c_int32),
                              _p(o["top1"], ctypes.c_double), _p(o["top2"], ctypes.c_double),

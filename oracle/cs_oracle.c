@@ -14,7 +14,10 @@
  *     the selected columns by least squares (the pinv of A(:,Mask)), update
  *     the residual.  The least-squares fit here is a Householder QR of A_S
  *     recomputed from scratch at every iteration (a different algorithm from
- *     the GPU's incremental Cholesky).
+ *     the GPU's incremental Cholesky) while m k^3 / 3 <= 1e9; larger problems
+ *     (k in the thousands) grow a QR factorisation by one column per
+ *     iteration instead: modified Gram-Schmidt of the new column against the
+ *     previous orthonormal columns, applied twice, then back substitution.
  *   - CLOMP, structure 1 (Methods "Coefficients learning on OMP"): the same
  *     selection, but s (n learnable parameters) is masked by the OR-accumulated
  *     Mask, y' = A (s .* Mask) is formed, and s is learned by back-propagating
@@ -220,9 +223,108 @@ static int select_atoms_th(const double* A, int m, int n, int lda, const double*
     return take;
 }
 
+/*
+ * Incremental QR of A_S for large supports: Q (m x t, orthonormal columns)
+ * and R (t x t upper triangular, column-major with leading dimension kmax)
+ * gain column t from atom a.  Modified Gram-Schmidt against q_0..q_{t-1},
+ * run twice (the second pass removes what rounding left of the first), then
+ * R_tt = ||v|| and q_t = v / R_tt.  Returns 0, or 3 when the atom is
+ * dependent (R_tt^2 <= 1e-12 ||a||^2, the Householder path's rule).
+ */
+static int iqr_append(double* Q, double* Rm, int kmax, int m, int t, const double* a) {
+    double* v = Q + (size_t)t * m;
+    memcpy(v, a, sizeof(double) * m);
+    double* rc = Rm + (size_t)t * kmax;
+    for (int q = 0; q <= t; ++q) rc[q] = 0.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int q = 0; q < t; ++q) {
+            const double* qq = Q + (size_t)q * m;
+            double h = dot(qq, v, m);
+            for (int i = 0; i < m; ++i) v[i] -= h * qq[i];
+            rc[q] += h;
+        }
+    }
+    double anorm = nrm2(a, m), vn = nrm2(v, m);
+    if (vn * vn <= 1e-12 * anorm * anorm) return ST_DEP;
+    rc[t] = vn;
+    for (int i = 0; i < m; ++i) v[i] /= vn;
+    return 0;
+}
+
+/* Correlation + selection of select_atom with the atoms split over threads
+ * (used for a single large signal); the argmax is taken afterwards in atom
+ * order, so ties still go to the lowest index. */
+static int select_atom_par(const double* A, int m, int n, int lda, const double* r,
+                           const unsigned char* inS, double* c, double* top1, double* top2) {
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static)
+#endif
+    for (int j = 0; j < n; ++j) c[j] = inS[j] ? -1.0 : fabs(dot(A + (size_t)j * lda, r, m));
+    int best = -1;
+    double b1 = -1.0, b2 = -1.0;
+    for (int j = 0; j < n; ++j) {
+        if (inS[j]) continue;
+        double a = c[j];
+        if (a > b1) { b2 = b1; b1 = a; best = j; }
+        else if (a > b2) { b2 = a; }
+    }
+    *top1 = b1;
+    *top2 = b2;
+    return best;
+}
+
 static int all_finite(const double* y, int m) {
     for (int i = 0; i < m; ++i) if (!isfinite(y[i])) return 0;
     return 1;
+}
+
+/* OMP with the incremental QR (iqr_append), for supports too large to
+ * refactorise every iteration; same selection, stopping rules and outputs as
+ * omp_one.  par != 0 splits the correlation over threads. */
+static void omp_one_iqr(const double* A, int m, int n, int lda, const double* y, int k,
+                        double tol, int max_iter, int par, int32_t* support, double* coef,
+                        int32_t* n_iter, double* res_norm, int32_t* status,
+                        double* top1, double* top2, double* res_hist) {
+    for (int q = 0; q < k; ++q) { support[q] = -1; coef[q] = 0.0; top1[q] = -1.0; top2[q] = -1.0; res_hist[q] = NAN; }
+    if (!all_finite(y, m)) { *n_iter = 0; *res_norm = NAN; *status = ST_NONFINITE; return; }
+    double* r = (double*)malloc(sizeof(double) * m);
+    double* Q = (double*)malloc(sizeof(double) * (size_t)m * k);
+    double* Rm = (double*)malloc(sizeof(double) * (size_t)k * k);
+    double* qty = (double*)malloc(sizeof(double) * k);
+    double* z = (double*)malloc(sizeof(double) * k);
+    double* c = par ? (double*)malloc(sizeof(double) * n) : NULL;
+    unsigned char* inS = (unsigned char*)calloc(n, 1);
+    memcpy(r, y, sizeof(double) * m);
+    double rho = nrm2(r, m);
+    int iters = k < max_iter ? k : max_iter;
+    int t = 0, st = -1;
+    if (rho <= tol) st = ST_TOL;
+    while (st < 0 && t < iters) {
+        int j = par ? select_atom_par(A, m, n, lda, r, inS, c, &top1[t], &top2[t])
+                    : select_atom(A, m, n, lda, r, inS, &top1[t], &top2[t]);
+        if (j < 0) { st = ST_MAXIT; break; }
+        if (iqr_append(Q, Rm, k, m, t, A + (size_t)j * lda) != 0) { st = ST_DEP; top1[t] = top2[t] = -1.0; break; }
+        qty[t] = dot(Q + (size_t)t * m, y, m);
+        support[t] = j;
+        inS[j] = 1;
+        ++t;
+        /* back substitution R z = Q^T y */
+        for (int i = t - 1; i >= 0; --i) {
+            double sacc = qty[i];
+            for (int q = i + 1; q < t; ++q) sacc -= Rm[(size_t)q * k + i] * z[q];
+            z[i] = sacc / Rm[(size_t)i * k + i];
+        }
+        for (int q = 0; q < t; ++q) coef[q] = z[q];
+        residual(A, m, lda, support, t, coef, y, r);
+        rho = nrm2(r, m);
+        res_hist[t - 1] = rho;
+        if (rho <= tol) st = ST_TOL;
+    }
+    if (st < 0) st = (t == k) ? ST_K : ST_MAXIT;
+    *n_iter = t;
+    *res_norm = rho;
+    *status = st;
+    free(r); free(Q); free(Rm); free(qty); free(z); free(c); free(inS);
 }
 
 static void omp_one(const double* A, int m, int n, int lda, const double* y, int k,
@@ -429,21 +531,39 @@ static int bad_args(const double* A, int m, int n, int lda, const double* Y, int
     return 0;
 }
 
+/* method: 0 chooses by size (the incremental QR when the refactorisations
+ * would cost m k^3 / 3 > 1e9 flops in all, else the
+ * Householder QR recomputed each iteration), 1 forces the Householder QR,
+ * 2 the incremental QR.  A single signal (B = 1) correlates with the atoms
+ * split over the threads; larger batches split the signals. */
+int cs_oracle_omp_method(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
+                         int k, double tol, int max_iter, int method, int32_t* support, double* coef,
+                         int32_t* n_iter, double* res_norm, int32_t* status, double* top1,
+                         double* top2, double* res_hist, int nthreads) {
+    if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0 || method < 0 || method > 2) return -1;
+    const int iqr = method == 2 || (method == 0 && (double)m * (double)k * (double)k * (double)k / 3.0 > 1e9);
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4) if (B > 1)
+#endif
+    for (int b = 0; b < B; ++b) {
+        size_t o = (size_t)b * k;
+        if (iqr)
+            omp_one_iqr(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, B == 1, support + o, coef + o,
+                        n_iter + b, res_norm + b, status + b, top1 + o, top2 + o, res_hist + o);
+        else
+            omp_one(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, support + o, coef + o,
+                    n_iter + b, res_norm + b, status + b, top1 + o, top2 + o, res_hist + o);
+    }
+    return 0;
+}
+
 int cs_oracle_omp(const double* A, int m, int n, int lda, const double* Y, int ldy, int B,
                   int k, double tol, int max_iter, int32_t* support, double* coef,
                   int32_t* n_iter, double* res_norm, int32_t* status, double* top1,
                   double* top2, double* res_hist, int nthreads) {
-    if (bad_args(A, m, n, lda, Y, ldy, B, k) || max_iter <= 0) return -1;
-#ifdef _OPENMP
-    if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 4)
-#endif
-    for (int b = 0; b < B; ++b) {
-        size_t o = (size_t)b * k;
-        omp_one(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, support + o, coef + o,
-                n_iter + b, res_norm + b, status + b, top1 + o, top2 + o, res_hist + o);
-    }
-    return 0;
+    return cs_oracle_omp_method(A, m, n, lda, Y, ldy, B, k, tol, max_iter, 0, support, coef, n_iter,
+                                res_norm, status, top1, top2, res_hist, nthreads);
 }
 
 /* th: 0 (or >= 1) selects one atom per iteration; 0 < th < 1 selects by the

@@ -64,7 +64,8 @@ def _erc_holds(A, S):
     return max(np.abs(P @ A[:, j]).sum() for j in others) < 1.0
 
 
-def test_bruteforce_tiny_noiseless():
+@pytest.mark.parametrize("method", ["householder", "iqr"])
+def test_bruteforce_tiny_noiseless(method):
     """n <= 20, k <= 3: the minimum-residual support over all C(n,k) supports
     is the true one, and OMP recovers it wherever the ERC holds."""
     rng = np.random.default_rng(3)
@@ -83,7 +84,7 @@ def test_bruteforce_tiny_noiseless():
             if res < best_res - 1e-12:
                 best, best_res = list(S), res
         assert best == S_true
-        o = oracle.omp(A, y, k, tol=0.0)
+        o = oracle.omp(A, y, k, tol=0.0, method=method)
         if _erc_holds(A, S_true):
             n_erc += 1
             assert sorted(o["support"][0].tolist()) == S_true
@@ -93,13 +94,14 @@ def test_bruteforce_tiny_noiseless():
     assert n_erc >= 10
 
 
-def test_residual_orthogonal_and_monotone():
+@pytest.mark.parametrize("method", ["householder", "iqr"])
+def test_residual_orthogonal_and_monotone(method):
     rng = np.random.default_rng(4)
     A = _rand_A(rng, 48, 160)
     X = workloads.sparse_coefficients(rng, 160, 6, 10, values="gauss")
     Y = workloads.add_noise(rng, A @ X, 30.0)
     for kk in range(1, 11):
-        o = oracle.omp(A, Y, kk)
+        o = oracle.omp(A, Y, kk, method=method)
         for b in range(Y.shape[1]):
             S = o["support"][b]
             r = Y[:, b] - A[:, S] @ o["coef"][b]
@@ -110,7 +112,8 @@ def test_residual_orthogonal_and_monotone():
     assert np.all(np.diff(h, axis=1) <= 1e-12)
 
 
-def test_orthonormal_closed_form():
+@pytest.mark.parametrize("method", ["householder", "iqr"])
+def test_orthonormal_closed_form(method):
     """A orthonormal (m = n): supports come in descending |A^T y| order, the
     coefficients are (A^T y)_S and ||r||^2 = ||y||^2 - sum of selected c^2."""
     rng = np.random.default_rng(5)
@@ -118,7 +121,7 @@ def test_orthonormal_closed_form():
     Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
     Y = rng.standard_normal((n, 3))
     k = 7
-    o = oracle.omp(Q, Y, k)
+    o = oracle.omp(Q, Y, k, method=method)
     for b in range(3):
         c = Q.T @ Y[:, b]
         order = np.argsort(-np.abs(c), kind="stable")[:k]
@@ -140,50 +143,94 @@ def test_single_signal_exact_recovery():
     assert o["status"][0] == 1 and o["n_iter"][0] == 8
 
 
-def test_tie_lowest_index_and_dependent_atom():
+@pytest.mark.parametrize("method", ["householder", "iqr"])
+def test_tie_lowest_index_and_dependent_atom(method):
     rng = np.random.default_rng(6)
     A = _rand_A(rng, 12, 30)
     A[:, 17] = A[:, 5]                     # duplicated atom
     y = 3.0 * A[:, 5] + 0.5 * A[:, 9]
-    o = oracle.omp(A, y, 2)
+    o = oracle.omp(A, y, 2, method=method)
     assert o["support"][0, 0] == 5         # exact tie 5/17 -> lowest index
     assert o["top2"][0, 0] == o["top1"][0, 0]
     # more atoms than measurements can carry: the 13th column is dependent
     Y = rng.standard_normal((12, 1))
-    o = oracle.omp(A, Y, 12, tol=0.0)
+    o = oracle.omp(A, Y, 12, tol=0.0, method=method)
     assert o["status"][0] in (0, 3)
     B2 = _rand_A(rng, 4, 8)
     B2[:, 1] = B2[:, 0]
     B2[:, 2] = B2[:, 0]
     y2 = B2[:, 0] * 2.0
-    o = oracle.omp(B2, y2, 3, tol=0.0)
+    o = oracle.omp(B2, y2, 3, tol=0.0, method=method)
     # after picking atom 0 the residual is 0; the next pick is dependent
     assert o["status"][0] == 3 and o["n_iter"][0] == 1 and o["support"][0, 0] == 0
 
 
-def test_nonfinite_and_stop_rules():
+@pytest.mark.parametrize("method", ["householder", "iqr"])
+def test_nonfinite_and_stop_rules(method):
     rng = np.random.default_rng(7)
     A = _rand_A(rng, 16, 40)
     Y = rng.standard_normal((16, 4))
     Y[3, 1] = np.nan
     Y[:, 2] = 0.0
-    o = oracle.omp(A, Y, 5, tol=1e-9, max_iter=3)
+    o = oracle.omp(A, Y, 5, tol=1e-9, max_iter=3, method=method)
     assert o["status"].tolist() == [2, 4, 1, 2]
     assert o["n_iter"].tolist() == [3, 0, 0, 3]
     assert np.all(o["support"][1] == -1)
-    o = oracle.omp(A, Y[:, [0]], 5, tol=0.0, max_iter=5)
+    o = oracle.omp(A, Y[:, [0]], 5, tol=0.0, max_iter=5, method=method)
     assert o["status"][0] == 0 and o["n_iter"][0] == 5
 
 
-def test_batch_invariance_and_leading_dims():
+@pytest.mark.parametrize("method", ["householder", "iqr"])
+def test_batch_invariance_and_leading_dims(method):
     rng = np.random.default_rng(8)
     A = _rand_A(rng, 20, 50)
     Y = rng.standard_normal((20, 5))
-    o_all = oracle.omp(A, Y, 6)
+    o_all = oracle.omp(A, Y, 6, method=method)
     for b in range(5):
-        o1 = oracle.omp(A, Y[:, b], 6)
+        o1 = oracle.omp(A, Y[:, b], 6, method=method)
         assert np.array_equal(o1["support"][0], o_all["support"][b])
         assert np.array_equal(o1["coef"][0], o_all["coef"][b])
+
+
+def test_iqr_matches_householder_on_larger_supports():
+    """The incremental QR (modified Gram-Schmidt, twice) and the Householder
+    QR recomputed every iteration are different algorithms for the same
+    least-squares fits: same supports, coefficients to 1e-11, on noisy
+    signals with supports of 100 atoms."""
+    rng = np.random.default_rng(31)
+    A = _rand_A(rng, 300, 900)
+    X = workloads.sparse_coefficients(rng, 900, 3, 100, values="gauss")
+    Y = workloads.add_noise(rng, A @ X, 30.0)
+    a = oracle.omp(A, Y, 100, method="householder")
+    b = oracle.omp(A, Y, 100, method="iqr")
+    assert np.array_equal(a["support"], b["support"])
+    for q in range(3):
+        assert np.linalg.norm(a["coef"][q] - b["coef"][q]) <= 1e-11 * np.linalg.norm(a["coef"][q])
+    assert np.allclose(a["res_norm"], b["res_norm"], rtol=1e-11)
+
+
+def test_iqr_large_noiseless_exact_recovery_single_signal():
+    """A noiseless k-sparse signal with m well above 2 k log(n/k): the
+    incremental-QR oracle (one signal, atoms split over threads) recovers the
+    support and the coefficients to 1e-9, its residual is orthogonal to the
+    selected atoms, and the result equals the same signal solved inside a
+    batch (signals split over threads)."""
+    rng = np.random.default_rng(32)
+    m, n, k = 600, 2400, 120
+    A = _rand_A(rng, m, n)
+    X = workloads.sparse_coefficients(rng, n, 2, k, values="gauss")
+    Y = A @ X
+    o1 = oracle.omp(A, Y[:, 0], k, method="iqr")
+    assert sorted(o1["support"][0].tolist()) == sorted(np.nonzero(X[:, 0])[0].tolist())
+    xr = np.zeros(n)
+    xr[o1["support"][0]] = o1["coef"][0]
+    assert np.abs(xr - X[:, 0]).max() <= 1e-9 * np.abs(X[:, 0]).max()
+    S = o1["support"][0]
+    r = Y[:, 0] - A[:, S] @ o1["coef"][0]
+    assert np.abs(A[:, S].T @ r).max() <= 1e-10 * np.linalg.norm(A[:, S], 2) * np.linalg.norm(Y[:, 0])
+    o2 = oracle.omp(A, Y, k, method="iqr")
+    assert np.array_equal(o2["support"][0], o1["support"][0])
+    assert np.array_equal(o2["coef"][0], o1["coef"][0])
 
 
 def test_golden_worked_examples():
