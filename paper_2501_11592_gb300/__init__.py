@@ -349,9 +349,9 @@ def _varlen(fn, instances, params, plan, stream):
     if plan is None:
         # instances beyond the kernels' limits are refused per instance
         # (SIG_UNSUPPORTED), so the default plan stops at those limits
-        m_max = min(1024, max(int(A.shape[0]) for A, _, _ in instances))
+        m_max = min(32768, max(int(A.shape[0]) for A, _, _ in instances))
         n_max = max(int(A.shape[1]) for A, _, _ in instances)
-        k_max = min(64, max(int(k) for _, _, k in instances))
+        k_max = min(4096, max(int(k) for _, _, k in instances))
         plan = _plan_for(m_max, n_max, 1024, k_max, None)
     keep, outs = [], []
     arr = (Instance * len(instances))()

@@ -54,6 +54,10 @@ struct DeviceGuard {
 struct cs_plan {
     int device = 0;
     int m_max = 0, n_max = 0, B_max = 0, k_max = 0;
+    int k_user = 0;            // the plan's k_max as created (k_max: the on-chip kernels' 32 or 64)
+    int no_large = 0;          // 1: never run the large-instance path (it allocates)
+    char* lg = nullptr;        // workspace of the large-instance path, on first use
+    size_t lg_bytes = 0;
     int mp_max = 0, mh_max = 0, nw_max = 0, nch_max = 0;
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -293,11 +297,81 @@ cs_status validate(const cs_plan* P, const float* A, int m, int n, int lda, cons
     if (m > P->m_max || n > P->n_max || B > P->B_max)
         return fail(CS_EINVAL, "problem m=%d n=%d batch=%d exceeds the plan (%d, %d, %d)", m, n, B,
                     P->m_max, P->n_max, P->B_max);
-    if (op->k > P->k_max) return fail(CS_ENOTSUP, "k=%d exceeds the plan k_max=%d", op->k, P->k_max);
+    if (op->k > P->k_user) return fail(CS_ENOTSUP, "k=%d exceeds the plan k_max=%d", op->k, P->k_user);
     if (B > 0 && (!A || !Y || !support || !coef || !n_iter || !res_norm || !sig_status))
         return fail(CS_EINVAL, "a required array pointer is NULL");
-    if (op->prec == CS_CORR_BF16 && !corr_tc_supported(m, n))
-        return fail(CS_ENOTSUP, "bf16 tensor-core correlation unavailable for m=%d n=%d", m, n);
+    return CS_OK;
+}
+
+// Instances the on-chip batched kernels do not take: more rows than a warp
+// holds, a support beyond the plan's on-chip K, or the bf16 correlation
+// outside the tensor-core kernel's sizes.  Plain OMP runs them on the
+// large-instance path.
+bool needs_large(const cs_plan* P, int m, int n, int k, int prec) {
+    return m > kMaxRowChunks * 128 || k > P->k_max || (prec == CS_CORR_BF16 && !corr_tc_supported(m, n));
+}
+
+cs_status ensure_lg(cs_plan* P, size_t bytes) {
+    if (bytes <= P->lg_bytes) return CS_OK;
+    if (P->lg) {
+        cudaError_t e = cudaFree(P->lg);
+        P->lg = nullptr;
+        P->lg_bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
+    }
+    cudaError_t e = cudaMalloc(&P->lg, bytes);
+    if (e != cudaSuccess) {
+        P->lg = nullptr;
+        return fail(CS_ENOMEM, "cudaMalloc(large-instance workspace, %zu bytes): %s", bytes, cudaGetErrorString(e));
+    }
+    P->lg_bytes = bytes;
+    return CS_OK;
+}
+
+// Plain OMP of signals sharing A on the large-instance path, in chunks whose
+// workspace stays within a few GB.
+constexpr size_t kLargeChunkBytes = (size_t)8 << 30;
+
+cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const std::vector<const float*>& ys,
+                      const std::vector<LargeOut>& outs, const cs_omp_params* op, cudaStream_t s) {
+    if (P->no_large) return fail(CS_ENOTSUP, "this entry point runs only the on-chip kernels (m <= 1024, k <= 64, "
+                                             "bf16: m <= 256, n <= 4096)");
+    const size_t count = ys.size();
+    int kmax = 1;
+    for (const LargeOut& o : outs) kmax = std::max(kmax, o.k);
+    if (!large_supported(m, n, kmax))
+        return fail(CS_ENOTSUP, "large OMP supports m <= %d and k <= %d (m=%d k=%d)", kLargeMaxM, kLargeMaxK, m, kmax);
+    const int bf16 = op->prec == CS_CORR_BF16 ? 1 : 0;
+    // signals per chunk: the fixed part (bf16 A) plus as many signals as fit the budget
+    const size_t one = large_ws_bytes(m, n, 1, kmax, bf16), two = large_ws_bytes(m, n, 2, kmax, bf16);
+    const size_t per = two > one ? two - one : one;
+    size_t cap = one >= kLargeChunkBytes ? 1 : 1 + (kLargeChunkBytes - one) / per;
+    cap = std::min(cap, (size_t)std::max(P->B_max, 1));
+    DeviceGuard dg(P->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    int live = 0;
+    for (size_t b0 = 0; b0 < count; b0 += cap) {
+        const size_t nb = std::min(cap, count - b0);
+        LargeCall call;
+        call.A = A;
+        call.m = m;
+        call.n = n;
+        call.lda = lda;
+        call.ys.assign(ys.begin() + b0, ys.begin() + b0 + nb);
+        call.outs.assign(outs.begin() + b0, outs.begin() + b0 + nb);
+        call.ks.resize(nb);
+        for (size_t b = 0; b < nb; ++b) call.ks[b] = call.outs[b].k;
+        call.max_iter = op->max_iter;
+        call.tol = op->tol;
+        call.bf16 = bf16;
+        call.live_host = &live;
+        const size_t need = large_ws_bytes(m, n, (int)nb, kmax, bf16);
+        cs_status st = ensure_lg(P, need);
+        if (st != CS_OK) return st;
+        cudaError_t e = large_solve(call, P->lg, P->lg_bytes, s);
+        if (e != cudaSuccess) return cuda_fail(e, "large OMP solve");
+        P->launches[CS_PHASE_PERSIST] += 1;
+    }
     return CS_OK;
 }
 
@@ -419,6 +493,20 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             return fail(CS_EINVAL, "tv_D needs tv_ldd >= tv_N >= 1 (tv_N=%d tv_ldd=%d)", cp->tv_N, cp->tv_ldd);
     }
     if (B == 0) return CS_OK;
+    if (needs_large(P, m, n, op->k, op->prec)) {
+        if (cp)
+            return fail(CS_ENOTSUP, "CLOMP runs with m <= %d, k <= %d (the plan's on-chip limit) and, with the bf16 "
+                                    "correlation, m <= 256 and n <= %d (m=%d n=%d k=%d)",
+                        kMaxRowChunks * 128, P->k_max, kCorrTcMaxN, m, n, op->k);
+        std::vector<const float*> ys(B);
+        std::vector<LargeOut> outs(B);
+        for (int b = 0; b < B; ++b) {
+            const size_t o = (size_t)b * op->k;
+            ys[b] = Y + (size_t)b * ldy;
+            outs[b] = LargeOut{support + o, coef + o, n_iter + b, res_norm + b, sig_status + b, op->k};
+        }
+        return solve_large(P, A, m, n, lda, ys, outs, op, s);
+    }
     DeviceGuard dg(P->device);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
 
@@ -759,39 +847,46 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
         if (x.m < 1 || x.n < 1 || x.lda < x.m || x.k < 1 || x.k > x.m || x.k > x.n)
             return fail(CS_EINVAL, "instance %d: bad sizes m=%d n=%d lda=%d k=%d", i, x.m, x.n, x.lda, x.k);
     }
-    // instances beyond the plan or the correlation's limits are not solved
+    // Instances beyond the plan are not solved; those beyond the on-chip
+    // kernels run on the large-instance path (plain OMP), or are not solved
+    // (CLOMP, or sizes beyond that path).
+    auto large = [&](const cs_instance& x) { return needs_large(P, x.m, x.n, x.k, op->prec); };
     auto refused = [&](const cs_instance& x) {
-        return x.m > P->m_max || x.n > P->n_max || x.k > P->k_max ||
-               (op->prec == CS_CORR_BF16 && !corr_tc_supported(x.m, x.n));
+        return x.m > P->m_max || x.n > P->n_max || x.k > P->k_user ||
+               (large(x) && (cp || P->no_large || !large_supported(x.m, x.n, x.k)));
     };
-    // groups in order of first appearance
-    std::vector<std::vector<int>> groups;
+    // groups in order of first appearance: on-chip groups share (A, m, n,
+    // lda, k); large groups share (A, m, n, lda), each instance with its k
+    std::vector<std::vector<int>> groups, lgroups;
     std::vector<int> refuse;
     {
-        std::map<std::string, int> at;
+        std::map<std::string, int> at, lat;
         for (int i = 0; i < count; ++i) {
             const cs_instance& x = inst[i];
             if (refused(x)) {
                 refuse.push_back(i);
                 continue;
             }
+            const bool lg = large(x);
             std::string key;
             key.append(reinterpret_cast<const char*>(&x.A), sizeof(x.A));
-            const int dims[] = {x.m, x.n, x.lda, x.k};
+            const int dims[] = {x.m, x.n, x.lda, lg ? 0 : x.k};
             key.append(reinterpret_cast<const char*>(dims), sizeof(dims));
-            auto it = at.find(key);
-            if (it == at.end()) {
-                at[key] = (int)groups.size();
-                groups.push_back({i});
+            auto& where = lg ? lat : at;
+            auto& list = lg ? lgroups : groups;
+            auto it = where.find(key);
+            if (it == where.end()) {
+                where[key] = (int)list.size();
+                list.push_back({i});
             } else {
-                groups[it->second].push_back(i);
+                list[it->second].push_back(i);
             }
         }
     }
     // staging: batch measurements, batch outputs and the pointer tables
     const size_t Bm = (size_t)P->B_max, K = (size_t)P->k_max;
     Carver cv;
-    const size_t oY = cv.take<float>((size_t)P->m_max * Bm);
+    const size_t oY = cv.take<float>((size_t)std::min(P->m_max, kMaxRowChunks * 128) * Bm);
     const size_t oS = cv.take<int32_t>(K * Bm);
     const size_t oC = cv.take<float>(K * Bm);
     const size_t oN = cv.take<int32_t>(Bm);
@@ -866,6 +961,18 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
             CS_TRY_LAUNCH(launch_varlen_scatter(Ot, x0.k, Bg, Sb, Cb, Nb, Rb, Tb, s), "varlen scatter");
         }
     }
+    for (const auto& g : lgroups) {
+        const cs_instance& x0 = inst[g[0]];
+        std::vector<const float*> ys(g.size());
+        std::vector<LargeOut> outs(g.size());
+        for (size_t j = 0; j < g.size(); ++j) {
+            const cs_instance& x = inst[g[j]];
+            ys[j] = x.y;
+            outs[j] = LargeOut{x.support, x.coef, x.n_iter, x.res_norm, x.sig_status, x.k};
+        }
+        cs_status st = solve_large(P, x0.A, x0.m, x0.n, x0.lda, ys, outs, op, s);
+        if (st != CS_OK) return st;
+    }
     return CS_OK;
 }
 
@@ -880,8 +987,8 @@ cs_status cs_plan_create(cs_plan** plan, int32_t m_max, int32_t n_max, int32_t b
     if (m_max < 1 || n_max < 1 || batch_max < 1 || k_max < 1)
         return fail(CS_EINVAL, "plan sizes must be >= 1 (m_max=%d n_max=%d batch_max=%d k_max=%d)",
                     m_max, n_max, batch_max, k_max);
-    if (k_max > kKmaxLimit) return fail(CS_ENOTSUP, "k_max=%d exceeds %d", k_max, kKmaxLimit);
-    if (m_max > kMaxRowChunks * 128) return fail(CS_ENOTSUP, "m_max=%d exceeds %d", m_max, kMaxRowChunks * 128);
+    if (k_max > kLargeMaxK) return fail(CS_ENOTSUP, "k_max=%d exceeds %d", k_max, kLargeMaxK);
+    if (m_max > kLargeMaxM) return fail(CS_ENOTSUP, "m_max=%d exceeds %d", m_max, kLargeMaxM);
     cs_plan* P = new cs_plan();
     cudaError_t e = cudaGetDevice(&P->device);
     if (e != cudaSuccess) {
@@ -891,13 +998,17 @@ cs_status cs_plan_create(cs_plan** plan, int32_t m_max, int32_t n_max, int32_t b
     P->m_max = m_max;
     P->n_max = n_max;
     P->B_max = batch_max;
+    P->k_user = k_max;
     P->k_max = k_max <= 32 ? 32 : 64;   // on-chip kernels are built for 32 or 64
-    P->mp_max = round_up(m_max, 4);
-    P->mh_max = round_up(m_max, 64);
+    // the on-chip kernels' workspace (m <= 1024); larger instances run on the
+    // large-instance path, whose workspace is allocated on first use
+    const int m_chip = std::min(m_max, kMaxRowChunks * 128);
+    P->mp_max = round_up(m_chip, 4);
+    P->mh_max = round_up(m_chip, 64);
     P->nw_max = ceil_div(n_max, 32);
     P->nch_max = ceil_div(n_max, kCorrFp32TileN);
     const bool gram_a = n_max <= kGramAMax;
-    const WsLayout L = ws_layout(m_max, n_max, batch_max, P->k_max, true, gram_a);
+    const WsLayout L = ws_layout(m_chip, n_max, batch_max, P->k_max, true, gram_a);
     e = cudaMalloc(&P->ws, L.total);
     if (e != cudaSuccess) {
         delete P;
@@ -935,6 +1046,7 @@ cs_status cs_plan_destroy(cs_plan* plan) {
     if (plan->tvT) cudaFree(plan->tvT);
     if (plan->io) cudaFree(plan->io);
     if (plan->vl) cudaFree(plan->vl);
+    if (plan->lg) cudaFree(plan->lg);
     delete plan;
     return CS_OK;
 }
@@ -1049,6 +1161,7 @@ cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int3
     if (lda < m || ldr < m || ldc < n) return fail(CS_EINVAL, "bad leading dimension");
     if (m > plan->m_max || n > plan->n_max || batch > plan->B_max)
         return fail(CS_EINVAL, "problem exceeds the plan");
+    if (m > kMaxRowChunks * 128) return fail(CS_ENOTSUP, "cs_correlate takes m <= %d (m=%d)", kMaxRowChunks * 128, m);
     if (prec != CS_CORR_FP32 && prec != CS_CORR_BF16) return fail(CS_EINVAL, "prec=%d", prec);
     if (prec == CS_CORR_BF16 && !corr_tc_supported(m, n))
         return fail(CS_ENOTSUP, "bf16 tensor-core correlation unavailable for m=%d n=%d", m, n);
@@ -1239,6 +1352,8 @@ extern "C" cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_
     P.n_max = n;
     P.B_max = std::max(batch, 1);
     P.k_max = params->k <= 32 ? 32 : 64;
+    P.k_user = params->k;
+    P.no_large = 1;
     P.mp_max = round_up(m, 4);
     P.mh_max = round_up(m, 64);
     P.nw_max = ceil_div(n, 32);

@@ -7,6 +7,8 @@
 #include <cuda_bf16.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "cs_omp.h"
 
 namespace cs {
@@ -20,6 +22,8 @@ constexpr int kTcGroup = 16;         // bf16 mode keeps the two largest |c| of e
 constexpr int kTcCandPerTile = 2 * kCorrTcTileN / kTcGroup;   // 32 candidates per 256-atom tile
 constexpr int kGramAMax = 4096;      // n up to which A^T A is precomputed per solve
 constexpr int kCorrTcMaxN = 4096;    // candidate merge holds <= 512 per signal
+constexpr int kLargeMaxM = 32768;    // large OMP solves: rows (residual staged in shared memory)
+constexpr int kLargeMaxK = 4096;     // large OMP solves: support size (float64 W = L^{-T} in HBM)
 
 // Candidate slots per signal, enough for either correlation kernel.
 __host__ __device__ inline int cand_slots(int n) {
@@ -110,6 +114,34 @@ struct VarlenRefuse {
     const float* y;
     int m, k;
 };
+
+// Large OMP solves (k_large.cu): signals sharing the caller's A (m x n,
+// leading dimension lda), each with its own measurement vector, sparsity and
+// outputs (device pointers; support and coef hold k entries).
+struct LargeOut {
+    int* support;
+    float* coef;
+    int* n_iter;
+    float* res_norm;
+    int* status;
+    int k;
+};
+struct LargeCall {
+    const float* A;
+    int m, n, lda;
+    std::vector<const float*> ys;
+    std::vector<LargeOut> outs;
+    std::vector<int> ks;
+    int max_iter;          // <= 0: k
+    double tol;
+    int bf16;              // 1: correlate with a bf16 copy of A (certified, re-scored in float32)
+    int* live_host;        // host int for the early end of the iteration loop (NULL: none)
+};
+bool large_supported(int m, int n, int k);
+size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16);
+// Runs a whole solve on `s` (synchronising `s` every 64 iterations to end
+// early once every signal has stopped, when live_host is set).
+cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaStream_t s);
 
 // ---- launchers (defined in the .cu files) --------------------------------
 // Outputs of refused instances: support -1, coef 0, n_iter 0, res_norm ||y||,

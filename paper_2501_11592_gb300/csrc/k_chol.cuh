@@ -44,16 +44,31 @@ __device__ __forceinline__ bool chol_warp(const int t, const int K, const float 
     double l[NP];
 #pragma unroll
     for (int e = 0; e < NP; ++e) l[e] = 0.0;
+    // eight rows' loads are issued before their multiply-adds (the loads
+    // are independent; the sums stay in ascending i)
 #pragma unroll
     for (int h = 0; h < NP; ++h) {
         const int i1 = min(t, 32 * (h + 1));
-        for (int i = 32 * h; i < i1; ++i) {
-            const double gi = (double)__shfl_sync(0xffffffffu, g[h], i & 31);
-            const double* row = Wr + (size_t)i * K;
+        for (int i0 = 32 * h; i0 < i1; i0 += 8) {
+            double wv[8][NP];
 #pragma unroll
-            for (int e = h; e < NP; ++e) {
-                const int p = lane + 32 * e;
-                if (i <= p && p < t) l[e] = fma(row[p], gi, l[e]);
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u;
+#pragma unroll
+                for (int e = h; e < NP; ++e) {
+                    const int p = lane + 32 * e;
+                    wv[u][e] = (i < i1 && i <= p && p < t) ? Wr[(size_t)i * K + p] : 0.0;
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int i = i0 + u;
+                const double gi = (double)__shfl_sync(0xffffffffu, g[h], i & 31);
+#pragma unroll
+                for (int e = h; e < NP; ++e) {
+                    const int p = lane + 32 * e;
+                    if (i < i1 && i <= p && p < t) l[e] = fma(wv[u][e], gi, l[e]);
+                }
             }
         }
     }
@@ -80,13 +95,26 @@ __device__ __forceinline__ bool chol_warp(const int t, const int K, const float 
 #pragma unroll
     for (int h = 0; h < NP; ++h) {
         const int p1 = min(t, 32 * (h + 1));
-        for (int p = 32 * h; p < p1; ++p) {
-            const double lp = __shfl_sync(0xffffffffu, l[h], p & 31);
-            const double* col = Wc + (size_t)p * K;
+        for (int p0 = 32 * h; p0 < p1; p0 += 8) {
+            double wv[8][NP];
 #pragma unroll
-            for (int e = 0; e <= h; ++e) {
-                const int i = lane + 32 * e;
-                if (i <= p) u[e] = fma(col[i], lp, u[e]);
+            for (int v = 0; v < 8; ++v) {
+                const int p = p0 + v;
+#pragma unroll
+                for (int e = 0; e <= h; ++e) {
+                    const int i = lane + 32 * e;
+                    wv[v][e] = (p < p1 && i <= p) ? Wc[(size_t)p * K + i] : 0.0;
+                }
+            }
+#pragma unroll
+            for (int v = 0; v < 8; ++v) {
+                const int p = p0 + v;
+                const double lp = __shfl_sync(0xffffffffu, l[h], p & 31);
+#pragma unroll
+                for (int e = 0; e <= h; ++e) {
+                    const int i = lane + 32 * e;
+                    if (p < p1 && i <= p) u[e] = fma(wv[v][e], lp, u[e]);
+                }
             }
         }
     }

@@ -1,0 +1,739 @@
+// Plain OMP for instances beyond the on-chip kernels: supports of up to
+// kLargeMaxK atoms and measurements of up to kLargeMaxM rows (the flattened
+// images of Results, "Evaluation with synthetic 2D data", solved as one long
+// 1-D signal, and the large members of uneven batches).  A batch of signals
+// sharing A runs as a sequence of grid-wide kernels per iteration of Eq. 2's
+// greedy loop, each signal with its own sparsity k:
+//
+//   correlation   c~ = A^T r streamed from HBM (bf16 copy of A, or the
+//                 caller's float32 A), r in shared memory, eight atoms per
+//                 warp, float32 accumulation; each warp folds the largest
+//                 unselected |c~| of every signal into a per-signal maximum;
+//   selection     every unselected atom with |c~_j| >= max - 2 delta (delta
+//                 bounds |c~_j - c_j| for every atom, see below) is re-scored
+//                 in float32 against the caller's A by a whole CTA, and the
+//                 largest |c_j| (lowest atom on ties) wins through one 64-bit
+//                 atomicMax of (value bits, ~atom) -- the float32 argmax over
+//                 all unselected atoms;
+//   Gram column   g_i = a_{S_i}^T a_j, ||a_j||^2 and a_j^T y in float32, each
+//                 dot product split into 2048-row segments summed afterwards
+//                 in segment order;
+//   least squares the float64 update of W = L^{-T} of k_chol.cuh -- l = W^T g,
+//                 pivot, z_t, u = W l, the new column of W, x += z_t w --
+//                 with both products split over the grid into partial sums
+//                 that are added in a fixed order;
+//   residual      r = y - A_S x (x as float32), partial sums over chunks of
+//                 128 support atoms added in chunk order, ||r||, the stopping
+//                 rule of Eq. 2.
+// Every reduction has a fixed order, so a solve is deterministic.
+//
+// Certificate.  With bf16 A (unit roundoff 2^-8) and float32 accumulation
+// of N1 = m/32 + 13 terms per lane plus the warp tree, and the float32
+// re-score summing N2 = m/1024 + 16 terms per thread plus the block tree,
+// for every atom |c~_j - c_j^{fp32}| <= delta =
+//   (2^-8 (1 + g1) + g1 + g2) max_j ||a_j|| ||r||,  g = N 2^-24 (1.01 margin),
+// so the atom whose re-scored |c| is largest has |c~| >= max|c~| - 2 delta.
+// The float32 path drops the 2^-8 term.
+#include <algorithm>
+#include <vector>
+
+#include "k_common.cuh"
+
+namespace cs {
+namespace {
+
+constexpr int LG_CORR_THREADS = 256;   // correlation CTA: 8 warps x 8 atoms
+constexpr int LG_ATOMS_PER_WARP = 8;
+constexpr int LG_SEG = 2048;           // rows per partial Gram dot product
+constexpr int LG_LC = 256;             // inner-index chunk of the float64 products
+constexpr int LG_RQ = 128;             // support atoms per residual partial sum
+constexpr int LG_RESCORE_CTAS = 64;    // CTAs per signal re-scoring candidates
+constexpr int LG_SMEM_R = 160 * 1024;  // shared memory for the residuals of one pass
+
+// Per-signal state (Bl signals, K = largest k rounded up to 32, mp = m
+// rounded up to 8, NSEG = ceil(m / LG_SEG), LCH = ceil(K / LG_LC),
+// RCH = ceil(K / LG_RQ)).
+struct LgState {
+    int m, n, lda, mp, K, nseg, lch, rch, Bl, nb, bf16;
+    double tol;
+    const float* A;                 // caller's A (float32, leading dimension lda)
+    const __nv_bfloat16* A16;       // [n][mp] bf16 copy (bf16 mode)
+    const float* colmax;            // max_j ||a_j||
+    const float* const* ys;         // [Bl] caller's measurement vectors
+    const LargeOut* outs;           // [Bl] caller's outputs
+    const int* kv;                  // [Bl] sparsity
+    const int* itv;                 // [Bl] iteration limit min(k, max_iter)
+    float* y;                       // [Bl][mp]
+    float* r;                       // [Bl][mp]
+    float* c;                       // [Bl][n] |c~|
+    uint32_t* mask;                 // [Bl][nw]
+    int* cand;                      // [Bl][n] candidate atoms
+    int* ncand;                     // [Bl]
+    unsigned* cmax;                 // [Bl] bits of the largest unselected |c~|
+    unsigned long long* best;       // [Bl] (|c| bits << 32) | ~atom of the re-scored winner
+    int* sup;                       // [Bl][K]
+    float* gpart;                   // [Bl][nseg][K + 2]
+    float* gsum;                    // [Bl][K + 2]
+    double* W;                      // [Bl][2][K][K] (rows, then columns)
+    double* z;                      // [Bl][K]
+    double* x;                      // [Bl][K]
+    float* xf;                      // [Bl][K]
+    double* lpart;                  // [Bl][lch][K]
+    double* l;                      // [Bl][K]
+    double* upart;                  // [Bl][lch][K]
+    double* scal;                   // [Bl][2] 1/L_tt, z_t
+    float* rpart;                   // [Bl][rch][mp]
+    float* rnorm;                   // [Bl]
+    int* nit;                       // [Bl]
+    int* st;                        // [Bl] status (-1 running)
+    int* live;                      // [1] signals still running after the last check
+};
+
+__device__ __forceinline__ float lg_delta(const LgState& S, int b) {
+    const float g1 = ((float)S.m / 32.f + 13.f) * 0x1p-24f;
+    const float g2 = ((float)S.m / 1024.f + 16.f) * 0x1p-24f;
+    const float ua = S.bf16 ? 0x1p-8f * (1.f + g1) : 0.f;
+    return (ua + g1 + g2) * 1.01f * (*S.colmax) * S.rnorm[b] * 1.01f;
+}
+
+// Block-wide sum (blockDim.x a multiple of 32, <= 1024), fixed order: each
+// warp's butterfly, then warp 0 over the warps' sums in warp order.
+template <typename T>
+__device__ T block_sum(T v, T* sh) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    __syncthreads();
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        T w = lane < nw ? sh[lane] : T(0);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (lane == 0) sh[32] = w;
+    }
+    __syncthreads();
+    const T out = sh[32];
+    __syncthreads();
+    return out;
+}
+
+// ------------------------------------------------------------- set-up --
+// bf16 copy of A (rows padded to mp with zeros) and the largest column norm.
+__global__ void k_lg_prep(const float* __restrict__ A, int lda, int m, int n, int mp,
+                          __nv_bfloat16* __restrict__ A16, float* colmax) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const float* a = A + (size_t)j * lda;
+    float ss = 0.f;
+    for (int i = lane; i < mp; i += 32) {
+        const float v = i < m ? a[i] : 0.f;
+        ss = fmaf(v, v, ss);
+        if (A16) A16[(size_t)j * mp + i] = __float2bfloat16_rn(v);
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned*>(colmax), __float_as_uint(sqrtf(ss)));
+}
+
+// Per signal (one CTA): y, r = y, ||y||, the non-finite and tolerance tests.
+__global__ void __launch_bounds__(1024) k_lg_setup(LgState S) {
+    __shared__ float sh[33];
+    const int b = blockIdx.x;
+    const float* y = S.ys[b];
+    float ss = 0.f;
+    int finite = 1;
+    for (int i = threadIdx.x; i < S.mp; i += blockDim.x) {
+        const float v = i < S.m ? y[i] : 0.f;
+        finite &= isfinite(v) ? 1 : 0;
+        S.y[(size_t)b * S.mp + i] = v;
+        S.r[(size_t)b * S.mp + i] = v;
+        ss = fmaf(v, v, ss);
+    }
+    const int nw = (S.n + 31) / 32;
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) S.mask[(size_t)b * nw + w] = 0u;
+    finite = __syncthreads_and(finite);
+    ss = block_sum(ss, sh);
+    if (threadIdx.x == 0) {
+        const float rho = sqrtf(ss);
+        S.rnorm[b] = finite ? rho : NAN;
+        S.nit[b] = 0;
+        S.ncand[b] = 0;
+        S.cmax[b] = 0u;
+        S.best[b] = 0ull;
+        if (!finite) S.st[b] = CS_SIG_NONFINITE;
+        else if ((double)rho <= S.tol) S.st[b] = CS_SIG_REACHED_TOL;
+        else S.st[b] = -1;
+    }
+}
+
+// ------------------------------------------------------- correlation --
+// |c~_j| for the NB signals of pass blockIdx.y and the atoms of this CTA,
+// and the largest unselected one per signal.  bf16 A: lane l covers rows
+// i0 + 8l .. i0 + 8l + 7 of every 256-row chunk (one 16-byte load per atom);
+// float32 A: rows i0 + l + 32e (eight coalesced loads per atom).
+template <bool BF16, int NB>
+__global__ void __launch_bounds__(LG_CORR_THREADS) k_lg_corr(LgState S) {
+    extern __shared__ __align__(16) float rs[];   // [NB][mp]
+    const int s0 = blockIdx.y * NB;
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < NB; ++s) any |= (s0 + s < S.Bl) && S.st[s0 + s] < 0;
+    if (!any) return;
+    for (int e = threadIdx.x; e < NB * S.mp; e += blockDim.x) {
+        const int s = e / S.mp, i = e - s * S.mp;
+        rs[e] = (s0 + s < S.Bl) ? S.r[(size_t)(s0 + s) * S.mp + i] : 0.f;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j0 = (blockIdx.x * (LG_CORR_THREADS / 32) + warp) * LG_ATOMS_PER_WARP;
+    if (j0 >= S.n) return;
+    float acc[LG_ATOMS_PER_WARP][NB];
+#pragma unroll
+    for (int a = 0; a < LG_ATOMS_PER_WARP; ++a)
+#pragma unroll
+        for (int s = 0; s < NB; ++s) acc[a][s] = 0.f;
+    for (int i0 = 0; i0 < S.mp; i0 += 256) {
+        if (BF16) {
+            const int i = i0 + 8 * lane;
+            if (i < S.mp) {
+                uint4 av[LG_ATOMS_PER_WARP];
+#pragma unroll
+                for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
+                    const int j = min(j0 + a, S.n - 1);
+                    av[a] = *reinterpret_cast<const uint4*>(S.A16 + (size_t)j * S.mp + i);
+                }
+#pragma unroll
+                for (int s = 0; s < NB; ++s) {
+                    const float4 r0 = *reinterpret_cast<const float4*>(rs + s * S.mp + i);
+                    const float4 r1 = *reinterpret_cast<const float4*>(rs + s * S.mp + i + 4);
+                    const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+                    for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
+                        const unsigned w[4] = {av[a].x, av[a].y, av[a].z, av[a].w};
+#pragma unroll
+                        for (int q = 0; q < 4; ++q) {
+                            acc[a][s] = fmaf(__uint_as_float(w[q] << 16), rv[2 * q], acc[a][s]);
+                            acc[a][s] = fmaf(__uint_as_float(w[q] & 0xffff0000u), rv[2 * q + 1], acc[a][s]);
+                        }
+                    }
+                }
+            }
+        } else {
+            float av[LG_ATOMS_PER_WARP][8];
+#pragma unroll
+            for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
+                const float* col = S.A + (size_t)min(j0 + a, S.n - 1) * S.lda;
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int i = i0 + lane + 32 * e;
+                    av[a][e] = i < S.m ? col[i] : 0.f;
+                }
+            }
+#pragma unroll
+            for (int s = 0; s < NB; ++s)
+#pragma unroll
+                for (int e = 0; e < 8; ++e) {
+                    const int i = i0 + lane + 32 * e;
+                    const float rv = i < S.mp ? rs[s * S.mp + i] : 0.f;
+#pragma unroll
+                    for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) acc[a][s] = fmaf(av[a][e], rv, acc[a][s]);
+                }
+        }
+    }
+    const int nw = (S.n + 31) / 32;
+#pragma unroll
+    for (int s = 0; s < NB; ++s) {
+        const int b = s0 + s;
+        float mx = 0.f;
+#pragma unroll
+        for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
+            const float v = fabsf(warp_sum(acc[a][s]));
+            const int j = j0 + a;
+            if (b < S.Bl && j < S.n) {
+                if (lane == 0) S.c[(size_t)b * S.n + j] = v;
+                const bool sel = (S.mask[(size_t)b * nw + (j >> 5)] >> (j & 31)) & 1u;
+                if (!sel) mx = fmaxf(mx, v);
+            }
+        }
+        if (lane == 0 && b < S.Bl && S.st[b] < 0) atomicMax(S.cmax + b, __float_as_uint(mx));
+    }
+}
+
+// ---------------------------------------------------------- selection --
+// Candidates: unselected atoms with |c~| >= max - 2 delta.
+__global__ void __launch_bounds__(256) k_lg_scan(LgState S) {
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= S.n) return;
+    const int nw = (S.n + 31) / 32;
+    if ((S.mask[(size_t)b * nw + (j >> 5)] >> (j & 31)) & 1u) return;
+    const float theta = __uint_as_float(S.cmax[b]) - 2.f * lg_delta(S, b);
+    if (S.c[(size_t)b * S.n + j] >= theta) {
+        const int q = atomicAdd(S.ncand + b, 1);
+        S.cand[(size_t)b * S.n + q] = j;
+    }
+}
+
+// float32 re-score of the candidates (one CTA per candidate) and the argmax.
+__global__ void __launch_bounds__(1024) k_lg_rescore(LgState S) {
+    __shared__ float sh[33];
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const int nc = S.ncand[b];
+    const float* r = S.r + (size_t)b * S.mp;
+    for (int q = blockIdx.x; q < nc; q += gridDim.x) {
+        const int j = S.cand[(size_t)b * S.n + q];
+        const float* a = S.A + (size_t)j * S.lda;
+        float acc = 0.f;
+        for (int i = threadIdx.x; i < S.m; i += blockDim.x) acc = fmaf(a[i], r[i], acc);
+        const float v = fabsf(block_sum(acc, sh));
+        if (threadIdx.x == 0) {
+            const unsigned long long key =
+                ((unsigned long long)__float_as_uint(v) << 32) | (unsigned long long)(0xffffffffu - (unsigned)j);
+            atomicMax(S.best + b, key);
+        }
+    }
+}
+
+// ------------------------------------------------------- Gram column --
+// Append the winner (CTA 0) and the partial dot products of a_j with the
+// support atoms (i < t), itself (i = t) and y (i = t + 1), one warp per
+// (entry, 2048-row segment).
+__global__ void __launch_bounds__(256) k_lg_gram(LgState S, int t) {
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const unsigned long long key = S.best[b];
+    const int lane = threadIdx.x & 31;
+    const int nw = (S.n + 31) / 32;
+    if (key == 0ull) {                       // no unselected atom left
+        if (blockIdx.x == 0 && threadIdx.x == 0) S.st[b] = CS_SIG_MAX_ITER;
+        return;
+    }
+    const int j = (int)(0xffffffffu - (unsigned)(key & 0xffffffffull));
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        S.sup[(size_t)b * S.K + t] = j;
+        S.mask[(size_t)b * nw + (j >> 5)] |= 1u << (j & 31);
+    }
+    const int items = (t + 2) * S.nseg;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (item >= items) return;
+    const int i = item % (t + 2), seg = item / (t + 2);
+    const float* aj = S.A + (size_t)j * S.lda;
+    const float* other = (i < t) ? S.A + (size_t)S.sup[(size_t)b * S.K + i] * S.lda
+                                 : (i == t ? aj : S.y + (size_t)b * S.mp);
+    const int r0 = seg * LG_SEG, r1 = min(S.m, r0 + LG_SEG);
+    float acc = 0.f;
+    for (int q = r0 + lane; q < r1; q += 32) acc = fmaf(other[q], aj[q], acc);
+    acc = warp_sum(acc);
+    if (lane == 0) S.gpart[((size_t)b * S.nseg + seg) * (S.K + 2) + i] = acc;
+}
+
+__global__ void __launch_bounds__(256) k_lg_gsum(LgState S, int t) {
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= t + 2) return;
+    float v = 0.f;
+    for (int seg = 0; seg < S.nseg; ++seg) v += S.gpart[((size_t)b * S.nseg + seg) * (S.K + 2) + i];
+    S.gsum[(size_t)b * (S.K + 2) + i] = v;
+}
+
+// -------------------------------------------------- float64 Cholesky --
+// Partial sums of l_p = sum_{i <= p} W_ip g_i over 256-entry chunks of i:
+// one warp per (32 entries p, chunk), lanes over p.
+__global__ void __launch_bounds__(256) k_lg_lpart(LgState S, int t) {
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int pblocks = (t + 31) / 32;
+    if (item >= pblocks * S.lch) return;
+    const int pb = item % pblocks, ic = item / pblocks;
+    const int p = pb * 32 + lane;
+    const int i0 = ic * LG_LC, i1 = min(t, i0 + LG_LC);
+    const double* Wr = S.W + (size_t)b * 2 * S.K * S.K;
+    const float* g = S.gsum + (size_t)b * (S.K + 2);
+    double acc = 0.0;
+    for (int ib = i0; ib < i1; ib += 8) {
+        double wv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = ib + u;
+            wv[u] = (i < i1 && i <= p && p < t) ? Wr[(size_t)i * S.K + p] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int i = ib + u;
+            if (i < i1 && i <= p && p < t) acc = fma(wv[u], (double)g[i], acc);
+        }
+    }
+    if (p < t) S.lpart[((size_t)b * S.lch + ic) * S.K + p] = acc;
+}
+
+// l from its partial sums (chunk order), the pivot, L_tt and z_t (one CTA).
+__global__ void __launch_bounds__(1024) k_lg_pivot(LgState S, int t) {
+    __shared__ double sh[33];
+    const int b = blockIdx.x;
+    if (S.st[b] >= 0) return;
+    const int ich = (t + LG_LC - 1) / LG_LC;
+    double ssq = 0.0, lz = 0.0;
+    for (int p = threadIdx.x; p < t; p += blockDim.x) {
+        double lp = 0.0;
+        for (int ic = 0; ic < ich; ++ic) lp += S.lpart[((size_t)b * S.lch + ic) * S.K + p];
+        S.l[(size_t)b * S.K + p] = lp;
+        ssq = fma(lp, lp, ssq);
+        lz = fma(lp, S.z[(size_t)b * S.K + p], lz);
+    }
+    ssq = block_sum(ssq, sh);
+    lz = block_sum(lz, sh);
+    if (threadIdx.x == 0) {
+        const double d = (double)S.gsum[(size_t)b * (S.K + 2) + t];
+        const double bt = (double)S.gsum[(size_t)b * (S.K + 2) + t + 1];
+        const double piv = d - ssq;
+        if (!(piv > 0x1p-20 * d)) {
+            S.st[b] = CS_SIG_DEPENDENT;
+        } else {
+            const double ltt = sqrt(piv);
+            const double zt = (bt - lz) / ltt;
+            S.scal[2 * b] = 1.0 / ltt;
+            S.scal[2 * b + 1] = zt;
+            S.z[(size_t)b * S.K + t] = zt;
+        }
+    }
+}
+
+// Partial sums of u_i = sum_{p >= i} W_ip l_p over 256-entry chunks of p:
+// one warp per (32 entries i, chunk), lanes over i.
+__global__ void __launch_bounds__(256) k_lg_upart(LgState S, int t) {
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const int lane = threadIdx.x & 31;
+    const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const int iblocks = (t + 31) / 32;
+    if (item >= iblocks * S.lch) return;
+    const int ib = item % iblocks, pc = item / iblocks;
+    const int i = ib * 32 + lane;
+    const int p0 = pc * LG_LC, p1 = min(t, p0 + LG_LC);
+    const double* Wc = S.W + (size_t)b * 2 * S.K * S.K + (size_t)S.K * S.K;
+    const double* l = S.l + (size_t)b * S.K;
+    double acc = 0.0;
+    for (int pb = p0; pb < p1; pb += 8) {
+        double wv[8];
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int p = pb + v;
+            wv[v] = (p < p1 && i <= p) ? Wc[(size_t)p * S.K + i] : 0.0;
+        }
+#pragma unroll
+        for (int v = 0; v < 8; ++v) {
+            const int p = pb + v;
+            if (p < p1 && i <= p) acc = fma(wv[v], l[p], acc);
+        }
+    }
+    if (i < t) S.upart[((size_t)b * S.lch + pc) * S.K + i] = acc;
+}
+
+// The new column of W and x += z_t w (one thread per entry i <= t).
+__global__ void __launch_bounds__(256) k_lg_update(LgState S, int t) {
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > t) return;
+    double* Wr = S.W + (size_t)b * 2 * S.K * S.K;
+    double* Wc = Wr + (size_t)S.K * S.K;
+    const double rinv = S.scal[2 * b], zt = S.scal[2 * b + 1];
+    double xi;
+    if (i < t) {
+        const int pch = (t + LG_LC - 1) / LG_LC;
+        double u = 0.0;
+        for (int pc = 0; pc < pch; ++pc) {
+            // entry i has terms only in the chunks at or after its own
+            if ((pc + 1) * LG_LC > i) u += S.upart[((size_t)b * S.lch + pc) * S.K + i];
+        }
+        const double w = -u * rinv;
+        Wr[(size_t)i * S.K + t] = w;
+        Wc[(size_t)t * S.K + i] = w;
+        xi = fma(zt, w, S.x[(size_t)b * S.K + i]);
+    } else {
+        Wr[(size_t)t * S.K + t] = rinv;
+        Wc[(size_t)t * S.K + t] = rinv;
+        xi = zt * rinv;
+        S.nit[b] = t + 1;
+    }
+    S.x[(size_t)b * S.K + i] = xi;
+    S.xf[(size_t)b * S.K + i] = (float)xi;
+}
+
+// ----------------------------------------------------------- residual --
+// Partial sums sum_{q in chunk} a_{S_q}[i] x_q over chunks of 128 atoms
+// (one thread per row i).
+__global__ void __launch_bounds__(256) k_lg_rpart(LgState S, int t1) {
+    __shared__ int sj[LG_RQ];
+    __shared__ float sx[LG_RQ];
+    const int b = blockIdx.z;
+    if (S.st[b] >= 0) return;
+    const int qc = blockIdx.y;
+    const int q0 = qc * LG_RQ, q1 = min(t1, q0 + LG_RQ);
+    if (q0 >= q1) return;
+    for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
+        sj[q - q0] = S.sup[(size_t)b * S.K + q];
+        sx[q - q0] = S.xf[(size_t)b * S.K + q];
+    }
+    __syncthreads();
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.m) return;
+    float acc = 0.f;
+    int q = 0;
+    const int nq = q1 - q0;
+    for (; q + 4 <= nq; q += 4) {
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = S.A[(size_t)sj[q + u] * S.lda + i];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = fmaf(v[u], sx[q + u], acc);
+    }
+    for (; q < nq; ++q) acc = fmaf(S.A[(size_t)sj[q] * S.lda + i], sx[q], acc);
+    S.rpart[((size_t)b * S.rch + qc) * S.mp + i] = acc;
+}
+
+// r = y - (partial sums in chunk order), ||r||, the stopping rule, and the
+// reset of the selection state for the next iteration (one CTA per signal).
+__global__ void __launch_bounds__(1024) k_lg_resid(LgState S) {
+    __shared__ float sh[33];
+    const int b = blockIdx.x;
+    if (S.st[b] >= 0) return;
+    const int t1 = S.nit[b];
+    const int qch = (t1 + LG_RQ - 1) / LG_RQ;
+    float ss = 0.f;
+    for (int i = threadIdx.x; i < S.m; i += blockDim.x) {
+        float acc = 0.f;
+        for (int qc = 0; qc < qch; ++qc) acc += S.rpart[((size_t)b * S.rch + qc) * S.mp + i];
+        const float ri = S.y[(size_t)b * S.mp + i] - acc;
+        S.r[(size_t)b * S.mp + i] = ri;
+        ss = fmaf(ri, ri, ss);
+    }
+    ss = block_sum(ss, sh);
+    if (threadIdx.x == 0) {
+        const float rho = sqrtf(ss);
+        S.rnorm[b] = rho;
+        S.ncand[b] = 0;
+        S.cmax[b] = 0u;
+        S.best[b] = 0ull;
+        if ((double)rho <= S.tol) S.st[b] = CS_SIG_REACHED_TOL;
+        else if (t1 >= S.kv[b]) S.st[b] = CS_SIG_REACHED_K;
+        else if (t1 >= S.itv[b]) S.st[b] = CS_SIG_MAX_ITER;
+    }
+}
+
+// Signals still running (for the host's early end of the iteration loop).
+__global__ void k_lg_count(LgState S) {
+    int c = 0;
+    for (int b = threadIdx.x; b < S.Bl; b += blockDim.x) c += S.st[b] < 0 ? 1 : 0;
+    c = __reduce_add_sync(0xffffffffu, c);
+    if (threadIdx.x == 0) *S.live = c;
+}
+
+// Outputs: support and coefficients (-1 / 0 past n_iter), n_iter, ||r||, status.
+__global__ void k_lg_out(LgState S) {
+    const int b = blockIdx.x;
+    const LargeOut o = S.outs[b];
+    const int t = S.nit[b];
+    for (int q = threadIdx.x; q < o.k; q += blockDim.x) {
+        o.support[q] = q < t ? S.sup[(size_t)b * S.K + q] : -1;
+        o.coef[q] = q < t ? S.xf[(size_t)b * S.K + q] : 0.f;
+    }
+    if (threadIdx.x == 0) {
+        *o.n_iter = t;
+        *o.res_norm = S.rnorm[b];
+        *o.status = S.st[b] < 0 ? CS_SIG_MAX_ITER : S.st[b];
+    }
+}
+
+struct LgLayout {
+    size_t A16, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
+        xf, lpart, l, upart, scal, rpart, rnorm, nit, st, live, total;
+};
+
+LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16) {
+    const size_t B = (size_t)Bl, K = (size_t)round_up(kmax, 32), mp = (size_t)round_up(m, 8);
+    const size_t nseg = (size_t)ceil_div(m, LG_SEG), lch = (size_t)ceil_div((int)K, LG_LC),
+                 rch = (size_t)ceil_div((int)K, LG_RQ), nw = (size_t)ceil_div(n, 32);
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        off = (off + 255) & ~(size_t)255;
+        const size_t o = off;
+        off += bytes;
+        return o;
+    };
+    LgLayout L{};
+    L.A16 = bf16 ? take(sizeof(__nv_bfloat16) * (size_t)n * mp) : 0;
+    L.colmax = take(sizeof(float));
+    L.ys = take(sizeof(const float*) * B);
+    L.outs = take(sizeof(LargeOut) * B);
+    L.kv = take(sizeof(int) * B);
+    L.itv = take(sizeof(int) * B);
+    L.y = take(sizeof(float) * B * mp);
+    L.r = take(sizeof(float) * B * mp);
+    L.c = take(sizeof(float) * B * n);
+    L.mask = take(sizeof(uint32_t) * B * nw);
+    L.cand = take(sizeof(int) * B * n);
+    L.ncand = take(sizeof(int) * B);
+    L.cmax = take(sizeof(unsigned) * B);
+    L.best = take(sizeof(unsigned long long) * B);
+    L.sup = take(sizeof(int) * B * K);
+    L.gpart = take(sizeof(float) * B * nseg * (K + 2));
+    L.gsum = take(sizeof(float) * B * (K + 2));
+    L.W = take(sizeof(double) * B * 2 * K * K);
+    L.z = take(sizeof(double) * B * K);
+    L.x = take(sizeof(double) * B * K);
+    L.xf = take(sizeof(float) * B * K);
+    L.lpart = take(sizeof(double) * B * lch * K);
+    L.l = take(sizeof(double) * B * K);
+    L.upart = take(sizeof(double) * B * lch * K);
+    L.scal = take(sizeof(double) * B * 2);
+    L.rpart = take(sizeof(float) * B * rch * mp);
+    L.rnorm = take(sizeof(float) * B);
+    L.nit = take(sizeof(int) * B);
+    L.st = take(sizeof(int) * B);
+    L.live = take(sizeof(int));
+    L.total = off;
+    return L;
+}
+
+template <bool BF16, int NB>
+cudaError_t launch_corr_nb(const LgState& S, cudaStream_t s) {
+    const size_t smem = sizeof(float) * (size_t)NB * S.mp;
+    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr<BF16, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   LG_SMEM_R);
+    if (attr != cudaSuccess) return attr;
+    const dim3 grid(ceil_div(S.n, (LG_CORR_THREADS / 32) * LG_ATOMS_PER_WARP), ceil_div(S.Bl, NB));
+    k_lg_corr<BF16, NB><<<grid, LG_CORR_THREADS, smem, s>>>(S);
+    return cudaGetLastError();
+}
+
+template <bool BF16>
+cudaError_t launch_corr(const LgState& S, cudaStream_t s) {
+    switch (S.nb) {
+        case 1: return launch_corr_nb<BF16, 1>(S, s);
+        case 2: return launch_corr_nb<BF16, 2>(S, s);
+        default: return launch_corr_nb<BF16, 4>(S, s);
+    }
+}
+
+}  // namespace
+
+bool large_supported(int m, int n, int k) {
+    return m >= 1 && m <= kLargeMaxM && n >= 1 && k >= 1 && k <= kLargeMaxK;
+}
+
+size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16) { return lg_layout(m, n, Bl, kmax, bf16).total; }
+
+cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaStream_t s) {
+    const int Bl = (int)call.ys.size();
+    if (Bl == 0) return cudaSuccess;
+    const int kmax = *std::max_element(call.ks.begin(), call.ks.end());
+    const LgLayout L = lg_layout(call.m, call.n, Bl, kmax, call.bf16);
+    if (L.total > ws_bytes) return cudaErrorInvalidValue;
+    char* w = static_cast<char*>(ws);
+    LgState S{};
+    S.m = call.m;
+    S.n = call.n;
+    S.lda = call.lda;
+    S.mp = round_up(call.m, 8);
+    S.K = round_up(kmax, 32);
+    S.nseg = ceil_div(call.m, LG_SEG);
+    S.lch = ceil_div(S.K, LG_LC);
+    S.rch = ceil_div(S.K, LG_RQ);
+    S.Bl = Bl;
+    S.bf16 = call.bf16;
+    S.tol = call.tol;
+    S.nb = std::max(1, std::min(4, (int)(LG_SMEM_R / (sizeof(float) * (size_t)S.mp))));
+    if (S.nb == 3) S.nb = 2;
+    while (S.nb > 1 && S.nb / 2 >= Bl) S.nb /= 2;   // no empty signal slots
+    S.A = call.A;
+    S.A16 = call.bf16 ? reinterpret_cast<__nv_bfloat16*>(w + L.A16) : nullptr;
+    S.colmax = reinterpret_cast<float*>(w + L.colmax);
+    S.ys = reinterpret_cast<const float* const*>(w + L.ys);
+    S.outs = reinterpret_cast<const LargeOut*>(w + L.outs);
+    S.kv = reinterpret_cast<const int*>(w + L.kv);
+    S.itv = reinterpret_cast<const int*>(w + L.itv);
+    S.y = reinterpret_cast<float*>(w + L.y);
+    S.r = reinterpret_cast<float*>(w + L.r);
+    S.c = reinterpret_cast<float*>(w + L.c);
+    S.mask = reinterpret_cast<uint32_t*>(w + L.mask);
+    S.cand = reinterpret_cast<int*>(w + L.cand);
+    S.ncand = reinterpret_cast<int*>(w + L.ncand);
+    S.cmax = reinterpret_cast<unsigned*>(w + L.cmax);
+    S.best = reinterpret_cast<unsigned long long*>(w + L.best);
+    S.sup = reinterpret_cast<int*>(w + L.sup);
+    S.gpart = reinterpret_cast<float*>(w + L.gpart);
+    S.gsum = reinterpret_cast<float*>(w + L.gsum);
+    S.W = reinterpret_cast<double*>(w + L.W);
+    S.z = reinterpret_cast<double*>(w + L.z);
+    S.x = reinterpret_cast<double*>(w + L.x);
+    S.xf = reinterpret_cast<float*>(w + L.xf);
+    S.lpart = reinterpret_cast<double*>(w + L.lpart);
+    S.l = reinterpret_cast<double*>(w + L.l);
+    S.upart = reinterpret_cast<double*>(w + L.upart);
+    S.scal = reinterpret_cast<double*>(w + L.scal);
+    S.rpart = reinterpret_cast<float*>(w + L.rpart);
+    S.rnorm = reinterpret_cast<float*>(w + L.rnorm);
+    S.nit = reinterpret_cast<int*>(w + L.nit);
+    S.st = reinterpret_cast<int*>(w + L.st);
+    S.live = reinterpret_cast<int*>(w + L.live);
+
+    // the per-signal tables (pageable host vectors: staged before the calls return)
+    std::vector<int> itv(Bl);
+    int iters = 0;
+    for (int b = 0; b < Bl; ++b) {
+        itv[b] = call.max_iter > 0 ? std::min(call.ks[b], call.max_iter) : call.ks[b];
+        iters = std::max(iters, itv[b]);
+    }
+    cudaError_t e;
+#define LG_TRY(x)                          \
+    do {                                   \
+        e = (x);                           \
+        if (e != cudaSuccess) return e;    \
+    } while (0)
+    LG_TRY(cudaMemcpyAsync(w + L.ys, call.ys.data(), sizeof(const float*) * Bl, cudaMemcpyHostToDevice, s));
+    LG_TRY(cudaMemcpyAsync(w + L.outs, call.outs.data(), sizeof(LargeOut) * Bl, cudaMemcpyHostToDevice, s));
+    LG_TRY(cudaMemcpyAsync(w + L.kv, call.ks.data(), sizeof(int) * Bl, cudaMemcpyHostToDevice, s));
+    LG_TRY(cudaMemcpyAsync(w + L.itv, itv.data(), sizeof(int) * Bl, cudaMemcpyHostToDevice, s));
+    LG_TRY(cudaMemsetAsync(w + L.colmax, 0, sizeof(float), s));
+    k_lg_prep<<<ceil_div(S.n, 8), 256, 0, s>>>(S.A, S.lda, S.m, S.n, S.mp,
+                                               const_cast<__nv_bfloat16*>(S.A16), const_cast<float*>(S.colmax));
+    LG_TRY(cudaGetLastError());
+    k_lg_setup<<<Bl, 1024, 0, s>>>(S);
+    LG_TRY(cudaGetLastError());
+    int* live_h = call.live_host;
+    for (int it = 0; it < iters; ++it) {
+        const int t = it;
+        LG_TRY(S.bf16 ? launch_corr<true>(S, s) : launch_corr<false>(S, s));
+        k_lg_scan<<<dim3(ceil_div(S.n, 256), Bl), 256, 0, s>>>(S);
+        k_lg_rescore<<<dim3(LG_RESCORE_CTAS, Bl), 1024, 0, s>>>(S);
+        k_lg_gram<<<dim3(ceil_div((t + 2) * S.nseg, 8), Bl), 256, 0, s>>>(S, t);
+        k_lg_gsum<<<dim3(ceil_div(t + 2, 256), Bl), 256, 0, s>>>(S, t);
+        if (t > 0) k_lg_lpart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
+        k_lg_pivot<<<Bl, 1024, 0, s>>>(S, t);
+        if (t > 0) k_lg_upart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
+        k_lg_update<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t);
+        k_lg_rpart<<<dim3(ceil_div(S.m, 256), ceil_div(t + 1, LG_RQ), Bl), 256, 0, s>>>(S, t + 1);
+        k_lg_resid<<<Bl, 1024, 0, s>>>(S);
+        LG_TRY(cudaGetLastError());
+        // every 64 iterations: stop once no signal is running
+        if (live_h && (it % 64) == 63 && it + 1 < iters) {
+            k_lg_count<<<1, 32, 0, s>>>(S);
+            LG_TRY(cudaMemcpyAsync(live_h, S.live, sizeof(int), cudaMemcpyDeviceToHost, s));
+            LG_TRY(cudaStreamSynchronize(s));
+            if (*live_h == 0) break;
+        }
+    }
+    k_lg_out<<<Bl, 256, 0, s>>>(S);
+    LG_TRY(cudaGetLastError());
+#undef LG_TRY
+    return cudaSuccess;
+}
+
+}  // namespace cs

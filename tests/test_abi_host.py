@@ -36,8 +36,8 @@ def test_plan_argument_checks_without_gpu(lib):
     h = ctypes.c_void_p()
     assert lib.cs_plan_create(ctypes.byref(h), 0, 10, 10, 4) == -1
     assert b"sizes" in lib.cs_last_error()
-    assert lib.cs_plan_create(ctypes.byref(h), 64, 256, 10, 65) == -5
-    assert lib.cs_plan_create(ctypes.byref(h), 2048, 256, 10, 8) == -5
+    assert lib.cs_plan_create(ctypes.byref(h), 64, 256, 10, 4097) == -5
+    assert lib.cs_plan_create(ctypes.byref(h), 32769, 256, 10, 8) == -5
     assert lib.cs_plan_create(None, 64, 256, 10, 8) == -1
     assert lib.cs_plan_destroy(None) == 0
 

@@ -1,0 +1,114 @@
+"""The large-instance OMP path (supports beyond the on-chip 64 atoms, more
+than 1024 rows, the bf16 correlation beyond the tensor-core kernel's sizes)
+against the FP64 oracle, through the C ABI (via the ctypes binding)."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads
+from parity import compare, f32_problem, to_numpy
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    import torch as t
+    return t
+
+
+def run(cs, torch, A32, Y32, k, prec, plan=None, **kw):
+    A = torch.from_numpy(np.asfortranarray(A32)).cuda()
+    Y = torch.from_numpy(np.asfortranarray(Y32)).cuda()
+    m, n = A32.shape
+    plan = plan or cs.Plan(m, n, Y32.shape[1], k)
+    r = cs.omp_solve_batched(A, Y, k, prec=prec, plan=plan, **kw)
+    torch.cuda.synchronize()
+    g = to_numpy(r)
+    g["launches"] = {ph: v[0] for ph, v in plan.profile(reset=True).items()}
+    return g
+
+
+def large_signal(n, m, k, seed):
+    """A noiseless k-sparse signal with N(0,1) values in a Gaussian dictionary
+    with unit columns (the large 1-D workload's recipe at a smaller size)."""
+    rng = np.random.default_rng(seed)
+    A = workloads.gaussian_matrix(rng, m, n)
+    X = workloads.sparse_coefficients(rng, n, 1, k, values="gauss")
+    return A, A @ X, X
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+def test_large_signal_full_length(cs_gpu, torch, prec):
+    """n = 16384, m = 4915, k = 500 (the large 1-D workload scaled down by 4
+    in n and m), all 500 iterations against the incremental-QR oracle, and
+    exact recovery of the noiseless signal."""
+    A, Y, X = large_signal(16384, 4915, 500, seed=401)
+    A32, Y32, A64, Y64 = f32_problem(A, Y)
+    g = run(cs_gpu, torch, A32, Y32, 500, prec)
+    o = oracle.omp(A64, Y64, 500)
+    s = compare(g, o)
+    print(prec, s)
+    assert g["status"][0] == 0 and g["n_iter"][0] == 500
+    truth = np.nonzero(X[:, 0])[0]
+    assert sorted(g["support"][0].tolist()) == sorted(truth.tolist())
+    xr = np.zeros(A.shape[1])
+    xr[g["support"][0]] = g["coef"][0]
+    assert np.linalg.norm(xr - X[:, 0]) <= 1e-5 * np.linalg.norm(X[:, 0])
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("m,n,B,k,snr", [(300, 1000, 5, 100, 30.0),      # k beyond the on-chip 64
+                                         (1500, 3001, 3, 20, 40.0),      # more rows than a warp holds
+                                         (333, 1203, 7, 40, 30.0),       # bf16 beyond the tensor-core sizes
+                                         (150, 301, 9, 65, 20.0)])       # ragged, k near m / 2
+def test_large_path_matches_oracle(cs_gpu, torch, prec, m, n, B, k, snr):
+    p = workloads.random_problem(m, n, B, k, seed=m + n + k, snr_db=snr, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    g = run(cs_gpu, torch, A32, Y32, k, prec)
+    s = compare(g, oracle.omp(A64, Y64, k))
+    print(prec, m, n, B, k, s)
+
+
+def test_large_path_stop_rules_and_edges(cs_gpu, torch):
+    """Non-finite input (status 4), a zero signal under tol (1), max_iter (2),
+    a duplicated atom (tie to the lower index)."""
+    rng = np.random.default_rng(402)
+    m, n, k = 120, 400, 80
+    A = workloads.gaussian_matrix(rng, m, n)
+    A[:, 250] = A[:, 17]
+    Y = rng.standard_normal((m, 4))
+    Y[5, 1] = np.nan
+    Y[:, 2] = 0.0
+    Y[:, 3] = 3.0 * A[:, 17] + 0.25 * A[:, 90]
+    A32, Y32, A64, Y64 = f32_problem(A, Y)
+    g = run(cs_gpu, torch, A32, Y32, k, "fp32", max_iter=60, tol=1e-3)
+    o = oracle.omp(A64, Y64, k, max_iter=60, tol=1e-3)
+    assert g["status"].tolist()[:3] == [2, 4, 1]
+    assert g["n_iter"].tolist()[:3] == [60, 0, 0]
+    assert g["support"][3, 0] == 17
+    compare({q: v[[0]] for q, v in g.items() if q != "launches"},
+            {q: v[[0]] for q, v in o.items()})
+    # y on atom 17 alone: the tie with its copy goes to 17, then the exact
+    # fit stops on tol after one atom
+    y = np.float32(A32[:, 17] * 2.0)
+    g = run(cs_gpu, torch, A32, y.reshape(-1, 1), 70, "fp32", tol=1e-3)
+    assert g["support"][0, 0] == 17 and g["status"][0] == 1 and g["n_iter"][0] == 1
+
+
+def test_large_path_deterministic_and_routed(cs_gpu, torch):
+    """Two solves give the same bits; the large path is one solve per chunk
+    (no per-iteration launches of the on-chip kernels); CLOMP beyond the
+    on-chip limits is refused."""
+    p = workloads.random_problem(400, 2000, 4, 90, seed=403, snr_db=30.0)
+    A32, Y32, _, _ = f32_problem(p.A, p.Y)
+    a = run(cs_gpu, torch, A32, Y32, 90, "bf16")
+    b = run(cs_gpu, torch, A32, Y32, 90, "bf16")
+    for q in ("support", "coef", "n_iter", "res_norm", "status"):
+        assert np.array_equal(a[q], b[q]), q
+    assert a["launches"]["persist"] == 1 and a["launches"]["correlation"] == 0
+    A = torch.from_numpy(A32).cuda()
+    Y = torch.from_numpy(Y32).cuda()
+    with pytest.raises(cs_gpu.CSError) as e:
+        cs_gpu.clomp_solve_batched(A, Y, 90, plan=cs_gpu.Plan(400, 2000, 4, 90))
+    assert e.value.code == -5
