@@ -184,6 +184,131 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "sm_max_mhz": 2070.0}, "fallback"
 
 
+def peaks_and_src():
+    return measured_peaks()
+
+
+def events_ms(torch, stream, fn, reps):
+    """Mean device time of fn over reps runs (CUDA events on `stream`)."""
+    out = []
+    for _ in range(reps):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        out.append(a.elapsed_time(b))
+    return float(np.mean(out))
+
+
+def bench_large_1d(cs, torch, stream, barrier, rank, peaks_src):
+    """The long 1-D signal (n = 65536, m = 19661, k = 2000; A 5.2 GB float32):
+    one plain-OMP solve on the large-instance path per correlation precision,
+    the correlation's achieved HBM bandwidth, exact recovery of the noiseless
+    signal, and parity of the first 200 iterations with the FP64 oracle."""
+    import workloads
+    peaks, src = peaks_src
+    pl = workloads.config_large_1d()
+    m, n, k = pl.m, pl.n, pl.k
+    A = torch.from_numpy(pl.A).cuda()
+    y = torch.from_numpy(np.float32(pl.Y)).cuda()
+    plan = cs.Plan(m, n, 1, k)
+    res = {"workload": f"n={n}, m={m}, k={k}, one signal, Gaussian A (unit columns, float32, "
+                       f"{m * n * 4 / 1e9:.2f} GB), x k-sparse N(0,1), noiseless"}
+    truth = np.nonzero(pl.X_true[:, 0])[0]
+    for prec in ("bf16", "fp32"):
+        fn = lambda: cs.omp_solve_batched(A, y, k, prec=prec, plan=plan)
+        fn()
+        barrier()
+        ms = events_ms(torch, stream, fn, 2)
+        plan.set_profiling(True)
+        plan.profile(reset=True)
+        r = fn()
+        torch.cuda.synchronize()
+        ph = plan.profile(reset=True)
+        plan.set_profiling(False)
+        sup = r.support.cpu().numpy()[0]
+        coef = r.coef.cpu().numpy()[0].astype(np.float64)
+        xr = np.zeros(n)
+        xr[sup[sup >= 0]] = coef[sup >= 0]
+        n_c, t_c = ph["correlation"]
+        mp = (m + 7) // 8 * 8
+        a_bytes = n * mp * 2 if prec == "bf16" else n * m * 4
+        per_launch = a_bytes + mp * 4 + n * 4          # A once, r, the |c| written
+        gbs = per_launch * n_c / (t_c / 1e3) / 1e9 if n_c else None
+        res[prec] = {"ms_per_solve": ms, "signals_per_s": 1e3 / ms,
+                     "support_is_the_true_support": bool(sorted(sup.tolist()) == sorted(truth.tolist())),
+                     "coef_rel_err_vs_x_true": float(np.linalg.norm(xr - pl.X_true[:, 0]) /
+                                                     np.linalg.norm(pl.X_true[:, 0])),
+                     "status": int(r.status.cpu()[0]), "n_iter": int(r.n_iter.cpu()[0]),
+                     "phase_ms": {q: round(v[1], 3) for q, v in ph.items() if v[0]},
+                     "roofline_correlation": {"bound": "hbm", "achieved": gbs, "peak": peaks["hbm_gbs"],
+                                              "unit": "GB/s", "frac": (gbs / peaks["hbm_gbs"]) if gbs else None,
+                                              "bytes_per_launch": per_launch, "launches": n_c,
+                                              "peak_source": f"hbm_gbs ({src})"}}
+    if rank == 0:
+        # the first 200 iterations against the FP64 oracle (incremental QR, atoms over the host's threads)
+        import oracle
+        sys.path.insert(0, os.path.join(ROOT, "tests"))
+        import parity as prules
+        it = 200
+        r = cs.omp_solve_batched(A, y, k, prec="bf16", plan=plan, max_iter=it)
+        torch.cuda.synchronize()
+        g = prules.to_numpy(r)
+        t0 = time.perf_counter()
+        o = oracle.omp(pl.A.astype(np.float64, order="F"), np.float32(pl.Y).astype(np.float64), k, max_iter=it)
+        to = time.perf_counter() - t0
+        g = {q: v[:, :it] if v.ndim == 2 else v for q, v in g.items()}
+        o = {q: v[:, :it] if v.ndim == 2 else v for q, v in o.items()}
+        summ, fails = prules.summarize(g, o)
+        res["parity_first_200_iterations_bf16"] = {
+            "supports_identical": bool(np.array_equal(g["support"], o["support"])),
+            "ambiguous_ties": summ["ambiguous"], "non_ambiguous_mismatches": summ["failures"],
+            "max_coef_rel_err": summ["max_coef_rel_err"], "oracle_s": to, "oracle_cores": oracle.max_threads()}
+    del A, plan
+    torch.cuda.empty_cache()
+    return res
+
+
+def bench_uneven(cs, torch, stream, barrier):
+    """The uneven batch (2000 instances in 32 size classes, n in [512, 16384],
+    m/n in [0.1, 0.5], k = 1-10 % of n) through omp_solve_varlen: instances
+    within the on-chip kernels run batched per (A, m, n, k) group, the others
+    on the large-instance path per (A, m, n) group."""
+    import workloads
+    classes, assign, ks = workloads.config_uneven()
+    keep, items = [], [None] * len(assign)
+    work = 0.0
+    for c in range(len(classes)):
+        A, inst = workloads.uneven_class_data(classes, assign, ks, c, dtype=np.float32)
+        At = torch.from_numpy(A).cuda()
+        keep.append(At)
+        for i, yv, _ in inst:
+            items[i] = (At, torch.from_numpy(np.float32(yv)).cuda(), ks[i])
+            work += 2.0 * A.shape[0] * A.shape[1] * ks[i]
+    m_max = max(cl["m"] for cl in classes)
+    n_max = max(cl["n"] for cl in classes)
+    plan = cs.Plan(m_max, n_max, 128, max(ks))
+    res = {"workload": "2000 instances, 32 classes, n log-uniform in [512, 16384], m/n in [0.1, 0.5], "
+                       "k uniform in [0.01 n, 0.1 n], Gaussian/Bernoulli A, 30 dB",
+           "correlation_flops": work}
+    for prec in ("fp32", "bf16"):
+        fn = lambda: cs.omp_solve_varlen(items, prec=prec, plan=plan)
+        outs = fn()
+        barrier()
+        t0 = time.perf_counter()
+        outs = fn()
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - t0
+        st = np.array([int(o.status[0]) for o in outs])
+        res["omp_" + prec] = {"s_per_batch": wall, "instances_per_s": len(items) / wall,
+                              "solved": int(np.sum(st != cs.SIG_UNSUPPORTED)), "refused": int(np.sum(st == cs.SIG_UNSUPPORTED)),
+                              "note": "wall clock of one call (host loop over groups; large groups synchronise every 64 iterations)"}
+    del keep, plan
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -426,6 +551,8 @@ def main():
             single["oracle_ms_median_1_core"] = 1e3 * float(np.median(tt))
         compare["single_signal_n256_m64_k8"] = single
         del plan1
+        compare["large_1d_n65536_m19661_k2000"] = bench_large_1d(cs, torch, stream, barrier, rank, peaks_and_src())
+        compare["uneven_batch_2000"] = bench_uneven(cs, torch, stream, barrier)
         compare["clomp_headline"] = {"ms_per_step": ms, "signals_per_s": value}
         compare["clomp_over_omp_fp32"] = value / compare["omp_fp32"]["signals_per_s"]
 

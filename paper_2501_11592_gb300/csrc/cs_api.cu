@@ -328,6 +328,38 @@ cs_status ensure_lg(cs_plan* P, size_t bytes) {
     return CS_OK;
 }
 
+cudaEvent_t pool_event(cs_plan* P);
+
+// Measurement hook of the large-instance path: every group of launches of
+// one phase is counted and, when profiling, bracketed by CUDA events.
+struct LargeMarkCtx {
+    cs_plan* P;
+    cudaStream_t s;
+    cudaEvent_t a = nullptr;
+};
+void large_mark(void* vctx, int phase, int after) {
+    LargeMarkCtx* c = static_cast<LargeMarkCtx*>(vctx);
+    cs_plan* P = c->P;
+    if (!after) {
+        P->launches[phase] += 1;
+        if (P->profiling) {
+            c->a = pool_event(P);
+            if (c->a) cudaEventRecord(c->a, c->s);
+        }
+        return;
+    }
+    if (P->profiling && c->a) {
+        cudaEvent_t b = pool_event(P);
+        if (b) {
+            cudaEventRecord(b, c->s);
+            P->marks.push_back({phase, c->a, b});
+        } else {
+            P->pool.push_back(c->a);
+        }
+        c->a = nullptr;
+    }
+}
+
 // Plain OMP of signals sharing A on the large-instance path, in chunks whose
 // workspace stays within a few GB.
 constexpr size_t kLargeChunkBytes = (size_t)8 << 30;
@@ -365,12 +397,14 @@ cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const s
         call.tol = op->tol;
         call.bf16 = bf16;
         call.live_host = &live;
+        LargeMarkCtx mc{P, s};
+        call.mark = large_mark;
+        call.mark_ctx = &mc;
         const size_t need = large_ws_bytes(m, n, (int)nb, kmax, bf16);
         cs_status st = ensure_lg(P, need);
         if (st != CS_OK) return st;
         cudaError_t e = large_solve(call, P->lg, P->lg_bytes, s);
         if (e != cudaSuccess) return cuda_fail(e, "large OMP solve");
-        P->launches[CS_PHASE_PERSIST] += 1;
     }
     return CS_OK;
 }

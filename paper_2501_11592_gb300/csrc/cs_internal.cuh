@@ -136,6 +136,9 @@ struct LargeCall {
     double tol;
     int bf16;              // 1: correlate with a bf16 copy of A (certified, re-scored in float32)
     int* live_host;        // host int for the early end of the iteration loop (NULL: none)
+    // measurement hook: called around each launch with (ctx, CS_PHASE_*, 0 before / 1 after)
+    void (*mark)(void* ctx, int phase, int after);
+    void* mark_ctx;
 };
 bool large_supported(int m, int n, int k);
 size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16);

@@ -702,25 +702,38 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     LG_TRY(cudaMemcpyAsync(w + L.kv, call.ks.data(), sizeof(int) * Bl, cudaMemcpyHostToDevice, s));
     LG_TRY(cudaMemcpyAsync(w + L.itv, itv.data(), sizeof(int) * Bl, cudaMemcpyHostToDevice, s));
     LG_TRY(cudaMemsetAsync(w + L.colmax, 0, sizeof(float), s));
+    auto mark = [&](int phase, int after) {
+        if (call.mark) call.mark(call.mark_ctx, phase, after);
+    };
+    mark(CS_PHASE_SETUP, 0);
     k_lg_prep<<<ceil_div(S.n, 8), 256, 0, s>>>(S.A, S.lda, S.m, S.n, S.mp,
                                                const_cast<__nv_bfloat16*>(S.A16), const_cast<float*>(S.colmax));
     LG_TRY(cudaGetLastError());
     k_lg_setup<<<Bl, 1024, 0, s>>>(S);
     LG_TRY(cudaGetLastError());
+    mark(CS_PHASE_SETUP, 1);
     int* live_h = call.live_host;
     for (int it = 0; it < iters; ++it) {
         const int t = it;
+        mark(CS_PHASE_CORR, 0);
         LG_TRY(S.bf16 ? launch_corr<true>(S, s) : launch_corr<false>(S, s));
+        mark(CS_PHASE_CORR, 1);
+        mark(CS_PHASE_SELECT, 0);
         k_lg_scan<<<dim3(ceil_div(S.n, 256), Bl), 256, 0, s>>>(S);
         k_lg_rescore<<<dim3(LG_RESCORE_CTAS, Bl), 1024, 0, s>>>(S);
         k_lg_gram<<<dim3(ceil_div((t + 2) * S.nseg, 8), Bl), 256, 0, s>>>(S, t);
         k_lg_gsum<<<dim3(ceil_div(t + 2, 256), Bl), 256, 0, s>>>(S, t);
+        mark(CS_PHASE_SELECT, 1);
+        mark(CS_PHASE_FIT, 0);
         if (t > 0) k_lg_lpart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
         k_lg_pivot<<<Bl, 1024, 0, s>>>(S, t);
         if (t > 0) k_lg_upart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
         k_lg_update<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t);
+        mark(CS_PHASE_FIT, 1);
+        mark(CS_PHASE_RESID, 0);
         k_lg_rpart<<<dim3(ceil_div(S.m, 256), ceil_div(t + 1, LG_RQ), Bl), 256, 0, s>>>(S, t + 1);
         k_lg_resid<<<Bl, 1024, 0, s>>>(S);
+        mark(CS_PHASE_RESID, 1);
         LG_TRY(cudaGetLastError());
         // every 64 iterations: stop once no signal is running
         if (live_h && (it % 64) == 63 && it + 1 < iters) {

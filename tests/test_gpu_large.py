@@ -97,16 +97,19 @@ def test_large_path_stop_rules_and_edges(cs_gpu, torch):
 
 
 def test_large_path_deterministic_and_routed(cs_gpu, torch):
-    """Two solves give the same bits; the large path is one solve per chunk
-    (no per-iteration launches of the on-chip kernels); CLOMP beyond the
-    on-chip limits is refused."""
+    """Two solves give the same bits; the large path runs its own launch
+    groups (one correlation, selection, least-squares and residual group per
+    iteration, none of the on-chip kernels); CLOMP beyond the on-chip limits
+    is refused."""
     p = workloads.random_problem(400, 2000, 4, 90, seed=403, snr_db=30.0)
     A32, Y32, _, _ = f32_problem(p.A, p.Y)
     a = run(cs_gpu, torch, A32, Y32, 90, "bf16")
     b = run(cs_gpu, torch, A32, Y32, 90, "bf16")
     for q in ("support", "coef", "n_iter", "res_norm", "status"):
         assert np.array_equal(a[q], b[q]), q
-    assert a["launches"]["persist"] == 1 and a["launches"]["correlation"] == 0
+    ln = a["launches"]
+    assert ln["correlation"] == ln["select"] == ln["fit"] == ln["residual"] == 90
+    assert ln["persist"] == 0 and ln["update"] == 0 and ln["setup"] == 1
     A = torch.from_numpy(A32).cuda()
     Y = torch.from_numpy(Y32).cuda()
     with pytest.raises(cs_gpu.CSError) as e:

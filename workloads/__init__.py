@@ -176,6 +176,29 @@ def config_columnwise_2d(sr=0.3, n_images=64) -> Problem:
                    meta=dict(sr=sr, images=n_images, X_img=X_img, D=D))
 
 
+def config_large_1d(n=65536, m=19661, k=2000, block=4096) -> Problem:
+    """One long 1-D signal: a 256 x 256 image flattened to n = 65536 and
+    measured at rate 0.3 (m = 19661) by a dense Gaussian A with unit columns,
+    held in float32 (about 5.2 GB) and drawn in column blocks; x is k-sparse
+    with N(0,1) values at uniform positions; y = A x, noiseless.  The image is
+    taken as k-sparse in the 2D DCT basis; since a Gaussian matrix times an
+    orthonormal basis is again a Gaussian matrix, A stands for that product
+    directly.  A is float32 here (the other generators return float64)."""
+    rng = rng_for(CFG_LARGE_1D)
+    A = np.empty((m, n), dtype=np.float32, order="F")
+    for j0 in range(0, n, block):
+        j1 = min(n, j0 + block)
+        G = rng.standard_normal((j1 - j0, m), dtype=np.float32)
+        G /= np.linalg.norm(G.astype(np.float64), axis=1, keepdims=True).astype(np.float32)
+        A[:, j0:j1] = G.T
+    S = np.sort(rng.choice(n, size=k, replace=False))
+    X = np.zeros((n, 1))
+    X[S, 0] = rng.standard_normal(k)
+    y = A[:, S].astype(np.float64) @ X[S, 0]
+    return Problem(name=f"large1d_n{n}_m{m}_k{k}", A=A, Y=np.asfortranarray(y.reshape(-1, 1)), k=k, tol=0.0,
+                   max_iter=k, X_true=X)
+
+
 def config_uneven(n_instances=2000, n_classes=32):
     """Uneven batch: 32 size classes with n log-uniform in [512,16384]
     (rounded to 64), m/n uniform in [0.1,0.5] (rounded to 16), Gaussian A for
