@@ -422,6 +422,7 @@ def main():
     if not args.no_extras:
         ksteps = max(3, min(args.steps, 10))
         for name, algo, prec, form in [("omp_fp32", "omp", "fp32", "gram"), ("omp_bf16", "omp", "bf16", "gram"),
+                                       ("omp_fp8", "omp", "fp8", "gram"), ("clomp_fp8_gram", "clomp", "fp8", "gram"),
                                        ("clomp_fp32_gram", "clomp", "fp32", "gram"),
                                        ("clomp_bf16_gather", "clomp", "bf16", "gather"),
                                        ("clomp_bf16_gram_per_iteration", "clomp", "bf16", "gram"),

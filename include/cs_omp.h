@@ -70,10 +70,18 @@ enum {
  * re-scores the low-precision candidates in float32. */
 typedef enum {
     CS_CORR_FP32 = 0,   /* float32 SIMT correlation, exact float32 argmax */
-    CS_CORR_BF16 = 1    /* bf16 tensor-core correlation (tcgen05, fp32 accumulate), two
+    CS_CORR_BF16 = 1,   /* bf16 tensor-core correlation (tcgen05, fp32 accumulate), two
                            best atoms per 16-atom group, fp32 re-score of the 8 best and of
                            every atom the rounding bound cannot rule out (n <= 4096,
-                           m <= 256) */
+                           m <= 256; plain OMP beyond that runs the large-instance path
+                           with a bf16 copy of A, see omp_solve_batched) */
+    CS_CORR_FP8 = 2     /* FP8 (E4M3) tensor-core correlation (tcgen05 kind::f8f6f4, fp32
+                           accumulate): each column of A scaled by max|a_j| / 448 once per
+                           solve, each residual by max|r| / 448 every iteration; the same
+                           candidates and fp32 re-score as bf16, with a rounding bound built
+                           from the exact quantisation-error norms of both operands
+                           (n <= 4096, m <= 256, k within the plan's on-chip 32 or 64;
+                           CS_ENOTSUP otherwise) */
 } cs_corr_prec;
 
 /* How the CLOMP coefficient fit evaluates its gradient -A_S^T (y - A_S s_S). */

@@ -30,7 +30,7 @@ _LIB_PATH = os.path.join(_PKG, "_lib", "libcs_omp.so")
 
 CS_OK, CS_EINVAL, CS_ENOMEM, CS_ECUDA, CS_ETIMEOUT, CS_ENOTSUP = 0, -1, -2, -3, -4, -5
 SIG_REACHED_K, SIG_REACHED_TOL, SIG_MAX_ITER, SIG_DEPENDENT, SIG_NONFINITE, SIG_UNSUPPORTED = 0, 1, 2, 3, 4, 5
-PREC = {"fp32": 0, "bf16": 1}
+PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 FORM = {"gather": 0, "gram": 1}
 PHASES = ("setup", "correlation", "select", "fit", "residual", "update", "persist")
 OPT_GRAPHS, OPT_FUSE_UPDATE, OPT_PERSIST, OPT_STALL_TEST, OPT_FUSED_OMP = 0, 1, 2, 3, 4

@@ -2,6 +2,7 @@
 // validation, the per-iteration launch sequence and the C ABI declared in
 // include/cs_omp.h.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -63,6 +64,12 @@ struct cs_plan {
     size_t ws_bytes = 0;
     float* A32 = nullptr;
     __nv_bfloat16* A16 = nullptr;
+    uint8_t* A8 = nullptr;     // FP8 copy of A, its per-column scales and largest error norm
+    float* sa = nullptr;
+    float* ea = nullptr;
+    uint8_t* R8 = nullptr;     // FP8 residuals, per-signal scales and error norms
+    float* sr = nullptr;
+    float* er = nullptr;
     float* Y32 = nullptr;
     float* R32 = nullptr;
     __nv_bfloat16* R16 = nullptr;
@@ -121,7 +128,7 @@ struct cs_plan {
         const void* A = nullptr;   // the caller's A (device, or host for the host-buffer calls)
         int m = 0, n = 0, lda = 0;
         uint64_t gen = 0;
-        int bf16 = 0, gram = 0;
+        int bf16 = 0, fp8 = 0, gram = 0;
     } prep;
     const void* a_host = nullptr;   // set by the host-buffer solve around its call of solve()
     int img_ready = 0, img_ready_h = 0;   // image shape whose cluster launch was checked
@@ -146,21 +153,27 @@ struct Carver {
 // entry point.  clomp: CLOMP state (G, bvec, Adam moments); gram_a: the
 // n x n Gram matrix of A.
 struct WsLayout {
-    size_t A32, A16, Y32, R32, R16, mask, cval, cidx, cbound, gcol, dnorm, bt, L, z, x64, G, bvec, am,
-        av, tau, colnorm, counters, GA, total;
+    size_t A32, A16, A8, sa, ea, Y32, R32, R16, R8, sr, er, mask, cval, cidx, cbound, gcol, dnorm, bt, L, z, x64,
+        G, bvec, am, av, tau, colnorm, counters, GA, total;
 };
 
 WsLayout ws_layout(int m, int n, int B, int K, bool clomp, bool gram_a) {
     const size_t Bm = (size_t)B, Kk = (size_t)K;
-    const size_t mp = round_up(m, 4), mh = round_up(m, 64), nw = ceil_div(n, 32);
+    const size_t mp = round_up(m, 4), mh = round_up(m, 64), mq = round_up(m, 128), nw = ceil_div(n, 32);
     const size_t slots = cand_slots(n), tiles = ceil_div(n, kCorrTcTileN);
     Carver cv;
     WsLayout L{};
     L.A32 = cv.take<float>((size_t)n * mp);
     L.A16 = cv.take<__nv_bfloat16>((size_t)n * mh);
+    L.A8 = cv.take<uint8_t>((size_t)n * mq);
+    L.sa = cv.take<float>(n);
+    L.ea = cv.take<float>(1);
     L.Y32 = cv.take<float>(Bm * mp);
     L.R32 = cv.take<float>(Bm * mp);
     L.R16 = cv.take<__nv_bfloat16>(Bm * mh);
+    L.R8 = cv.take<uint8_t>(Bm * mq);
+    L.sr = cv.take<float>(Bm);
+    L.er = cv.take<float>(Bm);
     L.mask = cv.take<uint32_t>(Bm * nw);
     L.cval = cv.take<float>(Bm * slots);
     L.cidx = cv.take<int>(Bm * slots);
@@ -188,9 +201,15 @@ WsLayout ws_layout(int m, int n, int B, int K, bool clomp, bool gram_a) {
 void bind_workspace(cs_plan* P, char* w, const WsLayout& L) {
     P->A32 = reinterpret_cast<float*>(w + L.A32);
     P->A16 = reinterpret_cast<__nv_bfloat16*>(w + L.A16);
+    P->A8 = reinterpret_cast<uint8_t*>(w + L.A8);
+    P->sa = reinterpret_cast<float*>(w + L.sa);
+    P->ea = reinterpret_cast<float*>(w + L.ea);
     P->Y32 = reinterpret_cast<float*>(w + L.Y32);
     P->R32 = reinterpret_cast<float*>(w + L.R32);
     P->R16 = reinterpret_cast<__nv_bfloat16*>(w + L.R16);
+    P->R8 = reinterpret_cast<uint8_t*>(w + L.R8);
+    P->sr = reinterpret_cast<float*>(w + L.sr);
+    P->er = reinterpret_cast<float*>(w + L.er);
     P->mask = reinterpret_cast<uint32_t*>(w + L.mask);
     P->cand_val = reinterpret_cast<float*>(w + L.cval);
     P->cand_idx = reinterpret_cast<int*>(w + L.cidx);
@@ -291,7 +310,7 @@ cs_status validate(const cs_plan* P, const float* A, int m, int n, int lda, cons
     if (op->k < 1 || op->k > m || op->k > n)
         return fail(CS_EINVAL, "k=%d must satisfy 1 <= k <= min(m=%d, n=%d)", op->k, m, n);
     if (!(op->tol >= 0.0)) return fail(CS_EINVAL, "tol must be >= 0");
-    if (op->prec != CS_CORR_FP32 && op->prec != CS_CORR_BF16)
+    if (op->prec != CS_CORR_FP32 && op->prec != CS_CORR_BF16 && op->prec != CS_CORR_FP8)
         return fail(CS_EINVAL, "prec=%d is not a cs_corr_prec", op->prec);
     if (op->topc < 0 || op->topc > kTopcMax) return fail(CS_EINVAL, "topc=%d not in [0, 8]", op->topc);
     if (m > P->m_max || n > P->n_max || B > P->B_max)
@@ -420,6 +439,7 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
     a.iters = (op->max_iter > 0) ? std::min(op->k, op->max_iter) : op->k;
     a.mp = round_up(m, 4);
     a.mh = round_up(m, 64);   // bf16 rows: whole 128-byte swizzle rows for TMA
+    a.mq = round_up(m, 128);  // fp8 rows: the same
     a.nw = ceil_div(n, 32);
     a.prec = op->prec;
     if (op->prec == CS_CORR_FP32) {
@@ -435,6 +455,13 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
     a.Y32 = P->Y32;
     a.R32 = P->R32;
     a.R16 = (op->prec == CS_CORR_BF16) ? P->R16 : nullptr;
+    const bool fp8 = op->prec == CS_CORR_FP8;
+    a.R8 = fp8 ? P->R8 : nullptr;
+    a.A8 = P->A8;
+    a.sa = P->sa;
+    a.ea_max = P->ea;
+    a.sr = P->sr;
+    a.er = P->er;
     a.mask = P->mask;
     a.cand_val = P->cand_val;
     a.cand_idx = P->cand_idx;
@@ -527,6 +554,9 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             return fail(CS_EINVAL, "tv_D needs tv_ldd >= tv_N >= 1 (tv_N=%d tv_ldd=%d)", cp->tv_N, cp->tv_ldd);
     }
     if (B == 0) return CS_OK;
+    if (op->prec == CS_CORR_FP8 && (!corr_tc_supported(m, n) || op->k > P->k_max))
+        return fail(CS_ENOTSUP, "the FP8 correlation runs with m <= 256, n <= %d and k <= %d (m=%d n=%d k=%d)",
+                    kCorrTcMaxN, P->k_max, m, n, op->k);
     if (needs_large(P, m, n, op->k, op->prec)) {
         if (cp)
             return fail(CS_ENOTSUP, "CLOMP runs with m <= %d, k <= %d (the plan's on-chip limit) and, with the bf16 "
@@ -546,6 +576,8 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
 
     IterArgs a = make_args(P, m, n, B, op, support, coef, n_iter, res_norm, sig_status);
     const bool bf16 = (op->prec == CS_CORR_BF16);
+    const bool fp8 = (op->prec == CS_CORR_FP8);
+    const bool lowp = bf16 || fp8;   // tensor-core correlation, certified candidates
     a.need_gcol = cp ? 0 : 1;
     a.need_gram = (cp && cp->form == CS_CL_GRAM) ? 1 : 0;
 
@@ -610,7 +642,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
     const cs_plan::Prep& pr = P->prep;
     const void* a_key = P->a_host ? P->a_host : (const void*)A;
     const bool reuse_a = P->a_gen != 0 && pr.gen == P->a_gen && pr.A == a_key && pr.m == m && pr.n == n &&
-                         pr.lda == lda && (pr.bf16 || !bf16) && (pr.gram || !need_gram) && !tv;
+                         pr.lda == lda && (pr.bf16 || !bf16) && (pr.fp8 || !fp8) && (pr.gram || !need_gram) && !tv;
 
     // plain OMP on small batches: the whole solve in one kernel, one CTA per signal
     const bool omp_fused = !cp && P->fused_omp && a.B <= device_sm_count() && omp_fused_supported(a);
@@ -624,7 +656,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
     // selection + fit + residual kernel per iteration
     const bool th_rule = cp && c.th > 0.f;
     if (th_rule) {
-        if (cp->form != CS_CL_GRAM || bf16 || !clomp_th_supported(a))
+        if (cp->form != CS_CL_GRAM || lowp || !clomp_th_supported(a))
             return fail(CS_ENOTSUP, "select_threshold in (0, 1) runs with the float32 correlation "
                                     "(CS_CORR_FP32), the Gram-form fit, m <= 1024 and k <= 32");
         st = ensure_cbuf(P);
@@ -642,6 +674,12 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
                               return launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, bf16 ? P->A16 : nullptr,
                                                    P->colnorm_max, st);
                           }), "prep A");
+            if (fp8) {
+                CS_TRY_LAUNCH(cudaMemsetAsync(P->ea, 0, sizeof(float), st), "clear FP8 error norm");
+                CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
+                                  return launch_prep_A8(A, lda, m, n, a.mq, P->A8, P->sa, P->ea, st);
+                              }), "prep A (FP8)");
+            }
             if (need_gram)
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] { return launch_gram_A(P->A32, a.mp, n, P->GA, st); }),
                               "gram of A");
@@ -675,7 +713,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         }
         for (int it = 0; it < a.iters; ++it) {
             c.tau0 = c.reset ? 0 : it * c.steps;
-            if (bf16)
+            if (lowp)
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, st, [&] { return launch_corr_tc(a, st); }), "correlation (tcgen05)");
             else
                 CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, st, [&] { return launch_corr_fp32(a, st); }), "correlation (fp32)");
@@ -712,6 +750,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         np.lda = lda;
         np.gen = P->a_gen;
         np.bf16 = bf16 ? 1 : 0;
+        np.fp8 = fp8 ? 1 : 0;
         np.gram = (need_gram && !tv) ? 1 : 0;
         P->prep = np;
     }
@@ -886,6 +925,8 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
     // (CLOMP, or sizes beyond that path).
     auto large = [&](const cs_instance& x) { return needs_large(P, x.m, x.n, x.k, op->prec); };
     auto refused = [&](const cs_instance& x) {
+        if (op->prec == CS_CORR_FP8)   // the FP8 correlation has no large-instance form
+            return x.m > P->m_max || x.n > P->n_max || x.k > P->k_max || !corr_tc_supported(x.m, x.n);
         return x.m > P->m_max || x.n > P->n_max || x.k > P->k_user ||
                (large(x) && (cp || P->no_large || !large_supported(x.m, x.n, x.k)));
     };
@@ -953,6 +994,19 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
     std::vector<const float*> yp;
     std::vector<VarlenOut> ot;
     std::vector<VarlenRefuse> rt;
+    // A does not change during the call: groups sharing it keep its
+    // preparation (copies, A^T A) under a generation of this call alone
+    const uint64_t saved_gen = P->a_gen;
+    static std::atomic<uint64_t> call_gen{1};
+    P->a_gen = (uint64_t)0x8000000000000000ull | call_gen.fetch_add(1);
+    struct Restore {
+        cs_plan* P;
+        uint64_t gen;
+        ~Restore() {
+            P->a_gen = gen;
+            P->prep = cs_plan::Prep{};
+        }
+    } restore{P, saved_gen};   // the caller's generation back, nothing of this call kept
     for (size_t r0 = 0; r0 < refuse.size(); r0 += Bm) {
         const int nr = (int)std::min(Bm, refuse.size() - r0);
         rt.assign(nr, VarlenRefuse{});
@@ -1196,17 +1250,25 @@ cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int3
     if (m > plan->m_max || n > plan->n_max || batch > plan->B_max)
         return fail(CS_EINVAL, "problem exceeds the plan");
     if (m > kMaxRowChunks * 128) return fail(CS_ENOTSUP, "cs_correlate takes m <= %d (m=%d)", kMaxRowChunks * 128, m);
-    if (prec != CS_CORR_FP32 && prec != CS_CORR_BF16) return fail(CS_EINVAL, "prec=%d", prec);
-    if (prec == CS_CORR_BF16 && !corr_tc_supported(m, n))
-        return fail(CS_ENOTSUP, "bf16 tensor-core correlation unavailable for m=%d n=%d", m, n);
+    if (prec != CS_CORR_FP32 && prec != CS_CORR_BF16 && prec != CS_CORR_FP8) return fail(CS_EINVAL, "prec=%d", prec);
+    if (prec != CS_CORR_FP32 && !corr_tc_supported(m, n))
+        return fail(CS_ENOTSUP, "tensor-core correlation unavailable for m=%d n=%d", m, n);
     if (batch == 0) return CS_OK;
     if (!A || !R || !C) return fail(CS_EINVAL, "NULL array");
     DeviceGuard dg(plan->device);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
     cudaStream_t s = (cudaStream_t)stream;
-    const int mp = round_up(m, 4), mh = round_up(m, 64);
+    const int mp = round_up(m, 4), mh = round_up(m, 64), mq = round_up(m, 128);
     const bool bf16 = (prec == CS_CORR_BF16);
-    plan->prep = cs_plan::Prep{};   // A32 / A16 are overwritten
+    plan->prep = cs_plan::Prep{};   // A32 / A16 / A8 are overwritten
+    if (prec == CS_CORR_FP8) {
+        CS_TRY_LAUNCH(cudaMemsetAsync(plan->ea, 0, sizeof(float), s), "clear FP8 error norm");
+        CS_TRY_LAUNCH(launch_prep_A8(A, lda, m, n, mq, plan->A8, plan->sa, plan->ea, s), "prep A (FP8)");
+        CS_TRY_LAUNCH(launch_prep_R8(R, ldr, m, batch, mq, plan->R8, plan->sr, plan->er, s), "prep R (FP8)");
+        CS_TRY_LAUNCH(launch_corr_tc8_dense(plan->R8, plan->A8, plan->sr, plan->sa, mq, batch, n, C, ldc,
+                                            plan->counters + 1, s), "correlation (tcgen05, FP8)");
+        return CS_OK;
+    }
     CS_TRY_LAUNCH(launch_prep_A(A, lda, m, n, mp, mh, plan->A32, bf16 ? plan->A16 : nullptr, nullptr, s),
                   "prep A");
     CS_TRY_LAUNCH(launch_prep_R(R, ldr, m, batch, mp, mh, bf16 ? nullptr : plan->R32,

@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cuda_bf16.h>
+#include <cuda_fp8.h>
 #include <stdint.h>
 
 #include <vector>
@@ -61,6 +62,16 @@ struct IterArgs {
     float* Y32;
     float* R32;
     __nv_bfloat16* R16;
+    // FP8 (E4M3) correlation: A8 [n][mq] with per-column scales sa (a_j ~ sa_j
+    // A8_j), ea_max = max_j ||a_j - sa_j A8_j||; R8 [B][mq] with per-signal
+    // scales sr and quantisation-error norms er; mq = m rounded up to 128
+    const uint8_t* A8;
+    const float* sa;
+    const float* ea_max;
+    uint8_t* R8;
+    float* sr;
+    float* er;
+    int mq;
     uint32_t* mask;
     float* cand_val;
     int* cand_idx;
@@ -155,6 +166,10 @@ cudaError_t launch_varlen_scatter(const VarlenOut* outs, int k, int B, const int
                                   const int* n_iter, const float* res_norm, const int* status, cudaStream_t s);
 cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh, float* A32,
                           __nv_bfloat16* A16, float* colnorm_max, cudaStream_t s);
+// FP8 copy of A: A8 [n][mq] (E4M3, zero padded), per-column scales sa and
+// the largest quantisation-error norm (ea_max, zeroed by the caller first).
+cudaError_t launch_prep_A8(const float* A, int lda, int m, int n, int mq, uint8_t* A8, float* sa, float* ea_max,
+                           cudaStream_t s);
 cudaError_t launch_setup(const IterArgs& a, const float* Y, int ldy, int clomp, cudaStream_t s);
 cudaError_t launch_adam_table(float2* tab, int len, float lr, float beta1, float beta2,
                               cudaStream_t s);
@@ -166,6 +181,9 @@ cudaError_t launch_corr_fp32_dense_live(const IterArgs& a, float* C, int ldc, cu
 cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n,
                                  float* C, int ldc, unsigned* errflag, cudaStream_t s);
+// FP8 tensor-core correlation, dense output C^T[b][j] = sr_b sa_j (R8_b . A8_j).
+cudaError_t launch_corr_tc8_dense(const uint8_t* R8, const uint8_t* A8, const float* sr, const float* sa, int mq,
+                                  int B, int n, float* C, int ldc, unsigned* errflag, cudaStream_t s);
 cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s);
 // Total-variation prior (Eq. 5): GA += lambda (Delta D)^T (Delta D), D N x n
 // (ld ldd; nullptr: the identity, N = n); E [n][Ep] and T [n][n] are scratch.
@@ -173,6 +191,8 @@ cudaError_t launch_tv_prior(const float* D, int N, int ldd, int n, float lambda,
                             float* GA, cudaStream_t s);
 cudaError_t launch_prep_R(const float* R, int ldr, int m, int B, int mp, int mh, float* R32,
                           __nv_bfloat16* R16, cudaStream_t s);
+cudaError_t launch_prep_R8(const float* R, int ldr, int m, int B, int mq, uint8_t* R8, float* sr, float* er,
+                           cudaStream_t s);
 bool corr_tc_supported(int m, int n);
 // 2-D bf16 TMA map over `rows` rows of `row_elems` elements (a multiple of 64,
 // byte stride row_bytes): box 64 x box_rows, 128-byte swizzle, zero fill.

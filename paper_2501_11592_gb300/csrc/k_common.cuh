@@ -25,6 +25,49 @@ __device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsign
 }
 
 
+// E4M3 (FP8) round-to-nearest with saturation to +-448, and its value.
+__device__ __forceinline__ uint32_t fp8_e4m3(float x) {
+    return (uint32_t)__nv_cvt_float_to_fp8(x, __NV_SATFINITE, __NV_E4M3);
+}
+__device__ __forceinline__ float fp8_e4m3_value(uint32_t q) {
+    return __half2float(__half(__nv_cvt_fp8_to_halfraw((__nv_fp8_storage_t)q, __NV_E4M3)));
+}
+// Scale that maps a vector's largest magnitude to the largest finite E4M3
+// value (448); 1 for a zero vector.
+__device__ __forceinline__ float fp8_scale(float amax) { return amax > 0.f ? amax / 448.f : 1.f; }
+
+__device__ __forceinline__ float warp_max(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// One warp quantises x[0..m) (zero past m, up to mq, a multiple of 128) to
+// E4M3 with the scale fp8_scale(max |x_i|): dst[i] = e4m3(x_i / scale).
+// Returns the scale; *err receives ||x - scale * dst||_2.
+__device__ __forceinline__ float quant_row_fp8(const float* __restrict__ x, int m, int mq, uint8_t* __restrict__ dst,
+                                               float* err) {
+    const int lane = threadIdx.x & 31;
+    float amax = 0.f;
+    for (int i = lane; i < m; i += 32) amax = fmaxf(amax, fabsf(x[i]));
+    const float scale = fp8_scale(warp_max(amax));
+    float e2 = 0.f;
+    for (int i = 4 * lane; i < mq; i += 128) {
+        uint32_t packed = 0;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const float v = i + u < m ? x[i + u] : 0.f;
+            const uint32_t q = fp8_e4m3(v / scale);
+            const float d = v - scale * fp8_e4m3_value(q);
+            e2 = fmaf(d, d, e2);
+            packed |= q << (8 * u);
+        }
+        *reinterpret_cast<uint32_t*>(dst + i) = packed;
+    }
+    *err = sqrtf(warp_sum(e2));
+    return scale;
+}
+
 // Approximate reciprocal (rcp.approx.ftz, relative error ~2^-23).
 __device__ __forceinline__ float rcp_approx(float x) {
     float y;

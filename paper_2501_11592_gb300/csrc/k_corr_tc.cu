@@ -1,5 +1,9 @@
-// K1: bf16 tensor-core correlation C^T = R^T A on sm_103a (tcgen05 + TMA),
-// fp32 accumulation in tensor memory, fused masked top-c epilogue.
+// K1: bf16 or FP8 (E4M3) tensor-core correlation C^T = R^T A on sm_103a
+// (tcgen05 + TMA), fp32 accumulation in tensor memory, fused masked top-c
+// epilogue.  In FP8 mode the operands carry per-atom and per-signal scales
+// (a_j ~ sa_j A8_j, r_b ~ sr_b R8_b) applied in the epilogue; a 128-element
+// E4M3 row is the same 128-byte swizzled row as 64 bf16 elements, so the
+// staging, the descriptors and the four MMAs per chunk are the same.
 //
 // The residual-injection branch (Methods, "Coefficients learning on OMP")
 // applies the fixed layer A to r^T for all signals at once -- a GEMM with
@@ -31,6 +35,7 @@ namespace {
 constexpr int TM = 128;              // signals per CTA (UMMA M, TMEM lanes)
 constexpr int TN = kCorrTcTileN;     // atoms per CTA (UMMA N, TMEM columns)
 constexpr int KCH = 64;              // bf16 elements per 128-byte swizzled row
+constexpr int KCH8 = 128;            // E4M3 elements per 128-byte swizzled row
 constexpr int R_CHUNK_BYTES = TM * KCH * 2;   // 16 KiB
 constexpr int A_CHUNK_BYTES = TN * KCH * 2;   // 32 KiB
 constexpr int MAX_KC = 4;            // m <= 256 staged at once
@@ -46,15 +51,20 @@ struct TcArgs {
     float* dense;       // optional dense output C^T (B x n, row stride ldd); nullptr = top-c only
     int ldd;
     unsigned* errflag;
+    const float* sa;    // FP8: per-atom scales
+    const float* sr;    // FP8: per-signal scales
 };
 
 constexpr int NTHREADS = 512;          // 16 warps: four per TMEM lane quadrant
 constexpr int NPART = NTHREADS / 128;  // column parts per quadrant
 constexpr int HALF = TN / NPART;       // columns per epilogue warp (64)
 
+template <bool FP8>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapA, TcArgs p) {
+    constexpr int KEL = FP8 ? KCH8 : KCH;   // elements per chunk row
     extern __shared__ uint8_t smem_raw[];
+    __shared__ float sSa[FP8 ? TN : 1];     // FP8: the tile's atom scales
     __shared__ __align__(8) uint64_t full_bar[MAX_KC];
     __shared__ __align__(8) uint64_t done_bar;
     __shared__ uint32_t tmem_slot;
@@ -123,17 +133,20 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
             sMask[sl][w] = bits;
         }
     }
+    if constexpr (FP8) {
+        for (int e = tid; e < TN; e += NTHREADS) sSa[e] = (j0 + e < p.n) ? p.sa[j0 + e] : 0.f;
+    }
 
     if (tid == 0) {
         // producer: all K chunks of both operands, one barrier per chunk
         for (int c = 0; c < p.kc; ++c) {
             mbar_arrive_expect_tx(&full_bar[c], R_CHUNK_BYTES + A_CHUNK_BYTES);
-            tma_load_2d(sR + (size_t)c * R_CHUNK_BYTES, &mapR, &full_bar[c], c * KCH, b0);
-            tma_load_2d(sA + (size_t)c * A_CHUNK_BYTES, &mapA, &full_bar[c], c * KCH, j0);
+            tma_load_2d(sR + (size_t)c * R_CHUNK_BYTES, &mapR, &full_bar[c], c * KEL, b0);
+            tma_load_2d(sA + (size_t)c * A_CHUNK_BYTES, &mapA, &full_bar[c], c * KEL, j0);
         }
     } else if (tid == 32) {
         // MMA issuer
-        constexpr uint32_t idesc = make_idesc(TM, TN);
+        constexpr uint32_t idesc = FP8 ? make_idesc_e4m3(TM, TN) : make_idesc(TM, TN);
         bool ok = true;
         for (int c = 0; c < p.kc && ok; ++c) {
             if (!mbar_wait(&full_bar[c], 0)) { ok = false; break; }
@@ -141,9 +154,12 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
             const uint64_t da = smem_desc_sw128(smem_u32(sR + (size_t)c * R_CHUNK_BYTES));
             const uint64_t db = smem_desc_sw128(smem_u32(sA + (size_t)c * A_CHUNK_BYTES));
 #pragma unroll
-            for (int k = 0; k < KCH / 16; ++k) {
-                // advance 16 elements (32 bytes) along K inside the swizzled row
-                umma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (c | k) != 0);
+            for (int k = 0; k < 4; ++k) {
+                // advance 32 bytes along K inside the swizzled row (16 bf16 / 32 E4M3 elements)
+                if constexpr (FP8)
+                    umma_e4m3(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (c | k) != 0);
+                else
+                    umma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (c | k) != 0);
             }
         }
         if (!ok) {
@@ -163,6 +179,8 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
     const bool live = sig < p.B;
     const uint32_t tbase = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)(half * HALF);
     const int a0 = j0 + half * HALF;     // first atom of this warp's half
+    // FP8: c = sr_b sa_j acc (the signal's scale here, the atom's per value)
+    const float srow = (FP8 && live) ? p.sr[sig] : 1.f;
 
     if (ok && p.dense) {
         for (int c0 = 0; c0 < HALF; c0 += 32) {
@@ -172,7 +190,9 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
             if (!live) continue;
             for (int q = 0; q < 32; ++q) {
                 const int atom = a0 + c0 + q;
-                if (atom < p.n) p.dense[(size_t)sig * p.ldd + atom] = __uint_as_float(v[q]);
+                float x = __uint_as_float(v[q]);
+                if constexpr (FP8) x = x * sSa[half * HALF + c0 + q] * srow;
+                if (atom < p.n) p.dense[(size_t)sig * p.ldd + atom] = x;
             }
         }
     } else if (ok) {
@@ -201,7 +221,9 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
 #pragma unroll
                 for (int q = 0; q < kTcGroup; ++q) {
                     const int qq = kTcGroup * g + q;
-                    const float x = ((mw >> qq) & 1u) ? -1.f : fabsf(__uint_as_float(v[qq]));
+                    float cv = __uint_as_float(v[qq]);
+                    if constexpr (FP8) cv = cv * sSa[half * HALF + 32 * c + qq] * srow;
+                    const float x = ((mw >> qq) & 1u) ? -1.f : fabsf(cv);
                     const bool gt1 = x > m1, gt2 = x > m2;
                     m3 = gt2 ? m2 : fmaxf(m3, x);
                     m2 = gt1 ? m1 : (gt2 ? x : m2);
@@ -262,16 +284,19 @@ EncodeFn get_encode() {
     return fn;
 }
 
-// 2-D bf16 map over rows of `row_elems` (a multiple of 64) with byte stride
-// `row_bytes`; box = 64 x box_rows, 128-byte swizzle, zero fill outside.
-bool make_map(CUtensorMap* map, const void* base, int row_elems, int rows, size_t row_bytes, int box_rows) {
+// 2-D map over rows of `row_elems` elements (bf16: a multiple of 64; fp8: of
+// 128) with byte stride `row_bytes`; box = one 128-byte row x box_rows,
+// 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap* map, const void* base, int row_elems, int rows, size_t row_bytes, int box_rows,
+              bool fp8 = false) {
     EncodeFn enc = get_encode();
     if (!enc) return false;
     cuuint64_t gdim[2] = {(cuuint64_t)row_elems, (cuuint64_t)rows};
     cuuint64_t gstride[1] = {(cuuint64_t)row_bytes};
-    cuuint32_t box[2] = {(cuuint32_t)KCH, (cuuint32_t)box_rows};
+    cuuint32_t box[2] = {(cuuint32_t)(fp8 ? KCH8 : KCH), (cuuint32_t)box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), gdim, gstride, box, estr,
+    CUresult r = enc(map, fp8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2,
+                     const_cast<void*>(base), gdim, gstride, box, estr,
                      CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
@@ -279,21 +304,23 @@ bool make_map(CUtensorMap* map, const void* base, int row_elems, int rows, size_
 
 size_t smem_bytes(int kc) { return (size_t)kc * (R_CHUNK_BYTES + A_CHUNK_BYTES) + 1024; }
 
-cudaError_t launch_tc(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n, TcArgs p,
-                      cudaStream_t s) {
+// R and A operand rows of `rowlen` elements (bf16: 2 bytes, fp8: 1 byte).
+template <bool FP8>
+cudaError_t launch_tc(const void* R, const void* A, int rowlen, int B, int n, TcArgs p, cudaStream_t s) {
     CUtensorMap mR, mA;
-    if (!make_map(&mR, R16, mh, B, (size_t)mh * 2, TM) || !make_map(&mA, A16, mh, n, (size_t)mh * 2, TN))
+    const size_t rb = (size_t)rowlen * (FP8 ? 1 : 2);
+    if (!make_map(&mR, R, rowlen, B, rb, TM, FP8) || !make_map(&mA, A, rowlen, n, rb, TN, FP8))
         return cudaErrorInvalidValue;
     const size_t smem = std::max(smem_bytes(p.kc), (size_t)100 * 1024);   // <= 2 CTAs per SM (TMEM)
     static int configured = 0;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_corr_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaError_t e = cudaFuncSetAttribute(k_corr_tc<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem_bytes(MAX_KC));
         if (e != cudaSuccess) return e;
         configured = 1;
     }
     dim3 grid(ceil_div(B, TM), ceil_div(n, TN));
-    return launch_pdl(k_corr_tc, grid, dim3(NTHREADS), smem, s, mR, mA, p);
+    return launch_pdl(k_corr_tc<FP8>, grid, dim3(NTHREADS), smem, s, mR, mA, p);
 }
 
 }  // namespace
@@ -308,10 +335,11 @@ bool corr_tc_supported(int m, int n) {
 }
 
 cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s) {
+    const bool fp8 = a.prec == CS_CORR_FP8;
     TcArgs p{};
     p.B = a.B;
     p.n = a.n;
-    p.kc = a.mh / KCH;
+    p.kc = fp8 ? a.mq / KCH8 : a.mh / KCH;
     p.nch = a.nch;
     p.topc = a.topc;
     p.nw = a.nw;
@@ -322,7 +350,12 @@ cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s) {
     p.cand_bound = a.cand_bound;
     p.dense = nullptr;
     p.errflag = a.counters + 1;
-    return launch_tc(a.R16, a.A16, a.mh, a.B, a.n, p, s);
+    if (fp8) {
+        p.sa = a.sa;
+        p.sr = a.sr;
+        return launch_tc<true>(a.R8, a.A8, a.mq, a.B, a.n, p, s);
+    }
+    return launch_tc<false>(a.R16, a.A16, a.mh, a.B, a.n, p, s);
 }
 
 cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n,
@@ -337,7 +370,24 @@ cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* 
     p.dense = C;
     p.ldd = ldc;
     p.errflag = errflag;
-    return launch_tc(R16, A16, mh, B, n, p, s);
+    return launch_tc<false>(R16, A16, mh, B, n, p, s);
+}
+
+cudaError_t launch_corr_tc8_dense(const uint8_t* R8, const uint8_t* A8, const float* sr, const float* sa, int mq,
+                                  int B, int n, float* C, int ldc, unsigned* errflag, cudaStream_t s) {
+    TcArgs p{};
+    p.B = B;
+    p.n = n;
+    p.kc = mq / KCH8;
+    p.nch = 1;
+    p.topc = 1;
+    p.nw = 1;
+    p.dense = C;
+    p.ldd = ldc;
+    p.errflag = errflag;
+    p.sa = sa;
+    p.sr = sr;
+    return launch_tc<true>(R8, A8, mq, B, n, p, s);
 }
 
 }  // namespace cs

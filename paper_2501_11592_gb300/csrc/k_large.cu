@@ -23,8 +23,8 @@
 //                 with both products split over the grid into partial sums
 //                 that are added in a fixed order;
 //   residual      r = y - A_S x (x as float32), partial sums over chunks of
-//                 128 support atoms added in chunk order, ||r||, the stopping
-//                 rule of Eq. 2.
+//                 32 support atoms added in chunk order, ||r|| from per-CTA
+//                 sums added in CTA order, the stopping rule of Eq. 2.
 // Every reduction has a fixed order, so a solve is deterministic.
 //
 // Certificate.  With bf16 A (unit roundoff 2^-8) and float32 accumulation
@@ -45,8 +45,9 @@ namespace {
 constexpr int LG_CORR_THREADS = 256;   // correlation CTA: 8 warps x 8 atoms
 constexpr int LG_ATOMS_PER_WARP = 8;
 constexpr int LG_SEG = 2048;           // rows per partial Gram dot product
-constexpr int LG_LC = 256;             // inner-index chunk of the float64 products
-constexpr int LG_RQ = 128;             // support atoms per residual partial sum
+constexpr int LG_LC = 64;              // inner-index chunk of the float64 products
+constexpr int LG_RQ = 32;              // support atoms per residual partial sum
+constexpr int LG_RROWS = 1024;         // rows per CTA of the residual reduction
 constexpr int LG_RESCORE_CTAS = 64;    // CTAs per signal re-scoring candidates
 constexpr int LG_SMEM_R = 160 * 1024;  // shared memory for the residuals of one pass
 
@@ -83,6 +84,8 @@ struct LgState {
     double* upart;                  // [Bl][lch][K]
     double* scal;                   // [Bl][2] 1/L_tt, z_t
     float* rpart;                   // [Bl][rch][mp]
+    float* nrm;                     // [Bl][rblk] sums of r_i^2 per residual CTA
+    int rblk;                       // ceil(m / LG_RROWS)
     float* rnorm;                   // [Bl]
     int* nit;                       // [Bl]
     int* st;                        // [Bl] status (-1 running)
@@ -193,28 +196,39 @@ __global__ void __launch_bounds__(LG_CORR_THREADS) k_lg_corr(LgState S) {
     for (int a = 0; a < LG_ATOMS_PER_WARP; ++a)
 #pragma unroll
         for (int s = 0; s < NB; ++s) acc[a][s] = 0.f;
-    for (int i0 = 0; i0 < S.mp; i0 += 256) {
+    // bf16: U chunks' loads are issued before their multiply-adds (the sums
+    // keep ascending row order per lane)
+    constexpr int U = BF16 ? (NB <= 2 ? 2 : 1) : 1;
+    for (int i0 = 0; i0 < S.mp; i0 += 256 * U) {
         if (BF16) {
-            const int i = i0 + 8 * lane;
-            if (i < S.mp) {
-                uint4 av[LG_ATOMS_PER_WARP];
+            uint4 av[U][LG_ATOMS_PER_WARP];
+#pragma unroll
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + 256 * u + 8 * lane;
 #pragma unroll
                 for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
                     const int j = min(j0 + a, S.n - 1);
-                    av[a] = *reinterpret_cast<const uint4*>(S.A16 + (size_t)j * S.mp + i);
+                    av[u][a] = i < S.mp ? *reinterpret_cast<const uint4*>(S.A16 + (size_t)j * S.mp + i)
+                                        : make_uint4(0u, 0u, 0u, 0u);
                 }
+            }
 #pragma unroll
-                for (int s = 0; s < NB; ++s) {
-                    const float4 r0 = *reinterpret_cast<const float4*>(rs + s * S.mp + i);
-                    const float4 r1 = *reinterpret_cast<const float4*>(rs + s * S.mp + i + 4);
-                    const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            for (int u = 0; u < U; ++u) {
+                const int i = i0 + 256 * u + 8 * lane;
+                if (i < S.mp) {
 #pragma unroll
-                    for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
-                        const unsigned w[4] = {av[a].x, av[a].y, av[a].z, av[a].w};
+                    for (int s = 0; s < NB; ++s) {
+                        const float4 r0 = *reinterpret_cast<const float4*>(rs + s * S.mp + i);
+                        const float4 r1 = *reinterpret_cast<const float4*>(rs + s * S.mp + i + 4);
+                        const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
-                        for (int q = 0; q < 4; ++q) {
-                            acc[a][s] = fmaf(__uint_as_float(w[q] << 16), rv[2 * q], acc[a][s]);
-                            acc[a][s] = fmaf(__uint_as_float(w[q] & 0xffff0000u), rv[2 * q + 1], acc[a][s]);
+                        for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
+                            const unsigned w[4] = {av[u][a].x, av[u][a].y, av[u][a].z, av[u][a].w};
+#pragma unroll
+                            for (int q = 0; q < 4; ++q) {
+                                acc[a][s] = fmaf(__uint_as_float(w[q] << 16), rv[2 * q], acc[a][s]);
+                                acc[a][s] = fmaf(__uint_as_float(w[q] & 0xffff0000u), rv[2 * q + 1], acc[a][s]);
+                            }
                         }
                     }
                 }
@@ -325,7 +339,17 @@ __global__ void __launch_bounds__(256) k_lg_gram(LgState S, int t) {
                                  : (i == t ? aj : S.y + (size_t)b * S.mp);
     const int r0 = seg * LG_SEG, r1 = min(S.m, r0 + LG_SEG);
     float acc = 0.f;
-    for (int q = r0 + lane; q < r1; q += 32) acc = fmaf(other[q], aj[q], acc);
+    for (int q0 = r0; q0 < r1; q0 += 256) {     // eight rows per lane in flight, ascending
+        float o[8], v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int q = q0 + lane + 32 * u;
+            o[u] = q < r1 ? other[q] : 0.f;
+            v[u] = q < r1 ? aj[q] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fmaf(o[u], v[u], acc);
+    }
     acc = warp_sum(acc);
     if (lane == 0) S.gpart[((size_t)b * S.nseg + seg) * (S.K + 2) + i] = acc;
 }
@@ -381,7 +405,15 @@ __global__ void __launch_bounds__(1024) k_lg_pivot(LgState S, int t) {
     double ssq = 0.0, lz = 0.0;
     for (int p = threadIdx.x; p < t; p += blockDim.x) {
         double lp = 0.0;
-        for (int ic = 0; ic < ich; ++ic) lp += S.lpart[((size_t)b * S.lch + ic) * S.K + p];
+        for (int ic0 = 0; ic0 < ich; ic0 += 8) {     // eight chunks' loads in flight, added in order
+            double v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = ic0 + u < ich ? S.lpart[((size_t)b * S.lch + ic0 + u) * S.K + p] : 0.0;
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                if (ic0 + u < ich) lp += v[u];
+        }
         S.l[(size_t)b * S.K + p] = lp;
         ssq = fma(lp, lp, ssq);
         lz = fma(lp, S.z[(size_t)b * S.K + p], lz);
@@ -447,10 +479,16 @@ __global__ void __launch_bounds__(256) k_lg_update(LgState S, int t) {
     double xi;
     if (i < t) {
         const int pch = (t + LG_LC - 1) / LG_LC;
+        // entry i has terms only in the chunks at or after its own
+        const int pc0 = i / LG_LC;
         double u = 0.0;
-        for (int pc = 0; pc < pch; ++pc) {
-            // entry i has terms only in the chunks at or after its own
-            if ((pc + 1) * LG_LC > i) u += S.upart[((size_t)b * S.lch + pc) * S.K + i];
+        for (int pb = pc0; pb < pch; pb += 8) {     // eight chunks' loads in flight, added in order
+            double v[8];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) v[q] = pb + q < pch ? S.upart[((size_t)b * S.lch + pb + q) * S.K + i] : 0.0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                if (pb + q < pch) u += v[q];
         }
         const double w = -u * rinv;
         Wr[(size_t)i * S.K + t] = w;
@@ -487,35 +525,46 @@ __global__ void __launch_bounds__(256) k_lg_rpart(LgState S, int t1) {
     float acc = 0.f;
     int q = 0;
     const int nq = q1 - q0;
-    for (; q + 4 <= nq; q += 4) {
-        float v[4];
+    for (; q + 8 <= nq; q += 8) {
+        float v[8];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) v[u] = S.A[(size_t)sj[q + u] * S.lda + i];
+        for (int u = 0; u < 8; ++u) v[u] = S.A[(size_t)sj[q + u] * S.lda + i];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) acc = fmaf(v[u], sx[q + u], acc);
+        for (int u = 0; u < 8; ++u) acc = fmaf(v[u], sx[q + u], acc);
     }
     for (; q < nq; ++q) acc = fmaf(S.A[(size_t)sj[q] * S.lda + i], sx[q], acc);
     S.rpart[((size_t)b * S.rch + qc) * S.mp + i] = acc;
 }
 
-// r = y - (partial sums in chunk order), ||r||, the stopping rule, and the
-// reset of the selection state for the next iteration (one CTA per signal).
-__global__ void __launch_bounds__(1024) k_lg_resid(LgState S) {
+// r = y - (partial sums in chunk order) for 1024 rows per CTA, and the CTA's
+// sum of r_i^2.
+__global__ void __launch_bounds__(LG_RROWS) k_lg_resid(LgState S) {
     __shared__ float sh[33];
-    const int b = blockIdx.x;
+    const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int t1 = S.nit[b];
     const int qch = (t1 + LG_RQ - 1) / LG_RQ;
-    float ss = 0.f;
-    for (int i = threadIdx.x; i < S.m; i += blockDim.x) {
+    const int i = blockIdx.x * LG_RROWS + threadIdx.x;
+    float ri = 0.f;
+    if (i < S.m) {
         float acc = 0.f;
         for (int qc = 0; qc < qch; ++qc) acc += S.rpart[((size_t)b * S.rch + qc) * S.mp + i];
-        const float ri = S.y[(size_t)b * S.mp + i] - acc;
+        ri = S.y[(size_t)b * S.mp + i] - acc;
         S.r[(size_t)b * S.mp + i] = ri;
-        ss = fmaf(ri, ri, ss);
     }
-    ss = block_sum(ss, sh);
+    const float ss = block_sum(ri * ri, sh);
+    if (threadIdx.x == 0) S.nrm[(size_t)b * S.rblk + blockIdx.x] = ss;
+}
+
+// ||r|| from the CTAs' sums (block order), the stopping rule, and the reset
+// of the selection state for the next iteration (one warp per signal).
+__global__ void k_lg_stop(LgState S) {
+    const int b = blockIdx.x;
+    if (S.st[b] >= 0) return;
+    const int t1 = S.nit[b];
     if (threadIdx.x == 0) {
+        float ss = 0.f;
+        for (int q = 0; q < S.rblk; ++q) ss += S.nrm[(size_t)b * S.rblk + q];
         const float rho = sqrtf(ss);
         S.rnorm[b] = rho;
         S.ncand[b] = 0;
@@ -553,7 +602,7 @@ __global__ void k_lg_out(LgState S) {
 
 struct LgLayout {
     size_t A16, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
-        xf, lpart, l, upart, scal, rpart, rnorm, nit, st, live, total;
+        xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, total;
 };
 
 LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16) {
@@ -594,6 +643,7 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16) {
     L.upart = take(sizeof(double) * B * lch * K);
     L.scal = take(sizeof(double) * B * 2);
     L.rpart = take(sizeof(float) * B * rch * mp);
+    L.nrm = take(sizeof(float) * B * (size_t)ceil_div(m, LG_RROWS));
     L.rnorm = take(sizeof(float) * B);
     L.nit = take(sizeof(int) * B);
     L.st = take(sizeof(int) * B);
@@ -679,6 +729,8 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     S.upart = reinterpret_cast<double*>(w + L.upart);
     S.scal = reinterpret_cast<double*>(w + L.scal);
     S.rpart = reinterpret_cast<float*>(w + L.rpart);
+    S.nrm = reinterpret_cast<float*>(w + L.nrm);
+    S.rblk = ceil_div(call.m, LG_RROWS);
     S.rnorm = reinterpret_cast<float*>(w + L.rnorm);
     S.nit = reinterpret_cast<int*>(w + L.nit);
     S.st = reinterpret_cast<int*>(w + L.st);
@@ -732,7 +784,8 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         mark(CS_PHASE_FIT, 1);
         mark(CS_PHASE_RESID, 0);
         k_lg_rpart<<<dim3(ceil_div(S.m, 256), ceil_div(t + 1, LG_RQ), Bl), 256, 0, s>>>(S, t + 1);
-        k_lg_resid<<<Bl, 1024, 0, s>>>(S);
+        k_lg_resid<<<dim3(S.rblk, Bl), LG_RROWS, 0, s>>>(S);
+        k_lg_stop<<<Bl, 32, 0, s>>>(S);
         mark(CS_PHASE_RESID, 1);
         LG_TRY(cudaGetLastError());
         // every 64 iterations: stop once no signal is running

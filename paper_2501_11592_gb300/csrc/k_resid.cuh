@@ -95,6 +95,39 @@ __device__ __forceinline__ void resid_one(const IterArgs& a, const int b) {
             }
         }
     }
+    if (a.R8) {
+        // FP8 copy for the FP8 tensor-core correlation: per-signal scale and
+        // quantisation-error norm; entries past mp keep the set-up's zeros
+        float amax = 0.f;
+#pragma unroll
+        for (int c = 0; c < MCH; ++c)
+            if ((c * 32 + lane) * 4 < a.mp)
+                amax = fmaxf(fmaxf(fabsf(r[c].x), fabsf(r[c].y)), fmaxf(fmaxf(fabsf(r[c].z), fabsf(r[c].w)), amax));
+        const float sc = fp8_scale(warp_max(amax));
+        float e2 = 0.f;
+        uint8_t* R8 = a.R8 + (size_t)b * a.mq;
+#pragma unroll
+        for (int c = 0; c < MCH; ++c) {
+            const int i = (c * 32 + lane) * 4;
+            if (i < a.mp) {
+                const float v[4] = {r[c].x, r[c].y, r[c].z, r[c].w};
+                uint32_t packed = 0;
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const uint32_t q = fp8_e4m3(v[u] / sc);
+                    const float d = v[u] - sc * fp8_e4m3_value(q);
+                    e2 = fmaf(d, d, e2);
+                    packed |= q << (8 * u);
+                }
+                *reinterpret_cast<uint32_t*>(R8 + i) = packed;
+            }
+        }
+        e2 = warp_sum(e2);
+        if (lane == 0) {
+            a.sr[b] = sc;
+            a.er[b] = sqrtf(e2);
+        }
+    }
     ss = warp_sum(ss);
     if (lane == 0) stop_test(a, b, t, sqrtf(ss));
 }

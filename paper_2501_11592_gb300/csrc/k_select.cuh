@@ -156,14 +156,24 @@ __device__ __forceinline__ void select_one(const IterArgs& a, const int b) {
         // Certificate.  For every atom |c_bf16 - c| <= delta (bf16 rounding
         // of both operands, 2u + u^2 with u = 2^-8; a generous m 2^-22 for the
         // tensor-core fp32 accumulation; m 2^-23 for the fp32 re-score; times
-        // ||a||_max ||r||).  An atom that was not re-scored can only beat the
+        // ||a||_max ||r||; FP8: see below).  An atom that was not re-scored can only beat the
         // float32 winner if its bf16 |c| exceeds bv - delta: such "suspects"
         // are candidates ranked 9th or lower above that threshold, and the
         // other atoms of any group whose third value (cand_bound) is above
         // it.  Suspects are re-scored in float32; usually there are none.
         const float rn = a.res_norm[b];
-        const float delta = (0x1p-7f + 0x1p-16f + (float)a.m * (0x1p-22f + 0x1p-23f)) *
-                            (*a.colnorm_max) * rn * 1.01f;
+        float delta;
+        if (a.prec == CS_CORR_FP8) {
+            // FP8: with the quantisation-error norms of the operands,
+            // |c8 - c| <= ||a - sa A8|| ||sr R8|| + ||a|| ||r - sr R8||
+            //            + m (2^-22 + 2^-23) ||sa A8|| ||sr R8||
+            // (accumulation, the two scalings, the fp32 re-score), where
+            // ||sa A8|| <= max||a|| + ea_max and ||sr R8|| <= ||r|| + er.
+            const float ea = *a.ea_max, er = a.er[b], cm = *a.colnorm_max;
+            delta = (ea * (rn + er) + cm * er + (float)a.m * (0x1p-22f + 0x1p-23f) * (cm + ea) * (rn + er)) * 1.01f;
+        } else {
+            delta = (0x1p-7f + 0x1p-16f + (float)a.m * (0x1p-22f + 0x1p-23f)) * (*a.colnorm_max) * rn * 1.01f;
+        }
         const float theta = bv - delta;
         bool any_suspect = false;
         for (int q = 0, e0 = 0; e0 < ncand; ++q, e0 += 32) {

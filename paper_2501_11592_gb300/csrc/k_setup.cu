@@ -116,6 +116,34 @@ __global__ void k_prep_R(const float* __restrict__ R, int ldr, int m, int B, int
         for (int i = lane; i < mh; i += 32) R16[(size_t)b * mh + i] = __float2bfloat16_rn(i < m ? r[i] : 0.f);
 }
 
+// FP8 copies: one warp per column of A (scale, error norm folded into the
+// largest) or per residual (scale and error norm per signal).
+__global__ void k_prep_A8(const float* __restrict__ A, int lda, int m, int n, int mq, uint8_t* __restrict__ A8,
+                          float* __restrict__ sa, float* ea_max) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    float err;
+    const float sc = quant_row_fp8(A + (size_t)j * lda, m, mq, A8 + (size_t)j * mq, &err);
+    if (lane == 0) {
+        sa[j] = sc;
+        atomicMax(reinterpret_cast<unsigned*>(ea_max), __float_as_uint(err));
+    }
+}
+
+__global__ void k_prep_R8(const float* __restrict__ R, int ldr, int m, int B, int mq, uint8_t* __restrict__ R8,
+                          float* __restrict__ sr, float* __restrict__ er) {
+    const int lane = threadIdx.x & 31;
+    const int b = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= B) return;
+    float err;
+    const float sc = quant_row_fp8(R + (size_t)b * ldr, m, mq, R8 + (size_t)b * mq, &err);
+    if (lane == 0) {
+        sr[b] = sc;
+        er[b] = err;
+    }
+}
+
 // Uneven batches: gather instance measurements into a batch (column b of Y
 // from the pointer ys[b]) and scatter the batch outputs back to the
 // instances' own arrays.  One warp per instance.
@@ -183,6 +211,14 @@ __global__ void k_setup(IterArgs a, const float* __restrict__ Y, int ldy, int cl
     if (a.R16)
         for (int i = lane; i < a.mh; i += 32)
             a.R16[(size_t)b * a.mh + i] = __float2bfloat16_rn(i < a.m ? y[i] : 0.f);
+    if (a.R8) {
+        float err;
+        const float sc = quant_row_fp8(y, a.m, a.mq, a.R8 + (size_t)b * a.mq, &err);
+        if (lane == 0) {
+            a.sr[b] = sc;
+            a.er[b] = err;
+        }
+    }
     for (int w = lane; w < a.nw; w += 32) a.mask[(size_t)b * a.nw + w] = 0u;
     for (int q = lane; q < a.k; q += 32) {
         a.support[(size_t)b * a.k + q] = -1;
@@ -232,6 +268,18 @@ cudaError_t launch_prep_A(const float* A, int lda, int m, int n, int mp, int mh,
         if (e != cudaSuccess) return e;
     }
     k_prep_A<<<ceil_div(n, 8), 256, 0, s>>>(A, lda, m, n, mp, mh, A32, A16, colnorm_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_A8(const float* A, int lda, int m, int n, int mq, uint8_t* A8, float* sa, float* ea_max,
+                           cudaStream_t s) {
+    k_prep_A8<<<ceil_div(n, 8), 256, 0, s>>>(A, lda, m, n, mq, A8, sa, ea_max);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_prep_R8(const float* R, int ldr, int m, int B, int mq, uint8_t* R8, float* sr, float* er,
+                           cudaStream_t s) {
+    k_prep_R8<<<ceil_div(B, 8), 256, 0, s>>>(R, ldr, m, B, mq, R8, sr, er);
     return cudaGetLastError();
 }
 

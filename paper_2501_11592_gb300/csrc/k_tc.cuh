@@ -99,6 +99,26 @@ constexpr uint32_t make_idesc(int M, int N) {
            | ((uint32_t)(M >> 4) << 24);     // M / 16
 }
 
+// Instruction descriptor, kind::f8f6f4: E4M3 A and B (format 0), fp32 D,
+// both K-major.
+constexpr uint32_t make_idesc_e4m3(int M, int N) {
+    return (1u << 4)                         // D format: f32
+           | ((uint32_t)(N >> 3) << 17)      // N / 8
+           | ((uint32_t)(M >> 4) << 24);     // M / 16
+}
+
+// One MMA of 8-bit operands (K = 32 per instruction, the same 32 bytes of a
+// swizzled row as K = 16 of bf16).
+__device__ __forceinline__ void umma_e4m3(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                          uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}\n"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
                                           uint32_t accumulate) {
     asm volatile(
