@@ -418,7 +418,19 @@ cs_status cs_plan_set_profiling(cs_plan* plan, int32_t enable);
  * |A^T r| (certified from the bf16 correlation) and runs the same float32
  * fit and residual arithmetic. */
 enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1, CS_OPT_PERSIST = 2, CS_OPT_STALL_TEST = 3,
-       CS_OPT_FUSED_OMP = 4 };
+       CS_OPT_FUSED_OMP = 4, CS_OPT_AUTOTUNE = 5, CS_OPT_TC_TILE = 6 };
+/* CS_OPT_AUTOTUNE (on by default): the first solve of each size class
+ * (kernel, correlation precision, m, n, batch) times the candidate
+ * configurations of its tunable kernels on its own data -- the tensor-core
+ * correlation's tile width (128 or 256 atoms per CTA) and the large-instance
+ * correlation's signals per pass and loads in flight -- and keeps the fastest
+ * in the plan for later solves.  Every configuration computes the same bits,
+ * so tuning changes only timing; the tuning solve synchronises its stream
+ * while it measures, and no tuning happens inside stream capture (the
+ * defaults run there until a class is tuned).  cs_plan_autotune_report lists
+ * the choices.
+ * CS_OPT_TC_TILE: 128 or 256 forces the tensor-core correlation's tile
+ * width; 0 (default) leaves it to the autotuner (256 untuned). */
 /* CS_OPT_STALL_TEST (test hook for the failure path, value 1): the next
  * persistent CLOMP solve on this plan runs without graphs and withholds the
  * completion signal of the last atom tile of its first correlation pass, so
@@ -428,6 +440,13 @@ enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1, CS_OPT_PERSIST = 2, CS_OPT_STA
  * unspecified; the context and the plan stay usable.  The option clears
  * itself after that solve. */
 cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value);
+
+/* The autotuner's choices so far, one line per size class ("<kernel>
+ * prec=.. m=.. n=.. B=.. -> <configuration index>"), NUL-terminated in buf
+ * (len bytes).  Configuration indices: tensor-core tile 0 = 256 atoms,
+ * 1 = 128; large-instance correlation 2 x (log2 signals per pass) + (loads
+ * in flight - 1).  CS_EINVAL when buf is too short (then truncated). */
+cs_status cs_plan_autotune_report(cs_plan* plan, char* buf, int32_t len);
 
 /* Kernel launches per phase since the last reset (always counted), and --
  * when profiling was enabled -- the summed event time per phase in

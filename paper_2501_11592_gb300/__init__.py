@@ -33,7 +33,7 @@ SIG_REACHED_K, SIG_REACHED_TOL, SIG_MAX_ITER, SIG_DEPENDENT, SIG_NONFINITE, SIG_
 PREC = {"fp32": 0, "bf16": 1, "fp8": 2}
 FORM = {"gather": 0, "gram": 1}
 PHASES = ("setup", "correlation", "select", "fit", "residual", "update", "persist")
-OPT_GRAPHS, OPT_FUSE_UPDATE, OPT_PERSIST, OPT_STALL_TEST, OPT_FUSED_OMP = 0, 1, 2, 3, 4
+OPT_GRAPHS, OPT_FUSE_UPDATE, OPT_PERSIST, OPT_STALL_TEST, OPT_FUSED_OMP, OPT_AUTOTUNE, OPT_TC_TILE = 0, 1, 2, 3, 4, 5, 6
 _STATUS_NAMES = {CS_EINVAL: "CS_EINVAL", CS_ENOMEM: "CS_ENOMEM", CS_ECUDA: "CS_ECUDA",
                  CS_ETIMEOUT: "CS_ETIMEOUT", CS_ENOTSUP: "CS_ENOTSUP"}
 
@@ -106,6 +106,8 @@ def load():
         L.cs_plan_set_profiling.argtypes = [vp, i32]
         L.cs_plan_profile.argtypes = [vp, vp, vp, i32]
         L.cs_plan_set_option.argtypes = [vp, i32, i32]
+        L.cs_plan_autotune_report.argtypes = [vp, ctypes.c_char_p, i32]
+        L.cs_plan_autotune_report.restype = ctypes.c_int
         L.omp_solve_varlen.argtypes = [vp, ctypes.POINTER(Instance), i32, ctypes.POINTER(OmpParams), vp]
         L.clomp_solve_varlen.argtypes = [vp, ctypes.POINTER(Instance), i32, ctypes.POINTER(ClompParams), vp]
         for fn in ("omp_solve_varlen", "clomp_solve_varlen", "cs_plan_set_option", "cs_correlate", "cs_plan_counters", "cs_plan_set_profiling", "cs_plan_profile",
@@ -183,6 +185,16 @@ class Plan:
         generation whenever A's contents change: a row-major A is copied to a
         temporary column-major buffer whose address can repeat."""
         _check(load().cs_plan_set_A_generation(self.h, int(generation)))
+
+    def autotune_report(self):
+        """{size class: chosen configuration index} of the autotuner."""
+        buf = ctypes.create_string_buffer(1 << 16)
+        _check(load().cs_plan_autotune_report(self.h, buf, len(buf)))
+        out = {}
+        for line in buf.value.decode().splitlines():
+            k, _, v = line.rpartition(" -> ")
+            out[k] = int(v)
+        return out
 
     def set_profiling(self, enable=True):
         _check(load().cs_plan_set_profiling(self.h, int(bool(enable))))

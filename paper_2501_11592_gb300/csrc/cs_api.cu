@@ -121,6 +121,9 @@ struct cs_plan {
     int persist = 1;           // CLOMP Gram form, bf16: one persistent kernel per solve
     int stall_test = 0;        // test hook: the next persistent solve lets a bounded wait run out
     int fused_omp = 1;         // plain OMP (fp32), at most one signal per SM: one kernel per solve
+    int autotune = 1;          // time candidate tile shapes on the first solve of a size class
+    int force_tile = 0;        // 128 / 256: tensor-core correlation tile width (0: tuned or 256)
+    std::map<std::string, int> tuned;   // size class -> chosen configuration
     // A's preparation (fp32 / bf16 copies, largest column norm, A^T A) kept
     // for later solves with the same A and generation (generation 0: never)
     uint64_t a_gen = 0;
@@ -349,6 +352,13 @@ cs_status ensure_lg(cs_plan* P, size_t bytes) {
 
 cudaEvent_t pool_event(cs_plan* P);
 
+// Key of an autotuned size class.
+std::string size_key(const char* kind, int prec, int m, int n, int B) {
+    char buf[96];
+    snprintf(buf, sizeof(buf), "%s prec=%d m=%d n=%d B=%d", kind, prec, m, n, B);
+    return buf;
+}
+
 // Measurement hook of the large-instance path: every group of launches of
 // one phase is counted and, when profiling, bracketed by CUDA events.
 struct LargeMarkCtx {
@@ -419,11 +429,20 @@ cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const s
         LargeMarkCtx mc{P, s};
         call.mark = large_mark;
         call.mark_ctx = &mc;
+        // the correlation's configuration for this size class (tuned once)
+        const std::string key = size_key("large correlation", op->prec, m, n, (int)nb);
+        auto tk = P->tuned.find(key);
+        int chosen = -1;
+        call.corr_cfg = tk != P->tuned.end() ? tk->second : -1;
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        call.tune = P->autotune && cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
+        call.chosen_cfg = &chosen;
         const size_t need = large_ws_bytes(m, n, (int)nb, kmax, bf16);
         cs_status st = ensure_lg(P, need);
         if (st != CS_OK) return st;
         cudaError_t e = large_solve(call, P->lg, P->lg_bytes, s);
         if (e != cudaSuccess) return cuda_fail(e, "large OMP solve");
+        if (call.tune && tk == P->tuned.end() && chosen >= 0) P->tuned[key] = chosen;
     }
     return CS_OK;
 }
@@ -446,6 +465,7 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
         a.nch = ceil_div(n, kCorrFp32TileN);
         a.topc = 1;
     } else {
+        a.tc_tile = kCorrTcTileN;
         a.nch = ceil_div(n, kCorrTcTileN);
         a.topc = kTcCandPerTile;
     }
@@ -518,6 +538,47 @@ cudaError_t timed(cs_plan* P, int phase, cudaStream_t s, F&& launch) {
         P->marks.push_back({phase, a, b});
     }
     return e;
+}
+
+// Autotuner: on the first solve of a size class (outside stream capture),
+// launch each of `ncand` configurations of one kernel on the solve's own data
+// (once to warm up, then three times between CUDA events), keep the fastest
+// in the plan and return it; later solves of the class reuse the choice.
+// The tuned kernels are idempotent -- a repeated launch rewrites the same
+// outputs -- and every configuration computes the same bits, so tuning
+// changes timing only.  Returns `fallback` when tuning is off or the stream
+// is being captured.
+template <class L>
+int autotune(cs_plan* P, const std::string& key, int ncand, L&& launch, cudaStream_t s, int fallback) {
+    auto it = P->tuned.find(key);
+    if (it != P->tuned.end()) return it->second;
+    if (!P->autotune || ncand <= 1) return fallback;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return fallback;
+    cudaEvent_t e0 = pool_event(P), e1 = pool_event(P);
+    if (!e0 || !e1) return fallback;
+    int best = -1;
+    float best_ms = 0.f;
+    for (int c = 0; c < ncand; ++c) {
+        if (launch(c) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaEventRecord(e0, s);
+        for (int r = 0; r < 3; ++r) launch(c);
+        cudaEventRecord(e1, s);
+        float ms = 0.f;
+        if (cudaEventSynchronize(e1) != cudaSuccess || cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) continue;
+        if (best < 0 || ms < best_ms) {
+            best_ms = ms;
+            best = c;
+        }
+    }
+    if (best < 0) best = fallback;
+    P->pool.push_back(e0);
+    P->pool.push_back(e1);
+    P->tuned[key] = best;
+    return best;
 }
 
 template <class E, class K>
@@ -710,6 +771,27 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         if (omp_fused) {
             CS_TRY_LAUNCH(timed(P, CS_PHASE_PERSIST, st, [&] { return launch_omp_fused(a, st); }), "fused OMP");
             return CS_OK;
+        }
+        if (lowp) {
+            // tensor-core tile width: forced, tuned for this size class, or 256
+            static const int widths[2] = {256, 128};
+            int tile = 256;
+            if (P->force_tile == 128 || P->force_tile == 256) {
+                tile = P->force_tile;
+            } else {
+                const int ci = autotune(P, size_key("tc-correlation tile", op->prec, m, n, B), 2,
+                                        [&](int cand) {
+                                            IterArgs t = a;
+                                            t.tc_tile = widths[cand];
+                                            t.nch = ceil_div(n, widths[cand]);
+                                            t.topc = 2 * widths[cand] / kTcGroup;
+                                            return launch_corr_tc(t, st);
+                                        }, st, 0);
+                tile = widths[ci];
+            }
+            a.tc_tile = tile;
+            a.nch = ceil_div(n, tile);
+            a.topc = 2 * tile / kTcGroup;
         }
         for (int it = 0; it < a.iters; ++it) {
             c.tau0 = c.reset ? 0 : it * c.steps;
@@ -1336,6 +1418,11 @@ cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value) {
         case CS_OPT_PERSIST: plan->persist = value ? 1 : 0; return CS_OK;
         case CS_OPT_STALL_TEST: plan->stall_test = value ? 1 : 0; return CS_OK;
         case CS_OPT_FUSED_OMP: plan->fused_omp = value ? 1 : 0; return CS_OK;
+        case CS_OPT_AUTOTUNE: plan->autotune = value ? 1 : 0; return CS_OK;
+        case CS_OPT_TC_TILE:
+            if (value != 0 && value != 128 && value != 256) return fail(CS_EINVAL, "tile width %d", value);
+            plan->force_tile = value;
+            return CS_OK;
         default: return fail(CS_EINVAL, "unknown option %d", option);
     }
 }
@@ -1366,6 +1453,21 @@ cs_status cs_plan_profile(cs_plan* plan, double* ms, int64_t* launches, int32_t 
         for (int i = 0; i < CS_PHASES; ++i) plan->launches[i] = 0;
     }
     return CS_OK;
+}
+
+cs_status cs_plan_autotune_report(cs_plan* plan, char* buf, int32_t len) {
+    if (!plan || !buf || len < 1) return fail(CS_EINVAL, "NULL plan or buffer");
+    std::string out;
+    for (const auto& kv : plan->tuned) {
+        out += kv.first;
+        out += " -> ";
+        out += std::to_string(kv.second);
+        out += "\n";
+    }
+    const size_t nb = std::min(out.size(), (size_t)len - 1);
+    memcpy(buf, out.data(), nb);
+    buf[nb] = '\0';
+    return out.size() < (size_t)len ? CS_OK : fail(CS_EINVAL, "buffer too short (%zu bytes needed)", out.size() + 1);
 }
 
 const char* cs_last_error(void) { return g_last_error.c_str(); }

@@ -95,6 +95,7 @@ struct IterArgs {
     int* n_iter;
     float* res_norm;
     int* status;
+    int tc_tile;     // atoms per CTA of the tensor-core correlation (128 or 256; nch, topc follow)
     int need_gcol;   // OMP: write gcol/dnorm/bt for the Cholesky update
     int need_gram;   // CLOMP Gram form: maintain G and bvec
 };
@@ -150,6 +151,12 @@ struct LargeCall {
     // measurement hook: called around each launch with (ctx, CS_PHASE_*, 0 before / 1 after)
     void (*mark)(void* ctx, int phase, int after);
     void* mark_ctx;
+    // correlation configuration (2 log2(signals per pass) + loads in flight - 1):
+    // corr_cfg >= 0 uses it; otherwise tune != 0 times the candidates on the
+    // first iteration, else the widest that fits; the choice goes to *chosen_cfg
+    int corr_cfg;
+    int tune;
+    int* chosen_cfg;
 };
 bool large_supported(int m, int n, int k);
 size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16);

@@ -7,7 +7,7 @@
 // instead of L.  Adding atom a with Gram column g = A_S^T a, d = ||a||^2 and
 // b_t = a^T y:
 //   l    = L^{-1} g = W^T g            (the new row of L, a matrix-vector product)
-//   L_tt = sqrt(d - l.l)
+//   L_tt = sqrt(d - l.l)               (only 1 / L_tt is formed, see rsqrt_f64)
 //   z_t  = (b_t - l.z) / L_tt          (forward substitution of L z = A_S^T y, one row)
 //   w    = [-W l; 1] / L_tt            (the new column of W = L'^{-T})
 //   x   += z_t w                       (x = W z = (A_S^T A_S)^{-1} A_S^T y)
@@ -21,6 +21,21 @@
 
 namespace cs {
 namespace {
+
+// 1/sqrt(x) in float64 for x > 0 without the float64 square root and
+// division (long sequences on this GPU's narrow float64 unit): the float32
+// estimate rsqrtf refined by two Newton-Raphson steps y <- y (3/2 - x y^2 / 2),
+// each of which doubles the number of correct bits (about 22 -> 44 -> 53).
+// Outside float32's normal range the float64 operations are used instead.
+__device__ __forceinline__ double rsqrt_f64(double x) {
+    const float xf = (float)x;
+    if (!(xf >= 0x1p-125f && xf <= 0x1p125f)) return 1.0 / sqrt(x);
+    double y = (double)rsqrtf(xf);
+    const double hx = 0.5 * x;
+    y = y * fma(-hx * y, y, 1.5);
+    y = y * fma(-hx * y, y, 1.5);
+    return y;
+}
 
 __device__ __forceinline__ double warp_sum_f64(double v) {
 #pragma unroll
@@ -85,9 +100,8 @@ __device__ __forceinline__ bool chol_warp(const int t, const int K, const float 
     lz = warp_sum_f64(lz);
     const double piv = d - ssq;
     if (!(piv > 0x1p-20 * d)) return false;
-    const double ltt = sqrt(piv);
-    const double rinv = 1.0 / ltt;
-    const double zt = (bt - lz) / ltt;
+    const double rinv = rsqrt_f64(piv);    // 1 / L_tt
+    const double zt = (bt - lz) * rinv;
     // u = W l: u_i = sum_{p >= i} W_ip l_p, p ascending
     double u[NP];
 #pragma unroll

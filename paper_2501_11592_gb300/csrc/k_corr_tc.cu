@@ -33,14 +33,14 @@ namespace cs {
 namespace {
 
 constexpr int TM = 128;              // signals per CTA (UMMA M, TMEM lanes)
-constexpr int TN = kCorrTcTileN;     // atoms per CTA (UMMA N, TMEM columns)
 constexpr int KCH = 64;              // bf16 elements per 128-byte swizzled row
 constexpr int KCH8 = 128;            // E4M3 elements per 128-byte swizzled row
-constexpr int R_CHUNK_BYTES = TM * KCH * 2;   // 16 KiB
-constexpr int A_CHUNK_BYTES = TN * KCH * 2;   // 32 KiB
+constexpr int R_CHUNK_BYTES = TM * 128;   // 16 KiB
 constexpr int MAX_KC = 4;            // m <= 256 staged at once
-
-static_assert(TN % 16 == 0 && TN >= 16 && TN <= 256, "UMMA N for M=128");
+// The tile width TN (atoms per CTA: UMMA N, TMEM columns) is a template
+// parameter, 128 or 256, chosen per problem size by the autotuner; the
+// candidates are the same two per 16-atom group either way.
+constexpr int a_chunk_bytes(int TN) { return TN * 128; }
 struct TcArgs {
     int B, n, kc, nch, topc, nw;
     const uint32_t* mask;
@@ -57,12 +57,15 @@ struct TcArgs {
 
 constexpr int NTHREADS = 512;          // 16 warps: four per TMEM lane quadrant
 constexpr int NPART = NTHREADS / 128;  // column parts per quadrant
-constexpr int HALF = TN / NPART;       // columns per epilogue warp (64)
 
-template <bool FP8>
+template <bool FP8, int TN>
 __global__ void __launch_bounds__(NTHREADS, 1)
 k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUtensorMap mapA, TcArgs p) {
+    static_assert(TN == 128 || TN == 256, "UMMA N for M=128");
     constexpr int KEL = FP8 ? KCH8 : KCH;   // elements per chunk row
+    constexpr int HALF = TN / NPART;        // columns per epilogue warp (32 or 64)
+    constexpr int CPT = 2 * TN / kTcGroup;  // candidates per tile
+    constexpr int A_CHUNK_BYTES = a_chunk_bytes(TN);
     extern __shared__ uint8_t smem_raw[];
     __shared__ float sSa[FP8 ? TN : 1];     // FP8: the tile's atom scales
     __shared__ __align__(8) uint64_t full_bar[MAX_KC];
@@ -201,13 +204,13 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
         // of the group.  Branch-free, ~11 instructions per value.  Results go
         // to shared memory first (the operand tiles are free now) and leave
         // the CTA in contiguous 128-byte rows per signal.
-        constexpr int SV = kTcCandPerTile + 1;                  // padded row strides
-        constexpr int SB = kCorrTcTileN / kTcGroup + 1;
+        constexpr int SV = CPT + 1;                             // padded row strides
+        constexpr int SB = TN / kTcGroup + 1;
         float* sVal = reinterpret_cast<float*>(sR);             // [TM][SV]
         int* sIdx = reinterpret_cast<int*>(sVal + TM * SV);     // [TM][SV]
         float* sBnd = reinterpret_cast<float*>(sIdx + TM * SV); // [TM][SB]
         const int sl = quad * 32 + lane;
-        constexpr int PER_HALF = 2 * HALF / kTcGroup;          // 8 candidates per part
+        constexpr int PER_HALF = 2 * HALF / kTcGroup;          // candidates per part
 #pragma unroll
         for (int c = 0; c < HALF / 32; ++c) {
             const uint32_t mw = sMask[sl][half * (HALF / 32) + c];
@@ -240,16 +243,16 @@ k_corr_tc(const __grid_constant__ CUtensorMap mapR, const __grid_constant__ CUte
             }
         }
         __syncthreads();
-        for (int e = tid; e < TM * kTcCandPerTile; e += NTHREADS) {
-            const int r = e / kTcCandPerTile, q = e % kTcCandPerTile;
+        for (int e = tid; e < TM * CPT; e += NTHREADS) {
+            const int r = e / CPT, q = e % CPT;
             const int sg = b0 + r;
             if (sg < p.B) {
-                const size_t o = ((size_t)sg * p.nch + blockIdx.y) * kTcCandPerTile + q;
+                const size_t o = ((size_t)sg * p.nch + blockIdx.y) * CPT + q;
                 p.cand_val[o] = sVal[r * SV + q];
                 p.cand_idx[o] = sIdx[r * SV + q];
             }
         }
-        constexpr int G = kCorrTcTileN / kTcGroup;
+        constexpr int G = TN / kTcGroup;
         for (int e = tid; e < TM * G; e += NTHREADS) {
             const int r = e / G, q = e % G;
             const int sg = b0 + r;
@@ -302,25 +305,32 @@ bool make_map(CUtensorMap* map, const void* base, int row_elems, int rows, size_
     return r == CUDA_SUCCESS;
 }
 
-size_t smem_bytes(int kc) { return (size_t)kc * (R_CHUNK_BYTES + A_CHUNK_BYTES) + 1024; }
+size_t smem_bytes(int kc, int TN) { return (size_t)kc * (R_CHUNK_BYTES + a_chunk_bytes(TN)) + 1024; }
 
 // R and A operand rows of `rowlen` elements (bf16: 2 bytes, fp8: 1 byte).
-template <bool FP8>
+// At most two CTAs share an SM (tensor memory: 2 x 256 columns), or four
+// with TN = 128.
+template <bool FP8, int TN>
 cudaError_t launch_tc(const void* R, const void* A, int rowlen, int B, int n, TcArgs p, cudaStream_t s) {
     CUtensorMap mR, mA;
     const size_t rb = (size_t)rowlen * (FP8 ? 1 : 2);
     if (!make_map(&mR, R, rowlen, B, rb, TM, FP8) || !make_map(&mA, A, rowlen, n, rb, TN, FP8))
         return cudaErrorInvalidValue;
-    const size_t smem = std::max(smem_bytes(p.kc), (size_t)100 * 1024);   // <= 2 CTAs per SM (TMEM)
+    const size_t smem = std::max(smem_bytes(p.kc, TN), (size_t)(TN == 256 ? 100 : 50) * 1024);
     static int configured = 0;
     if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_corr_tc<FP8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes(MAX_KC));
+        cudaError_t e = cudaFuncSetAttribute(k_corr_tc<FP8, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem_bytes(MAX_KC, TN));
         if (e != cudaSuccess) return e;
         configured = 1;
     }
     dim3 grid(ceil_div(B, TM), ceil_div(n, TN));
-    return launch_pdl(k_corr_tc<FP8>, grid, dim3(NTHREADS), smem, s, mR, mA, p);
+    return launch_pdl(k_corr_tc<FP8, TN>, grid, dim3(NTHREADS), smem, s, mR, mA, p);
+}
+
+template <bool FP8>
+cudaError_t launch_tc_w(const void* R, const void* A, int rowlen, int B, int n, TcArgs p, int tn, cudaStream_t s) {
+    return tn == 128 ? launch_tc<FP8, 128>(R, A, rowlen, B, n, p, s) : launch_tc<FP8, 256>(R, A, rowlen, B, n, p, s);
 }
 
 }  // namespace
@@ -350,12 +360,13 @@ cudaError_t launch_corr_tc(const IterArgs& a, cudaStream_t s) {
     p.cand_bound = a.cand_bound;
     p.dense = nullptr;
     p.errflag = a.counters + 1;
+    const int tn = a.tc_tile == 128 ? 128 : 256;
     if (fp8) {
         p.sa = a.sa;
         p.sr = a.sr;
-        return launch_tc<true>(a.R8, a.A8, a.mq, a.B, a.n, p, s);
+        return launch_tc_w<true>(a.R8, a.A8, a.mq, a.B, a.n, p, tn, s);
     }
-    return launch_tc<false>(a.R16, a.A16, a.mh, a.B, a.n, p, s);
+    return launch_tc_w<false>(a.R16, a.A16, a.mh, a.B, a.n, p, tn, s);
 }
 
 cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* A16, int mh, int B, int n,
@@ -370,7 +381,7 @@ cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* 
     p.dense = C;
     p.ldd = ldc;
     p.errflag = errflag;
-    return launch_tc<false>(R16, A16, mh, B, n, p, s);
+    return launch_tc<false, 256>(R16, A16, mh, B, n, p, s);
 }
 
 cudaError_t launch_corr_tc8_dense(const uint8_t* R8, const uint8_t* A8, const float* sr, const float* sa, int mq,
@@ -387,7 +398,7 @@ cudaError_t launch_corr_tc8_dense(const uint8_t* R8, const uint8_t* A8, const fl
     p.errflag = errflag;
     p.sa = sa;
     p.sr = sr;
-    return launch_tc<true>(R8, A8, mq, B, n, p, s);
+    return launch_tc<true, 256>(R8, A8, mq, B, n, p, s);
 }
 
 }  // namespace cs

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(1024) k_lg_setup(LgState S) {
 // and the largest unselected one per signal.  bf16 A: lane l covers rows
 // i0 + 8l .. i0 + 8l + 7 of every 256-row chunk (one 16-byte load per atom);
 // float32 A: rows i0 + l + 32e (eight coalesced loads per atom).
-template <bool BF16, int NB>
+template <bool BF16, int NB, int U>
 __global__ void __launch_bounds__(LG_CORR_THREADS) k_lg_corr(LgState S) {
     extern __shared__ __align__(16) float rs[];   // [NB][mp]
     const int s0 = blockIdx.y * NB;
@@ -197,8 +197,7 @@ __global__ void __launch_bounds__(LG_CORR_THREADS) k_lg_corr(LgState S) {
 #pragma unroll
         for (int s = 0; s < NB; ++s) acc[a][s] = 0.f;
     // bf16: U chunks' loads are issued before their multiply-adds (the sums
-    // keep ascending row order per lane)
-    constexpr int U = BF16 ? (NB <= 2 ? 2 : 1) : 1;
+    // keep ascending row order per lane, whatever U)
     for (int i0 = 0; i0 < S.mp; i0 += 256 * U) {
         if (BF16) {
             uint4 av[U][LG_ATOMS_PER_WARP];
@@ -652,24 +651,49 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16) {
     return L;
 }
 
-template <bool BF16, int NB>
+template <bool BF16, int NB, int U>
 cudaError_t launch_corr_nb(const LgState& S, cudaStream_t s) {
     const size_t smem = sizeof(float) * (size_t)NB * S.mp;
-    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr<BF16, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   LG_SMEM_R);
+    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr<BF16, NB, U>,
+                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, LG_SMEM_R);
     if (attr != cudaSuccess) return attr;
     const dim3 grid(ceil_div(S.n, (LG_CORR_THREADS / 32) * LG_ATOMS_PER_WARP), ceil_div(S.Bl, NB));
-    k_lg_corr<BF16, NB><<<grid, LG_CORR_THREADS, smem, s>>>(S);
+    k_lg_corr<BF16, NB, U><<<grid, LG_CORR_THREADS, smem, s>>>(S);
     return cudaGetLastError();
 }
 
-template <bool BF16>
-cudaError_t launch_corr(const LgState& S, cudaStream_t s) {
-    switch (S.nb) {
-        case 1: return launch_corr_nb<BF16, 1>(S, s);
-        case 2: return launch_corr_nb<BF16, 2>(S, s);
-        default: return launch_corr_nb<BF16, 4>(S, s);
+// Correlation configuration cfg = 2 log2(NB) + (U - 1): NB signals per pass
+// (residuals in shared memory), U 256-row chunks of loads in flight (bf16).
+cudaError_t launch_corr(const LgState& S, int cfg, cudaStream_t s) {
+    const int nbl = cfg >> 1, u2 = cfg & 1;
+    if (S.bf16) {
+        switch (nbl * 2 + u2) {
+            case 0: return launch_corr_nb<true, 1, 1>(S, s);
+            case 1: return launch_corr_nb<true, 1, 2>(S, s);
+            case 2: return launch_corr_nb<true, 2, 1>(S, s);
+            case 3: return launch_corr_nb<true, 2, 2>(S, s);
+            case 4: return launch_corr_nb<true, 4, 1>(S, s);
+            default: return launch_corr_nb<true, 4, 2>(S, s);
+        }
     }
+    switch (nbl) {
+        case 0: return launch_corr_nb<false, 1, 1>(S, s);
+        case 1: return launch_corr_nb<false, 2, 1>(S, s);
+        default: return launch_corr_nb<false, 4, 1>(S, s);
+    }
+}
+
+// The configurations that fit: NB residuals in shared memory, no more
+// signal slots than signals; U only matters for bf16.
+std::vector<int> corr_configs(const LgState& S) {
+    std::vector<int> out;
+    for (int nbl = 0; nbl <= 2; ++nbl) {
+        const int nb = 1 << nbl;
+        if (sizeof(float) * (size_t)nb * S.mp > (size_t)LG_SMEM_R) break;
+        if (nb > 1 && nb / 2 >= S.Bl) break;
+        for (int u2 = 0; u2 < (S.bf16 ? 2 : 1); ++u2) out.push_back(2 * nbl + u2);
+    }
+    return out;
 }
 
 }  // namespace
@@ -699,9 +723,7 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     S.Bl = Bl;
     S.bf16 = call.bf16;
     S.tol = call.tol;
-    S.nb = std::max(1, std::min(4, (int)(LG_SMEM_R / (sizeof(float) * (size_t)S.mp))));
-    if (S.nb == 3) S.nb = 2;
-    while (S.nb > 1 && S.nb / 2 >= Bl) S.nb /= 2;   // no empty signal slots
+    S.nb = 1;   // set from the chosen correlation configuration below
     S.A = call.A;
     S.A16 = call.bf16 ? reinterpret_cast<__nv_bfloat16*>(w + L.A16) : nullptr;
     S.colmax = reinterpret_cast<float*>(w + L.colmax);
@@ -764,11 +786,45 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     k_lg_setup<<<Bl, 1024, 0, s>>>(S);
     LG_TRY(cudaGetLastError());
     mark(CS_PHASE_SETUP, 1);
+    // correlation configuration: given, or tuned here on the first
+    // iteration's data (the kernel is idempotent), or the widest that fits
+    const std::vector<int> cfgs = corr_configs(S);
+    int cfg = call.corr_cfg;
+    if (cfg < 0 || std::find(cfgs.begin(), cfgs.end(), cfg) == cfgs.end()) {
+        cfg = cfgs.back();
+        if (call.tune && cfgs.size() > 1) {
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            LG_TRY(cudaEventCreate(&e0));
+            LG_TRY(cudaEventCreate(&e1));
+            float best_ms = 0.f;
+            int best = -1;
+            for (int cand : cfgs) {
+                LgState T = S;
+                T.nb = 1 << (cand >> 1);
+                LG_TRY(launch_corr(T, cand, s));
+                LG_TRY(cudaEventRecord(e0, s));
+                for (int r = 0; r < 3; ++r) LG_TRY(launch_corr(T, cand, s));
+                LG_TRY(cudaEventRecord(e1, s));
+                float ms = 0.f;
+                LG_TRY(cudaEventSynchronize(e1));
+                LG_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                if (best < 0 || ms < best_ms) {
+                    best_ms = ms;
+                    best = cand;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            cfg = best;
+        }
+    }
+    if (call.chosen_cfg) *call.chosen_cfg = cfg;
+    S.nb = 1 << (cfg >> 1);
     int* live_h = call.live_host;
     for (int it = 0; it < iters; ++it) {
         const int t = it;
         mark(CS_PHASE_CORR, 0);
-        LG_TRY(S.bf16 ? launch_corr<true>(S, s) : launch_corr<false>(S, s));
+        LG_TRY(launch_corr(S, cfg, s));
         mark(CS_PHASE_CORR, 1);
         mark(CS_PHASE_SELECT, 0);
         k_lg_scan<<<dim3(ceil_div(S.n, 256), Bl), 256, 0, s>>>(S);

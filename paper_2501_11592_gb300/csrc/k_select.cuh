@@ -187,7 +187,7 @@ __device__ __forceinline__ void select_one(const IterArgs& a, const int b) {
                 if (cand_better(v, jj, bv, bj)) { bv = v; bj = jj; }
             }
         }
-        const int ngroups = a.nch * (kCorrTcTileN / kTcGroup);
+        const int ngroups = a.nch * (a.topc / 2);     // two candidates per 16-atom group
         const float* cb = a.cand_bound + (size_t)b * ngroups;
         for (int g0 = 0; g0 < ngroups; g0 += 32) {
             const int g = g0 + lane;
