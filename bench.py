@@ -55,7 +55,63 @@ def parse():
     ap.add_argument("--cpu-sample", type=int, default=12288,
                     help="signals the FP64 oracle solves for cpu_baseline (the workload's signals, cycled)")
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--profile-case", default=None,
+                    help="run one small named workload once (for an ncu capture of its kernels) and exit: "
+                         + ", ".join(PROFILE_CASES))
     return ap.parse_args()
+
+
+PROFILE_CASES = ("omp_fp32", "omp_fp8", "clomp_bf16_per_iteration", "clomp_gather", "threshold", "single",
+                 "clfit_pair", "columnwise_image", "large_small", "persist")
+
+
+def profile_case(name):
+    """One solve of a named workload, for ncu: no timing, no oracle."""
+    import torch
+    import paper_2501_11592_gb300 as cs
+    import workloads
+    cs.load()
+    dev = lambda x: torch.from_numpy(np.asfortranarray(x, dtype=np.float32)).cuda()
+    if name in ("omp_fp32", "omp_fp8", "clomp_bf16_per_iteration", "clomp_gather", "threshold", "persist"):
+        p = workloads.config_batched()
+        A, Y = dev(p.A), dev(p.Y)
+        plan = cs.Plan(p.m, p.n, p.B, p.k)
+        if name == "omp_fp32":
+            cs.omp_solve_batched(A, Y, p.k, prec="fp32", plan=plan)
+        elif name == "omp_fp8":
+            cs.omp_solve_batched(A, Y, p.k, prec="fp8", plan=plan)
+        else:
+            plan.set_option(cs.OPT_PERSIST, 1 if name == "persist" else 0)
+            plan.set_option(cs.OPT_FUSE_UPDATE, 0 if name == "clomp_gather" else 1)
+            cs.clomp_solve_batched(A, Y, p.k, prec="fp32" if name == "threshold" else "bf16",
+                                   form="gather" if name == "clomp_gather" else "gram", plan=plan,
+                                   th=0.7 if name == "threshold" else 0.0, **CL)
+    elif name == "single":
+        p = workloads.config_single_fp64()
+        cs.omp_solve_batched(dev(p.A), dev(p.Y), p.k, tol=p.tol, plan=cs.Plan(64, 256, 1, 8))
+    elif name == "clfit_pair":
+        # the gradient sub-configuration of the long 1-D workload: n = 4096, m = 1024, t = 128, 1024 signals
+        rng = np.random.default_rng(11)
+        A = dev(workloads.gaussian_matrix(rng, 1024, 4096))
+        S = torch.from_numpy(np.stack([rng.choice(4096, 128, replace=False) for _ in range(1024)]).astype(np.int32)).cuda()
+        Sv = torch.randn(1024, 128, device="cuda")
+        Y = torch.randn(1024, 1024, device="cuda").t().contiguous().t()
+        R, _ = cs.clfit_forward(A, S, Sv, Y)
+        mom, vel = torch.zeros_like(Sv), torch.zeros_like(Sv)
+        cs.clfit_adam_step(A, S, Sv, R, mom, vel, 1)
+    elif name == "columnwise_image":
+        pc = workloads.config_columnwise_2d(0.3, n_images=8)
+        D = dev(pc.meta["D"])
+        cs.reconstruct_columnwise(dev(pc.A), D, dev(pc.Y), pc.k, 256, ref=dev(pc.meta["X_img"]), algo="clomp",
+                                  prec="bf16", plan=cs.Plan(pc.m, pc.n, pc.B, pc.k), tv_weight=32.0, image_prior=True,
+                                  **CL)
+    elif name == "large_small":
+        pl = workloads.config_large_1d(n=16384, m=4915, k=100)
+        cs.omp_solve_batched(dev(pl.A), dev(pl.Y), pl.k, prec="bf16", plan=cs.Plan(pl.m, pl.n, 1, pl.k))
+    else:
+        raise SystemExit(f"unknown profile case {name}")
+    torch.cuda.synchronize()
+    print(f"profile case {name}: done", flush=True)
 
 
 def dist_env():
@@ -311,6 +367,8 @@ def bench_uneven(cs, torch, stream, barrier):
 
 def main():
     args = parse()
+    if args.profile_case:
+        return profile_case(args.profile_case)
     if args.impl == "reference":
         return run_reference(args)
     ws, rank, local = dist_env()
