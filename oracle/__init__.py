@@ -82,6 +82,10 @@ def lib():
             L.cs_oracle_tv2d_h_loss_grad.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                      ctypes.c_int, pi, pi, pd, d, pd]
             L.cs_oracle_tv2d_h_loss_grad.restype = d
+            L.cs_oracle_iht.argtypes = [pd, ctypes.c_int, ctypes.c_int, ctypes.c_int, pd, ctypes.c_int,
+                                        ctypes.c_int, ctypes.c_int, d, d, ctypes.c_int, pi, pd, pi, pd, pi, pd,
+                                        ctypes.c_int]
+            L.cs_oracle_iht.restype = ctypes.c_int
             L.cs_oracle_max_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -177,6 +181,26 @@ def omp(A, Y, k, tol=0.0, max_iter=None, nthreads=0, method="auto"):
                              _p(o["res_hist"], ctypes.c_double), int(nthreads))
     if rc != 0:
         raise ValueError("cs_oracle_omp: invalid arguments")
+    return o
+
+
+def iht(A, Y, k, step, tol=0.0, max_iter=200, nthreads=0):
+    """IHT for every column of Y: s <- H_k(s + step A^T r), at most max_iter
+    iterations.  Returns support (ascending), coef, n_iter, res_norm, status
+    and margin (the smallest relative gap at the k-th largest |u|)."""
+    A = _f64F(A)
+    Y = _f64F(Y if np.ndim(Y) == 2 else np.reshape(Y, (-1, 1)))
+    m, n = A.shape
+    B = Y.shape[1]
+    o = dict(support=np.zeros((B, k), np.int32), coef=np.zeros((B, k)), n_iter=np.zeros(B, np.int32),
+             res_norm=np.zeros(B), status=np.zeros(B, np.int32), margin=np.zeros(B))
+    rc = lib().cs_oracle_iht(_p(A, ctypes.c_double), m, n, m, _p(Y, ctypes.c_double), m, B, int(k), float(step),
+                             float(tol), int(max_iter), _p(o["support"], ctypes.c_int32),
+                             _p(o["coef"], ctypes.c_double), _p(o["n_iter"], ctypes.c_int32),
+                             _p(o["res_norm"], ctypes.c_double), _p(o["status"], ctypes.c_int32),
+                             _p(o["margin"], ctypes.c_double), int(nthreads))
+    if rc != 0:
+        raise ValueError("cs_oracle_iht: invalid arguments")
     return o
 
 

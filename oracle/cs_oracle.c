@@ -18,6 +18,8 @@
  *     (k in the thousands) grow a QR factorisation by one column per
  *     iteration instead: modified Gram-Schmidt of the new column against the
  *     previous orthonormal columns, applied twice, then back substitution.
+ *   - IHT (Table "s forward block", IHT row), the paper's comparison method:
+ *     s <- H_k(s + t A^T r), keeping the k largest magnitudes.
  *   - CLOMP, structure 1 (Methods "Coefficients learning on OMP"): the same
  *     selection, but s (n learnable parameters) is masked by the OR-accumulated
  *     Mask, y' = A (s .* Mask) is formed, and s is learned by back-propagating
@@ -872,6 +874,97 @@ int cs_oracle_clomp_image(const double* A, int m, int n, int lda, const double* 
         clomp_image(A, m, n, lda, Y + b0 * ldy, ldy, W, k, tol, max_iter, steps, lr, beta1,
                     beta2, eps, reset_adam, tv_w, lv_w, lv_eps, D, N, ldd, support + o, coef + o, n_iter + b0,
                     res_norm + b0, status + b0, top1 + o, top2 + o, res_hist + o);
+    }
+    return 0;
+}
+
+/*
+ * IHT (Methods, Table "s forward block", IHT row): s <- H_k(s + t A^T r)
+ * with r = y - A s, where H_k keeps the k entries of largest magnitude
+ * (lowest index on exact ties) and zeroes the others, and t is the caller's
+ * scale factor.  s starts at zero.  Before the first iteration and after each
+ * one: stop with status 1 once ||r||_2 <= tol, else with status 2 after
+ * max_iter iterations (R).  Outputs: the k kept indices in ascending order
+ * and their values, the iterations run, ||r||_2, the status, and margin =
+ * the smallest relative gap (|u|_(k) - |u|_(k+1)) / |u|_(k) between the k-th
+ * and (k+1)-th largest |u| over the iterations (the float64 resolution of
+ * the kept set; 1 when k = n).
+ */
+static void iht_one(const double* A, int m, int n, int lda, const double* y, int k, double t,
+                    double tol, int max_iter, int32_t* support, double* coef, int32_t* n_iter,
+                    double* res_norm, int32_t* status, double* margin) {
+    for (int q = 0; q < k; ++q) { support[q] = -1; coef[q] = 0.0; }
+    *margin = 1.0;
+    if (!all_finite(y, m)) { *n_iter = 0; *res_norm = NAN; *status = ST_NONFINITE; return; }
+    double* s = (double*)calloc(n, sizeof(double));
+    double* u = (double*)malloc(sizeof(double) * n);
+    double* r = (double*)malloc(sizeof(double) * m);
+    int* idx = (int*)malloc(sizeof(int) * n);
+    memcpy(r, y, sizeof(double) * m);
+    double rho = nrm2(r, m);
+    int it = 0, st = -1;
+    if (rho <= tol) st = ST_TOL;
+    while (st < 0 && it < max_iter) {
+        for (int j = 0; j < n; ++j) u[j] = s[j] + t * dot(A + (size_t)j * lda, r, m);
+        /* order the indices by |u| descending, index ascending (insertion sort
+           into the first k + 1 places is enough for H_k and the margin) */
+        int top = k + 1 < n ? k + 1 : n, cnt = 0;
+        for (int j = 0; j < n; ++j) {
+            double a = fabs(u[j]);
+            int pos = cnt;
+            while (pos > 0 && fabs(u[idx[pos - 1]]) < a) --pos;   /* equal: the earlier index stays first */
+            if (pos >= top) continue;
+            int last = cnt < top ? cnt : top - 1;
+            for (int q = last; q > pos; --q) idx[q] = idx[q - 1];
+            idx[pos] = j;
+            if (cnt < top) ++cnt;
+        }
+        if (k < n) {
+            double a1 = fabs(u[idx[k - 1]]), a2 = fabs(u[idx[k]]);
+            double g = a1 > 0.0 ? (a1 - a2) / a1 : 0.0;
+            if (g < *margin) *margin = g;
+        }
+        for (int j = 0; j < n; ++j) s[j] = 0.0;
+        for (int q = 0; q < k; ++q) s[idx[q]] = u[idx[q]];
+        memcpy(r, y, sizeof(double) * m);
+        for (int j = 0; j < n; ++j) {
+            if (s[j] == 0.0) continue;
+            const double* a = A + (size_t)j * lda;
+            for (int i = 0; i < m; ++i) r[i] -= a[i] * s[j];
+        }
+        rho = nrm2(r, m);
+        ++it;
+        if (rho <= tol) st = ST_TOL;
+    }
+    if (st < 0) st = ST_MAXIT;
+    /* the kept set in ascending index order (the last H_k's k indices) */
+    if (it > 0) {
+        int q = 0;
+        for (int j = 0; j < n && q < k; ++j) {
+            int kept = 0;
+            for (int p = 0; p < k; ++p) if (idx[p] == j) { kept = 1; break; }
+            if (kept) { support[q] = j; coef[q] = s[j]; ++q; }
+        }
+    }
+    *n_iter = it;
+    *res_norm = rho;
+    *status = st;
+    free(s); free(u); free(r); free(idx);
+}
+
+int cs_oracle_iht(const double* A, int m, int n, int lda, const double* Y, int ldy, int B, int k,
+                  double t, double tol, int max_iter, int32_t* support, double* coef, int32_t* n_iter,
+                  double* res_norm, int32_t* status, double* margin, int nthreads) {
+    if (m <= 0 || n <= 0 || B < 0 || k <= 0 || k > n || lda < m || ldy < m || !A || (B > 0 && !Y)) return -1;
+    if (max_iter <= 0 || !(t > 0.0)) return -1;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 4)
+#endif
+    for (int b = 0; b < B; ++b) {
+        size_t o = (size_t)b * k;
+        iht_one(A, m, n, lda, Y + (size_t)b * ldy, k, t, tol, max_iter, support + o, coef + o, n_iter + b,
+                res_norm + b, status + b, margin + b);
     }
     return 0;
 }

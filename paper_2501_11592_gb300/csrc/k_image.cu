@@ -84,8 +84,8 @@ __device__ __forceinline__ float block_minmax(float v, float* sh, bool is_max) {
 
 // One block per image (H x W column-major, consecutive images).  Window
 // statistics in float32: the weighted means first, then the centred second
-// moments (no cancellation of E[x^2] - mean^2); per-window indices and the
-// squared errors are summed in float64.
+// moments (no cancellation of E[x^2] - mean^2), and each window's index;
+// the indices and the squared errors are summed in float64.
 __global__ void __launch_bounds__(QT) k_image_quality(const float* __restrict__ X, const float* __restrict__ R,
                                                       int H, int W, float peak,
                                                       float* __restrict__ psnr, float* __restrict__ ssim) {
@@ -143,9 +143,11 @@ __global__ void __launch_bounds__(QT) k_image_quality(const float* __restrict__ 
             vy = fmaf(c_gauss[v], syy, vy);
             cxy = fmaf(c_gauss[v], sxy, cxy);
         }
-        const double num = (2.0 * mx * my + C1) * (2.0 * cxy + C2);
-        const double den = ((double)mx * mx + (double)my * my + C1) * ((double)vx + vy + C2);
-        acc += num / den;
+        // the window's index in float32 (its terms are float32 already),
+        // summed over the windows in float64
+        const float num = fmaf(2.f * mx, my, C1) * fmaf(2.f, cxy, C2);
+        const float den = (fmaf(mx, mx, my * my) + C1) * ((vx + vy) + C2);
+        acc += (double)(num / den);
     }
     acc = block_sum(acc, shd);
     if (threadIdx.x == 0) {

@@ -950,3 +950,89 @@ def test_clomp_image_stopped_column_is_frozen_neighbour():
     o0 = oracle.clomp(A, Y0, k, tol=tol, steps=T, lr=lr, tv_weight=w, D=D, image_width=W)
     assert o0["n_iter"][1] == 0 and o0["support"][2, 0] == 5
     assert abs(o0["coef"][2, 0] - o["coef"][2, 0]) > 1e-3
+
+
+# ---------------------------------------------------------------- IHT pins
+def test_iht_orthonormal_closed_form():
+    """A orthonormal (m = n), t = 1: the first iteration gives
+    s = H_k(A^T y) and every later one returns the same point; ||r||^2 =
+    ||y||^2 - the kept sum of (A^T y)_j^2."""
+    rng = np.random.default_rng(41)
+    n, k = 24, 5
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    Y = rng.standard_normal((n, 3))
+    for it in (1, 4):
+        o = oracle.iht(Q, Y, k, 1.0, max_iter=it)
+        for b in range(3):
+            c = Q.T @ Y[:, b]
+            keep = np.sort(np.argsort(-np.abs(c), kind="stable")[:k])
+            assert o["support"][b].tolist() == keep.tolist()
+            assert np.allclose(o["coef"][b], c[keep], atol=1e-12)
+            assert abs(o["res_norm"][b] ** 2 - (np.sum(Y[:, b] ** 2) - np.sum(c[keep] ** 2))) < 1e-10
+            assert o["n_iter"][b] == it and o["status"][b] == 2
+
+
+def test_iht_ties_keep_the_lowest_indices():
+    y = np.array([1.0, -1.0, 1.0, 0.5, -1.0, 0.2])
+    o = oracle.iht(np.eye(6), y, 3, 1.0, max_iter=1)
+    assert o["support"][0].tolist() == [0, 1, 2]
+    assert o["coef"][0].tolist() == [1.0, -1.0, 1.0]
+    assert o["margin"][0] == 0.0
+
+
+def test_iht_objective_non_increasing_for_small_steps():
+    """With t <= 1 / sigma_max(A)^2 the residual norm of IHT does not grow
+    (Blumensath and Davies, 2008)."""
+    rng = np.random.default_rng(42)
+    A = _rand_A(rng, 40, 120)
+    Y = workloads.add_noise(rng, A @ workloads.sparse_coefficients(rng, 120, 4, 6), 20.0)
+    t = 0.99 / np.linalg.norm(A, 2) ** 2
+    prev = np.full(4, np.inf)
+    for it in range(1, 31):
+        o = oracle.iht(A, Y, 6, t, max_iter=it)
+        assert np.all(o["res_norm"] <= prev * (1 + 1e-12))
+        prev = o["res_norm"]
+
+
+def test_iht_noiseless_recovery():
+    """Noiseless sparse signals that IHT recovers (residual at rounding
+    level) come back with their exact support and coefficients; most of
+    them are recovered."""
+    rng = np.random.default_rng(43)
+    A = _rand_A(rng, 120, 300)
+    X = workloads.sparse_coefficients(rng, 300, 8, 6)
+    Y = A @ X
+    o = oracle.iht(A, Y, 6, 1.0 / np.linalg.norm(A, 2) ** 2, max_iter=3000)
+    ok = o["res_norm"] <= 1e-9 * np.linalg.norm(Y, axis=0)
+    assert ok.sum() >= 6
+    for b in np.nonzero(ok)[0]:
+        assert o["support"][b].tolist() == np.nonzero(X[:, b])[0].tolist()
+        assert np.allclose(o["coef"][b], X[o["support"][b], b], atol=1e-8)
+
+
+def test_iht_keeping_everything_is_landweber():
+    """k = n: H_k keeps every entry and IHT is gradient descent on
+    1/2 ||y - A s||^2, which converges to the least-squares solution of a
+    full-column-rank A (numpy lstsq, library)."""
+    rng = np.random.default_rng(44)
+    A = rng.standard_normal((30, 10))
+    y = rng.standard_normal(30)
+    o = oracle.iht(A, y, 10, 1.0 / np.linalg.norm(A, 2) ** 2, max_iter=4000)
+    assert o["support"][0].tolist() == list(range(10))
+    assert np.allclose(o["coef"][0], np.linalg.lstsq(A, y, rcond=None)[0], atol=1e-9)
+    assert o["margin"][0] == 1.0
+
+
+def test_iht_stop_rules():
+    rng = np.random.default_rng(45)
+    A = _rand_A(rng, 16, 40)
+    Y = rng.standard_normal((16, 3))
+    Y[3, 1] = np.nan
+    Y[:, 2] = 0.0
+    o = oracle.iht(A, Y, 4, 0.2, tol=1e-9, max_iter=7)
+    assert o["status"].tolist() == [2, 4, 1]
+    assert o["n_iter"].tolist() == [7, 0, 0]
+    assert np.all(o["support"][1] == -1) and np.all(o["support"][2] == -1)
+    z = A[:, [3, 11]] @ np.array([2.0, -1.0])
+    o = oracle.iht(np.eye(16), z[:16], 16, 1.0, tol=1e-12, max_iter=50)
+    assert o["status"][0] == 1 and o["n_iter"][0] == 1
