@@ -509,6 +509,13 @@ def main():
                                          "not the headline metric's selection rule")
         plan.set_option(cs.OPT_FUSE_UPDATE, 1)
         plan.set_option(cs.OPT_PERSIST, 1)
+        # IHT, the paper's comparison method, on the same workload: k = 32, R = 200
+        # iterations, step 1 / sigma_max(A)^2 (a configuration input, from numpy)
+        step = float(np.float32(1.0 / np.linalg.norm(A32.astype(np.float64), 2) ** 2))
+        fi = lambda: cs.iht_solve_batched(A, Y, p.k, step, max_iter=200, plan=plan, out=out)
+        mi, _, _ = timed(fi, ksteps, 3)
+        compare["iht_fp32_r200"] = {"ms_per_step": mi, "signals_per_s": ws * p.B / (mi / 1e3), "step": step,
+                                    "note": "IHT s <- H_k(s + t A^T r), 200 iterations, float32 correlation"}
         # column-wise 2D output path: 64 images of 256 x 256 at Sr = 0.3 (m = 77,
         # k = 25): CLOMP solve of the 16384 columns, x = D s, PSNR and SSIM
         pc = workloads.config_columnwise_2d(0.3, n_images=64)

@@ -332,6 +332,34 @@ cs_status cs_synthesize(const float* D, int32_t N, int32_t n, int32_t ldd, const
 cs_status cs_image_quality(const float* X, const float* Xref, int32_t H, int32_t W, int32_t count,
                            float peak, float* psnr, float* ssim, void* stream);
 
+/* Parameters of IHT. */
+typedef struct {
+    int32_t k;          /* sparsity kept by H_k, 1 <= k <= min(n, plan k_max, 64) */
+    double tol;         /* stop once ||r||_2 <= tol; 0 disables it */
+    int32_t max_iter;   /* R, the iteration limit; <= 0 means 200 (the paper's setting) */
+    float step;         /* t > 0, the scale factor of the update (t <= 1 / sigma_max(A)^2
+                           keeps the residual norm from growing) */
+} cs_iht_params;
+
+/* Batched IHT (Methods, Table "s forward block", IHT row), the paper's
+ * comparison method, on the same residual-injection layer:
+ *   s <- H_k(s + t A^T r),  r = y - A s,  s starting at zero,
+ * where H_k keeps the k entries of largest magnitude (lowest index on exact
+ * ties) and zeroes the rest.  The correlation is float32.  Stops a signal
+ * when ||r||_2 <= tol (checked before the first iteration and after each)
+ * with CS_SIG_REACHED_TOL, else after max_iter iterations with
+ * CS_SIG_MAX_ITER; a non-finite y gives CS_SIG_NONFINITE.  Outputs as for
+ * omp_solve_batched, except that support lists the k kept atoms in ascending
+ * index order (not selection order) and n_iter counts iterations.  Needs
+ * m <= 1024, n <= 4096 and k <= 64 (CS_ENOTSUP otherwise); the plan then
+ * holds two batch_max x n_max float32 buffers (the correlations and the dense
+ * s), allocated on first use.  Same argument conventions as the other
+ * batched calls. */
+cs_status iht_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
+                            const float* Y, int32_t ldy, int32_t batch, int32_t* support, float* coef,
+                            int32_t* n_iter, float* res_norm, int32_t* sig_status,
+                            const cs_iht_params* params, void* stream);
+
 /* Synchronise `stream` and copy the plan's device counters to out[0..3]:
  * out[0] = picks where the bf16 candidates did not certify the winner and
  * further atoms (the "suspects") were re-scored in float32; out[1] = device error flags (non-zero

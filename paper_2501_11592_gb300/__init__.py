@@ -22,7 +22,7 @@ __all__ = [
     "omp_solve_batched_host", "clomp_solve_batched_host", "clfit_forward", "clfit_adjoint",
     "clfit_adam_step", "CSError", "SIG_REACHED_K", "SIG_REACHED_TOL", "SIG_MAX_ITER",
     "SIG_DEPENDENT", "SIG_NONFINITE", "SIG_UNSUPPORTED", "library_path", "correlate", "PHASES", "omp_solve_varlen",
-    "clomp_solve_varlen", "synthesize", "image_quality", "reconstruct_columnwise",
+    "clomp_solve_varlen", "synthesize", "image_quality", "reconstruct_columnwise", "iht_solve_batched",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -54,6 +54,11 @@ class Instance(ctypes.Structure):
                 ("lda", ctypes.c_int32), ("y", ctypes.c_void_p), ("k", ctypes.c_int32),
                 ("support", ctypes.c_void_p), ("coef", ctypes.c_void_p), ("n_iter", ctypes.c_void_p),
                 ("res_norm", ctypes.c_void_p), ("sig_status", ctypes.c_void_p)]
+
+
+class IhtParams(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int32), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
+                ("step", ctypes.c_float)]
 
 
 class ClompParams(ctypes.Structure):
@@ -109,6 +114,8 @@ def load():
         L.cs_plan_autotune_report.argtypes = [vp, ctypes.c_char_p, i32]
         L.cs_plan_autotune_report.restype = ctypes.c_int
         L.omp_solve_varlen.argtypes = [vp, ctypes.POINTER(Instance), i32, ctypes.POINTER(OmpParams), vp]
+        L.iht_solve_batched.argtypes = solve_args + [ctypes.POINTER(IhtParams), vp]
+        L.iht_solve_batched.restype = ctypes.c_int
         L.clomp_solve_varlen.argtypes = [vp, ctypes.POINTER(Instance), i32, ctypes.POINTER(ClompParams), vp]
         for fn in ("omp_solve_varlen", "clomp_solve_varlen", "cs_plan_set_option", "cs_correlate", "cs_plan_counters", "cs_plan_set_profiling", "cs_plan_profile",
                    "cs_plan_create", "cs_plan_destroy", "omp_solve_batched", "omp_solve_batched_host",
@@ -311,6 +318,13 @@ def clomp_solve_batched(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, st
                     _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
                                   reset_adam, form, th, tv_weight, Dt, image_width, lv_weight, lv_eps), plan,
                     stream, out)
+
+
+def iht_solve_batched(A, Y, k, step, tol=0.0, max_iter=200, plan=None, stream=None, out=None) -> Result:
+    """Batched IHT, s <- H_k(s + step A^T r) for max_iter iterations (float32
+    correlation); support lists the kept atoms in ascending index order."""
+    return _batched(load().iht_solve_batched, A, Y, k, IhtParams(int(k), float(tol), int(max_iter), float(step)),
+                    plan, stream, out)
 
 
 def omp_solve(A, y, k, **kw) -> Result:

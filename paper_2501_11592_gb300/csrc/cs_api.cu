@@ -93,7 +93,8 @@ struct cs_plan {
     unsigned* counters = nullptr;
     float2* tab = nullptr;     // Adam bias-correction table, grown on demand
     int tab_cap = 0;
-    float* cbuf = nullptr;     // B_max x n_max float32 correlations (threshold rule), on first use
+    float* cbuf = nullptr;     // B_max x n_max float32 correlations (threshold rule, IHT), on first use
+    float* ihts = nullptr;     // B_max x n_max dense IHT coefficients, on first use
     float* tvE = nullptr;      // TV prior: differenced basis [n][Ep] (grown on demand)
     size_t tvE_cap = 0;
     float* tvT = nullptr;      // TV prior: (Delta D)^T (Delta D), n_max x n_max, on first use
@@ -984,6 +985,81 @@ cs_status solve_host(cs_plan* P, const float* A, int m, int n, int lda, const fl
     return CS_OK;
 }
 
+// Batched IHT: set-up, then per iteration the float32 correlation of the
+// live signals and the thresholded update (eagerly or as a replayed graph).
+cs_status iht_solve(cs_plan* P, const float* A, int m, int n, int lda, const float* Y, int ldy, int B,
+                    int32_t* support, float* coef, int32_t* n_iter, float* res_norm, int32_t* sig_status,
+                    const cs_iht_params* ip, cudaStream_t s) {
+    if (!ip) return fail(CS_EINVAL, "params is NULL");
+    cs_omp_params op{};
+    op.k = ip->k;
+    op.tol = ip->tol;
+    op.max_iter = ip->max_iter > 0 ? ip->max_iter : 200;
+    op.prec = CS_CORR_FP32;
+    cs_status st = validate(P, A, m, n, lda, Y, ldy, B, support, coef, n_iter, res_norm, sig_status, &op);
+    if (st != CS_OK) return st;
+    if (!(ip->step > 0.f) || !std::isfinite(ip->step)) return fail(CS_EINVAL, "step must be finite and > 0");
+    if (B == 0) return CS_OK;
+    if (m > kMaxRowChunks * 128 || n > kIhtMaxN || op.k > 64 || op.k > P->k_max)
+        return fail(CS_ENOTSUP, "IHT runs with m <= %d, n <= %d and k <= min(64, the plan's on-chip %d)",
+                    kMaxRowChunks * 128, kIhtMaxN, P->k_max);
+    DeviceGuard dg(P->device);
+    if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
+    st = ensure_cbuf(P);
+    if (st != CS_OK) return st;
+    if (!P->ihts) {
+        cudaError_t e = cudaMalloc(&P->ihts, sizeof(float) * (size_t)P->B_max * (size_t)P->n_max);
+        if (e != cudaSuccess) {
+            P->ihts = nullptr;
+            return fail(CS_ENOMEM, "cudaMalloc(IHT coefficients): %s", cudaGetErrorString(e));
+        }
+    }
+    IterArgs a = make_args(P, m, n, B, &op, support, coef, n_iter, res_norm, sig_status);
+    a.iters = op.max_iter;     // IHT runs iterations, not atoms: R may exceed k
+    a.need_gcol = 0;
+    a.need_gram = 0;
+    const cs_plan::Prep& pr = P->prep;
+    const bool reuse_a = P->a_gen != 0 && pr.gen == P->a_gen && pr.A == (const void*)A && pr.m == m &&
+                         pr.n == n && pr.lda == lda;
+    const float step = ip->step;
+    auto enqueue = [&](cudaStream_t st_) -> cs_status {
+        if (!reuse_a)
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st_, [&] {
+                              return launch_prep_A(A, lda, m, n, a.mp, a.mh, P->A32, nullptr, P->colnorm_max, st_);
+                          }), "prep A");
+        CS_TRY_LAUNCH(cudaMemsetAsync(P->ihts, 0, sizeof(float) * (size_t)B * n, st_), "clear s");
+        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st_, [&] { return launch_setup(a, Y, ldy, 0, st_); }), "setup");
+        for (int it = 0; it < a.iters; ++it) {
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_CORR, st_, [&] { return launch_corr_fp32_dense_live(a, P->cbuf, n, st_); }),
+                          "correlation (fp32, dense)");
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_UPDATE, st_, [&] { return launch_iht_update(a, P->cbuf, n, P->ihts, step, it, st_); }),
+                          "IHT update");
+        }
+        return CS_OK;
+    };
+    if (!reuse_a) {
+        cs_plan::Prep np;
+        np.A = A;
+        np.m = m;
+        np.n = n;
+        np.lda = lda;
+        np.gen = P->a_gen;
+        P->prep = np;
+    }
+    const cs_status rs = run_solve(P, s, enqueue, [&](std::string& key) {
+        const char tag[] = "iht";
+        key.append(tag, sizeof(tag));
+        const void* ptrs[] = {A, Y, support, coef, n_iter, res_norm, sig_status, P->cbuf, P->ihts};
+        key.append(reinterpret_cast<const char*>(ptrs), sizeof(ptrs));
+        const int ints[] = {m, n, lda, ldy, B, op.k, op.max_iter, reuse_a ? 1 : 0};
+        key.append(reinterpret_cast<const char*>(ints), sizeof(ints));
+        const double dk[] = {op.tol, (double)step};
+        key.append(reinterpret_cast<const char*>(dk), sizeof(dk));
+    }, P->use_graphs && !P->profiling);
+    if (rs != CS_OK) P->prep = cs_plan::Prep{};
+    return rs;
+}
+
 // Uneven batches: group instances by (A, m, n, lda, k), gather each group's
 // measurements into a batch, solve it with the batched path, scatter back.
 cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_omp_params* op,
@@ -1212,6 +1288,7 @@ cs_status cs_plan_destroy(cs_plan* plan) {
     if (plan->ws) cudaFree(plan->ws);
     if (plan->tab) cudaFree(plan->tab);
     if (plan->cbuf) cudaFree(plan->cbuf);
+    if (plan->ihts) cudaFree(plan->ihts);
     if (plan->tvE) cudaFree(plan->tvE);
     if (plan->tvT) cudaFree(plan->tvT);
     if (plan->io) cudaFree(plan->io);
@@ -1321,6 +1398,13 @@ cs_status clfit_adam_step(const float* A, int32_t m, int32_t n, int32_t lda, con
     cudaError_t e = launch_clfit_adjoint(A, m, lda, S, Sv, t, lds, R, ldr, batch, grad, mom, vel,
                                          tau, lr, beta1, beta2, eps, 1, (cudaStream_t)stream);
     return e == cudaSuccess ? CS_OK : cuda_fail(e, "clfit_adam_step");
+}
+
+cs_status iht_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda, const float* Y,
+                            int32_t ldy, int32_t batch, int32_t* support, float* coef, int32_t* n_iter,
+                            float* res_norm, int32_t* sig_status, const cs_iht_params* params, void* stream) {
+    return iht_solve(plan, A, m, n, lda, Y, ldy, batch, support, coef, n_iter, res_norm, sig_status, params,
+                     (cudaStream_t)stream);
 }
 
 cs_status cs_correlate(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,

@@ -23,6 +23,7 @@ constexpr int kTcGroup = 16;         // bf16 mode keeps the two largest |c| of e
 constexpr int kTcCandPerTile = 2 * kCorrTcTileN / kTcGroup;   // 32 candidates per 256-atom tile
 constexpr int kGramAMax = 4096;      // n up to which A^T A is precomputed per solve
 constexpr int kCorrTcMaxN = 4096;    // candidate merge holds <= 512 per signal
+constexpr int kIhtMaxN = 4096;       // IHT: u = s + t c of a signal in shared memory
 constexpr int kLargeMaxM = 32768;    // large OMP solves: rows (residual staged in shared memory)
 constexpr int kLargeMaxK = 4096;     // large OMP solves: support size (float64 W = L^{-T} in HBM)
 
@@ -234,6 +235,12 @@ cudaError_t launch_synthesize(const float* D, int N, int n, int ldd, const int* 
                               const int* n_iter, int k, int B, float* X, int ldx, cudaStream_t s);
 cudaError_t launch_image_quality(const float* X, const float* R, int H, int W, int count, float peak,
                                  float* psnr, float* ssim, cudaStream_t s);
+// IHT (k_iht.cu): one iteration's H_k(s + step c) from the float32
+// correlation C (B x n, row stride ldc), the dense s (sd, B x n), the
+// residual and the stopping rule (iteration `it` of a.iters).
+bool iht_supported(const IterArgs& a);
+cudaError_t launch_iht_update(const IterArgs& a, const float* C, int ldc, float* sd, float step, int it,
+                              cudaStream_t s);
 bool clomp_th_supported(const IterArgs& a);
 cudaError_t launch_clomp_th(const IterArgs& a, const ClArgs& c, const float* C, int ldc, int iter, cudaStream_t s);
 
