@@ -69,7 +69,7 @@ def test_iht_stop_rules_and_graph_replay(cs_gpu, torch):
     runs = [run(cs_gpu, torch, A32, Y32, 4, step, max_iter=400, tol=1e-4, plan=plan) for _ in range(3)]
     for r in runs[1:]:           # eager, captured, replayed: the same bits
         for q in r:
-            assert np.array_equal(r[q], runs[0][q]), q
+            assert np.array_equal(r[q], runs[0][q], equal_nan=True), q
     g = runs[0]
     o = oracle.iht(A64, Y64, 4, step, max_iter=400, tol=1e-4)
     assert g["status"][1] == 4 and g["n_iter"][1] == 0
