@@ -321,6 +321,7 @@ def bench_large_1d(cs, torch, stream, barrier, rank, peaks_src):
             "supports_identical": bool(np.array_equal(g["support"], o["support"])),
             "ambiguous_ties": summ["ambiguous"], "non_ambiguous_mismatches": summ["failures"],
             "max_coef_rel_err": summ["max_coef_rel_err"], "oracle_s": to, "oracle_cores": oracle.max_threads()}
+    res["autotune"] = plan.autotune_report()
     del A, plan
     torch.cuda.empty_cache()
     return res
@@ -360,6 +361,7 @@ def bench_uneven(cs, torch, stream, barrier):
         res["omp_" + prec] = {"s_per_batch": wall, "instances_per_s": len(items) / wall,
                               "solved": int(np.sum(st != cs.SIG_UNSUPPORTED)), "refused": int(np.sum(st == cs.SIG_UNSUPPORTED)),
                               "note": "wall clock of one call (host loop over groups; large groups synchronise every 64 iterations)"}
+    res["autotune"] = plan.autotune_report()
     del keep, plan
     torch.cuda.empty_cache()
     return res
@@ -764,6 +766,7 @@ def main():
             "clocks": clocks,
             "gpu_launches": int(launches),
             "parity": parity,
+            "autotune": plan.autotune_report(),
             "bf16_certificate_fallbacks": fallbacks,
             "device_error_flags": errflags,
             "compare": compare,
