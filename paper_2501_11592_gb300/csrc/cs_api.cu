@@ -34,6 +34,12 @@ cs_status cuda_fail(cudaError_t e, const char* where) {
     return fail(CS_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }
 
+#define CS_TRY_LAUNCH(expr, what)                         \
+    do {                                                  \
+        cudaError_t e_ = (expr);                          \
+        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
+    } while (0)
+
 struct DeviceGuard {
     int prev = -1;
     bool changed = false;
@@ -394,18 +400,51 @@ void large_mark(void* vctx, int phase, int after) {
 // workspace stays within a few GB.
 constexpr size_t kLargeChunkBytes = (size_t)8 << 30;
 
+// CLOMP configurations the large-instance path runs: the Gram form, one atom
+// per iteration, no prior.
+bool large_clomp_ok(const cs_clomp_params* cp) {
+    const bool th = cp->select_threshold > 0.f && cp->select_threshold < 1.f;
+    return cp->form == CS_CL_GRAM && !th && cp->tv_weight == 0.f && cp->lv_weight == 0.f;
+}
+
+template <class F>
+cudaError_t timed(cs_plan* P, int phase, cudaStream_t s, F&& launch);
+
 cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const std::vector<const float*>& ys,
-                      const std::vector<LargeOut>& outs, const cs_omp_params* op, cudaStream_t s) {
+                      const std::vector<LargeOut>& outs, const cs_omp_params* op, const cs_clomp_params* cp,
+                      cudaStream_t s) {
     if (P->no_large) return fail(CS_ENOTSUP, "this entry point runs only the on-chip kernels (m <= 1024, k <= 64, "
                                              "bf16: m <= 256, n <= 4096)");
+    if (cp && !large_clomp_ok(cp))
+        return fail(CS_ENOTSUP, "CLOMP beyond the on-chip sizes runs the Gram form with one atom per iteration "
+                                "and no prior");
     const size_t count = ys.size();
     int kmax = 1;
     for (const LargeOut& o : outs) kmax = std::max(kmax, o.k);
     if (!large_supported(m, n, kmax))
         return fail(CS_ENOTSUP, "large OMP supports m <= %d and k <= %d (m=%d k=%d)", kLargeMaxM, kLargeMaxK, m, kmax);
     const int bf16 = op->prec == CS_CORR_BF16 ? 1 : 0;
+    const int clf = cp ? 1 : 0;
+    ClArgs cl{};
+    if (cp) {
+        // Adam factors for every step of the longest signal (one state for the solve)
+        const int iters = op->max_iter > 0 ? std::min(kmax, op->max_iter) : kmax;
+        const int len = (cp->reset_adam_each_iter ? 1 : iters) * std::max(cp->steps, 1);
+        cs_status st = ensure_tab(P, len);
+        if (st != CS_OK) return st;
+        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] {
+                          return launch_adam_table(P->tab, len, cp->lr, cp->beta1, cp->beta2, s);
+                      }), "adam table");
+        cl.steps = cp->steps;
+        cl.beta1 = cp->beta1;
+        cl.beta2 = cp->beta2;
+        cl.eps = cp->eps;
+        cl.reset = cp->reset_adam_each_iter ? 1 : 0;
+        cl.tab = P->tab;
+        cl.tab_len = len;
+    }
     // signals per chunk: the fixed part (bf16 A) plus as many signals as fit the budget
-    const size_t one = large_ws_bytes(m, n, 1, kmax, bf16), two = large_ws_bytes(m, n, 2, kmax, bf16);
+    const size_t one = large_ws_bytes(m, n, 1, kmax, bf16, clf), two = large_ws_bytes(m, n, 2, kmax, bf16, clf);
     const size_t per = two > one ? two - one : one;
     size_t cap = one >= kLargeChunkBytes ? 1 : 1 + (kLargeChunkBytes - one) / per;
     cap = std::min(cap, (size_t)std::max(P->B_max, 1));
@@ -438,7 +477,8 @@ cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const s
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         call.tune = P->autotune && cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
         call.chosen_cfg = &chosen;
-        const size_t need = large_ws_bytes(m, n, (int)nb, kmax, bf16);
+        const size_t need = large_ws_bytes(m, n, (int)nb, kmax, bf16, clf);
+        call.cl = cp ? &cl : nullptr;
         cs_status st = ensure_lg(P, need);
         if (st != CS_OK) return st;
         cudaError_t e = large_solve(call, P->lg, P->lg_bytes, s);
@@ -509,11 +549,6 @@ IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int
     return a;
 }
 
-#define CS_TRY_LAUNCH(expr, what)                         \
-    do {                                                  \
-        cudaError_t e_ = (expr);                          \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
 
 cudaEvent_t pool_event(cs_plan* P) {
     if (!P->pool.empty()) {
@@ -620,10 +655,6 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         return fail(CS_ENOTSUP, "the FP8 correlation runs with m <= 256, n <= %d and k <= %d (m=%d n=%d k=%d)",
                     kCorrTcMaxN, P->k_max, m, n, op->k);
     if (needs_large(P, m, n, op->k, op->prec)) {
-        if (cp)
-            return fail(CS_ENOTSUP, "CLOMP runs with m <= %d, k <= %d (the plan's on-chip limit) and, with the bf16 "
-                                    "correlation, m <= 256 and n <= %d (m=%d n=%d k=%d)",
-                        kMaxRowChunks * 128, P->k_max, kCorrTcMaxN, m, n, op->k);
         std::vector<const float*> ys(B);
         std::vector<LargeOut> outs(B);
         for (int b = 0; b < B; ++b) {
@@ -631,7 +662,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             ys[b] = Y + (size_t)b * ldy;
             outs[b] = LargeOut{support + o, coef + o, n_iter + b, res_norm + b, sig_status + b, op->k};
         }
-        return solve_large(P, A, m, n, lda, ys, outs, op, s);
+        return solve_large(P, A, m, n, lda, ys, outs, op, cp, s);
     }
     DeviceGuard dg(P->device);
     if (dg.err != cudaSuccess) return cuda_fail(dg.err, "cudaSetDevice");
@@ -1086,7 +1117,7 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
         if (op->prec == CS_CORR_FP8)   // the FP8 correlation has no large-instance form
             return x.m > P->m_max || x.n > P->n_max || x.k > P->k_max || !corr_tc_supported(x.m, x.n);
         return x.m > P->m_max || x.n > P->n_max || x.k > P->k_user ||
-               (large(x) && (cp || P->no_large || !large_supported(x.m, x.n, x.k)));
+               (large(x) && ((cp && !large_clomp_ok(cp)) || P->no_large || !large_supported(x.m, x.n, x.k)));
     };
     // groups in order of first appearance: on-chip groups share (A, m, n,
     // lda, k); large groups share (A, m, n, lda), each instance with its k
@@ -1216,7 +1247,7 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
             ys[j] = x.y;
             outs[j] = LargeOut{x.support, x.coef, x.n_iter, x.res_norm, x.sig_status, x.k};
         }
-        cs_status st = solve_large(P, x0.A, x0.m, x0.n, x0.lda, ys, outs, op, s);
+        cs_status st = solve_large(P, x0.A, x0.m, x0.n, x0.lda, ys, outs, op, cp, s);
         if (st != CS_OK) return st;
     }
     return CS_OK;

@@ -158,9 +158,12 @@ struct LargeCall {
     int corr_cfg;
     int tune;
     int* chosen_cfg;
+    // CLOMP in Gram form (NULL: plain OMP): steps, betas, eps, reset and the
+    // Adam factor table (tab) of the solve
+    const struct ClArgs* cl;
 };
 bool large_supported(int m, int n, int k);
-size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16);
+size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16, int cl);
 // Runs a whole solve on `s` (synchronising `s` every 64 iterations to end
 // early once every signal has stopped, when live_host is set).
 cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaStream_t s);

@@ -90,6 +90,17 @@ struct LgState {
     int* nit;                       // [Bl]
     int* st;                        // [Bl] status (-1 running)
     int* live;                      // [1] signals still running after the last check
+    // CLOMP (Gram form): G = A_S^T A_S and b = A_S^T y grown by one row per
+    // iteration, s double-buffered across the Adam steps, the moments
+    int cl, steps, reset;
+    float beta1, beta2, eps;
+    const float2* tab;              // Adam factor pairs for tau = 1, 2, ...
+    float* G;                       // [Bl][K][K]
+    float* bv;                      // [Bl][K]
+    float* s0;                      // [Bl][K]
+    float* s1;                      // [Bl][K]
+    float* am;                      // [Bl][K]
+    float* av;                      // [Bl][K]
 };
 
 __device__ __forceinline__ float lg_delta(const LgState& S, int b) {
@@ -503,6 +514,76 @@ __global__ void __launch_bounds__(256) k_lg_update(LgState S, int t) {
     S.xf[(size_t)b * S.K + i] = (float)xi;
 }
 
+// ------------------------------------------------------ CLOMP Gram fit --
+// Append the new atom to the Gram form: row and column t of G from the Gram
+// column, G_tt = ||a_j||^2, b_t = a_j^T y; the new coefficient and its
+// moments start at zero (with reset_adam_each_iter every moment restarts).
+__global__ void __launch_bounds__(256) k_lgc_append(LgState S, int t) {
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > t) return;
+    const float* g = S.gsum + (size_t)b * (S.K + 2);
+    float* G = S.G + (size_t)b * S.K * S.K;
+    const size_t o = (size_t)b * S.K;
+    if (i < t) {
+        G[(size_t)t * S.K + i] = g[i];
+        G[(size_t)i * S.K + t] = g[i];
+        if (S.reset) {
+            S.am[o + i] = 0.f;
+            S.av[o + i] = 0.f;
+        }
+    } else {
+        G[(size_t)t * S.K + t] = g[t];
+        S.bv[o + t] = g[t + 1];
+        S.s0[o + t] = 0.f;
+        S.s1[o + t] = 0.f;
+        S.am[o + t] = 0.f;
+        S.av[o + t] = 0.f;
+        S.xf[o + t] = 0.f;
+        S.nit[b] = t + 1;
+    }
+}
+
+// One Adam step of every live signal on its t1 coordinates (one warp per
+// coordinate q): the gradient (G s - b)_q of 1/2 ||y - A_S s||^2 from
+// s_in, the moments, and s_out[q] (PyTorch's update rule, step tau).  The
+// last step of a fit also writes the coefficients used by the residual.
+__global__ void __launch_bounds__(256) k_lgc_step(LgState S, int t1, int tau, const float* __restrict__ s_in,
+                                                  float* __restrict__ s_out, int last) {
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= t1) return;
+    const size_t o = (size_t)b * S.K;
+    const float* Gq = S.G + (o + q) * S.K;
+    const float* sb = s_in + o;
+    float acc = 0.f;
+    for (int p0 = 0; p0 < t1; p0 += 256) {     // eight entries per lane in flight, ascending
+        float gv[8], sv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int p = p0 + lane + 32 * u;
+            gv[u] = p < t1 ? Gq[p] : 0.f;
+            sv[u] = p < t1 ? sb[p] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) acc = fmaf(gv[u], sv[u], acc);
+    }
+    const float g = warp_sum(acc) - S.bv[o + q];
+    if (lane == 0) {
+        const float2 cc = S.tab[tau - 1];
+        const float mo = fmaf(S.beta1, S.am[o + q], (1.f - S.beta1) * g);
+        const float ve = fmaf(S.beta2, S.av[o + q], (1.f - S.beta2) * g * g);
+        S.am[o + q] = mo;
+        S.av[o + q] = ve;
+        const float sn = sb[q] - cc.x * mo / fmaf(sqrtf(ve), cc.y, S.eps);
+        s_out[o + q] = sn;
+        if (last) S.xf[o + q] = sn;
+    }
+}
+
 // ----------------------------------------------------------- residual --
 // Partial sums sum_{q in chunk} a_{S_q}[i] x_q over chunks of 128 atoms
 // (one thread per row i).
@@ -601,10 +682,11 @@ __global__ void k_lg_out(LgState S) {
 
 struct LgLayout {
     size_t A16, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
-        xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, total;
+        xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, G, bv, s0, s1, am, av, total;
 };
 
-LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16) {
+// cl: CLOMP's Gram-form state instead of OMP's float64 W = L^{-T}.
+LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
     const size_t B = (size_t)Bl, K = (size_t)round_up(kmax, 32), mp = (size_t)round_up(m, 8);
     const size_t nseg = (size_t)ceil_div(m, LG_SEG), lch = (size_t)ceil_div((int)K, LG_LC),
                  rch = (size_t)ceil_div((int)K, LG_RQ), nw = (size_t)ceil_div(n, 32);
@@ -633,7 +715,7 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16) {
     L.sup = take(sizeof(int) * B * K);
     L.gpart = take(sizeof(float) * B * nseg * (K + 2));
     L.gsum = take(sizeof(float) * B * (K + 2));
-    L.W = take(sizeof(double) * B * 2 * K * K);
+    L.W = cl ? 0 : take(sizeof(double) * B * 2 * K * K);
     L.z = take(sizeof(double) * B * K);
     L.x = take(sizeof(double) * B * K);
     L.xf = take(sizeof(float) * B * K);
@@ -647,6 +729,14 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16) {
     L.nit = take(sizeof(int) * B);
     L.st = take(sizeof(int) * B);
     L.live = take(sizeof(int));
+    if (cl) {
+        L.G = take(sizeof(float) * B * K * K);
+        L.bv = take(sizeof(float) * B * K);
+        L.s0 = take(sizeof(float) * B * K);
+        L.s1 = take(sizeof(float) * B * K);
+        L.am = take(sizeof(float) * B * K);
+        L.av = take(sizeof(float) * B * K);
+    }
     L.total = off;
     return L;
 }
@@ -702,13 +792,16 @@ bool large_supported(int m, int n, int k) {
     return m >= 1 && m <= kLargeMaxM && n >= 1 && k >= 1 && k <= kLargeMaxK;
 }
 
-size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16) { return lg_layout(m, n, Bl, kmax, bf16).total; }
+size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16, int cl) {
+    return lg_layout(m, n, Bl, kmax, bf16, cl).total;
+}
 
 cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaStream_t s) {
     const int Bl = (int)call.ys.size();
     if (Bl == 0) return cudaSuccess;
     const int kmax = *std::max_element(call.ks.begin(), call.ks.end());
-    const LgLayout L = lg_layout(call.m, call.n, Bl, kmax, call.bf16);
+    const int cl = call.cl != nullptr ? 1 : 0;
+    const LgLayout L = lg_layout(call.m, call.n, Bl, kmax, call.bf16, cl);
     if (L.total > ws_bytes) return cudaErrorInvalidValue;
     char* w = static_cast<char*>(ws);
     LgState S{};
@@ -742,7 +835,22 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     S.sup = reinterpret_cast<int*>(w + L.sup);
     S.gpart = reinterpret_cast<float*>(w + L.gpart);
     S.gsum = reinterpret_cast<float*>(w + L.gsum);
-    S.W = reinterpret_cast<double*>(w + L.W);
+    S.W = cl ? nullptr : reinterpret_cast<double*>(w + L.W);
+    S.cl = cl;
+    if (cl) {
+        S.steps = call.cl->steps;
+        S.reset = call.cl->reset;
+        S.beta1 = call.cl->beta1;
+        S.beta2 = call.cl->beta2;
+        S.eps = call.cl->eps;
+        S.tab = call.cl->tab;
+        S.G = reinterpret_cast<float*>(w + L.G);
+        S.bv = reinterpret_cast<float*>(w + L.bv);
+        S.s0 = reinterpret_cast<float*>(w + L.s0);
+        S.s1 = reinterpret_cast<float*>(w + L.s1);
+        S.am = reinterpret_cast<float*>(w + L.am);
+        S.av = reinterpret_cast<float*>(w + L.av);
+    }
     S.z = reinterpret_cast<double*>(w + L.z);
     S.x = reinterpret_cast<double*>(w + L.x);
     S.xf = reinterpret_cast<float*>(w + L.xf);
@@ -821,6 +929,7 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     if (call.chosen_cfg) *call.chosen_cfg = cfg;
     S.nb = 1 << (cfg >> 1);
     int* live_h = call.live_host;
+    int s_parity = 0;   // CLOMP: which buffer holds the current coefficients
     for (int it = 0; it < iters; ++it) {
         const int t = it;
         mark(CS_PHASE_CORR, 0);
@@ -833,10 +942,23 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         k_lg_gsum<<<dim3(ceil_div(t + 2, 256), Bl), 256, 0, s>>>(S, t);
         mark(CS_PHASE_SELECT, 1);
         mark(CS_PHASE_FIT, 0);
-        if (t > 0) k_lg_lpart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
-        k_lg_pivot<<<Bl, 1024, 0, s>>>(S, t);
-        if (t > 0) k_lg_upart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
-        k_lg_update<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t);
+        if (cl) {
+            // Gram form: grow G and b, then the T Adam steps on t + 1 coordinates
+            k_lgc_append<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t);
+            const int tau0 = S.reset ? 0 : t * S.steps;
+            for (int step = 0; step < S.steps; ++step) {
+                const float* sin = (s_parity == 0) ? S.s0 : S.s1;
+                float* sout = (s_parity == 0) ? S.s1 : S.s0;
+                k_lgc_step<<<dim3(ceil_div(t + 1, 8), Bl), 256, 0, s>>>(S, t + 1, tau0 + step + 1, sin, sout,
+                                                                       step + 1 == S.steps ? 1 : 0);
+                s_parity ^= 1;
+            }
+        } else {
+            if (t > 0) k_lg_lpart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
+            k_lg_pivot<<<Bl, 1024, 0, s>>>(S, t);
+            if (t > 0) k_lg_upart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
+            k_lg_update<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t);
+        }
         mark(CS_PHASE_FIT, 1);
         mark(CS_PHASE_RESID, 0);
         k_lg_rpart<<<dim3(ceil_div(S.m, 256), ceil_div(t + 1, LG_RQ), Bl), 256, 0, s>>>(S, t + 1);

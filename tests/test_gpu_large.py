@@ -99,8 +99,7 @@ def test_large_path_stop_rules_and_edges(cs_gpu, torch):
 def test_large_path_deterministic_and_routed(cs_gpu, torch):
     """Two solves give the same bits; the large path runs its own launch
     groups (one correlation, selection, least-squares and residual group per
-    iteration, none of the on-chip kernels); CLOMP beyond the on-chip limits
-    is refused."""
+    iteration, none of the on-chip kernels)."""
     p = workloads.random_problem(400, 2000, 4, 90, seed=403, snr_db=30.0)
     A32, Y32, _, _ = f32_problem(p.A, p.Y)
     a = run(cs_gpu, torch, A32, Y32, 90, "bf16")
@@ -110,8 +109,42 @@ def test_large_path_deterministic_and_routed(cs_gpu, torch):
     ln = a["launches"]
     assert ln["correlation"] == ln["select"] == ln["fit"] == ln["residual"] == 90
     assert ln["persist"] == 0 and ln["update"] == 0 and ln["setup"] == 1
-    A = torch.from_numpy(A32).cuda()
-    Y = torch.from_numpy(Y32).cuda()
+
+
+def _oracle_clomp(A64, Y64, k, **kw):
+    f = lambda v: float(np.float32(v))
+    return oracle.clomp(A64, Y64, k, steps=50, lr=f(1e-2), beta1=f(0.9), beta2=f(0.999), eps=f(1e-8), **kw)
+
+
+@pytest.mark.parametrize("prec", ["fp32", "bf16"])
+@pytest.mark.parametrize("m,n,B,k,snr", [(2048, 8192, 1, 150, None),     # one long noiseless signal
+                                         (300, 1000, 4, 100, 30.0),      # k beyond the on-chip 64
+                                         (1500, 3001, 3, 20, 40.0)])     # more rows than a warp holds
+def test_large_path_clomp_matches_oracle(cs_gpu, torch, prec, m, n, B, k, snr):
+    """CLOMP in Gram form on the large-instance path (G and b grown per
+    iteration, 50 Adam steps per iteration, one Adam state for the solve)."""
+    p = workloads.random_problem(m, n, B, k, seed=m + 3 * k, snr_db=snr, values="gauss" if snr is None else "pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    A = torch.from_numpy(np.asfortranarray(A32)).cuda()
+    Y = torch.from_numpy(np.asfortranarray(Y32)).cuda()
+    plan = cs_gpu.Plan(m, n, B, k)
+    r = cs_gpu.clomp_solve_batched(A, Y, k, prec=prec, form="gram", plan=plan, steps=50, lr=1e-2)
+    torch.cuda.synchronize()
+    g = to_numpy(r)
+    ln = {ph: v[0] for ph, v in plan.profile(reset=True).items()}
+    assert ln["persist"] == 0 and ln["update"] == 0 and ln["correlation"] == k
+    print(prec, m, n, B, k, compare(g, _oracle_clomp(A64, Y64, k)))
+
+
+def test_large_path_clomp_refusals(cs_gpu, torch):
+    """Beyond the on-chip sizes CLOMP runs the Gram form with one atom per
+    iteration and no prior; the literal gather form is refused there."""
+    A = torch.randn(300, 1000, device="cuda")
+    Y = torch.randn(300, 2, device="cuda")
+    plan = cs_gpu.Plan(300, 1000, 2, 100)
     with pytest.raises(cs_gpu.CSError) as e:
-        cs_gpu.clomp_solve_batched(A, Y, 90, plan=cs_gpu.Plan(400, 2000, 4, 90))
+        cs_gpu.clomp_solve_batched(A, Y, 100, form="gather", plan=plan)
+    assert e.value.code == -5
+    with pytest.raises(cs_gpu.CSError) as e:
+        cs_gpu.clomp_solve_batched(A, Y, 100, form="gram", plan=plan, th=0.7)
     assert e.value.code == -5

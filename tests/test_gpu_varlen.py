@@ -44,20 +44,15 @@ def test_varlen_rejects_malformed_instances(cs_gpu):
 
 
 # The plan of the stated-size uneven batch below, and the limits the header
-# documents for a solved instance: plain OMP solves every instance within the
-# plan (beyond the on-chip kernels on the large-instance path); CLOMP solves
-# only what the on-chip kernels take.
+# documents for a solved instance: OMP and CLOMP (Gram form) solve every
+# instance within the plan, beyond the on-chip kernels on the large-instance
+# path.
 _C5_PLAN = (8192, 16384, 128, 2048)
 
 
 def _c5_solvable(m, n, k, prec, algo):
     m_max, n_max, _, k_max = _C5_PLAN
-    ok = m <= m_max and n <= n_max and k <= k_max
-    if algo == "clomp":
-        ok = ok and m <= 1024 and k <= 64
-        if prec == "bf16":
-            ok = ok and m <= 256 and n <= 4096
-    return ok
+    return m <= m_max and n <= n_max and k <= k_max
 
 
 def _on_chip(m, n, k, prec):
