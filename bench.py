@@ -341,6 +341,23 @@ def bench_large_1d(cs, torch, stream, barrier, rank, peaks_src):
             "supports_identical": bool(np.array_equal(g["support"], o["support"])),
             "ambiguous_ties": summ["ambiguous"], "non_ambiguous_mismatches": summ["failures"],
             "max_coef_rel_err": summ["max_coef_rel_err"], "oracle_s": to, "oracle_cores": oracle.max_threads()}
+        # CLOMP: the first 50 iterations (the Adam step counter does not depend on k)
+        it = 50
+        r = cs.clomp_solve_batched(A, y, k, prec="bf16", form="gram", plan=plan, max_iter=it, **CL)
+        torch.cuda.synchronize()
+        g = prules.to_numpy(r)
+        t0 = time.perf_counter()
+        o = oracle.clomp(pl.A.astype(np.float64, order="F"), np.float32(pl.Y).astype(np.float64), k,
+                         max_iter=it, steps=CL["steps"],
+                         **{q: float(np.float32(v)) for q, v in CL.items() if q != "steps"})
+        to = time.perf_counter() - t0
+        g = {q: v[:, :it] if v.ndim == 2 else v for q, v in g.items()}
+        o = {q: v[:, :it] if v.ndim == 2 else v for q, v in o.items()}
+        summ, fails = prules.summarize(g, o)
+        res["parity_first_50_iterations_clomp_bf16"] = {
+            "supports_identical": bool(np.array_equal(g["support"], o["support"])),
+            "ambiguous_ties": summ["ambiguous"], "non_ambiguous_mismatches": summ["failures"],
+            "max_coef_rel_err": summ["max_coef_rel_err"], "oracle_s": to, "oracle_cores": oracle.max_threads()}
     res["autotune"] = plan.autotune_report()
     del A, plan
     torch.cuda.empty_cache()

@@ -466,10 +466,12 @@ void cs_oracle_clfit_adam(const double* A, int m, int lda, const int32_t* S, int
                             0.0, NULL, 0, 0);
 }
 
+/* CLOMP on one signal.  par != 0 splits the correlation of the argmax rule
+ * over threads (select_atom_par: same values, same tie rule). */
 static void clomp_one(const double* A, int m, int n, int lda, const double* y, int k,
                       double tol, int max_iter, int steps, double lr, double beta1,
                       double beta2, double eps, int reset_adam, double th, double tv_w,
-                      const double* D, int N, int ldd, int32_t* support,
+                      const double* D, int N, int ldd, int par, int32_t* support,
                       double* coef, int32_t* n_iter, double* res_norm, int32_t* status,
                       double* top1, double* top2, double* res_hist) {
     for (int q = 0; q < k; ++q) { support[q] = -1; coef[q] = 0.0; top1[q] = -1.0; top2[q] = -1.0; res_hist[q] = NAN; }
@@ -478,6 +480,7 @@ static void clomp_one(const double* A, int m, int n, int lda, const double* y, i
     double* mom = (double*)calloc(k, sizeof(double));
     double* vel = (double*)calloc(k, sizeof(double));
     unsigned char* inS = (unsigned char*)calloc(n, 1);
+    double* cpar = par ? (double*)malloc(sizeof(double) * n) : NULL;
     int32_t tau = 0;
     memcpy(r, y, sizeof(double) * m);              /* s = 0  =>  r = y */
     double rho = nrm2(r, m);
@@ -487,7 +490,8 @@ static void clomp_one(const double* A, int m, int n, int lda, const double* y, i
     if (rho <= tol) st = ST_TOL;
     while (st < 0 && t < k && it < iters) {
         if (!multi) {
-            int j = select_atom(A, m, n, lda, r, inS, &top1[t], &top2[t]);
+            int j = cpar ? select_atom_par(A, m, n, lda, r, inS, cpar, &top1[t], &top2[t])
+                         : select_atom(A, m, n, lda, r, inS, &top1[t], &top2[t]);
             if (j < 0) { st = ST_MAXIT; break; }
             support[t] = j;                       /* Mask |= e_j (bitwise or) */
             inS[j] = 1;
@@ -522,7 +526,7 @@ static void clomp_one(const double* A, int m, int n, int lda, const double* y, i
     *n_iter = t;
     *res_norm = rho;
     *status = st;
-    free(r); free(mom); free(vel); free(inS);
+    free(r); free(mom); free(vel); free(inS); free(cpar);
 }
 
 static int bad_args(const double* A, int m, int n, int lda, const double* Y, int ldy,
@@ -583,12 +587,12 @@ int cs_oracle_clomp(const double* A, int m, int n, int lda, const double* Y, int
     if (!D) N = n;
 #ifdef _OPENMP
     if (nthreads > 0) omp_set_num_threads(nthreads);
-#pragma omp parallel for schedule(dynamic, 4)
+#pragma omp parallel for schedule(dynamic, 4) if (B > 1)
 #endif
     for (int b = 0; b < B; ++b) {
         size_t o = (size_t)b * k;
         clomp_one(A, m, n, lda, Y + (size_t)b * ldy, k, tol, max_iter, steps, lr, beta1,
-                  beta2, eps, reset_adam, th, tv_w, D, N, ldd, support + o, coef + o, n_iter + b, res_norm + b,
+                  beta2, eps, reset_adam, th, tv_w, D, N, ldd, B == 1, support + o, coef + o, n_iter + b, res_norm + b,
                   status + b, top1 + o, top2 + o, res_hist + o);
     }
     return 0;

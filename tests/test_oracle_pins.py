@@ -374,6 +374,23 @@ def test_clomp_excludes_selected_and_stops():
     assert o["status"][2] == 4
 
 
+def test_clomp_single_signal_parallel_correlation_matches_batch():
+    """A single signal takes the correlation split over threads; its results
+    equal the same signal solved inside a batch (serial correlation), bit for
+    bit, including an exact tie (a duplicated column)."""
+    rng = np.random.default_rng(17)
+    A = _rand_A(rng, 40, 300)
+    A[:, 201] = A[:, 7]
+    Y = A[:, [7, 50, 120]] @ np.array([1.0, -0.5, 0.25])[:, None] + 0.01 * rng.standard_normal((40, 1))
+    Y2 = np.concatenate([Y, rng.standard_normal((40, 1))], axis=1)
+    one = oracle.clomp(A, Y, 12, steps=7, nthreads=4)
+    two = oracle.clomp(A, Y2, 12, steps=7, nthreads=4)
+    assert one["support"][0].tolist() == two["support"][0].tolist()
+    assert 201 not in one["support"][0].tolist()[:1]
+    for q in ("coef", "top1", "top2"):
+        assert np.array_equal(one[q][0], two[q][0])
+
+
 # ------------------------------------------------ threshold selection pins
 
 def _threshold_sets(x, th, k):
