@@ -479,6 +479,7 @@ cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const s
         call.chosen_cfg = &chosen;
         const size_t need = large_ws_bytes(m, n, (int)nb, kmax, bf16, clf);
         call.cl = cp ? &cl : nullptr;
+        call.errflag = P->counters + 1;
         cs_status st = ensure_lg(P, need);
         if (st != CS_OK) return st;
         cudaError_t e = large_solve(call, P->lg, P->lg_bytes, s);

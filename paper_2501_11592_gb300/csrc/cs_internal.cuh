@@ -161,6 +161,8 @@ struct LargeCall {
     // CLOMP in Gram form (NULL: plain OMP): steps, betas, eps, reset and the
     // Adam factor table (tab) of the solve
     const struct ClArgs* cl;
+    // device error flags (bit 32: a grid-wide barrier of the CLOMP fit gave up)
+    unsigned* errflag;
 };
 bool large_supported(int m, int n, int k);
 size_t large_ws_bytes(int m, int n, int Bl, int kmax, int bf16, int cl);

@@ -101,6 +101,9 @@ struct LgState {
     float* s1;                      // [Bl][K]
     float* am;                      // [Bl][K]
     float* av;                      // [Bl][K]
+    unsigned* gbar;                 // [2] arrivals at the fit's grid-wide barriers, and the give-up
+                                    // word (both this solve's)
+    unsigned* errflag;              // device error flags
 };
 
 __device__ __forceinline__ float lg_delta(const LgState& S, int b) {
@@ -584,6 +587,100 @@ __global__ void __launch_bounds__(256) k_lgc_step(LgState S, int t1, int tau, co
     }
 }
 
+// All T Adam steps of one iteration in one cooperative launch (every CTA
+// resident): CTA (x, b) serves signal b, its warps the coordinates
+// q = x * 8 + warp + i * 8 * gridDim.x, the same ones at every step.  Per
+// step the CTA stages s_in of its signal in shared memory (read through L2:
+// other CTAs wrote it), each warp forms (G s - b)_q in the order of
+// k_lgc_step and lane 0 makes the same Adam update; then a grid-wide barrier
+// (bounded wait; on time-out the error flags get bit 32, the solve's give-up
+// word is set and every CTA of this and later fits of the solve returns).  The barrier counter only grows within a solve: the j-th barrier
+// of this launch is passed once it holds base + (j + 1) * (CTAs).
+constexpr unsigned long long LG_WAIT_CYCLES = 4000000000ull;   // ~2 s at 2 GHz
+constexpr unsigned LG_ERR_BARRIER = 32u;
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// false: the wait gave up (or another CTA's did)
+__device__ bool lg_grid_barrier(const LgState& S, unsigned target, int* ok_sh) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicAdd(S.gbar, 1u);
+        int ok = 1;
+        const unsigned long long t0 = clock64();
+        while ((int)(ld_acquire_u32(S.gbar) - target) < 0) {
+            if (ld_acquire_u32(S.gbar + 1) != 0u) {
+                ok = 0;
+                break;
+            }
+            if (clock64() - t0 > LG_WAIT_CYCLES) {
+                atomicOr(S.errflag, LG_ERR_BARRIER);
+                atomicExch(S.gbar + 1, 1u);
+                ok = 0;
+                break;
+            }
+        }
+        __threadfence();
+        *ok_sh = ok;
+    }
+    __syncthreads();
+    return *ok_sh != 0;
+}
+
+__global__ void __launch_bounds__(256) k_lgc_fit(LgState S, int t1, int tau0, int par0, unsigned base) {
+    __shared__ float ss[kLargeMaxK];
+    __shared__ int ok_sh;
+    const int b = blockIdx.y;
+    const bool live = S.st[b] < 0;   // fixed during the fit; dead signals still meet every barrier
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned nctas = gridDim.x * gridDim.y;
+    if (threadIdx.x == 0) ok_sh = ld_acquire_u32(S.gbar + 1) == 0u;
+    __syncthreads();
+    if (!ok_sh) return;
+    const size_t o = (size_t)b * S.K;
+    const int stride = 8 * gridDim.x;
+    for (int step = 0; step < S.steps; ++step) {
+        const float* s_in = (((par0 + step) & 1) == 0 ? S.s0 : S.s1) + o;
+        float* s_out = (((par0 + step) & 1) == 0 ? S.s1 : S.s0) + o;
+        if (live) {
+            for (int p = threadIdx.x; p < t1; p += blockDim.x) ss[p] = __ldcg(s_in + p);
+            __syncthreads();
+            const float2 cc = S.tab[tau0 + step];
+            for (int q = blockIdx.x * 8 + warp; q < t1; q += stride) {
+                const float* Gq = S.G + (o + q) * S.K;
+                float acc = 0.f;
+                for (int p0 = 0; p0 < t1; p0 += 256) {
+                    float gv[8], sv[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int p = p0 + lane + 32 * u;
+                        gv[u] = p < t1 ? Gq[p] : 0.f;
+                        sv[u] = p < t1 ? ss[p] : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) acc = fmaf(gv[u], sv[u], acc);
+                }
+                const float g = warp_sum(acc) - S.bv[o + q];
+                if (lane == 0) {
+                    const float mo = fmaf(S.beta1, S.am[o + q], (1.f - S.beta1) * g);
+                    const float ve = fmaf(S.beta2, S.av[o + q], (1.f - S.beta2) * g * g);
+                    S.am[o + q] = mo;
+                    S.av[o + q] = ve;
+                    const float sn = ss[q] - cc.x * mo / fmaf(sqrtf(ve), cc.y, S.eps);
+                    s_out[q] = sn;
+                    if (step + 1 == S.steps) S.xf[o + q] = sn;
+                }
+            }
+        }
+        if (step + 1 < S.steps && !lg_grid_barrier(S, base + (unsigned)(step + 1) * nctas, &ok_sh)) return;
+    }
+}
+
 // ----------------------------------------------------------- residual --
 // Partial sums sum_{q in chunk} a_{S_q}[i] x_q over chunks of 128 atoms
 // (one thread per row i).
@@ -682,7 +779,7 @@ __global__ void k_lg_out(LgState S) {
 
 struct LgLayout {
     size_t A16, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
-        xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, G, bv, s0, s1, am, av, total;
+        xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, G, bv, s0, s1, am, av, gbar, total;
 };
 
 // cl: CLOMP's Gram-form state instead of OMP's float64 W = L^{-T}.
@@ -736,6 +833,7 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
         L.s1 = take(sizeof(float) * B * K);
         L.am = take(sizeof(float) * B * K);
         L.av = take(sizeof(float) * B * K);
+        L.gbar = take(2 * sizeof(unsigned));
     }
     L.total = off;
     return L;
@@ -850,7 +948,9 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         S.s1 = reinterpret_cast<float*>(w + L.s1);
         S.am = reinterpret_cast<float*>(w + L.am);
         S.av = reinterpret_cast<float*>(w + L.av);
+        S.gbar = reinterpret_cast<unsigned*>(w + L.gbar);
     }
+    S.errflag = call.errflag;
     S.z = reinterpret_cast<double*>(w + L.z);
     S.x = reinterpret_cast<double*>(w + L.x);
     S.xf = reinterpret_cast<float*>(w + L.xf);
@@ -930,6 +1030,19 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     S.nb = 1 << (cfg >> 1);
     int* live_h = call.live_host;
     int s_parity = 0;   // CLOMP: which buffer holds the current coefficients
+    // CLOMP: the most CTAs of the cooperative fit that can be resident at once
+    // (0: no cooperative launch here), and the barrier counter so far
+    int coop_max = 0;
+    unsigned gbar_base = 0;
+    if (cl) {
+        int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+        LG_TRY(cudaGetDevice(&dev));
+        LG_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
+        LG_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
+        LG_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lgc_fit, 256, 0));
+        coop_max = coop ? nsm * per_sm : 0;
+        LG_TRY(cudaMemsetAsync(S.gbar, 0, 2 * sizeof(unsigned), s));
+    }
     for (int it = 0; it < iters; ++it) {
         const int t = it;
         mark(CS_PHASE_CORR, 0);
@@ -943,10 +1056,19 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         mark(CS_PHASE_SELECT, 1);
         mark(CS_PHASE_FIT, 0);
         if (cl) {
-            // Gram form: grow G and b, then the T Adam steps on t + 1 coordinates
+            // Gram form: grow G and b, then the T Adam steps on t + 1 coordinates,
+            // in one cooperative launch where the grid fits, else one launch per step
             k_lgc_append<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t);
             const int tau0 = S.reset ? 0 : t * S.steps;
-            for (int step = 0; step < S.steps; ++step) {
+            const int gx = std::min(ceil_div(t + 1, 8), coop_max / Bl);
+            if (S.steps > 0 && gx >= 1) {
+                int t1 = t + 1, par0 = s_parity;
+                unsigned base = gbar_base;
+                void* args[] = {&S, &t1, const_cast<int*>(&tau0), &par0, &base};
+                LG_TRY(cudaLaunchCooperativeKernel((const void*)k_lgc_fit, dim3(gx, Bl), dim3(256), args, 0, s));
+                gbar_base += (unsigned)(gx * Bl) * (unsigned)(S.steps - 1);
+                s_parity ^= S.steps & 1;
+            } else for (int step = 0; step < S.steps; ++step) {
                 const float* sin = (s_parity == 0) ? S.s0 : S.s1;
                 float* sout = (s_parity == 0) ? S.s1 : S.s0;
                 k_lgc_step<<<dim3(ceil_div(t + 1, 8), Bl), 256, 0, s>>>(S, t + 1, tau0 + step + 1, sin, sout,

@@ -133,7 +133,36 @@ def test_large_path_clomp_matches_oracle(cs_gpu, torch, prec, m, n, B, k, snr):
     g = to_numpy(r)
     ln = {ph: v[0] for ph, v in plan.profile(reset=True).items()}
     assert ln["persist"] == 0 and ln["update"] == 0 and ln["correlation"] == k
+    assert plan.counters(reset=True)[1] == 0
     print(prec, m, n, B, k, compare(g, _oracle_clomp(A64, Y64, k)))
+
+
+def test_large_path_clomp_reset_adam(cs_gpu, torch):
+    """reset_adam_each_iter on the large-instance path: the moments and the
+    step counter restart at every iteration."""
+    p = workloads.random_problem(1100, 2000, 3, 40, seed=77, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    r = cs_gpu.clomp_solve_batched(torch.from_numpy(np.asfortranarray(A32)).cuda(),
+                                   torch.from_numpy(np.asfortranarray(Y32)).cuda(), 40, form="gram",
+                                   plan=cs_gpu.Plan(1100, 2000, 3, 40), steps=50, lr=1e-2, reset_adam=True)
+    torch.cuda.synchronize()
+    print(compare(to_numpy(r), _oracle_clomp(A64, Y64, 40, reset_adam=True)))
+
+
+def test_large_path_clomp_many_signals(cs_gpu, torch):
+    """More signals than the fit's cooperative launch can hold resident
+    (1300 > 152 SMs x 8 CTAs): the fit runs one launch per Adam step; the
+    results still match the oracle."""
+    m, n, B, k = 1100, 1200, 1300, 3
+    p = workloads.random_problem(m, n, B, k, seed=78, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    plan = cs_gpu.Plan(m, n, B, k)
+    r = cs_gpu.clomp_solve_batched(torch.from_numpy(np.asfortranarray(A32)).cuda(),
+                                   torch.from_numpy(np.asfortranarray(Y32)).cuda(), k, form="gram",
+                                   plan=plan, steps=50, lr=1e-2)
+    torch.cuda.synchronize()
+    assert plan.counters(reset=True)[1] == 0
+    print(compare(to_numpy(r), _oracle_clomp(A64, Y64, k)))
 
 
 def test_large_path_clomp_refusals(cs_gpu, torch):
