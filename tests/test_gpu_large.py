@@ -139,14 +139,20 @@ def test_large_path_clomp_matches_oracle(cs_gpu, torch, prec, m, n, B, k, snr):
 
 def test_large_path_clomp_reset_adam(cs_gpu, torch):
     """reset_adam_each_iter on the large-instance path: the moments and the
-    step counter restart at every iteration."""
+    step counter restart at every iteration.  Supports identical; the
+    coefficients within 1e-3, not 1e-5: every restart's first steps move each
+    coordinate by about lr sign(g), and for coordinates already at their
+    optimum g is at float32 rounding level, so its sign is noise.  The same
+    steps in numpy float32 differ from the FP64 oracle by 2.6e-4 to 3.4e-4
+    here (in float64 by 1e-13); without the reset the moments keep these
+    steps small (2e-7)."""
     p = workloads.random_problem(1100, 2000, 3, 40, seed=77, snr_db=30.0, values="pm")
     A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
     r = cs_gpu.clomp_solve_batched(torch.from_numpy(np.asfortranarray(A32)).cuda(),
                                    torch.from_numpy(np.asfortranarray(Y32)).cuda(), 40, form="gram",
                                    plan=cs_gpu.Plan(1100, 2000, 3, 40), steps=50, lr=1e-2, reset_adam=True)
     torch.cuda.synchronize()
-    print(compare(to_numpy(r), _oracle_clomp(A64, Y64, 40, reset_adam=True)))
+    print(compare(to_numpy(r), _oracle_clomp(A64, Y64, 40, reset_adam=True), coef_rtol=1e-3))
 
 
 def test_large_path_clomp_many_signals(cs_gpu, torch):
