@@ -35,6 +35,7 @@
 // so the atom whose re-scored |c| is largest has |c~| >= max|c~| - 2 delta.
 // The float32 path drops the 2^-8 term.
 #include <algorithm>
+#include <map>
 #include <vector>
 
 #include "k_common.cuh"
@@ -97,12 +98,13 @@ struct LgState {
     const float2* tab;              // Adam factor pairs for tau = 1, 2, ...
     float* G;                       // [Bl][K][K]
     float* bv;                      // [Bl][K]
-    float* s0;                      // [Bl][K]
-    float* s1;                      // [Bl][K]
+    // s as tagged words (tag << 32 | float bits), two buffers: the value of
+    // Adam step number `tag` of the solve sits in buffer tag & 1
+    unsigned long long* s0;         // [Bl][K]
+    unsigned long long* s1;         // [Bl][K]
     float* am;                      // [Bl][K]
     float* av;                      // [Bl][K]
-    unsigned* gbar;                 // [2] arrivals at the fit's grid-wide barriers, and the give-up
-                                    // word (both this solve's)
+    unsigned* gbar;                 // [1] the solve's give-up word (a fit's wait ran out)
     unsigned* errflag;              // device error flags
 };
 
@@ -518,10 +520,15 @@ __global__ void __launch_bounds__(256) k_lg_update(LgState S, int t) {
 }
 
 // ------------------------------------------------------ CLOMP Gram fit --
+__device__ __forceinline__ unsigned long long lg_tagged(unsigned tag, float v) {
+    return ((unsigned long long)tag << 32) | __float_as_uint(v);
+}
+
 // Append the new atom to the Gram form: row and column t of G from the Gram
-// column, G_tt = ||a_j||^2, b_t = a_j^T y; the new coefficient and its
-// moments start at zero (with reset_adam_each_iter every moment restarts).
-__global__ void __launch_bounds__(256) k_lgc_append(LgState S, int t) {
+// column, G_tt = ||a_j||^2, b_t = a_j^T y; the new coefficient (zero, with
+// the fit's first tag) and its moments start at zero (with
+// reset_adam_each_iter every moment restarts).
+__global__ void __launch_bounds__(256) k_lgc_append(LgState S, int t, unsigned tag0) {
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -539,8 +546,7 @@ __global__ void __launch_bounds__(256) k_lgc_append(LgState S, int t) {
     } else {
         G[(size_t)t * S.K + t] = g[t];
         S.bv[o + t] = g[t + 1];
-        S.s0[o + t] = 0.f;
-        S.s1[o + t] = 0.f;
+        ((tag0 & 1u) ? S.s1 : S.s0)[o + t] = lg_tagged(tag0, 0.f);
         S.am[o + t] = 0.f;
         S.av[o + t] = 0.f;
         S.xf[o + t] = 0.f;
@@ -548,136 +554,193 @@ __global__ void __launch_bounds__(256) k_lgc_append(LgState S, int t) {
     }
 }
 
-// One Adam step of every live signal on its t1 coordinates (one warp per
-// coordinate q): the gradient (G s - b)_q of 1/2 ||y - A_S s||^2 from
-// s_in, the moments, and s_out[q] (PyTorch's update rule, step tau).  The
-// last step of a fit also writes the coefficients used by the residual.
-__global__ void __launch_bounds__(256) k_lgc_step(LgState S, int t1, int tau, const float* __restrict__ s_in,
-                                                  float* __restrict__ s_out, int last) {
-    const int b = blockIdx.y;
-    if (S.st[b] >= 0) return;
-    const int lane = threadIdx.x & 31;
-    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (q >= t1) return;
-    const size_t o = (size_t)b * S.K;
-    const float* Gq = S.G + (o + q) * S.K;
-    const float* sb = s_in + o;
+// (G s - b)_q by one warp, lane-strided with eight entries in flight per
+// lane, ascending; Gq and sv may sit in global or shared memory.
+__device__ __forceinline__ float lg_gram_row_dot(const float* Gq, const float* sv, int t1, int lane) {
     float acc = 0.f;
-    for (int p0 = 0; p0 < t1; p0 += 256) {     // eight entries per lane in flight, ascending
-        float gv[8], sv[8];
+    for (int p0 = 0; p0 < t1; p0 += 256) {
+        float gv[8], xv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int p = p0 + lane + 32 * u;
             gv[u] = p < t1 ? Gq[p] : 0.f;
-            sv[u] = p < t1 ? sb[p] : 0.f;
+            xv[u] = p < t1 ? sv[p] : 0.f;
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc = fmaf(gv[u], sv[u], acc);
+        for (int u = 0; u < 8; ++u) acc = fmaf(gv[u], xv[u], acc);
     }
-    const float g = warp_sum(acc) - S.bv[o + q];
+    return warp_sum(acc);
+}
+
+// Adam on one coordinate (PyTorch's update rule; cc = the step's factors)
+__device__ __forceinline__ float lg_adam(const LgState& S, float g, float s_q, float2 cc, float& mo, float& ve) {
+    mo = fmaf(S.beta1, mo, (1.f - S.beta1) * g);
+    ve = fmaf(S.beta2, ve, (1.f - S.beta2) * g * g);
+    return s_q - cc.x * mo / fmaf(sqrtf(ve), cc.y, S.eps);
+}
+
+// One Adam step of every live signal on its t1 coordinates (one warp per
+// coordinate q): reads s of step `tag` (stream order makes it complete),
+// writes step tag + 1.  The last step of a fit also writes the coefficients
+// used by the residual.
+__global__ void __launch_bounds__(256) k_lgc_step(LgState S, int t1, int tau, unsigned tag, int last) {
+    __shared__ float ss[kLargeMaxK];
+    const int b = blockIdx.y;
+    if (S.st[b] >= 0) return;
+    const size_t o = (size_t)b * S.K;
+    const unsigned long long* in = ((tag & 1u) ? S.s1 : S.s0) + o;
+    unsigned long long* out = (((tag + 1u) & 1u) ? S.s1 : S.s0) + o;
+    for (int p = threadIdx.x; p < t1; p += blockDim.x) ss[p] = __uint_as_float((unsigned)in[p]);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int q = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (q >= t1) return;
+    const float g = lg_gram_row_dot(S.G + (o + q) * S.K, ss, t1, lane) - S.bv[o + q];
     if (lane == 0) {
-        const float2 cc = S.tab[tau - 1];
-        const float mo = fmaf(S.beta1, S.am[o + q], (1.f - S.beta1) * g);
-        const float ve = fmaf(S.beta2, S.av[o + q], (1.f - S.beta2) * g * g);
+        float mo = S.am[o + q], ve = S.av[o + q];
+        const float sn = lg_adam(S, g, ss[q], S.tab[tau - 1], mo, ve);
         S.am[o + q] = mo;
         S.av[o + q] = ve;
-        const float sn = sb[q] - cc.x * mo / fmaf(sqrtf(ve), cc.y, S.eps);
-        s_out[o + q] = sn;
+        out[q] = lg_tagged(tag + 1u, sn);
         if (last) S.xf[o + q] = sn;
     }
 }
 
 // All T Adam steps of one iteration in one cooperative launch (every CTA
-// resident): CTA (x, b) serves signal b, its warps the coordinates
-// q = x * 8 + warp + i * 8 * gridDim.x, the same ones at every step.  Per
-// step the CTA stages s_in of its signal in shared memory (read through L2:
-// other CTAs wrote it), each warp forms (G s - b)_q in the order of
-// k_lgc_step and lane 0 makes the same Adam update; then a grid-wide barrier
-// (bounded wait; on time-out the error flags get bit 32, the solve's give-up
-// word is set and every CTA of this and later fits of the solve returns).  The barrier counter only grows within a solve: the j-th barrier
-// of this launch is passed once it holds base + (j + 1) * (CTAs).
+// resident).  CTA (x, b) owns the rows q0 = x R .. q0 + R - 1 of signal b's G,
+// copied to shared memory once, with their moments and b_q.  Per step it
+// waits for all t1 words of s carrying the step's tag (each written, value
+// and tag in one 64-bit store, by the CTA that owns the coordinate), stages
+// the values, forms its rows of G s - b in the order of k_lgc_step and
+// writes the new values with the next tag into the other buffer.  No CTA can
+// overwrite a word another still has to read: writing step j + 2 needs all of
+// step j + 1, which each CTA writes only after reading all of step j.  Waits
+// are bounded; on time-out the error flags get bit 32, the solve's give-up
+// word is set, and every CTA of this and later fits of the solve returns.
 constexpr unsigned long long LG_WAIT_CYCLES = 4000000000ull;   // ~2 s at 2 GHz
-constexpr unsigned LG_ERR_BARRIER = 32u;
+constexpr unsigned LG_ERR_WAIT = 32u;
 
 __device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
     unsigned v;
     asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
-
-// false: the wait gave up (or another CTA's did)
-__device__ bool lg_grid_barrier(const LgState& S, unsigned target, int* ok_sh) {
-    __syncthreads();
-    if (threadIdx.x == 0) {
-        __threadfence();
-        atomicAdd(S.gbar, 1u);
-        int ok = 1;
-        const unsigned long long t0 = clock64();
-        while ((int)(ld_acquire_u32(S.gbar) - target) < 0) {
-            if (ld_acquire_u32(S.gbar + 1) != 0u) {
-                ok = 0;
-                break;
-            }
-            if (clock64() - t0 > LG_WAIT_CYCLES) {
-                atomicOr(S.errflag, LG_ERR_BARRIER);
-                atomicExch(S.gbar + 1, 1u);
-                ok = 0;
-                break;
-            }
-        }
-        __threadfence();
-        *ok_sh = ok;
-    }
-    __syncthreads();
-    return *ok_sh != 0;
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-__global__ void __launch_bounds__(256) k_lgc_fit(LgState S, int t1, int tau0, int par0, unsigned base) {
-    __shared__ float ss[kLargeMaxK];
-    __shared__ int ok_sh;
+// Wait until *p carries `tag` (v: the last value read); false on give-up.
+__device__ bool lg_wait_tag(const LgState& S, const unsigned long long* p, unsigned tag, unsigned long long& v) {
+    const unsigned long long t0 = clock64();
+    unsigned spins = 0;
+    while ((unsigned)(v >> 32) != tag) {
+        if ((++spins & 63u) == 0u) {
+            if (ld_acquire_u32(S.gbar) != 0u) return false;
+            if (clock64() - t0 > LG_WAIT_CYCLES) {
+                atomicOr(S.errflag, LG_ERR_WAIT);
+                atomicExch(S.gbar, 1u);
+                return false;
+            }
+        }
+        v = ld_relaxed_u64(p);
+    }
+    return true;
+}
+
+// Shared memory of k_lgc_fit in floats: s, the moments and b of R rows, and
+// the R rows of G (t1 rounded up to 4 per row, for 16-byte copies).
+__host__ __device__ constexpr int lg_fit_smem_floats(int t1, int R) {
+    return (t1 + 3) / 4 * 4 * (R + 1) + 3 * R;
+}
+
+__global__ void __launch_bounds__(256) k_lgc_fit(LgState S, int t1, int R, int tau0, unsigned tag0) {
+    extern __shared__ __align__(16) float fsh[];
+    __shared__ int go;
+    const int t1p = (t1 + 3) / 4 * 4;
+    float* ss = fsh;                 // [t1p] s of the step
+    float* ams = ss + t1p;           // [R] moments and b of the CTA's rows
+    float* avs = ams + R;
+    float* bvs = avs + R;
+    float* Gs = bvs + R;             // [R][t1p] (16-byte aligned: t1p and 3 R are multiples of 4)
     const int b = blockIdx.y;
-    const bool live = S.st[b] < 0;   // fixed during the fit; dead signals still meet every barrier
+    if (S.st[b] >= 0) return;        // no CTA of a finished signal is waited for
+    const int q0 = blockIdx.x * R, nr = min(R, t1 - q0);
+    if (nr <= 0) return;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const unsigned nctas = gridDim.x * gridDim.y;
-    if (threadIdx.x == 0) ok_sh = ld_acquire_u32(S.gbar + 1) == 0u;
-    __syncthreads();
-    if (!ok_sh) return;
     const size_t o = (size_t)b * S.K;
-    const int stride = 8 * gridDim.x;
+    if (threadIdx.x == 0) go = ld_acquire_u32(S.gbar) == 0u;
+    __syncthreads();
+    if (!go) return;
+    // the rows (16-byte copies, eight in flight per lane; G's rows are K
+    // floats apart, K a multiple of 32, and t1p <= K)
+    for (int r = warp; r < nr; r += blockDim.x >> 5) {
+        const float4* src = reinterpret_cast<const float4*>(S.G + (o + q0 + r) * S.K);
+        float4* dst = reinterpret_cast<float4*>(Gs + (size_t)r * t1p);
+        const int n4 = t1p / 4;
+        for (int c0 = 0; c0 < n4; c0 += 256) {
+            float4 v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + lane + 32 * u;
+                if (c < n4) v[u] = src[c];
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int c = c0 + lane + 32 * u;
+                if (c < n4) dst[c] = v[u];
+            }
+        }
+    }
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        ams[r] = S.am[o + q0 + r];
+        avs[r] = S.av[o + q0 + r];
+        bvs[r] = S.bv[o + q0 + r];
+    }
     for (int step = 0; step < S.steps; ++step) {
-        const float* s_in = (((par0 + step) & 1) == 0 ? S.s0 : S.s1) + o;
-        float* s_out = (((par0 + step) & 1) == 0 ? S.s1 : S.s0) + o;
-        if (live) {
-            for (int p = threadIdx.x; p < t1; p += blockDim.x) ss[p] = __ldcg(s_in + p);
-            __syncthreads();
-            const float2 cc = S.tab[tau0 + step];
-            for (int q = blockIdx.x * 8 + warp; q < t1; q += stride) {
-                const float* Gq = S.G + (o + q) * S.K;
-                float acc = 0.f;
-                for (int p0 = 0; p0 < t1; p0 += 256) {
-                    float gv[8], sv[8];
+        const unsigned tag = tag0 + (unsigned)step;
+        const unsigned long long* in = ((tag & 1u) ? S.s1 : S.s0) + o;
+        unsigned long long* out = (((tag + 1u) & 1u) ? S.s1 : S.s0) + o;
+        bool ok = true;
+        for (int p0 = 0; p0 < t1 && ok; p0 += 8 * blockDim.x) {
+            unsigned long long v[8];
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int p = p0 + lane + 32 * u;
-                        gv[u] = p < t1 ? Gq[p] : 0.f;
-                        sv[u] = p < t1 ? ss[p] : 0.f;
-                    }
+            for (int u = 0; u < 8; ++u) {
+                const int p = p0 + threadIdx.x + u * blockDim.x;
+                v[u] = p < t1 ? ld_relaxed_u64(in + p) : 0ull;
+            }
 #pragma unroll
-                    for (int u = 0; u < 8; ++u) acc = fmaf(gv[u], sv[u], acc);
-                }
-                const float g = warp_sum(acc) - S.bv[o + q];
-                if (lane == 0) {
-                    const float mo = fmaf(S.beta1, S.am[o + q], (1.f - S.beta1) * g);
-                    const float ve = fmaf(S.beta2, S.av[o + q], (1.f - S.beta2) * g * g);
-                    S.am[o + q] = mo;
-                    S.av[o + q] = ve;
-                    const float sn = ss[q] - cc.x * mo / fmaf(sqrtf(ve), cc.y, S.eps);
-                    s_out[q] = sn;
-                    if (step + 1 == S.steps) S.xf[o + q] = sn;
+            for (int u = 0; u < 8; ++u) {
+                const int p = p0 + threadIdx.x + u * blockDim.x;
+                if (p < t1 && ok) {
+                    ok = lg_wait_tag(S, in + p, tag, v[u]);
+                    ss[p] = __uint_as_float((unsigned)v[u]);
                 }
             }
         }
-        if (step + 1 < S.steps && !lg_grid_barrier(S, base + (unsigned)(step + 1) * nctas, &ok_sh)) return;
+        if (__syncthreads_or(!ok)) return;
+        const float2 cc = S.tab[tau0 + step];
+        for (int r = warp; r < nr; r += blockDim.x >> 5) {
+            const int q = q0 + r;
+            const float g = lg_gram_row_dot(Gs + (size_t)r * t1p, ss, t1, lane) - bvs[r];
+            if (lane == 0) {
+                float mo = ams[r], ve = avs[r];
+                const float sn = lg_adam(S, g, ss[q], cc, mo, ve);
+                ams[r] = mo;
+                avs[r] = ve;
+                st_relaxed_u64(out + q, lg_tagged(tag + 1u, sn));
+                if (step + 1 == S.steps) S.xf[o + q] = sn;
+            }
+        }
+        __syncthreads();
+    }
+    for (int r = threadIdx.x; r < nr; r += blockDim.x) {
+        S.am[o + q0 + r] = ams[r];
+        S.av[o + q0 + r] = avs[r];
     }
 }
 
@@ -829,11 +892,11 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
     if (cl) {
         L.G = take(sizeof(float) * B * K * K);
         L.bv = take(sizeof(float) * B * K);
-        L.s0 = take(sizeof(float) * B * K);
-        L.s1 = take(sizeof(float) * B * K);
+        L.s0 = take(sizeof(unsigned long long) * B * K);
+        L.s1 = take(sizeof(unsigned long long) * B * K);
         L.am = take(sizeof(float) * B * K);
         L.av = take(sizeof(float) * B * K);
-        L.gbar = take(2 * sizeof(unsigned));
+        L.gbar = take(sizeof(unsigned));
     }
     L.total = off;
     return L;
@@ -944,8 +1007,8 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         S.tab = call.cl->tab;
         S.G = reinterpret_cast<float*>(w + L.G);
         S.bv = reinterpret_cast<float*>(w + L.bv);
-        S.s0 = reinterpret_cast<float*>(w + L.s0);
-        S.s1 = reinterpret_cast<float*>(w + L.s1);
+        S.s0 = reinterpret_cast<unsigned long long*>(w + L.s0);
+        S.s1 = reinterpret_cast<unsigned long long*>(w + L.s1);
         S.am = reinterpret_cast<float*>(w + L.am);
         S.av = reinterpret_cast<float*>(w + L.av);
         S.gbar = reinterpret_cast<unsigned*>(w + L.gbar);
@@ -1029,20 +1092,40 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     if (call.chosen_cfg) *call.chosen_cfg = cfg;
     S.nb = 1 << (cfg >> 1);
     int* live_h = call.live_host;
-    int s_parity = 0;   // CLOMP: which buffer holds the current coefficients
-    // CLOMP: the most CTAs of the cooperative fit that can be resident at once
-    // (0: no cooperative launch here), and the barrier counter so far
-    int coop_max = 0;
-    unsigned gbar_base = 0;
+    // CLOMP: the device's limits for the cooperative fit, the CTAs of it that
+    // fit an SM per shared-memory size (cached), and the tag of the next step
+    int coop = 0, nsm = 0, smem_optin = 0;
+    std::map<int, int> per_sm;
+    unsigned tag = 0;
     if (cl) {
-        int dev = 0, coop = 0, nsm = 0, per_sm = 0;
+        int dev = 0;
         LG_TRY(cudaGetDevice(&dev));
         LG_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         LG_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
-        LG_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_lgc_fit, 256, 0));
-        coop_max = coop ? nsm * per_sm : 0;
-        LG_TRY(cudaMemsetAsync(S.gbar, 0, 2 * sizeof(unsigned), s));
+        LG_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        LG_TRY(cudaFuncSetAttribute(k_lgc_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
+        LG_TRY(cudaMemsetAsync(S.s0, 0, sizeof(unsigned long long) * Bl * S.K, s));
+        LG_TRY(cudaMemsetAsync(S.s1, 0, sizeof(unsigned long long) * Bl * S.K, s));
+        LG_TRY(cudaMemsetAsync(S.gbar, 0, sizeof(unsigned), s));
     }
+    // rows per CTA of the cooperative fit at t1 coordinates (0: it does not fit)
+    auto fit_rows = [&](int t1, int& gx, int& smem) -> int {
+        if (!coop || S.steps <= 0) return 0;
+        for (int R = 8; R <= round_up(t1, 8); R *= 2) {
+            smem = (int)sizeof(float) * lg_fit_smem_floats(t1, R);
+            if (smem > smem_optin) return 0;
+            const int key = round_up(smem, 1024);
+            auto f = per_sm.find(key);
+            if (f == per_sm.end()) {
+                int v = 0;
+                if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&v, k_lgc_fit, 256, key) != cudaSuccess) v = 0;
+                f = per_sm.emplace(key, v).first;
+            }
+            gx = ceil_div(t1, R);
+            if ((long long)gx * Bl <= (long long)nsm * f->second) return R;
+        }
+        return 0;
+    };
     for (int it = 0; it < iters; ++it) {
         const int t = it;
         mark(CS_PHASE_CORR, 0);
@@ -1058,23 +1141,23 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         if (cl) {
             // Gram form: grow G and b, then the T Adam steps on t + 1 coordinates,
             // in one cooperative launch where the grid fits, else one launch per step
-            k_lgc_append<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t);
+            k_lgc_append<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t, tag);
             const int tau0 = S.reset ? 0 : t * S.steps;
-            const int gx = std::min(ceil_div(t + 1, 8), coop_max / Bl);
-            if (S.steps > 0 && gx >= 1) {
-                int t1 = t + 1, par0 = s_parity;
-                unsigned base = gbar_base;
-                void* args[] = {&S, &t1, const_cast<int*>(&tau0), &par0, &base};
-                LG_TRY(cudaLaunchCooperativeKernel((const void*)k_lgc_fit, dim3(gx, Bl), dim3(256), args, 0, s));
-                gbar_base += (unsigned)(gx * Bl) * (unsigned)(S.steps - 1);
-                s_parity ^= S.steps & 1;
-            } else for (int step = 0; step < S.steps; ++step) {
-                const float* sin = (s_parity == 0) ? S.s0 : S.s1;
-                float* sout = (s_parity == 0) ? S.s1 : S.s0;
-                k_lgc_step<<<dim3(ceil_div(t + 1, 8), Bl), 256, 0, s>>>(S, t + 1, tau0 + step + 1, sin, sout,
-                                                                       step + 1 == S.steps ? 1 : 0);
-                s_parity ^= 1;
+            int gx = 0, smem = 0;
+            const int R = fit_rows(t + 1, gx, smem);
+            if (R > 0) {
+                int t1 = t + 1, r = R, tz = tau0;
+                unsigned tg = tag;
+                void* args[] = {&S, &t1, &r, &tz, &tg};
+                LG_TRY(cudaLaunchCooperativeKernel((const void*)k_lgc_fit, dim3(gx, Bl), dim3(256), args,
+                                                   (size_t)smem, s));
+            } else {
+                for (int step = 0; step < S.steps; ++step)
+                    k_lgc_step<<<dim3(ceil_div(t + 1, 8), Bl), 256, 0, s>>>(S, t + 1, tau0 + step + 1,
+                                                                           tag + (unsigned)step,
+                                                                           step + 1 == S.steps ? 1 : 0);
             }
+            tag += (unsigned)S.steps;
         } else {
             if (t > 0) k_lg_lpart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
             k_lg_pivot<<<Bl, 1024, 0, s>>>(S, t);
