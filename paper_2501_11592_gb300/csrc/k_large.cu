@@ -1103,6 +1103,9 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         LG_TRY(cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev));
         LG_TRY(cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev));
         LG_TRY(cudaDeviceGetAttribute(&smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+        cudaFuncAttributes fa{};
+        LG_TRY(cudaFuncGetAttributes(&fa, k_lgc_fit));
+        smem_optin -= (int)fa.sharedSizeBytes;   // the dynamic part's limit
         LG_TRY(cudaFuncSetAttribute(k_lgc_fit, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_optin));
         LG_TRY(cudaMemsetAsync(S.s0, 0, sizeof(unsigned long long) * Bl * S.K, s));
         LG_TRY(cudaMemsetAsync(S.s1, 0, sizeof(unsigned long long) * Bl * S.K, s));
