@@ -634,26 +634,42 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
-// Wait until *p carries `tag` (v: the last value read); false on give-up.
-__device__ bool lg_wait_tag(const LgState& S, const unsigned long long* p, unsigned tag, unsigned long long& v) {
+// Stage s of step `tag` (t1 words from `in`) in ss: every thread polls its
+// words (up to eight per round, all re-read together) until each carries the
+// tag; false on give-up (time-out here, or another CTA's).
+__device__ bool lg_stage_tagged(const LgState& S, const unsigned long long* in, unsigned tag, int t1, float* ss) {
     const unsigned long long t0 = clock64();
     unsigned spins = 0;
-    while ((unsigned)(v >> 32) != tag) {
-        if ((++spins & 63u) == 0u) {
-            if (ld_acquire_u32(S.gbar) != 0u) return false;
-            if (clock64() - t0 > LG_WAIT_CYCLES) {
-                atomicOr(S.errflag, LG_ERR_WAIT);
-                atomicExch(S.gbar, 1u);
-                return false;
+    for (int p0 = 0; p0 < t1; p0 += 8 * blockDim.x) {
+        unsigned pending = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+            if (p0 + (int)threadIdx.x + u * (int)blockDim.x < t1) pending |= 1u << u;
+        while (pending != 0u) {
+            unsigned long long v[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                v[u] = (pending >> u) & 1u ? ld_relaxed_u64(in + p0 + threadIdx.x + u * blockDim.x) : 0ull;
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                if (((pending >> u) & 1u) && (unsigned)(v[u] >> 32) == tag) {
+                    ss[p0 + threadIdx.x + u * blockDim.x] = __uint_as_float((unsigned)v[u]);
+                    pending &= ~(1u << u);
+                }
+            }
+            if (pending != 0u && (++spins & 15u) == 0u) {
+                if (ld_acquire_u32(S.gbar) != 0u) return false;
+                if (clock64() - t0 > LG_WAIT_CYCLES) {
+                    atomicOr(S.errflag, LG_ERR_WAIT);
+                    atomicExch(S.gbar, 1u);
+                    return false;
+                }
             }
         }
-        v = ld_relaxed_u64(p);
     }
     return true;
 }
 
-// Shared memory of k_lgc_fit in floats: s, the moments and b of R rows, and
-// the R rows of G (t1 rounded up to 4 per row, for 16-byte copies).
 __host__ __device__ constexpr int lg_fit_smem_floats(int t1, int R) {
     return (t1 + 3) / 4 * 4 * (R + 1) + 3 * R;
 }
@@ -705,23 +721,7 @@ __global__ void __launch_bounds__(256) k_lgc_fit(LgState S, int t1, int R, int t
         const unsigned tag = tag0 + (unsigned)step;
         const unsigned long long* in = ((tag & 1u) ? S.s1 : S.s0) + o;
         unsigned long long* out = (((tag + 1u) & 1u) ? S.s1 : S.s0) + o;
-        bool ok = true;
-        for (int p0 = 0; p0 < t1 && ok; p0 += 8 * blockDim.x) {
-            unsigned long long v[8];
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int p = p0 + threadIdx.x + u * blockDim.x;
-                v[u] = p < t1 ? ld_relaxed_u64(in + p) : 0ull;
-            }
-#pragma unroll
-            for (int u = 0; u < 8; ++u) {
-                const int p = p0 + threadIdx.x + u * blockDim.x;
-                if (p < t1 && ok) {
-                    ok = lg_wait_tag(S, in + p, tag, v[u]);
-                    ss[p] = __uint_as_float((unsigned)v[u]);
-                }
-            }
-        }
+        const bool ok = lg_stage_tagged(S, in, tag, t1, ss);
         if (__syncthreads_or(!ok)) return;
         const float2 cc = S.tab[tau0 + step];
         for (int r = warp; r < nr; r += blockDim.x >> 5) {
