@@ -73,8 +73,9 @@ typedef enum {
     CS_CORR_BF16 = 1,   /* bf16 tensor-core correlation (tcgen05, fp32 accumulate), two
                            best atoms per 16-atom group, fp32 re-score of the 8 best and of
                            every atom the rounding bound cannot rule out (n <= 4096,
-                           m <= 256; plain OMP beyond that runs the large-instance path
-                           with a bf16 copy of A, see omp_solve_batched) */
+                           m <= 256; OMP and Gram-form CLOMP beyond that run the
+                           large-instance path with a bf16 copy of A, see
+                           omp_solve_batched) */
     CS_CORR_FP8 = 2     /* FP8 (E4M3) tensor-core correlation (tcgen05 kind::f8f6f4, fp32
                            accumulate): each column of A scaled by max|a_j| / 448 once per
                            solve, each residual by max|r| / 448 every iteration; the same
@@ -167,12 +168,15 @@ typedef struct {
 typedef struct cs_plan cs_plan;
 
 /* Create a plan on the current CUDA device with workspace for problems up to
- * m_max x n_max (m_max <= 1024), batch_max signals and k_max <= 64
- * iterations.  Allocates the workspace once.  Later calls allocate only
- * when a CLOMP call needs a longer Adam bias-correction table than any
- * earlier call, and on the first use of the host-buffer entry points.
- * Returns CS_EINVAL for non-positive sizes, CS_ENOTSUP for k_max > 64,
- * CS_ENOMEM / CS_ECUDA on allocation failure (then *plan is NULL). */
+ * m_max x n_max (m_max <= 32768), batch_max signals and k_max <= 4096
+ * iterations.  Allocates the on-chip kernels' workspace (for m up to 1024 and
+ * k up to 32 or 64) at once.  Later calls allocate when a CLOMP call needs a
+ * longer Adam bias-correction table than any earlier call, on the first use
+ * of the host-buffer and varlen entry points, and when a solve first needs
+ * the large-instance path (sized for that solve's chunk of signals: at most
+ * about 8 GB plus one signal).  Returns CS_EINVAL for non-positive sizes,
+ * CS_ENOTSUP for k_max > 4096 or m_max > 32768, CS_ENOMEM / CS_ECUDA on
+ * allocation failure (then *plan is NULL). */
 cs_status cs_plan_create(cs_plan** plan, int32_t m_max, int32_t n_max, int32_t batch_max,
                          int32_t k_max);
 
@@ -185,7 +189,13 @@ cs_status cs_plan_destroy(cs_plan* plan);
  * float64 (Gram entries from float32 dot products), triangular solves in
  * float64; correlation and residual in float32 (or bf16 correlation, see prec).
  * Outputs (device, caller-owned): support, coef (k x batch), n_iter, res_norm
- * (||r||_2 at exit), sig_status (batch each).  batch == 0 is a no-op. */
+ * (||r||_2 at exit), sig_status (batch each).  batch == 0 is a no-op.
+ * Problems beyond the on-chip kernels (m > 1024, k above the plan's on-chip
+ * 32 or 64, or bf16 with m > 256 or n > 4096) run the large-instance path:
+ * A streamed from HBM every iteration (bf16 copy or the float32 A), the same
+ * certified selection, float64 W = L^-T updated by grid-wide partial sums;
+ * up to m = 32768 and k = 4096; the call synchronises `stream` every 64
+ * iterations to end early once every signal has stopped. */
 cs_status omp_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
                             const float* Y, int32_t ldy, int32_t batch, int32_t* support,
                             float* coef, int32_t* n_iter, float* res_norm, int32_t* sig_status,
@@ -200,7 +210,14 @@ cs_status omp_solve(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t
 /* Batched CLOMP (Methods, "Coefficients learning on OMP", structure 1): the
  * OMP selection, then `steps` Adam steps on L = 1/2 ||y - A(s .* Mask)||^2
  * per iteration, s starting at zero and persisting across iterations.  coef
- * holds s on the support.  Same layouts and outputs as omp_solve_batched. */
+ * holds s on the support.  Same layouts and outputs as omp_solve_batched.
+ * Beyond the on-chip kernels (the sizes listed at omp_solve_batched) the
+ * large-instance path runs the Gram form with one atom per iteration and no
+ * prior (form CS_CL_GRAM, select_threshold 0 or 1, tv_weight and lv_weight
+ * 0; otherwise CS_ENOTSUP): G = A_S^T A_S and A_S^T y grown by one row per
+ * iteration, all Adam steps of an iteration in one cooperative launch whose
+ * CTAs keep their rows of G on chip and wait for each other's coefficients
+ * (bounded: a wait that runs out sets error flag 32, see cs_plan_counters). */
 cs_status clomp_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n, int32_t lda,
                               const float* Y, int32_t ldy, int32_t batch, int32_t* support,
                               float* coef, int32_t* n_iter, float* res_norm,
@@ -246,14 +263,18 @@ typedef struct {
 } cs_instance;
 
 /* Uneven batches: instances is a HOST array of `count` descriptors.  The
- * call groups the instances that share (A, m, n, lda, k), gathers each
- * group's measurements into a batch, runs the batched solver on it and
- * scatters the outputs back, all on `stream`.  params->k is ignored (each
- * instance has its own).  An instance whose sizes exceed the plan (m > m_max,
- * n > n_max or k > k_max) or the chosen correlation (bf16: m <= 256,
- * n <= 4096) is not solved: its sig_status is set to CS_SIG_UNSUPPORTED
- * (its A is never read) and the call goes on with the others.  Groups larger
- * than batch_max run in chunks.  Device staging for the gather/scatter is
+ * call groups the instances the on-chip kernels take by (A, m, n, lda, k),
+ * gathers each group's measurements into a batch, runs the batched solver on
+ * it and scatters the outputs back; the others run on the large-instance
+ * path grouped by (A, m, n, lda), each with its own k; all on `stream`, one
+ * group after another.  params->k is ignored (each instance has its own).
+ * An instance is not solved -- its sig_status is set to CS_SIG_UNSUPPORTED
+ * (its A is never read) and the call goes on with the others -- when its
+ * sizes exceed the plan (m > m_max, n > n_max or k > k_max), when it needs
+ * the large-instance path and CLOMP is asked for outside the Gram form with
+ * one atom per iteration and no prior, and with the FP8 correlation when it
+ * exceeds the tensor-core sizes (m <= 256, n <= 4096, k within the plan's
+ * on-chip 32 or 64).  Groups larger than batch_max run in chunks.  Device staging for the gather/scatter is
  * allocated on first use.  Malformed instances (NULL pointers, k > m or
  * k > n, lda < m) are argument errors (CS_EINVAL, nothing launched).  The
  * image priors (image_width >= 2 with tv_weight or lv_weight > 0) couple
@@ -363,8 +384,10 @@ cs_status iht_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n,
 /* Synchronise `stream` and copy the plan's device counters to out[0..3]:
  * out[0] = picks where the bf16 candidates did not certify the winner and
  * further atoms (the "suspects") were re-scored in float32; out[1] = device error flags (non-zero
- * when a bounded wait inside a kernel gave up).  reset != 0 zeroes them.
- * Returns CS_ETIMEOUT when out[1] != 0. */
+ * when a bounded wait inside a kernel gave up: 1, 2 the tensor-core
+ * correlation's tile pipeline; 4, 8, 16 the persistent CLOMP solve's roles;
+ * 32 the large-instance CLOMP fit's wait for other CTAs' coefficients).
+ * reset != 0 zeroes them.  Returns CS_ETIMEOUT when out[1] != 0. */
 cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* stream);
 
 /* Batched plain OMP without any device allocation.  The paper has no

@@ -334,8 +334,8 @@ cs_status validate(const cs_plan* P, const float* A, int m, int n, int lda, cons
 
 // Instances the on-chip batched kernels do not take: more rows than a warp
 // holds, a support beyond the plan's on-chip K, or the bf16 correlation
-// outside the tensor-core kernel's sizes.  Plain OMP runs them on the
-// large-instance path.
+// outside the tensor-core kernel's sizes.  OMP and Gram-form CLOMP run them
+// on the large-instance path.
 bool needs_large(const cs_plan* P, int m, int n, int k, int prec) {
     return m > kMaxRowChunks * 128 || k > P->k_max || (prec == CS_CORR_BF16 && !corr_tc_supported(m, n));
 }
@@ -396,8 +396,8 @@ void large_mark(void* vctx, int phase, int after) {
     }
 }
 
-// Plain OMP of signals sharing A on the large-instance path, in chunks whose
-// workspace stays within a few GB.
+// OMP or Gram-form CLOMP of signals sharing A on the large-instance path, in
+// chunks whose workspace stays within a few GB.
 constexpr size_t kLargeChunkBytes = (size_t)8 << 30;
 
 // CLOMP configurations the large-instance path runs: the Gram form, one atom
@@ -422,7 +422,7 @@ cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const s
     int kmax = 1;
     for (const LargeOut& o : outs) kmax = std::max(kmax, o.k);
     if (!large_supported(m, n, kmax))
-        return fail(CS_ENOTSUP, "large OMP supports m <= %d and k <= %d (m=%d k=%d)", kLargeMaxM, kLargeMaxK, m, kmax);
+        return fail(CS_ENOTSUP, "the large-instance path supports m <= %d and k <= %d (m=%d k=%d)", kLargeMaxM, kLargeMaxK, m, kmax);
     const int bf16 = op->prec == CS_CORR_BF16 ? 1 : 0;
     const int clf = cp ? 1 : 0;
     ClArgs cl{};
@@ -483,7 +483,7 @@ cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const s
         cs_status st = ensure_lg(P, need);
         if (st != CS_OK) return st;
         cudaError_t e = large_solve(call, P->lg, P->lg_bytes, s);
-        if (e != cudaSuccess) return cuda_fail(e, "large OMP solve");
+        if (e != cudaSuccess) return cuda_fail(e, "large-instance solve");
         if (call.tune && tk == P->tuned.end() && chosen >= 0) P->tuned[key] = chosen;
     }
     return CS_OK;
@@ -1111,8 +1111,8 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
             return fail(CS_EINVAL, "instance %d: bad sizes m=%d n=%d lda=%d k=%d", i, x.m, x.n, x.lda, x.k);
     }
     // Instances beyond the plan are not solved; those beyond the on-chip
-    // kernels run on the large-instance path (plain OMP), or are not solved
-    // (CLOMP, or sizes beyond that path).
+    // kernels run on the large-instance path (OMP, Gram-form CLOMP), or are
+    // not solved (other CLOMP forms, FP8, or sizes beyond that path).
     auto large = [&](const cs_instance& x) { return needs_large(P, x.m, x.n, x.k, op->prec); };
     auto refused = [&](const cs_instance& x) {
         if (op->prec == CS_CORR_FP8)   // the FP8 correlation has no large-instance form

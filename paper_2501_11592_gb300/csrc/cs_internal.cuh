@@ -24,8 +24,8 @@ constexpr int kTcCandPerTile = 2 * kCorrTcTileN / kTcGroup;   // 32 candidates p
 constexpr int kGramAMax = 4096;      // n up to which A^T A is precomputed per solve
 constexpr int kCorrTcMaxN = 4096;    // candidate merge holds <= 512 per signal
 constexpr int kIhtMaxN = 4096;       // IHT: u = s + t c of a signal in shared memory
-constexpr int kLargeMaxM = 32768;    // large OMP solves: rows (residual staged in shared memory)
-constexpr int kLargeMaxK = 4096;     // large OMP solves: support size (float64 W = L^{-T} in HBM)
+constexpr int kLargeMaxM = 32768;    // large-instance solves: rows (residual staged in shared memory)
+constexpr int kLargeMaxK = 4096;     // large-instance solves: support size (OMP float64 W = L^{-T}, CLOMP G in HBM)
 
 // Candidate slots per signal, enough for either correlation kernel.
 __host__ __device__ inline int cand_slots(int n) {

@@ -1,4 +1,4 @@
-// Plain OMP for instances beyond the on-chip kernels: supports of up to
+// OMP and CLOMP for instances beyond the on-chip kernels: supports of up to
 // kLargeMaxK atoms and measurements of up to kLargeMaxM rows (the flattened
 // images of Results, "Evaluation with synthetic 2D data", solved as one long
 // 1-D signal, and the large members of uneven batches).  A batch of signals
@@ -19,9 +19,14 @@
 //                 dot product split into 2048-row segments summed afterwards
 //                 in segment order;
 //   least squares the float64 update of W = L^{-T} of k_chol.cuh -- l = W^T g,
-//                 pivot, z_t, u = W l, the new column of W, x += z_t w --
+//   (OMP)         pivot, z_t, u = W l, the new column of W, x += z_t w --
 //                 with both products split over the grid into partial sums
 //                 that are added in a fixed order;
+//   CL fit        (CLOMP, Gram form) row t of G = A_S^T A_S and b_t = a_j^T y
+//   (CLOMP)       from the same Gram column, then the T Adam steps on
+//                 1/2 ||y - A_S s||^2 with gradient G s - b, one cooperative
+//                 launch per iteration whose CTAs keep their rows of G in
+//                 shared memory (see k_lgc_fit);
 //   residual      r = y - A_S x (x as float32), partial sums over chunks of
 //                 32 support atoms added in chunk order, ||r|| from per-CTA
 //                 sums added in CTA order, the stopping rule of Eq. 2.
