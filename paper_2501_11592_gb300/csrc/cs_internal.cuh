@@ -197,7 +197,11 @@ cudaError_t launch_corr_tc_dense(const __nv_bfloat16* R16, const __nv_bfloat16* 
 // FP8 tensor-core correlation, dense output C^T[b][j] = sr_b sa_j (R8_b . A8_j).
 cudaError_t launch_corr_tc8_dense(const uint8_t* R8, const uint8_t* A8, const float* sr, const float* sa, int mq,
                                   int B, int n, float* C, int ldc, unsigned* errflag, cudaStream_t s);
+// GA = A^T A from the padded float32 copy (mp <= kMaxRowChunks * 128), each
+// entry bit-identical to the selection's on-the-fly Gram entry
 cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s);
+// T = E^T E of a [n][ep] matrix (any ep that is a multiple of 4)
+cudaError_t launch_gram_tiled(const float* E, int ep, int n, float* T, cudaStream_t s);
 // Total-variation prior (Eq. 5): GA += lambda (Delta D)^T (Delta D), D N x n
 // (ld ldd; nullptr: the identity, N = n); E [n][Ep] and T [n][n] are scratch.
 cudaError_t launch_tv_prior(const float* D, int N, int ldd, int n, float lambda, float* E, int Ep, float* T,

@@ -41,7 +41,7 @@ cudaError_t launch_tv_prior(const float* D, int N, int ldd, int n, float lambda,
     k_tv_diff<<<g1, 256, 0, s>>>(D, N, ldd, n, E, Ep);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    e = launch_gram_A(E, Ep, n, T, s);
+    e = launch_gram_tiled(E, Ep, n, T, s);
     if (e != cudaSuccess) return e;
     const size_t len = (size_t)n * n;
     const int blocks = (int)std::min<size_t>((len + 255) / 256, 4096);

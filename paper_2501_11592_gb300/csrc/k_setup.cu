@@ -38,11 +38,39 @@ __global__ void k_prep_A(const float* __restrict__ A, int lda, int m, int n, int
 }
 
 // Gram matrix of the dictionary, GA = A^T A (n x n, row j = a_j^T A), from
-// the padded float32 copy.  Each thread owns a 4 x 4 block of outputs; the
-// K = m sum is accumulated in 16-term partial sums that are then added, so
-// the rounding error grows with 16 + m/16 rather than with m.
+// the padded float32 copy, each entry in the arithmetic of warp_dots32 (per
+// lane the float4 chunks c * 32 + lane in c order, then the lanes combined
+// in pairs by bit 4, 3, ..., 0 of the lane index).  That is the arithmetic
+// of a Gram entry the selection forms without the table (the same value
+// whatever slot the atom takes, and symmetric), so a solve gives the same
+// bits with or without the table (plans with n_max above kGramAMax have
+// none).  CTA (x, y): rows y * 8 + warp, columns x * 32 + lane; blocks
+// wholly below the diagonal exit, the others write (i, j) and, for j > i,
+// (j, i).
+template <int MCH>
 __global__ void __launch_bounds__(256) k_gram_A(const float* __restrict__ A32, int mp, int n,
                                                 float* __restrict__ GA) {
+    const int i0 = blockIdx.y * 8, j0 = blockIdx.x * 32;
+    if (j0 + 31 < i0) return;
+    const int lane = threadIdx.x & 31;
+    const int i = i0 + (threadIdx.x >> 5);
+    if (i >= n) return;
+    float4 x[MCH];
+    load_row<MCH>(A32 + (size_t)i * mp, mp, x);
+    const int j = j0 + lane;
+    const float g = warp_dots32<MCH>(A32, mp, j < n ? j : -1, x);
+    if (j < n) {
+        GA[(size_t)i * n + j] = g;
+        if (j > i) GA[(size_t)j * n + i] = g;
+    }
+}
+
+// Gram matrix E^T E of another matrix (the TV prior's difference operator):
+// each thread owns a 4 x 4 block of outputs; the K = m sum is accumulated in
+// 16-term partial sums that are then added, so the rounding error grows with
+// 16 + m/16 rather than with m.
+__global__ void __launch_bounds__(256) k_gram_tiled(const float* __restrict__ A32, int mp, int n,
+                                                    float* __restrict__ GA) {
     constexpr int T = 64, BK = 16;
     __shared__ __align__(16) float Ai[BK][T + 4];
     __shared__ __align__(16) float Aj[BK][T + 4];
@@ -284,8 +312,16 @@ cudaError_t launch_prep_R8(const float* R, int ldr, int m, int B, int mq, uint8_
 }
 
 cudaError_t launch_gram_A(const float* A32, int mp, int n, float* GA, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (row_chunks(mp) > kMaxRowChunks) return cudaErrorNotSupported;
+    const dim3 grid(ceil_div(n, 32), ceil_div(n, 8));
+    CS_DISPATCH_MCH(mp, k_gram_A, grid, 256, s, A32, mp, n, GA);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gram_tiled(const float* E, int ep, int n, float* T, cudaStream_t s) {
     const int t = ceil_div(n, 64);
-    k_gram_A<<<t * (t + 1) / 2, 256, 0, s>>>(A32, mp, n, GA);
+    k_gram_tiled<<<t * (t + 1) / 2, 256, 0, s>>>(E, ep, n, T);
     return cudaGetLastError();
 }
 

@@ -221,6 +221,23 @@ def test_graph_replay_matches_eager(cs_gpu, torch, algo):
     assert np.array_equal(fresh["coef"], got[1]["coef"].cpu().numpy())
 
 
+@pytest.mark.parametrize("algo,prec", [("omp", "fp32"), ("omp", "bf16"), ("clomp", "bf16"), ("clomp", "fp32")])
+def test_same_bits_with_and_without_gram_table(cs_gpu, torch, algo, prec):
+    """A plan sized for n <= 4096 keeps A^T A and reads Gram entries from
+    it; a larger plan forms them from the columns.  Both give the same bits
+    (the table is built in the selection's own dot-product arithmetic), and
+    so does the process-wide default plan whatever sizes it grew to."""
+    p = workloads.random_problem(96, 700, 300, 12, seed=64, snr_db=30.0, values="pm")
+    A32, Y32, _, _ = f32_problem(p.A, p.Y)
+    kw = {} if algo == "omp" else dict(form="gram", **CL)
+    small = run_gpu(cs_gpu, torch, A32, Y32, 12, algo, prec=prec, plan=cs_gpu.Plan(96, 700, 300, 12), **kw)
+    big = run_gpu(cs_gpu, torch, A32, Y32, 12, algo, prec=prec, plan=cs_gpu.Plan(96, 5000, 300, 12), **kw)
+    dflt = run_gpu(cs_gpu, torch, A32, Y32, 12, algo, prec=prec, **kw)
+    for q in ("support", "coef", "n_iter", "res_norm", "status"):
+        assert np.array_equal(small[q], big[q]), q
+        assert np.array_equal(small[q], dflt[q]), q
+
+
 def test_fused_update_matches_separate_kernels(cs_gpu, torch):
     """The fused CLOMP update (selection + fit + residual in one kernel) runs
     the same per-signal arithmetic as the three separate kernels."""
