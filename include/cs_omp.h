@@ -474,7 +474,7 @@ enum { CS_OPT_GRAPHS = 0, CS_OPT_FUSE_UPDATE = 1, CS_OPT_PERSIST = 2, CS_OPT_STA
  * (kernel, correlation precision, m, n, batch) times the candidate
  * configurations of its tunable kernels on its own data -- the tensor-core
  * correlation's tile width (128 or 256 atoms per CTA) and the large-instance
- * correlation's signals per pass and loads in flight -- and keeps the fastest
+ * correlation's signals per pass -- and keeps the fastest
  * in the plan for later solves.  Every configuration computes the same bits,
  * so tuning changes only timing; the tuning solve synchronises its stream
  * while it measures, and no tuning happens inside stream capture (the
@@ -495,8 +495,8 @@ cs_status cs_plan_set_option(cs_plan* plan, int32_t option, int32_t value);
 /* The autotuner's choices so far, one line per size class ("<kernel>
  * prec=.. m=.. n=.. B=.. -> <configuration index>"), NUL-terminated in buf
  * (len bytes).  Configuration indices: tensor-core tile 0 = 256 atoms,
- * 1 = 128; large-instance correlation 2 x (log2 signals per pass) + (loads
- * in flight - 1).  CS_EINVAL when buf is too short (then truncated). */
+ * 1 = 128; large-instance correlation 2 x log2(signals per pass: 1, 2 or
+ * 4).  CS_EINVAL when buf is too short (then truncated). */
 cs_status cs_plan_autotune_report(cs_plan* plan, char* buf, int32_t len);
 
 /* Kernel launches per phase since the last reset (always counted), and --

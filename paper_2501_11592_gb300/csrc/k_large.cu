@@ -44,6 +44,7 @@
 #include <vector>
 
 #include "k_common.cuh"
+#include "k_tc.cuh"
 
 namespace cs {
 namespace {
@@ -56,15 +57,29 @@ constexpr int LG_RQ = 32;              // support atoms per residual partial sum
 constexpr int LG_RROWS = 1024;         // rows per CTA of the residual reduction
 constexpr int LG_RESCORE_CTAS = 64;    // CTAs per signal re-scoring candidates
 constexpr int LG_SMEM_R = 160 * 1024;  // shared memory for the residuals of one pass
+// bf16 correlation: A's copy in tiles of 64 atoms x 256 rows (32 KB, one
+// bulk copy each), streamed through a ring of shared-memory stages
+constexpr int LG_TA = 64;
+constexpr int LG_TR = 256;
+constexpr int LG_TILE_BYTES = LG_TA * LG_TR * 2;
+constexpr int LG_TMA_CONSUMERS = 8;                       // warps, eight atoms each
+constexpr int LG_TMA_THREADS = 32 * (LG_TMA_CONSUMERS + 1);
+constexpr int LG_TMA_MAX_STAGES = 6;
+constexpr unsigned LG_ERR_CORR = 64u;                     // a wait of the bf16 correlation gave up
 
 // Per-signal state (Bl signals, K = largest k rounded up to 32, mp = m
 // rounded up to 8, NSEG = ceil(m / LG_SEG), LCH = ceil(K / LG_LC),
 // RCH = ceil(K / LG_RQ)).
 struct LgState {
     int m, n, lda, mp, K, nseg, lch, rch, Bl, nb, bf16;
+    int mp256, nc, njb;             // bf16 tiles: rows padded to 256, row chunks, atom blocks of 64
+    int nsm, smem_optin;            // the device's SMs and per-CTA shared-memory limit
     double tol;
     const float* A;                 // caller's A (float32, leading dimension lda)
-    const __nv_bfloat16* A16;       // [n][mp] bf16 copy (bf16 mode)
+    const __nv_bfloat16* A16;       // [njb][nc][64][256] bf16 copy in tiles (bf16 mode): tile (jb, ic)
+                                    // holds rows 256 ic .. 256 ic + 255 of atoms 64 jb .. 64 jb + 63,
+                                    // atom-major; rows >= m and atoms >= n are zero
+    int* cblk;                      // [Bl] next atom block per pass of the bf16 correlation
     const float* colmax;            // max_j ||a_j||
     const float* const* ys;         // [Bl] caller's measurement vectors
     const LargeOut* outs;           // [Bl] caller's outputs
@@ -143,21 +158,26 @@ __device__ T block_sum(T v, T* sh) {
 }
 
 // ------------------------------------------------------------- set-up --
-// bf16 copy of A (rows padded to mp with zeros) and the largest column norm.
-__global__ void k_lg_prep(const float* __restrict__ A, int lda, int m, int n, int mp,
+// The largest column norm and the tiled bf16 copy of A (rows padded to a
+// multiple of 256, atoms to a multiple of 64, with zeros).  One warp per
+// atom of the padded range.
+__global__ void k_lg_prep(const float* __restrict__ A, int lda, int m, int n, int mp256, int njb,
                           __nv_bfloat16* __restrict__ A16, float* colmax) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= n) return;
-    const float* a = A + (size_t)j * lda;
+    if (j >= (A16 ? njb * LG_TA : n)) return;
+    const float* a = A + (size_t)min(j, n - 1) * lda;
+    const int nc = mp256 / LG_TR;
     float ss = 0.f;
-    for (int i = lane; i < mp; i += 32) {
-        const float v = i < m ? a[i] : 0.f;
+    for (int i = lane; i < (A16 ? mp256 : m); i += 32) {
+        const float v = (i < m && j < n) ? a[i] : 0.f;
         ss = fmaf(v, v, ss);
-        if (A16) A16[(size_t)j * mp + i] = __float2bfloat16_rn(v);
+        if (A16)
+            A16[(((size_t)(j / LG_TA) * nc + i / LG_TR) * LG_TA + (j % LG_TA)) * LG_TR + (i % LG_TR)] =
+                __float2bfloat16_rn(v);
     }
     ss = warp_sum(ss);
-    if (lane == 0) atomicMax(reinterpret_cast<unsigned*>(colmax), __float_as_uint(sqrtf(ss)));
+    if (lane == 0 && j < n) atomicMax(reinterpret_cast<unsigned*>(colmax), __float_as_uint(sqrtf(ss)));
 }
 
 // Per signal (one CTA): y, r = y, ||y||, the non-finite and tolerance tests.
@@ -192,12 +212,12 @@ __global__ void __launch_bounds__(1024) k_lg_setup(LgState S) {
 }
 
 // ------------------------------------------------------- correlation --
-// |c~_j| for the NB signals of pass blockIdx.y and the atoms of this CTA,
-// and the largest unselected one per signal.  bf16 A: lane l covers rows
-// i0 + 8l .. i0 + 8l + 7 of every 256-row chunk (one 16-byte load per atom);
-// float32 A: rows i0 + l + 32e (eight coalesced loads per atom).
-template <bool BF16, int NB, int U>
+// float32 |c~_j| for the NB signals of pass blockIdx.y and the atoms of this
+// CTA (the caller's A read directly, lane l covering rows i0 + l + 32e, eight
+// coalesced loads per atom), and the largest unselected one per signal.
+template <int NB, int U>
 __global__ void __launch_bounds__(LG_CORR_THREADS) k_lg_corr(LgState S) {
+    static_assert(U == 1, "the float32 form keeps one chunk of loads in flight");
     extern __shared__ __align__(16) float rs[];   // [NB][mp]
     const int s0 = blockIdx.y * NB;
     bool any = false;
@@ -217,63 +237,26 @@ __global__ void __launch_bounds__(LG_CORR_THREADS) k_lg_corr(LgState S) {
     for (int a = 0; a < LG_ATOMS_PER_WARP; ++a)
 #pragma unroll
         for (int s = 0; s < NB; ++s) acc[a][s] = 0.f;
-    // bf16: U chunks' loads are issued before their multiply-adds (the sums
-    // keep ascending row order per lane, whatever U)
-    for (int i0 = 0; i0 < S.mp; i0 += 256 * U) {
-        if (BF16) {
-            uint4 av[U][LG_ATOMS_PER_WARP];
+    for (int i0 = 0; i0 < S.mp; i0 += 256) {
+        float av[LG_ATOMS_PER_WARP][8];
 #pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = i0 + 256 * u + 8 * lane;
+        for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
+            const float* col = S.A + (size_t)min(j0 + a, S.n - 1) * S.lda;
 #pragma unroll
-                for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
-                    const int j = min(j0 + a, S.n - 1);
-                    av[u][a] = i < S.mp ? *reinterpret_cast<const uint4*>(S.A16 + (size_t)j * S.mp + i)
-                                        : make_uint4(0u, 0u, 0u, 0u);
-                }
+            for (int e = 0; e < 8; ++e) {
+                const int i = i0 + lane + 32 * e;
+                av[a][e] = i < S.m ? col[i] : 0.f;
             }
-#pragma unroll
-            for (int u = 0; u < U; ++u) {
-                const int i = i0 + 256 * u + 8 * lane;
-                if (i < S.mp) {
-#pragma unroll
-                    for (int s = 0; s < NB; ++s) {
-                        const float4 r0 = *reinterpret_cast<const float4*>(rs + s * S.mp + i);
-                        const float4 r1 = *reinterpret_cast<const float4*>(rs + s * S.mp + i + 4);
-                        const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
-#pragma unroll
-                        for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
-                            const unsigned w[4] = {av[u][a].x, av[u][a].y, av[u][a].z, av[u][a].w};
-#pragma unroll
-                            for (int q = 0; q < 4; ++q) {
-                                acc[a][s] = fmaf(__uint_as_float(w[q] << 16), rv[2 * q], acc[a][s]);
-                                acc[a][s] = fmaf(__uint_as_float(w[q] & 0xffff0000u), rv[2 * q + 1], acc[a][s]);
-                            }
-                        }
-                    }
-                }
-            }
-        } else {
-            float av[LG_ATOMS_PER_WARP][8];
-#pragma unroll
-            for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
-                const float* col = S.A + (size_t)min(j0 + a, S.n - 1) * S.lda;
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int i = i0 + lane + 32 * e;
-                    av[a][e] = i < S.m ? col[i] : 0.f;
-                }
-            }
-#pragma unroll
-            for (int s = 0; s < NB; ++s)
-#pragma unroll
-                for (int e = 0; e < 8; ++e) {
-                    const int i = i0 + lane + 32 * e;
-                    const float rv = i < S.mp ? rs[s * S.mp + i] : 0.f;
-#pragma unroll
-                    for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) acc[a][s] = fmaf(av[a][e], rv, acc[a][s]);
-                }
         }
+#pragma unroll
+        for (int s = 0; s < NB; ++s)
+#pragma unroll
+            for (int e = 0; e < 8; ++e) {
+                const int i = i0 + lane + 32 * e;
+                const float rv = i < S.mp ? rs[s * S.mp + i] : 0.f;
+#pragma unroll
+                for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) acc[a][s] = fmaf(av[a][e], rv, acc[a][s]);
+            }
     }
     const int nw = (S.n + 31) / 32;
 #pragma unroll
@@ -291,6 +274,153 @@ __global__ void __launch_bounds__(LG_CORR_THREADS) k_lg_corr(LgState S) {
             }
         }
         if (lane == 0 && b < S.Bl && S.st[b] < 0) atomicMax(S.cmax + b, __float_as_uint(mx));
+    }
+}
+
+// bf16 correlation streamed through shared memory: one CTA per SM (per
+// pass of NB signals), the pass's residuals in shared memory once, and A's
+// tiles (64 atoms x 256 rows, 32 KB) brought in by one-dimensional bulk
+// copies into a ring of `stages` buffers.  Warp 8's lane 0 takes atom blocks
+// from the pass's counter (cblk) and issues their row chunks in order; warp
+// w < 8 owns atoms 8w .. 8w + 7 of the block, lane l rows 8l .. 8l + 7 of
+// every chunk -- the per-lane order of k_lg_corr's bf16 form -- and after a
+// block's last chunk writes |c~| and folds the per-signal maximum.  Every
+// wait is bounded (about 2 s); on time-out the error flags get bit 64 and the
+// CTA stops after the copies it issued have landed.
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+                 : "memory");
+}
+
+__host__ __device__ constexpr size_t lg_tma_smem(int stages, int nb, int mp256) {
+    return (size_t)stages * LG_TILE_BYTES + sizeof(float) * (size_t)nb * mp256 + (size_t)stages * 24;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, int stages) {
+    extern __shared__ __align__(1024) unsigned char lsm[];
+    unsigned char* tiles = lsm;
+    float* rs = reinterpret_cast<float*>(lsm + (size_t)stages * LG_TILE_BYTES);   // [NB][mp256]
+    uint64_t* full = reinterpret_cast<uint64_t*>(rs + (size_t)NB * S.mp256);
+    uint64_t* empty = full + stages;
+    int2* info = reinterpret_cast<int2*>(empty + stages);                       // (block, chunk)
+    const int s0 = blockIdx.y * NB;
+    bool any = false;
+#pragma unroll
+    for (int s = 0; s < NB; ++s) any |= (s0 + s < S.Bl) && S.st[s0 + s] < 0;
+    if (!any) return;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid == 0) {
+        for (int st = 0; st < stages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], LG_TMA_CONSUMERS);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = tid; e < NB * S.mp256; e += blockDim.x) {
+        const int s = e / S.mp256, i = e - s * S.mp256;
+        rs[e] = (s0 + s < S.Bl && i < S.mp) ? S.r[(size_t)(s0 + s) * S.mp + i] : 0.f;
+    }
+    __syncthreads();
+
+    if (warp == LG_TMA_CONSUMERS) {
+        if (lane != 0) return;
+        // producer
+        int it = 0;
+        bool ok = true;
+        for (;;) {
+            const int blk = atomicAdd(S.cblk + blockIdx.y, 1);
+            if (blk >= S.njb) break;
+            const __nv_bfloat16* src = S.A16 + (size_t)blk * S.nc * LG_TA * LG_TR;
+            for (int ic = 0; ic < S.nc; ++ic, ++it) {
+                const int st = it % stages;
+                if (it >= stages && !mbar_wait(&empty[st], ((it / stages) - 1) & 1)) {
+                    ok = false;
+                    break;
+                }
+                info[st] = make_int2(blk, ic);
+                mbar_arrive_expect_tx(&full[st], LG_TILE_BYTES);
+                bulk_load_1d(tiles + (size_t)st * LG_TILE_BYTES, src + (size_t)ic * LG_TA * LG_TR, LG_TILE_BYTES,
+                             &full[st]);
+            }
+            if (!ok) break;
+        }
+        if (ok) {
+            // end of the work: a stage whose block is -1
+            const int st = it % stages;
+            if (it >= stages && !mbar_wait(&empty[st], ((it / stages) - 1) & 1)) ok = false;
+            if (ok) {
+                info[st] = make_int2(-1, 0);
+                mbar_arrive(&full[st]);
+            }
+        }
+        if (!ok) {
+            atomicOr(S.errflag, LG_ERR_CORR);
+            // let the copies in flight land before the CTA ends
+            for (int q = (it > stages ? it - stages : 0); q < it; ++q) mbar_wait(&full[q % stages], (q / stages) & 1);
+        }
+        return;
+    }
+
+    // consumers
+    const int nw = (S.n + 31) / 32;
+    float acc[8][NB];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+#pragma unroll
+        for (int s = 0; s < NB; ++s) acc[a][s] = 0.f;
+    for (int it = 0;; ++it) {
+        const int st = it % stages;
+        if (!mbar_wait(&full[st], (it / stages) & 1)) {
+            if (lane == 0) atomicOr(S.errflag, LG_ERR_CORR);
+            break;
+        }
+        const int2 inf = info[st];
+        if (inf.x < 0) break;
+        const unsigned char* tile = tiles + (size_t)st * LG_TILE_BYTES;
+        uint4 av[8];
+#pragma unroll
+        for (int a = 0; a < 8; ++a)
+            av[a] = *reinterpret_cast<const uint4*>(tile + ((size_t)(warp * 8 + a) * LG_TR + 8 * lane) * 2);
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[st]);
+        const int i = inf.y * LG_TR + 8 * lane;
+#pragma unroll
+        for (int s = 0; s < NB; ++s) {
+            const float4 r0 = *reinterpret_cast<const float4*>(rs + (size_t)s * S.mp256 + i);
+            const float4 r1 = *reinterpret_cast<const float4*>(rs + (size_t)s * S.mp256 + i + 4);
+            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+#pragma unroll
+            for (int a = 0; a < 8; ++a) {
+                const unsigned w[4] = {av[a].x, av[a].y, av[a].z, av[a].w};
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    acc[a][s] = fmaf(__uint_as_float(w[q] << 16), rv[2 * q], acc[a][s]);
+                    acc[a][s] = fmaf(__uint_as_float(w[q] & 0xffff0000u), rv[2 * q + 1], acc[a][s]);
+                }
+            }
+        }
+        if (inf.y == S.nc - 1) {
+            const int j0 = inf.x * LG_TA + warp * 8;
+#pragma unroll
+            for (int s = 0; s < NB; ++s) {
+                const int b = s0 + s;
+                float mx = 0.f;
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    const float v = fabsf(warp_sum(acc[a][s]));
+                    acc[a][s] = 0.f;
+                    const int j = j0 + a;
+                    if (b < S.Bl && j < S.n) {
+                        if (lane == 0) S.c[(size_t)b * S.n + j] = v;
+                        const bool sel = (S.mask[(size_t)b * nw + (j >> 5)] >> (j & 31)) & 1u;
+                        if (!sel) mx = fmaxf(mx, v);
+                    }
+                }
+                if (lane == 0 && b < S.Bl && S.st[b] < 0) atomicMax(S.cmax + b, __float_as_uint(mx));
+            }
+        }
     }
 }
 
@@ -846,7 +976,7 @@ __global__ void k_lg_out(LgState S) {
 }
 
 struct LgLayout {
-    size_t A16, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
+    size_t A16, cblk, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
         xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, G, bv, s0, s1, am, av, gbar, total;
 };
 
@@ -863,7 +993,8 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
         return o;
     };
     LgLayout L{};
-    L.A16 = bf16 ? take(sizeof(__nv_bfloat16) * (size_t)n * mp) : 0;
+    L.A16 = bf16 ? take(sizeof(__nv_bfloat16) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, LG_TR)) : 0;
+    L.cblk = take(sizeof(int) * B);
     L.colmax = take(sizeof(float));
     L.ys = take(sizeof(const float*) * B);
     L.outs = take(sizeof(LargeOut) * B);
@@ -907,47 +1038,70 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
     return L;
 }
 
-template <bool BF16, int NB, int U>
+template <int NB, int U>
 cudaError_t launch_corr_nb(const LgState& S, cudaStream_t s) {
     const size_t smem = sizeof(float) * (size_t)NB * S.mp;
-    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr<BF16, NB, U>,
+    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr<NB, U>,
                                                    cudaFuncAttributeMaxDynamicSharedMemorySize, LG_SMEM_R);
     if (attr != cudaSuccess) return attr;
     const dim3 grid(ceil_div(S.n, (LG_CORR_THREADS / 32) * LG_ATOMS_PER_WARP), ceil_div(S.Bl, NB));
-    k_lg_corr<BF16, NB, U><<<grid, LG_CORR_THREADS, smem, s>>>(S);
+    k_lg_corr<NB, U><<<grid, LG_CORR_THREADS, smem, s>>>(S);
     return cudaGetLastError();
 }
 
-// Correlation configuration cfg = 2 log2(NB) + (U - 1): NB signals per pass
-// (residuals in shared memory), U 256-row chunks of loads in flight (bf16).
+// Ring stages of the bf16 correlation with NB residuals in shared memory
+// (0: it does not fit).
+int lg_tma_stages(const LgState& S, int nb) {
+    const size_t fixed = lg_tma_smem(0, nb, S.mp256);
+    if (fixed >= (size_t)S.smem_optin) return 0;
+    const int st = (int)(((size_t)S.smem_optin - fixed) / (LG_TILE_BYTES + 24));
+    return st >= 2 ? std::min(st, LG_TMA_MAX_STAGES) : 0;
+}
+
+template <int NB>
+cudaError_t launch_corr_tma(const LgState& S, cudaStream_t s) {
+    const int stages = lg_tma_stages(S, NB);
+    if (stages == 0) return cudaErrorInvalidValue;
+    const size_t smem = lg_tma_smem(stages, NB, S.mp256);
+    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr_tma<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   S.smem_optin);
+    if (attr != cudaSuccess) return attr;
+    const int npass = ceil_div(S.Bl, NB);
+    cudaError_t e = cudaMemsetAsync(S.cblk, 0, sizeof(int) * npass, s);
+    if (e != cudaSuccess) return e;
+    const dim3 grid(std::max(1, std::min(S.njb, S.nsm / npass)), npass);
+    k_lg_corr_tma<NB><<<grid, LG_TMA_THREADS, smem, s>>>(S, stages);
+    return cudaGetLastError();
+}
+
+// Correlation configuration: bf16, cfg = 2 log2(NB) (NB signals per pass,
+// A's tiles streamed through shared memory); float32, cfg = 2 log2(NB)
+// (NB residuals in shared memory, the caller's A read directly).
 cudaError_t launch_corr(const LgState& S, int cfg, cudaStream_t s) {
-    const int nbl = cfg >> 1, u2 = cfg & 1;
+    const int nbl = cfg >> 1;
     if (S.bf16) {
-        switch (nbl * 2 + u2) {
-            case 0: return launch_corr_nb<true, 1, 1>(S, s);
-            case 1: return launch_corr_nb<true, 1, 2>(S, s);
-            case 2: return launch_corr_nb<true, 2, 1>(S, s);
-            case 3: return launch_corr_nb<true, 2, 2>(S, s);
-            case 4: return launch_corr_nb<true, 4, 1>(S, s);
-            default: return launch_corr_nb<true, 4, 2>(S, s);
+        switch (nbl) {
+            case 0: return launch_corr_tma<1>(S, s);
+            case 1: return launch_corr_tma<2>(S, s);
+            default: return launch_corr_tma<4>(S, s);
         }
     }
     switch (nbl) {
-        case 0: return launch_corr_nb<false, 1, 1>(S, s);
-        case 1: return launch_corr_nb<false, 2, 1>(S, s);
-        default: return launch_corr_nb<false, 4, 1>(S, s);
+        case 0: return launch_corr_nb<1, 1>(S, s);
+        case 1: return launch_corr_nb<2, 1>(S, s);
+        default: return launch_corr_nb<4, 1>(S, s);
     }
 }
 
-// The configurations that fit: NB residuals in shared memory, no more
-// signal slots than signals; U only matters for bf16.
+// The configurations that fit: NB residuals in shared memory (bf16: beside
+// at least two ring stages), no more signal slots than signals.
 std::vector<int> corr_configs(const LgState& S) {
     std::vector<int> out;
     for (int nbl = 0; nbl <= 2; ++nbl) {
         const int nb = 1 << nbl;
-        if (sizeof(float) * (size_t)nb * S.mp > (size_t)LG_SMEM_R) break;
+        if (S.bf16 ? lg_tma_stages(S, nb) == 0 : sizeof(float) * (size_t)nb * S.mp > (size_t)LG_SMEM_R) break;
         if (nb > 1 && nb / 2 >= S.Bl) break;
-        for (int u2 = 0; u2 < (S.bf16 ? 2 : 1); ++u2) out.push_back(2 * nbl + u2);
+        out.push_back(2 * nbl);
     }
     return out;
 }
@@ -985,6 +1139,17 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     S.nb = 1;   // set from the chosen correlation configuration below
     S.A = call.A;
     S.A16 = call.bf16 ? reinterpret_cast<__nv_bfloat16*>(w + L.A16) : nullptr;
+    S.mp256 = round_up(call.m, LG_TR);
+    S.nc = S.mp256 / LG_TR;
+    S.njb = ceil_div(call.n, LG_TA);
+    S.cblk = reinterpret_cast<int*>(w + L.cblk);
+    {
+        int dev = 0;
+        cudaError_t e0 = cudaGetDevice(&dev);
+        if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&S.nsm, cudaDevAttrMultiProcessorCount, dev);
+        if (e0 == cudaSuccess) e0 = cudaDeviceGetAttribute(&S.smem_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        if (e0 != cudaSuccess) return e0;
+    }
     S.colmax = reinterpret_cast<float*>(w + L.colmax);
     S.ys = reinterpret_cast<const float* const*>(w + L.ys);
     S.outs = reinterpret_cast<const LargeOut*>(w + L.outs);
@@ -1056,8 +1221,8 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         if (call.mark) call.mark(call.mark_ctx, phase, after);
     };
     mark(CS_PHASE_SETUP, 0);
-    k_lg_prep<<<ceil_div(S.n, 8), 256, 0, s>>>(S.A, S.lda, S.m, S.n, S.mp,
-                                               const_cast<__nv_bfloat16*>(S.A16), const_cast<float*>(S.colmax));
+    k_lg_prep<<<ceil_div(S.bf16 ? S.njb * LG_TA : S.n, 8), 256, 0, s>>>(
+        S.A, S.lda, S.m, S.n, S.mp256, S.njb, const_cast<__nv_bfloat16*>(S.A16), const_cast<float*>(S.colmax));
     LG_TRY(cudaGetLastError());
     k_lg_setup<<<Bl, 1024, 0, s>>>(S);
     LG_TRY(cudaGetLastError());
