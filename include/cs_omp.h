@@ -386,7 +386,8 @@ cs_status iht_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n,
  * further atoms (the "suspects") were re-scored in float32; out[1] = device error flags (non-zero
  * when a bounded wait inside a kernel gave up: 1, 2 the tensor-core
  * correlation's tile pipeline; 4, 8, 16 the persistent CLOMP solve's roles;
- * 32 the large-instance CLOMP fit's wait for other CTAs' coefficients).
+ * 32 the large-instance CLOMP fit's wait for other CTAs' coefficients; 64
+ * the large-instance bf16 correlation's tile ring).
  * reset != 0 zeroes them.  Returns CS_ETIMEOUT when out[1] != 0. */
 cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* stream);
 
