@@ -62,7 +62,7 @@ def parse():
 
 
 PROFILE_CASES = ("omp_fp32", "omp_fp8", "clomp_bf16_per_iteration", "clomp_gather", "threshold", "single",
-                 "clfit_pair", "columnwise_image", "large_small", "persist")
+                 "clfit_pair", "columnwise_image", "large_small", "large_small_clomp", "persist")
 
 
 def profile_case(name):
@@ -105,9 +105,11 @@ def profile_case(name):
         cs.reconstruct_columnwise(dev(pc.A), D, dev(pc.Y), pc.k, 256, ref=dev(pc.meta["X_img"]), algo="clomp",
                                   prec="bf16", plan=cs.Plan(pc.m, pc.n, pc.B, pc.k), tv_weight=32.0, image_prior=True,
                                   **CL)
-    elif name == "large_small":
+    elif name in ("large_small", "large_small_clomp"):
         pl = workloads.config_large_1d(n=16384, m=4915, k=100)
-        cs.omp_solve_batched(dev(pl.A), dev(pl.Y), pl.k, prec="bf16", plan=cs.Plan(pl.m, pl.n, 1, pl.k))
+        fn = cs.omp_solve_batched if name == "large_small" else cs.clomp_solve_batched
+        kw = {} if name == "large_small" else dict(form="gram", **CL)
+        fn(dev(pl.A), dev(pl.Y), pl.k, prec="bf16", plan=cs.Plan(pl.m, pl.n, 1, pl.k), **kw)
     else:
         raise SystemExit(f"unknown profile case {name}")
     torch.cuda.synchronize()
