@@ -740,6 +740,9 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
 
     // plain OMP on small batches: the whole solve in one kernel, one CTA per signal
     const bool omp_fused = !cp && P->fused_omp && a.B <= device_sm_count() && omp_fused_supported(a);
+    // ... and A resident in the kernel's shared memory: it reads the caller's
+    // A and Y and does the set-up itself (the only launch of the solve)
+    const bool omp_self = omp_fused && omp_fused_self_contained(a);
 
     // CLOMP in Gram form runs selection, fit and residual as one kernel, or
     // (bf16 correlation) the whole solve as one persistent kernel
@@ -759,6 +762,11 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
 
     // Every launch of the solve, on stream `st`.
     auto enqueue = [&](cudaStream_t st) -> cs_status {
+        if (omp_self) {
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_PERSIST, st, [&] { return launch_omp_fused(a, A, lda, Y, ldy, st); }),
+                          "fused OMP");
+            return CS_OK;
+        }
         if (cp)
             CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, st, [&] {
                               return launch_adam_table(P->tab, c.tab_len, cp->lr, cp->beta1, cp->beta2, st);
@@ -802,7 +810,8 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
             return CS_OK;
         }
         if (omp_fused) {
-            CS_TRY_LAUNCH(timed(P, CS_PHASE_PERSIST, st, [&] { return launch_omp_fused(a, st); }), "fused OMP");
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_PERSIST, st, [&] { return launch_omp_fused(a, nullptr, 0, nullptr, 0, st); }),
+                          "fused OMP");
             return CS_OK;
         }
         if (lowp) {
@@ -867,6 +876,7 @@ cs_status solve(cs_plan* P, const float* A, int m, int n, int lda, const float* 
         np.bf16 = bf16 ? 1 : 0;
         np.fp8 = fp8 ? 1 : 0;
         np.gram = (need_gram && !tv) ? 1 : 0;
+        if (omp_self) np.gen = 0;     // the self-contained solve prepares nothing
         P->prep = np;
     }
     const cs_status rs = run_solve(P, s, enqueue, [&](std::string& key) {

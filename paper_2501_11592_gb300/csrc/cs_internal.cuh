@@ -222,7 +222,10 @@ cudaError_t launch_select(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_chol(const IterArgs& a, cudaStream_t s);
 // Whole plain-OMP solves (float32 correlation), one CTA per signal, one launch.
 bool omp_fused_supported(const IterArgs& a);
-cudaError_t launch_omp_fused(const IterArgs& a, cudaStream_t s);
+// A fits the kernel's shared memory: then it may read the caller's A and Y
+// (A != nullptr) and do the set-up itself, needing no other launch.
+bool omp_fused_self_contained(const IterArgs& a);
+cudaError_t launch_omp_fused(const IterArgs& a, const float* A, int lda, const float* Y, int ldy, cudaStream_t s);
 cudaError_t launch_resid(const IterArgs& a, cudaStream_t s);
 cudaError_t launch_clfit_gram(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 // CL fit with the image priors of Eq. 6 and 7 (k_image_prior.cu): images of

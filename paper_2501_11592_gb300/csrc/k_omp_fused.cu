@@ -41,8 +41,90 @@ __host__ __device__ inline bool of_a_fits(int K, int mp, int nw, int n) {
     return of_state(K, mp, nw) + of_resident_a(mp, n) + OF_STATIC <= (size_t)OF_MAX_SMEM;
 }
 
+// Column j of the shared-memory A (sa[q * np1 + j]) row-sliced like load_row.
 template <int MCH>
-__global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
+__device__ __forceinline__ void load_col_sa(const float* sa, int np1, int mp, int j, float4 (&v)[MCH]) {
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < MCH; ++c) {
+        const int i = 4 * (c * 32 + lane);
+        v[c] = (i < mp) ? make_float4(sa[(size_t)i * np1 + j], sa[(size_t)(i + 1) * np1 + j],
+                                      sa[(size_t)(i + 2) * np1 + j], sa[(size_t)(i + 3) * np1 + j])
+                        : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+}
+
+// warp_dots32 with the columns read from the shared-memory A (the same sums
+// in the same order, so the same values as the Gram table).
+template <int MCH>
+__device__ __forceinline__ float warp_dots32_sa(const float* sa, int np1, int mp, int my_atom,
+                                                const float4 (&x)[MCH]) {
+    const int lane = threadIdx.x & 31;
+    float part[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const int j = __shfl_sync(FULL, my_atom, q);
+        float acc = 0.f;
+        if (j >= 0) {
+#pragma unroll
+            for (int c = 0; c < MCH; ++c) {
+                const int i = 4 * (c * 32 + lane);
+                if (i < mp) {
+                    const float4 col = make_float4(sa[(size_t)i * np1 + j], sa[(size_t)(i + 1) * np1 + j],
+                                                   sa[(size_t)(i + 2) * np1 + j], sa[(size_t)(i + 3) * np1 + j]);
+                    acc += dot4(col, x[c]);
+                }
+            }
+        }
+        part[q] = acc;
+    }
+    warp_reduce_scatter32(part);
+    return part[0];
+}
+
+// resid_vector_from (k_resid.cuh) with the columns read from the
+// shared-memory A: the same fused multiply-adds in the same order.
+template <int MCH>
+__device__ __forceinline__ void resid_vector_sa(const float* sa, int np1, int mp, const int t, float4 (&r)[MCH],
+                                                const int* sup, const float* x) {
+    const int lane = threadIdx.x & 31;
+    for (int q0 = 0; q0 < t; q0 += 32) {
+        const int qn = min(32, t - q0);
+        const int my_j = (lane < qn) ? sup[q0 + lane] : 0;
+        const float my_x = (lane < qn) ? x[q0 + lane] : 0.f;
+        for (int u0 = 0; u0 < qn; u0 += 4) {
+            float4 v[4][MCH];
+            float xq[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int j = __shfl_sync(FULL, my_j, u0 + u);
+                xq[u] = __shfl_sync(FULL, my_x, u0 + u);
+                if (u0 + u < qn) {
+                    load_col_sa<MCH>(sa, np1, mp, j, v[u]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < MCH; ++c) v[u][c] = make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int c = 0; c < MCH; ++c) {
+                    r[c].x = fmaf(-v[u][c].x, xq[u], r[c].x);
+                    r[c].y = fmaf(-v[u][c].y, xq[u], r[c].y);
+                    r[c].z = fmaf(-v[u][c].z, xq[u], r[c].z);
+                    r[c].w = fmaf(-v[u][c].w, xq[u], r[c].w);
+                }
+        }
+    }
+}
+
+// Ac / Yc non-null (A resident in shared memory): the solve reads the
+// caller's A (leading dimension lda) and Y (ldy) itself and does the
+// set-up of k_setup (same sums), so it is the only launch of the solve.
+template <int MCH>
+__global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a, const float* __restrict__ Ac, int lda,
+                                                          const float* __restrict__ Yc, int ldy) {
     __shared__ float sh_v[OF_THREADS / 32];
     __shared__ int sh_j[OF_THREADS / 32];
     __shared__ float sh_a[OF_KC][OF_THREADS + 1];   // A[q0 + q][j0 + atom], padded rows
@@ -65,19 +147,62 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
 
     const int b = blockIdx.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < a.mp; i += OF_THREADS) {
-        rs[i] = a.R32[(size_t)b * a.mp + i];
-        ys[i] = a.Y32[(size_t)b * a.mp + i];
-    }
-    for (int w = tid; w < a.nw; w += OF_THREADS) ms[w] = a.mask[(size_t)b * a.nw + w];
-    if (resident)
-        for (int e = tid; e < a.n * a.mp; e += OF_THREADS) {
-            const int j = e / a.mp, q = e % a.mp;    // consecutive threads: one column's consecutive K values
-            sa[(size_t)q * np1 + j] = a.A32[(size_t)j * a.mp + q];
+    const bool self = Ac != nullptr;     // only with A resident
+    if (self) {
+        // k_setup's work for this signal (warp 0, the same sums)
+        if (warp == 0) {
+            const float* y = Yc + (size_t)b * ldy;
+            float ssq = 0.f;
+            int finite = 1;
+            for (int i = lane; i < a.mp; i += 32) {
+                const float v = (i < a.m) ? y[i] : 0.f;
+                finite &= isfinite(v) ? 1 : 0;
+                ys[i] = v;
+                rs[i] = v;
+                ssq = fmaf(v, v, ssq);
+            }
+            for (int q = lane; q < a.k; q += 32) {
+                a.support[(size_t)b * a.k + q] = -1;
+                a.coef[(size_t)b * a.k + q] = 0.f;
+            }
+            ssq = warp_sum(ssq);
+            finite = __all_sync(FULL, finite);
+            if (lane == 0) {
+                const float rho = sqrtf(ssq);
+                int st;
+                a.n_iter[b] = 0;
+                if (!finite) {
+                    st = CS_SIG_NONFINITE;
+                    a.res_norm[b] = __int_as_float(0x7fffffff);
+                } else {
+                    a.res_norm[b] = rho;
+                    st = ((double)rho <= a.tol) ? CS_SIG_REACHED_TOL : -1;
+                }
+                a.status[b] = st;
+                sh_status = st;
+                sh_t = 0;
+            }
         }
-    if (tid == 0) {
-        sh_status = a.status[b];
-        sh_t = a.n_iter[b];
+        for (int w = tid; w < a.nw; w += OF_THREADS) ms[w] = 0u;
+        for (int e = tid; e < a.n * a.mp; e += OF_THREADS) {
+            const int j = e / a.mp, q = e % a.mp;
+            sa[(size_t)q * np1 + j] = (q < a.m) ? Ac[(size_t)j * lda + q] : 0.f;
+        }
+    } else {
+        for (int i = tid; i < a.mp; i += OF_THREADS) {
+            rs[i] = a.R32[(size_t)b * a.mp + i];
+            ys[i] = a.Y32[(size_t)b * a.mp + i];
+        }
+        for (int w = tid; w < a.nw; w += OF_THREADS) ms[w] = a.mask[(size_t)b * a.nw + w];
+        if (resident)
+            for (int e = tid; e < a.n * a.mp; e += OF_THREADS) {
+                const int j = e / a.mp, q = e % a.mp;    // consecutive threads: one column's consecutive K values
+                sa[(size_t)q * np1 + j] = a.A32[(size_t)j * a.mp + q];
+            }
+        if (tid == 0) {
+            sh_status = a.status[b];
+            sh_t = a.n_iter[b];
+        }
     }
     for (int it = 0; it < a.iters; ++it) {
         __syncthreads();                 // last iteration's residual, bitset and status
@@ -137,7 +262,8 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
             a.support[(size_t)b * a.k + t] = j;
         }
         float4 aj[MCH], yv[MCH];
-        load_row<MCH>(a.A32 + (size_t)j * a.mp, a.mp, aj);
+        if (resident) load_col_sa<MCH>(sa, np1, a.mp, j, aj);
+        else load_row<MCH>(a.A32 + (size_t)j * a.mp, a.mp, aj);
         load_row<MCH>(ys, a.mp, yv);
         float dd = 0.f, by = 0.f;
 #pragma unroll
@@ -145,14 +271,24 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
             dd += dot4(aj[c], aj[c]);
             by += dot4(aj[c], yv[c]);
         }
-        dd = warp_sum(dd);
+        dd = warp_sum(dd);               // the Gram table's a_j . a_j (same sums)
         by = warp_sum(by);
-        const float* garow = a.GA + (size_t)j * a.n;
-        dd = garow[j];
         __syncwarp();                    // the support entry
-        for (int i0 = 0; i0 < t; i0 += 32) {
-            const int i = i0 + lane;
-            if (i < t) gs[i] = garow[ss[i]];
+        if (resident) {
+            // the Gram column formed here from the shared-memory A, in the
+            // Gram table's arithmetic
+            for (int i0 = 0; i0 < t; i0 += 32) {
+                const int i = i0 + lane;
+                const float g = warp_dots32_sa<MCH>(sa, np1, a.mp, i < t ? ss[i] : -1, aj);
+                if (i < t) gs[i] = g;
+            }
+        } else {
+            const float* garow = a.GA + (size_t)j * a.n;
+            dd = garow[j];
+            for (int i0 = 0; i0 < t; i0 += 32) {
+                const int i = i0 + lane;
+                if (i < t) gs[i] = garow[ss[i]];
+            }
         }
         __syncwarp();                    // the Gram column
         // ---- float64 Cholesky update (the batched kernel's arithmetic)
@@ -183,7 +319,8 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
         float4 rv[MCH];
 #pragma unroll
         for (int c = 0; c < MCH; ++c) rv[c] = yv[c];
-        resid_vector_from<MCH>(a, t1, rv, ss, cs_);
+        if (resident) resid_vector_sa<MCH>(sa, np1, a.mp, t1, rv, ss, cs_);
+        else resid_vector_from<MCH>(a, t1, rv, ss, cs_);
         float sq = 0.f;
         float4* R = reinterpret_cast<float4*>(rs);
 #pragma unroll
@@ -203,32 +340,37 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a) {
 }
 
 template <int MCH>
-cudaError_t launch_m(const IterArgs& a, cudaStream_t s) {
+cudaError_t launch_m(const IterArgs& a, const float* Ac, int lda, const float* Yc, int ldy, cudaStream_t s) {
     static const cudaError_t attr =
         cudaFuncSetAttribute(k_omp_fused<MCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, OF_MAX_SMEM);
     if (attr != cudaSuccess) return attr;
     const size_t smem = of_state(a.kmax, a.mp, a.nw) +
                         (of_a_fits(a.kmax, a.mp, a.nw, a.n) ? of_resident_a(a.mp, a.n) : 0);
-    k_omp_fused<MCH><<<a.B, OF_THREADS, smem, s>>>(a);
+    k_omp_fused<MCH><<<a.B, OF_THREADS, smem, s>>>(a, Ac, lda, Yc, ldy);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 bool omp_fused_supported(const IterArgs& a) {
-    return a.need_gcol && a.GA != nullptr && a.prec == CS_CORR_FP32 && row_chunks(a.mp) <= kMaxRowChunks &&
-           of_state(a.kmax, a.mp, a.nw) + OF_STATIC <= (size_t)OF_MAX_SMEM;
+    return a.need_gcol && a.prec == CS_CORR_FP32 && row_chunks(a.mp) <= kMaxRowChunks &&
+           of_state(a.kmax, a.mp, a.nw) + OF_STATIC <= (size_t)OF_MAX_SMEM &&
+           (a.GA != nullptr || of_a_fits(a.kmax, a.mp, a.nw, a.n));
 }
 
-cudaError_t launch_omp_fused(const IterArgs& a, cudaStream_t s) {
-    if (!omp_fused_supported(a)) return cudaErrorNotSupported;
+bool omp_fused_self_contained(const IterArgs& a) {
+    return omp_fused_supported(a) && of_a_fits(a.kmax, a.mp, a.nw, a.n);
+}
+
+cudaError_t launch_omp_fused(const IterArgs& a, const float* A, int lda, const float* Y, int ldy, cudaStream_t s) {
+    if (!omp_fused_supported(a) || (A != nullptr && !omp_fused_self_contained(a))) return cudaErrorNotSupported;
     if (a.B <= 0) return cudaSuccess;
     switch (row_chunks(a.mp)) {
-        case 1: return launch_m<1>(a, s);
-        case 2: return launch_m<2>(a, s);
+        case 1: return launch_m<1>(a, A, lda, Y, ldy, s);
+        case 2: return launch_m<2>(a, A, lda, Y, ldy, s);
         case 3:
-        case 4: return launch_m<4>(a, s);
-        default: return launch_m<8>(a, s);
+        case 4: return launch_m<4>(a, A, lda, Y, ldy, s);
+        default: return launch_m<8>(a, A, lda, Y, ldy, s);
     }
 }
 

@@ -63,3 +63,36 @@ def test_fused_omp_only_for_small_batches(cs_gpu, torch):
     A32, Y32, _, _ = f32_problem(p.A, p.Y)
     f = omp(cs_gpu, torch, A32, Y32, 6, 1)
     assert f["launches"]["persist"] == 0 and f["launches"]["correlation"] == 6
+
+
+def test_fused_omp_self_contained_reads_callers_layout(cs_gpu, torch):
+    """With A resident in shared memory the fused solve is the only launch:
+    it reads the caller's A and Y through their leading dimensions (both
+    larger than m here) and does the set-up itself -- a NaN signal (status
+    4), a zero signal under tol (1) -- with the per-iteration kernels' bits."""
+    m, n, B, k = 61, 250, 5, 9
+    p = workloads.random_problem(m, n, B, k, seed=133, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    Y32 = np.array(Y32)
+    Y32[7, 1] = np.nan
+    Y32[:, 3] = 0.0
+    Abig = torch.zeros((m + 7, n), dtype=torch.float32).t().contiguous().t().cuda()   # column-major, lda = m + 7
+    Abig[:m] = torch.from_numpy(A32).cuda()
+    Ybig = torch.zeros((m + 3, B), dtype=torch.float32).t().contiguous().t().cuda()
+    Ybig[:m] = torch.from_numpy(Y32).cuda()
+    outs = {}
+    for fused in (1, 0):
+        plan = cs_gpu.Plan(m, n, B, k)
+        plan.set_option(cs_gpu.OPT_FUSED_OMP, fused)
+        r = cs_gpu.omp_solve_batched(Abig[:m], Ybig[:m], k, prec="fp32", plan=plan, tol=1e-6)
+        torch.cuda.synchronize()
+        outs[fused] = to_numpy(r)
+        outs[fused]["launches"] = {ph: v[0] for ph, v in plan.profile(reset=True).items()}
+    f, g = outs[1], outs[0]
+    assert sum(f["launches"].values()) == 1 and f["launches"]["persist"] == 1, f["launches"]
+    assert f["status"][1] == 4 and f["status"][3] == 1 and f["n_iter"][3] == 0
+    for q in ("support", "coef", "n_iter", "status"):
+        assert np.array_equal(f[q], g[q]), q
+    assert np.array_equal(f["res_norm"], g["res_norm"], equal_nan=True)
+    ok = [0, 2, 4]
+    compare({q: v[ok] for q, v in f.items() if q != "launches"}, oracle.omp(A64, Y64[:, ok], k, tol=1e-6))
