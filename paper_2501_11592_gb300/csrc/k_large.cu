@@ -49,37 +49,37 @@
 namespace cs {
 namespace {
 
-constexpr int LG_CORR_THREADS = 256;   // correlation CTA: 8 warps x 8 atoms
-constexpr int LG_ATOMS_PER_WARP = 8;
 constexpr int LG_SEG = 2048;           // rows per partial Gram dot product
 constexpr int LG_LC = 64;              // inner-index chunk of the float64 products
 constexpr int LG_RQ = 32;              // support atoms per residual partial sum
 constexpr int LG_RROWS = 1024;         // rows per CTA of the residual reduction
 constexpr int LG_RESCORE_CTAS = 64;    // CTAs per signal re-scoring candidates
-constexpr int LG_SMEM_R = 160 * 1024;  // shared memory for the residuals of one pass
-// bf16 correlation: A's copy in tiles of 64 atoms x 256 rows (32 KB, one
-// bulk copy each), streamed through a ring of shared-memory stages
+// Correlation: A's copy (bf16, or float32) in tiles of 64 atoms x 256 (bf16)
+// or 128 (float32) rows, 32 KB each, one bulk copy per tile, streamed through
+// a ring of shared-memory stages
 constexpr int LG_TA = 64;
-constexpr int LG_TR = 256;
-constexpr int LG_TILE_BYTES = LG_TA * LG_TR * 2;
+constexpr int LG_TILE_BYTES = 32 * 1024;
+template <typename T>
+__host__ __device__ constexpr int lg_tr() { return LG_TILE_BYTES / (LG_TA * (int)sizeof(T)); }
 constexpr int LG_TMA_CONSUMERS = 8;                       // warps, eight atoms each
 constexpr int LG_TMA_THREADS = 32 * (LG_TMA_CONSUMERS + 1);
 constexpr int LG_TMA_MAX_STAGES = 6;
-constexpr unsigned LG_ERR_CORR = 64u;                     // a wait of the bf16 correlation gave up
+constexpr unsigned LG_ERR_CORR = 64u;                     // a wait of the correlation's ring gave up
 
 // Per-signal state (Bl signals, K = largest k rounded up to 32, mp = m
 // rounded up to 8, NSEG = ceil(m / LG_SEG), LCH = ceil(K / LG_LC),
 // RCH = ceil(K / LG_RQ)).
 struct LgState {
     int m, n, lda, mp, K, nseg, lch, rch, Bl, nb, bf16;
-    int mp256, nc, njb;             // bf16 tiles: rows padded to 256, row chunks, atom blocks of 64
+    int mpt, nc, njb;               // tiles: rows padded to the tile height, row chunks, atom blocks of 64
     int nsm, smem_optin;            // the device's SMs and per-CTA shared-memory limit
     double tol;
     const float* A;                 // caller's A (float32, leading dimension lda)
-    const __nv_bfloat16* A16;       // [njb][nc][64][256] bf16 copy in tiles (bf16 mode): tile (jb, ic)
-                                    // holds rows 256 ic .. 256 ic + 255 of atoms 64 jb .. 64 jb + 63,
-                                    // atom-major; rows >= m and atoms >= n are zero
-    int* cblk;                      // [Bl] next atom block per pass of the bf16 correlation
+    const void* At;                 // [njb][nc][64][TR] copy of A in tiles (bf16, TR = 256; or float32,
+                                    // TR = 128): tile (jb, ic) holds rows TR ic .. TR ic + TR - 1 of
+                                    // atoms 64 jb .. 64 jb + 63, atom-major; rows >= m and atoms >= n
+                                    // are zero
+    int* cblk;                      // [Bl] next atom block per pass of the correlation
     const float* colmax;            // max_j ||a_j||
     const float* const* ys;         // [Bl] caller's measurement vectors
     const LargeOut* outs;           // [Bl] caller's outputs
@@ -158,23 +158,25 @@ __device__ T block_sum(T v, T* sh) {
 }
 
 // ------------------------------------------------------------- set-up --
-// The largest column norm and the tiled bf16 copy of A (rows padded to a
-// multiple of 256, atoms to a multiple of 64, with zeros).  One warp per
-// atom of the padded range.
-__global__ void k_lg_prep(const float* __restrict__ A, int lda, int m, int n, int mp256, int njb,
-                          __nv_bfloat16* __restrict__ A16, float* colmax) {
+// The largest column norm and the tiled copy of A (bf16 or float32; rows
+// padded to the tile height, atoms to a multiple of 64, with zeros).  One
+// warp per atom of the padded range.
+template <typename T>
+__global__ void k_lg_prep(const float* __restrict__ A, int lda, int m, int n, int mpt, int njb,
+                          T* __restrict__ At, float* colmax) {
+    constexpr int TR = lg_tr<T>();
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= (A16 ? njb * LG_TA : n)) return;
+    if (j >= njb * LG_TA) return;
     const float* a = A + (size_t)min(j, n - 1) * lda;
-    const int nc = mp256 / LG_TR;
+    const int nc = mpt / TR;
     float ss = 0.f;
-    for (int i = lane; i < (A16 ? mp256 : m); i += 32) {
+    for (int i = lane; i < mpt; i += 32) {
         const float v = (i < m && j < n) ? a[i] : 0.f;
         ss = fmaf(v, v, ss);
-        if (A16)
-            A16[(((size_t)(j / LG_TA) * nc + i / LG_TR) * LG_TA + (j % LG_TA)) * LG_TR + (i % LG_TR)] =
-                __float2bfloat16_rn(v);
+        T* dst = At + (((size_t)(j / LG_TA) * nc + i / TR) * LG_TA + (j % LG_TA)) * TR + (i % TR);
+        if constexpr (sizeof(T) == 2) *dst = __float2bfloat16_rn(v);
+        else *dst = v;
     }
     ss = warp_sum(ss);
     if (lane == 0 && j < n) atomicMax(reinterpret_cast<unsigned*>(colmax), __float_as_uint(sqrtf(ss)));
@@ -212,79 +214,16 @@ __global__ void __launch_bounds__(1024) k_lg_setup(LgState S) {
 }
 
 // ------------------------------------------------------- correlation --
-// float32 |c~_j| for the NB signals of pass blockIdx.y and the atoms of this
-// CTA (the caller's A read directly, lane l covering rows i0 + l + 32e, eight
-// coalesced loads per atom), and the largest unselected one per signal.
-template <int NB, int U>
-__global__ void __launch_bounds__(LG_CORR_THREADS) k_lg_corr(LgState S) {
-    static_assert(U == 1, "the float32 form keeps one chunk of loads in flight");
-    extern __shared__ __align__(16) float rs[];   // [NB][mp]
-    const int s0 = blockIdx.y * NB;
-    bool any = false;
-#pragma unroll
-    for (int s = 0; s < NB; ++s) any |= (s0 + s < S.Bl) && S.st[s0 + s] < 0;
-    if (!any) return;
-    for (int e = threadIdx.x; e < NB * S.mp; e += blockDim.x) {
-        const int s = e / S.mp, i = e - s * S.mp;
-        rs[e] = (s0 + s < S.Bl) ? S.r[(size_t)(s0 + s) * S.mp + i] : 0.f;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int j0 = (blockIdx.x * (LG_CORR_THREADS / 32) + warp) * LG_ATOMS_PER_WARP;
-    if (j0 >= S.n) return;
-    float acc[LG_ATOMS_PER_WARP][NB];
-#pragma unroll
-    for (int a = 0; a < LG_ATOMS_PER_WARP; ++a)
-#pragma unroll
-        for (int s = 0; s < NB; ++s) acc[a][s] = 0.f;
-    for (int i0 = 0; i0 < S.mp; i0 += 256) {
-        float av[LG_ATOMS_PER_WARP][8];
-#pragma unroll
-        for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
-            const float* col = S.A + (size_t)min(j0 + a, S.n - 1) * S.lda;
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int i = i0 + lane + 32 * e;
-                av[a][e] = i < S.m ? col[i] : 0.f;
-            }
-        }
-#pragma unroll
-        for (int s = 0; s < NB; ++s)
-#pragma unroll
-            for (int e = 0; e < 8; ++e) {
-                const int i = i0 + lane + 32 * e;
-                const float rv = i < S.mp ? rs[s * S.mp + i] : 0.f;
-#pragma unroll
-                for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) acc[a][s] = fmaf(av[a][e], rv, acc[a][s]);
-            }
-    }
-    const int nw = (S.n + 31) / 32;
-#pragma unroll
-    for (int s = 0; s < NB; ++s) {
-        const int b = s0 + s;
-        float mx = 0.f;
-#pragma unroll
-        for (int a = 0; a < LG_ATOMS_PER_WARP; ++a) {
-            const float v = fabsf(warp_sum(acc[a][s]));
-            const int j = j0 + a;
-            if (b < S.Bl && j < S.n) {
-                if (lane == 0) S.c[(size_t)b * S.n + j] = v;
-                const bool sel = (S.mask[(size_t)b * nw + (j >> 5)] >> (j & 31)) & 1u;
-                if (!sel) mx = fmaxf(mx, v);
-            }
-        }
-        if (lane == 0 && b < S.Bl && S.st[b] < 0) atomicMax(S.cmax + b, __float_as_uint(mx));
-    }
-}
-
-// bf16 correlation streamed through shared memory: one CTA per SM (per
+// Correlation |c~_j| streamed through shared memory: one CTA per SM (per
 // pass of NB signals), the pass's residuals in shared memory once, and A's
-// tiles (64 atoms x 256 rows, 32 KB) brought in by one-dimensional bulk
+// tiles (64 atoms x TR rows, 32 KB) brought in by one-dimensional bulk
 // copies into a ring of `stages` buffers.  Warp 8's lane 0 takes atom blocks
 // from the pass's counter (cblk) and issues their row chunks in order; warp
-// w < 8 owns atoms 8w .. 8w + 7 of the block, lane l rows 8l .. 8l + 7 of
-// every chunk -- the per-lane order of k_lg_corr's bf16 form -- and after a
-// block's last chunk writes |c~| and folds the per-signal maximum.  Every
+// w < 8 owns atoms 8w .. 8w + 7 of the block, lane l the 16 bytes at rows
+// RPL l .. RPL l + RPL - 1 of every chunk (RPL = 8 bf16 or 4 float32 values),
+// summed in ascending row order with float32 fused multiply-adds, and after
+// a block's last chunk writes |c~| and folds the per-signal maximum (the
+// largest unselected |c~|, atomicMax on the float bits).  Every
 // wait is bounded (about 2 s); on time-out the error flags get bit 64 and the
 // CTA stops after the copies it issued have landed.
 __device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -293,16 +232,17 @@ __device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_
                  : "memory");
 }
 
-__host__ __device__ constexpr size_t lg_tma_smem(int stages, int nb, int mp256) {
-    return (size_t)stages * LG_TILE_BYTES + sizeof(float) * (size_t)nb * mp256 + (size_t)stages * 24;
+__host__ __device__ constexpr size_t lg_tma_smem(int stages, int nb, int mpt) {
+    return (size_t)stages * LG_TILE_BYTES + sizeof(float) * (size_t)nb * mpt + (size_t)stages * 24;
 }
 
-template <int NB>
+template <typename T, int NB>
 __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, int stages) {
+    constexpr int TR = lg_tr<T>(), RPL = TR / 32;
     extern __shared__ __align__(1024) unsigned char lsm[];
     unsigned char* tiles = lsm;
-    float* rs = reinterpret_cast<float*>(lsm + (size_t)stages * LG_TILE_BYTES);   // [NB][mp256]
-    uint64_t* full = reinterpret_cast<uint64_t*>(rs + (size_t)NB * S.mp256);
+    float* rs = reinterpret_cast<float*>(lsm + (size_t)stages * LG_TILE_BYTES);   // [NB][mpt]
+    uint64_t* full = reinterpret_cast<uint64_t*>(rs + (size_t)NB * S.mpt);
     uint64_t* empty = full + stages;
     int2* info = reinterpret_cast<int2*>(empty + stages);                       // (block, chunk)
     const int s0 = blockIdx.y * NB;
@@ -318,8 +258,8 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
-    for (int e = tid; e < NB * S.mp256; e += blockDim.x) {
-        const int s = e / S.mp256, i = e - s * S.mp256;
+    for (int e = tid; e < NB * S.mpt; e += blockDim.x) {
+        const int s = e / S.mpt, i = e - s * S.mpt;
         rs[e] = (s0 + s < S.Bl && i < S.mp) ? S.r[(size_t)(s0 + s) * S.mp + i] : 0.f;
     }
     __syncthreads();
@@ -332,7 +272,7 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
         for (;;) {
             const int blk = atomicAdd(S.cblk + blockIdx.y, 1);
             if (blk >= S.njb) break;
-            const __nv_bfloat16* src = S.A16 + (size_t)blk * S.nc * LG_TA * LG_TR;
+            const T* src = static_cast<const T*>(S.At) + (size_t)blk * S.nc * LG_TA * TR;
             for (int ic = 0; ic < S.nc; ++ic, ++it) {
                 const int st = it % stages;
                 if (it >= stages && !mbar_wait(&empty[st], ((it / stages) - 1) & 1)) {
@@ -341,7 +281,7 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
                 }
                 info[st] = make_int2(blk, ic);
                 mbar_arrive_expect_tx(&full[st], LG_TILE_BYTES);
-                bulk_load_1d(tiles + (size_t)st * LG_TILE_BYTES, src + (size_t)ic * LG_TA * LG_TR, LG_TILE_BYTES,
+                bulk_load_1d(tiles + (size_t)st * LG_TILE_BYTES, src + (size_t)ic * LG_TA * TR, LG_TILE_BYTES,
                              &full[st]);
             }
             if (!ok) break;
@@ -382,22 +322,32 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
         uint4 av[8];
 #pragma unroll
         for (int a = 0; a < 8; ++a)
-            av[a] = *reinterpret_cast<const uint4*>(tile + ((size_t)(warp * 8 + a) * LG_TR + 8 * lane) * 2);
+            av[a] = *reinterpret_cast<const uint4*>(tile + ((size_t)(warp * 8 + a) * TR + RPL * lane) * sizeof(T));
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[st]);
-        const int i = inf.y * LG_TR + 8 * lane;
+        const int i = inf.y * TR + RPL * lane;
 #pragma unroll
         for (int s = 0; s < NB; ++s) {
-            const float4 r0 = *reinterpret_cast<const float4*>(rs + (size_t)s * S.mp256 + i);
-            const float4 r1 = *reinterpret_cast<const float4*>(rs + (size_t)s * S.mp256 + i + 4);
-            const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
+            const float4 r0 = *reinterpret_cast<const float4*>(rs + (size_t)s * S.mpt + i);
+            if constexpr (sizeof(T) == 2) {
+                const float4 r1 = *reinterpret_cast<const float4*>(rs + (size_t)s * S.mpt + i + 4);
+                const float rv[8] = {r0.x, r0.y, r0.z, r0.w, r1.x, r1.y, r1.z, r1.w};
 #pragma unroll
-            for (int a = 0; a < 8; ++a) {
-                const unsigned w[4] = {av[a].x, av[a].y, av[a].z, av[a].w};
+                for (int a = 0; a < 8; ++a) {
+                    const unsigned w[4] = {av[a].x, av[a].y, av[a].z, av[a].w};
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    acc[a][s] = fmaf(__uint_as_float(w[q] << 16), rv[2 * q], acc[a][s]);
-                    acc[a][s] = fmaf(__uint_as_float(w[q] & 0xffff0000u), rv[2 * q + 1], acc[a][s]);
+                    for (int q = 0; q < 4; ++q) {
+                        acc[a][s] = fmaf(__uint_as_float(w[q] << 16), rv[2 * q], acc[a][s]);
+                        acc[a][s] = fmaf(__uint_as_float(w[q] & 0xffff0000u), rv[2 * q + 1], acc[a][s]);
+                    }
+                }
+            } else {
+#pragma unroll
+                for (int a = 0; a < 8; ++a) {
+                    acc[a][s] = fmaf(__uint_as_float(av[a].x), r0.x, acc[a][s]);
+                    acc[a][s] = fmaf(__uint_as_float(av[a].y), r0.y, acc[a][s]);
+                    acc[a][s] = fmaf(__uint_as_float(av[a].z), r0.z, acc[a][s]);
+                    acc[a][s] = fmaf(__uint_as_float(av[a].w), r0.w, acc[a][s]);
                 }
             }
         }
@@ -976,7 +926,7 @@ __global__ void k_lg_out(LgState S) {
 }
 
 struct LgLayout {
-    size_t A16, cblk, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
+    size_t At, cblk, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
         xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, G, bv, s0, s1, am, av, gbar, total;
 };
 
@@ -993,7 +943,8 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
         return o;
     };
     LgLayout L{};
-    L.A16 = bf16 ? take(sizeof(__nv_bfloat16) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, LG_TR)) : 0;
+    L.At = bf16 ? take(sizeof(__nv_bfloat16) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, lg_tr<__nv_bfloat16>()))
+                : take(sizeof(float) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, lg_tr<float>()));
     L.cblk = take(sizeof(int) * B);
     L.colmax = take(sizeof(float));
     L.ys = take(sizeof(const float*) * B);
@@ -1038,68 +989,55 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
     return L;
 }
 
-template <int NB, int U>
-cudaError_t launch_corr_nb(const LgState& S, cudaStream_t s) {
-    const size_t smem = sizeof(float) * (size_t)NB * S.mp;
-    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr<NB, U>,
-                                                   cudaFuncAttributeMaxDynamicSharedMemorySize, LG_SMEM_R);
-    if (attr != cudaSuccess) return attr;
-    const dim3 grid(ceil_div(S.n, (LG_CORR_THREADS / 32) * LG_ATOMS_PER_WARP), ceil_div(S.Bl, NB));
-    k_lg_corr<NB, U><<<grid, LG_CORR_THREADS, smem, s>>>(S);
-    return cudaGetLastError();
-}
-
-// Ring stages of the bf16 correlation with NB residuals in shared memory
-// (0: it does not fit).
+// Ring stages of the correlation with NB residuals in shared memory (0: it
+// does not fit).
 int lg_tma_stages(const LgState& S, int nb) {
-    const size_t fixed = lg_tma_smem(0, nb, S.mp256);
+    const size_t fixed = lg_tma_smem(0, nb, S.mpt);
     if (fixed >= (size_t)S.smem_optin) return 0;
     const int st = (int)(((size_t)S.smem_optin - fixed) / (LG_TILE_BYTES + 24));
     return st >= 2 ? std::min(st, LG_TMA_MAX_STAGES) : 0;
 }
 
-template <int NB>
+template <typename T, int NB>
 cudaError_t launch_corr_tma(const LgState& S, cudaStream_t s) {
     const int stages = lg_tma_stages(S, NB);
     if (stages == 0) return cudaErrorInvalidValue;
-    const size_t smem = lg_tma_smem(stages, NB, S.mp256);
-    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr_tma<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t smem = lg_tma_smem(stages, NB, S.mpt);
+    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr_tma<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                    S.smem_optin);
     if (attr != cudaSuccess) return attr;
     const int npass = ceil_div(S.Bl, NB);
     cudaError_t e = cudaMemsetAsync(S.cblk, 0, sizeof(int) * npass, s);
     if (e != cudaSuccess) return e;
     const dim3 grid(std::max(1, std::min(S.njb, S.nsm / npass)), npass);
-    k_lg_corr_tma<NB><<<grid, LG_TMA_THREADS, smem, s>>>(S, stages);
+    k_lg_corr_tma<T, NB><<<grid, LG_TMA_THREADS, smem, s>>>(S, stages);
     return cudaGetLastError();
 }
 
-// Correlation configuration: bf16, cfg = 2 log2(NB) (NB signals per pass,
-// A's tiles streamed through shared memory); float32, cfg = 2 log2(NB)
-// (NB residuals in shared memory, the caller's A read directly).
+// Correlation configuration cfg = 2 log2(NB): NB signals per pass.
 cudaError_t launch_corr(const LgState& S, int cfg, cudaStream_t s) {
     const int nbl = cfg >> 1;
     if (S.bf16) {
         switch (nbl) {
-            case 0: return launch_corr_tma<1>(S, s);
-            case 1: return launch_corr_tma<2>(S, s);
-            default: return launch_corr_tma<4>(S, s);
+            case 0: return launch_corr_tma<__nv_bfloat16, 1>(S, s);
+            case 1: return launch_corr_tma<__nv_bfloat16, 2>(S, s);
+            default: return launch_corr_tma<__nv_bfloat16, 4>(S, s);
         }
     }
     switch (nbl) {
-        case 0: return launch_corr_nb<1, 1>(S, s);
-        case 1: return launch_corr_nb<2, 1>(S, s);
-        default: return launch_corr_nb<4, 1>(S, s);
+        case 0: return launch_corr_tma<float, 1>(S, s);
+        case 1: return launch_corr_tma<float, 2>(S, s);
+        default: return launch_corr_tma<float, 4>(S, s);
     }
 }
 
-// The configurations that fit: NB residuals in shared memory (bf16: beside
-// at least two ring stages), no more signal slots than signals.
+// The configurations that fit: NB residuals in shared memory beside at least
+// two ring stages, no more signal slots than signals.
 std::vector<int> corr_configs(const LgState& S) {
     std::vector<int> out;
     for (int nbl = 0; nbl <= 2; ++nbl) {
         const int nb = 1 << nbl;
-        if (S.bf16 ? lg_tma_stages(S, nb) == 0 : sizeof(float) * (size_t)nb * S.mp > (size_t)LG_SMEM_R) break;
+        if (lg_tma_stages(S, nb) == 0) break;
         if (nb > 1 && nb / 2 >= S.Bl) break;
         out.push_back(2 * nbl);
     }
@@ -1138,9 +1076,9 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     S.tol = call.tol;
     S.nb = 1;   // set from the chosen correlation configuration below
     S.A = call.A;
-    S.A16 = call.bf16 ? reinterpret_cast<__nv_bfloat16*>(w + L.A16) : nullptr;
-    S.mp256 = round_up(call.m, LG_TR);
-    S.nc = S.mp256 / LG_TR;
+    S.At = w + L.At;
+    S.mpt = round_up(call.m, call.bf16 ? lg_tr<__nv_bfloat16>() : lg_tr<float>());
+    S.nc = S.mpt / (call.bf16 ? lg_tr<__nv_bfloat16>() : lg_tr<float>());
     S.njb = ceil_div(call.n, LG_TA);
     S.cblk = reinterpret_cast<int*>(w + L.cblk);
     {
@@ -1221,8 +1159,14 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         if (call.mark) call.mark(call.mark_ctx, phase, after);
     };
     mark(CS_PHASE_SETUP, 0);
-    k_lg_prep<<<ceil_div(S.bf16 ? S.njb * LG_TA : S.n, 8), 256, 0, s>>>(
-        S.A, S.lda, S.m, S.n, S.mp256, S.njb, const_cast<__nv_bfloat16*>(S.A16), const_cast<float*>(S.colmax));
+    if (S.bf16)
+        k_lg_prep<__nv_bfloat16><<<ceil_div(S.njb * LG_TA, 8), 256, 0, s>>>(
+            S.A, S.lda, S.m, S.n, S.mpt, S.njb, static_cast<__nv_bfloat16*>(const_cast<void*>(S.At)),
+            const_cast<float*>(S.colmax));
+    else
+        k_lg_prep<float><<<ceil_div(S.njb * LG_TA, 8), 256, 0, s>>>(
+            S.A, S.lda, S.m, S.n, S.mpt, S.njb, static_cast<float*>(const_cast<void*>(S.At)),
+            const_cast<float*>(S.colmax));
     LG_TRY(cudaGetLastError());
     k_lg_setup<<<Bl, 1024, 0, s>>>(S);
     LG_TRY(cudaGetLastError());
