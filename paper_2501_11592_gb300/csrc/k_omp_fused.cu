@@ -119,6 +119,30 @@ __device__ __forceinline__ void resid_vector_sa(const float* sa, int np1, int mp
     }
 }
 
+// A (m rows of leading dimension ld, zero rows up to mp) into sa[q * np1 + j]:
+// consecutive threads take one column's consecutive rows (the stores hit
+// distinct banks when np1 is odd), sixteen loads in flight per thread before
+// their stores.
+__device__ __forceinline__ void copy_a_to_sa(const float* __restrict__ A, int ld, int m, int mp, int n, float* sa,
+                                             int np1) {
+    constexpr int U = 16;
+    const int total = n * mp;
+    for (int e0 = threadIdx.x; e0 < total; e0 += U * OF_THREADS) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * OF_THREADS;
+            const int j = e / mp, q = e - (e / mp) * mp;
+            v[u] = (e < total && q < m) ? A[(size_t)j * ld + q] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+            const int e = e0 + u * OF_THREADS;
+            if (e < total) sa[(size_t)(e % mp) * np1 + e / mp] = v[u];
+        }
+    }
+}
+
 // Ac / Yc non-null (A resident in shared memory): the solve reads the
 // caller's A (leading dimension lda) and Y (ldy) itself and does the
 // set-up of k_setup (same sums), so it is the only launch of the solve.
@@ -184,10 +208,7 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a, const floa
             }
         }
         for (int w = tid; w < a.nw; w += OF_THREADS) ms[w] = 0u;
-        for (int e = tid; e < a.n * a.mp; e += OF_THREADS) {
-            const int j = e / a.mp, q = e % a.mp;
-            sa[(size_t)q * np1 + j] = (q < a.m) ? Ac[(size_t)j * lda + q] : 0.f;
-        }
+        copy_a_to_sa(Ac, lda, a.m, a.mp, a.n, sa, np1);
     } else {
         for (int i = tid; i < a.mp; i += OF_THREADS) {
             rs[i] = a.R32[(size_t)b * a.mp + i];
@@ -195,10 +216,7 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a, const floa
         }
         for (int w = tid; w < a.nw; w += OF_THREADS) ms[w] = a.mask[(size_t)b * a.nw + w];
         if (resident)
-            for (int e = tid; e < a.n * a.mp; e += OF_THREADS) {
-                const int j = e / a.mp, q = e % a.mp;    // consecutive threads: one column's consecutive K values
-                sa[(size_t)q * np1 + j] = a.A32[(size_t)j * a.mp + q];
-            }
+            copy_a_to_sa(a.A32, a.mp, a.mp, a.mp, a.n, sa, np1);
         if (tid == 0) {
             sh_status = a.status[b];
             sh_t = a.n_iter[b];
@@ -333,8 +351,11 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a, const floa
         }
         sq = warp_sum(sq);
         if (lane == 0) {
-            stop_test(a, b, t1, sqrtf(sq));
-            sh_status = a.status[b];
+            const float rho = sqrtf(sq);
+            stop_test(a, b, t1, rho);
+            // the status stop_test wrote, without reading it back
+            sh_status = ((double)rho <= a.tol) ? CS_SIG_REACHED_TOL
+                        : (t1 >= a.k) ? CS_SIG_REACHED_K : (t1 >= a.iters) ? CS_SIG_MAX_ITER : -1;
         }
     }
 }
