@@ -62,7 +62,7 @@ def parse():
 
 
 PROFILE_CASES = ("omp_fp32", "omp_fp8", "clomp_bf16_per_iteration", "clomp_gather", "threshold", "single",
-                 "clfit_pair", "columnwise_image", "large_small", "large_small_clomp", "persist")
+                 "clfit_pair", "columnwise_image", "large_small", "large_small_clomp", "large_1d", "persist")
 
 
 def profile_case(name):
@@ -105,6 +105,10 @@ def profile_case(name):
         cs.reconstruct_columnwise(dev(pc.A), D, dev(pc.Y), pc.k, 256, ref=dev(pc.meta["X_img"]), algo="clomp",
                                   prec="bf16", plan=cs.Plan(pc.m, pc.n, pc.B, pc.k), tv_weight=32.0, image_prior=True,
                                   **CL)
+    elif name == "large_1d":
+        # the full-size long signal (for a launch list of a few iterations only)
+        pl = workloads.config_large_1d()
+        cs.omp_solve_batched(dev(pl.A), dev(pl.Y), pl.k, prec="bf16", plan=cs.Plan(pl.m, pl.n, 1, pl.k))
     elif name in ("large_small", "large_small_clomp"):
         pl = workloads.config_large_1d(n=16384, m=4915, k=100)
         fn = cs.omp_solve_batched if name == "large_small" else cs.clomp_solve_batched
