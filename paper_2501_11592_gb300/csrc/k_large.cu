@@ -65,6 +65,16 @@ constexpr int LG_TMA_CONSUMERS = 8;                       // warps, eight atoms 
 constexpr int LG_TMA_THREADS = 32 * (LG_TMA_CONSUMERS + 1);
 constexpr int LG_TMA_MAX_STAGES = 6;
 constexpr unsigned LG_ERR_CORR = 64u;                     // a wait of the correlation's ring gave up
+// Many signals sharing A (bf16): the correlation as a tcgen05 GEMM, M = 128
+// atoms, N = up to 256 signals, K in chunks of 64 through a TMA ring
+constexpr int LG_MMA_MIN_SIGNALS = 8;
+constexpr int LG_MMA_MAXN = 256;
+constexpr int LG_MMA_KCH = 64;
+constexpr int LG_MMA_ATILE = 128 * 128;                   // 128 atoms x 128 bytes
+constexpr int LG_MMA_MAX_STAGES = 8;
+constexpr int LG_MMA_THREADS = 128;
+constexpr int LG_MMA_CFG = 8;                             // its configuration index
+constexpr unsigned LG_ERR_MMA = 128u;                     // a wait of the GEMM correlation gave up
 
 // Per-signal state (Bl signals, K = largest k rounded up to 32, mp = m
 // rounded up to 8, NSEG = ceil(m / LG_SEG), LCH = ceil(K / LG_LC),
@@ -73,6 +83,9 @@ struct LgState {
     int m, n, lda, mp, K, nseg, lch, rch, Bl, nb, bf16;
     int mpt, nc, njb;               // tiles: rows padded to the tile height, row chunks, atom blocks of 64
     int nsm, smem_optin;            // the device's SMs and per-CTA shared-memory limit
+    int mma, mpk;                   // correlation as a tensor-core GEMM (bf16, many signals); rows to 64
+    const __nv_bfloat16* Ak;        // mma: [n][mpk] bf16 copy of A, K-major (rows >= m zero)
+    __nv_bfloat16* R16;             // mma: [Bl][mpk] bf16 copy of the residuals (rows >= m zero)
     double tol;
     const float* A;                 // caller's A (float32, leading dimension lda)
     const void* At;                 // [njb][nc][64][TR] copy of A in tiles (bf16, TR = 256; or float32,
@@ -129,8 +142,14 @@ struct LgState {
 };
 
 __device__ __forceinline__ float lg_delta(const LgState& S, int b) {
-    const float g1 = ((float)S.m / 32.f + 13.f) * 0x1p-24f;
     const float g2 = ((float)S.m / 1024.f + 16.f) * 0x1p-24f;
+    if (S.mma) {
+        // both operands rounded to bf16 (2u + u^2, u = 2^-8) and the tensor
+        // core's float32 accumulation, taken as m 2^-22 of sum |a_i r_i|
+        const float g1 = (float)S.m * 0x1p-22f;
+        return (0x1p-7f + 0x1p-16f + g1 + g2) * 1.01f * (*S.colmax) * S.rnorm[b] * 1.01f;
+    }
+    const float g1 = ((float)S.m / 32.f + 13.f) * 0x1p-24f;
     const float ua = S.bf16 ? 0x1p-8f * (1.f + g1) : 0.f;
     return (ua + g1 + g2) * 1.01f * (*S.colmax) * S.rnorm[b] * 1.01f;
 }
@@ -194,8 +213,11 @@ __global__ void __launch_bounds__(1024) k_lg_setup(LgState S) {
         finite &= isfinite(v) ? 1 : 0;
         S.y[(size_t)b * S.mp + i] = v;
         S.r[(size_t)b * S.mp + i] = v;
+        if (S.mma) S.R16[(size_t)b * S.mpk + i] = __float2bfloat16_rn(v);
         ss = fmaf(v, v, ss);
     }
+    if (S.mma)
+        for (int i = S.mp + threadIdx.x; i < S.mpk; i += blockDim.x) S.R16[(size_t)b * S.mpk + i] = __float2bfloat16_rn(0.f);
     const int nw = (S.n + 31) / 32;
     for (int w = threadIdx.x; w < nw; w += blockDim.x) S.mask[(size_t)b * nw + w] = 0u;
     finite = __syncthreads_and(finite);
@@ -372,6 +394,161 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
             }
         }
     }
+}
+
+// Correlation of a pass of up to 256 signals as one tensor-core GEMM
+// (bf16 operands, float32 accumulation in tensor memory): CTA x owns atoms
+// 128 x .. 128 x + 127 (UMMA M, the TMEM lanes) and the pass's N signals
+// (UMMA N, TMEM columns); the K = m dimension streams by TMA in 64-element
+// chunks -- the atom tile (128 rows of A's K-major copy) and the residual
+// tile (N rows of the residuals' copy), 128-byte swizzled -- through a ring
+// of `stages` buffers.  Thread 0 issues the copies, thread 32 the four
+// MMAs of each chunk and a commit that frees the stage; after the last
+// chunk a commit signals the epilogue, where thread t reads its atom's N
+// accumulators (tcgen05.ld), writes |c~| per signal and folds each signal's
+// largest unselected |c~| (a warp maximum, then atomicMax on the float
+// bits).  Every wait is bounded (about 2 s); on time-out the error flags
+// get bit 128, the epilogue is skipped and the CTA returns after its copies
+// and MMAs in flight have finished and its tensor memory is freed.
+__global__ void __launch_bounds__(LG_MMA_THREADS, 1)
+k_lg_corr_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapR, LgState S,
+              int stages, int N, int tmem_cols) {
+    extern __shared__ uint8_t lmsm[];
+    __shared__ __align__(8) uint64_t full[LG_MMA_MAX_STAGES];
+    __shared__ __align__(8) uint64_t empty[LG_MMA_MAX_STAGES];
+    __shared__ __align__(8) uint64_t done;
+    __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int j0 = blockIdx.x * 128;
+    const int s0 = blockIdx.y * LG_MMA_MAXN;
+    bool any = false;
+    for (int s = 0; s < N && s0 + s < S.Bl; ++s) any |= S.st[s0 + s] < 0;
+    if (!any) return;
+    const int rbytes = N * 128;
+    const int stage_bytes = LG_MMA_ATILE + rbytes;
+    const uint32_t raw = smem_u32(lmsm);
+    uint8_t* base = lmsm + (((raw + 1023u) & ~1023u) - raw);
+    if (tid == 0) {
+        failed = 0;
+        for (int st = 0; st < stages; ++st) {
+            mbar_init(&full[st], 1);
+            mbar_init(&empty[st], 1);
+        }
+        mbar_init(&done, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                     "r"(tmem_cols)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = tmem_slot;
+    const int nk = S.mpk / LG_MMA_KCH;
+
+    if (tid == 0) {
+        // producer: the K chunks in order, one stage each
+        int it = 0;
+        bool ok = true;
+        for (; it < nk; ++it) {
+            const int st = it % stages;
+            if (it >= stages && !mbar_wait(&empty[st], ((it / stages) - 1) & 1)) {
+                ok = false;
+                break;
+            }
+            uint8_t* sa = base + (size_t)st * stage_bytes;
+            mbar_arrive_expect_tx(&full[st], (uint32_t)stage_bytes);
+            tma_load_2d(sa, &mapA, &full[st], it * LG_MMA_KCH, j0);
+            tma_load_2d(sa + LG_MMA_ATILE, &mapR, &full[st], it * LG_MMA_KCH, s0);
+        }
+        if (!ok) {
+            failed = 1;
+            atomicOr(S.errflag, LG_ERR_MMA);
+            // let the copies in flight land
+            for (int q = (it > stages ? it - stages : 0); q < it; ++q) mbar_wait(&full[q % stages], (q / stages) & 1);
+        }
+    } else if (tid == 32) {
+        // MMA issuer
+        const uint32_t idesc = make_idesc(128, N);
+        bool ok = true;
+        for (int it = 0; it < nk; ++it) {
+            const int st = it % stages;
+            if (!mbar_wait(&full[st], (it / stages) & 1)) {
+                ok = false;
+                break;
+            }
+            tc_fence_after();
+            const uint8_t* sa = base + (size_t)st * stage_bytes;
+            const uint64_t da = smem_desc_sw128(smem_u32(sa));
+            const uint64_t db = smem_desc_sw128(smem_u32(sa + LG_MMA_ATILE));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) umma_bf16(tmem, da + (uint64_t)(2 * k), db + (uint64_t)(2 * k), idesc, (it | k) != 0);
+            umma_commit(&empty[st]);   // the stage is free once these MMAs have read it
+        }
+        if (!ok) {
+            failed = 1;
+            atomicOr(S.errflag, LG_ERR_MMA);
+        }
+        umma_commit(&done);            // arrives once every issued MMA has completed
+    }
+    __syncwarp();
+    const bool waited = mbar_wait(&done, 0);
+    tc_fence_after();
+    if (!waited && lane == 0) atomicOr(S.errflag, LG_ERR_MMA);
+    const bool ok = __syncthreads_and(waited && !failed) != 0;
+    if (ok) {
+        // epilogue: thread tid holds atom j0 + tid (TMEM lane tid)
+        const int j = j0 + tid;
+        const int nw = (S.n + 31) / 32;
+        const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+        for (int c0 = 0; c0 < N; c0 += 32) {
+            uint32_t v[32];
+            tmem_ld32(tbase + (uint32_t)c0, v);
+            tmem_ld_wait();
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int b = s0 + c0 + q;
+                if (c0 + q >= N || b >= S.Bl) continue;     // the same for the whole warp
+                const float x = fabsf(__uint_as_float(v[q]));
+                float mx = 0.f;
+                if (j < S.n) {
+                    S.c[(size_t)b * S.n + j] = x;
+                    const bool sel = (S.mask[(size_t)b * nw + (j >> 5)] >> (j & 31)) & 1u;
+                    if (!sel) mx = x;
+                }
+                mx = warp_max(mx);
+                if (lane == 0 && S.st[b] < 0) atomicMax(S.cmax + b, __float_as_uint(mx));
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 0) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols) : "memory");
+    }
+}
+
+// bf16 copy of A, K-major ([n][mpk], rows >= m zero), and the largest column
+// norm (one warp per atom).
+__global__ void k_lg_prep_k(const float* __restrict__ A, int lda, int m, int n, int mpk,
+                            __nv_bfloat16* __restrict__ Ak, float* colmax) {
+    const int lane = threadIdx.x & 31;
+    const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (j >= n) return;
+    const float* a = A + (size_t)j * lda;
+    float ss = 0.f;
+    for (int i = lane; i < mpk; i += 32) {
+        const float v = i < m ? a[i] : 0.f;
+        ss = fmaf(v, v, ss);
+        Ak[(size_t)j * mpk + i] = __float2bfloat16_rn(v);
+    }
+    ss = warp_sum(ss);
+    if (lane == 0) atomicMax(reinterpret_cast<unsigned*>(colmax), __float_as_uint(sqrtf(ss)));
 }
 
 // ---------------------------------------------------------- selection --
@@ -876,6 +1053,7 @@ __global__ void __launch_bounds__(LG_RROWS) k_lg_resid(LgState S) {
         for (int qc = 0; qc < qch; ++qc) acc += S.rpart[((size_t)b * S.rch + qc) * S.mp + i];
         ri = S.y[(size_t)b * S.mp + i] - acc;
         S.r[(size_t)b * S.mp + i] = ri;
+        if (S.mma) S.R16[(size_t)b * S.mpk + i] = __float2bfloat16_rn(ri);
     }
     const float ss = block_sum(ri * ri, sh);
     if (threadIdx.x == 0) S.nrm[(size_t)b * S.rblk + blockIdx.x] = ss;
@@ -926,9 +1104,14 @@ __global__ void k_lg_out(LgState S) {
 }
 
 struct LgLayout {
-    size_t At, cblk, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
+    size_t At, Ak, R16, cblk, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
         xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, G, bv, s0, s1, am, av, gbar, total;
 };
+
+// The correlation runs as a tensor-core GEMM for bf16 and at least
+// LG_MMA_MIN_SIGNALS signals sharing A (one pass over A per iteration instead
+// of one per pass of up to four signals).
+bool lg_uses_mma(int bf16, int Bl) { return bf16 && Bl >= LG_MMA_MIN_SIGNALS; }
 
 // cl: CLOMP's Gram-form state instead of OMP's float64 W = L^{-T}.
 LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
@@ -943,8 +1126,14 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
         return o;
     };
     LgLayout L{};
-    L.At = bf16 ? take(sizeof(__nv_bfloat16) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, lg_tr<__nv_bfloat16>()))
-                : take(sizeof(float) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, lg_tr<float>()));
+    if (lg_uses_mma(bf16, Bl)) {
+        const size_t mpk = (size_t)round_up(m, LG_MMA_KCH);
+        L.Ak = take(sizeof(__nv_bfloat16) * (size_t)n * mpk);
+        L.R16 = take(sizeof(__nv_bfloat16) * B * mpk);
+    } else {
+        L.At = bf16 ? take(sizeof(__nv_bfloat16) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, lg_tr<__nv_bfloat16>()))
+                    : take(sizeof(float) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, lg_tr<float>()));
+    }
     L.cblk = take(sizeof(int) * B);
     L.colmax = take(sizeof(float));
     L.ys = take(sizeof(const float*) * B);
@@ -1014,6 +1203,39 @@ cudaError_t launch_corr_tma(const LgState& S, cudaStream_t s) {
     return cudaGetLastError();
 }
 
+// The GEMM correlation: N = the signals per pass rounded up to 16 (at most
+// 256), as many ring stages as shared memory holds.
+struct LgMma {
+    CUtensorMap mapA, mapR;
+    int N, stages, tmem_cols;
+    size_t smem;
+};
+
+cudaError_t setup_corr_mma(const LgState& S, LgMma& M) {
+    M.N = round_up(std::min(S.Bl, LG_MMA_MAXN), 16);
+    M.tmem_cols = 32;
+    while (M.tmem_cols < M.N) M.tmem_cols *= 2;
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, k_lg_corr_mma);
+    if (e != cudaSuccess) return e;
+    const int dyn_max = S.smem_optin - (int)fa.sharedSizeBytes;   // the dynamic part's limit
+    const int stage_bytes = LG_MMA_ATILE + M.N * 128;
+    M.stages = std::min(LG_MMA_MAX_STAGES, (dyn_max - 1024) / stage_bytes);   // 1024: alignment slack
+    if (M.stages < 2) return cudaErrorInvalidValue;
+    M.smem = (size_t)M.stages * stage_bytes + 1024;
+    if (!make_tma_map_bf16(&M.mapA, S.Ak, S.mpk, S.n, (size_t)S.mpk * 2, 128) ||
+        !make_tma_map_bf16(&M.mapR, S.R16, S.mpk, S.Bl, (size_t)S.mpk * 2, M.N))
+        return cudaErrorInvalidValue;
+    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+    return attr;
+}
+
+cudaError_t launch_corr_mma(const LgState& S, const LgMma& M, cudaStream_t s) {
+    const dim3 grid(ceil_div(S.n, 128), ceil_div(S.Bl, LG_MMA_MAXN));
+    k_lg_corr_mma<<<grid, LG_MMA_THREADS, M.smem, s>>>(M.mapA, M.mapR, S, M.stages, M.N, M.tmem_cols);
+    return cudaGetLastError();
+}
+
 // Correlation configuration cfg = 2 log2(NB): NB signals per pass.
 cudaError_t launch_corr(const LgState& S, int cfg, cudaStream_t s) {
     const int nbl = cfg >> 1;
@@ -1035,6 +1257,7 @@ cudaError_t launch_corr(const LgState& S, int cfg, cudaStream_t s) {
 // two ring stages, no more signal slots than signals.
 std::vector<int> corr_configs(const LgState& S) {
     std::vector<int> out;
+    if (S.mma) return {LG_MMA_CFG};
     for (int nbl = 0; nbl <= 2; ++nbl) {
         const int nb = 1 << nbl;
         if (lg_tma_stages(S, nb) == 0) break;
@@ -1076,10 +1299,14 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     S.tol = call.tol;
     S.nb = 1;   // set from the chosen correlation configuration below
     S.A = call.A;
-    S.At = w + L.At;
+    S.mma = lg_uses_mma(call.bf16, Bl) ? 1 : 0;
+    S.At = S.mma ? nullptr : w + L.At;
     S.mpt = round_up(call.m, call.bf16 ? lg_tr<__nv_bfloat16>() : lg_tr<float>());
     S.nc = S.mpt / (call.bf16 ? lg_tr<__nv_bfloat16>() : lg_tr<float>());
     S.njb = ceil_div(call.n, LG_TA);
+    S.mpk = round_up(call.m, LG_MMA_KCH);
+    S.Ak = S.mma ? reinterpret_cast<__nv_bfloat16*>(w + L.Ak) : nullptr;
+    S.R16 = S.mma ? reinterpret_cast<__nv_bfloat16*>(w + L.R16) : nullptr;
     S.cblk = reinterpret_cast<int*>(w + L.cblk);
     {
         int dev = 0;
@@ -1158,8 +1385,13 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     auto mark = [&](int phase, int after) {
         if (call.mark) call.mark(call.mark_ctx, phase, after);
     };
+    LgMma mm{};
+    if (S.mma) LG_TRY(setup_corr_mma(S, mm));
     mark(CS_PHASE_SETUP, 0);
-    if (S.bf16)
+    if (S.mma)
+        k_lg_prep_k<<<ceil_div(S.n, 8), 256, 0, s>>>(S.A, S.lda, S.m, S.n, S.mpk, const_cast<__nv_bfloat16*>(S.Ak),
+                                                     const_cast<float*>(S.colmax));
+    else if (S.bf16)
         k_lg_prep<__nv_bfloat16><<<ceil_div(S.njb * LG_TA, 8), 256, 0, s>>>(
             S.A, S.lda, S.m, S.n, S.mpt, S.njb, static_cast<__nv_bfloat16*>(const_cast<void*>(S.At)),
             const_cast<float*>(S.colmax));
@@ -1248,7 +1480,8 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     for (int it = 0; it < iters; ++it) {
         const int t = it;
         mark(CS_PHASE_CORR, 0);
-        LG_TRY(launch_corr(S, cfg, s));
+        if (S.mma) LG_TRY(launch_corr_mma(S, mm, s));
+        else LG_TRY(launch_corr(S, cfg, s));
         mark(CS_PHASE_CORR, 1);
         mark(CS_PHASE_SELECT, 0);
         k_lg_scan<<<dim3(ceil_div(S.n, 256), Bl), 256, 0, s>>>(S);

@@ -183,3 +183,45 @@ def test_large_path_clomp_refusals(cs_gpu, torch):
     with pytest.raises(cs_gpu.CSError) as e:
         cs_gpu.clomp_solve_batched(A, Y, 100, form="gram", plan=plan, th=0.7)
     assert e.value.code == -5
+
+
+def _large_solve(cs, torch, A32, Y32, k, algo, prec="bf16"):
+    A = torch.from_numpy(np.asfortranarray(A32)).cuda()
+    Y = torch.from_numpy(np.asfortranarray(Y32)).cuda()
+    m, n = A32.shape
+    plan = cs.Plan(m, n, Y32.shape[1], k)
+    if algo == "omp":
+        r = cs.omp_solve_batched(A, Y, k, prec=prec, plan=plan)
+    else:
+        r = cs.clomp_solve_batched(A, Y, k, prec=prec, form="gram", plan=plan, steps=50, lr=1e-2)
+    torch.cuda.synchronize()
+    g = to_numpy(r)
+    assert plan.counters(reset=True)[1] == 0
+    return g
+
+
+@pytest.mark.parametrize("algo", ["omp", "clomp"])
+def test_large_path_gemm_correlation_same_bits(cs_gpu, torch, algo):
+    """Eight or more signals sharing A (bf16) correlate as one tensor-core
+    GEMM over bf16 residuals; fewer stream A once per pass.  Both lists are
+    certified and re-scored in float32, so the float32 argmax -- and every
+    output -- is the same: 40 signals solved as one group and as ten groups
+    of four give the same bits (n and m not multiples of the tile sizes)."""
+    m, n, B, k = 1100, 3001, 40, 60
+    p = workloads.random_problem(m, n, B, k, seed=501, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    one = _large_solve(cs_gpu, torch, A32, Y32, k, algo)
+    parts = [_large_solve(cs_gpu, torch, A32, np.asfortranarray(Y32[:, i:i + 4]), k, algo) for i in range(0, B, 4)]
+    for q in ("support", "coef", "n_iter", "res_norm", "status"):
+        assert np.array_equal(one[q], np.concatenate([g[q] for g in parts], axis=0)), q
+    o = oracle.omp(A64, Y64, k) if algo == "omp" else _oracle_clomp(A64, Y64, k)
+    print(algo, compare(one, o))
+
+
+def test_large_path_gemm_correlation_two_passes(cs_gpu, torch):
+    """300 signals: the GEMM runs two passes (256 and 44 signals)."""
+    m, n, B, k = 1030, 1500, 300, 8
+    p = workloads.random_problem(m, n, B, k, seed=502, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    g = _large_solve(cs_gpu, torch, A32, Y32, k, "omp")
+    print(compare(g, oracle.omp(A64, Y64, k)))
