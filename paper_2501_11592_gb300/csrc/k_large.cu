@@ -53,7 +53,8 @@ constexpr int LG_SEG = 2048;           // rows per partial Gram dot product
 constexpr int LG_LC = 64;              // inner-index chunk of the float64 products
 constexpr int LG_RQ = 32;              // support atoms per residual partial sum
 constexpr int LG_RROWS = 1024;         // rows per CTA of the residual reduction
-constexpr int LG_RESCORE_CTAS = 64;    // CTAs per signal re-scoring candidates
+constexpr int LG_RESCORE_MIN_CTAS = 16;   // CTAs per signal re-scoring candidates: at least this,
+                                          // else two per SM shared by the chunk's signals
 // Correlation: A's copy (bf16, or float32) in tiles of 64 atoms x 256 (bf16)
 // or 128 (float32) rows, 32 KB each, one bulk copy per tile, streamed through
 // a ring of shared-memory stages
@@ -578,6 +579,7 @@ __global__ void __launch_bounds__(1024) k_lg_rescore(LgState S) {
         const int j = S.cand[(size_t)b * S.n + q];
         const float* a = S.A + (size_t)j * S.lda;
         float acc = 0.f;
+#pragma unroll 8
         for (int i = threadIdx.x; i < S.m; i += blockDim.x) acc = fmaf(a[i], r[i], acc);
         const float v = fabsf(block_sum(acc, sh));
         if (threadIdx.x == 0) {
@@ -1485,7 +1487,7 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         mark(CS_PHASE_CORR, 1);
         mark(CS_PHASE_SELECT, 0);
         k_lg_scan<<<dim3(ceil_div(S.n, 256), Bl), 256, 0, s>>>(S);
-        k_lg_rescore<<<dim3(LG_RESCORE_CTAS, Bl), 1024, 0, s>>>(S);
+        k_lg_rescore<<<dim3(std::max(LG_RESCORE_MIN_CTAS, 2 * S.nsm / Bl), Bl), 1024, 0, s>>>(S);
         k_lg_gram<<<dim3(ceil_div((t + 2) * S.nseg, 8), Bl), 256, 0, s>>>(S, t);
         k_lg_gsum<<<dim3(ceil_div(t + 2, 256), Bl), 256, 0, s>>>(S, t);
         mark(CS_PHASE_SELECT, 1);
