@@ -52,7 +52,6 @@ namespace {
 constexpr int LG_SEG = 2048;           // rows per partial Gram dot product
 constexpr int LG_LC = 64;              // inner-index chunk of the float64 products
 constexpr int LG_RQ = 32;              // support atoms per residual partial sum
-constexpr int LG_RROWS = 1024;         // rows per CTA of the residual reduction
 constexpr int LG_RESCORE_MIN_CTAS = 16;   // CTAs per signal re-scoring candidates: at least this,
                                           // else two per SM shared by the chunk's signals
 // Correlation: A's copy (bf16, or float32) in tiles of 64 atoms x 256 (bf16)
@@ -119,8 +118,18 @@ struct LgState {
     double* upart;                  // [Bl][lch][K]
     double* scal;                   // [Bl][2] 1/L_tt, z_t
     float* rpart;                   // [Bl][rch][mp]
-    float* nrm;                     // [Bl][rblk] sums of r_i^2 per residual CTA
-    int rblk;                       // ceil(m / LG_RROWS)
+    float* nrm;                     // [Bl][rblk] sums of r_i^2 per 256-row block
+    int rblk;                       // ceil(m / 256)
+    // Arrival counters of the fused reductions (zero between uses: the last
+    // arriver resets its counter), per signal: pbmax = K / 32
+    int pbmax;
+    unsigned* cntG;                 // [Bl][K + 2] Gram entries: segments done
+    unsigned* cntL;                 // [Bl][pbmax] blocks of l: chunks done
+    unsigned* cntP;                 // [Bl] blocks of l done
+    unsigned* cntU;                 // [Bl][pbmax] blocks of u: chunks done
+    unsigned* cntR;                 // [Bl][rblk] residual row blocks: atom chunks done
+    unsigned* cntN;                 // [Bl] residual row blocks done
+    double* pbpart;                 // [Bl][pbmax][2] sum l_p^2 and sum l_p z_p per block of l
     float* rnorm;                   // [Bl]
     int* nit;                       // [Bl]
     int* st;                        // [Bl] status (-1 running)
@@ -630,29 +639,70 @@ __global__ void __launch_bounds__(256) k_lg_gram(LgState S, int t) {
         for (int u = 0; u < 8; ++u) acc = fmaf(o[u], v[u], acc);
     }
     acc = warp_sum(acc);
-    if (lane == 0) S.gpart[((size_t)b * S.nseg + seg) * (S.K + 2) + i] = acc;
-}
-
-__global__ void __launch_bounds__(256) k_lg_gsum(LgState S, int t) {
-    const int b = blockIdx.y;
-    if (S.st[b] >= 0) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= t + 2) return;
-    float v = 0.f;
-    for (int seg = 0; seg < S.nseg; ++seg) v += S.gpart[((size_t)b * S.nseg + seg) * (S.K + 2) + i];
-    S.gsum[(size_t)b * (S.K + 2) + i] = v;
+    // the warp that completes entry i sums its segments in order
+    unsigned prev = 0;
+    if (lane == 0) {
+        S.gpart[((size_t)b * S.nseg + seg) * (S.K + 2) + i] = acc;
+        __threadfence();
+        prev = atomicAdd(S.cntG + (size_t)b * (S.K + 2) + i, 1u);
+    }
+    if (lane == 0 && prev == (unsigned)(S.nseg - 1)) {
+        __threadfence();
+        float v = 0.f;
+        for (int sg = 0; sg < S.nseg; ++sg) v += __ldcg(S.gpart + ((size_t)b * S.nseg + sg) * (S.K + 2) + i);
+        S.gsum[(size_t)b * (S.K + 2) + i] = v;
+        S.cntG[(size_t)b * (S.K + 2) + i] = 0u;
+    }
 }
 
 // -------------------------------------------------- float64 Cholesky --
-// Partial sums of l_p = sum_{i <= p} W_ip g_i over 256-entry chunks of i:
-// one warp per (32 entries p, chunk), lanes over p.
-__global__ void __launch_bounds__(256) k_lg_lpart(LgState S, int t) {
+__device__ __forceinline__ double warp_sum_f64(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// The pivot and the diagonal entries once sum l_p^2 (ssq) and sum l_p z_p (lz)
+// are known: 1 / L_tt, z_t, W_tt, x_t (or status 3 for a dependent atom).
+__device__ void lg_pivot_finish(const LgState& S, int b, int t, double ssq, double lz) {
+    const double d = (double)S.gsum[(size_t)b * (S.K + 2) + t];
+    const double bt = (double)S.gsum[(size_t)b * (S.K + 2) + t + 1];
+    const double piv = d - ssq;
+    if (!(piv > 0x1p-20 * d)) {
+        S.st[b] = CS_SIG_DEPENDENT;
+        return;
+    }
+    const double ltt = sqrt(piv);
+    const double zt = (bt - lz) / ltt;
+    const double rinv = 1.0 / ltt;
+    S.scal[2 * b] = rinv;
+    S.scal[2 * b + 1] = zt;
+    S.z[(size_t)b * S.K + t] = zt;
+    double* Wr = S.W + (size_t)b * 2 * S.K * S.K;
+    Wr[(size_t)t * S.K + t] = rinv;
+    Wr[(size_t)S.K * S.K + (size_t)t * S.K + t] = rinv;
+    const double xt = zt * rinv;
+    S.x[(size_t)b * S.K + t] = xt;
+    S.xf[(size_t)b * S.K + t] = (float)xt;
+    S.nit[b] = t + 1;
+}
+
+// l = W^T g, l_p = sum_{i <= p} W_ip g_i, and the pivot: one warp per
+// (32 entries p, 64-entry chunk of i), lanes over p, partial sums per chunk.
+// The warp that completes a block of p sums its chunks in order (l_p) and
+// that block's sum l_p^2 and l_p z_p; the last block adds the blocks' sums
+// in order and finishes the pivot.  t = 0: one warp, no l.
+__global__ void __launch_bounds__(256) k_lg_lpiv(LgState S, int t) {
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int lane = threadIdx.x & 31;
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int pblocks = (t + 31) / 32;
-    if (item >= pblocks * S.lch) return;
+    if (t == 0) {
+        if (item == 0 && lane == 0) lg_pivot_finish(S, b, 0, 0.0, 0.0);
+        return;
+    }
+    const int pblocks = (t + 31) / 32, ich = (t + LG_LC - 1) / LG_LC;
+    if (item >= pblocks * ich) return;
     const int pb = item % pblocks, ic = item / pblocks;
     const int p = pb * 32 + lane;
     const int i0 = ic * LG_LC, i1 = min(t, i0 + LG_LC);
@@ -673,61 +723,68 @@ __global__ void __launch_bounds__(256) k_lg_lpart(LgState S, int t) {
         }
     }
     if (p < t) S.lpart[((size_t)b * S.lch + ic) * S.K + p] = acc;
-}
-
-// l from its partial sums (chunk order), the pivot, L_tt and z_t (one CTA).
-__global__ void __launch_bounds__(1024) k_lg_pivot(LgState S, int t) {
-    __shared__ double sh[33];
-    const int b = blockIdx.x;
-    if (S.st[b] >= 0) return;
-    const int ich = (t + LG_LC - 1) / LG_LC;
-    double ssq = 0.0, lz = 0.0;
-    for (int p = threadIdx.x; p < t; p += blockDim.x) {
-        double lp = 0.0;
-        for (int ic0 = 0; ic0 < ich; ic0 += 8) {     // eight chunks' loads in flight, added in order
-            double v[8];
+    __threadfence();
+    unsigned prev = 0;
+    if (lane == 0) prev = atomicAdd(S.cntL + (size_t)b * S.pbmax + pb, 1u);
+    prev = __shfl_sync(FULL, prev, 0);
+    if (prev != (unsigned)(ich - 1)) return;
+    // last chunk of this block: l_p over the chunks in order
+    __threadfence();
+    double lp = 0.0;
+    for (int ic0 = 0; ic0 < ich; ic0 += 8) {
+        double v[8];
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                v[u] = ic0 + u < ich ? S.lpart[((size_t)b * S.lch + ic0 + u) * S.K + p] : 0.0;
+        for (int u = 0; u < 8; ++u)
+            v[u] = (ic0 + u < ich && p < t) ? __ldcg(S.lpart + ((size_t)b * S.lch + ic0 + u) * S.K + p) : 0.0;
 #pragma unroll
-            for (int u = 0; u < 8; ++u)
-                if (ic0 + u < ich) lp += v[u];
-        }
+        for (int u = 0; u < 8; ++u)
+            if (ic0 + u < ich) lp += v[u];
+    }
+    double sq = 0.0, lz = 0.0;
+    if (p < t) {
         S.l[(size_t)b * S.K + p] = lp;
-        ssq = fma(lp, lp, ssq);
-        lz = fma(lp, S.z[(size_t)b * S.K + p], lz);
+        sq = lp * lp;
+        lz = lp * S.z[(size_t)b * S.K + p];
     }
-    ssq = block_sum(ssq, sh);
-    lz = block_sum(lz, sh);
-    if (threadIdx.x == 0) {
-        const double d = (double)S.gsum[(size_t)b * (S.K + 2) + t];
-        const double bt = (double)S.gsum[(size_t)b * (S.K + 2) + t + 1];
-        const double piv = d - ssq;
-        if (!(piv > 0x1p-20 * d)) {
-            S.st[b] = CS_SIG_DEPENDENT;
-        } else {
-            const double ltt = sqrt(piv);
-            const double zt = (bt - lz) / ltt;
-            S.scal[2 * b] = 1.0 / ltt;
-            S.scal[2 * b + 1] = zt;
-            S.z[(size_t)b * S.K + t] = zt;
+    sq = warp_sum_f64(sq);
+    lz = warp_sum_f64(lz);
+    if (lane == 0) {
+        S.pbpart[((size_t)b * S.pbmax + pb) * 2] = sq;
+        S.pbpart[((size_t)b * S.pbmax + pb) * 2 + 1] = lz;
+        S.cntL[(size_t)b * S.pbmax + pb] = 0u;
+        __threadfence();
+        prev = atomicAdd(S.cntP + b, 1u);
+        if (prev == (unsigned)(pblocks - 1)) {
+            // last block: the blocks' sums in order, then the pivot
+            __threadfence();
+            double ssq = 0.0, lzs = 0.0;
+            for (int q = 0; q < pblocks; ++q) {
+                ssq += __ldcg(S.pbpart + ((size_t)b * S.pbmax + q) * 2);
+                lzs += __ldcg(S.pbpart + ((size_t)b * S.pbmax + q) * 2 + 1);
+            }
+            S.cntP[b] = 0u;
+            lg_pivot_finish(S, b, t, ssq, lzs);
         }
     }
 }
 
-// Partial sums of u_i = sum_{p >= i} W_ip l_p over 256-entry chunks of p:
-// one warp per (32 entries i, chunk), lanes over i.
-__global__ void __launch_bounds__(256) k_lg_upart(LgState S, int t) {
+// u = W l, u_i = sum_{p >= i} W_ip l_p, then the new column of W and
+// x += z_t w: one warp per (32 entries i, 64-entry chunk of p), lanes over
+// i; the warp that completes a block of i sums its chunks in order (from the
+// block's own chunk: earlier chunks hold no p >= i) and updates those
+// entries (t >= 1; W_tt and x_t come with the pivot).
+__global__ void __launch_bounds__(256) k_lg_uupd(LgState S, int t) {
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int lane = threadIdx.x & 31;
     const int item = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const int iblocks = (t + 31) / 32;
-    if (item >= iblocks * S.lch) return;
+    const int iblocks = (t + 31) / 32, pch = (t + LG_LC - 1) / LG_LC;
+    if (item >= iblocks * pch) return;
     const int ib = item % iblocks, pc = item / iblocks;
     const int i = ib * 32 + lane;
     const int p0 = pc * LG_LC, p1 = min(t, p0 + LG_LC);
-    const double* Wc = S.W + (size_t)b * 2 * S.K * S.K + (size_t)S.K * S.K;
+    double* Wr = S.W + (size_t)b * 2 * S.K * S.K;
+    double* Wc = Wr + (size_t)S.K * S.K;
     const double* l = S.l + (size_t)b * S.K;
     double acc = 0.0;
     for (int pb = p0; pb < p1; pb += 8) {
@@ -744,41 +801,30 @@ __global__ void __launch_bounds__(256) k_lg_upart(LgState S, int t) {
         }
     }
     if (i < t) S.upart[((size_t)b * S.lch + pc) * S.K + i] = acc;
-}
-
-// The new column of W and x += z_t w (one thread per entry i <= t).
-__global__ void __launch_bounds__(256) k_lg_update(LgState S, int t) {
-    const int b = blockIdx.y;
-    if (S.st[b] >= 0) return;
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i > t) return;
-    double* Wr = S.W + (size_t)b * 2 * S.K * S.K;
-    double* Wc = Wr + (size_t)S.K * S.K;
-    const double rinv = S.scal[2 * b], zt = S.scal[2 * b + 1];
-    double xi;
-    if (i < t) {
-        const int pch = (t + LG_LC - 1) / LG_LC;
-        // entry i has terms only in the chunks at or after its own
-        const int pc0 = i / LG_LC;
-        double u = 0.0;
-        for (int pb = pc0; pb < pch; pb += 8) {     // eight chunks' loads in flight, added in order
-            double v[8];
+    __threadfence();
+    unsigned prev = 0;
+    if (lane == 0) prev = atomicAdd(S.cntU + (size_t)b * S.pbmax + ib, 1u);
+    prev = __shfl_sync(FULL, prev, 0);
+    if (prev != (unsigned)(pch - 1)) return;
+    __threadfence();
+    if (lane == 0) S.cntU[(size_t)b * S.pbmax + ib] = 0u;
+    if (i >= t) return;
+    const int pc0 = (ib * 32) / LG_LC;
+    double u = 0.0;
+    for (int q0 = pc0; q0 < pch; q0 += 8) {
+        double v[8];
 #pragma unroll
-            for (int q = 0; q < 8; ++q) v[q] = pb + q < pch ? S.upart[((size_t)b * S.lch + pb + q) * S.K + i] : 0.0;
+        for (int q = 0; q < 8; ++q)
+            v[q] = q0 + q < pch ? __ldcg(S.upart + ((size_t)b * S.lch + q0 + q) * S.K + i) : 0.0;
 #pragma unroll
-            for (int q = 0; q < 8; ++q)
-                if (pb + q < pch) u += v[q];
-        }
-        const double w = -u * rinv;
-        Wr[(size_t)i * S.K + t] = w;
-        Wc[(size_t)t * S.K + i] = w;
-        xi = fma(zt, w, S.x[(size_t)b * S.K + i]);
-    } else {
-        Wr[(size_t)t * S.K + t] = rinv;
-        Wc[(size_t)t * S.K + t] = rinv;
-        xi = zt * rinv;
-        S.nit[b] = t + 1;
+        for (int q = 0; q < 8; ++q)
+            if (q0 + q < pch) u += v[q];
     }
+    const double rinv = S.scal[2 * b], zt = S.scal[2 * b + 1];
+    const double w = -u * rinv;
+    Wr[(size_t)i * S.K + t] = w;
+    Wc[(size_t)t * S.K + i] = w;
+    const double xi = fma(zt, w, S.x[(size_t)b * S.K + i]);
     S.x[(size_t)b * S.K + i] = xi;
     S.xf[(size_t)b * S.K + i] = (float)xi;
 }
@@ -1009,75 +1055,77 @@ __global__ void __launch_bounds__(256) k_lgc_fit(LgState S, int t1, int R, int t
 }
 
 // ----------------------------------------------------------- residual --
-// Partial sums sum_{q in chunk} a_{S_q}[i] x_q over chunks of 128 atoms
-// (one thread per row i).
-__global__ void __launch_bounds__(256) k_lg_rpart(LgState S, int t1) {
+// r = y - A_S x (x as float32): CTA (row block x of 256 rows, chunk qc of
+// 32 support atoms) forms the chunk's partial sums for its rows; the CTA
+// that completes a row block adds the chunks in order, writes r (and its
+// bf16 copy) and the block's sum of r_i^2; the last row block adds those in
+// order and applies the stopping rule of Eq. 2, resetting the selection
+// state for the next iteration.
+__global__ void __launch_bounds__(256) k_lg_resid(LgState S, int t1) {
     __shared__ int sj[LG_RQ];
     __shared__ float sx[LG_RQ];
+    __shared__ float sh[33];
+    __shared__ unsigned last;
     const int b = blockIdx.z;
     if (S.st[b] >= 0) return;
-    const int qc = blockIdx.y;
+    const int qc = blockIdx.y, rb = blockIdx.x;
     const int q0 = qc * LG_RQ, q1 = min(t1, q0 + LG_RQ);
-    if (q0 >= q1) return;
+    const int nq = q1 - q0;
     for (int q = q0 + threadIdx.x; q < q1; q += blockDim.x) {
         sj[q - q0] = S.sup[(size_t)b * S.K + q];
         sx[q - q0] = S.xf[(size_t)b * S.K + q];
     }
     __syncthreads();
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= S.m) return;
-    float acc = 0.f;
-    int q = 0;
-    const int nq = q1 - q0;
-    for (; q + 8 <= nq; q += 8) {
-        float v[8];
+    const int i = rb * 256 + threadIdx.x;
+    if (i < S.m) {
+        float acc = 0.f;
+        int q = 0;
+        for (; q + 8 <= nq; q += 8) {
+            float v[8];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) v[u] = S.A[(size_t)sj[q + u] * S.lda + i];
+            for (int u = 0; u < 8; ++u) v[u] = S.A[(size_t)sj[q + u] * S.lda + i];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) acc = fmaf(v[u], sx[q + u], acc);
+            for (int u = 0; u < 8; ++u) acc = fmaf(v[u], sx[q + u], acc);
+        }
+        for (; q < nq; ++q) acc = fmaf(S.A[(size_t)sj[q] * S.lda + i], sx[q], acc);
+        S.rpart[((size_t)b * S.rch + qc) * S.mp + i] = acc;
     }
-    for (; q < nq; ++q) acc = fmaf(S.A[(size_t)sj[q] * S.lda + i], sx[q], acc);
-    S.rpart[((size_t)b * S.rch + qc) * S.mp + i] = acc;
-}
-
-// r = y - (partial sums in chunk order) for 1024 rows per CTA, and the CTA's
-// sum of r_i^2.
-__global__ void __launch_bounds__(LG_RROWS) k_lg_resid(LgState S) {
-    __shared__ float sh[33];
-    const int b = blockIdx.y;
-    if (S.st[b] >= 0) return;
-    const int t1 = S.nit[b];
-    const int qch = (t1 + LG_RQ - 1) / LG_RQ;
-    const int i = blockIdx.x * LG_RROWS + threadIdx.x;
+    __threadfence();
+    __syncthreads();
+    const int qch = gridDim.y;
+    if (threadIdx.x == 0) last = atomicAdd(S.cntR + (size_t)b * S.rblk + rb, 1u) == (unsigned)(qch - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!last) return;
+    // this row block's chunks are all in: r over the chunks in order
+    __threadfence();
     float ri = 0.f;
     if (i < S.m) {
         float acc = 0.f;
-        for (int qc = 0; qc < qch; ++qc) acc += S.rpart[((size_t)b * S.rch + qc) * S.mp + i];
+        for (int c = 0; c < qch; ++c) acc += __ldcg(S.rpart + ((size_t)b * S.rch + c) * S.mp + i);
         ri = S.y[(size_t)b * S.mp + i] - acc;
         S.r[(size_t)b * S.mp + i] = ri;
         if (S.mma) S.R16[(size_t)b * S.mpk + i] = __float2bfloat16_rn(ri);
     }
     const float ss = block_sum(ri * ri, sh);
-    if (threadIdx.x == 0) S.nrm[(size_t)b * S.rblk + blockIdx.x] = ss;
-}
-
-// ||r|| from the CTAs' sums (block order), the stopping rule, and the reset
-// of the selection state for the next iteration (one warp per signal).
-__global__ void k_lg_stop(LgState S) {
-    const int b = blockIdx.x;
-    if (S.st[b] >= 0) return;
-    const int t1 = S.nit[b];
     if (threadIdx.x == 0) {
-        float ss = 0.f;
-        for (int q = 0; q < S.rblk; ++q) ss += S.nrm[(size_t)b * S.rblk + q];
-        const float rho = sqrtf(ss);
-        S.rnorm[b] = rho;
-        S.ncand[b] = 0;
-        S.cmax[b] = 0u;
-        S.best[b] = 0ull;
-        if ((double)rho <= S.tol) S.st[b] = CS_SIG_REACHED_TOL;
-        else if (t1 >= S.kv[b]) S.st[b] = CS_SIG_REACHED_K;
-        else if (t1 >= S.itv[b]) S.st[b] = CS_SIG_MAX_ITER;
+        S.nrm[(size_t)b * S.rblk + rb] = ss;
+        S.cntR[(size_t)b * S.rblk + rb] = 0u;
+        __threadfence();
+        if (atomicAdd(S.cntN + b, 1u) == (unsigned)(S.rblk - 1)) {
+            // the last row block: ||r|| over the blocks in order, the stopping rule
+            __threadfence();
+            float tot = 0.f;
+            for (int q = 0; q < S.rblk; ++q) tot += __ldcg(S.nrm + (size_t)b * S.rblk + q);
+            S.cntN[b] = 0u;
+            const float rho = sqrtf(tot);
+            S.rnorm[b] = rho;
+            S.ncand[b] = 0;
+            S.cmax[b] = 0u;
+            S.best[b] = 0ull;
+            if ((double)rho <= S.tol) S.st[b] = CS_SIG_REACHED_TOL;
+            else if (t1 >= S.kv[b]) S.st[b] = CS_SIG_REACHED_K;
+            else if (t1 >= S.itv[b]) S.st[b] = CS_SIG_MAX_ITER;
+        }
     }
 }
 
@@ -1106,7 +1154,7 @@ __global__ void k_lg_out(LgState S) {
 }
 
 struct LgLayout {
-    size_t At, Ak, R16, cblk, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
+    size_t At, Ak, R16, cblk, cnt, pbpart, colmax, ys, outs, kv, itv, y, r, c, mask, cand, ncand, cmax, best, sup, gpart, gsum, W, z, x,
         xf, lpart, l, upart, scal, rpart, nrm, rnorm, nit, st, live, G, bv, s0, s1, am, av, gbar, total;
 };
 
@@ -1162,7 +1210,12 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
     L.upart = take(sizeof(double) * B * lch * K);
     L.scal = take(sizeof(double) * B * 2);
     L.rpart = take(sizeof(float) * B * rch * mp);
-    L.nrm = take(sizeof(float) * B * (size_t)ceil_div(m, LG_RROWS));
+    L.nrm = take(sizeof(float) * B * (size_t)ceil_div(m, 256));
+    {
+        const size_t pbmax = K / 32, rbl = (size_t)ceil_div(m, 256);
+        L.cnt = take(sizeof(unsigned) * B * ((K + 2) + 2 * pbmax + rbl + 2));
+        L.pbpart = take(sizeof(double) * B * pbmax * 2);
+    }
     L.rnorm = take(sizeof(float) * B);
     L.nit = take(sizeof(int) * B);
     L.st = take(sizeof(int) * B);
@@ -1360,7 +1413,18 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     S.scal = reinterpret_cast<double*>(w + L.scal);
     S.rpart = reinterpret_cast<float*>(w + L.rpart);
     S.nrm = reinterpret_cast<float*>(w + L.nrm);
-    S.rblk = ceil_div(call.m, LG_RROWS);
+    S.rblk = ceil_div(call.m, 256);
+    S.pbmax = S.K / 32;
+    {
+        unsigned* c = reinterpret_cast<unsigned*>(w + L.cnt);
+        S.cntG = c;
+        S.cntL = S.cntG + (size_t)Bl * (S.K + 2);
+        S.cntU = S.cntL + (size_t)Bl * S.pbmax;
+        S.cntR = S.cntU + (size_t)Bl * S.pbmax;
+        S.cntP = S.cntR + (size_t)Bl * S.rblk;
+        S.cntN = S.cntP + Bl;
+    }
+    S.pbpart = reinterpret_cast<double*>(w + L.pbpart);
     S.rnorm = reinterpret_cast<float*>(w + L.rnorm);
     S.nit = reinterpret_cast<int*>(w + L.nit);
     S.st = reinterpret_cast<int*>(w + L.st);
@@ -1389,6 +1453,7 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     };
     LgMma mm{};
     if (S.mma) LG_TRY(setup_corr_mma(S, mm));
+    LG_TRY(cudaMemsetAsync(S.cntG, 0, sizeof(unsigned) * (size_t)Bl * ((S.K + 2) + 2 * S.pbmax + S.rblk + 2), s));
     mark(CS_PHASE_SETUP, 0);
     if (S.mma)
         k_lg_prep_k<<<ceil_div(S.n, 8), 256, 0, s>>>(S.A, S.lda, S.m, S.n, S.mpk, const_cast<__nv_bfloat16*>(S.Ak),
@@ -1489,7 +1554,6 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         k_lg_scan<<<dim3(ceil_div(S.n, 256), Bl), 256, 0, s>>>(S);
         k_lg_rescore<<<dim3(std::max(LG_RESCORE_MIN_CTAS, 2 * S.nsm / Bl), Bl), 1024, 0, s>>>(S);
         k_lg_gram<<<dim3(ceil_div((t + 2) * S.nseg, 8), Bl), 256, 0, s>>>(S, t);
-        k_lg_gsum<<<dim3(ceil_div(t + 2, 256), Bl), 256, 0, s>>>(S, t);
         mark(CS_PHASE_SELECT, 1);
         mark(CS_PHASE_FIT, 0);
         if (cl) {
@@ -1513,16 +1577,13 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
             }
             tag += (unsigned)S.steps;
         } else {
-            if (t > 0) k_lg_lpart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
-            k_lg_pivot<<<Bl, 1024, 0, s>>>(S, t);
-            if (t > 0) k_lg_upart<<<dim3(ceil_div(ceil_div(t, 32) * S.lch, 8), Bl), 256, 0, s>>>(S, t);
-            k_lg_update<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t);
+            const int nl = t > 0 ? ceil_div(t, 32) * ceil_div(t, LG_LC) : 1;
+            k_lg_lpiv<<<dim3(ceil_div(nl, 8), Bl), 256, 0, s>>>(S, t);
+            if (t > 0) k_lg_uupd<<<dim3(ceil_div(ceil_div(t, 32) * ceil_div(t, LG_LC), 8), Bl), 256, 0, s>>>(S, t);
         }
         mark(CS_PHASE_FIT, 1);
         mark(CS_PHASE_RESID, 0);
-        k_lg_rpart<<<dim3(ceil_div(S.m, 256), ceil_div(t + 1, LG_RQ), Bl), 256, 0, s>>>(S, t + 1);
-        k_lg_resid<<<dim3(S.rblk, Bl), LG_RROWS, 0, s>>>(S);
-        k_lg_stop<<<Bl, 32, 0, s>>>(S);
+        k_lg_resid<<<dim3(S.rblk, ceil_div(t + 1, LG_RQ), Bl), 256, 0, s>>>(S, t + 1);
         mark(CS_PHASE_RESID, 1);
         LG_TRY(cudaGetLastError());
         // every 64 iterations: stop once no signal is running
