@@ -258,10 +258,28 @@ __global__ void __launch_bounds__(1024) k_lg_setup(LgState S) {
 // largest unselected |c~|, atomicMax on the float bits).  Every
 // wait is bounded (about 2 s); on time-out the error flags get bit 64 and the
 // CTA stops after the copies it issued have landed.
-__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar))
+// A's tiles are read once per iteration and are larger than L2: they are
+// copied with an evict-first L2 policy, so that what the rest of the
+// iteration reuses (W, G, the support's columns, the residuals) stays in L2.
+__device__ __forceinline__ uint64_t l2_evict_first() {
+    uint64_t pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+
+__device__ __forceinline__ void bulk_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar, uint64_t pol) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;"
+                 ::"r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)), "l"(pol)
                  : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d_hint(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y,
+                                                 uint64_t pol) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1, {%3, %4}], [%2], %5;"
+        ::"r"(smem_u32(dst)), "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y), "l"(pol)
+        : "memory");
 }
 
 __host__ __device__ constexpr size_t lg_tma_smem(int stages, int nb, int mpt) {
@@ -299,6 +317,7 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
     if (warp == LG_TMA_CONSUMERS) {
         if (lane != 0) return;
         // producer
+        const uint64_t pol = l2_evict_first();
         int it = 0;
         bool ok = true;
         for (;;) {
@@ -314,7 +333,7 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
                 info[st] = make_int2(blk, ic);
                 mbar_arrive_expect_tx(&full[st], LG_TILE_BYTES);
                 bulk_load_1d(tiles + (size_t)st * LG_TILE_BYTES, src + (size_t)ic * LG_TA * TR, LG_TILE_BYTES,
-                             &full[st]);
+                             &full[st], pol);
             }
             if (!ok) break;
         }
@@ -462,6 +481,7 @@ k_lg_corr_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
 
     if (tid == 0) {
         // producer: the K chunks in order, one stage each
+        const uint64_t pol = l2_evict_first();
         int it = 0;
         bool ok = true;
         for (; it < nk; ++it) {
@@ -472,7 +492,7 @@ k_lg_corr_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             }
             uint8_t* sa = base + (size_t)st * stage_bytes;
             mbar_arrive_expect_tx(&full[st], (uint32_t)stage_bytes);
-            tma_load_2d(sa, &mapA, &full[st], it * LG_MMA_KCH, j0);
+            tma_load_2d_hint(sa, &mapA, &full[st], it * LG_MMA_KCH, j0, pol);
             tma_load_2d(sa + LG_MMA_ATILE, &mapR, &full[st], it * LG_MMA_KCH, s0);
         }
         if (!ok) {
