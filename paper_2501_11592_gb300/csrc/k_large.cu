@@ -730,17 +730,16 @@ __global__ void __launch_bounds__(256) k_lg_lpiv(LgState S, int t) {
     const float* g = S.gsum + (size_t)b * (S.K + 2);
     double acc = 0.0;
     for (int ib = i0; ib < i1; ib += 8) {
-        double wv[8], gv[8];                    // the eight rows' W and g loads before their FMAs
+        double wv[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int i = ib + u;
             wv[u] = (i < i1 && i <= p && p < t) ? Wr[(size_t)i * S.K + p] : 0.0;
-            gv[u] = i < i1 ? (double)g[i] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             const int i = ib + u;
-            if (i < i1 && i <= p && p < t) acc = fma(wv[u], gv[u], acc);
+            if (i < i1 && i <= p && p < t) acc = fma(wv[u], (double)g[i], acc);
         }
     }
     if (p < t) S.lpart[((size_t)b * S.lch + ic) * S.K + p] = acc;
@@ -809,17 +808,16 @@ __global__ void __launch_bounds__(256) k_lg_uupd(LgState S, int t) {
     const double* l = S.l + (size_t)b * S.K;
     double acc = 0.0;
     for (int pb = p0; pb < p1; pb += 8) {
-        double wv[8], lv[8];                    // the eight columns' W and l loads before their FMAs
+        double wv[8];
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
             const int p = pb + v;
             wv[v] = (p < p1 && i <= p) ? Wc[(size_t)p * S.K + i] : 0.0;
-            lv[v] = p < p1 ? __ldcg(l + p) : 0.0;
         }
 #pragma unroll
         for (int v = 0; v < 8; ++v) {
             const int p = pb + v;
-            if (p < p1 && i <= p) acc = fma(wv[v], lv[v], acc);
+            if (p < p1 && i <= p) acc = fma(wv[v], l[p], acc);
         }
     }
     if (i < t) S.upart[((size_t)b * S.lch + pc) * S.K + i] = acc;
