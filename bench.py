@@ -62,7 +62,8 @@ def parse():
 
 
 PROFILE_CASES = ("omp_fp32", "omp_fp8", "clomp_bf16_per_iteration", "clomp_gather", "threshold", "single",
-                 "clfit_pair", "columnwise_image", "large_small", "large_small_clomp", "large_1d", "persist")
+                 "clfit_pair", "columnwise_image", "large_small", "large_small_clomp", "large_mid", "large_1d",
+                 "persist")
 
 
 def profile_case(name):
@@ -108,6 +109,9 @@ def profile_case(name):
     elif name == "large_1d":
         # the full-size long signal (for a launch list of a few iterations only)
         pl = workloads.config_large_1d()
+        cs.omp_solve_batched(dev(pl.A), dev(pl.Y), pl.k, prec="bf16", plan=cs.Plan(pl.m, pl.n, 1, pl.k))
+    elif name == "large_mid":
+        pl = workloads.config_large_1d(n=16384, m=4915, k=600)
         cs.omp_solve_batched(dev(pl.A), dev(pl.Y), pl.k, prec="bf16", plan=cs.Plan(pl.m, pl.n, 1, pl.k))
     elif name in ("large_small", "large_small_clomp"):
         pl = workloads.config_large_1d(n=16384, m=4915, k=100)
