@@ -712,7 +712,7 @@ __device__ void lg_pivot_finish(const LgState& S, int b, int t, double ssq, doub
 // The warp that completes a block of p sums its chunks in order (l_p) and
 // that block's sum l_p^2 and l_p z_p; the last block adds the blocks' sums
 // in order and finishes the pivot.  t = 0: one warp, no l.
-__global__ void __launch_bounds__(256) k_lg_lpiv(LgState S, int t) {
+__global__ void __launch_bounds__(32) k_lg_lpiv(LgState S, int t) {
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int lane = threadIdx.x & 31;
@@ -793,7 +793,7 @@ __global__ void __launch_bounds__(256) k_lg_lpiv(LgState S, int t) {
 // i; the warp that completes a block of i sums its chunks in order (from the
 // block's own chunk: earlier chunks hold no p >= i) and updates those
 // entries (t >= 1; W_tt and x_t come with the pivot).
-__global__ void __launch_bounds__(256) k_lg_uupd(LgState S, int t) {
+__global__ void __launch_bounds__(32) k_lg_uupd(LgState S, int t) {
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int lane = threadIdx.x & 31;
@@ -1597,9 +1597,11 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
             }
             tag += (unsigned)S.steps;
         } else {
+            // one warp per CTA: the items spread over every SM (the float64
+            // unit of one SM is narrow; eight warps on one SM queue on it)
             const int nl = t > 0 ? ceil_div(t, 32) * ceil_div(t, LG_LC) : 1;
-            k_lg_lpiv<<<dim3(ceil_div(nl, 8), Bl), 256, 0, s>>>(S, t);
-            if (t > 0) k_lg_uupd<<<dim3(ceil_div(ceil_div(t, 32) * ceil_div(t, LG_LC), 8), Bl), 256, 0, s>>>(S, t);
+            k_lg_lpiv<<<dim3(nl, Bl), 32, 0, s>>>(S, t);
+            if (t > 0) k_lg_uupd<<<dim3(nl, Bl), 32, 0, s>>>(S, t);
         }
         mark(CS_PHASE_FIT, 1);
         mark(CS_PHASE_RESID, 0);
