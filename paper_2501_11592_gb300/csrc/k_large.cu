@@ -535,23 +535,30 @@ k_lg_corr_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
         const int j = j0 + tid;
         const int nw = (S.n + 31) / 32;
         const uint32_t tbase = tmem + ((uint32_t)(warp * 32) << 16);
+        const int jw = (j0 + warp * 32) >> 5;        // this warp's mask word (32-aligned atoms)
         for (int c0 = 0; c0 < N; c0 += 32) {
+            // lane q fetches signal c0 + q's mask word and status for the whole warp
+            const int bq = s0 + c0 + lane;
+            const bool vq = c0 + lane < N && bq < S.Bl;
+            const uint32_t mword = (vq && jw < nw) ? S.mask[(size_t)bq * nw + jw] : 0u;
+            const int stq = vq ? S.st[bq] : 0;
             uint32_t v[32];
             tmem_ld32(tbase + (uint32_t)c0, v);
             tmem_ld_wait();
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int b = s0 + c0 + q;
+                const uint32_t mw = __shfl_sync(FULL, mword, q);
+                const int stb = __shfl_sync(FULL, stq, q);
                 if (c0 + q >= N || b >= S.Bl) continue;     // the same for the whole warp
                 const float x = fabsf(__uint_as_float(v[q]));
                 float mx = 0.f;
                 if (j < S.n) {
                     S.c[(size_t)b * S.n + j] = x;
-                    const bool sel = (S.mask[(size_t)b * nw + (j >> 5)] >> (j & 31)) & 1u;
-                    if (!sel) mx = x;
+                    if (!((mw >> lane) & 1u)) mx = x;
                 }
                 mx = warp_max(mx);
-                if (lane == 0 && S.st[b] < 0) atomicMax(S.cmax + b, __float_as_uint(mx));
+                if (lane == 0 && stb < 0) atomicMax(S.cmax + b, __float_as_uint(mx));
             }
         }
     }
@@ -774,14 +781,20 @@ __global__ void __launch_bounds__(32) k_lg_lpiv(LgState S, int t) {
         S.cntL[(size_t)b * S.pbmax + pb] = 0u;
         __threadfence();
         prev = atomicAdd(S.cntP + b, 1u);
-        if (prev == (unsigned)(pblocks - 1)) {
-            // last block: the blocks' sums in order, then the pivot
-            __threadfence();
-            double ssq = 0.0, lzs = 0.0;
-            for (int q = 0; q < pblocks; ++q) {
-                ssq += __ldcg(S.pbpart + ((size_t)b * S.pbmax + q) * 2);
-                lzs += __ldcg(S.pbpart + ((size_t)b * S.pbmax + q) * 2 + 1);
-            }
+    }
+    prev = __shfl_sync(FULL, prev, 0);
+    if (prev == (unsigned)(pblocks - 1)) {
+        // last block: the blocks' sums (lane q takes blocks q, q + 32, ...,
+        // then the warp tree), then the pivot
+        __threadfence();
+        double ssq = 0.0, lzs = 0.0;
+        for (int q = lane; q < pblocks; q += 32) {
+            ssq += __ldcg(S.pbpart + ((size_t)b * S.pbmax + q) * 2);
+            lzs += __ldcg(S.pbpart + ((size_t)b * S.pbmax + q) * 2 + 1);
+        }
+        ssq = warp_sum_f64(ssq);
+        lzs = warp_sum_f64(lzs);
+        if (lane == 0) {
             S.cntP[b] = 0u;
             lg_pivot_finish(S, b, t, ssq, lzs);
         }
@@ -1131,21 +1144,26 @@ __global__ void __launch_bounds__(256) k_lg_resid(LgState S, int t1) {
         S.nrm[(size_t)b * S.rblk + rb] = ss;
         S.cntR[(size_t)b * S.rblk + rb] = 0u;
         __threadfence();
-        if (atomicAdd(S.cntN + b, 1u) == (unsigned)(S.rblk - 1)) {
-            // the last row block: ||r|| over the blocks in order, the stopping rule
-            __threadfence();
-            float tot = 0.f;
-            for (int q = 0; q < S.rblk; ++q) tot += __ldcg(S.nrm + (size_t)b * S.rblk + q);
-            S.cntN[b] = 0u;
-            const float rho = sqrtf(tot);
-            S.rnorm[b] = rho;
-            S.ncand[b] = 0;
-            S.cmax[b] = 0u;
-            S.best[b] = 0ull;
-            if ((double)rho <= S.tol) S.st[b] = CS_SIG_REACHED_TOL;
-            else if (t1 >= S.kv[b]) S.st[b] = CS_SIG_REACHED_K;
-            else if (t1 >= S.itv[b]) S.st[b] = CS_SIG_MAX_ITER;
-        }
+        last = atomicAdd(S.cntN + b, 1u) == (unsigned)(S.rblk - 1) ? 1u : 0u;
+    }
+    __syncthreads();
+    if (!last) return;
+    // the last row block: ||r||^2 over the blocks (thread q takes blocks
+    // q, q + 256, ..., then the block tree), the stopping rule
+    __threadfence();
+    float part = 0.f;
+    for (int q = threadIdx.x; q < S.rblk; q += blockDim.x) part += __ldcg(S.nrm + (size_t)b * S.rblk + q);
+    const float tot = block_sum(part, sh);
+    if (threadIdx.x == 0) {
+        S.cntN[b] = 0u;
+        const float rho = sqrtf(tot);
+        S.rnorm[b] = rho;
+        S.ncand[b] = 0;
+        S.cmax[b] = 0u;
+        S.best[b] = 0ull;
+        if ((double)rho <= S.tol) S.st[b] = CS_SIG_REACHED_TOL;
+        else if (t1 >= S.kv[b]) S.st[b] = CS_SIG_REACHED_K;
+        else if (t1 >= S.itv[b]) S.st[b] = CS_SIG_MAX_ITER;
     }
 }
 
