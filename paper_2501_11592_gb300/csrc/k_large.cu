@@ -591,6 +591,8 @@ __global__ void k_lg_prep_k(const float* __restrict__ A, int lda, int m, int n, 
 // ---------------------------------------------------------- selection --
 // Candidates: unselected atoms with |c~| >= max - 2 delta.
 __global__ void __launch_bounds__(256) k_lg_scan(LgState S) {
+    pdl_wait();      // the previous launch of the iteration is complete
+    pdl_trigger();
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -606,6 +608,8 @@ __global__ void __launch_bounds__(256) k_lg_scan(LgState S) {
 
 // float32 re-score of the candidates (one CTA per candidate) and the argmax.
 __global__ void __launch_bounds__(1024) k_lg_rescore(LgState S) {
+    pdl_wait();      // the previous launch of the iteration is complete
+    pdl_trigger();
     __shared__ float sh[33];
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
@@ -631,6 +635,8 @@ __global__ void __launch_bounds__(1024) k_lg_rescore(LgState S) {
 // support atoms (i < t), itself (i = t) and y (i = t + 1), one warp per
 // (entry, 2048-row segment).
 __global__ void __launch_bounds__(256) k_lg_gram(LgState S, int t) {
+    pdl_wait();      // the previous launch of the iteration is complete
+    pdl_trigger();
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const unsigned long long key = S.best[b];
@@ -720,6 +726,8 @@ __device__ void lg_pivot_finish(const LgState& S, int b, int t, double ssq, doub
 // that block's sum l_p^2 and l_p z_p; the last block adds the blocks' sums
 // in order and finishes the pivot.  t = 0: one warp, no l.
 __global__ void __launch_bounds__(32) k_lg_lpiv(LgState S, int t) {
+    pdl_wait();      // the previous launch of the iteration is complete
+    pdl_trigger();
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int lane = threadIdx.x & 31;
@@ -807,6 +815,8 @@ __global__ void __launch_bounds__(32) k_lg_lpiv(LgState S, int t) {
 // block's own chunk: earlier chunks hold no p >= i) and updates those
 // entries (t >= 1; W_tt and x_t come with the pivot).
 __global__ void __launch_bounds__(32) k_lg_uupd(LgState S, int t) {
+    pdl_wait();      // the previous launch of the iteration is complete
+    pdl_trigger();
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int lane = threadIdx.x & 31;
@@ -872,6 +882,8 @@ __device__ __forceinline__ unsigned long long lg_tagged(unsigned tag, float v) {
 // the fit's first tag) and its moments start at zero (with
 // reset_adam_each_iter every moment restarts).
 __global__ void __launch_bounds__(256) k_lgc_append(LgState S, int t, unsigned tag0) {
+    pdl_wait();      // the previous launch of the iteration is complete
+    pdl_trigger();
     const int b = blockIdx.y;
     if (S.st[b] >= 0) return;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -1095,6 +1107,8 @@ __global__ void __launch_bounds__(256) k_lgc_fit(LgState S, int t1, int R, int t
 // order and applies the stopping rule of Eq. 2, resetting the selection
 // state for the next iteration.
 __global__ void __launch_bounds__(256) k_lg_resid(LgState S, int t1) {
+    pdl_wait();      // the previous launch of the iteration is complete
+    pdl_trigger();
     __shared__ int sj[LG_RQ];
     __shared__ float sx[LG_RQ];
     __shared__ float sh[33];
@@ -1589,15 +1603,15 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
         else LG_TRY(launch_corr(S, cfg, s));
         mark(CS_PHASE_CORR, 1);
         mark(CS_PHASE_SELECT, 0);
-        k_lg_scan<<<dim3(ceil_div(S.n, 256), Bl), 256, 0, s>>>(S);
-        k_lg_rescore<<<dim3(std::max(LG_RESCORE_MIN_CTAS, 2 * S.nsm / Bl), Bl), 1024, 0, s>>>(S);
-        k_lg_gram<<<dim3(ceil_div((t + 2) * S.nseg, 8), Bl), 256, 0, s>>>(S, t);
+        LG_TRY(launch_pdl(k_lg_scan, dim3(ceil_div(S.n, 256), Bl), dim3(256), 0, s, S));
+        LG_TRY(launch_pdl(k_lg_rescore, dim3(std::max(LG_RESCORE_MIN_CTAS, 2 * S.nsm / Bl), Bl), dim3(1024), 0, s, S));
+        LG_TRY(launch_pdl(k_lg_gram, dim3(ceil_div((t + 2) * S.nseg, 8), Bl), dim3(256), 0, s, S, t));
         mark(CS_PHASE_SELECT, 1);
         mark(CS_PHASE_FIT, 0);
         if (cl) {
             // Gram form: grow G and b, then the T Adam steps on t + 1 coordinates,
             // in one cooperative launch where the grid fits, else one launch per step
-            k_lgc_append<<<dim3(ceil_div(t + 1, 256), Bl), 256, 0, s>>>(S, t, tag);
+            LG_TRY(launch_pdl(k_lgc_append, dim3(ceil_div(t + 1, 256), Bl), dim3(256), 0, s, S, t, tag));
             const int tau0 = S.reset ? 0 : t * S.steps;
             int gx = 0, smem = 0;
             const int R = fit_rows(t + 1, gx, smem);
@@ -1618,12 +1632,12 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
             // one warp per CTA: the items spread over every SM (the float64
             // unit of one SM is narrow; eight warps on one SM queue on it)
             const int nl = t > 0 ? ceil_div(t, 32) * ceil_div(t, LG_LC) : 1;
-            k_lg_lpiv<<<dim3(nl, Bl), 32, 0, s>>>(S, t);
-            if (t > 0) k_lg_uupd<<<dim3(nl, Bl), 32, 0, s>>>(S, t);
+            LG_TRY(launch_pdl(k_lg_lpiv, dim3(nl, Bl), dim3(32), 0, s, S, t));
+            if (t > 0) LG_TRY(launch_pdl(k_lg_uupd, dim3(nl, Bl), dim3(32), 0, s, S, t));
         }
         mark(CS_PHASE_FIT, 1);
         mark(CS_PHASE_RESID, 0);
-        k_lg_resid<<<dim3(S.rblk, ceil_div(t + 1, LG_RQ), Bl), 256, 0, s>>>(S, t + 1);
+        LG_TRY(launch_pdl(k_lg_resid, dim3(S.rblk, ceil_div(t + 1, LG_RQ), Bl), dim3(256), 0, s, S, t + 1));
         mark(CS_PHASE_RESID, 1);
         LG_TRY(cudaGetLastError());
         // every 64 iterations: stop once no signal is running
