@@ -84,7 +84,9 @@ struct LgState {
     int mpt, nc, njb;               // tiles: rows padded to the tile height, row chunks, atom blocks of 64
     int nsm, smem_optin;            // the device's SMs and per-CTA shared-memory limit
     int mma, mpk;                   // correlation as a tensor-core GEMM (bf16, many signals); rows to 64
-    const __nv_bfloat16* Ak;        // mma: [n][mpk] bf16 copy of A, K-major (rows >= m zero)
+    const __nv_bfloat16* Ak;        // mma: bf16 copy of A in 16 KB tiles [n/128][mpk/64] of 128 atoms x 64
+                                    // K values, each the 128-byte-swizzled shared-memory image of the
+                                    // tile (rows >= m and atoms >= n zero)
     __nv_bfloat16* R16;             // mma: [Bl][mpk] bf16 copy of the residuals (rows >= m zero)
     double tol;
     const float* A;                 // caller's A (float32, leading dimension lda)
@@ -440,8 +442,7 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
 // get bit 128, the epilogue is skipped and the CTA returns after its copies
 // and MMAs in flight have finished and its tensor memory is freed.
 __global__ void __launch_bounds__(LG_MMA_THREADS, 1)
-k_lg_corr_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapR, LgState S,
-              int stages, int N, int tmem_cols) {
+k_lg_corr_mma(const __grid_constant__ CUtensorMap mapR, LgState S, int stages, int N, int tmem_cols) {
     extern __shared__ uint8_t lmsm[];
     __shared__ __align__(8) uint64_t full[LG_MMA_MAX_STAGES];
     __shared__ __align__(8) uint64_t empty[LG_MMA_MAX_STAGES];
@@ -492,7 +493,7 @@ k_lg_corr_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
             }
             uint8_t* sa = base + (size_t)st * stage_bytes;
             mbar_arrive_expect_tx(&full[st], (uint32_t)stage_bytes);
-            tma_load_2d_hint(sa, &mapA, &full[st], it * LG_MMA_KCH, j0, pol);
+            bulk_load_1d(sa, S.Ak + ((size_t)blockIdx.x * nk + it) * (LG_MMA_ATILE / 2), LG_MMA_ATILE, &full[st], pol);
             tma_load_2d(sa + LG_MMA_ATILE, &mapR, &full[st], it * LG_MMA_KCH, s0);
         }
         if (!ok) {
@@ -570,22 +571,30 @@ k_lg_corr_mma(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ 
     }
 }
 
-// bf16 copy of A, K-major ([n][mpk], rows >= m zero), and the largest column
-// norm (one warp per atom).
+// bf16 copy of A for the GEMM correlation, in 16 KB tiles of 128 atoms x 64
+// K values, each stored as the shared-memory image that a TMA copy with the
+// 128-byte swizzle would produce -- row r (atom) of 128 bytes, its 16-byte
+// chunk c at position c ^ (r mod 8) -- so that one 1-D bulk copy per tile
+// lands it ready for the MMA descriptor; and the largest column norm (one
+// warp per atom of the padded range).
 __global__ void k_lg_prep_k(const float* __restrict__ A, int lda, int m, int n, int mpk,
                             __nv_bfloat16* __restrict__ Ak, float* colmax) {
     const int lane = threadIdx.x & 31;
     const int j = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (j >= n) return;
-    const float* a = A + (size_t)j * lda;
+    if (j >= round_up(n, 128)) return;
+    const float* a = A + (size_t)min(j, n - 1) * lda;
+    const int nkc = mpk / LG_MMA_KCH, r = j % 128;
+    __nv_bfloat16* tiles = Ak + (size_t)(j / 128) * nkc * (LG_MMA_ATILE / 2);
     float ss = 0.f;
     for (int i = lane; i < mpk; i += 32) {
-        const float v = i < m ? a[i] : 0.f;
+        const float v = (i < m && j < n) ? a[i] : 0.f;
         ss = fmaf(v, v, ss);
-        Ak[(size_t)j * mpk + i] = __float2bfloat16_rn(v);
+        const int kc = i / LG_MMA_KCH, e = i % LG_MMA_KCH;
+        const int off = r * 64 + (((e >> 3) ^ (r & 7)) << 3) + (e & 7);   // bf16 elements within the tile
+        tiles[(size_t)kc * (LG_MMA_ATILE / 2) + off] = __float2bfloat16_rn(v);
     }
     ss = warp_sum(ss);
-    if (lane == 0) atomicMax(reinterpret_cast<unsigned*>(colmax), __float_as_uint(sqrtf(ss)));
+    if (lane == 0 && j < n) atomicMax(reinterpret_cast<unsigned*>(colmax), __float_as_uint(sqrtf(ss)));
 }
 
 // ---------------------------------------------------------- selection --
@@ -1230,7 +1239,7 @@ LgLayout lg_layout(int m, int n, int Bl, int kmax, int bf16, int cl) {
     LgLayout L{};
     if (lg_uses_mma(bf16, Bl)) {
         const size_t mpk = (size_t)round_up(m, LG_MMA_KCH);
-        L.Ak = take(sizeof(__nv_bfloat16) * (size_t)n * mpk);
+        L.Ak = take(sizeof(__nv_bfloat16) * (size_t)round_up(n, 128) * mpk);
         L.R16 = take(sizeof(__nv_bfloat16) * B * mpk);
     } else {
         L.At = bf16 ? take(sizeof(__nv_bfloat16) * (size_t)round_up(n, LG_TA) * (size_t)round_up(m, lg_tr<__nv_bfloat16>()))
@@ -1313,7 +1322,7 @@ cudaError_t launch_corr_tma(const LgState& S, cudaStream_t s) {
 // The GEMM correlation: N = the signals per pass rounded up to 16 (at most
 // 256), as many ring stages as shared memory holds.
 struct LgMma {
-    CUtensorMap mapA, mapR;
+    CUtensorMap mapR;
     int N, stages, tmem_cols;
     size_t smem;
 };
@@ -1330,8 +1339,7 @@ cudaError_t setup_corr_mma(const LgState& S, LgMma& M) {
     M.stages = std::min(LG_MMA_MAX_STAGES, (dyn_max - 1024) / stage_bytes);   // 1024: alignment slack
     if (M.stages < 2) return cudaErrorInvalidValue;
     M.smem = (size_t)M.stages * stage_bytes + 1024;
-    if (!make_tma_map_bf16(&M.mapA, S.Ak, S.mpk, S.n, (size_t)S.mpk * 2, 128) ||
-        !make_tma_map_bf16(&M.mapR, S.R16, S.mpk, S.Bl, (size_t)S.mpk * 2, M.N))
+    if (!make_tma_map_bf16(&M.mapR, S.R16, S.mpk, S.Bl, (size_t)S.mpk * 2, M.N))
         return cudaErrorInvalidValue;
     static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
     return attr;
@@ -1339,7 +1347,7 @@ cudaError_t setup_corr_mma(const LgState& S, LgMma& M) {
 
 cudaError_t launch_corr_mma(const LgState& S, const LgMma& M, cudaStream_t s) {
     const dim3 grid(ceil_div(S.n, 128), ceil_div(S.Bl, LG_MMA_MAXN));
-    k_lg_corr_mma<<<grid, LG_MMA_THREADS, M.smem, s>>>(M.mapA, M.mapR, S, M.stages, M.N, M.tmem_cols);
+    k_lg_corr_mma<<<grid, LG_MMA_THREADS, M.smem, s>>>(M.mapR, S, M.stages, M.N, M.tmem_cols);
     return cudaGetLastError();
 }
 
@@ -1508,7 +1516,7 @@ cudaError_t large_solve(const LargeCall& call, void* ws, size_t ws_bytes, cudaSt
     LG_TRY(cudaMemsetAsync(S.cntG, 0, sizeof(unsigned) * (size_t)Bl * ((S.K + 2) + 2 * S.pbmax + S.rblk + 2), s));
     mark(CS_PHASE_SETUP, 0);
     if (S.mma)
-        k_lg_prep_k<<<ceil_div(S.n, 8), 256, 0, s>>>(S.A, S.lda, S.m, S.n, S.mpk, const_cast<__nv_bfloat16*>(S.Ak),
+        k_lg_prep_k<<<ceil_div(round_up(S.n, 128), 8), 256, 0, s>>>(S.A, S.lda, S.m, S.n, S.mpk, const_cast<__nv_bfloat16*>(S.Ak),
                                                      const_cast<float*>(S.colmax));
     else if (S.bf16)
         k_lg_prep<__nv_bfloat16><<<ceil_div(S.njb * LG_TA, 8), 256, 0, s>>>(
