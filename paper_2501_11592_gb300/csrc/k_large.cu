@@ -427,6 +427,22 @@ __global__ void __launch_bounds__(LG_TMA_THREADS, 1) k_lg_corr_tma(LgState S, in
     }
 }
 
+// Transposed max-reduction: lane l ends with the maximum over the warp of
+// k[l] (in k[0]), 31 shuffles for the 32 values.
+__device__ __forceinline__ void lg_max_scatter32(uint32_t (&k)[32]) {
+    const unsigned lane = threadIdx.x & 31u;
+#pragma unroll
+    for (int off = 16; off >= 1; off >>= 1) {
+        const bool upper = (lane & off) != 0;
+#pragma unroll
+        for (int i = 0; i < off; ++i) {
+            const uint32_t send = upper ? k[i] : k[i + off];
+            const uint32_t keep = upper ? k[i + off] : k[i];
+            k[i] = max(keep, __shfl_xor_sync(0xffffffffu, send, off));
+        }
+    }
+}
+
 // Correlation of a pass of up to 256 signals as one tensor-core GEMM
 // (bf16 operands, float32 accumulation in tensor memory): CTA x owns atoms
 // 128 x .. 128 x + 127 (UMMA M, the TMEM lanes) and the pass's N signals
@@ -546,21 +562,22 @@ k_lg_corr_mma(const __grid_constant__ CUtensorMap mapR, LgState S, int stages, i
             uint32_t v[32];
             tmem_ld32(tbase + (uint32_t)c0, v);
             tmem_ld_wait();
+            // |c~| of the 32 signals for this atom; the unselected ones (as
+            // float bits: non-negative floats order like their bits) go to a
+            // transposed max-reduction, after which lane q holds the warp's
+            // largest for signal c0 + q
+            uint32_t key[32];
 #pragma unroll
             for (int q = 0; q < 32; ++q) {
                 const int b = s0 + c0 + q;
                 const uint32_t mw = __shfl_sync(FULL, mword, q);
-                const int stb = __shfl_sync(FULL, stq, q);
-                if (c0 + q >= N || b >= S.Bl) continue;     // the same for the whole warp
                 const float x = fabsf(__uint_as_float(v[q]));
-                float mx = 0.f;
-                if (j < S.n) {
-                    S.c[(size_t)b * S.n + j] = x;
-                    if (!((mw >> lane) & 1u)) mx = x;
-                }
-                mx = warp_max(mx);
-                if (lane == 0 && stb < 0) atomicMax(S.cmax + b, __float_as_uint(mx));
+                const bool valid = c0 + q < N && b < S.Bl && j < S.n;
+                if (valid) S.c[(size_t)b * S.n + j] = x;
+                key[q] = (valid && !((mw >> lane) & 1u)) ? __float_as_uint(x) : 0u;
             }
+            lg_max_scatter32(key);
+            if (vq && stq < 0) atomicMax(S.cmax + bq, key[0]);
         }
     }
     tc_fence_before();
