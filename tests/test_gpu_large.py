@@ -225,3 +225,40 @@ def test_large_path_gemm_correlation_two_passes(cs_gpu, torch):
     A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
     g = _large_solve(cs_gpu, torch, A32, Y32, k, "omp")
     print(compare(g, oracle.omp(A64, Y64, k)))
+
+
+def test_large_path_gemm_correlation_edges(cs_gpu, torch):
+    """The GEMM correlation's group (10 signals, bf16) with a NaN signal
+    (status 4: its residual column is NaN but no other signal's is touched),
+    a zero signal under tol (1), max_iter (2) and a duplicated atom (the tie
+    to the lower index): the same bits as the signals solved in groups of
+    fewer than eight (streaming), and the oracle's results."""
+    rng = np.random.default_rng(503)
+    m, n, k = 1100, 900, 40
+    A = workloads.gaussian_matrix(rng, m, n)
+    A[:, 610] = A[:, 23]
+    X = workloads.sparse_coefficients(rng, n, 10, 12, values="pm")
+    Y = A @ X + 0.01 * rng.standard_normal((m, 10))
+    Y[5, 1] = np.nan
+    Y[:, 2] = 0.0
+    Y[:, 3] = 3.0 * A[:, 23] + 0.25 * A[:, 90]
+    A32, Y32, A64, Y64 = f32_problem(A, Y)
+    Am = torch.from_numpy(np.asfortranarray(A32)).cuda()
+
+    def solve(cols):
+        Yc = torch.from_numpy(np.asfortranarray(Y32[:, cols])).cuda()
+        r = cs_gpu.omp_solve_batched(Am, Yc, k, prec="bf16", plan=cs_gpu.Plan(m, n, len(cols), k), tol=1e-3,
+                                     max_iter=30)
+        torch.cuda.synchronize()
+        return to_numpy(r)
+
+    one = solve(list(range(10)))
+    a, b = solve(list(range(5))), solve(list(range(5, 10)))
+    for q in ("support", "coef", "n_iter", "status"):
+        assert np.array_equal(one[q], np.concatenate([a[q], b[q]], axis=0)), q
+    assert np.array_equal(one["res_norm"], np.concatenate([a["res_norm"], b["res_norm"]]), equal_nan=True)
+    assert one["status"][1] == 4 and one["status"][2] == 1 and one["support"][3, 0] == 23
+    assert one["status"][0] == 2 and one["n_iter"][0] == 30
+    ok = [0, 3, 4, 5, 6, 7, 8, 9]
+    o = oracle.omp(A64, Y64[:, ok], k, tol=1e-3, max_iter=30)
+    compare({q: v[ok] for q, v in one.items()}, o)
