@@ -10,6 +10,7 @@
 #include <map>
 #include <mutex>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "cs_internal.cuh"
@@ -65,6 +66,15 @@ struct cs_plan {
     int no_large = 0;          // 1: never run the large-instance path (it allocates)
     char* lg = nullptr;        // workspace of the large-instance path, on first use
     size_t lg_bytes = 0;
+    // workers that run an uneven batch's large OMP groups side by side: a
+    // stream, a workspace and a completion event each (made on first use)
+    struct LgWorker {
+        cudaStream_t s = nullptr;
+        char* ws = nullptr;
+        size_t bytes = 0;
+        cudaEvent_t done = nullptr;
+    };
+    std::vector<LgWorker> lgw;
     int mp_max = 0, mh_max = 0, nw_max = 0, nch_max = 0;
     char* ws = nullptr;
     size_t ws_bytes = 0;
@@ -340,20 +350,20 @@ bool needs_large(const cs_plan* P, int m, int n, int k, int prec) {
     return m > kMaxRowChunks * 128 || k > P->k_max || (prec == CS_CORR_BF16 && !corr_tc_supported(m, n));
 }
 
-cs_status ensure_lg(cs_plan* P, size_t bytes) {
-    if (bytes <= P->lg_bytes) return CS_OK;
-    if (P->lg) {
-        cudaError_t e = cudaFree(P->lg);
-        P->lg = nullptr;
-        P->lg_bytes = 0;
+cs_status ensure_lg(char** buf, size_t* have, size_t bytes) {
+    if (bytes <= *have) return CS_OK;
+    if (*buf) {
+        cudaError_t e = cudaFree(*buf);
+        *buf = nullptr;
+        *have = 0;
         if (e != cudaSuccess) return cuda_fail(e, "cudaFree");
     }
-    cudaError_t e = cudaMalloc(&P->lg, bytes);
+    cudaError_t e = cudaMalloc(buf, bytes);
     if (e != cudaSuccess) {
-        P->lg = nullptr;
+        *buf = nullptr;
         return fail(CS_ENOMEM, "cudaMalloc(large-instance workspace, %zu bytes): %s", bytes, cudaGetErrorString(e));
     }
-    P->lg_bytes = bytes;
+    *have = bytes;
     return CS_OK;
 }
 
@@ -399,6 +409,8 @@ void large_mark(void* vctx, int phase, int after) {
 // OMP or Gram-form CLOMP of signals sharing A on the large-instance path, in
 // chunks whose workspace stays within a few GB.
 constexpr size_t kLargeChunkBytes = (size_t)8 << 30;
+// Large OMP groups of an uneven batch run at once, at most this many.
+constexpr int kVarlenWorkers = 4;
 
 // CLOMP configurations the large-instance path runs: the Gram form, one atom
 // per iteration, no prior.
@@ -410,9 +422,13 @@ bool large_clomp_ok(const cs_clomp_params* cp) {
 template <class F>
 cudaError_t timed(cs_plan* P, int phase, cudaStream_t s, F&& launch);
 
-cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const std::vector<const float*>& ys,
-                      const std::vector<LargeOut>& outs, const cs_omp_params* op, const cs_clomp_params* cp,
-                      cudaStream_t s) {
+// The large-instance solve on stream s with the workspace *ws (grown as
+// needed).  marks: count and time the phases in the plan (one thread at a
+// time only); tune_mu: guards the plan's tuned configurations when several
+// threads solve at once.
+cs_status solve_large_on(cs_plan* P, const float* A, int m, int n, int lda, const std::vector<const float*>& ys,
+                         const std::vector<LargeOut>& outs, const cs_omp_params* op, const cs_clomp_params* cp,
+                         cudaStream_t s, char** ws, size_t* ws_bytes, bool marks, std::mutex* tune_mu) {
     if (P->no_large) return fail(CS_ENOTSUP, "this entry point runs only the on-chip kernels (m <= 1024, k <= 64, "
                                              "bf16: m <= 256, n <= 4096)");
     if (cp && !large_clomp_ok(cp))
@@ -467,26 +483,42 @@ cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const s
         call.bf16 = bf16;
         call.live_host = &live;
         LargeMarkCtx mc{P, s};
-        call.mark = large_mark;
+        call.mark = marks ? large_mark : nullptr;
         call.mark_ctx = &mc;
         // the correlation's configuration for this size class (tuned once)
         const std::string key = size_key("large correlation", op->prec, m, n, (int)nb);
-        auto tk = P->tuned.find(key);
         int chosen = -1;
-        call.corr_cfg = tk != P->tuned.end() ? tk->second : -1;
+        bool known;
+        {
+            std::unique_lock<std::mutex> lk;
+            if (tune_mu) lk = std::unique_lock<std::mutex>(*tune_mu);
+            auto tk = P->tuned.find(key);
+            known = tk != P->tuned.end();
+            call.corr_cfg = known ? tk->second : -1;
+        }
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         call.tune = P->autotune && cudaStreamIsCapturing(s, &cap) == cudaSuccess && cap == cudaStreamCaptureStatusNone;
         call.chosen_cfg = &chosen;
         const size_t need = large_ws_bytes(m, n, (int)nb, kmax, bf16, clf);
         call.cl = cp ? &cl : nullptr;
         call.errflag = P->counters + 1;
-        cs_status st = ensure_lg(P, need);
+        cs_status st = ensure_lg(ws, ws_bytes, need);
         if (st != CS_OK) return st;
-        cudaError_t e = large_solve(call, P->lg, P->lg_bytes, s);
+        cudaError_t e = large_solve(call, *ws, *ws_bytes, s);
         if (e != cudaSuccess) return cuda_fail(e, "large-instance solve");
-        if (call.tune && tk == P->tuned.end() && chosen >= 0) P->tuned[key] = chosen;
+        if (call.tune && !known && chosen >= 0) {
+            std::unique_lock<std::mutex> lk;
+            if (tune_mu) lk = std::unique_lock<std::mutex>(*tune_mu);
+            P->tuned[key] = chosen;
+        }
     }
     return CS_OK;
+}
+
+cs_status solve_large(cs_plan* P, const float* A, int m, int n, int lda, const std::vector<const float*>& ys,
+                      const std::vector<LargeOut>& outs, const cs_omp_params* op, const cs_clomp_params* cp,
+                      cudaStream_t s) {
+    return solve_large_on(P, A, m, n, lda, ys, outs, op, cp, s, &P->lg, &P->lg_bytes, true, nullptr);
 }
 
 IterArgs make_args(cs_plan* P, int m, int n, int B, const cs_omp_params* op, int32_t* support,
@@ -1249,18 +1281,93 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
             CS_TRY_LAUNCH(launch_varlen_scatter(Ot, x0.k, Bg, Sb, Cb, Nb, Rb, Tb, s), "varlen scatter");
         }
     }
-    for (const auto& g : lgroups) {
-        const cs_instance& x0 = inst[g[0]];
-        std::vector<const float*> ys(g.size());
-        std::vector<LargeOut> outs(g.size());
+    auto group_args = [&](const std::vector<int>& g, std::vector<const float*>& ys, std::vector<LargeOut>& outs) {
+        ys.resize(g.size());
+        outs.resize(g.size());
         for (size_t j = 0; j < g.size(); ++j) {
             const cs_instance& x = inst[g[j]];
             ys[j] = x.y;
             outs[j] = LargeOut{x.support, x.coef, x.n_iter, x.res_norm, x.sig_status, x.k};
         }
-        cs_status st = solve_large(P, x0.A, x0.m, x0.n, x0.lda, ys, outs, op, cp, s);
-        if (st != CS_OK) return st;
+    };
+    // CLOMP's large groups, or a single one: one after another on s (the
+    // CLOMP fit is a cooperative launch: its CTAs must all be resident)
+    if (cp || lgroups.size() < 2) {
+        for (const auto& g : lgroups) {
+            const cs_instance& x0 = inst[g[0]];
+            std::vector<const float*> ys;
+            std::vector<LargeOut> outs;
+            group_args(g, ys, outs);
+            cs_status st = solve_large(P, x0.A, x0.m, x0.n, x0.lda, ys, outs, op, cp, s);
+            if (st != CS_OK) return st;
+        }
+        return CS_OK;
     }
+    // OMP's large groups side by side: each group's iterations are
+    // latency-bound launches that leave most of the GPU idle, so up to
+    // kVarlenWorkers groups run at once, each worker with its own host
+    // thread, stream and workspace, taking the groups in order of decreasing
+    // work (k x n x m) from a shared counter.  The workers' streams start
+    // after the work already on s, and s continues after all of them.
+    const int nw = (int)std::min<size_t>(kVarlenWorkers, lgroups.size());
+    while ((int)P->lgw.size() < nw) {
+        cs_plan::LgWorker w;
+        cudaError_t e = cudaStreamCreateWithFlags(&w.s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&w.done, cudaEventDisableTiming);
+        if (e != cudaSuccess) {
+            if (w.s) cudaStreamDestroy(w.s);
+            return cuda_fail(e, "varlen worker stream");
+        }
+        P->lgw.push_back(w);
+    }
+    std::vector<size_t> order(lgroups.size());
+    std::vector<double> cost(lgroups.size());
+    for (size_t g = 0; g < lgroups.size(); ++g) {
+        const cs_instance& x0 = inst[lgroups[g][0]];
+        int kmax = 0;
+        for (int i : lgroups[g]) kmax = std::max(kmax, inst[i].k);
+        cost[g] = (double)kmax * x0.n * x0.m;
+        order[g] = g;
+    }
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    cudaEvent_t start = pool_event(P);
+    if (!start) return fail(CS_ECUDA, "varlen: no event");
+    CS_TRY_LAUNCH(cudaEventRecord(start, s), "varlen start event");
+    for (int w = 0; w < nw; ++w) CS_TRY_LAUNCH(cudaStreamWaitEvent(P->lgw[w].s, start, 0), "varlen worker wait");
+    std::atomic<size_t> next{0};
+    std::mutex tune_mu;
+    std::vector<cs_status> wst(nw, CS_OK);
+    std::vector<std::string> wmsg(nw);
+    auto work = [&](int w) {
+        cudaSetDevice(P->device);
+        cs_plan::LgWorker& W = P->lgw[w];
+        for (;;) {
+            const size_t q = next.fetch_add(1);
+            if (q >= order.size()) break;
+            const auto& g = lgroups[order[q]];
+            const cs_instance& x0 = inst[g[0]];
+            std::vector<const float*> ys;
+            std::vector<LargeOut> outs;
+            group_args(g, ys, outs);
+            const cs_status st = solve_large_on(P, x0.A, x0.m, x0.n, x0.lda, ys, outs, op, nullptr, W.s, &W.ws,
+                                                &W.bytes, false, &tune_mu);
+            if (st != CS_OK) {
+                wst[w] = st;
+                wmsg[w] = g_last_error;
+                next.store(order.size());      // the other workers stop after their current group
+                break;
+            }
+        }
+        cudaEventRecord(W.done, W.s);
+    };
+    std::vector<std::thread> threads;
+    for (int w = 1; w < nw; ++w) threads.emplace_back(work, w);
+    work(0);
+    for (auto& t : threads) t.join();
+    for (int w = 0; w < nw; ++w) CS_TRY_LAUNCH(cudaStreamWaitEvent(s, P->lgw[w].done, 0), "varlen join");
+    P->pool.push_back(start);
+    for (int w = 0; w < nw; ++w)
+        if (wst[w] != CS_OK) return fail(wst[w], "%s", wmsg[w].c_str());
     return CS_OK;
 }
 
@@ -1336,6 +1443,11 @@ cs_status cs_plan_destroy(cs_plan* plan) {
     if (plan->io) cudaFree(plan->io);
     if (plan->vl) cudaFree(plan->vl);
     if (plan->lg) cudaFree(plan->lg);
+    for (auto& w : plan->lgw) {
+        if (w.s) cudaStreamDestroy(w.s);
+        if (w.ws) cudaFree(w.ws);
+        if (w.done) cudaEventDestroy(w.done);
+    }
     delete plan;
     return CS_OK;
 }
