@@ -266,8 +266,14 @@ typedef struct {
  * call groups the instances the on-chip kernels take by (A, m, n, lda, k),
  * gathers each group's measurements into a batch, runs the batched solver on
  * it and scatters the outputs back; the others run on the large-instance
- * path grouped by (A, m, n, lda), each with its own k; all on `stream`, one
- * group after another.  params->k is ignored (each instance has its own).
+ * path grouped by (A, m, n, lda), each with its own k.  The on-chip groups
+ * run one after another on `stream`; with plain OMP, up to four large
+ * groups run at once, each on its own host thread, stream and workspace
+ * (the plan keeps them for later calls), started after the work already on
+ * `stream`, which waits for all of them before the call returns (CLOMP's
+ * large groups run one after another on `stream`).  Those concurrent groups
+ * are not counted in cs_plan_profile.  params->k is ignored (each instance
+ * has its own).
  * An instance is not solved -- its sig_status is set to CS_SIG_UNSUPPORTED
  * (its A is never read) and the call goes on with the others -- when its
  * sizes exceed the plan (m > m_max, n > n_max or k > k_max), when it needs
