@@ -411,7 +411,7 @@ def bench_uneven(cs, torch, stream, barrier):
         st = np.array([int(o.status[0]) for o in outs])
         res["omp_" + prec] = {"s_per_batch": wall, "instances_per_s": len(items) / wall,
                               "solved": int(np.sum(st != cs.SIG_UNSUPPORTED)), "refused": int(np.sum(st == cs.SIG_UNSUPPORTED)),
-                              "note": "wall clock of one call (host loop over groups; large groups synchronise every 64 iterations)"}
+                              "note": "wall clock of one call (on-chip groups one after another; plain-OMP large groups up to four at once on their own streams, each synchronising every 64 iterations)"}
     fn = lambda: cs.clomp_solve_varlen(items, prec="bf16", plan=plan, **CL)
     outs = fn()
     barrier()
