@@ -267,12 +267,12 @@ typedef struct {
  * gathers each group's measurements into a batch, runs the batched solver on
  * it and scatters the outputs back; the others run on the large-instance
  * path grouped by (A, m, n, lda), each with its own k.  The on-chip groups
- * run one after another on `stream`; with plain OMP, up to four large
- * groups run at once, each on its own host thread, stream and workspace
- * (the plan keeps them for later calls), started after the work already on
- * `stream`, which waits for all of them before the call returns (CLOMP's
- * large groups run one after another on `stream`).  Those concurrent groups
- * are not counted in cs_plan_profile.  params->k is ignored (each instance
+ * run one after another on `stream`; up to four large groups run at once,
+ * each on its own host thread, stream and workspace (the plan keeps them for
+ * later calls), started after the work already on `stream`, which waits for
+ * all of them before the call returns (CLOMP's fits then run one launch per
+ * Adam step instead of the cooperative launch).  Those concurrent groups are
+ * not counted in cs_plan_profile.  params->k is ignored (each instance
  * has its own).
  * An instance is not solved -- its sig_status is set to CS_SIG_UNSUPPORTED
  * (its A is never read) and the call goes on with the others -- when its

@@ -424,8 +424,9 @@ cudaError_t timed(cs_plan* P, int phase, cudaStream_t s, F&& launch);
 
 // The large-instance solve on stream s with the workspace *ws (grown as
 // needed).  marks: count and time the phases in the plan (one thread at a
-// time only); tune_mu: guards the plan's tuned configurations when several
-// threads solve at once.
+// time only); tune_mu (non-null: the solve runs beside others on the device)
+// guards the plan's tuned configurations, and then CLOMP finds its Adam
+// table already made and runs no cooperative launch.
 cs_status solve_large_on(cs_plan* P, const float* A, int m, int n, int lda, const std::vector<const float*>& ys,
                          const std::vector<LargeOut>& outs, const cs_omp_params* op, const cs_clomp_params* cp,
                          cudaStream_t s, char** ws, size_t* ws_bytes, bool marks, std::mutex* tune_mu) {
@@ -446,11 +447,15 @@ cs_status solve_large_on(cs_plan* P, const float* A, int m, int n, int lda, cons
         // Adam factors for every step of the longest signal (one state for the solve)
         const int iters = op->max_iter > 0 ? std::min(kmax, op->max_iter) : kmax;
         const int len = (cp->reset_adam_each_iter ? 1 : iters) * std::max(cp->steps, 1);
-        cs_status st = ensure_tab(P, len);
-        if (st != CS_OK) return st;
-        CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] {
-                          return launch_adam_table(P->tab, len, cp->lr, cp->beta1, cp->beta2, s);
-                      }), "adam table");
+        if (!tune_mu) {
+            cs_status st = ensure_tab(P, len);
+            if (st != CS_OK) return st;
+            CS_TRY_LAUNCH(timed(P, CS_PHASE_SETUP, s, [&] {
+                              return launch_adam_table(P->tab, len, cp->lr, cp->beta1, cp->beta2, s);
+                          }), "adam table");
+        } else if (len > P->tab_cap) {
+            return fail(CS_EINVAL, "internal: the Adam table was not made for this group");
+        }
         cl.steps = cp->steps;
         cl.beta1 = cp->beta1;
         cl.beta2 = cp->beta2;
@@ -501,6 +506,7 @@ cs_status solve_large_on(cs_plan* P, const float* A, int m, int n, int lda, cons
         call.chosen_cfg = &chosen;
         const size_t need = large_ws_bytes(m, n, (int)nb, kmax, bf16, clf);
         call.cl = cp ? &cl : nullptr;
+        call.no_coop = tune_mu ? 1 : 0;
         call.errflag = P->counters + 1;
         cs_status st = ensure_lg(ws, ws_bytes, need);
         if (st != CS_OK) return st;
@@ -1290,9 +1296,8 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
             outs[j] = LargeOut{x.support, x.coef, x.n_iter, x.res_norm, x.sig_status, x.k};
         }
     };
-    // CLOMP's large groups, or a single one: one after another on s (the
-    // CLOMP fit is a cooperative launch: its CTAs must all be resident)
-    if (cp || lgroups.size() < 2) {
+    // a single large group: on s
+    if (lgroups.size() < 2) {
         for (const auto& g : lgroups) {
             const cs_instance& x0 = inst[g[0]];
             std::vector<const float*> ys;
@@ -1303,12 +1308,15 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
         }
         return CS_OK;
     }
-    // OMP's large groups side by side: each group's iterations are
-    // latency-bound launches that leave most of the GPU idle, so up to
-    // kVarlenWorkers groups run at once, each worker with its own host
-    // thread, stream and workspace, taking the groups in order of decreasing
-    // work (k x n x m) from a shared counter.  The workers' streams start
-    // after the work already on s, and s continues after all of them.
+    // Large groups side by side: each group's iterations are latency-bound
+    // launches that leave most of the GPU idle, so up to kVarlenWorkers
+    // groups run at once, each worker with its own host thread, stream and
+    // workspace, taking the groups in order of decreasing work (k x n x m)
+    // from a shared counter.  The workers' streams start after the work
+    // already on s, and s continues after all of them.  CLOMP: the Adam table
+    // is made once, here, for the longest group, and the fits run without
+    // cooperative launches (a cooperative grid's CTAs could not all be
+    // resident beside the other groups' kernels).
     const int nw = (int)std::min<size_t>(kVarlenWorkers, lgroups.size());
     while ((int)P->lgw.size() < nw) {
         cs_plan::LgWorker w;
@@ -1330,6 +1338,18 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
         order[g] = g;
     }
     std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return cost[a] > cost[b]; });
+    if (cp) {
+        int len = 1;
+        for (const auto& g : lgroups) {
+            int kmax = 1;
+            for (int i : g) kmax = std::max(kmax, inst[i].k);
+            const int iters = op->max_iter > 0 ? std::min(kmax, op->max_iter) : kmax;
+            len = std::max(len, (cp->reset_adam_each_iter ? 1 : iters) * std::max(cp->steps, 1));
+        }
+        cs_status st = ensure_tab(P, len);
+        if (st != CS_OK) return st;
+        CS_TRY_LAUNCH(launch_adam_table(P->tab, len, cp->lr, cp->beta1, cp->beta2, s), "adam table");
+    }
     cudaEvent_t start = pool_event(P);
     if (!start) return fail(CS_ECUDA, "varlen: no event");
     CS_TRY_LAUNCH(cudaEventRecord(start, s), "varlen start event");
@@ -1349,7 +1369,7 @@ cs_status solve_varlen(cs_plan* P, const cs_instance* inst, int count, const cs_
             std::vector<const float*> ys;
             std::vector<LargeOut> outs;
             group_args(g, ys, outs);
-            const cs_status st = solve_large_on(P, x0.A, x0.m, x0.n, x0.lda, ys, outs, op, nullptr, W.s, &W.ws,
+            const cs_status st = solve_large_on(P, x0.A, x0.m, x0.n, x0.lda, ys, outs, op, cp, W.s, &W.ws,
                                                 &W.bytes, false, &tune_mu);
             if (st != CS_OK) {
                 wst[w] = st;

@@ -161,6 +161,9 @@ struct LargeCall {
     // CLOMP in Gram form (NULL: plain OMP): steps, betas, eps, reset and the
     // Adam factor table (tab) of the solve
     const struct ClArgs* cl;
+    // 1: no cooperative launch (the solve runs beside others on the device:
+    // a cooperative grid's CTAs could not all be resident)
+    int no_coop;
     // device error flags (bit 32: a grid-wide barrier of the CLOMP fit gave up)
     unsigned* errflag;
 };
