@@ -50,7 +50,7 @@ namespace cs {
 namespace {
 
 constexpr int LG_SEG = 2048;           // rows per partial Gram dot product
-constexpr int LG_LC = 64;              // inner-index chunk of the float64 products
+constexpr int LG_LC = 32;              // inner-index chunk of the float64 products
 constexpr int LG_RQ = 32;              // support atoms per residual partial sum
 constexpr int LG_RESCORE_MIN_CTAS = 16;   // CTAs per signal re-scoring candidates: at least this,
                                           // else two per SM shared by the chunk's signals
@@ -747,7 +747,7 @@ __device__ void lg_pivot_finish(const LgState& S, int b, int t, double ssq, doub
 }
 
 // l = W^T g, l_p = sum_{i <= p} W_ip g_i, and the pivot: one warp per
-// (32 entries p, 64-entry chunk of i), lanes over p, partial sums per chunk.
+// (32 entries p, 32-entry chunk of i), lanes over p, partial sums per chunk.
 // The warp that completes a block of p sums its chunks in order (l_p) and
 // that block's sum l_p^2 and l_p z_p; the last block adds the blocks' sums
 // in order and finishes the pivot.  t = 0: one warp, no l.
@@ -836,7 +836,7 @@ __global__ void __launch_bounds__(32) k_lg_lpiv(LgState S, int t) {
 }
 
 // u = W l, u_i = sum_{p >= i} W_ip l_p, then the new column of W and
-// x += z_t w: one warp per (32 entries i, 64-entry chunk of p), lanes over
+// x += z_t w: one warp per (32 entries i, 32-entry chunk of p), lanes over
 // i; the warp that completes a block of i sums its chunks in order (from the
 // block's own chunk: earlier chunks hold no p >= i) and updates those
 // entries (t >= 1; W_tt and x_t come with the pivot).
