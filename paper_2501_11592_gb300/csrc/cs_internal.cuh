@@ -152,7 +152,7 @@ struct LargeCall {
     // measurement hook: called around each launch with (ctx, CS_PHASE_*, 0 before / 1 after)
     void (*mark)(void* ctx, int phase, int after);
     void* mark_ctx;
-    // correlation configuration (2 log2(signals per pass) + loads in flight - 1):
+    // correlation configuration (2 log2(signals per pass) of the streamed form):
     // corr_cfg >= 0 uses it; otherwise tune != 0 times the candidates on the
     // first iteration, else the widest that fits; the choice goes to *chosen_cfg
     int corr_cfg;
