@@ -317,7 +317,7 @@ def bench_large_1d(cs, torch, stream, barrier, rank, peaks_src):
                                               "bytes_per_launch": per_launch, "launches": n_c,
                                               "peak_source": f"hbm_gbs ({src})"}}
     # CLOMP (Gram form, 50 Adam steps per iteration at lr 1e-2), bf16 correlation:
-    # the benchmark spec's configuration for this signal
+    # the configuration the long 1-D CLOMP workload is stated for
     fn = lambda: cs.clomp_solve_batched(A, y, k, prec="bf16", form="gram", plan=plan, **CL)
     fn()
     barrier()
