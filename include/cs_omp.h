@@ -393,7 +393,7 @@ cs_status iht_solve_batched(cs_plan* plan, const float* A, int32_t m, int32_t n,
  * when a bounded wait inside a kernel gave up: 1, 2 the tensor-core
  * correlation's tile pipeline; 4, 8, 16 the persistent CLOMP solve's roles;
  * 32 the large-instance CLOMP fit's wait for other CTAs' coefficients; 64
- * the large-instance bf16 correlation's tile ring).
+ * the large-instance correlation's tile ring; 128 its tensor-core GEMM form).
  * reset != 0 zeroes them.  Returns CS_ETIMEOUT when out[1] != 0. */
 cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* stream);
 
