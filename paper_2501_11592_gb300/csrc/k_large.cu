@@ -5,10 +5,12 @@
 // sharing A runs as a sequence of grid-wide kernels per iteration of Eq. 2's
 // greedy loop, each signal with its own sparsity k:
 //
-//   correlation   c~ = A^T r streamed from HBM (bf16 copy of A, or the
-//                 caller's float32 A), r in shared memory, eight atoms per
-//                 warp, float32 accumulation; each warp folds the largest
-//                 unselected |c~| of every signal into a per-signal maximum;
+//   correlation   c~ = A^T r: A's copy (bf16, or float32) streamed from HBM
+//                 in 32 KB tiles through a shared-memory ring, r in shared
+//                 memory, float32 accumulation (k_lg_corr_tma); or, for
+//                 eight or more bf16 signals, one tcgen05 GEMM over bf16
+//                 residuals (k_lg_corr_mma); each signal's largest
+//                 unselected |c~| is folded into a per-signal maximum;
 //   selection     every unselected atom with |c~_j| >= max - 2 delta (delta
 //                 bounds |c~_j - c_j| for every atom, see below) is re-scored
 //                 in float32 against the caller's A by a whole CTA, and the
@@ -16,21 +18,24 @@
 //                 atomicMax of (value bits, ~atom) -- the float32 argmax over
 //                 all unselected atoms;
 //   Gram column   g_i = a_{S_i}^T a_j, ||a_j||^2 and a_j^T y in float32, each
-//                 dot product split into 2048-row segments summed afterwards
-//                 in segment order;
+//                 dot product split into 2048-row segments summed in segment
+//                 order by the warp that completes the entry;
 //   least squares the float64 update of W = L^{-T} of k_chol.cuh -- l = W^T g,
 //   (OMP)         pivot, z_t, u = W l, the new column of W, x += z_t w --
-//                 with both products split over the grid into partial sums
-//                 that are added in a fixed order;
+//                 both products as partial sums over 32-entry chunks, added
+//                 in chunk order by the warp that completes a block
+//                 (k_lg_lpiv, k_lg_uupd);
 //   CL fit        (CLOMP, Gram form) row t of G = A_S^T A_S and b_t = a_j^T y
 //   (CLOMP)       from the same Gram column, then the T Adam steps on
 //                 1/2 ||y - A_S s||^2 with gradient G s - b, one cooperative
 //                 launch per iteration whose CTAs keep their rows of G in
-//                 shared memory (see k_lgc_fit);
+//                 shared memory (see k_lgc_fit), or one launch per step;
 //   residual      r = y - A_S x (x as float32), partial sums over chunks of
-//                 32 support atoms added in chunk order, ||r|| from per-CTA
-//                 sums added in CTA order, the stopping rule of Eq. 2.
-// Every reduction has a fixed order, so a solve is deterministic.
+//                 32 support atoms added in chunk order, ||r|| from per-block
+//                 sums, the stopping rule of Eq. 2 (k_lg_resid).
+// The reductions across CTAs are last-arriver reductions: arrival counters
+// (reset by the last arriver) and a fixed summation order, no CTA waiting
+// for another, so a solve is deterministic.
 //
 // Certificate.  With bf16 A (unit roundoff 2^-8) and float32 accumulation
 // of N1 = m/32 + 13 terms per lane plus the warp tree, and the float32
@@ -38,7 +43,8 @@
 // for every atom |c~_j - c_j^{fp32}| <= delta =
 //   (2^-8 (1 + g1) + g1 + g2) max_j ||a_j|| ||r||,  g = N 2^-24 (1.01 margin),
 // so the atom whose re-scored |c| is largest has |c~| >= max|c~| - 2 delta.
-// The float32 path drops the 2^-8 term.
+// The float32 path drops the 2^-8 term; the GEMM form (both operands bf16)
+// uses 2^-7 + 2^-16 and m 2^-22 for the tensor core's accumulation.
 #include <algorithm>
 #include <map>
 #include <vector>
