@@ -63,7 +63,7 @@ def parse():
 
 PROFILE_CASES = ("omp_fp32", "omp_fp8", "clomp_bf16_per_iteration", "clomp_gather", "threshold", "single",
                  "clfit_pair", "columnwise_image", "large_small", "large_small_clomp", "large_mid", "large_1d",
-                 "large_group", "persist")
+                 "large_group", "iht", "persist")
 
 
 def profile_case(name):
@@ -110,6 +110,11 @@ def profile_case(name):
         # the full-size long signal (for a launch list of a few iterations only)
         pl = workloads.config_large_1d()
         cs.omp_solve_batched(dev(pl.A), dev(pl.Y), pl.k, prec="bf16", plan=cs.Plan(pl.m, pl.n, 1, pl.k))
+    elif name == "iht":
+        # IHT on the batched workload, 20 iterations, t = 1 / sigma_max(A)^2
+        p = workloads.config_batched()
+        step = float(np.float32(1.0 / np.linalg.norm(p.A, 2) ** 2))
+        cs.iht_solve_batched(dev(p.A), dev(p.Y), p.k, step, max_iter=20)
     elif name == "large_group":
         # one large class of the uneven batch: 72 signals sharing A (the GEMM correlation)
         p = workloads.random_problem(4336, 15360, 72, 40, seed=7, snr_db=30.0, values="pm")
