@@ -4,8 +4,10 @@
 // signal
 //   * forms u = s + t c for every atom (s dense, kept per signal) in shared
 //     memory;
-//   * finds the k-th largest |u| by bisection on its float32 bit pattern
-//     (non-negative floats order like their bits), 32 counting passes;
+//   * finds the k-th largest |u| from its float32 bit pattern (non-negative
+//     floats order like their bits) by a radix select: four passes of
+//     256-bin histograms over 8-bit digits, most significant first, each
+//     over the keys that match the digits found so far;
 //   * keeps the atoms above it and, of those equal to it, the lowest
 //     indices -- H_k with the lowest-index tie rule -- written in ascending
 //     index order with their values u_j, and clears the atoms it dropped;
@@ -18,15 +20,17 @@
 namespace cs {
 namespace {
 
-constexpr int IH_WARPS = 4;   // warps per CTA, each with n floats of shared memory
+constexpr int IH_WARPS = 4;   // warps per CTA, each with n floats and a 256-bin histogram of shared memory
+constexpr int IH_BINS = 256;
 
 template <int MCH>
 __global__ void __launch_bounds__(32 * IH_WARPS) k_iht_update(IterArgs a, const float* __restrict__ C, int ldc,
                                                              float* __restrict__ sd, float step, int it) {
-    extern __shared__ float sh_u[];   // [IH_WARPS][n]
+    extern __shared__ float sh_u[];   // [IH_WARPS][n], then [IH_WARPS][IH_BINS] counts
     pdl_wait();
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     float* u = sh_u + (size_t)w * a.n;
+    unsigned* hist = reinterpret_cast<unsigned*>(sh_u + (size_t)IH_WARPS * a.n) + w * IH_BINS;
     const int nwarps = gridDim.x * IH_WARPS;
     const unsigned lt = (1u << lane) - 1u;
     for (int b = blockIdx.x * IH_WARPS + w; b < a.B; b += nwarps) {
@@ -35,13 +39,56 @@ __global__ void __launch_bounds__(32 * IH_WARPS) k_iht_update(IterArgs a, const 
         const float* cb = C + (size_t)b * ldc;
         for (int j = lane; j < a.n; j += 32) u[j] = fmaf(step, cb[j], sb[j]);
         __syncwarp();
-        // T = the k-th largest key: the largest value with #{key >= T} >= k
-        unsigned T = 0;
-        for (int bit = 31; bit >= 0; --bit) {
-            const unsigned cand = T | (1u << bit);
-            int cnt = 0;
-            for (int j = lane; j < a.n; j += 32) cnt += (__float_as_uint(u[j]) & 0x7fffffffu) >= cand ? 1 : 0;
-            if (__reduce_add_sync(FULL, cnt) >= a.k) T = cand;
+        // T = the k-th largest key (the largest value with #{key >= T} >= k),
+        // one 8-bit digit per pass: among the keys whose higher digits equal
+        // T's, the digit d with #{digit > d} < need <= #{digit >= d}
+        unsigned T = 0, hi_mask = 0;
+        int rem = a.k;                                     // rank of T among the keys still matching
+        for (int shift = 24; shift >= 0; shift -= 8) {
+            for (int q = lane; q < IH_BINS; q += 32) hist[q] = 0u;
+            __syncwarp();
+            for (int j = lane; j < a.n; j += 32) {
+                const unsigned key = __float_as_uint(u[j]) & 0x7fffffffu;
+                if ((key & hi_mask) == T) atomicAdd(&hist[(key >> shift) & 255u], 1u);
+            }
+            __syncwarp();
+            // lane l holds bins 8l .. 8l + 7; counts above each lane's bins by a suffix scan
+            unsigned c[8], sum = 0;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                c[q] = hist[8 * lane + q];
+                sum += c[q];
+            }
+            unsigned incl = sum;                           // keys in this lane's bins and above
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const unsigned v = __shfl_down_sync(FULL, incl, o);
+                if (lane + o < 32) incl += v;
+            }
+            const unsigned above = incl - sum;             // keys in the bins of higher lanes
+            // the lane whose bins hold the rem-th largest key: above < rem <= above + sum
+            const bool mine = above < (unsigned)rem && (unsigned)rem <= above + sum;
+            const unsigned owner = __ballot_sync(FULL, mine);
+            const int L = __ffs(owner) - 1;
+            int d = 0;
+            unsigned gt = 0;                               // keys with a larger digit
+            if (lane == L) {
+                unsigned acc = above;
+                for (int q = 7; q >= 0; --q) {
+                    if (acc + c[q] >= (unsigned)rem) {
+                        d = 8 * lane + q;
+                        break;
+                    }
+                    acc += c[q];
+                }
+                gt = acc;
+            }
+            d = __shfl_sync(FULL, d, L);
+            gt = __shfl_sync(FULL, gt, L);
+            T |= (unsigned)d << shift;
+            hi_mask |= 255u << shift;
+            rem -= (int)gt;
+            __syncwarp();
         }
         int gt = 0;
         for (int j = lane; j < a.n; j += 32) gt += (__float_as_uint(u[j]) & 0x7fffffffu) > T ? 1 : 0;
@@ -104,10 +151,10 @@ __global__ void __launch_bounds__(32 * IH_WARPS) k_iht_update(IterArgs a, const 
 
 template <int MCH>
 cudaError_t launch_m(const IterArgs& a, const float* C, int ldc, float* sd, float step, int it, cudaStream_t s) {
-    const size_t smem = sizeof(float) * IH_WARPS * (size_t)a.n;
+    const size_t smem = sizeof(float) * IH_WARPS * (size_t)a.n + sizeof(unsigned) * IH_WARPS * IH_BINS;
     static const cudaError_t attr =
         cudaFuncSetAttribute(k_iht_update<MCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float) * IH_WARPS * kIhtMaxN));
+                             (int)(sizeof(float) * IH_WARPS * kIhtMaxN + sizeof(unsigned) * IH_WARPS * IH_BINS));
     if (attr != cudaSuccess) return attr;
     const int grid = std::min(ceil_div(a.B, IH_WARPS), 65535);   // warps stride over the signals
     return launch_pdl(k_iht_update<MCH>, dim3(grid), dim3(32 * IH_WARPS), smem, s, a, C, ldc, sd, step, it);
