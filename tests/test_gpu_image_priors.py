@@ -147,11 +147,11 @@ def test_image_prior_limits(cs_gpu, torch):
 LV_EPS = 1e-4          # the binding's default smoothing of the window deviation
 
 
-def oracle_img(A64, Y64, k, W, tv=0.0, lv=0.0, D64=None, **kw):
+def oracle_img(A64, Y64, k, W, tv=0.0, lv=0.0, D64=None, lv_eps=LV_EPS, **kw):
     p = {q: f32(v) for q, v in CL.items() if q != "steps"}
     p.update({q: f32(v) for q, v in kw.items() if q in p})
     return oracle.clomp(A64, Y64, k, steps=kw.get("steps", CL["steps"]), tv_weight=f32(tv),
-                        lv_weight=f32(lv), lv_eps=f32(LV_EPS), D=D64, image_width=W, **p)
+                        lv_weight=f32(lv), lv_eps=f32(lv_eps), D=D64, image_width=W, **p)
 
 
 @pytest.mark.parametrize("W,images,tv,lv", [(24, 3, 0.0, 0.5), (24, 3, 0.5, 0.5), (40, 2, 0.0, 1.0),
@@ -166,6 +166,27 @@ def test_local_variation_without_basis(cs_gpu, torch, W, images, tv, lv):
     g = gpu_solve(cs_gpu, torch, A32, Y32, k, W, tv_weight=tv, lv_weight=lv)
     assert g["launches"]["persist"] == 0 and g["launches"]["fit"] == k
     print(compare(g, oracle_img(A64, Y64, k, W, tv=tv, lv=lv)))
+
+
+@pytest.mark.parametrize("W,images,tv,lv", [(24, 3, 0.5, 0.5), (40, 2, 0.0, 1.0), (3, 5, 0.0, 2.0)])
+def test_local_variation_plain_deviation_without_basis(cs_gpu, torch, W, images, tv, lv):
+    """Eq. 7 as printed (eps = 0, the plain sample deviation) where it is
+    well-conditioned: with x = s the pixels off the support are exact zeros,
+    so a window is either exactly constant (no gradient on either side) or
+    holds a support pixel and has a deviation of the order of the
+    coefficients.  The test first checks that conditioning on the oracle (a
+    1e-7 relative change of Y leaves its supports in place and moves its
+    coefficients by < 1e-6), then compares."""
+    k = 8
+    p = workloads.random_problem(64, 200, W * images, k, seed=180 + W, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    o = oracle_img(A64, Y64, k, W, tv=tv, lv=lv, lv_eps=0.0)
+    rng = np.random.default_rng(189)
+    o2 = oracle_img(A64, Y64 * (1 + 1e-7 * rng.standard_normal(Y64.shape)), k, W, tv=tv, lv=lv, lv_eps=0.0)
+    assert np.array_equal(o["support"], o2["support"])
+    assert np.max(np.linalg.norm(o["coef"] - o2["coef"], axis=1) / np.linalg.norm(o["coef"], axis=1)) < 1e-6
+    g = gpu_solve(cs_gpu, torch, A32, Y32, k, W, tv_weight=tv, lv_weight=lv, lv_eps=0.0)
+    print(compare(g, o))
 
 
 def test_local_variation_columnwise_dct_strip(cs_gpu, torch):
