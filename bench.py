@@ -383,6 +383,21 @@ def bench_large_1d(cs, torch, stream, barrier, rank, peaks_src):
     return res
 
 
+def uneven_class_roofline(m, n, kss, seconds, tc_tflops, hbm_gbs):
+    """Roofline of one size class of the uneven batch solved on its own: its
+    correlation flops (2 m n k per instance) against min(tensor peak, AI x
+    HBM), AI = those flops over the algorithmic bytes -- A's bf16 copy read
+    once per iteration, k_max iterations."""
+    flops = sum(2.0 * m * n * k for k in kss)
+    bytes_a = 2.0 * m * n * max(kss)
+    ai = flops / bytes_a
+    roof = min(tc_tflops, ai * hbm_gbs / 1e3)
+    ach = flops / seconds / 1e12
+    return {"m": m, "n": n, "instances": len(kss), "k_max": max(kss), "ms": 1e3 * seconds,
+            "tflops": ach, "ai_flop_per_byte": ai, "bound": "hbm" if roof < tc_tflops else "tensor",
+            "roof_tflops": roof, "frac": ach / roof, "a_stream_gbs": bytes_a / seconds / 1e9}
+
+
 def bench_uneven(cs, torch, stream, barrier):
     """The uneven batch (2000 instances in 32 size classes, n in [512, 16384],
     m/n in [0.1, 0.5], k = 1-10 % of n) through omp_solve_varlen: instances
@@ -417,6 +432,30 @@ def bench_uneven(cs, torch, stream, barrier):
         res["omp_" + prec] = {"s_per_batch": wall, "instances_per_s": len(items) / wall,
                               "solved": int(np.sum(st != cs.SIG_UNSUPPORTED)), "refused": int(np.sum(st == cs.SIG_UNSUPPORTED)),
                               "note": "wall clock of one call (on-chip groups one after another; plain-OMP large groups up to four at once on their own streams, each synchronising every 64 iterations)"}
+    # bf16 OMP one size class per call (the plan is tuned by the calls above):
+    # each class's roofline, and the aggregate of the one-call time above
+    peaks, src = measured_peaks()
+    per_class = []
+    for c, cl in enumerate(classes):
+        idx = [i for i in range(len(assign)) if assign[i] == c]
+        if not idx:
+            continue
+        sub = [items[i] for i in idx]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        cs.omp_solve_varlen(sub, prec="bf16", plan=plan)
+        torch.cuda.synchronize()
+        per_class.append(uneven_class_roofline(cl["m"], cl["n"], [ks[i] for i in idx], time.perf_counter() - t0,
+                                               peaks["bf16_tflops"], peaks["hbm_gbs"]))
+    agg_s = res["omp_bf16"]["s_per_batch"]
+    res["roofline_omp_bf16"] = {
+        "per_class": per_class,
+        "sum_of_class_seconds": sum(q["ms"] for q in per_class) / 1e3,
+        "aggregate": {"tflops": work / agg_s / 1e12, "unit": "TFLOP/s",
+                      "frac_of_tensor_peak": work / agg_s / 1e12 / peaks["bf16_tflops"],
+                      "a_stream_gbs": sum(2.0 * q["m"] * q["n"] * q["k_max"] for q in per_class) / agg_s / 1e9},
+        "peak_source": f"bf16_tflops burst, hbm_gbs ({src})",
+        "note": "wall clock per class (host-timed, one call each); AI = correlation flops over A's bf16 copy read once per iteration"}
     fn = lambda: cs.clomp_solve_varlen(items, prec="bf16", plan=plan, **CL)
     outs = fn()
     barrier()
