@@ -227,6 +227,7 @@ cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cu
     int rpt = std::min(4, 128 / kt);
     while (rpt > 1 && a.m <= 32 * (rpt / 2)) rpt /= 2;
     while (rpt < 4 && ceil_div(a.m, rpt) > GF_MAXT) rpt *= 2;
+    if (ceil_div(a.m, rpt) > GF_MAXT) return cudaErrorInvalidValue;   // m > 4 * GF_MAXT: not an on-chip size
     const int nth = std::min(GF_MAXT, round_up(ceil_div(a.m, rpt), 32));
 #define CS_GATHER_LAUNCH(KT_)                                                                     \
     do {                                                                                          \
