@@ -69,6 +69,16 @@ def test_ragged_sizes(cs_gpu, torch, algo, form):
     print(algo, form, s)
 
 
+@pytest.mark.parametrize("m,k", [(600, 30), (600, 40)])
+def test_gather_form_long_columns(cs_gpu, torch, m, k):
+    """The gather-form fit beyond 256 rows (float32 correlation): four rows
+    per thread over 150 threads, support tiles up to 32 and up to 64."""
+    p = workloads.random_problem(m, 900, 24, k, seed=13 + k, snr_db=30.0, values="pm")
+    A32, Y32, A64, Y64 = f32_problem(p.A, p.Y)
+    g = run_gpu(cs_gpu, torch, A32, Y32, p.k, "clomp", prec="fp32", form="gather", **CL)
+    print(compare(g, run_oracle(A64, Y64, p.k, "clomp")))
+
+
 _BATCHED_ORACLE = {}
 
 
