@@ -412,7 +412,9 @@ cs_status cs_plan_counters(cs_plan* plan, uint32_t* out, int32_t reset, void* st
  * of that device (cudaDeviceReset).  Calls whose GPU work overlaps -- on
  * different streams or threads -- race on the shared array.  Each call
  * clears the device counters (certificate fallbacks, error flags) when it
- * starts; omp_solve_batched_noalloc_counters reads them. */
+ * starts; omp_solve_batched_noalloc_counters reads them.  It tunes no tile
+ * shape (the default tile gives the same results as a tuned one), so a call
+ * creates no CUDA events and does not wait on the stream. */
 cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_t n, int32_t lda,
                                     const float* Y, int32_t ldy, int32_t batch, int32_t* support,
                                     float* coef, int32_t* n_iter, float* res_norm,

@@ -1828,6 +1828,10 @@ extern "C" cs_status omp_solve_batched_noalloc(const float* A, int32_t m, int32_
     if (st != CS_OK) return st;
     P.device = dev;
     P.use_graphs = 0;
+    // No tile tuning: this plan lives for one call, so tuning would time the
+    // candidates (a stream synchronisation and two events) on every call.
+    // The default tile computes the same bits as every other.
+    P.autotune = 0;
     bind_workspace(&P, base + kNoAllocCounterBytes, L);
     P.counters = reinterpret_cast<unsigned*>(base);
     // The previous call's counters must not leak into this one.
