@@ -606,6 +606,11 @@ cudaError_t timed(cs_plan* P, int phase, cudaStream_t s, F&& launch) {
     P->launches[phase] += 1;
     if (!P->profiling) return launch();
     cudaEvent_t a = pool_event(P), b = pool_event(P);
+    if (!(a && b)) {            // no pair: untimed (the one event made goes back)
+        if (a) P->pool.push_back(a);
+        if (b) P->pool.push_back(b);
+        a = b = nullptr;
+    }
     if (a && b) cudaEventRecord(a, s);
     cudaError_t e = launch();
     if (a && b) {
@@ -631,7 +636,11 @@ int autotune(cs_plan* P, const std::string& key, int ncand, L&& launch, cudaStre
     cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) return fallback;
     cudaEvent_t e0 = pool_event(P), e1 = pool_event(P);
-    if (!e0 || !e1) return fallback;
+    if (!e0 || !e1) {
+        if (e0) P->pool.push_back(e0);
+        if (e1) P->pool.push_back(e1);
+        return fallback;
+    }
     int best = -1;
     float best_ms = 0.f;
     for (int c = 0; c < ncand; ++c) {
