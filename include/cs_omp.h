@@ -232,8 +232,10 @@ cs_status clomp_solve(cs_plan* plan, const float* A, int32_t m, int32_t n, int32
 /* Host-buffer forms of the batched solvers: every array pointer is a HOST
  * pointer (pinned memory gives the fastest copies).  The call copies A and Y
  * into plan-owned device buffers, solves on `stream`, copies the five
- * outputs back and synchronises `stream` before returning.  The plan must
- * have been created with room for the inputs (as for the device forms). */
+ * outputs back and synchronises `stream` before returning -- also when the
+ * solve fails after the input copies were issued, so the caller's buffers
+ * are free to reuse on any return.  The plan must have been created with
+ * room for the inputs (as for the device forms). */
 cs_status omp_solve_batched_host(cs_plan* plan, const float* A, int32_t m, int32_t n,
                                  int32_t lda, const float* Y, int32_t ldy, int32_t batch,
                                  int32_t* support, float* coef, int32_t* n_iter,

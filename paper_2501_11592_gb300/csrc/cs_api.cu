@@ -1064,7 +1064,10 @@ cs_status solve_host(cs_plan* P, const float* A, int m, int n, int lda, const fl
     P->a_host = A;
     st = solve(P, dA, m, n, m, dY, m, B, dS, dC, dN, dR, dT, op, cp, s);
     P->a_host = nullptr;
-    if (st != CS_OK) return st;
+    if (st != CS_OK) {
+        cudaStreamSynchronize(s);   // the copies of the caller's A and Y have finished on return
+        return st;
+    }
     CS_TRY_LAUNCH(cudaMemcpyAsync(support, dS, sizeof(int32_t) * k * B, cudaMemcpyDeviceToHost, s), "copy support");
     CS_TRY_LAUNCH(cudaMemcpyAsync(coef, dC, sizeof(float) * k * B, cudaMemcpyDeviceToHost, s), "copy coef");
     CS_TRY_LAUNCH(cudaMemcpyAsync(n_iter, dN, sizeof(int32_t) * B, cudaMemcpyDeviceToHost, s), "copy n_iter");
