@@ -240,6 +240,12 @@ cudaError_t clfit_image_prepare(int W, bool lv, int H, int* ok);
 cudaError_t launch_clfit_image(const IterArgs& a, const ClArgs& c, int iter, int W, float lam_h, float lv_scale,
                                float lv_eps, const float* D, int H, int ldd, cudaStream_t s);
 cudaError_t launch_clfit_gather(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
+
+// Raises `kernel`'s dynamic shared-memory limit to `bytes` on the current
+// device, once per (device, kernel, bytes): a kernel attribute belongs to the
+// device's context, so every device that launches the kernel needs its own.
+// Thread-safe.
+cudaError_t set_smem_limit(const void* kernel, int bytes);
 bool update_clomp_fused_supported(const IterArgs& a);
 cudaError_t launch_update_clomp(const IterArgs& a, const ClArgs& c, int iter, cudaStream_t s);
 // Threshold rule (0 < c.th < 1): one iteration's selection, Gram-form fit,

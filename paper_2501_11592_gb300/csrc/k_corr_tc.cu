@@ -317,13 +317,8 @@ cudaError_t launch_tc(const void* R, const void* A, int rowlen, int B, int n, Tc
     if (!make_map(&mR, R, rowlen, B, rb, TM, FP8) || !make_map(&mA, A, rowlen, n, rb, TN, FP8))
         return cudaErrorInvalidValue;
     const size_t smem = std::max(smem_bytes(p.kc, TN), (size_t)(TN == 256 ? 100 : 50) * 1024);
-    static int configured = 0;
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(k_corr_tc<FP8, TN>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem_bytes(MAX_KC, TN));
-        if (e != cudaSuccess) return e;
-        configured = 1;
-    }
+    const cudaError_t e = set_smem_limit((const void*)k_corr_tc<FP8, TN>, (int)smem_bytes(MAX_KC, TN));
+    if (e != cudaSuccess) return e;
     dim3 grid(ceil_div(B, TM), ceil_div(n, TN));
     return launch_pdl(k_corr_tc<FP8, TN>, grid, dim3(NTHREADS), smem, s, mR, mA, p);
 }

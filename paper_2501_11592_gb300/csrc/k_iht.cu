@@ -152,9 +152,9 @@ __global__ void __launch_bounds__(32 * IH_WARPS) k_iht_update(IterArgs a, const 
 template <int MCH>
 cudaError_t launch_m(const IterArgs& a, const float* C, int ldc, float* sd, float step, int it, cudaStream_t s) {
     const size_t smem = sizeof(float) * IH_WARPS * (size_t)a.n + sizeof(unsigned) * IH_WARPS * IH_BINS;
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(k_iht_update<MCH>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)(sizeof(float) * IH_WARPS * kIhtMaxN + sizeof(unsigned) * IH_WARPS * IH_BINS));
+    const cudaError_t attr =
+        set_smem_limit((const void*)k_iht_update<MCH>,
+                       (int)(sizeof(float) * IH_WARPS * kIhtMaxN + sizeof(unsigned) * IH_WARPS * IH_BINS));
     if (attr != cudaSuccess) return attr;
     const int grid = std::min(ceil_div(a.B, IH_WARPS), 65535);   // warps stride over the signals
     return launch_pdl(k_iht_update<MCH>, dim3(grid), dim3(32 * IH_WARPS), smem, s, a, C, ldc, sd, step, it);

@@ -1331,8 +1331,7 @@ cudaError_t launch_corr_tma(const LgState& S, cudaStream_t s) {
     const int stages = lg_tma_stages(S, NB);
     if (stages == 0) return cudaErrorInvalidValue;
     const size_t smem = lg_tma_smem(stages, NB, S.mpt);
-    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr_tma<T, NB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   S.smem_optin);
+    const cudaError_t attr = set_smem_limit((const void*)k_lg_corr_tma<T, NB>, S.smem_optin);
     if (attr != cudaSuccess) return attr;
     const int npass = ceil_div(S.Bl, NB);
     cudaError_t e = cudaMemsetAsync(S.cblk, 0, sizeof(int) * npass, s);
@@ -1364,8 +1363,7 @@ cudaError_t setup_corr_mma(const LgState& S, LgMma& M) {
     M.smem = (size_t)M.stages * stage_bytes + 1024;
     if (!make_tma_map_bf16(&M.mapR, S.R16, S.mpk, S.Bl, (size_t)S.mpk * 2, M.N))
         return cudaErrorInvalidValue;
-    static cudaError_t attr = cudaFuncSetAttribute(k_lg_corr_mma, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
-    return attr;
+    return set_smem_limit((const void*)k_lg_corr_mma, dyn_max);
 }
 
 cudaError_t launch_corr_mma(const LgState& S, const LgMma& M, cudaStream_t s) {

@@ -362,8 +362,7 @@ __global__ void __launch_bounds__(OF_THREADS) k_omp_fused(IterArgs a, const floa
 
 template <int MCH>
 cudaError_t launch_m(const IterArgs& a, const float* Ac, int lda, const float* Yc, int ldy, cudaStream_t s) {
-    static const cudaError_t attr =
-        cudaFuncSetAttribute(k_omp_fused<MCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, OF_MAX_SMEM);
+    const cudaError_t attr = set_smem_limit((const void*)k_omp_fused<MCH>, OF_MAX_SMEM);
     if (attr != cudaSuccess) return attr;
     const size_t smem = of_state(a.kmax, a.mp, a.nw) +
                         (of_a_fits(a.kmax, a.mp, a.nw, a.n) ? of_resident_a(a.mp, a.n) : 0);

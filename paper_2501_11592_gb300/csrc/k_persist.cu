@@ -686,15 +686,13 @@ bool clomp_persist_supported(const IterArgs& a, const ClArgs& c) {
 namespace {
 
 template <int KB>
-cudaError_t configure_once() {
-    static const cudaError_t st =
-        cudaFuncSetAttribute(k_clomp_persist<KB>, cudaFuncAttributeMaxDynamicSharedMemorySize, PS_SMEM);
-    return st;
+cudaError_t configure_smem() {
+    return set_smem_limit((const void*)k_clomp_persist<KB>, PS_SMEM);
 }
 
 template <int KB>
 cudaError_t launch_kb(const IterArgs& a, const ClArgs& c, int stall, cudaStream_t s) {
-    cudaError_t e = configure_once<KB>();
+    cudaError_t e = configure_smem<KB>();
     if (e != cudaSuccess) return e;
     PsArgs p{};
     p.a = a;

@@ -2,6 +2,8 @@
 // residuals, the Gram matrix of A, the initial per-signal state (r = y,
 // s = 0, empty support, status "running") and the Adam bias-correction table.
 #include <mutex>
+#include <set>
+#include <tuple>
 #include <unordered_map>
 
 #include "k_common.cuh"
@@ -384,6 +386,19 @@ int resident_grid(const void* kernel, int block, int needed) {
     }
     const long long g = (long long)per_sm * sms;
     return (int)(g < needed ? g : needed);
+}
+
+cudaError_t set_smem_limit(const void* kernel, int bytes) {
+    static std::mutex mu;
+    static std::set<std::tuple<int, const void*, int>> done;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    std::lock_guard<std::mutex> lk(mu);
+    if (done.count(std::make_tuple(dev, kernel, bytes))) return cudaSuccess;
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess) done.insert(std::make_tuple(dev, kernel, bytes));
+    return e;
 }
 
 }  // namespace cs
