@@ -144,9 +144,26 @@ def _stream_ptr(stream=None):
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def _require_cuda(*xs):
+    """Every given tensor is a CUDA tensor and all are on one device: the
+    library reads its arguments on the GPU, where a host address faults."""
+    dev = None
+    for x in xs:
+        if x is None:
+            continue
+        if not getattr(x, "is_cuda", False):
+            raise ValueError("expected CUDA tensors (host arrays go through the *_host entry points)")
+        if dev is None:
+            dev = x.device
+        elif x.device != dev:
+            raise ValueError(f"tensors on {dev} and {x.device}: every argument must be on one device")
+    return dev
+
+
 def _colmajor(x, dtype):
     """(rows, cols) tensor with contiguous columns (stride (1, ld)), on its device."""
     torch = _torch()
+    _require_cuda(x)
     if x.dim() == 1:
         x = x.reshape(-1, 1)
     if x.dtype != dtype:
@@ -288,6 +305,7 @@ def _batched(fn, A, Y, k, params, plan, stream, out):
         raise ValueError(f"Y has {Y.shape[0]} rows, A has {m}")
     p = _plan_for(m, n, B, k, plan)
     o = out if out is not None else _outputs(B, k, A.device)
+    _require_cuda(A, Y, o.support, o.coef, o.n_iter, o.res_norm, o.status)
     _check(fn(p.h, ctypes.c_void_p(A.data_ptr()), m, n, _ld(A), ctypes.c_void_p(Y.data_ptr()), m if B <= 1 else _ld(Y),
               B, ctypes.c_void_p(o.support.data_ptr()), ctypes.c_void_p(o.coef.data_ptr()),
               ctypes.c_void_p(o.n_iter.data_ptr()), ctypes.c_void_p(o.res_norm.data_ptr()),
@@ -314,6 +332,7 @@ def clomp_solve_batched(A, Y, k, tol=0.0, max_iter=None, prec="fp32", topc=8, st
     variation of Eq. 7 over those images (any D), each window's deviation
     smoothed as sqrt(var + lv_eps^2)."""
     Dt = None if D is None else _colmajor(D, _torch().float32)
+    _require_cuda(A, Y, Dt)
     return _batched(load().clomp_solve_batched, A, Y, k,
                     _clomp_params(k, tol, max_iter, prec, topc, steps, lr, beta1, beta2, eps,
                                   reset_adam, form, th, tv_weight, Dt, image_width, lv_weight, lv_eps), plan,
@@ -372,6 +391,8 @@ def _varlen(fn, instances, params, plan, stream):
     """instances: list of (A (m, n) column-major tensor, y (m,) tensor, k).
     Returns a list of Result (one signal each)."""
     torch = _torch()
+    for A, y, _ in instances:
+        _require_cuda(A, y)
     if plan is None:
         # instances beyond the kernels' limits are refused per instance
         # (SIG_UNSUPPORTED), so the default plan stops at those limits
@@ -412,6 +433,7 @@ def correlate(A, R, prec="fp32", plan=None, stream=None):
     torch = _torch()
     A = _colmajor(A, torch.float32)
     R = _colmajor(R, torch.float32)
+    _require_cuda(A, R)
     m, n = A.shape
     B = R.shape[1]
     p = _plan_for(m, n, B, 1, plan)
@@ -439,6 +461,7 @@ def synthesize(D, support, coef, n_iter, stream=None, n=None):
         N, n = D.shape
         Dp, ldd = ctypes.c_void_p(D.data_ptr()), _ld(D)
         dev = D.device
+    _require_cuda(D, support, coef, n_iter)
     support = support.to(torch.int32).contiguous()
     coef = coef.to(torch.float32).contiguous()
     n_iter = n_iter.to(torch.int32).contiguous()
@@ -457,6 +480,7 @@ def image_quality(X, Xref, W, peak=0.0, stream=None):
     torch = _torch()
     X = _colmajor(X, torch.float32)
     R = _colmajor(Xref, torch.float32)
+    _require_cuda(X, R)
     H = X.shape[0]
     if X.shape != R.shape or X.shape[1] % W:
         raise ValueError(f"X {tuple(X.shape)} and Xref {tuple(R.shape)} must match and hold whole H x {W} images")
@@ -500,6 +524,7 @@ def clfit_forward(A, S, Sv, Y, stream=None):
     torch = _torch()
     A = _colmajor(A, torch.float32)
     Y = _colmajor(Y, torch.float32)
+    _require_cuda(A, Y, S, Sv)
     m, n = A.shape
     S = S.to(torch.int32).contiguous()
     Sv = Sv.to(torch.float32).contiguous()
@@ -518,6 +543,7 @@ def clfit_adjoint(A, S, R, stream=None):
     torch = _torch()
     A = _colmajor(A, torch.float32)
     R = _colmajor(R, torch.float32)
+    _require_cuda(A, R, S)
     m, n = A.shape
     S = S.to(torch.int32).contiguous()
     B, t = S.shape
@@ -536,6 +562,7 @@ def clfit_adam_step(A, S, Sv, R, mom, vel, tau, lr=1e-2, beta1=0.9, beta2=0.999,
     A = _colmajor(A, torch.float32)
     R = _colmajor(R, torch.float32)
     m, n = A.shape
+    _require_cuda(A, R, S, Sv, mom, vel)
     S = S.to(torch.int32).contiguous()
     for x in (Sv, mom, vel):
         if x.dtype != torch.float32 or not x.is_contiguous():
