@@ -336,6 +336,43 @@ def test_clomp_first_iteration_is_adam_on_growing_mask():
     assert abs(float(torch.linalg.norm(r)) - o["res_norm"][0]) < 1e-12
 
 
+def test_clomp_reset_adam_is_a_fresh_optimizer_per_pick():
+    """The restart option: every iteration starts a new Adam (moments zero,
+    step counter back at 1) on the grown mask, while the coefficients carry
+    over -- a fresh torch optimizer per pick on the same parameter.  Its
+    result differs from the single-optimizer run, so the option matters."""
+    torch = pytest.importorskip("torch")
+    rng = np.random.default_rng(14)
+    A = _rand_A(rng, 24, 60)
+    X = workloads.sparse_coefficients(rng, 60, 1, 4, values="pm")
+    y = (A @ X)[:, 0]
+    T, k = 20, 4
+    o = oracle.clomp(A, y, k, steps=T, lr=5e-2, reset_adam=True)
+    S = o["support"][0]
+    p = torch.zeros(60, dtype=torch.float64, requires_grad=True)
+    At = torch.tensor(A, dtype=torch.float64)
+    yt = torch.tensor(y, dtype=torch.float64)
+    mask = torch.zeros(60, dtype=torch.float64)
+    r = yt.clone()
+    for t in range(k):
+        c = (At.T @ r).abs().numpy()
+        c[mask.numpy() > 0] = -1
+        assert int(np.argmax(c)) == S[t]
+        mask[S[t]] = 1.0
+        opt = torch.optim.Adam([p], lr=5e-2, foreach=False)
+        for _ in range(T):
+            opt.zero_grad()
+            loss = 0.5 * torch.sum((yt - At @ (p * mask)) ** 2)
+            loss.backward()
+            opt.step()
+        with torch.no_grad():
+            r = yt - At @ (p * mask)
+    assert np.allclose(p.detach().numpy()[S], o["coef"][0], atol=1e-12)
+    assert abs(float(torch.linalg.norm(r)) - o["res_norm"][0]) < 1e-12
+    one = oracle.clomp(A, y, k, steps=T, lr=5e-2, reset_adam=False)
+    assert np.max(np.abs(one["coef"][0] - o["coef"][0])) > 1e-6
+
+
 def test_clomp_orthonormal_decouples():
     """With orthonormal A the CL gradient of coordinate q is s_q - c_q
     (c = A^T y): every coordinate runs its own scalar Adam on 1/2(s - c)^2."""
