@@ -13,7 +13,8 @@ STRUCTS = {
     "cs_omp_params": ("OmpParams", ["k", "tol", "max_iter", "prec", "topc"]),
     "cs_clomp_params": ("ClompParams", ["base", "steps", "lr", "beta1", "beta2", "eps",
                                         "reset_adam_each_iter", "form", "select_threshold", "tv_weight",
-                                        "tv_D", "tv_N", "tv_ldd"]),
+                                        "tv_D", "tv_N", "tv_ldd", "image_width", "lv_weight", "lv_eps"]),
+    "cs_iht_params": ("IhtParams", ["k", "tol", "max_iter", "step"]),
     "cs_instance": ("Instance", ["A", "m", "n", "lda", "y", "k", "support", "coef", "n_iter", "res_norm",
                                  "sig_status"]),
 }
@@ -40,6 +41,7 @@ def test_struct_layouts_match(c_layout):
     import paper_2501_11592_gb300 as cs
     for cname, (pyname, fields) in STRUCTS.items():
         py = getattr(cs, pyname)
+        assert [f[0] for f in py._fields_] == fields, f"{pyname} fields differ from the checked list"
         assert ctypes.sizeof(py) == c_layout[f"{cname} size"], cname
         for f in fields or []:
             assert getattr(py, f).offset == c_layout[f"{cname}.{f}"], f"{cname}.{f}"
